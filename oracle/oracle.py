@@ -1,0 +1,214 @@
+"""ctypes wrapper of the plain CPU oracle (TEST INFRASTRUCTURE ONLY).
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg import
+this module.  It compiles ``orrb_oracle.c`` with gcc (fp32 forward with no
+FMA contraction, fp64 shading adjoint) and runs it over images with a pool of
+host threads; the C code releases nothing shared, so images are independent.
+
+Inputs are the numpy arrays of a ``scenegen.Batch``; outputs are numpy arrays
+laid out like the renderer's channels (flat over all pixels of all images).
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "orrb_oracle.c")
+HDR = os.path.join(HERE, "orrb_oracle.h")
+LIB = os.path.join(HERE, "_build", "liborrb_oracle.so")
+CFLAGS = ["-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-Wall"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle if the shared object is missing or older than its sources."""
+    os.makedirs(os.path.dirname(LIB), exist_ok=True)
+    stale = force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(SRC), os.path.getmtime(HDR))
+    if stale:
+        tmp = LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, SRC, "-lm"])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+class _Meshes(C.Structure):
+    _fields_ = [("n_meshes", C.c_int32), ("vert_offset", C.c_void_p), ("tri_offset", C.c_void_p),
+                ("pos", C.c_void_p), ("nrm", C.c_void_p), ("idx", C.c_void_p), ("tri_mat", C.c_void_p)]
+
+
+class _Batch(C.Structure):
+    _fields_ = [("n_samples", C.c_int32)] + [(n, C.c_void_p) for n in (
+        "inst_offset", "inst_mesh", "inst_pose", "inst_seg", "inst_mat_base",
+        "cam_offset", "cam_sample", "cam_view", "cam_intr", "cam_wh", "img_offset",
+        "light", "light_meta", "material", "exposure_ev", "ambient", "background")]
+
+
+class _Outputs(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in (
+        "rgb", "depth", "normal", "seg", "rgb_linear", "gb_pos", "gb_nrm", "gb_mat", "prim", "depth2", "counters")]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            L.orc_render.argtypes = [C.POINTER(_Meshes), C.POINTER(_Batch), C.c_int32, C.c_int32, C.POINTER(_Outputs)]
+            L.orc_render.restype = C.c_int
+            L.orc_raster_fixed.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                           C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
+            L.orc_raster_fixed.restype = C.c_int
+            L.orc_f32_to_f16.argtypes = [C.c_float]
+            L.orc_f32_to_f16.restype = C.c_uint16
+            L.orc_shade_f64.argtypes = [C.POINTER(_Batch), C.c_int32, C.c_int32] + [C.c_void_p] * 8
+            L.orc_shade_f64.restype = None
+            L.orc_shade_backward_f64.argtypes = [C.POINTER(_Batch), C.c_int32, C.c_int32] + [C.c_void_p] * 11
+            L.orc_shade_backward_f64.restype = None
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+class _Pinned:
+    """Keeps the contiguous numpy copies alive while C holds their pointers."""
+
+    def __init__(self, batch):
+        ms = batch.meshes
+        self.vo = _c(np.concatenate([[0], np.cumsum([m.n_verts for m in ms])]), np.int32)
+        self.to = _c(np.concatenate([[0], np.cumsum([m.n_tris for m in ms])]), np.int32)
+        self.pos = _c(np.concatenate([m.pos for m in ms]), np.float32)
+        self.nrm = _c(np.concatenate([m.nrm for m in ms]), np.float32)
+        self.idx = _c(np.concatenate([m.idx for m in ms]), np.uint32)
+        self.tm = _c(np.concatenate([m.tri_mat for m in ms]), np.uint8)
+        self.meshes = _Meshes(len(ms), _p(self.vo), _p(self.to), _p(self.pos), _p(self.nrm), _p(self.idx), _p(self.tm))
+        self.arrs = dict(
+            inst_offset=_c(batch.inst_offset, np.int32), inst_mesh=_c(batch.inst_mesh, np.uint32),
+            inst_pose=_c(batch.inst_pose, np.float32), inst_seg=_c(batch.inst_seg, np.uint8),
+            inst_mat_base=_c(batch.inst_mat_base, np.int16), cam_offset=_c(batch.cam_offset, np.int32),
+            cam_sample=_c(batch.cam_sample, np.int32), cam_view=_c(batch.cam_view, np.float32),
+            cam_intr=_c(batch.cam_intr, np.float32), cam_wh=_c(batch.cam_wh, np.int32),
+            img_offset=_c(batch.img_offset, np.int64), light=_c(batch.light, np.float32),
+            light_meta=_c(batch.light_meta, np.int32), material=_c(batch.material, np.float32),
+            exposure_ev=_c(batch.exposure_ev, np.float32), ambient=_c(batch.ambient, np.float32),
+            background=_c(batch.background, np.float32))
+        self.batch = _Batch(batch.n_samples, *[_p(self.arrs[n]) for n, _ in _Batch._fields_[1:]])
+
+
+def _chunks(n_cams: int, threads: int):
+    k = max(1, min(n_cams, threads * 4))
+    edges = np.linspace(0, n_cams, k + 1).astype(int)
+    return [(int(a), int(b)) for a, b in zip(edges[:-1], edges[1:]) if b > a]
+
+
+def default_threads() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def render(batch, threads: int | None = None, gbuffer: bool = False, debug: bool = False, cams=None):
+    """Oracle render of a batch.  Returns a dict of numpy channel arrays.
+
+    `cams`: optional (begin, end) camera range; pixels of other images stay zero.
+    """
+    L = lib()
+    pin = _Pinned(batch)
+    N = batch.total_pixels
+    out = dict(rgb=np.zeros((N, 3), np.uint8), depth=np.zeros(N, np.float32), normal=np.zeros((N, 3), np.uint16),
+               seg=np.zeros(N, np.uint8), rgb_linear=np.zeros((N, 3), np.float32))
+    if gbuffer:
+        out.update(gb_pos=np.zeros((N, 3), np.float32), gb_nrm=np.zeros((N, 3), np.float32),
+                   gb_mat=np.zeros(N, np.int32))
+    if debug:
+        out.update(prim=np.zeros(N, np.int64), depth2=np.zeros(N, np.float32))
+    threads = threads or default_threads()
+    c0, c1 = cams if cams is not None else (0, batch.n_cams)
+    chunks = [(a + c0, b + c0) for a, b in _chunks(c1 - c0, threads)]
+    counters = np.zeros((len(chunks), 4), np.int64)
+
+    def run(i):
+        o = _Outputs(*[_p(out.get(n)) for n, _ in _Outputs._fields_[:-1]], _p(counters[i]))
+        rc = L.orc_render(C.byref(pin.meshes), C.byref(pin.batch), chunks[i][0], chunks[i][1], C.byref(o))
+        if rc != 0:
+            raise MemoryError("oracle: allocation failed")
+
+    if threads == 1 or len(chunks) == 1:
+        for i in range(len(chunks)):
+            run(i)
+    else:
+        with ThreadPoolExecutor(threads) as ex:
+            list(ex.map(run, range(len(chunks))))
+    out["counters"] = counters.sum(0)
+    return out
+
+
+def raster_fixed(W: int, H: int, X, Y, iw, ortho: bool = False):
+    """Coverage/visibility of snapped triangles.
+
+    Returns (key [H,W] int64, depth [H,W] f32, fragment count [H,W] int32)."""
+    X = _c(X, np.int32).reshape(-1, 3)
+    Y = _c(Y, np.int32).reshape(-1, 3)
+    iw = _c(iw, np.float32).reshape(-1, 3)
+    prim = np.zeros(W * H, np.int64)
+    depth = np.zeros(W * H, np.float32)
+    count = np.zeros(W * H, np.int32)
+    rc = lib().orc_raster_fixed(W, H, len(X), _p(X), _p(Y), _p(iw), int(ortho), _p(prim), _p(depth), _p(count))
+    assert rc == 0
+    return prim.reshape(H, W), depth.reshape(H, W), count.reshape(H, W)
+
+
+def f32_to_f16_bits(x) -> np.ndarray:
+    L = lib()
+    x = np.asarray(x, np.float32).reshape(-1)
+    return np.array([L.orc_f32_to_f16(float(v)) for v in x], np.uint16)
+
+
+def _params64(batch, material=None, light=None, exposure_ev=None, ambient=None):
+    m = _c(batch.material if material is None else material, np.float64)
+    l = _c(batch.light if light is None else light, np.float64)
+    e = _c(batch.exposure_ev if exposure_ev is None else exposure_ev, np.float64)
+    a = _c(batch.ambient if ambient is None else ambient, np.float64)
+    return m, l, e, a
+
+
+def shade_f64(batch, gb_pos, gb_nrm, gb_mat, material=None, light=None, exposure_ev=None, ambient=None):
+    """fp64 shading of a fixed G-buffer (the function finite differences are taken of)."""
+    pin = _Pinned(batch)
+    m, l, e, a = _params64(batch, material, light, exposure_ev, ambient)
+    gp, gn, gm = _c(gb_pos, np.float32), _c(gb_nrm, np.float32), _c(gb_mat, np.int32)
+    rgb = np.zeros((batch.total_pixels, 3), np.float64)
+    lib().orc_shade_f64(C.byref(pin.batch), 0, batch.n_cams, _p(gp), _p(gn), _p(gm), _p(m), _p(l), _p(e), _p(a), _p(rgb))
+    return rgb
+
+
+def shade_backward_f64(batch, gb_pos, gb_nrm, gb_mat, d_rgb, material=None, light=None, exposure_ev=None,
+                       ambient=None):
+    """fp64 adjoint: (d_material [S,32,4], d_light [S,4,4], d_ev [S])."""
+    pin = _Pinned(batch)
+    m, l, e, a = _params64(batch, material, light, exposure_ev, ambient)
+    gp, gn, gm = _c(gb_pos, np.float32), _c(gb_nrm, np.float32), _c(gb_mat, np.int32)
+    g = _c(d_rgb, np.float64)
+    S = batch.n_samples
+    dm = np.zeros((S, 32, 4), np.float64)
+    dl = np.zeros((S, 4, 4), np.float64)
+    de = np.zeros(S, np.float64)
+    lib().orc_shade_backward_f64(C.byref(pin.batch), 0, batch.n_cams, _p(gp), _p(gn), _p(gm), _p(m), _p(l), _p(e),
+                                 _p(a), _p(g), _p(dm), _p(dl), _p(de))
+    return dm, dl, de

@@ -1,0 +1,668 @@
+/*
+ * orrb_oracle.c -- plain CPU oracle of the batched renderer.
+ *
+ * TEST INFRASTRUCTURE ONLY (see orrb_oracle.h).  One image at a time, one
+ * triangle at a time, every pixel of the triangle's bounding box tested: no
+ * binning, no tiles, nothing shared with the CUDA path.
+ *
+ * What is computed (the paper fixes the channels -- RGB, segmentation, depth,
+ * screen-space normal, Sec. 4.4 -- and the randomized inputs, Sec. 4.3.1; it
+ * gives no rasterisation rule, so each numbered step below is the reading
+ * this project adopts):
+ *   1  world is z-up; the camera looks down -z with +y up; screen x right,
+ *      y down; pixel (x, y) has its centre at (x + 1/2, y + 1/2).
+ *   2  MV = V * M per (image, instance), fixed summation order; vertices and
+ *      normals go to view space with the same fixed order.
+ *   3  triangles are clipped against z <= -near (Sutherland-Hodgman); the
+ *      cut point is always interpolated from the inside vertex towards the
+ *      outside one, so two triangles sharing an edge cut it identically; the
+ *      cut is computed in fp64 and rounded once to fp32, with z = -near
+ *      exactly.  A clipped quad is split into (o0,o1,o2) sub 0 and
+ *      (o0,o2,o3) sub 1.
+ *   4  projection x_s = cx + fx*(x*iw), y_s = cy - fy*(y*iw), iw = 1/(-z)
+ *      (orthographic: x_s = cx + fx*x, y_s = cy - fy*y, depth -z); snapped
+ *      to 8 fractional bits with round-half-even; a triangle with a vertex
+ *      beyond |x_s|, |y_s| >= 2^20 px is dropped and counted.
+ *   5  integer edge functions E_ab(p) = (p.x-a.x)(b.y-a.y) - (p.y-a.y)(b.x-a.x)
+ *      in 64 bits; area A = E_01(v2); triangles with A <= 0 are culled.
+ *   6  pixel centre (256x+128, 256y+128) is covered iff every edge weight is
+ *      > 0, or == 0 on a top edge (dy == 0, dx < 0) or left edge (dy > 0).
+ *   7  depth = A / (w0*iw0 + w1*iw1 + w2*iw2) with the w_i, A converted to
+ *      float and summed left to right (orthographic: (w0*d0+w1*d1+w2*d2)/A).
+ *   8  the nearest fragment wins by (depth, key) ascending, key = 2*prim+sub,
+ *      prim = triangle index in the sample's concatenated triangle list.
+ *   9  G-buffer: P = depth*((x+1/2-cx)/fx, -(y+1/2-cy)/fy, -1); normal =
+ *      sum_i (w_i*iw_i) n_i normalised; material = base + tri_mat; seg id.
+ *  10  Blinn-Phong over the sample's lights, inverse-square falloff for
+ *      point lights, white specular, times 2^EV, plus ambient*albedo.
+ *  11  rgb8 = floor(clamp(rgb,0,1)*255 + 1/2); normal -> binary16 (RNE);
+ *      background: rgb = background colour, depth 0, normal 0, seg 0.
+ *  12  the adjoint of step 10 at fixed visibility, in fp64.
+ */
+#include "orrb_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define GUARD_PX 1048576.0f /* 2^20 */
+
+typedef struct {
+  float p[3];
+  float n[3];
+} vtx;
+
+typedef struct {
+  int64_t key;
+  float depth;
+  float depth2;
+  int32_t X[3], Y[3];
+  float iw[3];
+  float n[3][3];
+  int32_t mat;
+  int32_t seg;
+  int32_t count;
+} pixel_winner;
+
+/* ------------------------------------------------------------------ */
+/* step 2: MV = V * M with a fixed order of the sums                   */
+/* ------------------------------------------------------------------ */
+static void compose_mv(const float* V, const float* M, float* MV) {
+  for (int i = 0; i < 3; i++) {
+    for (int j = 0; j < 4; j++) {
+      float s = V[i * 4 + 0] * M[0 * 4 + j];
+      s = s + V[i * 4 + 1] * M[1 * 4 + j];
+      s = s + V[i * 4 + 2] * M[2 * 4 + j];
+      if (j == 3) s = s + V[i * 4 + 3];
+      MV[i * 4 + j] = s;
+    }
+  }
+}
+
+static vtx to_view(const float* MV, const float* p, const float* n) {
+  vtx v;
+  for (int i = 0; i < 3; i++) {
+    v.p[i] = ((MV[i * 4 + 0] * p[0] + MV[i * 4 + 1] * p[1]) + MV[i * 4 + 2] * p[2]) + MV[i * 4 + 3];
+    v.n[i] = (MV[i * 4 + 0] * n[0] + MV[i * 4 + 1] * n[1]) + MV[i * 4 + 2] * n[2];
+  }
+  return v;
+}
+
+/* ------------------------------------------------------------------ */
+/* step 3: near-plane clipping                                         */
+/* ------------------------------------------------------------------ */
+static vtx cut(const vtx* in, const vtx* out, float near) {
+  /* fp64, rounded once to fp32: an fp32 lerp leaves an absolute error of
+     the far vertex's magnitude, which seen from z = -near tilts the clipped
+     triangle by (error / near) radians */
+  double t = (-(double)near - (double)in->p[2]) / ((double)out->p[2] - (double)in->p[2]);
+  vtx r;
+  for (int k = 0; k < 3; k++) {
+    r.p[k] = (float)((double)in->p[k] + t * ((double)out->p[k] - (double)in->p[k]));
+    r.n[k] = (float)((double)in->n[k] + t * ((double)out->n[k] - (double)in->n[k]));
+  }
+  r.p[2] = -near; /* on the near plane by construction */
+  return r;
+}
+
+static int clip_near(const vtx* v, float near, vtx* o) {
+  int n = 0;
+  for (int k = 0; k < 3; k++) {
+    const vtx* a = &v[k];
+    const vtx* b = &v[(k + 1) % 3];
+    int ain = a->p[2] <= -near;
+    int bin = b->p[2] <= -near;
+    if (ain) o[n++] = *a;
+    if (ain && !bin) o[n++] = cut(a, b, near);
+    if (!ain && bin) o[n++] = cut(b, a, near);
+  }
+  return n;
+}
+
+/* ------------------------------------------------------------------ */
+/* step 5 helpers                                                      */
+/* ------------------------------------------------------------------ */
+static int64_t edge(int64_t ax, int64_t ay, int64_t bx, int64_t by, int64_t px, int64_t py) {
+  return (px - ax) * (by - ay) - (py - ay) * (bx - ax);
+}
+
+static int top_left(int64_t ax, int64_t ay, int64_t bx, int64_t by) {
+  int64_t dx = bx - ax, dy = by - ay;
+  return (dy == 0 && dx < 0) || dy > 0;
+}
+
+static int64_t floor_div(int64_t a, int64_t b) {
+  int64_t q = a / b;
+  if ((a % b != 0) && ((a < 0) != (b < 0))) q--;
+  return q;
+}
+
+/* Coverage and visibility of one snapped triangle (steps 5-8).
+ * Returns the number of covered pixels; updates the per-pixel winners. */
+static int64_t raster_triangle(int32_t W, int32_t H, const int32_t X[3], const int32_t Y[3],
+                               const float iw[3], int ortho, int64_t key, const float n[3][3],
+                               int32_t mat, int32_t seg, pixel_winner* px, int64_t* culled) {
+  int64_t A = edge(X[0], Y[0], X[1], Y[1], X[2], Y[2]);
+  if (A <= 0) {
+    if (culled) (*culled)++;
+    return 0;
+  }
+  int tl0 = top_left(X[1], Y[1], X[2], Y[2]);
+  int tl1 = top_left(X[2], Y[2], X[0], Y[0]);
+  int tl2 = top_left(X[0], Y[0], X[1], Y[1]);
+  int64_t xmin = X[0], xmax = X[0], ymin = Y[0], ymax = Y[0];
+  for (int k = 1; k < 3; k++) {
+    if (X[k] < xmin) xmin = X[k];
+    if (X[k] > xmax) xmax = X[k];
+    if (Y[k] < ymin) ymin = Y[k];
+    if (Y[k] > ymax) ymax = Y[k];
+  }
+  /* pixel x has its centre at 256x+128: candidates are the centres inside the box */
+  int64_t x0 = -floor_div(-(xmin - 128), 256), x1 = floor_div(xmax - 128, 256);
+  int64_t y0 = -floor_div(-(ymin - 128), 256), y1 = floor_div(ymax - 128, 256);
+  if (x0 < 0) x0 = 0;
+  if (y0 < 0) y0 = 0;
+  if (x1 > W - 1) x1 = W - 1;
+  if (y1 > H - 1) y1 = H - 1;
+  float fA = (float)A;
+  int64_t covered = 0;
+  for (int64_t y = y0; y <= y1; y++) {
+    for (int64_t x = x0; x <= x1; x++) {
+      int64_t cxp = 256 * x + 128, cyp = 256 * y + 128;
+      int64_t w0 = edge(X[1], Y[1], X[2], Y[2], cxp, cyp);
+      int64_t w1 = edge(X[2], Y[2], X[0], Y[0], cxp, cyp);
+      int64_t w2 = edge(X[0], Y[0], X[1], Y[1], cxp, cyp);
+      int in0 = w0 > 0 || (w0 == 0 && tl0);
+      int in1 = w1 > 0 || (w1 == 0 && tl1);
+      int in2 = w2 > 0 || (w2 == 0 && tl2);
+      if (!(in0 && in1 && in2)) continue;
+      float f0 = (float)w0, f1 = (float)w1, f2 = (float)w2;
+      float depth;
+      if (ortho) {
+        float s = (f0 * iw[0] + f1 * iw[1]) + f2 * iw[2];
+        depth = s / fA;
+      } else {
+        float s = (f0 * iw[0] + f1 * iw[1]) + f2 * iw[2];
+        depth = fA / s;
+      }
+      covered++;
+      pixel_winner* p = &px[y * W + x];
+      p->count++;
+      int wins = depth < p->depth || (depth == p->depth && key < p->key);
+      if (wins) {
+        if (p->key != key && p->depth < p->depth2) p->depth2 = p->depth;
+        p->key = key;
+        p->depth = depth;
+        for (int k = 0; k < 3; k++) {
+          p->X[k] = X[k];
+          p->Y[k] = Y[k];
+          p->iw[k] = iw[k];
+          if (n) {
+            p->n[k][0] = n[k][0];
+            p->n[k][1] = n[k][1];
+            p->n[k][2] = n[k][2];
+          }
+        }
+        p->mat = mat;
+        p->seg = seg;
+      } else if (key != p->key && depth < p->depth2) {
+        p->depth2 = depth;
+      }
+    }
+  }
+  return covered;
+}
+
+static void reset_winners(pixel_winner* px, int64_t n) {
+  for (int64_t i = 0; i < n; i++) {
+    px[i].key = -1;
+    px[i].depth = INFINITY;
+    px[i].depth2 = INFINITY;
+    px[i].mat = -1;
+    px[i].seg = 0;
+    px[i].count = 0;
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* step 11: binary16 encoding, round to nearest even                   */
+/* ------------------------------------------------------------------ */
+uint16_t orc_f32_to_f16(float f) {
+  uint32_t x;
+  memcpy(&x, &f, 4);
+  uint32_t sign = (x >> 16) & 0x8000u;
+  int32_t exp = (int32_t)((x >> 23) & 0xffu);
+  uint32_t man = x & 0x7fffffu;
+  if (exp == 0xff) return (uint16_t)(sign | 0x7c00u | (man ? 0x200u : 0u));
+  int32_t e = exp - 127 + 15;
+  if (e >= 31) return (uint16_t)(sign | 0x7c00u);
+  if (e <= 0) {
+    if (exp == 0) return (uint16_t)sign; /* fp32 zero or subnormal: far below binary16 range */
+    uint64_t M = (uint64_t)(man | 0x800000u);
+    int shift = 14 - e;
+    if (shift > 40) return (uint16_t)sign;
+    uint64_t m = M >> shift;
+    uint64_t rem = M & ((1ull << shift) - 1ull);
+    uint64_t half = 1ull << (shift - 1);
+    if (rem > half || (rem == half && (m & 1ull))) m++;
+    return (uint16_t)(sign | (uint32_t)m);
+  }
+  uint32_t h = ((uint32_t)e << 10) | (man >> 13);
+  uint32_t rem = man & 0x1fffu;
+  if (rem > 0x1000u || (rem == 0x1000u && (h & 1u))) h++;
+  return (uint16_t)(sign | h);
+}
+
+static uint8_t quantise(float v) {
+  float c = v < 0.0f ? 0.0f : (v > 1.0f ? 1.0f : v);
+  return (uint8_t)floorf(c * 255.0f + 0.5f);
+}
+
+/* ------------------------------------------------------------------ */
+/* step 10: shading in fp32                                            */
+/* ------------------------------------------------------------------ */
+static void shade_f32(const orc_batch* b, int32_t s, const float* V, int ortho, const float P[3],
+                      const float n[3], int32_t mat, float rgb[3]) {
+  const float* m = b->material + ((int64_t)s * ORC_MAX_MATERIALS + mat) * 5;
+  const float* amb = b->ambient + (int64_t)s * 3;
+  int32_t count = b->light_meta[s * 2 + 0];
+  int32_t type = b->light_meta[s * 2 + 1];
+  float c[3] = {0.0f, 0.0f, 0.0f};
+  float Vv[3];
+  if (ortho) {
+    Vv[0] = 0.0f;
+    Vv[1] = 0.0f;
+    Vv[2] = 1.0f;
+  } else {
+    float lp = sqrtf((P[0] * P[0] + P[1] * P[1]) + P[2] * P[2]);
+    for (int k = 0; k < 3; k++) Vv[k] = -P[k] / lp;
+  }
+  for (int l = 0; l < count; l++) {
+    const float* L4 = b->light + ((int64_t)s * ORC_MAX_LIGHTS + l) * 4;
+    float L[3], E;
+    if (type == 0) {
+      float Lv[3];
+      for (int i = 0; i < 3; i++) {
+        float lpv = ((V[i * 4 + 0] * L4[0] + V[i * 4 + 1] * L4[1]) + V[i * 4 + 2] * L4[2]) + V[i * 4 + 3];
+        Lv[i] = lpv - P[i];
+      }
+      float d2 = (Lv[0] * Lv[0] + Lv[1] * Lv[1]) + Lv[2] * Lv[2];
+      float dl = sqrtf(d2);
+      for (int i = 0; i < 3; i++) L[i] = Lv[i] / dl;
+      E = L4[3] / d2;
+    } else {
+      for (int i = 0; i < 3; i++) L[i] = -((V[i * 4 + 0] * L4[0] + V[i * 4 + 1] * L4[1]) + V[i * 4 + 2] * L4[2]);
+      E = L4[3];
+    }
+    float ndl = (n[0] * L[0] + n[1] * L[1]) + n[2] * L[2];
+    if (ndl < 0.0f) ndl = 0.0f;
+    float spec = 0.0f;
+    if (ndl > 0.0f) {
+      float Hv[3] = {L[0] + Vv[0], L[1] + Vv[1], L[2] + Vv[2]};
+      float h2 = (Hv[0] * Hv[0] + Hv[1] * Hv[1]) + Hv[2] * Hv[2];
+      if (h2 > 0.0f) {
+        float hl = sqrtf(h2);
+        float H[3] = {Hv[0] / hl, Hv[1] / hl, Hv[2] / hl};
+        float ndh = (n[0] * H[0] + n[1] * H[1]) + n[2] * H[2];
+        if (ndh < 0.0f) ndh = 0.0f;
+        spec = m[3] * powf(ndh, m[4]);
+      }
+    }
+    for (int k = 0; k < 3; k++) c[k] = c[k] + E * (m[k] * ndl + spec);
+  }
+  float scale = exp2f(b->exposure_ev[s]);
+  for (int k = 0; k < 3; k++) rgb[k] = scale * (amb[k] * m[k] + c[k]);
+}
+
+/* ------------------------------------------------------------------ */
+/* one image: steps 2-11                                               */
+/* ------------------------------------------------------------------ */
+static int render_image(const orc_meshes* me, const orc_batch* b, int32_t c, const orc_outputs* out,
+                        pixel_winner* px) {
+  int32_t W = b->cam_wh[c * 2 + 0], H = b->cam_wh[c * 2 + 1];
+  int32_t s = b->cam_sample[c];
+  const float* V = b->cam_view + (int64_t)c * 12;
+  const float* in = b->cam_intr + (int64_t)c * 6;
+  float fx = in[0], fy = in[1], cx = in[2], cy = in[3], near = in[4];
+  int ortho = in[5] != 0.0f;
+  int64_t npx = (int64_t)W * H;
+  int64_t base = b->img_offset[c];
+  int64_t frags = 0, culled = 0, clipped = 0, dropped = 0;
+  reset_winners(px, npx);
+
+  int64_t prim_base = 0;
+  for (int32_t inst = b->inst_offset[s]; inst < b->inst_offset[s + 1]; inst++) {
+    int32_t mesh = (int32_t)b->inst_mesh[inst];
+    float MV[12];
+    compose_mv(V, b->inst_pose + (int64_t)inst * 12, MV);
+    int32_t v0 = me->vert_offset[mesh];
+    int32_t t0 = me->tri_offset[mesh], t1 = me->tri_offset[mesh + 1];
+    for (int32_t t = t0; t < t1; t++) {
+      vtx tri[3];
+      for (int k = 0; k < 3; k++) {
+        int64_t vi = (int64_t)v0 + me->idx[(int64_t)t * 3 + k];
+        tri[k] = to_view(MV, me->pos + vi * 3, me->nrm + vi * 3);
+      }
+      vtx poly[4];
+      int np = clip_near(tri, near, poly);
+      if (!(tri[0].p[2] <= -near && tri[1].p[2] <= -near && tri[2].p[2] <= -near)) clipped++;
+      int64_t prim = prim_base + (t - t0);
+      int32_t mat = (int32_t)b->inst_mat_base[inst] + me->tri_mat[t];
+      int32_t seg = b->inst_seg[inst];
+      for (int sub = 0; sub + 2 < np; sub++) {
+        const vtx* q[3] = {&poly[0], &poly[sub + 1], &poly[sub + 2]};
+        int32_t X[3], Y[3];
+        float iw[3], nn[3][3];
+        int bad = 0;
+        for (int k = 0; k < 3; k++) {
+          float xs, ys;
+          if (ortho) {
+            iw[k] = -q[k]->p[2];
+            xs = cx + fx * q[k]->p[0];
+            ys = cy - fy * q[k]->p[1];
+          } else {
+            iw[k] = 1.0f / (-q[k]->p[2]);
+            xs = cx + fx * (q[k]->p[0] * iw[k]);
+            ys = cy - fy * (q[k]->p[1] * iw[k]);
+          }
+          if (!(fabsf(xs) < GUARD_PX) || !(fabsf(ys) < GUARD_PX)) bad = 1;
+          X[k] = bad ? 0 : (int32_t)rintf(xs * 256.0f);
+          Y[k] = bad ? 0 : (int32_t)rintf(ys * 256.0f);
+          for (int d = 0; d < 3; d++) nn[k][d] = q[k]->n[d];
+        }
+        if (bad) {
+          dropped++;
+          continue;
+        }
+        frags += raster_triangle(W, H, X, Y, iw, ortho, 2 * prim + sub, (const float(*)[3])nn, mat, seg, px,
+                                 &culled);
+      }
+    }
+    prim_base += t1 - t0;
+  }
+
+  /* steps 9-11 per pixel */
+  const float* bg = b->background + (int64_t)s * 3;
+  for (int32_t y = 0; y < H; y++) {
+    for (int32_t x = 0; x < W; x++) {
+      int64_t i = (int64_t)y * W + x;
+      int64_t o = base + i;
+      pixel_winner* p = &px[i];
+      if (out->prim) out->prim[o] = p->key;
+      if (out->depth2) out->depth2[o] = p->depth2;
+      if (p->key < 0) {
+        if (out->rgb)
+          for (int k = 0; k < 3; k++) out->rgb[o * 3 + k] = quantise(bg[k]);
+        if (out->rgb_linear)
+          for (int k = 0; k < 3; k++) out->rgb_linear[o * 3 + k] = bg[k];
+        if (out->depth) out->depth[o] = 0.0f;
+        if (out->normal)
+          for (int k = 0; k < 3; k++) out->normal[o * 3 + k] = 0;
+        if (out->seg) out->seg[o] = 0;
+        if (out->gb_pos)
+          for (int k = 0; k < 3; k++) out->gb_pos[o * 3 + k] = 0.0f;
+        if (out->gb_nrm)
+          for (int k = 0; k < 3; k++) out->gb_nrm[o * 3 + k] = 0.0f;
+        if (out->gb_mat) out->gb_mat[o] = -1;
+        continue;
+      }
+      int64_t cxp = 256 * (int64_t)x + 128, cyp = 256 * (int64_t)y + 128;
+      int64_t w0 = edge(p->X[1], p->Y[1], p->X[2], p->Y[2], cxp, cyp);
+      int64_t w1 = edge(p->X[2], p->Y[2], p->X[0], p->Y[0], cxp, cyp);
+      int64_t w2 = edge(p->X[0], p->Y[0], p->X[1], p->Y[1], cxp, cyp);
+      float a0 = (float)w0, a1 = (float)w1, a2 = (float)w2;
+      if (!ortho) {
+        a0 = a0 * p->iw[0];
+        a1 = a1 * p->iw[1];
+        a2 = a2 * p->iw[2];
+      }
+      float n[3];
+      for (int k = 0; k < 3; k++) n[k] = (a0 * p->n[0][k] + a1 * p->n[1][k]) + a2 * p->n[2][k];
+      float len = sqrtf((n[0] * n[0] + n[1] * n[1]) + n[2] * n[2]);
+      if (len > 0.0f)
+        for (int k = 0; k < 3; k++) n[k] = n[k] / len;
+      float ux = ((float)x + 0.5f - cx) / fx;
+      float uy = -(((float)y + 0.5f - cy) / fy);
+      float P[3];
+      if (ortho) {
+        P[0] = ux;
+        P[1] = uy;
+        P[2] = -p->depth;
+      } else {
+        P[0] = p->depth * ux;
+        P[1] = p->depth * uy;
+        P[2] = -p->depth;
+      }
+      float rgb[3];
+      shade_f32(b, s, V, ortho, P, n, p->mat, rgb);
+      if (out->rgb)
+        for (int k = 0; k < 3; k++) out->rgb[o * 3 + k] = quantise(rgb[k]);
+      if (out->rgb_linear)
+        for (int k = 0; k < 3; k++) out->rgb_linear[o * 3 + k] = rgb[k];
+      if (out->depth) out->depth[o] = p->depth;
+      if (out->normal)
+        for (int k = 0; k < 3; k++) out->normal[o * 3 + k] = orc_f32_to_f16(n[k]);
+      if (out->seg) out->seg[o] = (uint8_t)p->seg;
+      if (out->gb_pos)
+        for (int k = 0; k < 3; k++) out->gb_pos[o * 3 + k] = P[k];
+      if (out->gb_nrm)
+        for (int k = 0; k < 3; k++) out->gb_nrm[o * 3 + k] = n[k];
+      if (out->gb_mat) out->gb_mat[o] = p->mat;
+    }
+  }
+  if (out->counters) {
+    out->counters[0] += frags;
+    out->counters[1] += culled;
+    out->counters[2] += clipped;
+    out->counters[3] += dropped;
+  }
+  return 0;
+}
+
+int orc_render(const orc_meshes* m, const orc_batch* b, int32_t cam_begin, int32_t cam_end,
+               const orc_outputs* out) {
+  int64_t maxpx = 0;
+  for (int32_t c = cam_begin; c < cam_end; c++) {
+    int64_t n = (int64_t)b->cam_wh[c * 2] * b->cam_wh[c * 2 + 1];
+    if (n > maxpx) maxpx = n;
+  }
+  pixel_winner* px = (pixel_winner*)malloc((size_t)(maxpx > 0 ? maxpx : 1) * sizeof(pixel_winner));
+  if (!px) return -1;
+  for (int32_t c = cam_begin; c < cam_end; c++) render_image(m, b, c, out, px);
+  free(px);
+  return 0;
+}
+
+int orc_raster_fixed(int32_t W, int32_t H, int32_t n, const int32_t* X, const int32_t* Y, const float* iw,
+                     int32_t ortho, int64_t* prim_out, float* depth_out, int32_t* count_out) {
+  pixel_winner* px = (pixel_winner*)malloc((size_t)((int64_t)W * H > 0 ? (int64_t)W * H : 1) * sizeof(pixel_winner));
+  if (!px) return -1;
+  reset_winners(px, (int64_t)W * H);
+  for (int32_t t = 0; t < n; t++)
+    raster_triangle(W, H, X + 3 * t, Y + 3 * t, iw + 3 * t, ortho, 2 * (int64_t)t, NULL, 0, 0, px, NULL);
+  for (int64_t i = 0; i < (int64_t)W * H; i++) {
+    if (prim_out) prim_out[i] = px[i].key;
+    if (depth_out) depth_out[i] = px[i].key < 0 ? 0.0f : px[i].depth;
+    if (count_out) count_out[i] = px[i].count;
+  }
+  free(px);
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* step 10 in fp64 (finite differences) and its adjoint (step 12)      */
+/* ------------------------------------------------------------------ */
+typedef struct {
+  double L[3], E, ndl, spec, ndh, pw; /* pw = ndh^alpha */
+  double H[3], hl, Lv[3], dl, d2;
+  int lit, has_h;
+} light_term;
+
+static void view_lights_f64(const orc_batch* b, int32_t s, const float* V, const double* light,
+                            double out[ORC_MAX_LIGHTS][3]) {
+  int32_t count = b->light_meta[s * 2], type = b->light_meta[s * 2 + 1];
+  for (int l = 0; l < count; l++) {
+    const double* L4 = light + ((int64_t)s * ORC_MAX_LIGHTS + l) * 4;
+    for (int i = 0; i < 3; i++) {
+      double r = (double)V[i * 4 + 0] * L4[0] + (double)V[i * 4 + 1] * L4[1] + (double)V[i * 4 + 2] * L4[2];
+      out[l][i] = type == 0 ? r + (double)V[i * 4 + 3] : -r;
+    }
+  }
+}
+
+static void light_eval(int type, const double Lp[3], double I, const double P[3], const double n[3],
+                       const double Vv[3], double alpha, light_term* t) {
+  memset(t, 0, sizeof(*t));
+  if (type == 0) {
+    for (int i = 0; i < 3; i++) t->Lv[i] = Lp[i] - P[i];
+    t->d2 = t->Lv[0] * t->Lv[0] + t->Lv[1] * t->Lv[1] + t->Lv[2] * t->Lv[2];
+    t->dl = sqrt(t->d2);
+    for (int i = 0; i < 3; i++) t->L[i] = t->Lv[i] / t->dl;
+    t->E = I / t->d2;
+  } else {
+    for (int i = 0; i < 3; i++) t->L[i] = Lp[i];
+    t->E = I;
+  }
+  double ndl = n[0] * t->L[0] + n[1] * t->L[1] + n[2] * t->L[2];
+  t->lit = ndl > 0.0;
+  t->ndl = t->lit ? ndl : 0.0;
+  if (t->lit) {
+    double Hv[3] = {t->L[0] + Vv[0], t->L[1] + Vv[1], t->L[2] + Vv[2]};
+    double h2 = Hv[0] * Hv[0] + Hv[1] * Hv[1] + Hv[2] * Hv[2];
+    if (h2 > 0.0) {
+      t->has_h = 1;
+      t->hl = sqrt(h2);
+      for (int i = 0; i < 3; i++) t->H[i] = Hv[i] / t->hl;
+      double ndh = n[0] * t->H[0] + n[1] * t->H[1] + n[2] * t->H[2];
+      t->ndh = ndh > 0.0 ? ndh : 0.0;
+      t->pw = pow(t->ndh, alpha);
+    }
+  }
+}
+
+static void pixel_setup_f64(const float* gp, const float* gn, int ortho, double P[3], double n[3], double Vv[3]) {
+  for (int k = 0; k < 3; k++) {
+    P[k] = gp[k];
+    n[k] = gn[k];
+  }
+  if (ortho) {
+    Vv[0] = 0.0;
+    Vv[1] = 0.0;
+    Vv[2] = 1.0;
+  } else {
+    double lp = sqrt(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
+    for (int k = 0; k < 3; k++) Vv[k] = -P[k] / lp;
+  }
+}
+
+void orc_shade_f64(const orc_batch* b, int32_t cam_begin, int32_t cam_end, const float* gb_pos,
+                   const float* gb_nrm, const int32_t* gb_mat, const double* material, const double* light,
+                   const double* exposure_ev, const double* ambient, double* rgb) {
+  for (int32_t c = cam_begin; c < cam_end; c++) {
+    int32_t s = b->cam_sample[c];
+    const float* V = b->cam_view + (int64_t)c * 12;
+    int ortho = b->cam_intr[c * 6 + 5] != 0.0f;
+    int64_t npx = (int64_t)b->cam_wh[c * 2] * b->cam_wh[c * 2 + 1];
+    int64_t base = b->img_offset[c];
+    double Lp[ORC_MAX_LIGHTS][3];
+    view_lights_f64(b, s, V, light, Lp);
+    int32_t count = b->light_meta[s * 2], type = b->light_meta[s * 2 + 1];
+    double scale = exp2(exposure_ev[s]);
+    for (int64_t i = 0; i < npx; i++) {
+      int64_t o = base + i;
+      int32_t mat = gb_mat[o];
+      if (mat < 0) {
+        for (int k = 0; k < 3; k++) rgb[o * 3 + k] = b->background[s * 3 + k];
+        continue;
+      }
+      const double* m = material + ((int64_t)s * ORC_MAX_MATERIALS + mat) * 5;
+      double P[3], n[3], Vv[3];
+      pixel_setup_f64(gb_pos + o * 3, gb_nrm + o * 3, ortho, P, n, Vv);
+      double acc[3] = {0, 0, 0};
+      for (int l = 0; l < count; l++) {
+        light_term t;
+        light_eval(type, Lp[l], light[((int64_t)s * ORC_MAX_LIGHTS + l) * 4 + 3], P, n, Vv, m[4], &t);
+        double spec = m[3] * t.pw;
+        for (int k = 0; k < 3; k++) acc[k] += t.E * (m[k] * t.ndl + spec);
+      }
+      for (int k = 0; k < 3; k++) rgb[o * 3 + k] = scale * (ambient[s * 3 + k] * m[k] + acc[k]);
+    }
+  }
+}
+
+void orc_shade_backward_f64(const orc_batch* b, int32_t cam_begin, int32_t cam_end, const float* gb_pos,
+                            const float* gb_nrm, const int32_t* gb_mat, const double* material,
+                            const double* light, const double* exposure_ev, const double* ambient,
+                            const double* d_rgb, double* d_material, double* d_light, double* d_ev) {
+  const double ln2 = 0.69314718055994530942;
+  for (int32_t c = cam_begin; c < cam_end; c++) {
+    int32_t s = b->cam_sample[c];
+    const float* V = b->cam_view + (int64_t)c * 12;
+    int ortho = b->cam_intr[c * 6 + 5] != 0.0f;
+    int64_t npx = (int64_t)b->cam_wh[c * 2] * b->cam_wh[c * 2 + 1];
+    int64_t base = b->img_offset[c];
+    double Lp[ORC_MAX_LIGHTS][3];
+    view_lights_f64(b, s, V, light, Lp);
+    int32_t count = b->light_meta[s * 2], type = b->light_meta[s * 2 + 1];
+    double scale = exp2(exposure_ev[s]);
+    double dLp_view[ORC_MAX_LIGHTS][3];
+    memset(dLp_view, 0, sizeof(dLp_view));
+    for (int64_t i = 0; i < npx; i++) {
+      int64_t o = base + i;
+      int32_t mat = gb_mat[o];
+      if (mat < 0) continue;
+      const double* m = material + ((int64_t)s * ORC_MAX_MATERIALS + mat) * 5;
+      const double* g = d_rgb + o * 3;
+      double P[3], n[3], Vv[3];
+      pixel_setup_f64(gb_pos + o * 3, gb_nrm + o * 3, ortho, P, n, Vv);
+      double G = g[0] + g[1] + g[2];
+      double gr = g[0] * m[0] + g[1] * m[1] + g[2] * m[2];
+      double sum_endl = 0.0, sum_epw = 0.0, acc[3] = {0, 0, 0};
+      for (int l = 0; l < count; l++) {
+        light_term t;
+        double I = light[((int64_t)s * ORC_MAX_LIGHTS + l) * 4 + 3];
+        light_eval(type, Lp[l], I, P, n, Vv, m[4], &t);
+        double spec = m[3] * t.pw;
+        for (int k = 0; k < 3; k++) acc[k] += t.E * (m[k] * t.ndl + spec);
+        sum_endl += t.E * t.ndl;
+        sum_epw += t.E * t.pw;
+        /* rgb_k = scale*(amb_k*rho_k + sum_l E_l*(rho_k*ndl_l + ks*ndh_l^alpha)) */
+        double dE = scale * (gr * t.ndl + G * spec);
+        double dndl = t.lit ? scale * t.E * gr : 0.0;
+        double dndh = (t.has_h && t.ndh > 0.0) ? scale * t.E * G * m[3] * m[4] * pow(t.ndh, m[4] - 1.0) : 0.0;
+        double dLvec[3];
+        for (int k = 0; k < 3; k++) dLvec[k] = dndl * n[k];
+        if (dndh != 0.0) {
+          double dH[3] = {dndh * n[0], dndh * n[1], dndh * n[2]};
+          double hd = t.H[0] * dH[0] + t.H[1] * dH[1] + t.H[2] * dH[2];
+          for (int k = 0; k < 3; k++) dLvec[k] += (dH[k] - t.H[k] * hd) / t.hl;
+        }
+        double* dl = d_light + ((int64_t)s * ORC_MAX_LIGHTS + l) * 4;
+        if (type == 0) {
+          dl[3] += dE / t.d2;
+          double dd2 = -dE * I / (t.d2 * t.d2);
+          double ld = t.L[0] * dLvec[0] + t.L[1] * dLvec[1] + t.L[2] * dLvec[2];
+          for (int k = 0; k < 3; k++) dLp_view[l][k] += (dLvec[k] - t.L[k] * ld) / t.dl + 2.0 * dd2 * t.Lv[k];
+        } else {
+          dl[3] += dE;
+          for (int k = 0; k < 3; k++) dLp_view[l][k] += dLvec[k];
+        }
+      }
+      double* dm = d_material + ((int64_t)s * ORC_MAX_MATERIALS + mat) * 4;
+      for (int k = 0; k < 3; k++) dm[k] += g[k] * scale * (ambient[s * 3 + k] + sum_endl);
+      dm[3] += scale * G * sum_epw;
+      double dev = 0.0;
+      for (int k = 0; k < 3; k++) dev += g[k] * scale * (ambient[s * 3 + k] * m[k] + acc[k]);
+      d_ev[s] += ln2 * dev;
+    }
+    /* view-space light gradient back to world: point p_v = R p + t, direction L = -R d */
+    for (int l = 0; l < count; l++) {
+      double* dl = d_light + ((int64_t)s * ORC_MAX_LIGHTS + l) * 4;
+      for (int j = 0; j < 3; j++) {
+        double r = 0.0;
+        for (int i = 0; i < 3; i++) r += (double)V[i * 4 + j] * dLp_view[l][i];
+        dl[j] += type == 0 ? r : -r;
+      }
+    }
+  }
+}

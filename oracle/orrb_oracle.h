@@ -1,0 +1,120 @@
+/*
+ * orrb_oracle.h -- plain, slow CPU oracle of the batched renderer.
+ *
+ * TEST INFRASTRUCTURE ONLY.  The tests, the smoke check and the benchmark's
+ * CPU-baseline leg are the only code that may load this.  It shares no code,
+ * header, table or constant with the CUDA path; it is written from the
+ * definition of the rendered channels (Sec. 4.4: RGB, segmentation, depth,
+ * screen-space normal) and the randomized material / light / exposure
+ * parameters (Sec. 4.3.1), with every numeric rule the paper leaves open
+ * fixed by one stated reading (z-buffered rasterisation with one sample at
+ * each pixel centre, 8 fractional bits, top-left fill rule, Blinn-Phong).
+ *
+ * Precision: the forward pass is fp32 with every + and x separately rounded
+ * (build with -ffp-contract=off, no -ffast-math), IEEE division and sqrtf.
+ * The shading used for finite differences and the shading adjoint are fp64.
+ *
+ * Layouts (all flat, row-major):
+ *   pos/nrm        [V_total][3]   object space, per mesh at vert_offset[m]
+ *   idx            [T_total][3]   mesh-local vertex indices, at tri_offset[m]
+ *   inst_pose      [I][3][4]      world-from-object
+ *   cam_view       [C][3][4]      camera-from-world, camera looks down -z, +y up
+ *   cam_intr       [C][6]         fx, fy, cx, cy, near, type (0 persp, 1 ortho)
+ *   light          [S][4][4]      xyz (point position or direction), intensity
+ *   material       [S][32][5]     albedo rgb, specular k_s, shininess alpha
+ *   outputs        flat over pixels; image c starts at pixel img_offset[c]
+ */
+#ifndef ORRB_ORACLE_H
+#define ORRB_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_MAX_LIGHTS 4
+#define ORC_MAX_MATERIALS 32
+
+typedef struct {
+  int32_t n_meshes;
+  const int32_t* vert_offset;  /* [n_meshes + 1] */
+  const int32_t* tri_offset;   /* [n_meshes + 1] */
+  const float* pos;
+  const float* nrm;
+  const uint32_t* idx;
+  const uint8_t* tri_mat;
+} orc_meshes;
+
+typedef struct {
+  int32_t n_samples;
+  const int32_t* inst_offset;   /* [S + 1] */
+  const uint32_t* inst_mesh;    /* [I] */
+  const float* inst_pose;       /* [I][3][4] */
+  const uint8_t* inst_seg;      /* [I] */
+  const int16_t* inst_mat_base; /* [I] */
+  const int32_t* cam_offset;    /* [S + 1] */
+  const int32_t* cam_sample;    /* [C] */
+  const float* cam_view;        /* [C][3][4] */
+  const float* cam_intr;        /* [C][6] */
+  const int32_t* cam_wh;        /* [C][2] */
+  const int64_t* img_offset;    /* [C] */
+  const float* light;           /* [S][4][4] */
+  const int32_t* light_meta;    /* [S][2] count, type (0 point, 1 directional) */
+  const float* material;        /* [S][32][5] */
+  const float* exposure_ev;     /* [S] */
+  const float* ambient;         /* [S][3] */
+  const float* background;      /* [S][3] */
+} orc_batch;
+
+typedef struct {                /* every pointer may be NULL */
+  uint8_t* rgb;                 /* [N][3] */
+  float* depth;                 /* [N] view-axis distance, 0 = background */
+  uint16_t* normal;             /* [N][3] IEEE binary16 bits */
+  uint8_t* seg;                 /* [N] */
+  float* rgb_linear;            /* [N][3] before clamping and quantisation */
+  float* gb_pos;                /* [N][3] view-space position */
+  float* gb_nrm;                /* [N][3] unit view-space normal, fp32 */
+  int32_t* gb_mat;              /* [N] material slot, -1 = background */
+  int64_t* prim;                /* [N] winning key 2*prim_id + sub, -1 = background */
+  float* depth2;                /* [N] depth of the nearest fragment of another key, +inf if none */
+  int64_t* counters;            /* [4] fragments, triangles culled, clipped, dropped (accumulated) */
+} orc_outputs;
+
+/* Render images [cam_begin, cam_end).  Returns 0, or -1 on allocation failure. */
+int orc_render(const orc_meshes* m, const orc_batch* b, int32_t cam_begin, int32_t cam_end,
+               const orc_outputs* out);
+
+/* Rasterise already-snapped screen triangles (8 fractional bits) into one
+ * W x H image: coverage, depth and the (depth, key) visibility test only.
+ * X, Y: [n][3] fixed-point; iw: [n][3] 1/w (perspective) or view depth
+ * (ortho != 0).  prim_out [W*H] (-1 background), depth_out [W*H] (0 background),
+ * count_out [W*H] number of fragments that covered each pixel; any may be NULL. */
+int orc_raster_fixed(int32_t W, int32_t H, int32_t n, const int32_t* X, const int32_t* Y,
+                     const float* iw, int32_t ortho, int64_t* prim_out, float* depth_out,
+                     int32_t* count_out);
+
+/* float -> binary16 bits, round to nearest even (the normal channel's encoding). */
+uint16_t orc_f32_to_f16(float f);
+
+/* fp64 shading of a G-buffer over images [cam_begin, cam_end), parameters in
+ * fp64: material [S][32][5], light [S][4][4], exposure_ev [S], ambient [S][3].
+ * Writes rgb [N][3] (background pixels get the background colour). */
+void orc_shade_f64(const orc_batch* b, int32_t cam_begin, int32_t cam_end,
+                   const float* gb_pos, const float* gb_nrm, const int32_t* gb_mat,
+                   const double* material, const double* light, const double* exposure_ev,
+                   const double* ambient, double* rgb);
+
+/* fp64 adjoint of orc_shade_f64 at fixed visibility.  d_rgb [N][3] is dL/d rgb_linear.
+ * Accumulates (+=) into d_material [S][32][4] (albedo rgb, specular),
+ * d_light [S][4][4] (world position or direction xyz, intensity), d_ev [S]. */
+void orc_shade_backward_f64(const orc_batch* b, int32_t cam_begin, int32_t cam_end,
+                            const float* gb_pos, const float* gb_nrm, const int32_t* gb_mat,
+                            const double* material, const double* light, const double* exposure_ev,
+                            const double* ambient, const double* d_rgb,
+                            double* d_material, double* d_light, double* d_ev);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
