@@ -1,0 +1,381 @@
+"""Throughput benchmark of the batched renderer (one JSON line on rank 0).
+
+Workload: the hand-like scene -- 24 capsule links (320 triangles each) posed by
+seeded hinge angles, a 12-triangle block with 6 face materials, a 2-triangle
+table; 256 samples x 3 cameras at 200x200 with camera jitter, 1-4 point lights,
+random materials; all four channels (RGB u8, depth f32, normal f16x3, seg u8).
+The paper's benchmark scene (Sec. 5: Shadow hand + block, 3 cameras, 200x200)
+is not available; this seeded synthetic scene of the same shape stands in.
+
+A step renders one batch.  `value` is samples/s with inputs resident in HBM,
+timed per step with CUDA events on the launch stream, L2 flushed between
+steps (a 256 MB write) outside the events.  `e2e` is the same metric through
+the public API with host buffers: each step copies the batch parameters from
+pinned host memory, renders, and copies all four channels back to pinned host
+memory (the paper's capture pipeline returns the whole batch to the CPU,
+Sec. 4.4).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "samples/s (RGB+depth+normal+seg, 3x200² cams) at 1 B300, fused vs plain; % roofline"
+UNIT = "samples/s"
+N_SAMPLES = 256
+N_CAMS = 3
+RES = 200
+SEED = 0
+BYTES_PER_PX = 3 + 4 + 6 + 1           # rgb u8x3, depth f32, normal f16x3, seg u8
+CONFIG = {"workload": "hand-like scene: 256 samples x 3 cameras x 200x200, 24 capsule links + block + table, "
+                      "1-4 point lights, 4 channels", "global_batch": N_SAMPLES, "cameras": N_CAMS,
+          "resolution": RES, "tris_per_sample": 24 * 320 + 14, "l2": "flushed between timed steps (256 MB write)"}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0}, "fallback"
+
+
+def fp32_peak_tflops(sms: int, mhz: float) -> float:
+    """Dense FP32 FMA peak: SMs x 128 lanes x 2 flop x clock."""
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def shading_flops(n_visible: int, n_lit: int, n_light_terms: int) -> float:
+    """Algorithmic FP32 operations of the shading step over visible pixels (count documented in the design doc):
+    72 per visible pixel + 31 per (pixel, light) + 20 per (pixel, light) with n.L > 0 (specular lobe)."""
+    return float(72 * n_visible + 31 * n_light_terms + 20 * n_lit)
+
+
+class ClockSampler:
+    """Samples SM clock and clock-event reasons with nvidia-smi while the timed region runs (read-only)."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, gpu_id: str, period_ms: int = 20):
+        self.gpu_id, self.period_ms = gpu_id, period_ms
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        import subprocess
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.2)
+        return self
+
+    def __exit__(self, *a):
+        time.sleep(0.05)
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for name, v in zip(self.NAMES, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm), "source": "nvidia-smi during the timed fused steps"}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def shard_samples(rank: int, world: int, n: int) -> np.ndarray:
+    """Sample ids of rank `rank`: every rank renders its own n samples (weak scaling, no collective)."""
+    return np.arange(rank * n, (rank + 1) * n, dtype=np.int64)
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def oracle_baseline(batch, budget_s: float = 15.0):
+    """Time the CPU oracle on a bounded sample of the workload on all host cores."""
+    from oracle import oracle as orc
+    from paper_1906_11633_b300 import scenegen as sg
+    threads = orc.default_threads()
+    n, passes, dt = 16, 0, 0.0
+    sub = sg.select_samples(batch, list(range(n)))
+    while dt < budget_s and passes < 1000:
+        t0 = time.perf_counter()
+        orc.render(sub, threads=threads)
+        dt += time.perf_counter() - t0
+        passes += 1
+    return {"value": n * passes / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {n} of the {batch.n_samples} samples ({n * N_CAMS} images) x {passes} passes, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from paper_1906_11633_b300 import scenegen as sg
+    from oracle import oracle as orc
+    batch = sg.hand_batch(SEED, np.arange(N_SAMPLES), res=RES, n_cams=N_CAMS)
+    threads = orc.default_threads()
+    n = 8                                  # samples per step: a bounded slice of the batch
+    per = []
+    for i in range(args.warmup + args.steps):
+        ids = [(i * n + k) % N_SAMPLES for k in range(n)]
+        sub = sg.select_samples(batch, ids)
+        t0 = time.perf_counter()
+        orc.render(sub, threads=threads)
+        if i >= args.warmup:
+            per.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.mean(per))
+    value = n / (ms / 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": CONFIG,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{n} samples ({n * N_CAMS} images) per step of the same workload"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_1906_11633_b300 import scenegen as sg
+    from paper_1906_11633_b300 import lib as L
+    from paper_1906_11633_b300.render import Renderer, config, host_arrays, DeviceBatch, batch_shape
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ids = shard_samples(rank, world, N_SAMPLES)
+    batch = sg.hand_batch(SEED, ids, res=RES, n_cams=N_CAMS)
+    r = Renderer(batch.meshes, device=local)
+    db = r.upload(batch)
+    cfg = config(mode=L.ORRB_MODE_FUSED, tile_w=args.tile_w, tile_h=args.tile_h, threads=args.threads)
+    out = r.render(db, cfg=cfg, rgb_linear=False)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    N = batch.total_pixels
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        barrier(world)
+        evs = []
+        for _ in range(steps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        barrier(world)
+        return [a.elapsed_time(b) for a, b in evs]
+
+    # -- fused (the headline) ----------------------------------------------------
+    gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    with ClockSampler(gpu_id) as clk:
+        per = timed(lambda: r.render(db, out=out, cfg=cfg), args.steps, args.warmup)
+    status = r.status()
+    total_ms = max_over_ranks(float(np.sum(per)), world)
+    ms = total_ms / args.steps
+    value = world * N_SAMPLES * args.steps / (total_ms / 1e3)
+    kernel_ms = float(np.mean(per))
+
+    # -- plain per-sample launches (comparison) ----------------------------------
+    pcfg = config(mode=L.ORRB_MODE_PLAIN, tile_w=args.tile_w, tile_h=args.tile_h, threads=args.threads)
+    psteps = max(3, args.steps // 10)
+    pper = timed(lambda: r.render(db, out=out, cfg=pcfg), psteps, min(args.warmup, 3))
+    plain_ms = max_over_ranks(float(np.sum(pper)), world) / psteps
+    plain_value = world * N_SAMPLES / (plain_ms / 1e3)
+
+    # -- e2e through host buffers -------------------------------------------------
+    arrs = host_arrays(batch)
+    pinned_in = {k: torch.from_numpy(v).pin_memory() for k, v in arrs.items()}
+    dev_in = {k: torch.empty(v.shape, dtype=v.dtype, device=dev) for k, v in pinned_in.items()}
+    dbe = DeviceBatch(batch_shape(batch), dev_in)
+    host_out = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items()}
+    h2d = sum(v.numel() * v.element_size() for v in pinned_in.values())
+    d2h = sum(v.numel() * v.element_size() for v in out.values())
+
+    def e2e_step():
+        for k in dev_in:
+            dev_in[k].copy_(pinned_in[k], non_blocking=True)
+        r.render(dbe, out=out, cfg=cfg)
+        for k in out:
+            host_out[k].copy_(out[k], non_blocking=True)
+
+    esteps = max(3, args.steps // 5)
+    eper = timed(e2e_step, esteps, min(args.warmup, 3))
+    e2e_ms = max_over_ranks(float(np.sum(eper)), world) / esteps
+    e2e_value = world * N_SAMPLES / (e2e_ms / 1e3)
+    ok = (host_out["seg"].numpy() == out["seg"].cpu().numpy()).all()
+
+    if rank != 0:
+        return
+    # -- roofline -----------------------------------------------------------------
+    peaks, peak_kind = load_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    param_bytes = sum(v.nbytes for k, v in arrs.items())
+    mesh_bytes = int(r.arena.numel())
+    alg_bytes = BYTES_PER_PX * N + param_bytes + mesh_bytes
+    # algorithmic shading FLOPs from this batch's visible pixels and lights
+    o = r.render(db, cfg=cfg, rgb_linear=True, gbuffer=True)
+    gmat = o["gbuffer"][6].view(torch.int32).cpu().numpy()
+    fg = gmat >= 0
+    per_img_px = (batch.cam_wh[:, 0] * batch.cam_wh[:, 1]).astype(np.int64)
+    nl_px = np.repeat(batch.light_meta[batch.cam_sample, 0], per_img_px)
+    gb = o["gbuffer"].cpu().numpy()
+    lit = _lit_lights(batch, gb, fg, per_img_px)
+    flops = shading_flops(int(fg.sum()), lit, int(nl_px[fg].sum()))
+    props = torch.cuda.get_device_properties(dev)
+    clk_sum = clk.summary()
+    fp32_peak = fp32_peak_tflops(props.multi_processor_count, float(peaks.get("sm_max_mhz", 2032.0)))
+    t_hbm = alg_bytes / (hbm * 1e9)
+    t_fp32 = flops / (fp32_peak * 1e12)
+    bound = "hbm" if t_hbm >= t_fp32 else "alu"
+    achieved_gbs = alg_bytes / (kernel_ms / 1e3) / 1e9
+    achieved_tf = flops / (kernel_ms / 1e3) / 1e12
+    roof = {"bound": bound,
+            "achieved": achieved_gbs if bound == "hbm" else achieved_tf,
+            "peak": hbm if bound == "hbm" else fp32_peak,
+            "unit": "GB/s" if bound == "hbm" else "TFLOP/s",
+            "frac": (achieved_gbs / hbm) if bound == "hbm" else (achieved_tf / fp32_peak),
+            "traffic": args.traffic,
+            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if bound == "hbm" else
+                           "nominal: SMs x 128 x 2 x max SM clock",
+            "alg_bytes_per_launch": alg_bytes, "alg_fp32_flop_per_launch": flops,
+            "t_roof_us": 1e6 * max(t_hbm, t_fp32), "t_hbm_us": 1e6 * t_hbm, "t_fp32_us": 1e6 * t_fp32,
+            "roofline_frac_of_step": 1e3 * max(t_hbm, t_fp32) / kernel_ms,
+            "kernel": "render_fused_kernel"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded procedural hand scene)",
+            "config": dict(CONFIG, parallelism=f"replicas x{world}" if world > 1 else "single GPU",
+                           tile=[args.tile_w or 512, args.tile_h or 8], threads=args.threads or 512),
+            "plain": {"value": plain_value, "ms_per_step": plain_ms, "steps": psteps,
+                      "launches_per_step": 3 * N_SAMPLES},
+            "fused_over_plain": value / plain_value,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "ms_per_step": e2e_ms, "steps": esteps, "readback_ok": bool(ok)},
+            "gpu_launches": args.steps,
+            "roofline": roof,
+            "clocks": clk_sum,
+            "device_status": status}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_baseline(batch)
+    print(json.dumps(line), flush=True)
+
+
+def _lit_lights(batch, gb, fg, per_img_px):
+    """Number of (pixel, light) pairs with n.L > 0 (they evaluate the specular lobe)."""
+    total = 0
+    start = 0
+    for c in range(batch.n_cams):
+        n = int(per_img_px[c])
+        sl = slice(start, start + n)
+        start += n
+        m = fg[sl]
+        if not m.any():
+            continue
+        s = batch.cam_sample[c]
+        V = batch.cam_view[c].astype(np.float64)
+        P = gb[0:3, sl][:, m].T
+        nrm = gb[3:6, sl][:, m].T
+        for l in range(batch.light_meta[s, 0]):
+            lp = V[:, :3] @ batch.light[s, l, :3] + V[:, 3]
+            if batch.light_meta[s, 1] == 0:
+                Ld = lp - P
+            else:
+                Ld = np.broadcast_to(-(V[:, :3] @ batch.light[s, l, :3]), P.shape)
+            total += int((np.einsum("ij,ij->i", nrm, Ld) > 0).sum())
+    return total
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--tile-w", type=int, default=0)
+    ap.add_argument("--tile-h", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per launch of the fused kernel from an ncu capture of this build")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,220 @@
+/*
+ * orrb.h -- C-ABI of liborrb.so, a batched renderer for visually randomized
+ * robotics scenes on one B300 GPU (sm_103a).
+ *
+ * What it computes.  For every camera of every sample in a batch it renders
+ * the four channels the paper's capture pipeline produces (Sec. 4.4: RGB,
+ * segmentation, depth and screen-space normal) from geometry that is shared
+ * by all samples (Single Scene Multiple States, Sec. 3) and from per-sample
+ * state and randomization parameters (Sec. 4.3.1: joint positions -> link
+ * poses, camera pose, light positions and intensities, material tint /
+ * specular / glossiness, exposure).  Randomization itself happens on the
+ * host: the library renders the parameters it is given, so a sample renders
+ * identically alone or in any batch (seeded determinism, Sec. 4.3).  Outputs
+ * go to caller-preallocated batch buffers (Sec. 4.4: destination textures
+ * for the whole batch are preallocated).
+ *
+ * The numeric rules the paper leaves open are fixed as follows (the CPU
+ * oracle under oracle/ implements the same definition independently):
+ *   - camera looks down -z, +y up; screen x right, y down; pixel centres at
+ *     (x + 1/2, y + 1/2); triangles clipped at z = -near; vertices snapped to
+ *     8 fractional bits (round-half-even); integer edge functions, top-left
+ *     fill rule; triangles with non-positive screen area are culled;
+ *   - depth = view-axis distance (metres), 0 for background; the nearest
+ *     fragment wins by (depth, 2*prim + sub) where prim is the triangle's
+ *     index in the sample's concatenated triangle list (instances in order,
+ *     triangles in mesh order) and sub the half of a near-clipped quad;
+ *   - normal = perspective-correct interpolated view-space unit normal,
+ *     stored as IEEE binary16; seg = the instance's id, 0 for background;
+ *   - rgb = 2^EV * (ambient*albedo + sum_l E_l (albedo*max(0,n.L) +
+ *     k_s*max(0,n.H)^alpha [n.L > 0])), E = I/d^2 for point lights and I for
+ *     directional ones, quantised as floor(clamp(rgb,0,1)*255 + 1/2).
+ *
+ * Conventions of every entry point.
+ *   Memory:    every device buffer is allocated and owned by the caller; the
+ *              library owns only host metadata (the context).  Pointers
+ *              marked "device" must be device memory of the context's GPU.
+ *   Streams:   `stream` is a cudaStream_t passed as void*; all GPU work is
+ *              enqueued asynchronously on it.  NULL means the legacy default
+ *              stream.
+ *   Errors:    functions return an orrb_status and never throw.  Host-side
+ *              checks run before anything is enqueued.  Checks that need the
+ *              contents of device arrays run inside the kernels: a violation
+ *              sets a bit in the workspace status word and skips the
+ *              offending image (or instance, triangle); read it with
+ *              orrb_read_status().  orrb_last_error() gives a message for
+ *              the last failure on the context.
+ *   Threads:   a context may be used from several host threads; calls are
+ *              serialised by a mutex inside the context.
+ */
+#ifndef ORRB_H
+#define ORRB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORRB_MAX_LIGHTS 4
+#define ORRB_MAX_MATERIALS 32
+#define ORRB_MAX_RESOLUTION 4096
+#define ORRB_MAX_INSTANCES 1024
+#define ORRB_GBUFFER_PLANES 7
+
+typedef int32_t orrb_status;
+#define ORRB_OK 0
+#define ORRB_ERR_INVALID_ARG 1   /* a host-side argument check failed */
+#define ORRB_ERR_WORKSPACE 2     /* workspace or arena too small */
+#define ORRB_ERR_CUDA 3          /* a CUDA runtime call failed */
+#define ORRB_ERR_TIMEOUT 4       /* a bounded device wait gave up */
+#define ORRB_ERR_NOT_FOUND 5     /* no mesh set uploaded on the context */
+#define ORRB_ERR_UNSUPPORTED 6   /* device is not sm_103 or option unsupported */
+#define ORRB_ERR_DEVICE 7        /* the device status word is non-zero */
+
+/* Device status word bits (orrb_read_status). */
+#define ORRB_DEV_BAD_CAMERA 0x1u     /* width/height outside [1, declared max] or bad intrinsics */
+#define ORRB_DEV_BAD_INSTANCE 0x2u   /* mesh id out of range or too many instances */
+#define ORRB_DEV_TOO_MANY_TRIS 0x4u  /* sample has more triangles than declared */
+#define ORRB_DEV_BAD_MATERIAL 0x8u   /* material slot >= 32 (clamped to 31) */
+#define ORRB_DEV_BAD_LIGHTS 0x10u    /* light count outside [0, 4] (clamped) */
+#define ORRB_DEV_DROPPED 0x20u       /* a triangle left the +-2^20 px guard band and was dropped */
+
+typedef struct orrb_ctx orrb_ctx;
+
+/* Create a context on CUDA device `device` (must be compute capability 10.3).
+ * Returns ORRB_ERR_UNSUPPORTED on another architecture. */
+orrb_status orrb_create(int device, orrb_ctx** out);
+void orrb_destroy(orrb_ctx* ctx);
+const char* orrb_status_string(orrb_status s);
+/* Copies the message of the last failure on `ctx` into buf (NUL-terminated). */
+orrb_status orrb_last_error(orrb_ctx* ctx, char* buf, size_t len);
+
+/* ---------------------------------------------------------------------- */
+/* Meshes (shared by all samples: Single Scene Multiple States, Sec. 3).   */
+/* ---------------------------------------------------------------------- */
+typedef struct {
+  const float* pos;       /* host, [n_verts][3] object-space positions (metres) */
+  const float* nrm;       /* host, [n_verts][3] unit vertex normals */
+  int32_t n_verts;
+  const uint32_t* idx;    /* host, [n_tris][3] vertex indices, counter-clockwise seen from outside */
+  const uint8_t* tri_mat; /* host, [n_tris] material slot relative to the instance's base */
+  int32_t n_tris;
+} orrb_mesh_desc;
+
+/* Bytes of device arena needed to hold meshes[0..n). */
+orrb_status orrb_mesh_arena_size(const orrb_mesh_desc* meshes, int32_t n, size_t* bytes);
+
+/* Split the meshes into clusters of at most 64 vertices / 128 triangles
+ * (host), write them into the caller-owned device arena `dev_arena`
+ * (256-byte aligned, `arena_bytes` long) on `stream`, and make them the
+ * context's mesh set: mesh id k of later batches is meshes[k].  Returns
+ * after the copy has completed; host arrays may be freed on return.  The
+ * arena must stay alive and unmodified while batches that use it run.
+ * Replaces any previous mesh set (whose arena the caller may then free once
+ * its batches have finished). */
+orrb_status orrb_upload_meshes(orrb_ctx* ctx, const orrb_mesh_desc* meshes, int32_t n, void* dev_arena,
+                               size_t arena_bytes, void* stream);
+/* Forget the mesh set (no device work). */
+orrb_status orrb_release_meshes(orrb_ctx* ctx);
+
+/* ---------------------------------------------------------------------- */
+/* Batches                                                                  */
+/* ---------------------------------------------------------------------- */
+/* Host-side shape of a batch: sizes the workspace and the launch.  Every
+ * bound is checked again on the device against the actual arrays. */
+typedef struct {
+  int32_t n_samples;
+  int32_t n_cams;               /* total cameras = images */
+  int32_t max_tris_per_sample;  /* >= triangles of any sample's instances */
+  int32_t max_inst_per_sample;  /* <= ORRB_MAX_INSTANCES */
+  int32_t max_cams_per_sample;
+  int32_t max_width, max_height;/* <= ORRB_MAX_RESOLUTION */
+  int64_t total_pixels;         /* sum of width*height over cameras */
+} orrb_batch_shape;
+
+/* Per-sample state and randomization parameters; all device pointers. */
+typedef struct {
+  const int32_t* inst_offset;    /* [n_samples+1] CSR: instances of sample s are [off[s], off[s+1]) */
+  const uint32_t* inst_mesh;     /* [n_inst] mesh id */
+  const float* inst_pose;        /* [n_inst][3][4] world-from-object, rigid (rotation | translation) */
+  const uint8_t* inst_seg;       /* [n_inst] segmentation id written for the instance's pixels */
+  const int16_t* inst_mat_base;  /* [n_inst] first material slot; slot = base + tri_mat < 32 */
+  const int32_t* cam_offset;     /* [n_samples+1] CSR of cameras per sample */
+  const int32_t* cam_sample;     /* [n_cams] owning sample of each camera */
+  const float* cam_view;         /* [n_cams][3][4] camera-from-world, OpenGL axes */
+  const float* cam_intr;         /* [n_cams][6] fx, fy, cx, cy (pixels), near (m), type (0 persp, 1 ortho) */
+  const int32_t* cam_wh;         /* [n_cams][2] width, height */
+  const int64_t* img_offset;     /* [n_cams] first pixel of each image in the flat outputs */
+  const float* light;            /* [n_samples][4][4] world position (point) or travel direction
+                                    (directional) xyz, intensity */
+  const int32_t* light_meta;     /* [n_samples][2] light count (0..4), type (0 point, 1 directional) */
+  const float* material;         /* [n_samples][32][5] albedo rgb, specular k_s, shininess alpha */
+  const float* exposure_ev;      /* [n_samples] exposure in stops */
+  const float* ambient;          /* [n_samples][3] */
+  const float* background;       /* [n_samples][3] linear background colour */
+} orrb_batch_desc;
+
+/* Caller-preallocated outputs, flat over all pixels of all images (image c
+ * at img_offset[c], row-major, row 0 at the top); any pointer may be NULL. */
+typedef struct {
+  uint8_t* rgb;         /* device, [N][3] */
+  float* depth;         /* device, [N] */
+  uint16_t* normal;     /* device, [N][3] binary16 bits */
+  uint8_t* seg;         /* device, [N] */
+  float* rgb_linear;    /* device, [N][3] before clamp and quantisation */
+  float* gbuffer;       /* device, [7][N] planes: position xyz, normal xyz (view space),
+                           material slot as int32 bits (-1 background); input of the backward */
+} orrb_outputs;
+
+#define ORRB_MODE_FUSED 0  /* one persistent launch over all images (work queue) */
+#define ORRB_MODE_PLAIN 1  /* three launches (setup, bin, raster+shade) per sample */
+
+typedef struct {
+  int32_t mode;          /* ORRB_MODE_FUSED or ORRB_MODE_PLAIN */
+  int32_t tile_w;        /* screen-tile width in pixels, multiple of 8 in [8, 512]; 0 = 512 */
+  int32_t tile_h;        /* screen-tile height in pixels, in [1, 64]; 0 = 8 */
+  int32_t threads;       /* threads per CTA: 256, 512 or 1024; 0 = 512 */
+  int32_t ctas_per_sm;   /* fused mode: resident CTAs per SM; 0 = as many as fit */
+} orrb_config;
+
+/* Workspace bytes for `shape` under `cfg`.  The workspace is caller-owned
+ * device memory (256-byte aligned); its first 256 bytes hold the status word. */
+orrb_status orrb_workspace_size(orrb_ctx* ctx, const orrb_batch_shape* shape, const orrb_config* cfg,
+                                size_t* bytes);
+
+/* Render one batch into `out` (Sec. 4.4 channels), asynchronously on
+ * `stream`.  Clears the workspace status word first. */
+orrb_status orrb_render_batch(orrb_ctx* ctx, const orrb_batch_shape* shape, const orrb_batch_desc* batch,
+                              const orrb_outputs* out, const orrb_config* cfg, void* workspace,
+                              size_t ws_bytes, void* stream);
+
+/* Synchronise `stream` and read the workspace status word (ORRB_DEV_* bits). */
+orrb_status orrb_read_status(orrb_ctx* ctx, const void* workspace, void* stream, uint32_t* status);
+
+/* ---------------------------------------------------------------------- */
+/* Shading adjoint at fixed visibility                                      */
+/* ---------------------------------------------------------------------- */
+typedef struct {
+  float* d_material;   /* device, [n_samples][32][4]: d albedo rgb, d specular (overwritten) */
+  float* d_light;      /* device, [n_samples][4][4]: d world position/direction xyz, d intensity */
+  float* d_exposure;   /* device, [n_samples] */
+} orrb_param_grads;
+
+/* Workspace bytes of orrb_shade_backward for `shape` (partial sums). */
+orrb_status orrb_backward_workspace_size(orrb_ctx* ctx, const orrb_batch_shape* shape, size_t* bytes);
+
+/* Gradients of a loss L w.r.t. the randomized material, light and exposure
+ * parameters (Sec. 4.3.1), given d_rgb_linear = dL/d rgb_linear [N][3] and
+ * the G-buffer a render wrote.  Visibility is held fixed (it does not depend
+ * on these parameters).  The reduction over pixels runs in a fixed order, so
+ * results are bit-identical from run to run. */
+orrb_status orrb_shade_backward(orrb_ctx* ctx, const orrb_batch_shape* shape, const orrb_batch_desc* batch,
+                                const float* gbuffer, const float* d_rgb_linear, const orrb_param_grads* grads,
+                                void* workspace, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

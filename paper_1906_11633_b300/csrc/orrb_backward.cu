@@ -1,0 +1,275 @@
+// orrb_backward.cu -- adjoint of the shading at fixed visibility (sm_103a).
+//
+// Given the G-buffer a render wrote (view-space position, unit normal,
+// material slot per pixel) and dL/d rgb_linear, computes dL/d of the
+// randomized parameters the paper's randomizers draw (Sec. 4.3.1): per
+// material albedo (rgb) and specular k_s, per light position (or direction)
+// and intensity, and the exposure.  Visibility does not depend on these
+// parameters, so the gradient is exact, not an approximation.
+//
+// Pass 1 (grid = images x blocks_per_img): each CTA owns a fixed pixel range
+// of one image.  Light and exposure terms accumulate per thread; material
+// terms accumulate per warp with a segmented reduction: for every material
+// present in the warp's 32 pixels the lanes with that material are summed by
+// a fixed shuffle tree.  The CTA then combines its warps in warp order,
+// maps light gradients from view to world space (R^T) and writes one
+// partial row.  Pass 2 sums the partial rows of a sample in (camera, block)
+// order.  Every addition happens in an order fixed by the data layout, so
+// the result is bit-identical from run to run.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+
+#include "orrb.h"
+#include "orrb_internal.h"
+
+namespace orrb {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kBwdThreads = 256;
+constexpr int kBwdWarps = kBwdThreads / 32;
+
+struct BwdShared {
+  float V[12];
+  float lv[kMaxLights][4];
+  float mat[kMaxMaterials][5];
+  float amb[3];
+  float scale;
+  int n_lights, light_type, ortho, s;
+  float wmat[kBwdWarps][kMaxMaterials][4];      // per-warp material sums
+  float wred[kBwdWarps][kMaxLights * 4 + 1];    // per-warp light + exposure sums
+};
+
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(kBwdThreads) backward_partial_kernel(BackwardParams bp) {
+  const Params& p = bp.base;
+  __shared__ BwdShared sh;
+  const int cam = blockIdx.x, blk = blockIdx.y;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    int s = p.cam_sample[cam];
+    if (s < 0 || s >= p.n_samples) s = 0;
+    sh.s = s;
+    for (int k = 0; k < 12; k++) sh.V[k] = p.cam_view[cam * 12 + k];
+    sh.ortho = p.cam_intr[cam * 6 + 5] != 0.0f;
+    int nl = p.light_meta[s * 2];
+    sh.n_lights = nl < 0 ? 0 : (nl > kMaxLights ? kMaxLights : nl);
+    sh.light_type = p.light_meta[s * 2 + 1];
+    for (int l = 0; l < sh.n_lights; l++) {
+      const float* L4 = p.light + (s * kMaxLights + l) * 4;
+      for (int i = 0; i < 3; i++) {
+        float r = sh.V[i * 4 + 0] * L4[0] + sh.V[i * 4 + 1] * L4[1] + sh.V[i * 4 + 2] * L4[2];
+        sh.lv[l][i] = sh.light_type == 0 ? r + sh.V[i * 4 + 3] : -r;
+      }
+      sh.lv[l][3] = L4[3];
+    }
+    sh.scale = exp2f(p.exposure_ev[s]);
+    for (int k = 0; k < 3; k++) sh.amb[k] = p.ambient[s * 3 + k];
+  }
+  for (int k = tid; k < kBwdWarps * kMaxMaterials * 4; k += kBwdThreads) (&sh.wmat[0][0][0])[k] = 0.0f;
+  __syncthreads();
+  for (int k = tid; k < kMaxMaterials * 5; k += kBwdThreads)
+    sh.mat[k / 5][k % 5] = p.material[(size_t)sh.s * kMaxMaterials * 5 + k];
+  __syncthreads();
+
+  const long long N = p.total_pixels;
+  const long long npx = (long long)p.cam_wh[cam * 2] * p.cam_wh[cam * 2 + 1];
+  const long long chunk = (npx + bp.blocks_per_img - 1) / bp.blocks_per_img;
+  const long long i0 = blk * chunk, i1 = min(npx, i0 + chunk);
+  const long long base = p.img_offset[cam];
+  const float ln2 = 0.69314718055994530942f;
+  const float scale = sh.scale;
+
+  float dlv[kMaxLights][3], dI[kMaxLights], dev = 0.0f;
+  for (int l = 0; l < kMaxLights; l++) {
+    dlv[l][0] = dlv[l][1] = dlv[l][2] = 0.0f;
+    dI[l] = 0.0f;
+  }
+  for (long long r0 = i0; r0 < i1; r0 += kBwdThreads) {
+    const long long i = r0 + tid;
+    int mat = -1;
+    float dm[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (i < i1) {
+      const long long o = base + i;
+      mat = __float_as_int(bp.gbuffer[6 * N + o]);
+      if (mat >= kMaxMaterials) mat = -1;
+      if (mat >= 0) {
+        const float P[3] = {bp.gbuffer[o], bp.gbuffer[N + o], bp.gbuffer[2 * N + o]};
+        const float n[3] = {bp.gbuffer[3 * N + o], bp.gbuffer[4 * N + o], bp.gbuffer[5 * N + o]};
+        const float g[3] = {bp.d_rgb[3 * o], bp.d_rgb[3 * o + 1], bp.d_rgb[3 * o + 2]};
+        const float* m = sh.mat[mat];
+        float Vv[3];
+        if (sh.ortho) {
+          Vv[0] = 0.0f;
+          Vv[1] = 0.0f;
+          Vv[2] = 1.0f;
+        } else {
+          float rl = rsqrtf(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
+          Vv[0] = -P[0] * rl;
+          Vv[1] = -P[1] * rl;
+          Vv[2] = -P[2] * rl;
+        }
+        const float G = g[0] + g[1] + g[2];
+        const float gr = g[0] * m[0] + g[1] * m[1] + g[2] * m[2];
+        float sum_endl = 0.0f, sum_epw = 0.0f, acc[3] = {0.0f, 0.0f, 0.0f};
+        for (int l = 0; l < sh.n_lights; l++) {
+          float L[3], Lv[3] = {0.0f, 0.0f, 0.0f}, E, d2 = 1.0f, rinv = 1.0f;
+          const float I = sh.lv[l][3];
+          if (sh.light_type == 0) {
+            for (int k = 0; k < 3; k++) Lv[k] = sh.lv[l][k] - P[k];
+            d2 = Lv[0] * Lv[0] + Lv[1] * Lv[1] + Lv[2] * Lv[2];
+            rinv = rsqrtf(d2);
+            for (int k = 0; k < 3; k++) L[k] = Lv[k] * rinv;
+            E = I * (rinv * rinv);
+          } else {
+            for (int k = 0; k < 3; k++) L[k] = sh.lv[l][k];
+            E = I;
+          }
+          const float ndl_raw = n[0] * L[0] + n[1] * L[1] + n[2] * L[2];
+          const bool lit = ndl_raw > 0.0f;
+          const float ndl = lit ? ndl_raw : 0.0f;
+          float pw = 0.0f, ndh = 0.0f, H[3] = {0.0f, 0.0f, 0.0f}, rh = 0.0f;
+          bool has_h = false;
+          if (lit) {
+            float Hv[3] = {L[0] + Vv[0], L[1] + Vv[1], L[2] + Vv[2]};
+            float h2 = Hv[0] * Hv[0] + Hv[1] * Hv[1] + Hv[2] * Hv[2];
+            if (h2 > 0.0f) {
+              has_h = true;
+              rh = rsqrtf(h2);
+              for (int k = 0; k < 3; k++) H[k] = Hv[k] * rh;
+              ndh = fmaxf(0.0f, n[0] * H[0] + n[1] * H[1] + n[2] * H[2]);
+              pw = powf(ndh, m[4]);
+            }
+          }
+          const float spec = m[3] * pw;
+          for (int k = 0; k < 3; k++) acc[k] += E * (m[k] * ndl + spec);
+          sum_endl += E * ndl;
+          sum_epw += E * pw;
+          const float dE = scale * (gr * ndl + G * spec);
+          const float dndl = lit ? scale * E * gr : 0.0f;
+          // alpha * ndh^(alpha - 1) = alpha * pw / ndh for ndh > 0
+          const float dndh = (has_h && ndh > 0.0f) ? scale * E * G * m[3] * m[4] * (pw / ndh) : 0.0f;
+          float dL[3] = {dndl * n[0], dndl * n[1], dndl * n[2]};
+          if (dndh != 0.0f) {
+            float dH[3] = {dndh * n[0], dndh * n[1], dndh * n[2]};
+            float hd = H[0] * dH[0] + H[1] * dH[1] + H[2] * dH[2];
+            for (int k = 0; k < 3; k++) dL[k] += (dH[k] - H[k] * hd) * rh;
+          }
+          if (sh.light_type == 0) {
+            dI[l] += dE * (rinv * rinv);
+            const float dd2 = -dE * I * (rinv * rinv) * (rinv * rinv);
+            const float ld = L[0] * dL[0] + L[1] * dL[1] + L[2] * dL[2];
+            for (int k = 0; k < 3; k++) dlv[l][k] += (dL[k] - L[k] * ld) * rinv + 2.0f * dd2 * Lv[k];
+          } else {
+            dI[l] += dE;
+            for (int k = 0; k < 3; k++) dlv[l][k] += dL[k];
+          }
+        }
+        for (int k = 0; k < 3; k++) dm[k] = g[k] * scale * (sh.amb[k] + sum_endl);
+        dm[3] = scale * G * sum_epw;
+        float e = 0.0f;
+        for (int k = 0; k < 3; k++) e += g[k] * scale * (sh.amb[k] * m[k] + acc[k]);
+        dev += ln2 * e;
+      }
+    }
+    // segmented warp reduction over the materials present in these 32 pixels
+    unsigned pending = __ballot_sync(kFull, mat >= 0);
+    while (pending) {
+      const int leader = __ffs(pending) - 1;
+      const int mm = __shfl_sync(kFull, mat, leader);
+      const bool mine = mat == mm;
+      float v0 = warp_sum(mine ? dm[0] : 0.0f), v1 = warp_sum(mine ? dm[1] : 0.0f);
+      float v2 = warp_sum(mine ? dm[2] : 0.0f), v3 = warp_sum(mine ? dm[3] : 0.0f);
+      if (lane == 0) {
+        sh.wmat[warp][mm][0] += v0;
+        sh.wmat[warp][mm][1] += v1;
+        sh.wmat[warp][mm][2] += v2;
+        sh.wmat[warp][mm][3] += v3;
+      }
+      pending &= ~__ballot_sync(kFull, mine);
+    }
+  }
+  // per-thread light and exposure sums -> per warp (fixed tree) -> per CTA (warp order)
+  for (int l = 0; l < kMaxLights; l++) {
+    for (int k = 0; k < 3; k++) {
+      float v = warp_sum(dlv[l][k]);
+      if (lane == 0) sh.wred[warp][l * 4 + k] = v;
+    }
+    float v = warp_sum(dI[l]);
+    if (lane == 0) sh.wred[warp][l * 4 + 3] = v;
+  }
+  {
+    float v = warp_sum(dev);
+    if (lane == 0) sh.wred[warp][kMaxLights * 4] = v;
+  }
+  __syncthreads();
+  float* out = bp.partial + ((size_t)cam * bp.blocks_per_img + blk) * kGradFloats;
+  for (int k = tid; k < kMaxMaterials * 4; k += kBwdThreads) {
+    float v = 0.0f;
+    for (int w = 0; w < kBwdWarps; w++) v += (&sh.wmat[w][0][0])[k];
+    out[k] = v;
+  }
+  if (tid < kMaxLights) {
+    const int l = tid;
+    float dv[3], di = 0.0f;
+    for (int k = 0; k < 3; k++) {
+      dv[k] = 0.0f;
+      for (int w = 0; w < kBwdWarps; w++) dv[k] += sh.wred[w][l * 4 + k];
+    }
+    for (int w = 0; w < kBwdWarps; w++) di += sh.wred[w][l * 4 + 3];
+    // view -> world: point p_v = R p + t, so dp = R^T dp_v; direction L_v = -R d, so dd = -R^T dL_v
+    const float sgn = sh.light_type == 0 ? 1.0f : -1.0f;
+    for (int j = 0; j < 3; j++)
+      out[kMaxMaterials * 4 + l * 4 + j] =
+          sgn * (sh.V[0 * 4 + j] * dv[0] + sh.V[1 * 4 + j] * dv[1] + sh.V[2 * 4 + j] * dv[2]);
+    out[kMaxMaterials * 4 + l * 4 + 3] = di;
+  }
+  if (tid == 0) {
+    float v = 0.0f;
+    for (int w = 0; w < kBwdWarps; w++) v += sh.wred[w][kMaxLights * 4];
+    out[kMaxMaterials * 4 + kMaxLights * 4] = v;
+  }
+}
+
+// One thread per (sample, gradient float): sum the sample's partial rows in (camera, block) order.
+__global__ void backward_reduce_kernel(BackwardParams bp) {
+  const Params& p = bp.base;
+  const int s = blockIdx.x, k = threadIdx.x;
+  if (k >= kGradFloats) return;
+  float v = 0.0f;
+  for (int c = p.cam_offset[s]; c < p.cam_offset[s + 1]; c++)
+    for (int b = 0; b < bp.blocks_per_img; b++) v += bp.partial[((size_t)c * bp.blocks_per_img + b) * kGradFloats + k];
+  if (k < kMaxMaterials * 4) {
+    if (bp.d_material) bp.d_material[(size_t)s * kMaxMaterials * 4 + k] = v;
+  } else if (k < kMaxMaterials * 4 + kMaxLights * 4) {
+    if (bp.d_light) bp.d_light[(size_t)s * kMaxLights * 4 + (k - kMaxMaterials * 4)] = v;
+  } else {
+    if (bp.d_exposure) bp.d_exposure[s] = v;
+  }
+}
+
+}  // namespace
+
+int launch_backward(const BackwardParams& bp, int threads, void* stream, char* err, size_t errlen) {
+  (void)threads;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  backward_partial_kernel<<<dim3(bp.base.n_cams, bp.blocks_per_img), kBwdThreads, 0, st>>>(bp);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    backward_reduce_kernel<<<bp.base.n_samples, 160, 0, st>>>(bp);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    snprintf(err, errlen, "backward launch failed: %s", cudaGetErrorString(e));
+    return 1;
+  }
+  return 0;
+}
+
+}  // namespace orrb

@@ -1,0 +1,147 @@
+// orrb_internal.h -- layouts shared by the host API (orrb_api.cpp) and the
+// CUDA kernels (orrb_render.cu, orrb_backward.cu).  Not part of the C-ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#ifdef __CUDACC__
+#define ORRB_HD __host__ __device__
+#else
+#define ORRB_HD
+#endif
+
+namespace orrb {
+
+constexpr int kMaxLights = 4;
+constexpr int kMaxMaterials = 32;
+constexpr int kMeshletVerts = 64;
+constexpr int kMeshletTris = 128;
+constexpr int kMaxSpanTiles = 4;       // a binned triangle overlaps at most this many tiles
+constexpr int kSmallBoxFix = 64 * 256; // binned triangles have a vertex box below 64 px (fixed point)
+constexpr float kGuardPx = 1048576.0f; // 2^20 px
+
+// ---- mesh arena ----------------------------------------------------------
+struct MeshEntry {        // 16 B
+  int32_t meshlet_begin;
+  int32_t meshlet_count;
+  int32_t n_tris;
+  int32_t n_verts;
+};
+
+struct MeshletEntry {     // 16 B
+  int32_t vert_begin;     // into the arena's vertex arrays
+  int32_t tri_begin;      // into the arena's packed triangle array
+  int32_t counts;         // n_verts | n_tris << 16
+  int32_t mesh_tri_base;  // mesh-local index of the meshlet's first triangle
+};
+
+struct ArenaLayout {      // byte offsets inside the arena, all 256-aligned
+  size_t meshes, meshlets, vpos, vnrm, tris, total;
+  int32_t n_meshes, n_meshlets, n_verts, n_tris;
+};
+
+// ---- one visible (sub)triangle, 80 B ---------------------------------------
+// q0 = X0, Y0, X1, Y1 (8.8 fixed point)     q1 = X2, Y2, iw0, iw1 (float bits)
+// q2 = iw2, mat | seg << 16, n0x, n0y       q3 = n0z, n1x, n1y, n1z
+// q4 = n2x, n2y, n2z, unused
+// iw = 1/w (perspective) or view depth (orthographic).
+struct alignas(16) Record {
+  int32_t q0[4];
+  int32_t q1[4];
+  int32_t q2[4];
+  float q3[4];
+  float q4[4];
+};
+
+// ---- kernel parameters -----------------------------------------------------
+struct Params {
+  // batch (device)
+  int32_t n_samples, n_cams;
+  const int32_t* inst_offset;
+  const uint32_t* inst_mesh;
+  const float* inst_pose;
+  const uint8_t* inst_seg;
+  const int16_t* inst_mat_base;
+  const int32_t* cam_offset;
+  const int32_t* cam_sample;
+  const float* cam_view;
+  const float* cam_intr;
+  const int32_t* cam_wh;
+  const int64_t* img_offset;
+  const float* light;
+  const int32_t* light_meta;
+  const float* material;
+  const float* exposure_ev;
+  const float* ambient;
+  const float* background;
+  // outputs (device, any may be null)
+  uint8_t* rgb;
+  float* depth;
+  uint16_t* normal;
+  uint8_t* seg;
+  float* rgb_linear;
+  float* gbuffer;
+  int64_t total_pixels;
+  // mesh set
+  const MeshEntry* meshes;
+  const MeshletEntry* meshlets;
+  const float4* vpos;
+  const float4* vnrm;
+  const uint32_t* tris;  // 3 local vertex indices (u8) | tri_mat << 24
+  int32_t n_meshes;
+  // declared bounds
+  int32_t t_max, inst_max, w_max, h_max;
+  // tiling
+  int32_t tile_w, tile_h, max_tiles;
+  // workspace
+  uint32_t* status;
+  uint32_t* work_counter;
+  char* scratch;
+  size_t slot_bytes;
+  int32_t n_slots;
+  // plain mode: the sample this launch renders (-1 in fused mode)
+  int32_t plain_sample;
+};
+
+// Per-slot scratch (one image at a time): sizes in elements, from t_max.
+struct SlotLayout {
+  size_t rec, vis_key, vis_box, bins, big, tile_off, header, total;
+};
+
+ORRB_HD inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+ORRB_HD inline SlotLayout slot_layout(int t_max, int max_tiles) {
+  SlotLayout L;
+  size_t cap = 2 * size_t(t_max) + 2;
+  size_t o = 0;
+  L.header = o;   o = align256(o + 64);
+  L.rec = o;      o = align256(o + cap * sizeof(Record));
+  L.vis_key = o;  o = align256(o + cap * 4);
+  L.vis_box = o;  o = align256(o + cap * 8);
+  L.bins = o;     o = align256(o + cap * kMaxSpanTiles * 4);
+  L.big = o;      o = align256(o + cap * 4);
+  L.tile_off = o; o = align256(o + (size_t(max_tiles) + 1) * 4);
+  L.total = o;
+  return L;
+}
+
+// Host entry points implemented in the .cu files.
+int launch_render(const Params& p, int mode, int threads, int ctas_per_sm, int max_cams_per_sample,
+                  void* stream, char* err, size_t errlen);
+size_t render_smem_bytes(int threads, int tile_w, int tile_h, int inst_max, int max_tiles);
+
+struct BackwardParams {
+  Params base;           // batch + mesh-independent fields
+  const float* gbuffer;
+  const float* d_rgb;
+  float* d_material;
+  float* d_light;
+  float* d_exposure;
+  float* partial;        // [n_cams][blocks_per_img][kGradFloats]
+  int32_t blocks_per_img;
+};
+constexpr int kGradFloats = kMaxMaterials * 4 + kMaxLights * 4 + 1;  // 145
+int launch_backward(const BackwardParams& p, int threads, void* stream, char* err, size_t errlen);
+
+}  // namespace orrb

@@ -1,0 +1,1052 @@
+// orrb_render.cu -- forward renderer kernels for sm_103a.
+//
+// One image is processed in three phases, written once as device functions
+// and run either inside one persistent kernel (fused mode: each CTA pulls
+// images from a queue and runs all three phases on its own scratch slot) or
+// as three launches per sample (plain mode):
+//
+//   G  geometry: per (instance, 64-vertex/128-triangle mesh cluster) a warp
+//      composes MV = V * M, transforms the cluster's vertices into view space,
+//      projects and snaps them to 8 fractional bits, clips triangles at the
+//      near plane (Sutherland-Hodgman, cut computed in fp64), sets up and
+//      culls them, writes one 80-byte record per visible (sub)triangle at a
+//      slot fixed by its primitive id, and appends (key, pixel box) to the
+//      image's visible list with a warp prefix scan and one atomic per warp.
+//   B  binning: triangles whose vertex box is under 64 px and that touch at
+//      most 4 screen tiles are counted per tile, the counts are prefix-summed
+//      and the keys scattered into per-tile bins; the rest go to a "large"
+//      list that every tile tests itself (the table plane, block faces).
+//   R  raster + shade, per tile: large triangles pixel-parallel, binned ones
+//      triangle-parallel, each covered pixel centre folding
+//      (depth bits << 32 | key) into a shared-memory 64-bit atomicMin; then
+//      every pixel resolves its winner, interpolates the normal, shades
+//      (Blinn-Phong, point/directional lights, exposure) and writes the four
+//      channels; RGB and normals are staged in shared memory and written
+//      with 16-byte vector stores.
+//
+// Everything that decides coverage, visibility or depth (transform, clip,
+// projection, snapping, edge functions, depth) uses explicitly rounded fp32
+// intrinsics (__fmul_rn, __fadd_rn, __fdiv_rn: never contracted to FMA) or
+// integers, so those channels are bit-identical to any correct
+// implementation of the same definition.  Shading uses ordinary fp32 math.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+
+#include "orrb.h"
+#include "orrb_internal.h"
+
+namespace orrb {
+namespace {
+
+constexpr unsigned long long kEmpty = ~0ull;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kBigChunk = 128;
+
+struct ImageInfo {
+  int cam, s, W, H, inst0, n_inst, ortho, T, valid;
+  int tw, th, ntx, n_tiles;
+  long long px_off;
+  float fx, fy, cx, cy, near, inv_fx, inv_fy;
+  float V[12];
+  int n_lights, light_type;
+  float scale;
+  float amb[3], bg[3];
+  float lv[kMaxLights][4];  // view-space light position (point) or direction to the light, intensity
+};
+
+struct CtaShared {
+  ImageInfo im;
+  float mat[kMaxMaterials][5];
+  int n_vis, n_big, n_big_tile, img;
+  int scan_tmp[33];
+};
+
+struct WarpG {  // per-warp cluster staging for phase G
+  float mv[12];
+  float pv[kMeshletVerts * 3];
+  float nv[kMeshletVerts * 3];
+  int X[kMeshletVerts];
+  int Y[kMeshletVerts];
+  float iw[kMeshletVerts];
+  int flag[kMeshletVerts];  // bit 0: in front of the near plane; bit 1: inside the guard band
+};
+
+struct BigEntry {  // a large triangle prepared for one tile
+  int X[3], Y[3];
+  float iw[3];
+  float fA;
+  unsigned key;
+  int tl;  // top-left flags of edges 0, 1, 2 in bits 0, 1, 2
+};
+
+struct WarpTri {  // a binned triangle staged for the warp's fragment expansion (64 B)
+  int X[3], Y[3];
+  float iw[3];
+  float fA;
+  unsigned key;
+  int tl;
+  int px0, py0, bw, pad;
+};
+
+struct Scratch {
+  Record* rec;
+  uint32_t* vis_key;
+  uint2* vis_box;
+  uint32_t* bins;
+  uint32_t* big;
+  uint32_t* tile_off;
+  int* header;  // [0] n_vis, [1] n_big
+};
+
+struct SmemLayout {
+  size_t inst_tab, uni, g_size, b_size, r_keys, r_big, r_wtri, r_woff, r_rgb, r_nrm, r_size, total;
+};
+
+__host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
+
+__host__ __device__ inline SmemLayout smem_layout(int threads, int tile_w, int tile_h, int inst_max, int max_tiles) {
+  SmemLayout L;
+  size_t tile_px = size_t(tile_w) * tile_h;
+  L.inst_tab = 0;
+  L.uni = al16(size_t(2) * (inst_max + 2) * sizeof(int));
+  L.g_size = size_t(threads / 32) * al16(sizeof(WarpG));
+  L.b_size = al16(size_t(2) * (max_tiles + 2) * sizeof(int));
+  L.r_keys = 0;
+  L.r_big = al16(tile_px * 8);
+  L.r_wtri = L.r_big + al16(size_t(kBigChunk) * sizeof(BigEntry));
+  L.r_woff = L.r_wtri + al16(size_t(threads) * sizeof(WarpTri));
+  L.r_rgb = L.r_woff + al16(size_t(threads) * sizeof(int));
+  L.r_nrm = L.r_rgb + al16(tile_px * 3 + 16);
+  L.r_size = L.r_nrm + al16(tile_px * 6 + 16);
+  size_t u = L.g_size > L.b_size ? L.g_size : L.b_size;
+  u = u > L.r_size ? u : L.r_size;
+  L.total = L.uni + u;
+  return L;
+}
+
+__device__ inline Scratch slot_scratch(const Params& p, int slot) {
+  SlotLayout L = slot_layout(p.t_max, p.max_tiles);
+  char* b = p.scratch + size_t(slot) * p.slot_bytes;
+  Scratch s;
+  s.header = reinterpret_cast<int*>(b + L.header);
+  s.rec = reinterpret_cast<Record*>(b + L.rec);
+  s.vis_key = reinterpret_cast<uint32_t*>(b + L.vis_key);
+  s.vis_box = reinterpret_cast<uint2*>(b + L.vis_box);
+  s.bins = reinterpret_cast<uint32_t*>(b + L.bins);
+  s.big = reinterpret_cast<uint32_t*>(b + L.big);
+  s.tile_off = reinterpret_cast<uint32_t*>(b + L.tile_off);
+  return s;
+}
+
+__device__ inline void flag_status(const Params& p, unsigned bits) { atomicOr(p.status, bits); }
+
+// Exclusive scan of a[0..n) in place over the whole block; writes the total to a[n].
+__device__ void block_exclusive_scan(int* a, int n, int* tmp) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int per = (n + nt - 1) / nt;
+  const int b = min(tid * per, n), e = min(b + per, n);
+  int sum = 0;
+  for (int i = b; i < e; i++) sum += a[i];
+  const int lane = tid & 31, warp = tid >> 5;
+  int incl = sum;
+  for (int o = 1; o < 32; o <<= 1) {
+    int v = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) tmp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int nw = nt >> 5;
+    int v = lane < nw ? tmp[lane] : 0;
+    int inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      int u = __shfl_up_sync(kFull, inc, o);
+      if (lane >= o) inc += u;
+    }
+    if (lane < nw) tmp[lane] = inc - v;
+    if (lane == nw - 1) tmp[32] = inc;
+  }
+  __syncthreads();
+  int run = tmp[warp] + incl - sum;
+  for (int i = b; i < e; i++) {
+    int v = a[i];
+    a[i] = run;
+    run += v;
+  }
+  if (tid == 0) a[n] = tmp[32];
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// per-image set-up (camera, lights, materials, instance tables)
+// ---------------------------------------------------------------------------
+__device__ void setup_image(const Params& p, int cam, CtaShared& sh, int* mprefix, int* tprefix, bool tables) {
+  ImageInfo& im = sh.im;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    im.cam = cam;
+    int s = p.cam_sample[cam];
+    im.s = s;
+    im.W = p.cam_wh[cam * 2 + 0];
+    im.H = p.cam_wh[cam * 2 + 1];
+    im.valid = 1;
+    const float* in = p.cam_intr + cam * 6;
+    im.fx = in[0];
+    im.fy = in[1];
+    im.cx = in[2];
+    im.cy = in[3];
+    im.near = in[4];
+    im.ortho = in[5] != 0.0f;
+    im.inv_fx = 1.0f / im.fx;
+    im.inv_fy = 1.0f / im.fy;
+    if (s < 0 || s >= p.n_samples || im.W < 1 || im.H < 1 || im.W > p.w_max || im.H > p.h_max ||
+        !(im.near > 0.0f) || !(im.fx != 0.0f) || !(im.fy != 0.0f)) {
+      flag_status(p, ORRB_DEV_BAD_CAMERA);
+      im.valid = 0;
+      s = 0;
+      im.s = 0;
+    }
+    for (int k = 0; k < 12; k++) im.V[k] = p.cam_view[cam * 12 + k];
+    im.px_off = p.img_offset[cam];
+    if (im.valid && (im.px_off < 0 || im.px_off + (long long)im.W * im.H > p.total_pixels)) {
+      flag_status(p, ORRB_DEV_BAD_CAMERA);  // the image would not fit in the output arrays
+      im.valid = 0;
+    }
+    im.inst0 = p.inst_offset[s];
+    im.n_inst = p.inst_offset[s + 1] - im.inst0;
+    if (im.n_inst < 0 || im.n_inst > p.inst_max) {
+      flag_status(p, ORRB_DEV_BAD_INSTANCE);
+      im.valid = 0;
+      im.n_inst = 0;
+    }
+    im.tw = min(im.W, p.tile_w);
+    im.th = p.tile_h;
+    im.ntx = (im.W + im.tw - 1) / im.tw;
+    im.n_tiles = im.ntx * ((im.H + im.th - 1) / im.th);
+    int nl = p.light_meta[s * 2 + 0];
+    if (nl < 0 || nl > kMaxLights) {
+      flag_status(p, ORRB_DEV_BAD_LIGHTS);
+      nl = nl < 0 ? 0 : kMaxLights;
+    }
+    im.n_lights = nl;
+    im.light_type = p.light_meta[s * 2 + 1];
+    for (int l = 0; l < nl; l++) {
+      const float* L4 = p.light + (s * kMaxLights + l) * 4;
+      for (int i = 0; i < 3; i++) {
+        float r = im.V[i * 4 + 0] * L4[0] + im.V[i * 4 + 1] * L4[1] + im.V[i * 4 + 2] * L4[2];
+        im.lv[l][i] = im.light_type == 0 ? r + im.V[i * 4 + 3] : -r;
+      }
+      im.lv[l][3] = L4[3];
+    }
+    im.scale = exp2f(p.exposure_ev[s]);
+    for (int k = 0; k < 3; k++) {
+      im.amb[k] = p.ambient[s * 3 + k];
+      im.bg[k] = p.background[s * 3 + k];
+    }
+    sh.n_vis = 0;
+    sh.n_big = 0;
+  }
+  __syncthreads();
+  for (int k = tid; k < kMaxMaterials * 5; k += blockDim.x)
+    sh.mat[k / 5][k % 5] = p.material[(size_t)im.s * kMaxMaterials * 5 + k];
+  if (!tables) {
+    __syncthreads();
+    return;
+  }
+  const int n = im.n_inst;
+  for (int i = tid; i < n; i += blockDim.x) {
+    uint32_t mesh = p.inst_mesh[im.inst0 + i];
+    if (mesh >= (uint32_t)p.n_meshes) {
+      flag_status(p, ORRB_DEV_BAD_INSTANCE);
+      mprefix[i] = 0;
+      tprefix[i] = 0;
+    } else {
+      MeshEntry me = p.meshes[mesh];
+      mprefix[i] = me.meshlet_count;
+      tprefix[i] = me.n_tris;
+    }
+  }
+  __syncthreads();
+  block_exclusive_scan(mprefix, n, sh.scan_tmp);
+  block_exclusive_scan(tprefix, n, sh.scan_tmp);
+  if (tid == 0) {
+    im.T = tprefix[n];
+    if (im.T > p.t_max) {
+      flag_status(p, ORRB_DEV_TOO_MANY_TRIS);
+      im.valid = 0;
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// phase G helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void project(const ImageInfo& im, float x, float y, float z, int& X, int& Y, float& iw,
+                                        int& ok) {
+  float xs, ys;
+  if (im.ortho) {
+    iw = -z;
+    xs = __fadd_rn(im.cx, __fmul_rn(im.fx, x));
+    ys = __fsub_rn(im.cy, __fmul_rn(im.fy, y));
+  } else {
+    iw = __fdiv_rn(1.0f, -z);
+    xs = __fadd_rn(im.cx, __fmul_rn(im.fx, __fmul_rn(x, iw)));
+    ys = __fsub_rn(im.cy, __fmul_rn(im.fy, __fmul_rn(y, iw)));
+  }
+  ok = fabsf(xs) < kGuardPx && fabsf(ys) < kGuardPx;
+  X = ok ? __float2int_rn(__fmul_rn(xs, 256.0f)) : 0;
+  Y = ok ? __float2int_rn(__fmul_rn(ys, 256.0f)) : 0;
+}
+
+// Set up a snapped triangle: cull (area <= 0), clamp its pixel box to the image.
+// Returns false if culled or entirely off-screen.
+__device__ __forceinline__ bool setup_box(const ImageInfo& im, const int X[3], const int Y[3], uint2& box) {
+  long long A = (long long)(X[2] - X[0]) * (Y[1] - Y[0]) - (long long)(Y[2] - Y[0]) * (X[1] - X[0]);
+  if (A <= 0) return false;
+  int xmin = min(X[0], min(X[1], X[2])), xmax = max(X[0], max(X[1], X[2]));
+  int ymin = min(Y[0], min(Y[1], Y[2])), ymax = max(Y[0], max(Y[1], Y[2]));
+  // pixel x has its centre at 256x + 128
+  int x0 = max(0, -((128 - xmin) >> 8)), x1 = min(im.W - 1, (xmax - 128) >> 8);
+  int y0 = max(0, -((128 - ymin) >> 8)), y1 = min(im.H - 1, (ymax - 128) >> 8);
+  if (x0 > x1 || y0 > y1) return false;
+  unsigned small = (xmax - xmin) < kSmallBoxFix && (ymax - ymin) < kSmallBoxFix;
+  box.x = unsigned(x0) | (unsigned(x1) << 16) | (small << 31);
+  box.y = unsigned(y0) | (unsigned(y1) << 16);
+  return true;
+}
+
+__device__ __forceinline__ void write_record(Record* r, const int X[3], const int Y[3], const float iw[3],
+                                             const float n[3][3], int mat, int seg) {
+  int4* q = reinterpret_cast<int4*>(r);
+  q[0] = make_int4(X[0], Y[0], X[1], Y[1]);
+  q[1] = make_int4(X[2], Y[2], __float_as_int(iw[0]), __float_as_int(iw[1]));
+  q[2] = make_int4(__float_as_int(iw[2]), mat | (seg << 16), __float_as_int(n[0][0]), __float_as_int(n[0][1]));
+  float4* f = reinterpret_cast<float4*>(r);
+  f[3] = make_float4(n[0][2], n[1][0], n[1][1], n[1][2]);
+  f[4] = make_float4(n[2][0], n[2][1], n[2][2], 0.0f);
+}
+
+struct CutVert {
+  float p[3], n[3];
+  int X, Y, ok;
+  float iw;
+};
+
+// Cut point on edge (in -> out) with the near plane, fp64 rounded once to fp32, z = -near.
+__device__ __noinline__ void cut_vertex(const ImageInfo& im, const float* pin, const float* nin, const float* pout,
+                                        const float* nout, CutVert& c) {
+  double t = __ddiv_rn(__dsub_rn(-(double)im.near, (double)pin[2]), __dsub_rn((double)pout[2], (double)pin[2]));
+  for (int k = 0; k < 3; k++) {
+    c.p[k] = __double2float_rn(__dadd_rn((double)pin[k], __dmul_rn(t, __dsub_rn((double)pout[k], (double)pin[k]))));
+    c.n[k] = __double2float_rn(__dadd_rn((double)nin[k], __dmul_rn(t, __dsub_rn((double)nout[k], (double)nin[k]))));
+  }
+  c.p[2] = -im.near;
+  project(im, c.p[0], c.p[1], c.p[2], c.X, c.Y, c.iw, c.ok);
+}
+
+// Near-plane clip of triangle (a, b, c) of the staged cluster; emits up to two
+// sub-triangles.  Vertex order follows Sutherland-Hodgman: for each edge
+// (v_k, v_k+1) emit v_k if inside, then the cut if the edge crosses.
+__device__ __noinline__ int clip_triangle(const Params& p, const ImageInfo& im, const WarpG* wg, const int vi[3],
+                                          int prim, int mat, int seg, const Scratch& sc, unsigned* keys,
+                                          uint2* boxes, unsigned* dropped) {
+  CutVert poly[4];
+  int np = 0;
+  for (int k = 0; k < 3; k++) {
+    int a = vi[k], b = vi[(k + 1) % 3];
+    int ain = wg->flag[a] & 1, bin = wg->flag[b] & 1;
+    if (ain) {
+      CutVert& o = poly[np++];
+      for (int d = 0; d < 3; d++) {
+        o.p[d] = wg->pv[a * 3 + d];
+        o.n[d] = wg->nv[a * 3 + d];
+      }
+      o.X = wg->X[a];
+      o.Y = wg->Y[a];
+      o.iw = wg->iw[a];
+      o.ok = (wg->flag[a] >> 1) & 1;
+    }
+    if (ain && !bin) cut_vertex(im, &wg->pv[a * 3], &wg->nv[a * 3], &wg->pv[b * 3], &wg->nv[b * 3], poly[np++]);
+    if (!ain && bin) cut_vertex(im, &wg->pv[b * 3], &wg->nv[b * 3], &wg->pv[a * 3], &wg->nv[a * 3], poly[np++]);
+  }
+  int emitted = 0;
+  for (int sub = 0; sub + 2 < np; sub++) {
+    const CutVert* q[3] = {&poly[0], &poly[sub + 1], &poly[sub + 2]};
+    if (!(q[0]->ok && q[1]->ok && q[2]->ok)) {
+      *dropped = 1;
+      continue;
+    }
+    int X[3] = {q[0]->X, q[1]->X, q[2]->X}, Y[3] = {q[0]->Y, q[1]->Y, q[2]->Y};
+    uint2 box;
+    if (!setup_box(im, X, Y, box)) continue;
+    float iw[3] = {q[0]->iw, q[1]->iw, q[2]->iw};
+    float n[3][3];
+    for (int k = 0; k < 3; k++)
+      for (int d = 0; d < 3; d++) n[k][d] = q[k]->n[d];
+    write_record(sc.rec + (size_t)sub * p.t_max + prim, X, Y, iw, n, mat, seg);
+    keys[emitted] = 2u * prim + sub;
+    boxes[emitted] = box;
+    emitted++;
+  }
+  return emitted;
+}
+
+// ---------------------------------------------------------------------------
+// phase G: geometry of one image
+// ---------------------------------------------------------------------------
+__device__ void geometry_phase(const Params& p, CtaShared& sh, const int* mprefix, const int* tprefix, WarpG* wgs,
+                               const Scratch& sc) {
+  const ImageInfo& im = sh.im;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  WarpG* wg = wgs + warp;
+  const int jobs = mprefix[im.n_inst];
+  unsigned dropped = 0, badmat = 0;
+  for (int j = warp; j < jobs; j += nw) {
+    int lo = 0, hi = im.n_inst;  // mprefix[lo] <= j < mprefix[hi]
+    while (hi - lo > 1) {
+      int mid = (lo + hi) >> 1;
+      if (mprefix[mid] <= j) lo = mid;
+      else hi = mid;
+    }
+    const int inst = im.inst0 + lo;
+    const MeshEntry me = p.meshes[p.inst_mesh[inst]];
+    const MeshletEntry ml = p.meshlets[me.meshlet_begin + (j - mprefix[lo])];
+    if (lane < 12) {
+      const int r = lane >> 2, c = lane & 3;
+      const float* M = p.inst_pose + (size_t)inst * 12;
+      float s = __fmul_rn(im.V[r * 4 + 0], M[0 * 4 + c]);
+      s = __fadd_rn(s, __fmul_rn(im.V[r * 4 + 1], M[1 * 4 + c]));
+      s = __fadd_rn(s, __fmul_rn(im.V[r * 4 + 2], M[2 * 4 + c]));
+      if (c == 3) s = __fadd_rn(s, im.V[r * 4 + 3]);
+      wg->mv[lane] = s;
+    }
+    __syncwarp();
+    const int nv = ml.counts & 0xffff, nt = ml.counts >> 16;
+    for (int v = lane; v < nv; v += 32) {
+      const float4 P = p.vpos[ml.vert_begin + v];
+      const float4 N = p.vnrm[ml.vert_begin + v];
+      float pc[3];
+      for (int r = 0; r < 3; r++) {
+        const float* m = &wg->mv[r * 4];
+        pc[r] = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(m[0], P.x), __fmul_rn(m[1], P.y)), __fmul_rn(m[2], P.z)), m[3]);
+        wg->pv[v * 3 + r] = pc[r];
+        wg->nv[v * 3 + r] = __fadd_rn(__fadd_rn(__fmul_rn(m[0], N.x), __fmul_rn(m[1], N.y)), __fmul_rn(m[2], N.z));
+      }
+      int inside = pc[2] <= -im.near;
+      int X = 0, Y = 0, ok = 0;
+      float iw = 0.0f;
+      if (inside) project(im, pc[0], pc[1], pc[2], X, Y, iw, ok);
+      wg->X[v] = X;
+      wg->Y[v] = Y;
+      wg->iw[v] = iw;
+      wg->flag[v] = inside | (ok << 1);
+    }
+    __syncwarp();
+    const int prim_base = tprefix[lo] + ml.mesh_tri_base;
+    const int mat_base = p.inst_mat_base[inst];
+    const int seg = p.inst_seg[inst];
+    for (int base = 0; base < nt; base += 32) {
+      const int t = base + lane;
+      unsigned keys[2];
+      uint2 boxes[2];
+      int cnt = 0;
+      if (t < nt) {
+        const uint32_t tri = p.tris[ml.tri_begin + t];
+        const int vi[3] = {int(tri & 0xff), int((tri >> 8) & 0xff), int((tri >> 16) & 0xff)};
+        int mat = mat_base + int(tri >> 24);
+        if (mat < 0 || mat >= kMaxMaterials) {
+          badmat = 1;
+          mat = mat < 0 ? 0 : kMaxMaterials - 1;
+        }
+        const int prim = prim_base + t;
+        const int f0 = wg->flag[vi[0]], f1 = wg->flag[vi[1]], f2 = wg->flag[vi[2]];
+        if (f0 & f1 & f2 & 1) {
+          if (f0 & f1 & f2 & 2) {
+            int X[3] = {wg->X[vi[0]], wg->X[vi[1]], wg->X[vi[2]]};
+            int Y[3] = {wg->Y[vi[0]], wg->Y[vi[1]], wg->Y[vi[2]]};
+            if (setup_box(im, X, Y, boxes[0])) {
+              float iw[3] = {wg->iw[vi[0]], wg->iw[vi[1]], wg->iw[vi[2]]};
+              float n[3][3];
+              for (int k = 0; k < 3; k++)
+                for (int d = 0; d < 3; d++) n[k][d] = wg->nv[vi[k] * 3 + d];
+              write_record(sc.rec + prim, X, Y, iw, n, mat, seg);
+              keys[0] = 2u * prim;
+              cnt = 1;
+            }
+          } else {
+            dropped = 1;
+          }
+        } else if ((f0 | f1 | f2) & 1) {
+          cnt = clip_triangle(p, im, wg, vi, prim, mat, seg, sc, keys, boxes, &dropped);
+        }
+      }
+      // warp prefix scan of the per-lane counts, one atomic per warp
+      int incl = cnt;
+      for (int o = 1; o < 32; o <<= 1) {
+        int v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
+      }
+      const int total = __shfl_sync(kFull, incl, 31);
+      int wbase = 0;
+      if (lane == 31 && total) wbase = atomicAdd(&sh.n_vis, total);
+      wbase = __shfl_sync(kFull, wbase, 31);
+      int pos = wbase + incl - cnt;
+      for (int k = 0; k < cnt; k++) {
+        sc.vis_key[pos + k] = keys[k];
+        sc.vis_box[pos + k] = boxes[k];
+      }
+    }
+    __syncwarp();
+  }
+  if (dropped) flag_status(p, ORRB_DEV_DROPPED);
+  if (badmat) flag_status(p, ORRB_DEV_BAD_MATERIAL);
+}
+
+// ---------------------------------------------------------------------------
+// phase B: screen-tile binning
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool binned_span(uint2 box, int tw, int th, int& tx0, int& tx1, int& ty0, int& ty1) {
+  int x0 = box.x & 0xffff, x1 = (box.x >> 16) & 0x7fff, y0 = box.y & 0xffff, y1 = box.y >> 16;
+  tx0 = x0 / tw;
+  tx1 = x1 / tw;
+  ty0 = y0 / th;
+  ty1 = y1 / th;
+  return (box.x >> 31) && (tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= kMaxSpanTiles;
+}
+
+__device__ void bin_phase(const Params& p, CtaShared& sh, int* counts, int* cursor, const Scratch& sc) {
+  const ImageInfo& im = sh.im;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int t = tid; t < im.n_tiles; t += nt) counts[t] = 0;
+  __syncthreads();
+  const int n = sh.n_vis;
+  const int lane = tid & 31;
+  for (int e0 = 0; e0 < n; e0 += nt) {
+    const int e = e0 + tid;
+    bool big = false;
+    if (e < n) {
+      int tx0, tx1, ty0, ty1;
+      if (binned_span(sc.vis_box[e], im.tw, im.th, tx0, tx1, ty0, ty1)) {
+        for (int ty = ty0; ty <= ty1; ty++)
+          for (int tx = tx0; tx <= tx1; tx++) atomicAdd(&counts[ty * im.ntx + tx], 1);
+      } else {
+        big = true;
+      }
+    }
+    // ballot compaction of the large list: one atomic per warp
+    const unsigned m = __ballot_sync(kFull, big);
+    int wbase = 0;
+    if (lane == 0 && m) wbase = atomicAdd(&sh.n_big, __popc(m));
+    wbase = __shfl_sync(kFull, wbase, 0);
+    if (big) sc.big[wbase + __popc(m & ((1u << lane) - 1u))] = sc.vis_key[e];
+  }
+  __syncthreads();
+  block_exclusive_scan(counts, im.n_tiles, sh.scan_tmp);
+  for (int t = tid; t <= im.n_tiles; t += nt) {
+    sc.tile_off[t] = counts[t];
+    cursor[t] = counts[t];
+  }
+  __syncthreads();
+  for (int e = tid; e < n; e += nt) {
+    int tx0, tx1, ty0, ty1;
+    if (binned_span(sc.vis_box[e], im.tw, im.th, tx0, tx1, ty0, ty1)) {
+      const uint32_t key = sc.vis_key[e];
+      for (int ty = ty0; ty <= ty1; ty++)
+        for (int tx = tx0; tx <= tx1; tx++) sc.bins[atomicAdd(&cursor[ty * im.ntx + tx], 1)] = key;
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// phase R: raster + shade one tile
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int top_left(int ax, int ay, int bx, int by) {
+  int dx = bx - ax, dy = by - ay;
+  return (dy == 0 && dx < 0) || dy > 0;
+}
+
+// Fragment test at pixel centre (cx, cy): returns the 64-bit key or kEmpty.
+__device__ __forceinline__ unsigned long long fragment(const int X[3], const int Y[3], const float iw[3], float fA,
+                                                       int tl, unsigned key, int ortho, int cx, int cy) {
+  long long w0 = (long long)(cx - X[1]) * (Y[2] - Y[1]) - (long long)(cy - Y[1]) * (X[2] - X[1]);
+  long long w1 = (long long)(cx - X[2]) * (Y[0] - Y[2]) - (long long)(cy - Y[2]) * (X[0] - X[2]);
+  long long w2 = (long long)(cx - X[0]) * (Y[1] - Y[0]) - (long long)(cy - Y[0]) * (X[1] - X[0]);
+  if (!(w0 + (tl & 1) > 0 && w1 + ((tl >> 1) & 1) > 0 && w2 + ((tl >> 2) & 1) > 0)) return kEmpty;
+  float f0 = __ll2float_rn(w0), f1 = __ll2float_rn(w1), f2 = __ll2float_rn(w2);
+  float s = __fadd_rn(__fadd_rn(__fmul_rn(f0, iw[0]), __fmul_rn(f1, iw[1])), __fmul_rn(f2, iw[2]));
+  float depth = ortho ? __fdiv_rn(s, fA) : __fdiv_rn(fA, s);
+  return ((unsigned long long)__float_as_uint(depth) << 32) | key;
+}
+
+__device__ __forceinline__ void load_tri(const Record* r, int X[3], int Y[3], float iw[3]) {
+  const int4 q0 = reinterpret_cast<const int4*>(r)[0];
+  const int4 q1 = reinterpret_cast<const int4*>(r)[1];
+  const int q2x = reinterpret_cast<const int*>(r)[8];
+  X[0] = q0.x;
+  Y[0] = q0.y;
+  X[1] = q0.z;
+  Y[1] = q0.w;
+  X[2] = q1.x;
+  Y[2] = q1.y;
+  iw[0] = __int_as_float(q1.z);
+  iw[1] = __int_as_float(q1.w);
+  iw[2] = __int_as_float(q2x);
+}
+
+__device__ __forceinline__ void tri_setup(const int X[3], const int Y[3], float& fA, int& tl) {
+  long long A = (long long)(X[2] - X[0]) * (Y[1] - Y[0]) - (long long)(Y[2] - Y[0]) * (X[1] - X[0]);
+  fA = __ll2float_rn(A);
+  tl = top_left(X[1], Y[1], X[2], Y[2]) | (top_left(X[2], Y[2], X[0], Y[0]) << 1) |
+       (top_left(X[0], Y[0], X[1], Y[1]) << 2);
+}
+
+__device__ __forceinline__ const Record* rec_of(const Params& p, const Scratch& sc, unsigned key) {
+  return sc.rec + (size_t)(key & 1u) * p.t_max + (key >> 1);
+}
+
+__device__ void shade(const CtaShared& sh, const float P[3], const float n[3], int mat, float rgb[3]) {
+  const ImageInfo& im = sh.im;
+  const float* m = sh.mat[mat];
+  float Vv[3];
+  if (im.ortho) {
+    Vv[0] = 0.0f;
+    Vv[1] = 0.0f;
+    Vv[2] = 1.0f;
+  } else {
+    float rl = rsqrtf(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
+    Vv[0] = -P[0] * rl;
+    Vv[1] = -P[1] * rl;
+    Vv[2] = -P[2] * rl;
+  }
+  float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
+  for (int l = 0; l < im.n_lights; l++) {
+    float L[3], E;
+    if (im.light_type == 0) {
+      float Lv0 = im.lv[l][0] - P[0], Lv1 = im.lv[l][1] - P[1], Lv2 = im.lv[l][2] - P[2];
+      float d2 = Lv0 * Lv0 + Lv1 * Lv1 + Lv2 * Lv2;
+      float r = rsqrtf(d2);
+      L[0] = Lv0 * r;
+      L[1] = Lv1 * r;
+      L[2] = Lv2 * r;
+      E = im.lv[l][3] * (r * r);
+    } else {
+      L[0] = im.lv[l][0];
+      L[1] = im.lv[l][1];
+      L[2] = im.lv[l][2];
+      E = im.lv[l][3];
+    }
+    float ndl = fmaxf(0.0f, n[0] * L[0] + n[1] * L[1] + n[2] * L[2]);
+    float spec = 0.0f;
+    if (ndl > 0.0f && m[3] != 0.0f) {
+      float H0 = L[0] + Vv[0], H1 = L[1] + Vv[1], H2 = L[2] + Vv[2];
+      float h2 = H0 * H0 + H1 * H1 + H2 * H2;
+      if (h2 > 0.0f) {
+        float rh = rsqrtf(h2);
+        float ndh = fmaxf(0.0f, (n[0] * H0 + n[1] * H1 + n[2] * H2) * rh);
+        spec = m[3] * powf(ndh, m[4]);
+      }
+    }
+    c0 += E * (m[0] * ndl + spec);
+    c1 += E * (m[1] * ndl + spec);
+    c2 += E * (m[2] * ndl + spec);
+  }
+  rgb[0] = im.scale * (im.amb[0] * m[0] + c0);
+  rgb[1] = im.scale * (im.amb[1] * m[1] + c1);
+  rgb[2] = im.scale * (im.amb[2] * m[2] + c2);
+}
+
+__device__ __forceinline__ uint8_t quantise(float v) { return (uint8_t)floorf(fminf(fmaxf(v, 0.0f), 1.0f) * 255.0f + 0.5f); }
+
+// Copy nbytes from shared src to global dst, 16-byte vectors where both share alignment.
+__device__ void copy_out(char* dst, const char* src, int nbytes, int tid, int nt) {
+  const uintptr_t da = reinterpret_cast<uintptr_t>(dst), sa = reinterpret_cast<uintptr_t>(src);
+  if (((da ^ sa) & 15) == 0) {
+    int head = int((16 - (da & 15)) & 15);
+    if (head > nbytes) head = nbytes;
+    const int nvec = (nbytes - head) >> 4;
+    const int tail0 = head + (nvec << 4);
+    for (int i = tid; i < head; i += nt) dst[i] = src[i];
+    const uint4* s4 = reinterpret_cast<const uint4*>(src + head);
+    uint4* d4 = reinterpret_cast<uint4*>(dst + head);
+    for (int i = tid; i < nvec; i += nt) __stcs(d4 + i, s4[i]);
+    for (int i = tail0 + tid; i < nbytes; i += nt) dst[i] = src[i];
+  } else {
+    for (int i = tid; i < nbytes; i += nt) dst[i] = src[i];
+  }
+}
+
+__device__ void raster_tile(const Params& p, CtaShared& sh, const Scratch& sc, int tile, char* rbase,
+                            const SmemLayout& L) {
+  const ImageInfo& im = sh.im;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tx = tile % im.ntx, ty = tile / im.ntx;
+  const int x0 = tx * im.tw, y0 = ty * im.th;
+  const int cw = min(im.tw, im.W - x0), ch = min(im.th, im.H - y0);
+  const int npx = cw * ch;
+  unsigned long long* keys = reinterpret_cast<unsigned long long*>(rbase + L.r_keys);
+  BigEntry* bigs = reinterpret_cast<BigEntry*>(rbase + L.r_big);
+  const bool full_rows = cw == im.W;
+  const long long o0 = im.px_off + (long long)y0 * im.W + x0;
+  // staging buffers start at the destination's alignment modulo 16
+  char* st_rgb = rbase + L.r_rgb + (full_rows && p.rgb ? int((reinterpret_cast<uintptr_t>(p.rgb + 3 * o0)) & 15) : 0);
+  char* st_nrm =
+      rbase + L.r_nrm + (full_rows && p.normal ? int((reinterpret_cast<uintptr_t>(p.normal + 3 * o0)) & 15) : 0);
+
+  // large triangles first, pixel-parallel, in chunks staged in shared memory
+  for (int i = tid; i < npx; i += nt) keys[i] = kEmpty;
+  __syncthreads();
+  const int nbig = sh.n_big;
+  for (int c0 = 0; c0 < nbig; c0 += kBigChunk) {
+    if (tid == 0) sh.n_big_tile = 0;
+    __syncthreads();
+    const int lane = tid & 31;
+    for (int k0 = c0; k0 < min(nbig, c0 + kBigChunk); k0 += nt) {
+      const int k = k0 + tid;
+      bool keep = false;
+      BigEntry be;
+      if (k < min(nbig, c0 + kBigChunk)) {
+        be.key = sc.big[k];
+        load_tri(rec_of(p, sc, be.key), be.X, be.Y, be.iw);
+        int xmin = min(be.X[0], min(be.X[1], be.X[2])), xmax = max(be.X[0], max(be.X[1], be.X[2]));
+        int ymin = min(be.Y[0], min(be.Y[1], be.Y[2])), ymax = max(be.Y[0], max(be.Y[1], be.Y[2]));
+        int bx0 = -((128 - xmin) >> 8), bx1 = (xmax - 128) >> 8;
+        int by0 = -((128 - ymin) >> 8), by1 = (ymax - 128) >> 8;
+        keep = bx0 < x0 + cw && bx1 >= x0 && by0 < y0 + ch && by1 >= y0;
+        if (keep) tri_setup(be.X, be.Y, be.fA, be.tl);
+      }
+      const unsigned m = __ballot_sync(kFull, keep);
+      int wbase = 0;
+      if (lane == 0 && m) wbase = atomicAdd(&sh.n_big_tile, __popc(m));
+      wbase = __shfl_sync(kFull, wbase, 0);
+      if (keep) bigs[wbase + __popc(m & ((1u << lane) - 1u))] = be;
+    }
+    __syncthreads();
+    const int nb = sh.n_big_tile;
+    for (int i = tid; i < npx; i += nt) {
+      const int px = x0 + i % cw, py = y0 + i / cw;
+      const int cx = 256 * px + 128, cy = 256 * py + 128;
+      unsigned long long best = keys[i];
+      for (int b = 0; b < nb; b++) {
+        const BigEntry& be = bigs[b];
+        unsigned long long k = fragment(be.X, be.Y, be.iw, be.fA, be.tl, be.key, im.ortho, cx, cy);
+        best = k < best ? k : best;
+      }
+      keys[i] = best;
+    }
+    __syncthreads();
+  }
+  // binned triangles: each warp takes 32 at a time, prefix-sums their clamped pixel boxes
+  // and spreads the (triangle, pixel) candidates evenly over its lanes; every covered
+  // centre folds into the tile's keys with a shared-memory 64-bit atomicMin
+  {
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    WarpTri* wt = reinterpret_cast<WarpTri*>(rbase + L.r_wtri) + warp * 32;
+    int* woff = reinterpret_cast<int*>(rbase + L.r_woff) + warp * 32;
+    const int b0 = sc.tile_off[tile], b1 = sc.tile_off[tile + 1];
+    for (int c = b0 + warp * 32; c < b1; c += nw * 32) {
+      const int k = c + lane;
+      int cnt = 0;
+      if (k < b1) {
+        WarpTri T;
+        T.key = sc.bins[k];
+        load_tri(rec_of(p, sc, T.key), T.X, T.Y, T.iw);
+        tri_setup(T.X, T.Y, T.fA, T.tl);
+        int xmin = min(T.X[0], min(T.X[1], T.X[2])), xmax = max(T.X[0], max(T.X[1], T.X[2]));
+        int ymin = min(T.Y[0], min(T.Y[1], T.Y[2])), ymax = max(T.Y[0], max(T.Y[1], T.Y[2]));
+        T.px0 = max(x0, -((128 - xmin) >> 8));
+        T.py0 = max(y0, -((128 - ymin) >> 8));
+        const int bw = min(x0 + cw - 1, (xmax - 128) >> 8) - T.px0 + 1;
+        const int bh = min(y0 + ch - 1, (ymax - 128) >> 8) - T.py0 + 1;
+        T.bw = bw;
+        cnt = (bw > 0 && bh > 0) ? bw * bh : 0;
+        wt[lane] = T;
+      }
+      int incl = cnt;
+      for (int o = 1; o < 32; o <<= 1) {
+        int v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
+      }
+      woff[lane] = incl - cnt;
+      const int total = __shfl_sync(kFull, incl, 31);
+      __syncwarp();
+      for (int m = lane; m < total; m += 32) {
+        int lo = 0, hi = 31;  // largest t with woff[t] <= m (always a triangle with cnt > 0)
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (woff[mid] <= m) lo = mid;
+          else hi = mid - 1;
+        }
+        const WarpTri& T = wt[lo];
+        const int jj = m - woff[lo];
+        const int dy = jj / T.bw;
+        const int px = T.px0 + (jj - dy * T.bw), py = T.py0 + dy;
+        const unsigned long long f =
+            fragment(T.X, T.Y, T.iw, T.fA, T.tl, T.key, im.ortho, 256 * px + 128, 256 * py + 128);
+        if (f != kEmpty) atomicMin(&keys[(py - y0) * cw + (px - x0)], f);
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+
+  // resolve + shade + write
+  const long long N = p.total_pixels;
+  for (int i = tid; i < npx; i += nt) {
+    const int lx = i % cw, ly = i / cw;
+    const int px = x0 + lx, py = y0 + ly;
+    const long long o = im.px_off + (long long)py * im.W + px;
+    const unsigned long long k = keys[i];
+    float rgb[3], depth = 0.0f, n[3] = {0.0f, 0.0f, 0.0f}, P[3] = {0.0f, 0.0f, 0.0f};
+    int mat = -1, seg = 0;
+    if (k == kEmpty) {
+      rgb[0] = im.bg[0];
+      rgb[1] = im.bg[1];
+      rgb[2] = im.bg[2];
+    } else {
+      depth = __uint_as_float(unsigned(k >> 32));
+      const Record* r = rec_of(p, sc, unsigned(k));
+      int X[3], Y[3];
+      float iw[3];
+      load_tri(r, X, Y, iw);
+      const int4 q2 = reinterpret_cast<const int4*>(r)[2];
+      const float4 q3 = reinterpret_cast<const float4*>(r)[3];
+      const float4 q4 = reinterpret_cast<const float4*>(r)[4];
+      mat = q2.y & 0xffff;
+      seg = q2.y >> 16;
+      const int cx = 256 * px + 128, cy = 256 * py + 128;
+      float a0 = float(cx - X[1]) * float(Y[2] - Y[1]) - float(cy - Y[1]) * float(X[2] - X[1]);
+      float a1 = float(cx - X[2]) * float(Y[0] - Y[2]) - float(cy - Y[2]) * float(X[0] - X[2]);
+      float a2 = float(cx - X[0]) * float(Y[1] - Y[0]) - float(cy - Y[0]) * float(X[1] - X[0]);
+      if (!im.ortho) {
+        a0 *= iw[0];
+        a1 *= iw[1];
+        a2 *= iw[2];
+      }
+      n[0] = a0 * __int_as_float(q2.z) + a1 * q3.y + a2 * q4.x;
+      n[1] = a0 * __int_as_float(q2.w) + a1 * q3.z + a2 * q4.y;
+      n[2] = a0 * q3.x + a1 * q3.w + a2 * q4.z;
+      float l2 = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+      if (l2 > 0.0f) {
+        float rl = rsqrtf(l2);
+        n[0] *= rl;
+        n[1] *= rl;
+        n[2] *= rl;
+      }
+      const float ux = (float(px) + 0.5f - im.cx) * im.inv_fx;
+      const float uy = -((float(py) + 0.5f - im.cy) * im.inv_fy);
+      if (im.ortho) {
+        P[0] = ux;
+        P[1] = uy;
+        P[2] = -depth;
+      } else {
+        P[0] = depth * ux;
+        P[1] = depth * uy;
+        P[2] = -depth;
+      }
+      shade(sh, P, n, mat, rgb);
+    }
+    if (p.rgb) {
+      if (full_rows) {
+        st_rgb[3 * i + 0] = quantise(rgb[0]);
+        st_rgb[3 * i + 1] = quantise(rgb[1]);
+        st_rgb[3 * i + 2] = quantise(rgb[2]);
+      } else {
+        p.rgb[3 * o + 0] = quantise(rgb[0]);
+        p.rgb[3 * o + 1] = quantise(rgb[1]);
+        p.rgb[3 * o + 2] = quantise(rgb[2]);
+      }
+    }
+    if (p.normal) {
+      uint16_t h0 = __half_as_ushort(__float2half_rn(n[0])), h1 = __half_as_ushort(__float2half_rn(n[1])),
+               h2 = __half_as_ushort(__float2half_rn(n[2]));
+      if (full_rows) {
+        uint16_t* s16 = reinterpret_cast<uint16_t*>(st_nrm);
+        s16[3 * i + 0] = h0;
+        s16[3 * i + 1] = h1;
+        s16[3 * i + 2] = h2;
+      } else {
+        p.normal[3 * o + 0] = h0;
+        p.normal[3 * o + 1] = h1;
+        p.normal[3 * o + 2] = h2;
+      }
+    }
+    if (p.depth) __stcs(p.depth + o, depth);
+    if (p.seg) p.seg[o] = (uint8_t)seg;
+    if (p.rgb_linear) {
+      __stcs(p.rgb_linear + 3 * o + 0, rgb[0]);
+      __stcs(p.rgb_linear + 3 * o + 1, rgb[1]);
+      __stcs(p.rgb_linear + 3 * o + 2, rgb[2]);
+    }
+    if (p.gbuffer) {
+      __stcs(p.gbuffer + 0 * N + o, P[0]);
+      __stcs(p.gbuffer + 1 * N + o, P[1]);
+      __stcs(p.gbuffer + 2 * N + o, P[2]);
+      __stcs(p.gbuffer + 3 * N + o, n[0]);
+      __stcs(p.gbuffer + 4 * N + o, n[1]);
+      __stcs(p.gbuffer + 5 * N + o, n[2]);
+      __stcs(p.gbuffer + 6 * N + o, __int_as_float(mat));
+    }
+  }
+  if (full_rows) {
+    // the alignment offset is identical on both sides of the copy; 16 B vectors in the middle
+    // (16-byte staging slack keeps shared-memory reads in bounds)
+    // note: a CTA-wide barrier orders the staging writes before the copy
+    __syncthreads();
+    if (p.rgb) copy_out(reinterpret_cast<char*>(p.rgb + 3 * o0), st_rgb, 3 * npx, tid, nt);
+    if (p.normal) copy_out(reinterpret_cast<char*>(p.normal + 3 * o0), st_nrm, 6 * npx, tid, nt);
+  }
+  __syncthreads();
+}
+
+struct SmemPtrs {
+  int* mprefix;
+  int* tprefix;
+  char* uni;
+};
+
+__device__ inline SmemPtrs carve(char* smem, const Params& p) {
+  SmemPtrs s;
+  s.mprefix = reinterpret_cast<int*>(smem);
+  s.tprefix = s.mprefix + (p.inst_max + 2);
+  SmemLayout L = smem_layout(blockDim.x, p.tile_w, p.tile_h, p.inst_max, p.max_tiles);
+  s.uni = smem + L.uni;
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// fused: one persistent launch, CTAs pull whole images from a queue
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ CtaShared sh;
+  SmemPtrs sp = carve(smem, p);
+  const SmemLayout L = smem_layout(blockDim.x, p.tile_w, p.tile_h, p.inst_max, p.max_tiles);
+  const Scratch sc = slot_scratch(p, blockIdx.x);
+  while (true) {
+    if (threadIdx.x == 0) sh.img = atomicAdd(p.work_counter, 1);
+    __syncthreads();
+    const int cam = sh.img;
+    if (cam >= p.n_cams) break;
+    setup_image(p, cam, sh, sp.mprefix, sp.tprefix, true);
+    if (sh.im.valid) {
+      geometry_phase(p, sh, sp.mprefix, sp.tprefix, reinterpret_cast<WarpG*>(sp.uni), sc);
+      __syncthreads();
+      int* counts = reinterpret_cast<int*>(sp.uni);
+      bin_phase(p, sh, counts, counts + (p.max_tiles + 2), sc);
+      for (int t = 0; t < sh.im.n_tiles; t++) raster_tile(p, sh, sc, t, sp.uni, L);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// plain: three launches per sample; scratch slot = camera index within the sample
+// ---------------------------------------------------------------------------
+__device__ inline int plain_cam(const Params& p) {
+  const int s = p.plain_sample;
+  const int c = p.cam_offset[s] + blockIdx.x;
+  return c < p.cam_offset[s + 1] ? c : -1;
+}
+
+__global__ void __launch_bounds__(512, 2) plain_geometry_kernel(Params p) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ CtaShared sh;
+  const int cam = plain_cam(p);
+  if (cam < 0) return;
+  SmemPtrs sp = carve(smem, p);
+  const Scratch sc = slot_scratch(p, blockIdx.x);
+  setup_image(p, cam, sh, sp.mprefix, sp.tprefix, true);
+  if (!sh.im.valid) {
+    if (threadIdx.x == 0) sc.header[0] = -1;
+    return;
+  }
+  geometry_phase(p, sh, sp.mprefix, sp.tprefix, reinterpret_cast<WarpG*>(sp.uni), sc);
+  __syncthreads();
+  if (threadIdx.x == 0) sc.header[0] = sh.n_vis;
+}
+
+__global__ void __launch_bounds__(512, 2) plain_bin_kernel(Params p) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ CtaShared sh;
+  const int cam = plain_cam(p);
+  if (cam < 0) return;
+  SmemPtrs sp = carve(smem, p);
+  const Scratch sc = slot_scratch(p, blockIdx.x);
+  setup_image(p, cam, sh, sp.mprefix, sp.tprefix, false);
+  const int nvis = sc.header[0];
+  if (nvis < 0) return;
+  if (threadIdx.x == 0) sh.n_vis = nvis;
+  __syncthreads();
+  int* counts = reinterpret_cast<int*>(sp.uni);
+  bin_phase(p, sh, counts, counts + (p.max_tiles + 2), sc);
+  if (threadIdx.x == 0) sc.header[1] = sh.n_big;
+}
+
+__global__ void __launch_bounds__(512, 2) plain_raster_kernel(Params p) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ CtaShared sh;
+  const int cam = plain_cam(p);
+  if (cam < 0) return;
+  const Scratch sc = slot_scratch(p, blockIdx.x);
+  if (sc.header[0] < 0) return;
+  SmemPtrs sp = carve(smem, p);
+  const SmemLayout L = smem_layout(blockDim.x, p.tile_w, p.tile_h, p.inst_max, p.max_tiles);
+  setup_image(p, cam, sh, sp.mprefix, sp.tprefix, false);
+  if ((int)blockIdx.y >= sh.im.n_tiles) return;
+  if (threadIdx.x == 0) sh.n_big = sc.header[1];
+  __syncthreads();
+  raster_tile(p, sh, sc, blockIdx.y, sp.uni, L);
+}
+
+}  // namespace
+
+size_t render_smem_bytes(int threads, int tile_w, int tile_h, int inst_max, int max_tiles) {
+  return smem_layout(threads, tile_w, tile_h, inst_max, max_tiles).total;
+}
+
+int render_max_ctas_per_sm(int threads, size_t smem) {
+  int n = 0;
+  if (cudaFuncSetAttribute(render_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return -1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_fused_kernel, threads, smem) != cudaSuccess) return -1;
+  return n;
+}
+
+int launch_render(const Params& p, int mode, int threads, int n_ctas, int max_cams_per_sample, void* stream,
+                  char* err, size_t errlen) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t smem = render_smem_bytes(threads, p.tile_w, p.tile_h, p.inst_max, p.max_tiles);
+  cudaError_t e = cudaSuccess;
+  if (mode == 0) {
+    e = cudaFuncSetAttribute(render_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+      render_fused_kernel<<<n_ctas, threads, smem, st>>>(p);
+      e = cudaGetLastError();
+    }
+  } else {
+    const void* ks[3] = {(const void*)plain_geometry_kernel, (const void*)plain_bin_kernel,
+                         (const void*)plain_raster_kernel};
+    for (int k = 0; k < 3 && e == cudaSuccess; k++)
+      e = cudaFuncSetAttribute(ks[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    Params q = p;
+    for (int s = 0; s < p.n_samples && e == cudaSuccess; s++) {
+      q.plain_sample = s;
+      plain_geometry_kernel<<<max_cams_per_sample, threads, smem, st>>>(q);
+      plain_bin_kernel<<<max_cams_per_sample, threads, smem, st>>>(q);
+      plain_raster_kernel<<<dim3(max_cams_per_sample, p.max_tiles), threads, smem, st>>>(q);
+      e = cudaGetLastError();
+    }
+  }
+  if (e != cudaSuccess) {
+    snprintf(err, errlen, "render launch failed: %s", cudaGetErrorString(e));
+    return 1;
+  }
+  return 0;
+}
+
+}  // namespace orrb

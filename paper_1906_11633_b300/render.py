@@ -1,0 +1,210 @@
+"""Torch-level helpers around the C-ABI: device buffers, output tensors, autograd.
+
+PyTorch provides device memory and streams only; every step of rendering runs
+in liborrb.so's kernels.  Typical use::
+
+    r = Renderer(batch.meshes)                 # meshes resident once (Sec. 3, SSMS)
+    db = r.upload(batch)                       # per-sample state + randomization params
+    out = r.render(db)                         # dict of channel tensors (Sec. 4.4)
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass, field
+from typing import Dict, Optional
+
+import numpy as np
+import torch
+
+from . import lib as L
+
+_DESC_FIELDS = [n for n, _ in L.orrb_batch_desc._fields_]
+_DTYPES = dict(inst_offset=torch.int32, inst_mesh=torch.int32, inst_pose=torch.float32, inst_seg=torch.uint8,
+               inst_mat_base=torch.int16, cam_offset=torch.int32, cam_sample=torch.int32, cam_view=torch.float32,
+               cam_intr=torch.float32, cam_wh=torch.int32, img_offset=torch.int64, light=torch.float32,
+               light_meta=torch.int32, material=torch.float32, exposure_ev=torch.float32, ambient=torch.float32,
+               background=torch.float32)
+_NP = {torch.int32: np.int32, torch.float32: np.float32, torch.uint8: np.uint8, torch.int16: np.int16,
+       torch.int64: np.int64}
+
+
+def batch_shape(batch) -> L.orrb_batch_shape:
+    """Host-side shape of a scenegen.Batch."""
+    tps = batch.tris_per_sample()
+    return L.orrb_batch_shape(
+        n_samples=batch.n_samples, n_cams=batch.n_cams,
+        max_tris_per_sample=int(tps.max()) if len(tps) else 0,
+        max_inst_per_sample=int(np.diff(batch.inst_offset).max()) if batch.n_samples else 0,
+        max_cams_per_sample=int(np.diff(batch.cam_offset).max()) if batch.n_samples else 0,
+        max_width=int(batch.cam_wh[:, 0].max()) if batch.n_cams else 1,
+        max_height=int(batch.cam_wh[:, 1].max()) if batch.n_cams else 1,
+        total_pixels=batch.total_pixels)
+
+
+@dataclass
+class DeviceBatch:
+    """A batch's arrays as device tensors plus the C descriptor that points at them."""
+    shape: L.orrb_batch_shape
+    tensors: Dict[str, torch.Tensor]
+    desc: L.orrb_batch_desc = field(init=False)
+
+    def __post_init__(self):
+        self.desc = L.orrb_batch_desc(*[self.tensors[n].data_ptr() for n in _DESC_FIELDS])
+
+    @property
+    def total_pixels(self) -> int:
+        return int(self.shape.total_pixels)
+
+    def with_params(self, **kw) -> "DeviceBatch":
+        t = dict(self.tensors)
+        t.update(kw)
+        return DeviceBatch(self.shape, t)
+
+
+def host_arrays(batch) -> Dict[str, np.ndarray]:
+    """The batch's arrays in the C layout, contiguous, as numpy."""
+    return {n: np.ascontiguousarray(getattr(batch, n), dtype=_NP[_DTYPES[n]]) for n in _DESC_FIELDS}
+
+
+def _mesh_descs(meshes):
+    keep, descs = [], []
+    for m in meshes:
+        pos = np.ascontiguousarray(m.pos, np.float32)
+        nrm = np.ascontiguousarray(m.nrm, np.float32)
+        idx = np.ascontiguousarray(m.idx, np.uint32)
+        tm = np.ascontiguousarray(m.tri_mat, np.uint8)
+        keep += [pos, nrm, idx, tm]
+        descs.append(L.orrb_mesh_desc(pos.ctypes.data, nrm.ctypes.data, len(pos), idx.ctypes.data, tm.ctypes.data,
+                                      len(idx)))
+    return descs, keep
+
+
+def config(mode: int = L.ORRB_MODE_FUSED, tile_w: int = 0, tile_h: int = 0, threads: int = 0,
+           ctas_per_sm: int = 0) -> L.orrb_config:
+    return L.orrb_config(mode, tile_w, tile_h, threads, ctas_per_sm)
+
+
+class Renderer:
+    """Context + resident mesh arena on one GPU."""
+
+    def __init__(self, meshes, device: int = 0):
+        if not torch.cuda.is_available():
+            raise RuntimeError("Renderer needs a CUDA device; there is no CPU path")
+        self.device = torch.device("cuda", device)
+        self.ctx = L.orrb_create(device)
+        descs, keep = _mesh_descs(meshes)
+        n = L.orrb_mesh_arena_size(descs)
+        self.arena = torch.empty(n, dtype=torch.uint8, device=self.device)
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        L.orrb_upload_meshes(self.ctx, descs, self.arena.data_ptr(), n, stream)
+        del keep
+        self._ws: Optional[torch.Tensor] = None
+        self._bws: Optional[torch.Tensor] = None
+
+    def close(self):
+        if self.ctx is not None:
+            L.orrb_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- batches --------------------------------------------------------------
+    def upload(self, batch, pinned: bool = False, non_blocking: bool = False) -> DeviceBatch:
+        arrs = host_arrays(batch)
+        t = {}
+        for n, a in arrs.items():
+            h = torch.from_numpy(a)
+            if pinned:
+                h = h.pin_memory()
+            t[n] = h.to(self.device, non_blocking=non_blocking)
+        return DeviceBatch(batch_shape(batch), t)
+
+    def workspace(self, shape, cfg) -> torch.Tensor:
+        n = L.orrb_workspace_size(self.ctx, shape, cfg)
+        if self._ws is None or self._ws.numel() < n:
+            self._ws = torch.empty(n, dtype=torch.uint8, device=self.device)
+        return self._ws
+
+    def alloc_outputs(self, n_pixels: int, rgb_linear: bool = False, gbuffer: bool = False):
+        d = self.device
+        out = dict(rgb=torch.empty((n_pixels, 3), dtype=torch.uint8, device=d),
+                   depth=torch.empty(n_pixels, dtype=torch.float32, device=d),
+                   normal=torch.empty((n_pixels, 3), dtype=torch.int16, device=d),
+                   seg=torch.empty(n_pixels, dtype=torch.uint8, device=d))
+        if rgb_linear:
+            out["rgb_linear"] = torch.empty((n_pixels, 3), dtype=torch.float32, device=d)
+        if gbuffer:
+            out["gbuffer"] = torch.empty((L.ORRB_GBUFFER_PLANES, n_pixels), dtype=torch.float32, device=d)
+        return out
+
+    def render(self, db: DeviceBatch, out=None, cfg: Optional[L.orrb_config] = None, rgb_linear: bool = False,
+               gbuffer: bool = False, stream=None, workspace: Optional[torch.Tensor] = None):
+        cfg = cfg or config()
+        if out is None:
+            out = self.alloc_outputs(db.total_pixels, rgb_linear, gbuffer)
+        ws = workspace if workspace is not None else self.workspace(db.shape, cfg)
+        outs = L.orrb_outputs(*[out[k].data_ptr() if k in out else None
+                                for k in ("rgb", "depth", "normal", "seg", "rgb_linear", "gbuffer")])
+        st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        L.orrb_render_batch(self.ctx, db.shape, db.desc, outs, cfg, ws.data_ptr(), ws.numel(), st)
+        self._last_ws = ws
+        return out
+
+    def status(self, stream=None) -> int:
+        st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        return L.orrb_read_status(self.ctx, self._last_ws.data_ptr(), st)
+
+    def shade_backward(self, db: DeviceBatch, gbuffer: torch.Tensor, d_rgb: torch.Tensor, stream=None):
+        n = L.orrb_backward_workspace_size(self.ctx, db.shape)
+        if self._bws is None or self._bws.numel() < n:
+            self._bws = torch.empty(n, dtype=torch.uint8, device=self.device)
+        S = db.shape.n_samples
+        dm = torch.empty((S, L.ORRB_MAX_MATERIALS, 4), dtype=torch.float32, device=self.device)
+        dl = torch.empty((S, L.ORRB_MAX_LIGHTS, 4), dtype=torch.float32, device=self.device)
+        de = torch.empty(S, dtype=torch.float32, device=self.device)
+        grads = L.orrb_param_grads(dm.data_ptr(), dl.data_ptr(), de.data_ptr())
+        st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        d_rgb = d_rgb.contiguous()
+        L.orrb_shade_backward(self.ctx, db.shape, db.desc, gbuffer.data_ptr(), d_rgb.data_ptr(), grads,
+                              self._bws.data_ptr(), self._bws.numel(), st)
+        return dm, dl, de
+
+
+class ShadeFn(torch.autograd.Function):
+    """rgb_linear = shade(material, light, exposure_ev) at fixed visibility.
+
+    Forward renders the batch with the given parameter tensors (visibility does
+    not depend on them); backward runs the hand-written shading adjoint kernel
+    and returns d material [S,32,5] (albedo rgb and specular; shininess gets 0),
+    d light [S,4,4] and d exposure [S].
+    """
+
+    @staticmethod
+    def forward(ctx, material, light, exposure_ev, renderer: Renderer, db: DeviceBatch):
+        dbp = db.with_params(material=material.detach().contiguous(), light=light.detach().contiguous(),
+                             exposure_ev=exposure_ev.detach().contiguous())
+        out = renderer.render(dbp, rgb_linear=True, gbuffer=True)
+        ctx.renderer = renderer
+        ctx.db = dbp
+        ctx.save_for_backward(out["gbuffer"])
+        return out["rgb_linear"]
+
+    @staticmethod
+    def backward(ctx, g):
+        (gbuffer,) = ctx.saved_tensors
+        dm, dl, de = ctx.renderer.shade_backward(ctx.db, gbuffer, g.float())
+        dmat = torch.zeros_like(ctx.db.tensors["material"])
+        dmat[..., :4] = dm
+        return dmat, dl, de, None, None
+
+
+def to_numpy(out) -> Dict[str, np.ndarray]:
+    r = {k: v.cpu().numpy() for k, v in out.items()}
+    if "normal" in r:
+        r["normal"] = r["normal"].view(np.uint16)
+    return r

@@ -1,0 +1,151 @@
+"""GPU parity of the forward renderer against the CPU oracle, through the C-ABI.
+
+Workloads: the tiny cube scene, the hand-like scene (full 256-sample batch at
+200x200 x 3 cameras), the uneven batch (a stratified subset covering every
+resolution and both triangle-count extremes), plus ragged, orthographic,
+wide (> one tile column), empty and degenerate cases; and invariances that
+must hold bit for bit: fused vs plain launches, every tile shape and block
+size, a sample alone vs inside a batch.
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1906_11633_b300 import scenegen as sg
+from paper_1906_11633_b300 import lib as L
+from paper_1906_11633_b300.render import Renderer, config, to_numpy
+from tests import scenes
+from tests.parity import compare
+
+
+@pytest.fixture(scope="module")
+def oracle():
+    from oracle import oracle as orc
+    orc.build()
+    return orc
+
+
+@pytest.fixture(scope="module")
+def hand_renderer():
+    return Renderer(sg.hand_meshes())
+
+
+@pytest.fixture(scope="module")
+def tiny_renderer():
+    return Renderer(sg.tiny_meshes())
+
+
+def render_np(r, batch, cfg=None, **kw):
+    out = r.render(r.upload(batch), cfg=cfg, rgb_linear=True, **kw)
+    torch.cuda.synchronize()
+    assert r.status() == 0, f"device status {r.status():#x}"
+    return to_numpy(out)
+
+
+def test_tiny_matches_oracle(tiny_renderer, oracle):
+    b = sg.tiny_batch(0, n_samples=8)
+    st = compare(render_np(tiny_renderer, b), oracle.render(b, debug=True), "tiny")
+    assert st["depth_exact"] > 0.999
+
+
+@pytest.mark.parametrize("mode", [L.ORRB_MODE_FUSED, L.ORRB_MODE_PLAIN])
+def test_hand_full_batch_matches_oracle(hand_renderer, oracle, mode):
+    b = sg.hand_batch(0, np.arange(256))
+    st = compare(render_np(hand_renderer, b, config(mode=mode)), oracle.render(b, debug=True), "hand")
+    assert st["pixels"] == 256 * 3 * 200 * 200
+
+
+def test_uneven_stratified_subset_matches_oracle(hand_renderer, oracle):
+    full_layout = sg.uneven_layout(0, np.arange(1024))
+    n_links, res, cams = full_layout
+    pick = []
+    for r in sg.UNEVEN_RES:
+        idx = np.nonzero(res == r)[0]
+        order = idx[np.argsort(n_links[idx])]
+        pick += list(order[:8]) + list(order[-8:]) + list(order[len(order) // 2 - 8:len(order) // 2 + 8])
+    pick = np.unique(pick)
+    assert len(pick) >= 128
+    b = sg.uneven_batch(0, pick)
+    assert set(np.unique(b.cam_wh[:, 0])) == set(sg.UNEVEN_RES)
+    compare(render_np(hand_renderer, b), oracle.render(b, debug=True), "uneven")
+
+
+def test_ragged_wide_and_orthographic(oracle):
+    meshes = [sg.plane_mesh(3, 3), sg.box_mesh(0.5), sg.capsule_mesh(0.3, 0.8)]
+    r = Renderer(meshes)
+    poses = [scenes.identity_pose(), scenes.pose(t=(0.2, -0.1, 0.5)),
+             scenes.pose(R=sg._rot("z", np.array(0.7)), t=(-0.6, 0.3, 0.9))]
+    cams = [scenes.camera_look((2.0, -2.5, 1.8), (0, 0, 0.4), 67, 45, 50.0),      # ragged tiles
+            scenes.camera_look((1.0, -3.0, 1.0), (0, 0, 0.4), 600, 40, 30.0),     # two tile columns
+            scenes.camera_down((0.05, 0.02, 4.0), 53, 61, px_per_m=17.0),         # orthographic
+            scenes.camera_look((0.3, -0.2, 0.05), (0, 0, 0.6), 31, 29, 80.0)]     # near the plane: clipping
+    b = scenes.single_sample(meshes, [0, 1, 2], poses, cams, seg=[1, 2, 3], mat_base=[0, 1, 7],
+                             lights=[((0.5, -1.0, 2.0), 2.0), ((-1.0, 0.5, 1.5), 1.0)], albedo=(0.6, 0.4, 0.3),
+                             specular=0.5, shininess=20.0, ambient=(0.05, 0.05, 0.05), background=(0.2, 0.3, 0.4))
+    for th in (1, 8, 16):
+        compare(render_np(r, b, config(tile_h=th)), oracle.render(b, debug=True), f"ragged th={th}")
+
+
+def test_empty_scene_and_no_lights(tiny_renderer, oracle):
+    b = sg.tiny_batch(3, n_samples=3)
+    b = b.with_params(inst_offset=np.array([0, 2, 2, 4], np.int32),
+                      inst_mesh=b.inst_mesh[:4], inst_pose=b.inst_pose[:4], inst_seg=b.inst_seg[:4],
+                      inst_mat_base=b.inst_mat_base[:4], light_meta=np.array([[1, 1], [1, 1], [0, 1]], np.int32))
+    g = render_np(tiny_renderer, b)
+    o = oracle.render(b, debug=True)
+    compare(g, o, "empty")
+    n = 64 * 64
+    assert (g["seg"][n:2 * n] == 0).all() and (g["depth"][n:2 * n] == 0).all()
+
+
+@pytest.mark.parametrize("tile", [(512, 4), (64, 8), (128, 16), (32, 32), (200, 1)])
+@pytest.mark.parametrize("threads", [256, 512])
+def test_bit_identical_across_tilings_and_modes(hand_renderer, tile, threads):
+    b = sg.hand_batch(5, np.arange(6), res=200)
+    ref = render_np(hand_renderer, b, config())
+    got = render_np(hand_renderer, b, config(tile_w=tile[0], tile_h=tile[1], threads=threads))
+    plain = render_np(hand_renderer, b, config(mode=L.ORRB_MODE_PLAIN, tile_w=tile[0], tile_h=tile[1],
+                                               threads=threads))
+    for k in ref:
+        np.testing.assert_array_equal(got[k], ref[k], err_msg=k)
+        np.testing.assert_array_equal(plain[k], ref[k], err_msg=k)
+
+
+def test_sample_alone_equals_sample_in_batch(hand_renderer):
+    b = sg.hand_batch(8, np.arange(12), res=128)
+    full = render_np(hand_renderer, b)
+    n = 128 * 128 * 3
+    for s in (0, 7, 11):
+        alone = render_np(hand_renderer, sg.hand_batch(8, [s], res=128))
+        for k in full:
+            np.testing.assert_array_equal(alone[k], full[k][s * n:(s + 1) * n], err_msg=k)
+
+
+def test_device_checks_flag_bad_input(hand_renderer):
+    b = sg.hand_batch(1, np.arange(2), res=64)
+    ok = hand_renderer.upload(b)
+    bad_mesh = ok.tensors["inst_mesh"].clone()
+    bad_mesh[3] = 999                                   # no such mesh: the kernel skips the instance
+    hand_renderer.render(ok.with_params(inst_mesh=bad_mesh))
+    assert hand_renderer.status() & 0x2
+    bad_wh = ok.tensors["cam_wh"].clone()
+    bad_wh[1, 0] = 4000                                 # wider than the declared maximum
+    hand_renderer.render(ok.with_params(cam_wh=bad_wh))
+    assert hand_renderer.status() & 0x1
+    hand_renderer.render(ok)
+    assert hand_renderer.status() == 0
+
+
+def test_host_checks_reject_bad_arguments(hand_renderer):
+    b = sg.hand_batch(1, np.arange(1), res=64)
+    db = hand_renderer.upload(b)
+    with pytest.raises(L.OrrbError):
+        hand_renderer.render(db, cfg=config(tile_w=7))
+    with pytest.raises(L.OrrbError):
+        hand_renderer.render(db, cfg=config(threads=100))
+    with pytest.raises(L.OrrbError):
+        small = torch.empty(256, dtype=torch.uint8, device="cuda")
+        hand_renderer.render(db, workspace=small)
