@@ -190,6 +190,32 @@ orrb_status orrb_render_batch(orrb_ctx* ctx, const orrb_batch_shape* shape, cons
                               const orrb_outputs* out, const orrb_config* cfg, void* workspace,
                               size_t ws_bytes, void* stream);
 
+/* Render without any device allocation -- no counterpart in the paper.
+ *
+ * For callers that cannot hand the library a workspace: code running inside
+ * another runtime that owns the GPU's memory pool (a framework's custom op, a
+ * simulator's render callback) and may not call cudaMalloc, whether because
+ * the pool has already claimed the memory or because cudaMalloc can
+ * synchronise the device in the middle of that runtime's pipeline.  Same
+ * inputs, outputs and results as orrb_render_batch in ORRB_MODE_FUSED; the
+ * per-CTA scratch lives instead in one static device array of
+ * ORRB_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * the process exits.  Fewer CTAs run when a sample's scratch slot is large;
+ * a shape whose slot (about 224 bytes per triangle of the largest sample)
+ * does not fit even once is rejected with ORRB_ERR_WORKSPACE.  The entry
+ * point calls no cudaMalloc, cudaFree or allocating library routine.
+ *   device_status: optional device pointer to one uint32 that receives the
+ *     ORRB_DEV_* bits (cleared by this call); NULL discards them.
+ * The first call on a device looks up the static array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array: calls whose GPU work overlaps (different
+ * streams, threads or contexts on the same device) race and corrupt each
+ * other's results; serialise them on one stream. */
+#define ORRB_NOALLOC_SCRATCH_BYTES (64u << 20)
+orrb_status orrb_render_batch_noalloc(orrb_ctx* ctx, const orrb_batch_shape* shape, const orrb_batch_desc* batch,
+                                      const orrb_outputs* out, const orrb_config* cfg, uint32_t* device_status,
+                                      void* stream);
+
 /* Synchronise `stream` and read the workspace status word (ORRB_DEV_* bits). */
 orrb_status orrb_read_status(orrb_ctx* ctx, const void* workspace, void* stream, uint32_t* status);
 

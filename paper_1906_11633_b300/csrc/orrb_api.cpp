@@ -19,6 +19,7 @@
 
 namespace orrb {
 int render_max_ctas_per_sm(int threads, size_t smem);
+int noalloc_scratch(int device, void** ptr, size_t* bytes);
 }
 
 struct orrb_ctx {
@@ -433,6 +434,73 @@ orrb_status orrb_render_batch(orrb_ctx* ctx, const orrb_batch_shape* shape, cons
   char err[256] = {0};
   int n_ctas = c.mode == ORRB_MODE_FUSED ? std::min(P.n_slots, std::max(shape->n_cams, 1)) : 0;
   if (launch_render(p, c.mode, c.threads, n_ctas, std::max(shape->max_cams_per_sample, 1), stream, err, sizeof(err)))
+    return fail(ctx, ORRB_ERR_CUDA, "%s", err);
+  return ORRB_OK;
+}
+
+orrb_status orrb_render_batch_noalloc(orrb_ctx* ctx, const orrb_batch_shape* shape, const orrb_batch_desc* batch,
+                                      const orrb_outputs* out, const orrb_config* cfg, uint32_t* device_status,
+                                      void* stream) {
+  if (!ctx) return ORRB_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> g(ctx->mu);
+  if (!ctx->has_meshes) return fail(ctx, ORRB_ERR_NOT_FOUND, "upload meshes before rendering");
+  orrb_config c;
+  resolve_config(cfg, &c);
+  orrb_status st = check_config(ctx, c);
+  if (st == ORRB_OK) st = check_shape(ctx, shape);
+  if (st == ORRB_OK) st = check_desc(ctx, batch);
+  if (st != ORRB_OK) return st;
+  if (c.mode != ORRB_MODE_FUSED) return fail(ctx, ORRB_ERR_INVALID_ARG, "the allocation-free entry point runs the fused mode only");
+  if (!out) return fail(ctx, ORRB_ERR_INVALID_ARG, "null outputs");
+  DeviceGuard dg(ctx->device);
+  if (!dg.ok) return fail(ctx, ORRB_ERR_CUDA, "cudaSetDevice(%d) failed", ctx->device);
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  int rc = noalloc_scratch(ctx->device, &scratch, &scratch_bytes);
+  if (rc) return fail(ctx, ORRB_ERR_CUDA, "static scratch lookup: %s", cudaGetErrorString((cudaError_t)rc));
+  Plan P;
+  st = plan(ctx, *shape, c, &P);
+  if (st != ORRB_OK) return st;
+  const size_t fit = (scratch_bytes - 256) / P.slot_bytes;
+  if (fit < 1)
+    return fail(ctx, ORRB_ERR_WORKSPACE,
+                "samples of up to %d triangles need %zu B of scratch per CTA; the static scratch holds %zu B",
+                shape->max_tris_per_sample, P.slot_bytes, scratch_bytes - 256);
+  const int n_slots = (int)std::min<size_t>((size_t)P.n_slots, fit);
+  Params p{};
+  fill_batch(p, *shape, *batch);
+  p.rgb = out->rgb;
+  p.depth = out->depth;
+  p.normal = out->normal;
+  p.seg = out->seg;
+  p.rgb_linear = out->rgb_linear;
+  p.gbuffer = out->gbuffer;
+  const ArenaLayout& A = ctx->arena;
+  p.meshes = reinterpret_cast<const MeshEntry*>(ctx->arena_ptr + A.meshes);
+  p.meshlets = reinterpret_cast<const MeshletEntry*>(ctx->arena_ptr + A.meshlets);
+  p.vpos = reinterpret_cast<const float4*>(ctx->arena_ptr + A.vpos);
+  p.vnrm = reinterpret_cast<const float4*>(ctx->arena_ptr + A.vnrm);
+  p.tris = reinterpret_cast<const uint32_t*>(ctx->arena_ptr + A.tris);
+  p.n_meshes = A.n_meshes;
+  p.tile_w = c.tile_w;
+  p.tile_h = c.tile_h;
+  p.max_tiles = P.max_tiles;
+  char* ws = static_cast<char*>(scratch);
+  p.status = device_status ? device_status : reinterpret_cast<uint32_t*>(ws);
+  p.work_counter = reinterpret_cast<uint32_t*>(ws + 4);
+  p.scratch = ws + 256;
+  p.slot_bytes = P.slot_bytes;
+  p.n_slots = n_slots;
+  p.plain_sample = -1;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the array keeps the previous call's contents: the status word and the work counter restart at zero
+  cudaError_t e = cudaMemsetAsync(ws, 0, 8, s);
+  if (e == cudaSuccess && device_status) e = cudaMemsetAsync(device_status, 0, 4, s);
+  if (e != cudaSuccess) return fail(ctx, ORRB_ERR_CUDA, "scratch clear: %s", cudaGetErrorString(e));
+  if (shape->n_cams == 0 || shape->n_samples == 0) return ORRB_OK;
+  char err[256] = {0};
+  if (launch_render(p, ORRB_MODE_FUSED, c.threads, std::min(n_slots, std::max(shape->n_cams, 1)), 1, stream, err,
+                    sizeof(err)))
     return fail(ctx, ORRB_ERR_CUDA, "%s", err);
   return ORRB_OK;
 }

@@ -34,6 +34,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <mutex>
 
 #include "orrb.h"
 #include "orrb_internal.h"
@@ -1003,7 +1004,32 @@ __global__ void __launch_bounds__(512, 2) plain_raster_kernel(Params p) {
   raster_tile(p, sh, sc, blockIdx.y, sp.uni, L);
 }
 
+// Scratch of orrb_render_batch_noalloc: a file-scope device array, so that
+// entry point never allocates.  Host code must not pass the symbol itself to
+// a kernel (on the host it names a stand-in, not device memory); it passes
+// the device address looked up below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[ORRB_NOALLOC_SCRATCH_BYTES];
+
 }  // namespace
+
+// Device address of the static scratch on `device`, looked up once per device
+// with that device current (the caller makes it current).  Returns a CUDA
+// error code, 0 on success.
+int noalloc_scratch(int device, void** ptr, size_t* bytes) {
+  static std::mutex mu;
+  static void* cache[256] = {};
+  if (device < 0 || device >= 256) return (int)cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> g(mu);
+  if (!cache[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return (int)e;
+    cache[device] = p;
+  }
+  *ptr = cache[device];
+  *bytes = ORRB_NOALLOC_SCRATCH_BYTES;
+  return 0;
+}
 
 size_t render_smem_bytes(int threads, int tile_w, int tile_h, int inst_max, int max_tiles) {
   return smem_layout(threads, tile_w, tile_h, inst_max, max_tiles).total;

@@ -24,7 +24,7 @@ DEV_BITS = {0x1: "bad camera", 0x2: "bad instance", 0x4: "too many triangles", 0
 
 EXPORTS = ["orrb_create", "orrb_destroy", "orrb_status_string", "orrb_last_error", "orrb_mesh_arena_size",
            "orrb_upload_meshes", "orrb_release_meshes", "orrb_workspace_size", "orrb_render_batch",
-           "orrb_read_status", "orrb_backward_workspace_size", "orrb_shade_backward"]
+           "orrb_read_status", "orrb_backward_workspace_size", "orrb_shade_backward", "orrb_render_batch_noalloc"]
 
 
 class orrb_mesh_desc(C.Structure):
@@ -90,6 +90,8 @@ def load():
             "orrb_render_batch": ([C.c_void_p, P(orrb_batch_shape), P(orrb_batch_desc), P(orrb_outputs),
                                    P(orrb_config), C.c_void_p, C.c_size_t, C.c_void_p], C.c_int32),
             "orrb_read_status": ([C.c_void_p, C.c_void_p, C.c_void_p, P(C.c_uint32)], C.c_int32),
+            "orrb_render_batch_noalloc": ([C.c_void_p, P(orrb_batch_shape), P(orrb_batch_desc), P(orrb_outputs),
+                                           P(orrb_config), C.c_void_p, C.c_void_p], C.c_int32),
             "orrb_backward_workspace_size": ([C.c_void_p, P(orrb_batch_shape), P(C.c_size_t)], C.c_int32),
             "orrb_shade_backward": ([C.c_void_p, P(orrb_batch_shape), P(orrb_batch_desc), C.c_void_p, C.c_void_p,
                                      P(orrb_param_grads), C.c_void_p, C.c_size_t, C.c_void_p], C.c_int32),
@@ -155,6 +157,12 @@ def orrb_workspace_size(ctx, shape: orrb_batch_shape, cfg: orrb_config) -> int:
 def orrb_render_batch(ctx, shape, desc, outs, cfg, ws_ptr: int, ws_bytes: int, stream: int) -> None:
     check(load().orrb_render_batch(ctx, C.byref(shape), C.byref(desc), C.byref(outs), C.byref(cfg),
                                    C.c_void_p(ws_ptr), ws_bytes, C.c_void_p(stream)), ctx)
+
+
+def orrb_render_batch_noalloc(ctx, shape, desc, outs, cfg, status_ptr, stream: int) -> None:
+    """Render with the library's static scratch instead of a workspace (no device allocation)."""
+    check(load().orrb_render_batch_noalloc(ctx, C.byref(shape), C.byref(desc), C.byref(outs), C.byref(cfg),
+                                           C.c_void_p(status_ptr), C.c_void_p(stream)), ctx)
 
 
 def orrb_read_status(ctx, ws_ptr: int, stream: int) -> int:
