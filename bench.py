@@ -46,6 +46,29 @@ CONFIG = {"workload": "hand-like scene: 256 samples x 3 cameras x 200x200, 24 ca
           "resolution": RES, "tris_per_sample": 24 * 320 + 14, "l2": "flushed between timed steps (256 MB write)"}
 
 
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("orrb_render.cu", "orrb_internal.h"):
+        with open(os.path.join(ROOT, "paper_1906_11633_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this kernel source."""
+    try:
+        text = open(os.path.join(ROOT, "profiles", "render_fused_hand256.md")).read()
+    except OSError:
+        return None
+    if kernel_source_hash() not in text:
+        return None
+    for line in text.splitlines():
+        if line.startswith("traffic_bytes_per_launch:"):
+            return float(line.split(":")[1])
+    return None
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -60,9 +83,10 @@ def fp32_peak_tflops(sms: int, mhz: float) -> float:
 
 
 def shading_flops(n_visible: int, n_lit: int, n_light_terms: int) -> float:
-    """Algorithmic FP32 operations of the shading step over visible pixels (count documented in the design doc):
-    72 per visible pixel + 31 per (pixel, light) + 20 per (pixel, light) with n.L > 0 (specular lobe)."""
-    return float(72 * n_visible + 31 * n_light_terms + 20 * n_lit)
+    """Algorithmic FP32 operations of the shading step over visible pixels, counted from the defined
+    arithmetic (each +, -, x, /, sqrt, max, floor, conversion, exp2, log2 = 1; enumeration in DESIGN.md):
+    76 per visible pixel + 31 per (pixel, light) + 20 per (pixel, light) with n.L > 0 (specular lobe)."""
+    return float(76 * n_visible + 31 * n_light_terms + 20 * n_lit)
 
 
 class ClockSampler:
@@ -301,7 +325,7 @@ def run_ours(args, world, rank, local):
             "peak": hbm if bound == "hbm" else fp32_peak,
             "unit": "GB/s" if bound == "hbm" else "TFLOP/s",
             "frac": (achieved_gbs / hbm) if bound == "hbm" else (achieved_tf / fp32_peak),
-            "traffic": args.traffic,
+            "traffic": args.traffic if args.traffic is not None else profiled_traffic(),
             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if bound == "hbm" else
                            "nominal: SMs x 128 x 2 x max SM clock",
             "alg_bytes_per_launch": alg_bytes, "alg_fp32_flop_per_launch": flops,
@@ -312,7 +336,8 @@ def run_ours(args, world, rank, local):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded procedural hand scene)",
             "config": dict(CONFIG, parallelism=f"replicas x{world}" if world > 1 else "single GPU",
-                           tile=[args.tile_w or 512, args.tile_h or 8], threads=args.threads or 512),
+                           tile=[min(args.tile_w or L.DEFAULT_TILE_W, RES), args.tile_h or L.DEFAULT_TILE_H],
+                           threads=args.threads or L.DEFAULT_THREADS),
             "plain": {"value": plain_value, "ms_per_step": plain_ms, "steps": psteps,
                       "launches_per_step": 3 * N_SAMPLES},
             "fused_over_plain": value / plain_value,

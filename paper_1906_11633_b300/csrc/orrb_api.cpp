@@ -162,8 +162,8 @@ orrb_status check_meshes(orrb_ctx* ctx, const orrb_mesh_desc* meshes, int32_t n)
 void resolve_config(const orrb_config* in, orrb_config* out) {
   orrb_config c{};
   if (in) c = *in;
-  if (c.tile_w == 0) c.tile_w = 512;
-  if (c.tile_h == 0) c.tile_h = 8;
+  if (c.tile_w == 0) c.tile_w = 256;
+  if (c.tile_h == 0) c.tile_h = 1;
   if (c.threads == 0) c.threads = 512;
   *out = c;
 }
@@ -209,7 +209,7 @@ orrb_status plan(orrb_ctx* ctx, const orrb_batch_shape& s, const orrb_config& c,
   P->max_tiles = max_tiles_of(s, c);
   SlotLayout L = slot_layout(s.max_tris_per_sample, P->max_tiles);
   P->slot_bytes = L.total;
-  P->smem = render_smem_bytes(c.threads, c.tile_w, c.tile_h, s.max_inst_per_sample, P->max_tiles);
+  P->smem = render_smem_bytes(c.threads, c.tile_w, c.tile_h, s.max_inst_per_sample, P->max_tiles, s.max_width);
   if (P->smem > 227 * 1024) return fail(ctx, ORRB_ERR_INVALID_ARG, "tile / instance limits need %zu B of shared memory", P->smem);
   if (c.mode == ORRB_MODE_FUSED) {
     int fit = render_max_ctas_per_sm(c.threads, P->smem);

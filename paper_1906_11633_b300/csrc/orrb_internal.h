@@ -17,8 +17,7 @@ constexpr int kMaxLights = 4;
 constexpr int kMaxMaterials = 32;
 constexpr int kMeshletVerts = 64;
 constexpr int kMeshletTris = 128;
-constexpr int kMaxSpanTiles = 4;       // a binned triangle overlaps at most this many tiles
-constexpr int kSmallBoxFix = 64 * 256; // binned triangles have a vertex box below 64 px (fixed point)
+constexpr int kMaxSpanTiles = 64;      // a binned triangle overlaps at most this many tiles
 constexpr float kGuardPx = 1048576.0f; // 2^20 px
 
 // ---- mesh arena ----------------------------------------------------------
@@ -129,7 +128,7 @@ ORRB_HD inline SlotLayout slot_layout(int t_max, int max_tiles) {
 // Host entry points implemented in the .cu files.
 int launch_render(const Params& p, int mode, int threads, int ctas_per_sm, int max_cams_per_sample,
                   void* stream, char* err, size_t errlen);
-size_t render_smem_bytes(int threads, int tile_w, int tile_h, int inst_max, int max_tiles);
+size_t render_smem_bytes(int threads, int tile_w, int tile_h, int inst_max, int max_tiles, int w_max);
 
 struct BackwardParams {
   Params base;           // batch + mesh-independent fields

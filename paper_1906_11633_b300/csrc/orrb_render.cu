@@ -12,17 +12,21 @@
 //      culls them, writes one 80-byte record per visible (sub)triangle at a
 //      slot fixed by its primitive id, and appends (key, pixel box) to the
 //      image's visible list with a warp prefix scan and one atomic per warp.
-//   B  binning: triangles whose vertex box is under 64 px and that touch at
-//      most 4 screen tiles are counted per tile, the counts are prefix-summed
-//      and the keys scattered into per-tile bins; the rest go to a "large"
-//      list that every tile tests itself (the table plane, block faces).
-//   R  raster + shade, per tile: large triangles pixel-parallel, binned ones
-//      triangle-parallel, each covered pixel centre folding
-//      (depth bits << 32 | key) into a shared-memory 64-bit atomicMin; then
-//      every pixel resolves its winner, interpolates the normal, shades
-//      (Blinn-Phong, point/directional lights, exposure) and writes the four
-//      channels; RGB and normals are staged in shared memory and written
-//      with 16-byte vector stores.
+//   B  binning: triangles that touch at most 64 screen tiles are counted per
+//      tile, the counts are prefix-summed and the keys scattered into
+//      per-tile bins; the rest go to a "large" list that every tile tests
+//      itself (in practice the table plane).
+//   R  raster + shade: each warp owns one tile at a time (default: one image
+//      row), pulling tiles from a per-CTA counter, with its depth keys and
+//      output staging in warp-private shared memory, so the phase needs no
+//      CTA-wide barrier.  Large triangles: lanes split the triangle's box.
+//      Binned triangles: 32 at a time, their boxes prefix-summed and the
+//      (triangle, pixel) candidates spread evenly over the lanes, each
+//      covered centre folding (depth bits << 32 | key) into the tile's keys
+//      with a shared-memory 64-bit atomicMin.  Then every pixel resolves its
+//      winner, interpolates the normal, shades (Blinn-Phong, point or
+//      directional lights, exposure) and writes the four channels; RGB and
+//      normals are staged per row and written with 16-byte vector stores.
 //
 // Everything that decides coverage, visibility or depth (transform, clip,
 // projection, snapping, edge functions, depth) uses explicitly rounded fp32
@@ -44,7 +48,7 @@ namespace {
 
 constexpr unsigned long long kEmpty = ~0ull;
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kBigChunk = 128;
+constexpr int kPlainRasterSplit = 8;  // plain mode: CTAs sharing one image's tiles
 
 struct ImageInfo {
   int cam, s, W, H, inst0, n_inst, ortho, T, valid;
@@ -61,7 +65,7 @@ struct ImageInfo {
 struct CtaShared {
   ImageInfo im;
   float mat[kMaxMaterials][5];
-  int n_vis, n_big, n_big_tile, img;
+  int n_vis, n_big, next_tile, img;
   int scan_tmp[33];
 };
 
@@ -73,14 +77,6 @@ struct WarpG {  // per-warp cluster staging for phase G
   int Y[kMeshletVerts];
   float iw[kMeshletVerts];
   int flag[kMeshletVerts];  // bit 0: in front of the near plane; bit 1: inside the guard band
-};
-
-struct BigEntry {  // a large triangle prepared for one tile
-  int X[3], Y[3];
-  float iw[3];
-  float fA;
-  unsigned key;
-  int tl;  // top-left flags of edges 0, 1, 2 in bits 0, 1, 2
 };
 
 struct WarpTri {  // a binned triangle staged for the warp's fragment expansion (64 B)
@@ -103,25 +99,30 @@ struct Scratch {
 };
 
 struct SmemLayout {
-  size_t inst_tab, uni, g_size, b_size, r_keys, r_big, r_wtri, r_woff, r_rgb, r_nrm, r_size, total;
+  size_t uni, g_size, b_size;
+  // phase R, per warp: keys, staged triangles, their offsets, RGB and normal row staging
+  size_t w_keys, w_tri, w_off, w_rgb, w_nrm, w_bytes, rgb_row, nrm_row, r_size;
+  size_t total;
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
 
-__host__ __device__ inline SmemLayout smem_layout(int threads, int tile_w, int tile_h, int inst_max, int max_tiles) {
+__host__ __device__ inline SmemLayout smem_layout(int threads, int tile_w, int tile_h, int inst_max, int max_tiles,
+                                                  int w_max) {
   SmemLayout L;
-  size_t tile_px = size_t(tile_w) * tile_h;
-  L.inst_tab = 0;
+  const size_t tw = size_t(tile_w < w_max ? tile_w : w_max), th = size_t(tile_h);
   L.uni = al16(size_t(2) * (inst_max + 2) * sizeof(int));
   L.g_size = size_t(threads / 32) * al16(sizeof(WarpG));
   L.b_size = al16(size_t(2) * (max_tiles + 2) * sizeof(int));
-  L.r_keys = 0;
-  L.r_big = al16(tile_px * 8);
-  L.r_wtri = L.r_big + al16(size_t(kBigChunk) * sizeof(BigEntry));
-  L.r_woff = L.r_wtri + al16(size_t(threads) * sizeof(WarpTri));
-  L.r_rgb = L.r_woff + al16(size_t(threads) * sizeof(int));
-  L.r_nrm = L.r_rgb + al16(tile_px * 3 + 16);
-  L.r_size = L.r_nrm + al16(tile_px * 6 + 16);
+  L.rgb_row = al16(3 * tw + 16);
+  L.nrm_row = al16(6 * tw + 16);
+  L.w_keys = 0;
+  L.w_tri = al16(tw * th * 8);
+  L.w_off = L.w_tri + al16(32 * sizeof(WarpTri));
+  L.w_rgb = L.w_off + al16(32 * sizeof(int));
+  L.w_nrm = L.w_rgb + th * L.rgb_row;
+  L.w_bytes = L.w_nrm + th * L.nrm_row;
+  L.r_size = size_t(threads / 32) * L.w_bytes;
   size_t u = L.g_size > L.b_size ? L.g_size : L.b_size;
   u = u > L.r_size ? u : L.r_size;
   L.total = L.uni + u;
@@ -249,6 +250,7 @@ __device__ void setup_image(const Params& p, int cam, CtaShared& sh, int* mprefi
     }
     sh.n_vis = 0;
     sh.n_big = 0;
+    sh.next_tile = 0;
   }
   __syncthreads();
   for (int k = tid; k < kMaxMaterials * 5; k += blockDim.x)
@@ -314,8 +316,7 @@ __device__ __forceinline__ bool setup_box(const ImageInfo& im, const int X[3], c
   int x0 = max(0, -((128 - xmin) >> 8)), x1 = min(im.W - 1, (xmax - 128) >> 8);
   int y0 = max(0, -((128 - ymin) >> 8)), y1 = min(im.H - 1, (ymax - 128) >> 8);
   if (x0 > x1 || y0 > y1) return false;
-  unsigned small = (xmax - xmin) < kSmallBoxFix && (ymax - ymin) < kSmallBoxFix;
-  box.x = unsigned(x0) | (unsigned(x1) << 16) | (small << 31);
+  box.x = unsigned(x0) | (unsigned(x1) << 16);
   box.y = unsigned(y0) | (unsigned(y1) << 16);
   return true;
 }
@@ -511,12 +512,12 @@ __device__ void geometry_phase(const Params& p, CtaShared& sh, const int* mprefi
 // phase B: screen-tile binning
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool binned_span(uint2 box, int tw, int th, int& tx0, int& tx1, int& ty0, int& ty1) {
-  int x0 = box.x & 0xffff, x1 = (box.x >> 16) & 0x7fff, y0 = box.y & 0xffff, y1 = box.y >> 16;
+  int x0 = box.x & 0xffff, x1 = box.x >> 16, y0 = box.y & 0xffff, y1 = box.y >> 16;
   tx0 = x0 / tw;
   tx1 = x1 / tw;
   ty0 = y0 / th;
   ty1 = y1 / th;
-  return (box.x >> 31) && (tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= kMaxSpanTiles;
+  return (tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= kMaxSpanTiles;
 }
 
 __device__ void bin_phase(const Params& p, CtaShared& sh, int* counts, int* cursor, const Scratch& sc) {
@@ -649,7 +650,10 @@ __device__ void shade(const CtaShared& sh, const float P[3], const float n[3], i
       if (h2 > 0.0f) {
         float rh = rsqrtf(h2);
         float ndh = fmaxf(0.0f, (n[0] * H0 + n[1] * H1 + n[2] * H2) * rh);
-        spec = m[3] * powf(ndh, m[4]);
+        // ndh^alpha for ndh in [0, 1], alpha >= 1: both library calls are accurate to a
+        // couple of ulp, so the relative error is ~1e-7 * |alpha log2 ndh| (< 2e-6 wherever
+        // the term is not negligible), without powf's handling of negative bases
+        spec = ndh > 0.0f ? m[3] * exp2f(m[4] * log2f(ndh)) : 0.0f;
       }
     }
     c0 += E * (m[0] * ndl + spec);
@@ -681,225 +685,232 @@ __device__ void copy_out(char* dst, const char* src, int nbytes, int tid, int nt
   }
 }
 
-__device__ void raster_tile(const Params& p, CtaShared& sh, const Scratch& sc, int tile, char* rbase,
-                            const SmemLayout& L) {
+// Walks the pixels of a box (px0, py0, width bw) with index j = lane, lane+32, ...
+struct BoxWalk {
+  int px, py;
+  __device__ __forceinline__ BoxWalk(int j, int px0, int py0, int bw) {
+    const int dy = j < bw ? 0 : j / bw;
+    px = px0 + (j - dy * bw);
+    py = py0 + dy;
+  }
+  __device__ __forceinline__ void advance(int px0, int bw) {
+    px += 32;
+    while (px >= px0 + bw) {
+      px -= bw;
+      py++;
+    }
+  }
+};
+
+// Phase R for one tile, by one warp, in warp-private shared memory.
+__device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scratch& sc, int tile, char* wbase,
+                                 const SmemLayout& L) {
   const ImageInfo& im = sh.im;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = threadIdx.x & 31;
   const int tx = tile % im.ntx, ty = tile / im.ntx;
   const int x0 = tx * im.tw, y0 = ty * im.th;
   const int cw = min(im.tw, im.W - x0), ch = min(im.th, im.H - y0);
   const int npx = cw * ch;
-  unsigned long long* keys = reinterpret_cast<unsigned long long*>(rbase + L.r_keys);
-  BigEntry* bigs = reinterpret_cast<BigEntry*>(rbase + L.r_big);
-  const bool full_rows = cw == im.W;
-  const long long o0 = im.px_off + (long long)y0 * im.W + x0;
-  // staging buffers start at the destination's alignment modulo 16
-  char* st_rgb = rbase + L.r_rgb + (full_rows && p.rgb ? int((reinterpret_cast<uintptr_t>(p.rgb + 3 * o0)) & 15) : 0);
-  char* st_nrm =
-      rbase + L.r_nrm + (full_rows && p.normal ? int((reinterpret_cast<uintptr_t>(p.normal + 3 * o0)) & 15) : 0);
+  unsigned long long* keys = reinterpret_cast<unsigned long long*>(wbase + L.w_keys);
+  for (int i = lane; i < npx; i += 32) keys[i] = kEmpty;
+  __syncwarp();
 
-  // large triangles first, pixel-parallel, in chunks staged in shared memory
-  for (int i = tid; i < npx; i += nt) keys[i] = kEmpty;
-  __syncthreads();
+  // large triangles: the lanes split the triangle's box within the tile, one pixel each
   const int nbig = sh.n_big;
-  for (int c0 = 0; c0 < nbig; c0 += kBigChunk) {
-    if (tid == 0) sh.n_big_tile = 0;
-    __syncthreads();
-    const int lane = tid & 31;
-    for (int k0 = c0; k0 < min(nbig, c0 + kBigChunk); k0 += nt) {
-      const int k = k0 + tid;
-      bool keep = false;
-      BigEntry be;
-      if (k < min(nbig, c0 + kBigChunk)) {
-        be.key = sc.big[k];
-        load_tri(rec_of(p, sc, be.key), be.X, be.Y, be.iw);
-        int xmin = min(be.X[0], min(be.X[1], be.X[2])), xmax = max(be.X[0], max(be.X[1], be.X[2]));
-        int ymin = min(be.Y[0], min(be.Y[1], be.Y[2])), ymax = max(be.Y[0], max(be.Y[1], be.Y[2]));
-        int bx0 = -((128 - xmin) >> 8), bx1 = (xmax - 128) >> 8;
-        int by0 = -((128 - ymin) >> 8), by1 = (ymax - 128) >> 8;
-        keep = bx0 < x0 + cw && bx1 >= x0 && by0 < y0 + ch && by1 >= y0;
-        if (keep) tri_setup(be.X, be.Y, be.fA, be.tl);
+  for (int b = 0; b < nbig; b++) {
+    const unsigned key = sc.big[b];
+    int X[3], Y[3];
+    float iw[3];
+    load_tri(rec_of(p, sc, key), X, Y, iw);
+    const int xmin = min(X[0], min(X[1], X[2])), xmax = max(X[0], max(X[1], X[2]));
+    const int ymin = min(Y[0], min(Y[1], Y[2])), ymax = max(Y[0], max(Y[1], Y[2]));
+    const int bx0 = max(x0, -((128 - xmin) >> 8)), bx1 = min(x0 + cw - 1, (xmax - 128) >> 8);
+    const int by0 = max(y0, -((128 - ymin) >> 8)), by1 = min(y0 + ch - 1, (ymax - 128) >> 8);
+    if (bx0 > bx1 || by0 > by1) continue;
+    float fA;
+    int tl;
+    tri_setup(X, Y, fA, tl);
+    const int bw = bx1 - bx0 + 1, n = bw * (by1 - by0 + 1);
+    if (lane < n) {
+      BoxWalk w(lane, bx0, by0, bw);
+      for (int j = lane; j < n; j += 32) {
+        const unsigned long long f = fragment(X, Y, iw, fA, tl, key, im.ortho, 256 * w.px + 128, 256 * w.py + 128);
+        unsigned long long& k = keys[(w.py - y0) * cw + (w.px - x0)];
+        if (f < k) k = f;
+        w.advance(bx0, bw);
       }
-      const unsigned m = __ballot_sync(kFull, keep);
-      int wbase = 0;
-      if (lane == 0 && m) wbase = atomicAdd(&sh.n_big_tile, __popc(m));
-      wbase = __shfl_sync(kFull, wbase, 0);
-      if (keep) bigs[wbase + __popc(m & ((1u << lane) - 1u))] = be;
     }
-    __syncthreads();
-    const int nb = sh.n_big_tile;
-    for (int i = tid; i < npx; i += nt) {
-      const int px = x0 + i % cw, py = y0 + i / cw;
-      const int cx = 256 * px + 128, cy = 256 * py + 128;
-      unsigned long long best = keys[i];
-      for (int b = 0; b < nb; b++) {
-        const BigEntry& be = bigs[b];
-        unsigned long long k = fragment(be.X, be.Y, be.iw, be.fA, be.tl, be.key, im.ortho, cx, cy);
-        best = k < best ? k : best;
-      }
-      keys[i] = best;
-    }
-    __syncthreads();
+    __syncwarp();
   }
-  // binned triangles: each warp takes 32 at a time, prefix-sums their clamped pixel boxes
-  // and spreads the (triangle, pixel) candidates evenly over its lanes; every covered
-  // centre folds into the tile's keys with a shared-memory 64-bit atomicMin
-  {
-    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    WarpTri* wt = reinterpret_cast<WarpTri*>(rbase + L.r_wtri) + warp * 32;
-    int* woff = reinterpret_cast<int*>(rbase + L.r_woff) + warp * 32;
-    const int b0 = sc.tile_off[tile], b1 = sc.tile_off[tile + 1];
-    for (int c = b0 + warp * 32; c < b1; c += nw * 32) {
-      const int k = c + lane;
-      int cnt = 0;
-      if (k < b1) {
-        WarpTri T;
-        T.key = sc.bins[k];
-        load_tri(rec_of(p, sc, T.key), T.X, T.Y, T.iw);
-        tri_setup(T.X, T.Y, T.fA, T.tl);
-        int xmin = min(T.X[0], min(T.X[1], T.X[2])), xmax = max(T.X[0], max(T.X[1], T.X[2]));
-        int ymin = min(T.Y[0], min(T.Y[1], T.Y[2])), ymax = max(T.Y[0], max(T.Y[1], T.Y[2]));
-        T.px0 = max(x0, -((128 - xmin) >> 8));
-        T.py0 = max(y0, -((128 - ymin) >> 8));
-        const int bw = min(x0 + cw - 1, (xmax - 128) >> 8) - T.px0 + 1;
-        const int bh = min(y0 + ch - 1, (ymax - 128) >> 8) - T.py0 + 1;
-        T.bw = bw;
-        cnt = (bw > 0 && bh > 0) ? bw * bh : 0;
-        wt[lane] = T;
-      }
-      int incl = cnt;
-      for (int o = 1; o < 32; o <<= 1) {
-        int v = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += v;
-      }
-      woff[lane] = incl - cnt;
-      const int total = __shfl_sync(kFull, incl, 31);
-      __syncwarp();
-      for (int m = lane; m < total; m += 32) {
-        int lo = 0, hi = 31;  // largest t with woff[t] <= m (always a triangle with cnt > 0)
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (woff[mid] <= m) lo = mid;
-          else hi = mid - 1;
-        }
-        const WarpTri& T = wt[lo];
-        const int jj = m - woff[lo];
-        const int dy = jj / T.bw;
-        const int px = T.px0 + (jj - dy * T.bw), py = T.py0 + dy;
-        const unsigned long long f =
-            fragment(T.X, T.Y, T.iw, T.fA, T.tl, T.key, im.ortho, 256 * px + 128, 256 * py + 128);
-        if (f != kEmpty) atomicMin(&keys[(py - y0) * cw + (px - x0)], f);
-      }
-      __syncwarp();
-    }
-  }
-  __syncthreads();
 
-  // resolve + shade + write
+  // binned triangles: 32 at a time, their clamped boxes prefix-summed and the
+  // (triangle, pixel) candidates spread evenly over the lanes
+  WarpTri* wt = reinterpret_cast<WarpTri*>(wbase + L.w_tri);
+  int* woff = reinterpret_cast<int*>(wbase + L.w_off);
+  const int b0 = sc.tile_off[tile], b1 = sc.tile_off[tile + 1];
+  for (int c = b0; c < b1; c += 32) {
+    const int k = c + lane;
+    int cnt = 0;
+    if (k < b1) {
+      WarpTri T;
+      T.key = sc.bins[k];
+      load_tri(rec_of(p, sc, T.key), T.X, T.Y, T.iw);
+      tri_setup(T.X, T.Y, T.fA, T.tl);
+      const int xmin = min(T.X[0], min(T.X[1], T.X[2])), xmax = max(T.X[0], max(T.X[1], T.X[2]));
+      const int ymin = min(T.Y[0], min(T.Y[1], T.Y[2])), ymax = max(T.Y[0], max(T.Y[1], T.Y[2]));
+      T.px0 = max(x0, -((128 - xmin) >> 8));
+      T.py0 = max(y0, -((128 - ymin) >> 8));
+      const int bw = min(x0 + cw - 1, (xmax - 128) >> 8) - T.px0 + 1;
+      const int bh = min(y0 + ch - 1, (ymax - 128) >> 8) - T.py0 + 1;
+      T.bw = bw;
+      cnt = (bw > 0 && bh > 0) ? bw * bh : 0;
+      wt[lane] = T;
+    }
+    int incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += v;
+    }
+    woff[lane] = incl - cnt;
+    const int total = __shfl_sync(kFull, incl, 31);
+    __syncwarp();
+    for (int m = lane; m < total; m += 32) {
+      int lo = 0, hi = 31;  // largest t with woff[t] <= m: always a triangle with candidates
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (woff[mid] <= m) lo = mid;
+        else hi = mid - 1;
+      }
+      const WarpTri& T = wt[lo];
+      const BoxWalk w(m - woff[lo], T.px0, T.py0, T.bw);
+      const unsigned long long f =
+          fragment(T.X, T.Y, T.iw, T.fA, T.tl, T.key, im.ortho, 256 * w.px + 128, 256 * w.py + 128);
+      if (f != kEmpty) atomicMin(&keys[(w.py - y0) * cw + (w.px - x0)], f);
+    }
+    __syncwarp();
+  }
+
+  // resolve + shade; depth / seg / optional planes go straight out, RGB and normals are
+  // staged per tile row at the destination's 16-byte phase and copied with vector stores
   const long long N = p.total_pixels;
-  for (int i = tid; i < npx; i += nt) {
-    const int lx = i % cw, ly = i / cw;
-    const int px = x0 + lx, py = y0 + ly;
-    const long long o = im.px_off + (long long)py * im.W + px;
-    const unsigned long long k = keys[i];
-    float rgb[3], depth = 0.0f, n[3] = {0.0f, 0.0f, 0.0f}, P[3] = {0.0f, 0.0f, 0.0f};
-    int mat = -1, seg = 0;
-    if (k == kEmpty) {
-      rgb[0] = im.bg[0];
-      rgb[1] = im.bg[1];
-      rgb[2] = im.bg[2];
-    } else {
-      depth = __uint_as_float(unsigned(k >> 32));
-      const Record* r = rec_of(p, sc, unsigned(k));
-      int X[3], Y[3];
-      float iw[3];
-      load_tri(r, X, Y, iw);
-      const int4 q2 = reinterpret_cast<const int4*>(r)[2];
-      const float4 q3 = reinterpret_cast<const float4*>(r)[3];
-      const float4 q4 = reinterpret_cast<const float4*>(r)[4];
-      mat = q2.y & 0xffff;
-      seg = q2.y >> 16;
-      const int cx = 256 * px + 128, cy = 256 * py + 128;
-      float a0 = float(cx - X[1]) * float(Y[2] - Y[1]) - float(cy - Y[1]) * float(X[2] - X[1]);
-      float a1 = float(cx - X[2]) * float(Y[0] - Y[2]) - float(cy - Y[2]) * float(X[0] - X[2]);
-      float a2 = float(cx - X[0]) * float(Y[1] - Y[0]) - float(cy - Y[0]) * float(X[1] - X[0]);
-      if (!im.ortho) {
-        a0 *= iw[0];
-        a1 *= iw[1];
-        a2 *= iw[2];
-      }
-      n[0] = a0 * __int_as_float(q2.z) + a1 * q3.y + a2 * q4.x;
-      n[1] = a0 * __int_as_float(q2.w) + a1 * q3.z + a2 * q4.y;
-      n[2] = a0 * q3.x + a1 * q3.w + a2 * q4.z;
-      float l2 = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
-      if (l2 > 0.0f) {
-        float rl = rsqrtf(l2);
-        n[0] *= rl;
-        n[1] *= rl;
-        n[2] *= rl;
-      }
-      const float ux = (float(px) + 0.5f - im.cx) * im.inv_fx;
-      const float uy = -((float(py) + 0.5f - im.cy) * im.inv_fy);
-      if (im.ortho) {
-        P[0] = ux;
-        P[1] = uy;
-        P[2] = -depth;
+  const long long orow = im.px_off + (long long)y0 * im.W + x0;
+  auto rgb_phase = [&](int ly) { return p.rgb ? int(reinterpret_cast<uintptr_t>(p.rgb + 3 * (orow + (long long)ly * im.W)) & 15) : 0; };
+  auto nrm_phase = [&](int ly) { return p.normal ? int(reinterpret_cast<uintptr_t>(p.normal + 3 * (orow + (long long)ly * im.W)) & 15) : 0; };
+  if (lane < npx) {
+    int lx = lane % cw, ly = lane / cw;
+    for (int i = lane; i < npx; i += 32) {
+      const int px = x0 + lx, py = y0 + ly;
+      const long long o = im.px_off + (long long)py * im.W + px;
+      const unsigned long long kk = keys[i];
+      float rgb[3], depth = 0.0f, n[3] = {0.0f, 0.0f, 0.0f}, P[3] = {0.0f, 0.0f, 0.0f};
+      int mat = -1, seg = 0;
+      if (kk == kEmpty) {
+        rgb[0] = im.bg[0];
+        rgb[1] = im.bg[1];
+        rgb[2] = im.bg[2];
       } else {
-        P[0] = depth * ux;
-        P[1] = depth * uy;
-        P[2] = -depth;
+        depth = __uint_as_float(unsigned(kk >> 32));
+        const Record* r = rec_of(p, sc, unsigned(kk));
+        int X[3], Y[3];
+        float iw[3];
+        load_tri(r, X, Y, iw);
+        const int4 q2 = reinterpret_cast<const int4*>(r)[2];
+        const float4 q3 = reinterpret_cast<const float4*>(r)[3];
+        const float4 q4 = reinterpret_cast<const float4*>(r)[4];
+        mat = q2.y & 0xffff;
+        seg = q2.y >> 16;
+        const int cx = 256 * px + 128, cy = 256 * py + 128;
+        float a0 = float(cx - X[1]) * float(Y[2] - Y[1]) - float(cy - Y[1]) * float(X[2] - X[1]);
+        float a1 = float(cx - X[2]) * float(Y[0] - Y[2]) - float(cy - Y[2]) * float(X[0] - X[2]);
+        float a2 = float(cx - X[0]) * float(Y[1] - Y[0]) - float(cy - Y[0]) * float(X[1] - X[0]);
+        if (!im.ortho) {
+          a0 *= iw[0];
+          a1 *= iw[1];
+          a2 *= iw[2];
+        }
+        n[0] = a0 * __int_as_float(q2.z) + a1 * q3.y + a2 * q4.x;
+        n[1] = a0 * __int_as_float(q2.w) + a1 * q3.z + a2 * q4.y;
+        n[2] = a0 * q3.x + a1 * q3.w + a2 * q4.z;
+        const float l2 = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+        if (l2 > 0.0f) {
+          const float rl = rsqrtf(l2);
+          n[0] *= rl;
+          n[1] *= rl;
+          n[2] *= rl;
+        }
+        const float ux = (float(px) + 0.5f - im.cx) * im.inv_fx;
+        const float uy = -((float(py) + 0.5f - im.cy) * im.inv_fy);
+        if (im.ortho) {
+          P[0] = ux;
+          P[1] = uy;
+          P[2] = -depth;
+        } else {
+          P[0] = depth * ux;
+          P[1] = depth * uy;
+          P[2] = -depth;
+        }
+        shade(sh, P, n, mat, rgb);
       }
-      shade(sh, P, n, mat, rgb);
-    }
-    if (p.rgb) {
-      if (full_rows) {
-        st_rgb[3 * i + 0] = quantise(rgb[0]);
-        st_rgb[3 * i + 1] = quantise(rgb[1]);
-        st_rgb[3 * i + 2] = quantise(rgb[2]);
-      } else {
-        p.rgb[3 * o + 0] = quantise(rgb[0]);
-        p.rgb[3 * o + 1] = quantise(rgb[1]);
-        p.rgb[3 * o + 2] = quantise(rgb[2]);
+      if (p.rgb) {
+        char* st = wbase + L.w_rgb + ly * L.rgb_row + rgb_phase(ly) + 3 * lx;
+        st[0] = quantise(rgb[0]);
+        st[1] = quantise(rgb[1]);
+        st[2] = quantise(rgb[2]);
       }
-    }
-    if (p.normal) {
-      uint16_t h0 = __half_as_ushort(__float2half_rn(n[0])), h1 = __half_as_ushort(__float2half_rn(n[1])),
-               h2 = __half_as_ushort(__float2half_rn(n[2]));
-      if (full_rows) {
-        uint16_t* s16 = reinterpret_cast<uint16_t*>(st_nrm);
-        s16[3 * i + 0] = h0;
-        s16[3 * i + 1] = h1;
-        s16[3 * i + 2] = h2;
-      } else {
-        p.normal[3 * o + 0] = h0;
-        p.normal[3 * o + 1] = h1;
-        p.normal[3 * o + 2] = h2;
+      if (p.normal) {
+        uint16_t* st = reinterpret_cast<uint16_t*>(wbase + L.w_nrm + ly * L.nrm_row + nrm_phase(ly)) + 3 * lx;
+        st[0] = __half_as_ushort(__float2half_rn(n[0]));
+        st[1] = __half_as_ushort(__float2half_rn(n[1]));
+        st[2] = __half_as_ushort(__float2half_rn(n[2]));
       }
-    }
-    if (p.depth) __stcs(p.depth + o, depth);
-    if (p.seg) p.seg[o] = (uint8_t)seg;
-    if (p.rgb_linear) {
-      __stcs(p.rgb_linear + 3 * o + 0, rgb[0]);
-      __stcs(p.rgb_linear + 3 * o + 1, rgb[1]);
-      __stcs(p.rgb_linear + 3 * o + 2, rgb[2]);
-    }
-    if (p.gbuffer) {
-      __stcs(p.gbuffer + 0 * N + o, P[0]);
-      __stcs(p.gbuffer + 1 * N + o, P[1]);
-      __stcs(p.gbuffer + 2 * N + o, P[2]);
-      __stcs(p.gbuffer + 3 * N + o, n[0]);
-      __stcs(p.gbuffer + 4 * N + o, n[1]);
-      __stcs(p.gbuffer + 5 * N + o, n[2]);
-      __stcs(p.gbuffer + 6 * N + o, __int_as_float(mat));
+      if (p.depth) __stcs(p.depth + o, depth);
+      if (p.seg) p.seg[o] = (uint8_t)seg;
+      if (p.rgb_linear) {
+        __stcs(p.rgb_linear + 3 * o + 0, rgb[0]);
+        __stcs(p.rgb_linear + 3 * o + 1, rgb[1]);
+        __stcs(p.rgb_linear + 3 * o + 2, rgb[2]);
+      }
+      if (p.gbuffer) {
+        __stcs(p.gbuffer + 0 * N + o, P[0]);
+        __stcs(p.gbuffer + 1 * N + o, P[1]);
+        __stcs(p.gbuffer + 2 * N + o, P[2]);
+        __stcs(p.gbuffer + 3 * N + o, n[0]);
+        __stcs(p.gbuffer + 4 * N + o, n[1]);
+        __stcs(p.gbuffer + 5 * N + o, n[2]);
+        __stcs(p.gbuffer + 6 * N + o, __int_as_float(mat));
+      }
+      lx += 32;
+      while (lx >= cw) {
+        lx -= cw;
+        ly++;
+      }
     }
   }
-  if (full_rows) {
-    // the alignment offset is identical on both sides of the copy; 16 B vectors in the middle
-    // (16-byte staging slack keeps shared-memory reads in bounds)
-    // note: a CTA-wide barrier orders the staging writes before the copy
-    __syncthreads();
-    if (p.rgb) copy_out(reinterpret_cast<char*>(p.rgb + 3 * o0), st_rgb, 3 * npx, tid, nt);
-    if (p.normal) copy_out(reinterpret_cast<char*>(p.normal + 3 * o0), st_nrm, 6 * npx, tid, nt);
+  __syncwarp();
+  for (int ly = 0; ly < ch; ly++) {
+    const long long orr = orow + (long long)ly * im.W;
+    if (p.rgb)
+      copy_out(reinterpret_cast<char*>(p.rgb + 3 * orr), wbase + L.w_rgb + ly * L.rgb_row + rgb_phase(ly), 3 * cw,
+               lane, 32);
+    if (p.normal)
+      copy_out(reinterpret_cast<char*>(p.normal + 3 * orr), wbase + L.w_nrm + ly * L.nrm_row + nrm_phase(ly), 6 * cw,
+               lane, 32);
+  }
+  __syncwarp();
+}
+
+// Phase R for the current image: warps pull tiles first, first + stride, ... from the
+// CTA's counter until none is left.
+__device__ void raster_phase(const Params& p, CtaShared& sh, const Scratch& sc, char* uni, const SmemLayout& L,
+                             int first = 0, int stride = 1) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  char* wbase = uni + (size_t)warp * L.w_bytes;
+  while (true) {
+    int k = 0;
+    if (lane == 0) k = atomicAdd(&sh.next_tile, 1);
+    const int t = first + stride * __shfl_sync(kFull, k, 0);
+    if (t >= sh.im.n_tiles) break;
+    raster_tile_warp(p, sh, sc, t, wbase, L);
   }
   __syncthreads();
 }
@@ -910,11 +921,14 @@ struct SmemPtrs {
   char* uni;
 };
 
-__device__ inline SmemPtrs carve(char* smem, const Params& p) {
+__device__ inline SmemLayout layout_of(const Params& p) {
+  return smem_layout(blockDim.x, p.tile_w, p.tile_h, p.inst_max, p.max_tiles, p.w_max);
+}
+
+__device__ inline SmemPtrs carve(char* smem, const Params& p, const SmemLayout& L) {
   SmemPtrs s;
   s.mprefix = reinterpret_cast<int*>(smem);
   s.tprefix = s.mprefix + (p.inst_max + 2);
-  SmemLayout L = smem_layout(blockDim.x, p.tile_w, p.tile_h, p.inst_max, p.max_tiles);
   s.uni = smem + L.uni;
   return s;
 }
@@ -925,8 +939,8 @@ __device__ inline SmemPtrs carve(char* smem, const Params& p) {
 __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
   extern __shared__ __align__(16) char smem[];
   __shared__ CtaShared sh;
-  SmemPtrs sp = carve(smem, p);
-  const SmemLayout L = smem_layout(blockDim.x, p.tile_w, p.tile_h, p.inst_max, p.max_tiles);
+  const SmemLayout L = layout_of(p);
+  SmemPtrs sp = carve(smem, p, L);
   const Scratch sc = slot_scratch(p, blockIdx.x);
   while (true) {
     if (threadIdx.x == 0) sh.img = atomicAdd(p.work_counter, 1);
@@ -939,7 +953,7 @@ __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
       __syncthreads();
       int* counts = reinterpret_cast<int*>(sp.uni);
       bin_phase(p, sh, counts, counts + (p.max_tiles + 2), sc);
-      for (int t = 0; t < sh.im.n_tiles; t++) raster_tile(p, sh, sc, t, sp.uni, L);
+      raster_phase(p, sh, sc, sp.uni, L);
     }
     __syncthreads();
   }
@@ -959,7 +973,8 @@ __global__ void __launch_bounds__(512, 2) plain_geometry_kernel(Params p) {
   __shared__ CtaShared sh;
   const int cam = plain_cam(p);
   if (cam < 0) return;
-  SmemPtrs sp = carve(smem, p);
+  const SmemLayout L = layout_of(p);
+  SmemPtrs sp = carve(smem, p, L);
   const Scratch sc = slot_scratch(p, blockIdx.x);
   setup_image(p, cam, sh, sp.mprefix, sp.tprefix, true);
   if (!sh.im.valid) {
@@ -976,7 +991,8 @@ __global__ void __launch_bounds__(512, 2) plain_bin_kernel(Params p) {
   __shared__ CtaShared sh;
   const int cam = plain_cam(p);
   if (cam < 0) return;
-  SmemPtrs sp = carve(smem, p);
+  const SmemLayout L = layout_of(p);
+  SmemPtrs sp = carve(smem, p, L);
   const Scratch sc = slot_scratch(p, blockIdx.x);
   setup_image(p, cam, sh, sp.mprefix, sp.tprefix, false);
   const int nvis = sc.header[0];
@@ -995,13 +1011,12 @@ __global__ void __launch_bounds__(512, 2) plain_raster_kernel(Params p) {
   if (cam < 0) return;
   const Scratch sc = slot_scratch(p, blockIdx.x);
   if (sc.header[0] < 0) return;
-  SmemPtrs sp = carve(smem, p);
-  const SmemLayout L = smem_layout(blockDim.x, p.tile_w, p.tile_h, p.inst_max, p.max_tiles);
+  const SmemLayout L = layout_of(p);
+  SmemPtrs sp = carve(smem, p, L);
   setup_image(p, cam, sh, sp.mprefix, sp.tprefix, false);
-  if ((int)blockIdx.y >= sh.im.n_tiles) return;
   if (threadIdx.x == 0) sh.n_big = sc.header[1];
   __syncthreads();
-  raster_tile(p, sh, sc, blockIdx.y, sp.uni, L);
+  raster_phase(p, sh, sc, sp.uni, L, blockIdx.y, gridDim.y);
 }
 
 // Scratch of orrb_render_batch_noalloc: a file-scope device array, so that
@@ -1031,8 +1046,8 @@ int noalloc_scratch(int device, void** ptr, size_t* bytes) {
   return 0;
 }
 
-size_t render_smem_bytes(int threads, int tile_w, int tile_h, int inst_max, int max_tiles) {
-  return smem_layout(threads, tile_w, tile_h, inst_max, max_tiles).total;
+size_t render_smem_bytes(int threads, int tile_w, int tile_h, int inst_max, int max_tiles, int w_max) {
+  return smem_layout(threads, tile_w, tile_h, inst_max, max_tiles, w_max).total;
 }
 
 int render_max_ctas_per_sm(int threads, size_t smem) {
@@ -1046,7 +1061,7 @@ int render_max_ctas_per_sm(int threads, size_t smem) {
 int launch_render(const Params& p, int mode, int threads, int n_ctas, int max_cams_per_sample, void* stream,
                   char* err, size_t errlen) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const size_t smem = render_smem_bytes(threads, p.tile_w, p.tile_h, p.inst_max, p.max_tiles);
+  const size_t smem = render_smem_bytes(threads, p.tile_w, p.tile_h, p.inst_max, p.max_tiles, p.w_max);
   cudaError_t e = cudaSuccess;
   if (mode == 0) {
     e = cudaFuncSetAttribute(render_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1064,7 +1079,7 @@ int launch_render(const Params& p, int mode, int threads, int n_ctas, int max_ca
       q.plain_sample = s;
       plain_geometry_kernel<<<max_cams_per_sample, threads, smem, st>>>(q);
       plain_bin_kernel<<<max_cams_per_sample, threads, smem, st>>>(q);
-      plain_raster_kernel<<<dim3(max_cams_per_sample, p.max_tiles), threads, smem, st>>>(q);
+      plain_raster_kernel<<<dim3(max_cams_per_sample, kPlainRasterSplit), threads, smem, st>>>(q);
       e = cudaGetLastError();
     }
   }

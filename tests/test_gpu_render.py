@@ -85,8 +85,9 @@ def test_ragged_wide_and_orthographic(oracle):
     b = scenes.single_sample(meshes, [0, 1, 2], poses, cams, seg=[1, 2, 3], mat_base=[0, 1, 7],
                              lights=[((0.5, -1.0, 2.0), 2.0), ((-1.0, 0.5, 1.5), 1.0)], albedo=(0.6, 0.4, 0.3),
                              specular=0.5, shininess=20.0, ambient=(0.05, 0.05, 0.05), background=(0.2, 0.3, 0.4))
-    for th in (1, 8, 16):
-        compare(render_np(r, b, config(tile_h=th)), oracle.render(b, debug=True), f"ragged th={th}")
+    for tw, th in ((256, 1), (64, 4), (24, 8), (512, 1)):
+        compare(render_np(r, b, config(tile_w=tw, tile_h=th, threads=256)), oracle.render(b, debug=True),
+                f"ragged tile={tw}x{th}")
 
 
 def test_empty_scene_and_no_lights(tiny_renderer, oracle):
@@ -101,7 +102,7 @@ def test_empty_scene_and_no_lights(tiny_renderer, oracle):
     assert (g["seg"][n:2 * n] == 0).all() and (g["depth"][n:2 * n] == 0).all()
 
 
-@pytest.mark.parametrize("tile", [(512, 4), (64, 8), (128, 16), (32, 32), (200, 1)])
+@pytest.mark.parametrize("tile", [(256, 1), (200, 2), (64, 2), (32, 4), (16, 8), (8, 16), (120, 1)])
 @pytest.mark.parametrize("threads", [256, 512])
 def test_bit_identical_across_tilings_and_modes(hand_renderer, tile, threads):
     b = sg.hand_batch(5, np.arange(6), res=200)
