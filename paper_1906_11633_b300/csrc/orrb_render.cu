@@ -53,6 +53,7 @@ constexpr int kPlainRasterSplit = 8;  // plain mode: CTAs sharing one image's ti
 struct ImageInfo {
   int cam, s, W, H, inst0, n_inst, ortho, T, valid;
   int tw, th, ntx, n_tiles;
+  unsigned m_tw, m_th;  // ceil(2^32 / d) (0 for d = 1): x / d = umulhi(x, m) exactly for x < 2^16, d <= 4096
   long long px_off;
   float fx, fy, cx, cy, near, inv_fx, inv_fy;
   float V[12];
@@ -227,6 +228,8 @@ __device__ void setup_image(const Params& p, int cam, CtaShared& sh, int* mprefi
     im.tw = min(im.W, p.tile_w);
     im.th = p.tile_h;
     im.ntx = (im.W + im.tw - 1) / im.tw;
+    im.m_tw = im.tw > 1 ? unsigned((0x100000000ull + im.tw - 1) / im.tw) : 0u;
+    im.m_th = im.th > 1 ? unsigned((0x100000000ull + im.th - 1) / im.th) : 0u;
     im.n_tiles = im.ntx * ((im.H + im.th - 1) / im.th);
     int nl = p.light_meta[s * 2 + 0];
     if (nl < 0 || nl > kMaxLights) {
@@ -326,7 +329,12 @@ __device__ __forceinline__ void write_record(Record* r, const int X[3], const in
   int4* q = reinterpret_cast<int4*>(r);
   q[0] = make_int4(X[0], Y[0], X[1], Y[1]);
   q[1] = make_int4(X[2], Y[2], __float_as_int(iw[0]), __float_as_int(iw[1]));
-  q[2] = make_int4(__float_as_int(iw[2]), mat | (seg << 16), __float_as_int(n[0][0]), __float_as_int(n[0][1]));
+  // bit 24: the three vertex normals are bitwise equal (a flat face), so the interpolated
+  // normal is n0 up to rounding and the resolve skips the interpolation
+  const int flat = n[0][0] == n[1][0] && n[0][1] == n[1][1] && n[0][2] == n[1][2] && n[0][0] == n[2][0] &&
+                   n[0][1] == n[2][1] && n[0][2] == n[2][2];
+  q[2] = make_int4(__float_as_int(iw[2]), mat | (seg << 16) | (flat << 24), __float_as_int(n[0][0]),
+                   __float_as_int(n[0][1]));
   float4* f = reinterpret_cast<float4*>(r);
   f[3] = make_float4(n[0][2], n[1][0], n[1][1], n[1][2]);
   f[4] = make_float4(n[2][0], n[2][1], n[2][2], 0.0f);
@@ -511,12 +519,14 @@ __device__ void geometry_phase(const Params& p, CtaShared& sh, const int* mprefi
 // ---------------------------------------------------------------------------
 // phase B: screen-tile binning
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool binned_span(uint2 box, int tw, int th, int& tx0, int& tx1, int& ty0, int& ty1) {
-  int x0 = box.x & 0xffff, x1 = box.x >> 16, y0 = box.y & 0xffff, y1 = box.y >> 16;
-  tx0 = x0 / tw;
-  tx1 = x1 / tw;
-  ty0 = y0 / th;
-  ty1 = y1 / th;
+__device__ __forceinline__ unsigned udiv16(unsigned x, unsigned m) { return m ? __umulhi(x, m) : x; }
+
+__device__ __forceinline__ bool binned_span(uint2 box, const ImageInfo& im, int& tx0, int& tx1, int& ty0, int& ty1) {
+  const unsigned x0 = box.x & 0xffff, x1 = box.x >> 16, y0 = box.y & 0xffff, y1 = box.y >> 16;
+  tx0 = udiv16(x0, im.m_tw);
+  tx1 = udiv16(x1, im.m_tw);
+  ty0 = udiv16(y0, im.m_th);
+  ty1 = udiv16(y1, im.m_th);
   return (tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= kMaxSpanTiles;
 }
 
@@ -532,7 +542,7 @@ __device__ void bin_phase(const Params& p, CtaShared& sh, int* counts, int* curs
     bool big = false;
     if (e < n) {
       int tx0, tx1, ty0, ty1;
-      if (binned_span(sc.vis_box[e], im.tw, im.th, tx0, tx1, ty0, ty1)) {
+      if (binned_span(sc.vis_box[e], im, tx0, tx1, ty0, ty1)) {
         for (int ty = ty0; ty <= ty1; ty++)
           for (int tx = tx0; tx <= tx1; tx++) atomicAdd(&counts[ty * im.ntx + tx], 1);
       } else {
@@ -555,7 +565,7 @@ __device__ void bin_phase(const Params& p, CtaShared& sh, int* counts, int* curs
   __syncthreads();
   for (int e = tid; e < n; e += nt) {
     int tx0, tx1, ty0, ty1;
-    if (binned_span(sc.vis_box[e], im.tw, im.th, tx0, tx1, ty0, ty1)) {
+    if (binned_span(sc.vis_box[e], im, tx0, tx1, ty0, ty1)) {
       const uint32_t key = sc.vis_key[e];
       for (int ty = ty0; ty <= ty1; ty++)
         for (int tx = tx0; tx <= tx1; tx++) sc.bins[atomicAdd(&cursor[ty * im.ntx + tx], 1)] = key;
@@ -650,10 +660,14 @@ __device__ void shade(const CtaShared& sh, const float P[3], const float n[3], i
       if (h2 > 0.0f) {
         float rh = rsqrtf(h2);
         float ndh = fmaxf(0.0f, (n[0] * H0 + n[1] * H1 + n[2] * H2) * rh);
-        // ndh^alpha for ndh in [0, 1], alpha >= 1: both library calls are accurate to a
-        // couple of ulp, so the relative error is ~1e-7 * |alpha log2 ndh| (< 2e-6 wherever
-        // the term is not negligible), without powf's handling of negative bases
-        spec = ndh > 0.0f ? m[3] * exp2f(m[4] * log2f(ndh)) : 0.0f;
+        // ndh^alpha for ndh in [0, 1], alpha >= 1.  The MUFU form (__powf: lg2.approx with
+        // absolute error <= 2^-22.6 near 1, ex2.approx relative <= 2^-22) has relative error
+        // <= (alpha + 2.2) * 1.1e-7; it is used only where that, times the lobe's weight
+        // 2^EV * E * k_s, stays under 2e-5.  Otherwise exp2f(alpha * log2f(ndh)) with both
+        // calls accurate to a couple of ulp (~1e-7 * |alpha log2 ndh| relative).
+        const float w = im.scale * E * m[3];
+        if (w * (m[4] + 2.2f) <= 180.0f) spec = m[3] * __powf(ndh, m[4]);
+        else spec = ndh > 0.0f ? m[3] * exp2f(m[4] * log2f(ndh)) : 0.0f;
       }
     }
     c0 += E * (m[0] * ndl + spec);
@@ -730,14 +744,29 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
     float fA;
     int tl;
     tri_setup(X, Y, fA, tl);
-    const int bw = bx1 - bx0 + 1, n = bw * (by1 - by0 + 1);
-    if (lane < n) {
-      BoxWalk w(lane, bx0, by0, bw);
-      for (int j = lane; j < n; j += 32) {
-        const unsigned long long f = fragment(X, Y, iw, fA, tl, key, im.ortho, 256 * w.px + 128, 256 * w.py + 128);
-        unsigned long long& k = keys[(w.py - y0) * cw + (w.px - x0)];
-        if (f < k) k = f;
-        w.advance(bx0, bw);
+    const int bw = bx1 - bx0 + 1;
+    // per row: the lane's pixels are bx0 + lane + 32k, so each edge function advances by a
+    // constant 32 * 256 * dy between them (exact 64-bit integer steps)
+    const long long s0 = 8192ll * (Y[2] - Y[1]), s1 = 8192ll * (Y[0] - Y[2]), s2 = 8192ll * (Y[1] - Y[0]);
+    for (int py = by0; py <= by1; py++) {
+      int px = bx0 + lane;
+      if (px > bx1) continue;
+      const int cx = 256 * px + 128, cy = 256 * py + 128;
+      long long w0 = (long long)(cx - X[1]) * (Y[2] - Y[1]) - (long long)(cy - Y[1]) * (X[2] - X[1]);
+      long long w1 = (long long)(cx - X[2]) * (Y[0] - Y[2]) - (long long)(cy - Y[2]) * (X[0] - X[2]);
+      long long w2 = (long long)(cx - X[0]) * (Y[1] - Y[0]) - (long long)(cy - Y[0]) * (X[1] - X[0]);
+      unsigned long long* krow = keys + (py - y0) * cw - x0;
+      for (; px <= bx1; px += 32) {
+        if (w0 + (tl & 1) > 0 && w1 + ((tl >> 1) & 1) > 0 && w2 + ((tl >> 2) & 1) > 0) {
+          const float f0 = __ll2float_rn(w0), f1 = __ll2float_rn(w1), f2 = __ll2float_rn(w2);
+          const float sum = __fadd_rn(__fadd_rn(__fmul_rn(f0, iw[0]), __fmul_rn(f1, iw[1])), __fmul_rn(f2, iw[2]));
+          const float depth = im.ortho ? __fdiv_rn(sum, fA) : __fdiv_rn(fA, sum);
+          const unsigned long long f = ((unsigned long long)__float_as_uint(depth) << 32) | key;
+          if (f < krow[px]) krow[px] = f;
+        }
+        w0 += s0;
+        w1 += s1;
+        w2 += s2;
       }
     }
     __syncwarp();
@@ -793,15 +822,19 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
   // resolve + shade; depth / seg / optional planes go straight out, RGB and normals are
   // staged per tile row at the destination's 16-byte phase and copied with vector stores
   const long long N = p.total_pixels;
-  const long long orow = im.px_off + (long long)y0 * im.W + x0;
-  auto rgb_phase = [&](int ly) { return p.rgb ? int(reinterpret_cast<uintptr_t>(p.rgb + 3 * (orow + (long long)ly * im.W)) & 15) : 0; };
-  auto nrm_phase = [&](int ly) { return p.normal ? int(reinterpret_cast<uintptr_t>(p.normal + 3 * (orow + (long long)ly * im.W)) & 15) : 0; };
-  if (lane < npx) {
-    int lx = lane % cw, ly = lane / cw;
-    for (int i = lane; i < npx; i += 32) {
-      const int px = x0 + lx, py = y0 + ly;
-      const long long o = im.px_off + (long long)py * im.W + px;
-      const unsigned long long kk = keys[i];
+  for (int ly = 0; ly < ch; ly++) {
+    const long long orow = im.px_off + (long long)(y0 + ly) * im.W + x0;
+    const int py = y0 + ly;
+    const float uy = -((float(py) + 0.5f - im.cy) * im.inv_fy);
+    char* st_rgb = wbase + L.w_rgb + ly * L.rgb_row + (p.rgb ? int(reinterpret_cast<uintptr_t>(p.rgb + 3 * orow) & 15) : 0);
+    uint16_t* st_nrm = reinterpret_cast<uint16_t*>(
+        wbase + L.w_nrm + ly * L.nrm_row + (p.normal ? int(reinterpret_cast<uintptr_t>(p.normal + 3 * orow) & 15) : 0));
+    float* depth_row = p.depth ? p.depth + orow : nullptr;
+    uint8_t* seg_row = p.seg ? p.seg + orow : nullptr;
+    const unsigned long long* krow = keys + ly * cw;
+    for (int lx = lane; lx < cw; lx += 32) {
+      const int px = x0 + lx;
+      const unsigned long long kk = krow[lx];
       float rgb[3], depth = 0.0f, n[3] = {0.0f, 0.0f, 0.0f}, P[3] = {0.0f, 0.0f, 0.0f};
       int mat = -1, seg = 0;
       if (kk == kEmpty) {
@@ -811,26 +844,31 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
       } else {
         depth = __uint_as_float(unsigned(kk >> 32));
         const Record* r = rec_of(p, sc, unsigned(kk));
-        int X[3], Y[3];
-        float iw[3];
-        load_tri(r, X, Y, iw);
         const int4 q2 = reinterpret_cast<const int4*>(r)[2];
         const float4 q3 = reinterpret_cast<const float4*>(r)[3];
-        const float4 q4 = reinterpret_cast<const float4*>(r)[4];
         mat = q2.y & 0xffff;
-        seg = q2.y >> 16;
-        const int cx = 256 * px + 128, cy = 256 * py + 128;
-        float a0 = float(cx - X[1]) * float(Y[2] - Y[1]) - float(cy - Y[1]) * float(X[2] - X[1]);
-        float a1 = float(cx - X[2]) * float(Y[0] - Y[2]) - float(cy - Y[2]) * float(X[0] - X[2]);
-        float a2 = float(cx - X[0]) * float(Y[1] - Y[0]) - float(cy - Y[0]) * float(X[1] - X[0]);
-        if (!im.ortho) {
-          a0 *= iw[0];
-          a1 *= iw[1];
-          a2 *= iw[2];
+        seg = (q2.y >> 16) & 0xff;
+        if (q2.y & (1 << 24)) {  // flat face: the interpolated normal is the vertex normal
+          n[0] = __int_as_float(q2.z);
+          n[1] = __int_as_float(q2.w);
+          n[2] = q3.x;
+        } else {
+          const int4 q0 = reinterpret_cast<const int4*>(r)[0];
+          const int4 q1 = reinterpret_cast<const int4*>(r)[1];
+          const float4 q4 = reinterpret_cast<const float4*>(r)[4];
+          const int cx = 256 * px + 128, cy = 256 * py + 128;
+          float a0 = float(cx - q0.z) * float(q1.y - q0.w) - float(cy - q0.w) * float(q1.x - q0.z);
+          float a1 = float(cx - q1.x) * float(q0.y - q1.y) - float(cy - q1.y) * float(q0.x - q1.x);
+          float a2 = float(cx - q0.x) * float(q0.w - q0.y) - float(cy - q0.y) * float(q0.z - q0.x);
+          if (!im.ortho) {
+            a0 *= __int_as_float(q1.z);
+            a1 *= __int_as_float(q1.w);
+            a2 *= __int_as_float(q2.x);
+          }
+          n[0] = a0 * __int_as_float(q2.z) + a1 * q3.y + a2 * q4.x;
+          n[1] = a0 * __int_as_float(q2.w) + a1 * q3.z + a2 * q4.y;
+          n[2] = a0 * q3.x + a1 * q3.w + a2 * q4.z;
         }
-        n[0] = a0 * __int_as_float(q2.z) + a1 * q3.y + a2 * q4.x;
-        n[1] = a0 * __int_as_float(q2.w) + a1 * q3.z + a2 * q4.y;
-        n[2] = a0 * q3.x + a1 * q3.w + a2 * q4.z;
         const float l2 = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
         if (l2 > 0.0f) {
           const float rl = rsqrtf(l2);
@@ -839,7 +877,6 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
           n[2] *= rl;
         }
         const float ux = (float(px) + 0.5f - im.cx) * im.inv_fx;
-        const float uy = -((float(py) + 0.5f - im.cy) * im.inv_fy);
         if (im.ortho) {
           P[0] = ux;
           P[1] = uy;
@@ -852,25 +889,26 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
         shade(sh, P, n, mat, rgb);
       }
       if (p.rgb) {
-        char* st = wbase + L.w_rgb + ly * L.rgb_row + rgb_phase(ly) + 3 * lx;
-        st[0] = quantise(rgb[0]);
-        st[1] = quantise(rgb[1]);
-        st[2] = quantise(rgb[2]);
+        st_rgb[3 * lx + 0] = quantise(rgb[0]);
+        st_rgb[3 * lx + 1] = quantise(rgb[1]);
+        st_rgb[3 * lx + 2] = quantise(rgb[2]);
       }
       if (p.normal) {
-        uint16_t* st = reinterpret_cast<uint16_t*>(wbase + L.w_nrm + ly * L.nrm_row + nrm_phase(ly)) + 3 * lx;
-        st[0] = __half_as_ushort(__float2half_rn(n[0]));
-        st[1] = __half_as_ushort(__float2half_rn(n[1]));
-        st[2] = __half_as_ushort(__float2half_rn(n[2]));
+        const __half2 h01 = __floats2half2_rn(n[0], n[1]);
+        st_nrm[3 * lx + 0] = __half_as_ushort(__low2half(h01));
+        st_nrm[3 * lx + 1] = __half_as_ushort(__high2half(h01));
+        st_nrm[3 * lx + 2] = __half_as_ushort(__float2half_rn(n[2]));
       }
-      if (p.depth) __stcs(p.depth + o, depth);
-      if (p.seg) p.seg[o] = (uint8_t)seg;
+      if (depth_row) __stcs(depth_row + lx, depth);
+      if (seg_row) seg_row[lx] = (uint8_t)seg;
       if (p.rgb_linear) {
-        __stcs(p.rgb_linear + 3 * o + 0, rgb[0]);
-        __stcs(p.rgb_linear + 3 * o + 1, rgb[1]);
-        __stcs(p.rgb_linear + 3 * o + 2, rgb[2]);
+        float* o3 = p.rgb_linear + 3 * (orow + lx);
+        __stcs(o3 + 0, rgb[0]);
+        __stcs(o3 + 1, rgb[1]);
+        __stcs(o3 + 2, rgb[2]);
       }
       if (p.gbuffer) {
+        const long long o = orow + lx;
         __stcs(p.gbuffer + 0 * N + o, P[0]);
         __stcs(p.gbuffer + 1 * N + o, P[1]);
         __stcs(p.gbuffer + 2 * N + o, P[2]);
@@ -879,22 +917,10 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
         __stcs(p.gbuffer + 5 * N + o, n[2]);
         __stcs(p.gbuffer + 6 * N + o, __int_as_float(mat));
       }
-      lx += 32;
-      while (lx >= cw) {
-        lx -= cw;
-        ly++;
-      }
     }
-  }
-  __syncwarp();
-  for (int ly = 0; ly < ch; ly++) {
-    const long long orr = orow + (long long)ly * im.W;
-    if (p.rgb)
-      copy_out(reinterpret_cast<char*>(p.rgb + 3 * orr), wbase + L.w_rgb + ly * L.rgb_row + rgb_phase(ly), 3 * cw,
-               lane, 32);
-    if (p.normal)
-      copy_out(reinterpret_cast<char*>(p.normal + 3 * orr), wbase + L.w_nrm + ly * L.nrm_row + nrm_phase(ly), 6 * cw,
-               lane, 32);
+    __syncwarp();
+    if (p.rgb) copy_out(reinterpret_cast<char*>(p.rgb + 3 * orow), st_rgb, 3 * cw, lane, 32);
+    if (p.normal) copy_out(reinterpret_cast<char*>(p.normal + 3 * orow), reinterpret_cast<char*>(st_nrm), 6 * cw, lane, 32);
   }
   __syncwarp();
 }
