@@ -377,6 +377,151 @@ def _lit_lights(batch, gb, fg, per_img_px):
     return total
 
 
+def run_uneven(args, world, rank, local):
+    """1024 scenes with log-uniform [1k, 50k] triangles, square resolutions U{64..512}, 1-3 cameras: one
+    persistent launch replayed from a CUDA graph with the autotuned tiling, vs per-scene plain launches."""
+    import torch
+    from paper_1906_11633_b300 import scenegen as sg
+    from paper_1906_11633_b300 import lib as L
+    from paper_1906_11633_b300.render import GraphRender, Renderer, config
+    from paper_1906_11633_b300.tune import tune
+    torch.cuda.set_device(local)
+    n = 1024
+    batch = sg.uneven_batch(SEED, shard_samples(rank, world, n))
+    r = Renderer(batch.meshes, device=local)
+    db = r.upload(batch)
+    cfg, timings = tune(r, db, reps=3)
+    g = GraphRender(r, db, cfg=cfg)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    per = []
+    for _ in range(max(5, args.steps // 10)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.replay()
+        e1.record(stream)
+        per.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in per])), world)
+    out = g.out
+    pcfg = config(mode=L.ORRB_MODE_PLAIN, tile_w=cfg.tile_w, tile_h=cfg.tile_h, threads=cfg.threads)
+    r.render(db, out=out, cfg=pcfg)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r.render(db, out=out, cfg=pcfg)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = max_over_ranks(e0.elapsed_time(e1), world)
+    if rank != 0:
+        return
+    peaks, _ = load_peaks()
+    alg_bytes = BYTES_PER_PX * batch.total_pixels
+    line = {"workload": "uneven", "metric": "samples/s, uneven batch in one persistent launch (CUDA graph)",
+            "value": world * n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "n_gpus": world,
+            "config": {"scenes": n, "images": batch.n_cams, "pixels": batch.total_pixels,
+                       "triangles_per_scene": [int(batch.tris_per_sample().min()), int(batch.tris_per_sample().max())],
+                       "tile": [cfg.tile_w, cfg.tile_h], "threads": cfg.threads, "tuner_ms": timings},
+            "plain": {"value": world * n / (plain_ms / 1e3), "ms_per_step": plain_ms,
+                      "launches_per_step": 3 * n},
+            "fused_over_plain": plain_ms / ms,
+            "roofline": {"bound": "hbm", "achieved": alg_bytes / (ms / 1e3) / 1e9, "peak": float(peaks["hbm_gbs"]),
+                         "unit": "GB/s", "frac": alg_bytes / (ms / 1e3) / 1e9 / float(peaks["hbm_gbs"]),
+                         "alg_bytes_per_launch": alg_bytes},
+            "device_status": r.status()}
+    print(json.dumps(line), flush=True)
+
+
+def run_diff(args, world, rank, local):
+    """Forward with G-buffer + shading adjoint for 256 hand samples (L2 loss against perturbed-parameter targets)."""
+    import torch
+    from paper_1906_11633_b300 import scenegen as sg
+    from paper_1906_11633_b300.render import Renderer
+    torch.cuda.set_device(local)
+    batch = sg.hand_batch(SEED, shard_samples(rank, world, N_SAMPLES), res=RES, n_cams=N_CAMS)
+    r = Renderer(batch.meshes, device=local)
+    db = r.upload(batch)
+    mat_t, light_t, ev_t = sg.perturb_params(batch, SEED)
+    dbt = db.with_params(material=torch.from_numpy(mat_t).cuda(), light=torch.from_numpy(light_t).cuda(),
+                         exposure_ev=torch.from_numpy(ev_t).cuda())
+    target = r.render(dbt, rgb_linear=True)["rgb_linear"].clone()
+    out = r.render(db, rgb_linear=True, gbuffer=True)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        r.render(db, out=out, rgb_linear=True, gbuffer=True)
+        d = 2.0 * (out["rgb_linear"] - target)
+        return r.shade_backward(db, out["gbuffer"], d)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    fw, bw = [], []
+    d = 2.0 * (out["rgb_linear"] - target)
+    for _ in range(max(5, args.steps // 10)):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        r.render(db, out=out, rgb_linear=True, gbuffer=True)
+        e[1].record(stream)
+        r.shade_backward(db, out["gbuffer"], d)
+        e[2].record(stream)
+        fw.append(e[:2])
+        bw.append(e[1:])
+    torch.cuda.synchronize()
+    fms = float(np.mean([a.elapsed_time(b) for a, b in fw]))
+    bms = float(np.mean([a.elapsed_time(b) for a, b in bw]))
+    if rank != 0:
+        return
+    peaks, _ = load_peaks()
+    N = batch.total_pixels
+    bw_bytes = N * (7 * 4 + 12) + N_SAMPLES * (128 + 16 + 1) * 4
+    line = {"workload": "diff", "metric": "samples/s, forward with G-buffer + shading adjoint",
+            "value": world * N_SAMPLES / ((fms + bms) / 1e3), "unit": UNIT, "n_gpus": world,
+            "forward_ms": fms, "backward_ms": bms, "backward_samples_per_s": N_SAMPLES / (bms / 1e3),
+            "roofline_backward": {"bound": "hbm", "achieved": bw_bytes / (bms / 1e3) / 1e9,
+                                  "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                                  "frac": bw_bytes / (bms / 1e3) / 1e9 / float(peaks["hbm_gbs"]),
+                                  "alg_bytes_per_launch": bw_bytes},
+            "config": {"samples": N_SAMPLES, "cameras": N_CAMS, "resolution": RES}}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args, world, rank, local):
+    """Poisson arrivals at 2000 req/s of 1-64-sample hand requests at {64,128,200,256} px, 1-3 cameras."""
+    import torch
+    from paper_1906_11633_b300 import scenegen as sg
+    from paper_1906_11633_b300.serve import GpuBackend, Server, run_poisson
+    torch.cuda.set_device(local)
+    rate, dur = 2000.0, args.serve_seconds
+    reqs = sg.poisson_requests(SEED + rank, rate, dur)
+    meshes = sg.hand_meshes()
+    t0 = time.perf_counter()
+    batches = [sg.request_batch(SEED, q, meshes=meshes) for q in reqs]
+    gen_s = time.perf_counter() - t0
+    be = GpuBackend(meshes, device=local, n_streams=2)
+    # warm the path (workspace sizes, allocator) with a few requests first
+    warm = Server(be, n_streams=2, max_inflight=4, tick_ms=2.0)
+    run_poisson(warm, reqs[:64], batches[:64], 0.1)
+    warm.close()
+    srv = Server(be, n_streams=2, max_inflight=4, tick_ms=2.0)
+    subs, wall = run_poisson(srv, reqs, batches, dur)
+    st = srv.stats(wall)
+    srv.close()
+    if rank != 0:
+        return
+    line = {"workload": "serve", "metric": "samples/s and request latency under Poisson arrivals",
+            "value": st["samples_per_s"], "unit": UNIT, "n_gpus": world,
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+            "requests": st["requests"], "samples": st["samples"], "batches": st["batches"],
+            "max_concurrent_batches": st["max_concurrent_batches"], "memory_waits": st["memory_waits"],
+            "config": {"rate_hz": rate, "seconds": dur, "tick_ms": 2.0, "streams": 2, "max_inflight": 4,
+                       "request_samples": "U{1..64}", "resolution": list(sg.SERVE_RES), "cameras": "U{1..3}",
+                       "host_generation_s": gen_s}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -389,12 +534,21 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the fused kernel from an ncu capture of this build")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["hand", "uneven", "diff", "serve"], default="hand",
+                    help="hand: the headline line; the others print supplementary lines")
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "uneven":
+        run_uneven(args, world, rank, local)
+    elif args.workload == "diff":
+        run_diff(args, world, rank, local)
+    elif args.workload == "serve":
+        run_serve(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -25,6 +25,7 @@ int noalloc_scratch(int device, void** ptr, size_t* bytes);
 struct orrb_ctx {
   int device = 0;
   int sm_count = 0;
+  std::vector<std::pair<std::pair<int, size_t>, int>> occupancy;  // (threads, smem) -> CTAs per SM
   std::mutex mu;
   std::string err;
   bool has_meshes = false;
@@ -212,7 +213,13 @@ orrb_status plan(orrb_ctx* ctx, const orrb_batch_shape& s, const orrb_config& c,
   P->smem = render_smem_bytes(c.threads, c.tile_w, c.tile_h, s.max_inst_per_sample, P->max_tiles, s.max_width);
   if (P->smem > 227 * 1024) return fail(ctx, ORRB_ERR_INVALID_ARG, "tile / instance limits need %zu B of shared memory", P->smem);
   if (c.mode == ORRB_MODE_FUSED) {
-    int fit = render_max_ctas_per_sm(c.threads, P->smem);
+    int fit = -1;
+    for (const auto& o : ctx->occupancy)
+      if (o.first.first == c.threads && o.first.second == P->smem) fit = o.second;
+    if (fit < 0) {
+      fit = render_max_ctas_per_sm(c.threads, P->smem);
+      if (fit > 0) ctx->occupancy.push_back({{c.threads, P->smem}, fit});
+    }
     if (fit <= 0) return fail(ctx, ORRB_ERR_CUDA, "occupancy query failed for %zu B shared memory", P->smem);
     P->ctas_per_sm = c.ctas_per_sm > 0 ? std::min(c.ctas_per_sm, fit) : fit;
     P->n_slots = ctx->sm_count * P->ctas_per_sm;

@@ -1076,10 +1076,29 @@ size_t render_smem_bytes(int threads, int tile_w, int tile_h, int inst_max, int 
   return smem_layout(threads, tile_w, tile_h, inst_max, max_tiles, w_max).total;
 }
 
+namespace {
+// The dynamic shared-memory limit is a per-device function attribute: raise it only when a
+// larger size is needed, so steady-state launches (and launches inside a stream capture)
+// make no attribute calls.
+std::mutex g_attr_mu;
+size_t g_attr_set[4][64] = {};
+
+cudaError_t ensure_smem(const void* fn, int which, size_t smem) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> g(g_attr_mu);
+  if (g_attr_set[which][dev] >= smem) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) g_attr_set[which][dev] = smem;
+  return e;
+}
+}  // namespace
+
 int render_max_ctas_per_sm(int threads, size_t smem) {
   int n = 0;
-  if (cudaFuncSetAttribute(render_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return -1;
+  if (ensure_smem((const void*)render_fused_kernel, 0, smem) != cudaSuccess) return -1;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_fused_kernel, threads, smem) != cudaSuccess) return -1;
   return n;
 }
@@ -1090,7 +1109,7 @@ int launch_render(const Params& p, int mode, int threads, int n_ctas, int max_ca
   const size_t smem = render_smem_bytes(threads, p.tile_w, p.tile_h, p.inst_max, p.max_tiles, p.w_max);
   cudaError_t e = cudaSuccess;
   if (mode == 0) {
-    e = cudaFuncSetAttribute(render_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = ensure_smem((const void*)render_fused_kernel, 0, smem);
     if (e == cudaSuccess) {
       render_fused_kernel<<<n_ctas, threads, smem, st>>>(p);
       e = cudaGetLastError();
@@ -1098,8 +1117,7 @@ int launch_render(const Params& p, int mode, int threads, int n_ctas, int max_ca
   } else {
     const void* ks[3] = {(const void*)plain_geometry_kernel, (const void*)plain_bin_kernel,
                          (const void*)plain_raster_kernel};
-    for (int k = 0; k < 3 && e == cudaSuccess; k++)
-      e = cudaFuncSetAttribute(ks[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    for (int k = 0; k < 3 && e == cudaSuccess; k++) e = ensure_smem(ks[k], k + 1, smem);
     Params q = p;
     for (int s = 0; s < p.n_samples && e == cudaSuccess; s++) {
       q.plain_sample = s;

@@ -372,6 +372,15 @@ def perspective_intrinsics(width: int, height: int, fovy_deg: float, near: float
     return np.array([f, f, 0.5 * width, 0.5 * height, near, CAM_PERSPECTIVE], np.float64)
 
 
+def _square_intrinsics(res: np.ndarray, fovy_deg: float, near: float = 0.01):
+    """Perspective intrinsics [C, 6] and sizes [C, 2] of square images of side res[c]."""
+    res = np.asarray(res, np.float64)
+    f = 0.5 * res / math.tan(math.radians(fovy_deg) / 2.0)
+    intr = np.stack([f, f, 0.5 * res, 0.5 * res, np.full_like(res, near), np.full_like(res, CAM_PERSPECTIVE)], -1)
+    wh = np.stack([res, res], -1).astype(np.int32)
+    return intr.reshape(-1, 6), wh.reshape(-1, 2)
+
+
 def orthographic_intrinsics(width: int, height: int, px_per_m: float, near: float = 0.01) -> np.ndarray:
     return np.array([px_per_m, px_per_m, 0.5 * width, 0.5 * height, near, CAM_ORTHOGRAPHIC], np.float64)
 
@@ -483,21 +492,24 @@ def _forward_kinematics(tree, base: np.ndarray, angles: np.ndarray) -> np.ndarra
 def _rig_views(seed: int, ids: np.ndarray, n_cams: np.ndarray, jitter: bool = True):
     """Jittered camera-from-world matrices for the first n_cams[s] rig cameras of each sample."""
     ids = np.asarray(ids)
-    u = uniform(seed, STREAM_CAMERA, ids, 6 * len(CAMERA_RIG))
-    views, owner = [], []
-    for s in range(len(ids)):
-        for k in range(int(n_cams[s])):
-            az, el = (math.radians(a) for a in CAMERA_RIG[k])
-            eye = CAMERA_TARGET + CAMERA_DIST * np.array([math.cos(el) * math.cos(az), math.cos(el) * math.sin(az), math.sin(el)])
-            R = look_at(eye, CAMERA_TARGET)
-            if jitter:
-                j = u[s, 6 * k:6 * k + 6]
-                eye = eye + 0.02 * (2.0 * j[:3] - 1.0)
-                ang = np.radians(3.0) * (2.0 * j[3:] - 1.0)
-                R = _rot("x", ang[0]) @ _rot("y", ang[1]) @ _rot("z", ang[2]) @ R
-            views.append(view_matrix(R, eye))
-            owner.append(s)
-    return np.asarray(views).reshape(-1, 3, 4), np.asarray(owner, np.int32)
+    n_cams = np.asarray(n_cams, dtype=np.int64)
+    K = len(CAMERA_RIG)
+    u = uniform(seed, STREAM_CAMERA, ids, 6 * K).reshape(len(ids), K, 6)
+    az = np.radians([a for a, _ in CAMERA_RIG])
+    el = np.radians([e for _, e in CAMERA_RIG])
+    eye0 = CAMERA_TARGET + CAMERA_DIST * np.stack([np.cos(el) * np.cos(az), np.cos(el) * np.sin(az), np.sin(el)], -1)
+    R0 = look_at(eye0, np.broadcast_to(CAMERA_TARGET, eye0.shape))             # [K, 3, 3]
+    sel = np.arange(K)[None, :] < n_cams[:, None]                            # [S, K]
+    s_idx, k_idx = np.nonzero(sel)
+    j = u[s_idx, k_idx]                                                       # [C, 6]
+    eye = eye0[k_idx]
+    R = R0[k_idx]
+    if jitter:
+        eye = eye + 0.02 * (2.0 * j[:, :3] - 1.0)
+        ang = np.radians(3.0) * (2.0 * j[:, 3:] - 1.0)
+        R = _rot("x", ang[:, 0]) @ _rot("y", ang[:, 1]) @ _rot("z", ang[:, 2]) @ R
+    views = view_matrix(R, eye)
+    return views.reshape(-1, 3, 4), s_idx.astype(np.int32)
 
 
 def _lights(seed: int, ids: np.ndarray):
@@ -554,8 +566,7 @@ def hand_batch(seed: int, sample_ids, res: int = 200, n_cams: int = 3, meshes=No
     cams = np.full(B, n_cams) if cams_per_sample is None else np.asarray(cams_per_sample)
     res_s = np.full(B, res) if res_per_sample is None else np.asarray(res_per_sample)
     views, owner = _rig_views(seed, ids, cams)
-    intr = np.stack([perspective_intrinsics(res_s[s], res_s[s], FOVY_DEG) for s in owner]) if len(owner) else np.zeros((0, 6))
-    wh = np.stack([[res_s[s], res_s[s]] for s in owner]).astype(np.int32) if len(owner) else np.zeros((0, 2), np.int32)
+    intr, wh = _square_intrinsics(res_s[owner], FOVY_DEG)
     light, meta = _lights(seed, ids)
     ev, ambient, background = _post(seed, ids)
     return Batch(
@@ -629,8 +640,7 @@ def uneven_batch(seed: int, sample_ids, meshes=None) -> Batch:
         mbase[len(mbase) - n:len(mbase) - n] = [0, 1]
         counts.append(n + 2)
     views, owner = _rig_views(seed, ids, cams)
-    intr = np.stack([perspective_intrinsics(res[s], res[s], FOVY_DEG) for s in owner])
-    wh = np.stack([[res[s], res[s]] for s in owner]).astype(np.int32)
+    intr, wh = _square_intrinsics(res[owner], FOVY_DEG)
     light, meta = _lights(seed, ids)
     ev, ambient, background = _post(seed, ids)
     return Batch(

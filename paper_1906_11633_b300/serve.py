@@ -1,0 +1,276 @@
+"""Continuous-batching render service (the in-process analogue of the paper's render service, Sec. 4.1).
+
+Requests (a few samples of the resident scene at some resolution and camera
+count, each with fresh randomization parameters) arrive on any thread.  A
+scheduler thread wakes every `tick_ms`, takes the requests that have arrived,
+and -- while an in-flight slot is free and the device-memory budget allows --
+packs them into one batch and launches it on one of several CUDA streams, so
+a batch admitted while earlier ones are still rendering overlaps with them on
+the GPU.  One completion thread per stream waits for that stream's batches in
+order and stamps each request with the time its outputs became ready.  The
+meshes stay resident for the life of the server (SSMS, Sec. 3).
+
+A request's result does not depend on what it was batched with: the renderer
+computes every pixel from its own sample's inputs only.
+
+The device work sits behind a small backend interface (`memory_budget`,
+`bytes_needed`, `launch`, `wait`, `release`), so the scheduling logic is
+testable without a GPU.
+"""
+
+from __future__ import annotations
+
+import collections
+import itertools
+import threading
+import time
+from dataclasses import dataclass, field
+from typing import Any, Dict, List, Optional
+
+import numpy as np
+
+
+@dataclass
+class ServeRequest:
+    rid: int
+    batch: Any                      # scenegen.Batch of this request's samples
+    arrival: float = 0.0            # perf_counter() at submission
+    done: float = 0.0               # perf_counter() when the outputs were ready
+    result: Optional[Dict[str, Any]] = None
+    batch_id: int = -1
+    event: threading.Event = field(default_factory=threading.Event)
+
+    @property
+    def latency_ms(self) -> float:
+        return 1e3 * (self.done - self.arrival)
+
+
+@dataclass
+class InFlight:
+    batch_id: int
+    requests: List[ServeRequest]
+    handle: Any
+    nbytes: int
+    stream_index: int
+
+
+class Server:
+    """Scheduler + completion threads around a backend."""
+
+    def __init__(self, backend, n_streams: int = 2, max_inflight: int = 4, tick_ms: float = 2.0,
+                 max_batch_samples: int = 1024, memory_budget: Optional[int] = None):
+        self.backend = backend
+        self.n_streams = n_streams
+        self.max_inflight = max_inflight
+        self.tick = tick_ms / 1e3
+        self.max_batch_samples = max_batch_samples
+        self.budget = memory_budget if memory_budget is not None else backend.memory_budget()
+        self.pending: collections.deque = collections.deque()
+        self.lock = threading.Condition()
+        self.inflight: Dict[int, InFlight] = {}
+        self.inflight_bytes = 0
+        self.per_stream: List[collections.deque] = [collections.deque() for _ in range(n_streams)]
+        self.stream_cv = [threading.Condition() for _ in range(n_streams)]
+        self.completed: List[ServeRequest] = []
+        self.max_concurrent = 0
+        self.batches_launched = 0
+        self.rejected_for_memory = 0
+        self._ids = itertools.count()
+        self._next_stream = 0
+        self._stop = False
+        self._threads = [threading.Thread(target=self._schedule, daemon=True)]
+        self._threads += [threading.Thread(target=self._complete, args=(k,), daemon=True) for k in range(n_streams)]
+        for t in self._threads:
+            t.start()
+
+    # -- client side ------------------------------------------------------------
+    def submit(self, req: ServeRequest) -> ServeRequest:
+        req.arrival = time.perf_counter()
+        with self.lock:
+            self.pending.append(req)
+        return req
+
+    def close(self, timeout: float = 60.0) -> None:
+        deadline = time.perf_counter() + timeout
+        while True:
+            with self.lock:
+                idle = not self.pending and not self.inflight
+            if idle or time.perf_counter() > deadline:
+                break
+            time.sleep(self.tick)
+        self._stop = True
+        for cv in self.stream_cv:
+            with cv:
+                cv.notify_all()
+        for t in self._threads:
+            t.join(timeout=5.0)
+
+    # -- scheduler ----------------------------------------------------------------
+    def _schedule(self) -> None:
+        while not self._stop:
+            t0 = time.perf_counter()
+            self._admit()
+            dt = self.tick - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+
+    def _admit(self) -> None:
+        while True:
+            with self.lock:
+                if not self.pending or len(self.inflight) >= self.max_inflight:
+                    return
+                take, n = [], 0
+                for req in self.pending:
+                    if take and n + req.batch.n_samples > self.max_batch_samples:
+                        break
+                    take.append(req)
+                    n += req.batch.n_samples
+                need = self.backend.bytes_needed([r.batch for r in take])
+                while len(take) > 1 and self.inflight_bytes + need > self.budget:
+                    take.pop()                       # admit a smaller prefix that fits
+                    need = self.backend.bytes_needed([r.batch for r in take])
+                if self.inflight_bytes + need > self.budget:
+                    self.rejected_for_memory += 1
+                    return                           # wait for an in-flight batch to free memory
+                for _ in take:
+                    self.pending.popleft()
+                bid = next(self._ids)
+                k = self._next_stream
+                self._next_stream = (k + 1) % self.n_streams
+                self.inflight_bytes += need
+            handle = self.backend.launch([r.batch for r in take], k)
+            fl = InFlight(bid, take, handle, need, k)
+            for r in take:
+                r.batch_id = bid
+            with self.lock:
+                self.inflight[bid] = fl
+                self.max_concurrent = max(self.max_concurrent, len(self.inflight))
+                self.batches_launched += 1
+            with self.stream_cv[k]:
+                self.per_stream[k].append(fl)
+                self.stream_cv[k].notify()
+
+    # -- completion ----------------------------------------------------------------
+    def _complete(self, k: int) -> None:
+        q, cv = self.per_stream[k], self.stream_cv[k]
+        while True:
+            with cv:
+                while not q and not self._stop:
+                    cv.wait(timeout=0.05)
+                if not q:
+                    return
+                fl = q.popleft()
+            results = self.backend.wait(fl.handle)
+            now = time.perf_counter()
+            for r, res in zip(fl.requests, results):
+                r.result = res
+                r.done = now
+            self.backend.release(fl.handle)
+            with self.lock:
+                self.inflight.pop(fl.batch_id, None)
+                self.inflight_bytes -= fl.nbytes
+                self.completed.extend(fl.requests)
+            for r in fl.requests:      # signal only once the bookkeeping is visible to stats()
+                r.event.set()
+
+    # -- report ----------------------------------------------------------------------
+    def stats(self, wall_s: float) -> Dict[str, float]:
+        lat = np.array([r.latency_ms for r in self.completed]) if self.completed else np.zeros(1)
+        samples = sum(r.batch.n_samples for r in self.completed)
+        return {"requests": len(self.completed), "samples": samples, "samples_per_s": samples / wall_s,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "max_ms": float(lat.max()), "batches": self.batches_launched,
+                "max_concurrent_batches": self.max_concurrent, "memory_waits": self.rejected_for_memory}
+
+
+class GpuBackend:
+    """Packs requests into one batch and renders it on a per-slot CUDA stream.
+
+    Each in-flight batch gets its own workspace and outputs, so batches on
+    different streams never share scratch memory.  `readback` copies the
+    channels to pinned host memory before the request counts as done.
+    """
+
+    def __init__(self, meshes, device: int = 0, n_streams: int = 2, cfg=None, readback: bool = False,
+                 reserve_bytes: int = 8 << 30):
+        import torch
+
+        from . import lib as L
+        from .render import Renderer, config
+        self.torch, self.L = torch, L
+        self.r = Renderer(meshes, device=device)
+        self.cfg = cfg or config()
+        self.streams = [torch.cuda.Stream(device=self.r.device) for _ in range(n_streams)]
+        self.readback = readback
+        self.reserve = reserve_bytes
+        # workspace bytes ~ a + b * (triangles of the largest sample), fitted from two library queries
+        w = [L.orrb_workspace_size(self.r.ctx, L.orrb_batch_shape(1, 1, t, 64, 3, 512, 512, 1 << 18), self.cfg)
+             for t in (10000, 20000)]
+        self.ws_b = (w[1] - w[0]) / 10000.0
+        self.ws_a = w[0] - 10000 * self.ws_b
+
+    def memory_budget(self) -> int:
+        free, _ = self.torch.cuda.mem_get_info(self.r.device)
+        return max(0, free - self.reserve)
+
+    def _shape(self, batches):
+        from .render import batch_shape
+        from .scenegen import concat_batches
+        packed = concat_batches(batches)
+        return packed, batch_shape(packed)
+
+    def bytes_needed(self, batches) -> int:
+        px = sum(b.total_pixels for b in batches)
+        tris = max(int(b.tris_per_sample().max()) for b in batches)
+        # outputs (14 B per pixel) + workspace + parameters
+        return int(px * 14 + self.ws_a + self.ws_b * tris + sum(b.n_samples for b in batches) * 4096)
+
+    def launch(self, batches, k: int):
+        torch = self.torch
+        from .render import DeviceBatch, host_arrays
+        packed, shape = self._shape(batches)
+        s = self.streams[k]
+        with torch.cuda.stream(s):
+            arrs = host_arrays(packed)
+            t = {n: torch.from_numpy(a).pin_memory().to(self.r.device, non_blocking=True) for n, a in arrs.items()}
+            db = DeviceBatch(shape, t)
+            n_ws = self.L.orrb_workspace_size(self.r.ctx, shape, self.cfg)
+            ws = torch.empty(n_ws, dtype=torch.uint8, device=self.r.device)
+            out = self.r.render(db, cfg=self.cfg, stream=s, workspace=ws)
+            host = None
+            if self.readback:
+                host = {k2: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k2, v in out.items()}
+                for k2 in out:
+                    host[k2].copy_(out[k2], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(s)
+        return {"db": db, "ws": ws, "out": out, "host": host, "event": ev, "batches": batches, "stream": s}
+
+    def wait(self, h):
+        h["event"].synchronize()
+        res, p0 = [], 0
+        src = h["host"] if h["host"] is not None else h["out"]
+        for b in h["batches"]:
+            n = b.total_pixels
+            res.append({k: v[p0:p0 + n] for k, v in src.items()})
+            p0 += n
+        return res
+
+    def release(self, h):
+        # tensors return to torch's caching allocator once the stream's work is done
+        h["ws"].record_stream(h["stream"])
+        h.clear()
+
+
+def run_poisson(server: Server, requests, batches, duration_s: float, warmup_s: float = 0.0):
+    """Submit `batches[i]` at arrival time `requests[i].arrival_s`; returns (submitted ServeRequests, wall seconds)."""
+    t0 = time.perf_counter()
+    subs = []
+    for req, b in zip(requests, batches):
+        delay = t0 + req.arrival_s - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        subs.append(server.submit(ServeRequest(req.rid, b)))
+    for s in subs:
+        s.event.wait(timeout=60.0)
+    return subs, time.perf_counter() - t0

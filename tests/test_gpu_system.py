@@ -1,0 +1,95 @@
+"""Batched launch under a CUDA graph, the autotuner, and the continuous-batching server (GPU).
+
+- a captured graph replays to the same channels as a direct render, and again after new
+  batch contents of the same shapes are copied in;
+- the uneven batch (mixed triangle counts and resolutions) renders in one persistent launch
+  and matches per-scene plain launches bit for bit;
+- the autotuner returns a configuration whose output equals the default's and caches it;
+- served requests: each result equals the same request rendered alone, and batches overlap.
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1906_11633_b300 import lib as L
+from paper_1906_11633_b300 import scenegen as sg
+from paper_1906_11633_b300.render import GraphRender, Renderer, config, to_numpy
+
+
+@pytest.fixture(scope="module")
+def renderer():
+    return Renderer(sg.hand_meshes())
+
+
+def _equal(a, b):
+    for k in a:
+        np.testing.assert_array_equal(to_numpy({k: a[k]})[k], to_numpy({k: b[k]})[k], err_msg=k)
+
+
+def test_graph_replay_matches_direct_render_and_takes_new_contents(renderer):
+    b1 = sg.hand_batch(1, np.arange(8), res=128)
+    b2 = sg.hand_batch(2, np.arange(8), res=128)
+    g = GraphRender(renderer, renderer.upload(b1))
+    out = g.replay()
+    torch.cuda.synchronize()
+    _equal(out, renderer.render(renderer.upload(b1)))
+    g.update(b2)
+    out = g.replay()
+    torch.cuda.synchronize()
+    _equal(out, renderer.render(renderer.upload(b2)))
+
+
+def test_uneven_batch_in_one_launch_matches_plain_launches(renderer):
+    b = sg.uneven_batch(3, np.arange(48))
+    db = renderer.upload(b)
+    g = GraphRender(renderer, db)
+    fused = g.replay()
+    torch.cuda.synchronize()
+    plain = renderer.render(db, cfg=config(mode=L.ORRB_MODE_PLAIN))
+    torch.cuda.synchronize()
+    assert renderer.status() == 0
+    _equal(fused, plain)
+
+
+def test_autotuner_result_is_valid_and_cached(renderer, tmp_path):
+    from paper_1906_11633_b300.tune import tune
+    b = sg.hand_batch(4, np.arange(16), res=200)
+    db = renderer.upload(b)
+    cands = [(256, 1, 512), (64, 2, 512), (32, 4, 256), (512, 64, 512)]   # the last cannot fit
+    path = str(tmp_path / "tune.json")
+    cfg, timings = tune(renderer, db, candidates=cands, reps=2, cache_path=path)
+    assert (cfg.tile_w, cfg.tile_h, cfg.threads) in cands[:3]
+    assert "512x64x512" not in timings and len(timings) == 3
+    cfg2, _ = tune(renderer, db, candidates=cands, reps=2, cache_path=path)
+    assert (cfg2.tile_w, cfg2.tile_h, cfg2.threads) == (cfg.tile_w, cfg.tile_h, cfg.threads)
+    _equal(renderer.render(db, cfg=cfg), renderer.render(db))
+
+
+def test_served_requests_equal_their_solo_render():
+    from paper_1906_11633_b300.serve import GpuBackend, Server, ServeRequest
+    meshes = sg.hand_meshes()
+    be = GpuBackend(meshes, n_streams=2)
+    srv = Server(be, n_streams=2, max_inflight=4, tick_ms=2.0)
+    rng = np.random.default_rng(0)
+    batches = []
+    first = 0
+    for i in range(40):
+        n = int(rng.integers(1, 7))
+        batches.append(sg.hand_batch(7, np.arange(first, first + n), res=int(rng.choice([64, 128])),
+                                     n_cams=int(rng.integers(1, 4)), meshes=meshes))
+        first += n
+    reqs = [srv.submit(ServeRequest(i, b)) for i, b in enumerate(batches)]
+    for r in reqs:
+        assert r.event.wait(60.0)
+    st = srv.stats(1.0)
+    srv.close()
+    assert st["requests"] == 40
+    assert st["batches"] < 40                       # requests were batched together
+    solo = Renderer(meshes)
+    for r in reqs[::7]:
+        alone = solo.render(solo.upload(r.batch))
+        torch.cuda.synchronize()
+        _equal(r.result, alone)

@@ -1,0 +1,86 @@
+"""Scheduling logic of the continuous-batching server with a fake backend (no GPU).
+
+Checks: every request completes exactly once, in-flight batches never exceed
+the slot count or the memory budget, batches overlap (more than one in flight)
+when requests keep arriving, and a request larger than the budget is never
+admitted alongside others that would overflow it.
+"""
+
+import threading
+import time
+
+from paper_1906_11633_b300 import scenegen as sg
+from paper_1906_11633_b300.serve import Server, ServeRequest
+
+
+class FakeBackend:
+    def __init__(self, gpu_ms=4.0, budget=10_000_000):
+        self.gpu_ms = gpu_ms
+        self.budget = budget
+        self.lock = threading.Lock()
+        self.active_bytes = 0
+        self.peak_bytes = 0
+        self.active = 0
+        self.peak_active = 0
+
+    def memory_budget(self):
+        return self.budget
+
+    def bytes_needed(self, batches):
+        return sum(b.total_pixels for b in batches) * 14
+
+    def launch(self, batches, k):
+        nb = self.bytes_needed(batches)
+        with self.lock:
+            self.active_bytes += nb
+            self.active += 1
+            self.peak_bytes = max(self.peak_bytes, self.active_bytes)
+            self.peak_active = max(self.peak_active, self.active)
+        return {"t_end": time.perf_counter() + self.gpu_ms / 1e3, "batches": batches, "nb": nb}
+
+    def wait(self, h):
+        d = h["t_end"] - time.perf_counter()
+        if d > 0:
+            time.sleep(d)
+        return [{"n": b.n_samples} for b in h["batches"]]
+
+    def release(self, h):
+        with self.lock:
+            self.active_bytes -= h["nb"]
+            self.active -= 1
+
+
+def _req_batch(i, n, res):
+    return sg.hand_batch(0, range(1000 * i, 1000 * i + n), res=res, n_cams=1)
+
+
+def test_every_request_completes_within_budget_and_batches_overlap():
+    be = FakeBackend(gpu_ms=6.0, budget=64 * 64 * 14 * 40)
+    srv = Server(be, n_streams=2, max_inflight=3, tick_ms=1.0)
+    batches = [_req_batch(i, 1 + i % 4, 64) for i in range(40)]
+    reqs = []
+    for i in range(40):
+        reqs.append(srv.submit(ServeRequest(i, batches[i])))
+        time.sleep(0.0015)
+    for r in reqs:
+        assert r.event.wait(10.0)
+    st = srv.stats(1.0)
+    srv.close()
+    assert st["requests"] == 40 and len({r.rid for r in srv.completed}) == 40
+    assert all(r.result["n"] == r.batch.n_samples for r in reqs)
+    assert be.peak_bytes <= be.budget
+    assert 2 <= be.peak_active <= 3
+    assert st["batches"] < 40              # requests were batched together
+    assert all(r.latency_ms > 0 for r in reqs)
+
+
+def test_memory_budget_serialises_large_batches():
+    one = 128 * 128 * 14 * 8
+    be = FakeBackend(gpu_ms=3.0, budget=one)                # room for one 8-sample 128px request at a time
+    srv = Server(be, n_streams=2, max_inflight=4, tick_ms=1.0)
+    batches = [_req_batch(i, 8, 128) for i in range(5)]
+    reqs = [srv.submit(ServeRequest(i, b)) for i, b in enumerate(batches)]
+    for r in reqs:
+        assert r.event.wait(10.0)
+    srv.close()
+    assert be.peak_bytes <= one and be.peak_active == 1
