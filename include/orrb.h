@@ -80,6 +80,7 @@ typedef int32_t orrb_status;
 #define ORRB_DEV_BAD_MATERIAL 0x8u   /* material slot >= 32 (clamped to 31) */
 #define ORRB_DEV_BAD_LIGHTS 0x10u    /* light count outside [0, 4] (clamped) */
 #define ORRB_DEV_DROPPED 0x20u       /* a triangle left the +-2^20 px guard band and was dropped */
+#define ORRB_DEV_TIMEOUT 0x40u       /* a bounded wait between CTAs gave up (outputs may be incomplete) */
 
 typedef struct orrb_ctx orrb_ctx;
 
@@ -201,7 +202,7 @@ orrb_status orrb_render_batch(orrb_ctx* ctx, const orrb_batch_shape* shape, cons
  * per-CTA scratch lives instead in one static device array of
  * ORRB_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
  * the process exits.  Fewer CTAs run when a sample's scratch slot is large;
- * a shape whose slot (about 224 bytes per triangle of the largest sample)
+ * a shape whose slot (about 740 bytes per triangle of the largest sample)
  * does not fit even once is rejected with ORRB_ERR_WORKSPACE.  The entry
  * point calls no cudaMalloc, cudaFree or allocating library routine.
  *   device_status: optional device pointer to one uint32 that receives the

@@ -430,16 +430,18 @@ orrb_status orrb_render_batch(orrb_ctx* ctx, const orrb_batch_shape* shape, cons
   char* ws = static_cast<char*>(workspace);
   p.status = reinterpret_cast<uint32_t*>(ws);
   p.work_counter = reinterpret_cast<uint32_t*>(ws + 4);
+  p.images_done = reinterpret_cast<uint32_t*>(ws + 8);
   p.scratch = ws + 256;
   p.slot_bytes = P.slot_bytes;
   p.n_slots = P.n_slots;
   p.plain_sample = -1;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemsetAsync(ws, 0, 8, s);
+  cudaError_t e = cudaMemsetAsync(ws, 0, 16, s);
   if (e != cudaSuccess) return fail(ctx, ORRB_ERR_CUDA, "workspace clear: %s", cudaGetErrorString(e));
   if (shape->n_cams == 0 || shape->n_samples == 0) return ORRB_OK;
   char err[256] = {0};
   int n_ctas = c.mode == ORRB_MODE_FUSED ? std::min(P.n_slots, std::max(shape->n_cams, 1)) : 0;
+  p.n_slots = n_ctas;
   if (launch_render(p, c.mode, c.threads, n_ctas, std::max(shape->max_cams_per_sample, 1), stream, err, sizeof(err)))
     return fail(ctx, ORRB_ERR_CUDA, "%s", err);
   return ORRB_OK;
@@ -495,18 +497,19 @@ orrb_status orrb_render_batch_noalloc(orrb_ctx* ctx, const orrb_batch_shape* sha
   char* ws = static_cast<char*>(scratch);
   p.status = device_status ? device_status : reinterpret_cast<uint32_t*>(ws);
   p.work_counter = reinterpret_cast<uint32_t*>(ws + 4);
+  p.images_done = reinterpret_cast<uint32_t*>(ws + 8);
   p.scratch = ws + 256;
   p.slot_bytes = P.slot_bytes;
-  p.n_slots = n_slots;
+  p.n_slots = std::min(n_slots, std::max(shape->n_cams, 1));  // one slot per launched CTA
   p.plain_sample = -1;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // the array keeps the previous call's contents: the status word and the work counter restart at zero
-  cudaError_t e = cudaMemsetAsync(ws, 0, 8, s);
+  // the array keeps the previous call's contents: the status word and the queue counters restart at zero
+  cudaError_t e = cudaMemsetAsync(ws, 0, 16, s);
   if (e == cudaSuccess && device_status) e = cudaMemsetAsync(device_status, 0, 4, s);
   if (e != cudaSuccess) return fail(ctx, ORRB_ERR_CUDA, "scratch clear: %s", cudaGetErrorString(e));
   if (shape->n_cams == 0 || shape->n_samples == 0) return ORRB_OK;
   char err[256] = {0};
-  if (launch_render(p, ORRB_MODE_FUSED, c.threads, std::min(n_slots, std::max(shape->n_cams, 1)), 1, stream, err,
+  if (launch_render(p, ORRB_MODE_FUSED, c.threads, p.n_slots, 1, stream, err,
                     sizeof(err)))
     return fail(ctx, ORRB_ERR_CUDA, "%s", err);
   return ORRB_OK;

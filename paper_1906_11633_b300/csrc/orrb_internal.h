@@ -40,17 +40,13 @@ struct ArenaLayout {      // byte offsets inside the arena, all 256-aligned
   int32_t n_meshes, n_meshlets, n_verts, n_tris;
 };
 
-// ---- one visible (sub)triangle, 80 B ---------------------------------------
+// ---- one visible (sub)triangle, 96 B ---------------------------------------
 // q0 = X0, Y0, X1, Y1 (8.8 fixed point)     q1 = X2, Y2, iw0, iw1 (float bits)
-// q2 = iw2, mat | seg << 16, n0x, n0y       q3 = n0z, n1x, n1y, n1z
-// q4 = n2x, n2y, n2z, unused
+// q2 = iw2, float(area), pixel box x0 | x1 << 16, y0 | y1 << 16 | top-left << 28 | small << 31
+// q3 = mat | seg << 16 | flat << 24, n0 xyz  q4 = n1 xyz, n2x   q5 = n2y, n2z, -, -
 // iw = 1/w (perspective) or view depth (orthographic).
 struct alignas(16) Record {
-  int32_t q0[4];
-  int32_t q1[4];
-  int32_t q2[4];
-  float q3[4];
-  float q4[4];
+  int32_t q[24];
 };
 
 // ---- kernel parameters -----------------------------------------------------
@@ -96,6 +92,7 @@ struct Params {
   // workspace
   uint32_t* status;
   uint32_t* work_counter;
+  uint32_t* images_done;
   char* scratch;
   size_t slot_bytes;
   int32_t n_slots;

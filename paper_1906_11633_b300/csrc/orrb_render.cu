@@ -67,6 +67,7 @@ struct CtaShared {
   ImageInfo im;
   float mat[kMaxMaterials][5];
   int n_vis, n_big, next_tile, img;
+  int help_slot, help_cam;
   int scan_tmp[33];
 };
 
@@ -86,7 +87,7 @@ struct WarpTri {  // a binned triangle staged for the warp's fragment expansion 
   float fA;
   unsigned key;
   int tl;
-  int px0, py0, bw, pad;
+  int px0, py0, bw, small;
 };
 
 struct Scratch {
@@ -96,7 +97,10 @@ struct Scratch {
   uint32_t* bins;
   uint32_t* big;
   uint32_t* tile_off;
-  int* header;  // [0] n_vis, [1] n_big
+  // header: [0..1] claim word (camera + 1) << 32 | next tile, 0 while no raster phase is
+  // open; [2] n_vis; [3] n_big; [4] tiles finished; [5] tiles of the open image
+  int* header;
+  __device__ unsigned long long* claim() const { return reinterpret_cast<unsigned long long*>(header); }
 };
 
 struct SmemLayout {
@@ -308,9 +312,18 @@ __device__ __forceinline__ void project(const ImageInfo& im, float x, float y, f
   Y = ok ? __float2int_rn(__fmul_rn(ys, 256.0f)) : 0;
 }
 
+__device__ __forceinline__ int top_left(int ax, int ay, int bx, int by) {
+  int dx = bx - ax, dy = by - ay;
+  return (dy == 0 && dx < 0) || dy > 0;
+}
+
 // Set up a snapped triangle: cull (area <= 0), clamp its pixel box to the image.
-// Returns false if culled or entirely off-screen.
-__device__ __forceinline__ bool setup_box(const ImageInfo& im, const int X[3], const int Y[3], uint2& box) {
+// Returns false if culled or entirely off-screen.  box.x = x0 | x1 << 16; box.y =
+// y0 | y1 << 16 | top-left flags of edges 0..2 << 28 | small << 31, where "small"
+// means a vertex box under 128 px, for which every edge function and every term of
+// it fits in 32 bits relative to vertex 0.
+__device__ __forceinline__ bool setup_box(const ImageInfo& im, const int X[3], const int Y[3], uint2& box,
+                                          float& fA) {
   long long A = (long long)(X[2] - X[0]) * (Y[1] - Y[0]) - (long long)(Y[2] - Y[0]) * (X[1] - X[0]);
   if (A <= 0) return false;
   int xmin = min(X[0], min(X[1], X[2])), xmax = max(X[0], max(X[1], X[2]));
@@ -319,25 +332,30 @@ __device__ __forceinline__ bool setup_box(const ImageInfo& im, const int X[3], c
   int x0 = max(0, -((128 - xmin) >> 8)), x1 = min(im.W - 1, (xmax - 128) >> 8);
   int y0 = max(0, -((128 - ymin) >> 8)), y1 = min(im.H - 1, (ymax - 128) >> 8);
   if (x0 > x1 || y0 > y1) return false;
+  const unsigned tl = top_left(X[1], Y[1], X[2], Y[2]) | (top_left(X[2], Y[2], X[0], Y[0]) << 1) |
+                      (top_left(X[0], Y[0], X[1], Y[1]) << 2);
+  const unsigned small = (xmax - xmin) < 32768 && (ymax - ymin) < 32768;
   box.x = unsigned(x0) | (unsigned(x1) << 16);
-  box.y = unsigned(y0) | (unsigned(y1) << 16);
+  box.y = unsigned(y0) | (unsigned(y1) << 16) | (tl << 28) | (small << 31);
+  fA = __ll2float_rn(A);
   return true;
 }
 
 __device__ __forceinline__ void write_record(Record* r, const int X[3], const int Y[3], const float iw[3],
-                                             const float n[3][3], int mat, int seg) {
+                                             const float n[3][3], int mat, int seg, uint2 box, float fA) {
   int4* q = reinterpret_cast<int4*>(r);
   q[0] = make_int4(X[0], Y[0], X[1], Y[1]);
   q[1] = make_int4(X[2], Y[2], __float_as_int(iw[0]), __float_as_int(iw[1]));
+  q[2] = make_int4(__float_as_int(iw[2]), __float_as_int(fA), int(box.x), int(box.y));
   // bit 24: the three vertex normals are bitwise equal (a flat face), so the interpolated
   // normal is n0 up to rounding and the resolve skips the interpolation
   const int flat = n[0][0] == n[1][0] && n[0][1] == n[1][1] && n[0][2] == n[1][2] && n[0][0] == n[2][0] &&
                    n[0][1] == n[2][1] && n[0][2] == n[2][2];
-  q[2] = make_int4(__float_as_int(iw[2]), mat | (seg << 16) | (flat << 24), __float_as_int(n[0][0]),
-                   __float_as_int(n[0][1]));
+  q[3] = make_int4(mat | (seg << 16) | (flat << 24), __float_as_int(n[0][0]), __float_as_int(n[0][1]),
+                   __float_as_int(n[0][2]));
   float4* f = reinterpret_cast<float4*>(r);
-  f[3] = make_float4(n[0][2], n[1][0], n[1][1], n[1][2]);
-  f[4] = make_float4(n[2][0], n[2][1], n[2][2], 0.0f);
+  f[4] = make_float4(n[1][0], n[1][1], n[1][2], n[2][0]);
+  f[5] = make_float4(n[2][1], n[2][2], 0.0f, 0.0f);
 }
 
 struct CutVert {
@@ -361,9 +379,9 @@ __device__ __noinline__ void cut_vertex(const ImageInfo& im, const float* pin, c
 // Near-plane clip of triangle (a, b, c) of the staged cluster; emits up to two
 // sub-triangles.  Vertex order follows Sutherland-Hodgman: for each edge
 // (v_k, v_k+1) emit v_k if inside, then the cut if the edge crosses.
-__device__ __noinline__ int clip_triangle(const Params& p, const ImageInfo& im, const WarpG* wg, const int vi[3],
-                                          int prim, int mat, int seg, const Scratch& sc, unsigned* keys,
-                                          uint2* boxes, unsigned* dropped) {
+__device__ __noinline__ int clip_triangle(int t_max, Record* rec, const ImageInfo& im, const WarpG* wg,
+                                          const int vi[3], int prim, int mat, int seg, unsigned* keys, uint2* boxes,
+                                          unsigned* dropped) {
   CutVert poly[4];
   int np = 0;
   for (int k = 0; k < 3; k++) {
@@ -392,12 +410,13 @@ __device__ __noinline__ int clip_triangle(const Params& p, const ImageInfo& im, 
     }
     int X[3] = {q[0]->X, q[1]->X, q[2]->X}, Y[3] = {q[0]->Y, q[1]->Y, q[2]->Y};
     uint2 box;
-    if (!setup_box(im, X, Y, box)) continue;
+    float fA;
+    if (!setup_box(im, X, Y, box, fA)) continue;
     float iw[3] = {q[0]->iw, q[1]->iw, q[2]->iw};
     float n[3][3];
     for (int k = 0; k < 3; k++)
       for (int d = 0; d < 3; d++) n[k][d] = q[k]->n[d];
-    write_record(sc.rec + (size_t)sub * p.t_max + prim, X, Y, iw, n, mat, seg);
+    write_record(rec + (size_t)sub * t_max + prim, X, Y, iw, n, mat, seg, box, fA);
     keys[emitted] = 2u * prim + sub;
     boxes[emitted] = box;
     emitted++;
@@ -478,12 +497,13 @@ __device__ void geometry_phase(const Params& p, CtaShared& sh, const int* mprefi
           if (f0 & f1 & f2 & 2) {
             int X[3] = {wg->X[vi[0]], wg->X[vi[1]], wg->X[vi[2]]};
             int Y[3] = {wg->Y[vi[0]], wg->Y[vi[1]], wg->Y[vi[2]]};
-            if (setup_box(im, X, Y, boxes[0])) {
+            float fA;
+            if (setup_box(im, X, Y, boxes[0], fA)) {
               float iw[3] = {wg->iw[vi[0]], wg->iw[vi[1]], wg->iw[vi[2]]};
               float n[3][3];
               for (int k = 0; k < 3; k++)
                 for (int d = 0; d < 3; d++) n[k][d] = wg->nv[vi[k] * 3 + d];
-              write_record(sc.rec + prim, X, Y, iw, n, mat, seg);
+              write_record(sc.rec + prim, X, Y, iw, n, mat, seg, boxes[0], fA);
               keys[0] = 2u * prim;
               cnt = 1;
             }
@@ -491,7 +511,7 @@ __device__ void geometry_phase(const Params& p, CtaShared& sh, const int* mprefi
             dropped = 1;
           }
         } else if ((f0 | f1 | f2) & 1) {
-          cnt = clip_triangle(p, im, wg, vi, prim, mat, seg, sc, keys, boxes, &dropped);
+          cnt = clip_triangle(p.t_max, sc.rec, im, wg, vi, prim, mat, seg, keys, boxes, &dropped);
         }
       }
       // warp prefix scan of the per-lane counts, one atomic per warp
@@ -522,7 +542,7 @@ __device__ void geometry_phase(const Params& p, CtaShared& sh, const int* mprefi
 __device__ __forceinline__ unsigned udiv16(unsigned x, unsigned m) { return m ? __umulhi(x, m) : x; }
 
 __device__ __forceinline__ bool binned_span(uint2 box, const ImageInfo& im, int& tx0, int& tx1, int& ty0, int& ty1) {
-  const unsigned x0 = box.x & 0xffff, x1 = box.x >> 16, y0 = box.y & 0xffff, y1 = box.y >> 16;
+  const unsigned x0 = box.x & 0xffff, x1 = box.x >> 16, y0 = box.y & 0xffff, y1 = (box.y >> 16) & 0xfff;
   tx0 = udiv16(x0, im.m_tw);
   tx1 = udiv16(x1, im.m_tw);
   ty0 = udiv16(y0, im.m_th);
@@ -577,10 +597,6 @@ __device__ void bin_phase(const Params& p, CtaShared& sh, int* counts, int* curs
 // ---------------------------------------------------------------------------
 // phase R: raster + shade one tile
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int top_left(int ax, int ay, int bx, int by) {
-  int dx = bx - ax, dy = by - ay;
-  return (dy == 0 && dx < 0) || dy > 0;
-}
 
 // Fragment test at pixel centre (cx, cy): returns the 64-bit key or kEmpty.
 __device__ __forceinline__ unsigned long long fragment(const int X[3], const int Y[3], const float iw[3], float fA,
@@ -610,15 +626,60 @@ __device__ __forceinline__ void load_tri(const Record* r, int X[3], int Y[3], fl
   iw[2] = __int_as_float(q2x);
 }
 
-__device__ __forceinline__ void tri_setup(const int X[3], const int Y[3], float& fA, int& tl) {
-  long long A = (long long)(X[2] - X[0]) * (Y[1] - Y[0]) - (long long)(Y[2] - Y[0]) * (X[1] - X[0]);
-  fA = __ll2float_rn(A);
-  tl = top_left(X[1], Y[1], X[2], Y[2]) | (top_left(X[2], Y[2], X[0], Y[0]) << 1) |
-       (top_left(X[0], Y[0], X[1], Y[1]) << 2);
+// Set-up fields stored in the record by the geometry phase.
+__device__ __forceinline__ void load_setup(const Record* r, float& fA, uint2& box) {
+  const int4 q2 = reinterpret_cast<const int4*>(r)[2];
+  fA = __int_as_float(q2.y);
+  box = make_uint2(unsigned(q2.z), unsigned(q2.w));
+}
+
+// 32-bit fragment test for a "small" triangle: coordinates relative to vertex 0 keep every
+// product below 2^30, so the integers equal the 64-bit ones bit for bit.
+__device__ __forceinline__ unsigned long long fragment32(const int Xr[3], const int Yr[3], const float iw[3], float fA,
+                                                         int tl, unsigned key, int ortho, int cxr, int cyr) {
+  const int w0 = (cxr - Xr[1]) * (Yr[2] - Yr[1]) - (cyr - Yr[1]) * (Xr[2] - Xr[1]);
+  const int w1 = (cxr - Xr[2]) * (Yr[0] - Yr[2]) - (cyr - Yr[2]) * (Xr[0] - Xr[2]);
+  const int w2 = (cxr - Xr[0]) * (Yr[1] - Yr[0]) - (cyr - Yr[0]) * (Xr[1] - Xr[0]);
+  if (!(w0 + (tl & 1) > 0 && w1 + ((tl >> 1) & 1) > 0 && w2 + ((tl >> 2) & 1) > 0)) return kEmpty;
+  const float f0 = __int2float_rn(w0), f1 = __int2float_rn(w1), f2 = __int2float_rn(w2);
+  const float s = __fadd_rn(__fadd_rn(__fmul_rn(f0, iw[0]), __fmul_rn(f1, iw[1])), __fmul_rn(f2, iw[2]));
+  const float depth = ortho ? __fdiv_rn(s, fA) : __fdiv_rn(fA, s);
+  return ((unsigned long long)__float_as_uint(depth) << 32) | key;
+}
+
+__device__ __forceinline__ float exp2f_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
 __device__ __forceinline__ const Record* rec_of(const Params& p, const Scratch& sc, unsigned key) {
   return sc.rec + (size_t)(key & 1u) * p.t_max + (key >> 1);
+}
+
+// ndh^alpha for ndh in [0, 1], alpha >= 1 (the Blinn-Phong lobe).
+// Near 1, where the lobe is not negligible, d = 1 - ndh < 1/8 is exact (Sterbenz) and
+// log2(1 - d) = -(d + d^2/2 + d^3/3 + ...) / ln 2 is summed to d^8/8 by Horner (the
+// next term is below 1.2e-8 of the sum), so alpha*log2(ndh) = -t carries a relative
+// error of ~1e-7 and ex2.approx adds 2^-22: the result's absolute error is at most
+// ln2 * 1e-7 * t * 2^-t + 2.4e-7 * 2^-t < 3e-7.  Below ndh = 7/8, __powf's absolute
+// error (lg2.approx: 2^-22.6 absolute near 1, 2^-22 relative elsewhere) stays under
+// 6.4e-7 because alpha * 0.875^alpha <= 2.8.
+__device__ __forceinline__ float lobe_pow(float ndh, float alpha) {
+  const float d = 1.0f - ndh;
+  if (d < 0.125f) {
+    float s = 0.125f;
+    s = fmaf(s, d, 1.0f / 7.0f);
+    s = fmaf(s, d, 1.0f / 6.0f);
+    s = fmaf(s, d, 0.2f);
+    s = fmaf(s, d, 0.25f);
+    s = fmaf(s, d, 1.0f / 3.0f);
+    s = fmaf(s, d, 0.5f);
+    s = fmaf(s, d, 1.0f);
+    const float log2x = -(d * s) * 1.4426950408889634f;   // log2(1 - d) = ln(1 - d) / ln 2
+    return exp2f_approx(alpha * log2x);
+  }
+  return ndh > 0.0f ? __powf(ndh, alpha) : 0.0f;
 }
 
 __device__ void shade(const CtaShared& sh, const float P[3], const float n[3], int mat, float rgb[3]) {
@@ -660,14 +721,7 @@ __device__ void shade(const CtaShared& sh, const float P[3], const float n[3], i
       if (h2 > 0.0f) {
         float rh = rsqrtf(h2);
         float ndh = fmaxf(0.0f, (n[0] * H0 + n[1] * H1 + n[2] * H2) * rh);
-        // ndh^alpha for ndh in [0, 1], alpha >= 1.  The MUFU form (__powf: lg2.approx with
-        // absolute error <= 2^-22.6 near 1, ex2.approx relative <= 2^-22) has relative error
-        // <= (alpha + 2.2) * 1.1e-7; it is used only where that, times the lobe's weight
-        // 2^EV * E * k_s, stays under 2e-5.  Otherwise exp2f(alpha * log2f(ndh)) with both
-        // calls accurate to a couple of ulp (~1e-7 * |alpha log2 ndh| relative).
-        const float w = im.scale * E * m[3];
-        if (w * (m[4] + 2.2f) <= 180.0f) spec = m[3] * __powf(ndh, m[4]);
-        else spec = ndh > 0.0f ? m[3] * exp2f(m[4] * log2f(ndh)) : 0.0f;
+        spec = m[3] * lobe_pow(ndh, m[4]);
       }
     }
     c0 += E * (m[0] * ndl + spec);
@@ -707,13 +761,6 @@ struct BoxWalk {
     px = px0 + (j - dy * bw);
     py = py0 + dy;
   }
-  __device__ __forceinline__ void advance(int px0, int bw) {
-    px += 32;
-    while (px >= px0 + bw) {
-      px -= bw;
-      py++;
-    }
-  }
 };
 
 // Phase R for one tile, by one warp, in warp-private shared memory.
@@ -735,16 +782,15 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
     const unsigned key = sc.big[b];
     int X[3], Y[3];
     float iw[3];
-    load_tri(rec_of(p, sc, key), X, Y, iw);
-    const int xmin = min(X[0], min(X[1], X[2])), xmax = max(X[0], max(X[1], X[2]));
-    const int ymin = min(Y[0], min(Y[1], Y[2])), ymax = max(Y[0], max(Y[1], Y[2]));
-    const int bx0 = max(x0, -((128 - xmin) >> 8)), bx1 = min(x0 + cw - 1, (xmax - 128) >> 8);
-    const int by0 = max(y0, -((128 - ymin) >> 8)), by1 = min(y0 + ch - 1, (ymax - 128) >> 8);
-    if (bx0 > bx1 || by0 > by1) continue;
+    const Record* rb = rec_of(p, sc, key);
     float fA;
-    int tl;
-    tri_setup(X, Y, fA, tl);
-    const int bw = bx1 - bx0 + 1;
+    uint2 box;
+    load_setup(rb, fA, box);
+    const int bx0 = max(x0, int(box.x & 0xffff)), bx1 = min(x0 + cw - 1, int(box.x >> 16));
+    const int by0 = max(y0, int(box.y & 0xffff)), by1 = min(y0 + ch - 1, int((box.y >> 16) & 0xfff));
+    if (bx0 > bx1 || by0 > by1) continue;
+    load_tri(rb, X, Y, iw);
+    const int tl = (box.y >> 28) & 7;
     // per row: the lane's pixels are bx0 + lane + 32k, so each edge function advances by a
     // constant 32 * 256 * dy between them (exact 64-bit integer steps)
     const long long s0 = 8192ll * (Y[2] - Y[1]), s1 = 8192ll * (Y[0] - Y[2]), s2 = 8192ll * (Y[1] - Y[0]);
@@ -783,14 +829,22 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
     if (k < b1) {
       WarpTri T;
       T.key = sc.bins[k];
-      load_tri(rec_of(p, sc, T.key), T.X, T.Y, T.iw);
-      tri_setup(T.X, T.Y, T.fA, T.tl);
-      const int xmin = min(T.X[0], min(T.X[1], T.X[2])), xmax = max(T.X[0], max(T.X[1], T.X[2]));
-      const int ymin = min(T.Y[0], min(T.Y[1], T.Y[2])), ymax = max(T.Y[0], max(T.Y[1], T.Y[2]));
-      T.px0 = max(x0, -((128 - xmin) >> 8));
-      T.py0 = max(y0, -((128 - ymin) >> 8));
-      const int bw = min(x0 + cw - 1, (xmax - 128) >> 8) - T.px0 + 1;
-      const int bh = min(y0 + ch - 1, (ymax - 128) >> 8) - T.py0 + 1;
+      const Record* rb = rec_of(p, sc, T.key);
+      uint2 box;
+      load_setup(rb, T.fA, box);
+      load_tri(rb, T.X, T.Y, T.iw);
+      T.tl = (box.y >> 28) & 7;
+      T.small = box.y >> 31;
+      if (T.small) {  // relative to vertex 0 (exact 32-bit arithmetic)
+        T.X[1] -= T.X[0];
+        T.X[2] -= T.X[0];
+        T.Y[1] -= T.Y[0];
+        T.Y[2] -= T.Y[0];
+      }
+      T.px0 = max(x0, int(box.x & 0xffff));
+      T.py0 = max(y0, int(box.y & 0xffff));
+      const int bw = min(x0 + cw - 1, int(box.x >> 16)) - T.px0 + 1;
+      const int bh = min(y0 + ch - 1, int((box.y >> 16) & 0xfff)) - T.py0 + 1;
       T.bw = bw;
       cnt = (bw > 0 && bh > 0) ? bw * bh : 0;
       wt[lane] = T;
@@ -812,8 +866,13 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
       }
       const WarpTri& T = wt[lo];
       const BoxWalk w(m - woff[lo], T.px0, T.py0, T.bw);
-      const unsigned long long f =
-          fragment(T.X, T.Y, T.iw, T.fA, T.tl, T.key, im.ortho, 256 * w.px + 128, 256 * w.py + 128);
+      unsigned long long f;
+      if (T.small) {
+        const int Xr[3] = {0, T.X[1], T.X[2]}, Yr[3] = {0, T.Y[1], T.Y[2]};
+        f = fragment32(Xr, Yr, T.iw, T.fA, T.tl, T.key, im.ortho, 256 * w.px + 128 - T.X[0], 256 * w.py + 128 - T.Y[0]);
+      } else {
+        f = fragment(T.X, T.Y, T.iw, T.fA, T.tl, T.key, im.ortho, 256 * w.px + 128, 256 * w.py + 128);
+      }
       if (f != kEmpty) atomicMin(&keys[(w.py - y0) * cw + (w.px - x0)], f);
     }
     __syncwarp();
@@ -844,18 +903,19 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
       } else {
         depth = __uint_as_float(unsigned(kk >> 32));
         const Record* r = rec_of(p, sc, unsigned(kk));
-        const int4 q2 = reinterpret_cast<const int4*>(r)[2];
-        const float4 q3 = reinterpret_cast<const float4*>(r)[3];
-        mat = q2.y & 0xffff;
-        seg = (q2.y >> 16) & 0xff;
-        if (q2.y & (1 << 24)) {  // flat face: the interpolated normal is the vertex normal
-          n[0] = __int_as_float(q2.z);
-          n[1] = __int_as_float(q2.w);
-          n[2] = q3.x;
+        const int4 q3 = reinterpret_cast<const int4*>(r)[3];
+        mat = q3.x & 0xffff;
+        seg = (q3.x >> 16) & 0xff;
+        if (q3.x & (1 << 24)) {  // flat face: the interpolated normal is the vertex normal
+          n[0] = __int_as_float(q3.y);
+          n[1] = __int_as_float(q3.z);
+          n[2] = __int_as_float(q3.w);
         } else {
           const int4 q0 = reinterpret_cast<const int4*>(r)[0];
           const int4 q1 = reinterpret_cast<const int4*>(r)[1];
+          const float iw2 = reinterpret_cast<const float*>(r)[8];
           const float4 q4 = reinterpret_cast<const float4*>(r)[4];
+          const float2 q5 = reinterpret_cast<const float2*>(r)[10];
           const int cx = 256 * px + 128, cy = 256 * py + 128;
           float a0 = float(cx - q0.z) * float(q1.y - q0.w) - float(cy - q0.w) * float(q1.x - q0.z);
           float a1 = float(cx - q1.x) * float(q0.y - q1.y) - float(cy - q1.y) * float(q0.x - q1.x);
@@ -863,11 +923,11 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
           if (!im.ortho) {
             a0 *= __int_as_float(q1.z);
             a1 *= __int_as_float(q1.w);
-            a2 *= __int_as_float(q2.x);
+            a2 *= iw2;
           }
-          n[0] = a0 * __int_as_float(q2.z) + a1 * q3.y + a2 * q4.x;
-          n[1] = a0 * __int_as_float(q2.w) + a1 * q3.z + a2 * q4.y;
-          n[2] = a0 * q3.x + a1 * q3.w + a2 * q4.z;
+          n[0] = a0 * __int_as_float(q3.y) + a1 * q4.x + a2 * q4.w;
+          n[1] = a0 * __int_as_float(q3.z) + a1 * q4.y + a2 * q5.x;
+          n[2] = a0 * __int_as_float(q3.w) + a1 * q4.z + a2 * q5.y;
         }
         const float l2 = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
         if (l2 > 0.0f) {
@@ -959,8 +1019,57 @@ __device__ inline SmemPtrs carve(char* smem, const Params& p, const SmemLayout& 
   return s;
 }
 
+// Bounded waits: a spin that exceeds this many SM cycles (about a second) sets
+// ORRB_DEV_TIMEOUT and gives up instead of hanging.
+constexpr long long kSpinBudget = 2000000000ll;
+
+// Raster tiles of the image whose claim word is `claim`, for camera `cam`.  The owner of
+// the slot claims with atomicAdd and counts its own tiles in shared memory (its CTA wrote
+// the records, so it needs no fence); a helper claims with compare-and-swap, so it never
+// takes a tile of a later image that reused the slot, and publishes each finished tile
+// in the slot's counter after a fence.
+__device__ void raster_claimed(const Params& p, CtaShared& sh, const Scratch& sc, char* uni, const SmemLayout& L,
+                               int cam, bool owner) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  char* wbase = uni + (size_t)warp * L.w_bytes;
+  unsigned long long* word = sc.claim();
+  const unsigned long long tag = (unsigned long long)(cam + 1) << 32;
+  const int n_tiles = sh.im.n_tiles;
+  int mine = 0;
+  while (true) {
+    int t = 0;
+    if (lane == 0) {
+      if (owner) {
+        t = int(unsigned(atomicAdd(word, 1ull)));
+      } else {
+        t = n_tiles;
+        unsigned long long w = atomicAdd(word, 0ull);
+        while ((w & ~0xffffffffull) == tag && int(unsigned(w)) < n_tiles) {
+          const unsigned long long seen = atomicCAS(word, w, w + 1);
+          if (seen == w) {
+            t = int(unsigned(w));
+            break;
+          }
+          w = seen;
+        }
+      }
+    }
+    t = __shfl_sync(kFull, t, 0);
+    if (t >= n_tiles) break;
+    raster_tile_warp(p, sh, sc, t, wbase, L);
+    mine++;
+    if (!owner && lane == 0) {
+      __threadfence();
+      atomicAdd(reinterpret_cast<unsigned*>(sc.header + 4), 1u);
+    }
+  }
+  if (owner && lane == 0) atomicAdd(&sh.next_tile, mine);  // the owner's own count (shared memory)
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
-// fused: one persistent launch, CTAs pull whole images from a queue
+// fused: one persistent launch.  CTAs pull whole images from a queue; once the
+// queue is empty they help finish the raster phase of images other CTAs still own.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
   extern __shared__ __align__(16) char smem[];
@@ -979,7 +1088,89 @@ __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
       __syncthreads();
       int* counts = reinterpret_cast<int*>(sp.uni);
       bin_phase(p, sh, counts, counts + (p.max_tiles + 2), sc);
-      raster_phase(p, sh, sc, sp.uni, L);
+      if (threadIdx.x == 0) {  // open the raster phase to helpers
+        sc.header[3] = sh.n_big;
+        sc.header[4] = 0;
+        sc.header[5] = sh.im.n_tiles;
+        sh.next_tile = 0;
+        __threadfence();
+        atomicExch(sc.claim(), (unsigned long long)(cam + 1) << 32);
+      }
+      __syncthreads();
+      raster_claimed(p, sh, sc, sp.uni, L, cam, true);
+      if (threadIdx.x == 0) {  // close it and wait for helpers still on its other tiles
+        atomicExch(sc.claim(), 0ull);
+        const unsigned helped = unsigned(sh.im.n_tiles - sh.next_tile);
+        const long long t0 = clock64();
+        while (atomicAdd(reinterpret_cast<unsigned*>(sc.header + 4), 0u) < helped) {
+          if (clock64() - t0 > kSpinBudget) {
+            flag_status(p, ORRB_DEV_TIMEOUT);
+            break;
+          }
+          __nanosleep(200);
+        }
+      }
+    }
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(p.images_done, 1u);
+    }
+    __syncthreads();
+  }
+  // helper mode: join the open raster phase with the most tiles left, until every image is done
+  long long t0 = clock64();  // start of the current search (thread 0); reset whenever work is found
+  while (true) {
+    if (threadIdx.x < 32) {  // warp 0 scans the slots, one per lane at a time
+      int best = -1, best_left = 0;
+      for (int s = threadIdx.x; s < p.n_slots; s += 32) {
+        const Scratch o = slot_scratch(p, s);
+        const unsigned long long w = *reinterpret_cast<volatile unsigned long long*>(o.header);
+        if (w == 0ull) continue;
+        const int left = *reinterpret_cast<volatile int*>(o.header + 5) - int(unsigned(w));
+        if (left > best_left) {
+          best_left = left;
+          best = s;
+        }
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        const int ol = __shfl_down_sync(kFull, best_left, off), ob = __shfl_down_sync(kFull, best, off);
+        if (ol > best_left) {
+          best_left = ol;
+          best = ob;
+        }
+      }
+      int cam = -1;
+      if (best >= 0) {
+        const unsigned long long w = *reinterpret_cast<volatile unsigned long long*>(slot_scratch(p, best).header);
+        cam = int(w >> 32) - 1;   // 0 -> -1: closed meanwhile, search again
+        if (cam < 0) best = -1;
+      }
+      if (threadIdx.x == 0) {
+        if (best >= 0) {
+          t0 = clock64();
+        } else {
+          if (*reinterpret_cast<volatile unsigned*>(p.images_done) >= unsigned(p.n_cams)) cam = -2;
+          else if (clock64() - t0 > kSpinBudget) {
+            flag_status(p, ORRB_DEV_TIMEOUT);
+            cam = -2;
+          } else {
+            __nanosleep(500);
+          }
+        }
+        sh.help_slot = best;
+        sh.help_cam = cam;
+      }
+    }
+    __syncthreads();
+    const int slot = sh.help_slot, cam = sh.help_cam;
+    if (cam == -2) break;
+    if (slot >= 0 && cam >= 0) {
+      const Scratch o = slot_scratch(p, slot);
+      __threadfence();
+      setup_image(p, cam, sh, sp.mprefix, sp.tprefix, false);
+      if (threadIdx.x == 0) sh.n_big = *reinterpret_cast<volatile int*>(o.header + 3);
+      __syncthreads();
+      raster_claimed(p, sh, o, sp.uni, L, cam, false);
     }
     __syncthreads();
   }
@@ -1004,12 +1195,12 @@ __global__ void __launch_bounds__(512, 2) plain_geometry_kernel(Params p) {
   const Scratch sc = slot_scratch(p, blockIdx.x);
   setup_image(p, cam, sh, sp.mprefix, sp.tprefix, true);
   if (!sh.im.valid) {
-    if (threadIdx.x == 0) sc.header[0] = -1;
+    if (threadIdx.x == 0) sc.header[2] = -1;
     return;
   }
   geometry_phase(p, sh, sp.mprefix, sp.tprefix, reinterpret_cast<WarpG*>(sp.uni), sc);
   __syncthreads();
-  if (threadIdx.x == 0) sc.header[0] = sh.n_vis;
+  if (threadIdx.x == 0) sc.header[2] = sh.n_vis;
 }
 
 __global__ void __launch_bounds__(512, 2) plain_bin_kernel(Params p) {
@@ -1021,13 +1212,13 @@ __global__ void __launch_bounds__(512, 2) plain_bin_kernel(Params p) {
   SmemPtrs sp = carve(smem, p, L);
   const Scratch sc = slot_scratch(p, blockIdx.x);
   setup_image(p, cam, sh, sp.mprefix, sp.tprefix, false);
-  const int nvis = sc.header[0];
+  const int nvis = sc.header[2];
   if (nvis < 0) return;
   if (threadIdx.x == 0) sh.n_vis = nvis;
   __syncthreads();
   int* counts = reinterpret_cast<int*>(sp.uni);
   bin_phase(p, sh, counts, counts + (p.max_tiles + 2), sc);
-  if (threadIdx.x == 0) sc.header[1] = sh.n_big;
+  if (threadIdx.x == 0) sc.header[3] = sh.n_big;
 }
 
 __global__ void __launch_bounds__(512, 2) plain_raster_kernel(Params p) {
@@ -1036,11 +1227,11 @@ __global__ void __launch_bounds__(512, 2) plain_raster_kernel(Params p) {
   const int cam = plain_cam(p);
   if (cam < 0) return;
   const Scratch sc = slot_scratch(p, blockIdx.x);
-  if (sc.header[0] < 0) return;
+  if (sc.header[2] < 0) return;
   const SmemLayout L = layout_of(p);
   SmemPtrs sp = carve(smem, p, L);
   setup_image(p, cam, sh, sp.mprefix, sp.tprefix, false);
-  if (threadIdx.x == 0) sh.n_big = sc.header[1];
+  if (threadIdx.x == 0) sh.n_big = sc.header[3];
   __syncthreads();
   raster_phase(p, sh, sc, sp.uni, L, blockIdx.y, gridDim.y);
 }
@@ -1110,6 +1301,10 @@ int launch_render(const Params& p, int mode, int threads, int n_ctas, int max_ca
   cudaError_t e = cudaSuccess;
   if (mode == 0) {
     e = ensure_smem((const void*)render_fused_kernel, 0, smem);
+    if (e == cudaSuccess) {  // slot headers (claim words, counters) start at zero
+      const SlotLayout SL = slot_layout(p.t_max, p.max_tiles);
+      e = cudaMemset2DAsync(p.scratch + SL.header, p.slot_bytes, 0, 64, (size_t)n_ctas, st);
+    }
     if (e == cudaSuccess) {
       render_fused_kernel<<<n_ctas, threads, smem, st>>>(p);
       e = cudaGetLastError();
