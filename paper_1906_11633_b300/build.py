@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 SOURCES = ["orrb_api.cpp", "orrb_render.cu", "orrb_backward.cu"]
-HEADERS = [os.path.join(CSRC, "orrb_internal.h"), os.path.join(ROOT, "include", "orrb.h")]
+HEADERS = [os.path.join(CSRC, "orrb_internal.h"), os.path.join(CSRC, "orrb_shading.cuh"), os.path.join(ROOT, "include", "orrb.h")]
 LIB = os.path.join(HERE, "liborrb.so")
 NVCC_FLAGS = ["-std=c++17", "-O3", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
               "-Xcompiler", "-fPIC", "-shared", "-I" + os.path.join(ROOT, "include")]

@@ -23,6 +23,7 @@
 
 #include "orrb.h"
 #include "orrb_internal.h"
+#include "orrb_shading.cuh"
 
 namespace orrb {
 namespace {
@@ -118,7 +119,9 @@ __global__ void __launch_bounds__(kBwdThreads) backward_partial_kernel(BackwardP
         const float G = g[0] + g[1] + g[2];
         const float gr = g[0] * m[0] + g[1] * m[1] + g[2] * m[2];
         float sum_endl = 0.0f, sum_epw = 0.0f, acc[3] = {0.0f, 0.0f, 0.0f};
-        for (int l = 0; l < sh.n_lights; l++) {
+#pragma unroll
+        for (int l = 0; l < kMaxLights; l++) {
+          if (l >= sh.n_lights) break;
           float L[3], Lv[3] = {0.0f, 0.0f, 0.0f}, E, d2 = 1.0f, rinv = 1.0f;
           const float I = sh.lv[l][3];
           if (sh.light_type == 0) {
@@ -144,7 +147,7 @@ __global__ void __launch_bounds__(kBwdThreads) backward_partial_kernel(BackwardP
               rh = rsqrtf(h2);
               for (int k = 0; k < 3; k++) H[k] = Hv[k] * rh;
               ndh = fmaxf(0.0f, n[0] * H[0] + n[1] * H[1] + n[2] * H[2]);
-              pw = powf(ndh, m[4]);
+              pw = lobe_pow(ndh, m[4]);
             }
           }
           const float spec = m[3] * pw;
