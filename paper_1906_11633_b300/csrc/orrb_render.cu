@@ -17,16 +17,15 @@
 //      per-tile bins; the rest go to a "large" list that every tile tests
 //      itself (in practice the table plane).
 //   R  raster + shade: each warp owns one tile at a time (default: one image
-//      row), pulling tiles from a per-CTA counter, with its depth keys and
-//      output staging in warp-private shared memory, so the phase needs no
-//      CTA-wide barrier.  Large triangles: lanes split the triangle's box.
+//      row), claiming tiles from the image's counter, with its depth keys in
+//      warp-private shared memory, so the phase needs no CTA-wide barrier.  Large triangles: lanes split the triangle's box.
 //      Binned triangles: 32 at a time, their boxes prefix-summed and the
 //      (triangle, pixel) candidates spread evenly over the lanes, each
 //      covered centre folding (depth bits << 32 | key) into the tile's keys
 //      with a shared-memory 64-bit atomicMin.  Then every pixel resolves its
 //      winner, interpolates the normal, shades (Blinn-Phong, point or
-//      directional lights, exposure) and writes the four channels; RGB and
-//      normals are staged per row and written with 16-byte vector stores.
+//      directional lights, exposure) and writes the four channels, consecutive
+//      lanes on consecutive pixels of a row.
 //
 // Everything that decides coverage, visibility or depth (transform, clip,
 // projection, snapping, edge functions, depth) uses explicitly rounded fp32
@@ -106,8 +105,8 @@ struct Scratch {
 
 struct SmemLayout {
   size_t uni, g_size, b_size;
-  // phase R, per warp: keys, staged triangles, their offsets, RGB and normal row staging
-  size_t w_keys, w_tri, w_off, w_rgb, w_nrm, w_bytes, rgb_row, nrm_row, r_size;
+  // phase R, per warp: depth keys of the tile, staged triangles and their offsets
+  size_t w_keys, w_tri, w_off, w_bytes, r_size;
   size_t total;
 };
 
@@ -120,14 +119,10 @@ __host__ __device__ inline SmemLayout smem_layout(int threads, int tile_w, int t
   L.uni = al16(size_t(2) * (inst_max + 2) * sizeof(int));
   L.g_size = size_t(threads / 32) * al16(sizeof(WarpG));
   L.b_size = al16(size_t(2) * (max_tiles + 2) * sizeof(int));
-  L.rgb_row = al16(3 * tw + 16);
-  L.nrm_row = al16(6 * tw + 16);
   L.w_keys = 0;
   L.w_tri = al16(tw * th * 8);
   L.w_off = L.w_tri + al16(32 * sizeof(WarpTri));
-  L.w_rgb = L.w_off + al16(32 * sizeof(int));
-  L.w_nrm = L.w_rgb + th * L.rgb_row;
-  L.w_bytes = L.w_nrm + th * L.nrm_row;
+  L.w_bytes = L.w_off + al16(32 * sizeof(int));
   L.r_size = size_t(threads / 32) * L.w_bytes;
   size_t u = L.g_size > L.b_size ? L.g_size : L.b_size;
   u = u > L.r_size ? u : L.r_size;
@@ -705,23 +700,6 @@ __device__ void shade(const CtaShared& sh, const float P[3], const float n[3], i
 
 __device__ __forceinline__ uint8_t quantise(float v) { return (uint8_t)floorf(fminf(fmaxf(v, 0.0f), 1.0f) * 255.0f + 0.5f); }
 
-// Copy nbytes from shared src to global dst, 16-byte vectors where both share alignment.
-__device__ void copy_out(char* dst, const char* src, int nbytes, int tid, int nt) {
-  const uintptr_t da = reinterpret_cast<uintptr_t>(dst), sa = reinterpret_cast<uintptr_t>(src);
-  if (((da ^ sa) & 15) == 0) {
-    int head = int((16 - (da & 15)) & 15);
-    if (head > nbytes) head = nbytes;
-    const int nvec = (nbytes - head) >> 4;
-    const int tail0 = head + (nvec << 4);
-    for (int i = tid; i < head; i += nt) dst[i] = src[i];
-    const uint4* s4 = reinterpret_cast<const uint4*>(src + head);
-    uint4* d4 = reinterpret_cast<uint4*>(dst + head);
-    for (int i = tid; i < nvec; i += nt) __stcs(d4 + i, s4[i]);
-    for (int i = tail0 + tid; i < nbytes; i += nt) dst[i] = src[i];
-  } else {
-    for (int i = tid; i < nbytes; i += nt) dst[i] = src[i];
-  }
-}
 
 // Walks the pixels of a box (px0, py0, width bw) with index j = lane, lane+32, ...
 struct BoxWalk {
@@ -848,16 +826,14 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
     __syncwarp();
   }
 
-  // resolve + shade; depth / seg / optional planes go straight out, RGB and normals are
-  // staged per tile row at the destination's 16-byte phase and copied with vector stores
+  // resolve + shade; every channel goes straight out, lane-consecutive pixels per row
   const long long N = p.total_pixels;
   for (int ly = 0; ly < ch; ly++) {
     const long long orow = im.px_off + (long long)(y0 + ly) * im.W + x0;
     const int py = y0 + ly;
     const float uy = -((float(py) + 0.5f - im.cy) * im.inv_fy);
-    char* st_rgb = wbase + L.w_rgb + ly * L.rgb_row + (p.rgb ? int(reinterpret_cast<uintptr_t>(p.rgb + 3 * orow) & 15) : 0);
-    uint16_t* st_nrm = reinterpret_cast<uint16_t*>(
-        wbase + L.w_nrm + ly * L.nrm_row + (p.normal ? int(reinterpret_cast<uintptr_t>(p.normal + 3 * orow) & 15) : 0));
+    uint8_t* rgb_row = p.rgb ? p.rgb + 3 * orow : nullptr;
+    uint16_t* nrm_row = p.normal ? p.normal + 3 * orow : nullptr;
     float* depth_row = p.depth ? p.depth + orow : nullptr;
     uint8_t* seg_row = p.seg ? p.seg + orow : nullptr;
     const unsigned long long* krow = keys + ly * cw;
@@ -918,19 +894,23 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
         }
         shade(sh, P, n, mat, rgb);
       }
-      if (p.rgb) {
-        st_rgb[3 * lx + 0] = quantise(rgb[0]);
-        st_rgb[3 * lx + 1] = quantise(rgb[1]);
-        st_rgb[3 * lx + 2] = quantise(rgb[2]);
+      // consecutive lanes write consecutive pixels: the three byte (or half) stores of a
+      // warp fill whole sectors of the row between them
+      // (explicit global streaming stores: outputs are not re-read, and the compiler need not
+      // assume they alias the shared-memory light and material tables)
+      if (rgb_row) {
+        __stcs(rgb_row + 3 * lx + 0, quantise(rgb[0]));
+        __stcs(rgb_row + 3 * lx + 1, quantise(rgb[1]));
+        __stcs(rgb_row + 3 * lx + 2, quantise(rgb[2]));
       }
-      if (p.normal) {
+      if (nrm_row) {
         const __half2 h01 = __floats2half2_rn(n[0], n[1]);
-        st_nrm[3 * lx + 0] = __half_as_ushort(__low2half(h01));
-        st_nrm[3 * lx + 1] = __half_as_ushort(__high2half(h01));
-        st_nrm[3 * lx + 2] = __half_as_ushort(__float2half_rn(n[2]));
+        __stcs(nrm_row + 3 * lx + 0, __half_as_ushort(__low2half(h01)));
+        __stcs(nrm_row + 3 * lx + 1, __half_as_ushort(__high2half(h01)));
+        __stcs(nrm_row + 3 * lx + 2, __half_as_ushort(__float2half_rn(n[2])));
       }
       if (depth_row) __stcs(depth_row + lx, depth);
-      if (seg_row) seg_row[lx] = (uint8_t)seg;
+      if (seg_row) __stcs(seg_row + lx, (uint8_t)seg);
       if (p.rgb_linear) {
         float* o3 = p.rgb_linear + 3 * (orow + lx);
         __stcs(o3 + 0, rgb[0]);
@@ -948,9 +928,6 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
         __stcs(p.gbuffer + 6 * N + o, __int_as_float(mat));
       }
     }
-    __syncwarp();
-    if (p.rgb) copy_out(reinterpret_cast<char*>(p.rgb + 3 * orow), st_rgb, 3 * cw, lane, 32);
-    if (p.normal) copy_out(reinterpret_cast<char*>(p.normal + 3 * orow), reinterpret_cast<char*>(st_nrm), 6 * cw, lane, 32);
   }
   __syncwarp();
 }
