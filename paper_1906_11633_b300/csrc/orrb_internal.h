@@ -102,8 +102,11 @@ struct Params {
 
 // Per-slot scratch (one image at a time): sizes in elements, from t_max.
 struct SlotLayout {
-  size_t rec, vis_key, vis_box, bins, big, tile_off, header, total;
+  size_t rec, vis_key, vis_box, bins, big, tile_off, counts, header, total;
 };
+
+// Binning keeps its per-tile counters in shared memory up to this many tiles, else in the slot.
+constexpr int kSmemCountTiles = 4094;
 
 ORRB_HD inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -118,6 +121,7 @@ ORRB_HD inline SlotLayout slot_layout(int t_max, int max_tiles) {
   L.bins = o;     o = align256(o + cap * kMaxSpanTiles * 4);
   L.big = o;      o = align256(o + cap * 4);
   L.tile_off = o; o = align256(o + (size_t(max_tiles) + 1) * 4);
+  L.counts = o;   o = align256(o + (max_tiles > kSmemCountTiles ? 2 * (size_t(max_tiles) + 2) * 4 : 0));
   L.total = o;
   return L;
 }

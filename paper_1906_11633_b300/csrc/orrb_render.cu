@@ -99,6 +99,7 @@ struct Scratch {
   uint32_t* tile_off;
   // header: [0..1] claim word (camera + 1) << 32 | next tile, 0 while no raster phase is
   // open; [2] n_vis; [3] n_big; [4] tiles finished; [5] tiles of the open image
+  int* counts;  // per-tile counters and cursors when they do not fit in shared memory
   int* header;
   __device__ unsigned long long* claim() const { return reinterpret_cast<unsigned long long*>(header); }
 };
@@ -118,7 +119,7 @@ __host__ __device__ inline SmemLayout smem_layout(int threads, int tile_w, int t
   const size_t tw = size_t(tile_w < w_max ? tile_w : w_max), th = size_t(tile_h);
   L.uni = al16(size_t(2) * (inst_max + 2) * sizeof(int));
   L.g_size = size_t(threads / 32) * al16(sizeof(WarpG));
-  L.b_size = al16(size_t(2) * (max_tiles + 2) * sizeof(int));
+  L.b_size = max_tiles > kSmemCountTiles ? 0 : al16(size_t(2) * (max_tiles + 2) * sizeof(int));
   L.w_keys = 0;
   L.w_tri = al16(tw * th * 8);
   L.w_off = L.w_tri + al16(32 * sizeof(WarpTri));
@@ -141,6 +142,7 @@ __device__ inline Scratch slot_scratch(const Params& p, int slot) {
   s.bins = reinterpret_cast<uint32_t*>(b + L.bins);
   s.big = reinterpret_cast<uint32_t*>(b + L.big);
   s.tile_off = reinterpret_cast<uint32_t*>(b + L.tile_off);
+  s.counts = reinterpret_cast<int*>(b + L.counts);
   return s;
 }
 
@@ -662,7 +664,9 @@ __device__ void shade(const CtaShared& sh, const float P[3], const float n[3], i
     Vv[2] = -P[2] * rl;
   }
   float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
-  for (int l = 0; l < im.n_lights; l++) {
+#pragma unroll
+  for (int l = 0; l < kMaxLights; l++) {
+    if (l >= im.n_lights) break;
     float L[3], E;
     if (im.light_type == 0) {
       float Lv0 = im.lv[l][0] - P[0], Lv1 = im.lv[l][1] - P[1], Lv2 = im.lv[l][2] - P[2];
@@ -1033,7 +1037,7 @@ __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
     if (sh.im.valid) {
       geometry_phase(p, sh, sp.mprefix, sp.tprefix, reinterpret_cast<WarpG*>(sp.uni), sc);
       __syncthreads();
-      int* counts = reinterpret_cast<int*>(sp.uni);
+      int* counts = p.max_tiles > kSmemCountTiles ? sc.counts : reinterpret_cast<int*>(sp.uni);
       bin_phase(p, sh, counts, counts + (p.max_tiles + 2), sc);
       if (threadIdx.x == 0) {  // open the raster phase to helpers
         sc.header[3] = sh.n_big;
@@ -1163,7 +1167,7 @@ __global__ void __launch_bounds__(512, 2) plain_bin_kernel(Params p) {
   if (nvis < 0) return;
   if (threadIdx.x == 0) sh.n_vis = nvis;
   __syncthreads();
-  int* counts = reinterpret_cast<int*>(sp.uni);
+  int* counts = p.max_tiles > kSmemCountTiles ? sc.counts : reinterpret_cast<int*>(sp.uni);
   bin_phase(p, sh, counts, counts + (p.max_tiles + 2), sc);
   if (threadIdx.x == 0) sc.header[3] = sh.n_big;
 }

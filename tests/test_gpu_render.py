@@ -150,3 +150,26 @@ def test_host_checks_reject_bad_arguments(hand_renderer):
     with pytest.raises(L.OrrbError):
         small = torch.empty(256, dtype=torch.uint8, device="cuda")
         hand_renderer.render(db, workspace=small)
+
+
+def test_maximum_sizes(oracle):
+    """Largest image sides (4096 wide; 4096 tall, whose 4096 row tiles keep their binning counters in
+    global memory) and the largest instance count per sample (1024)."""
+    meshes = [sg.plane_mesh(3, 3), sg.box_mesh(0.05), sg.capsule_mesh(0.03, 0.1)]
+    r = Renderer(meshes)
+    rng = np.random.default_rng(11)
+    n = 1024
+    inst_mesh = np.concatenate([[0], rng.integers(1, 3, n - 1)])
+    poses = [scenes.identity_pose()] + [
+        scenes.pose(R=sg._rot("z", np.array(rng.uniform(0, 6.28))), t=(rng.uniform(-1, 1), rng.uniform(-1, 1),
+                                                                         rng.uniform(0.05, 0.6)))
+        for _ in range(n - 1)]
+    cams = [scenes.camera_look((0.0, -2.5, 2.0), (0, 0, 0.2), 4096, 64, 20.0),
+            scenes.camera_look((0.3, -2.0, 2.5), (0, 0, 0.2), 64, 4096, 60.0)]
+    b = scenes.single_sample(meshes, inst_mesh, poses, cams, seg=np.arange(n) % 250 + 1, mat_base=np.arange(n) % 26,
+                             lights=[((0.5, -1.0, 2.0), 2.0)], albedo=(0.6, 0.4, 0.3), specular=0.3,
+                             shininess=16.0, ambient=(0.05, 0.05, 0.05), background=(0.2, 0.3, 0.4))
+    g = render_np(r, b)
+    o = oracle.render(b, debug=True)
+    st = compare(g, o, "max sizes")
+    assert (o["seg"] > 2).sum() > 1000      # many of the 1023 small instances are visible
