@@ -856,7 +856,7 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
         const int4 q3 = reinterpret_cast<const int4*>(r)[3];
         mat = q3.x & 0xffff;
         seg = (q3.x >> 16) & 0xff;
-        if (q3.x & (1 << 24)) {  // flat face: the interpolated normal is the vertex normal
+        if (q3.x & (1 << 24)) {  // flat face: the normalised interpolated normal is the (unit) vertex normal
           n[0] = __int_as_float(q3.y);
           n[1] = __int_as_float(q3.z);
           n[2] = __int_as_float(q3.w);
@@ -878,13 +878,13 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
           n[0] = a0 * __int_as_float(q3.y) + a1 * q4.x + a2 * q4.w;
           n[1] = a0 * __int_as_float(q3.z) + a1 * q4.y + a2 * q5.x;
           n[2] = a0 * __int_as_float(q3.w) + a1 * q4.z + a2 * q5.y;
-        }
-        const float l2 = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
-        if (l2 > 0.0f) {
-          const float rl = rsqrtf(l2);
-          n[0] *= rl;
-          n[1] *= rl;
-          n[2] *= rl;
+          const float l2 = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+          if (l2 > 0.0f) {
+            const float rl = rsqrtf(l2);
+            n[0] *= rl;
+            n[1] *= rl;
+            n[2] *= rl;
+          }
         }
         const float ux = (float(px) + 0.5f - im.cx) * im.inv_fx;
         if (im.ortho) {
