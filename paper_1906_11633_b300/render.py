@@ -211,6 +211,63 @@ class GraphRender:
         return self.out
 
 
+class CapturePipeline:
+    """Round-robin pool of render targets with bulk readback (the capture pipeline of Sec. 4.4).
+
+    `depth` slots, each holding device inputs, a workspace, device outputs and pinned
+    host outputs for batches of one shape.  `submit` copies a batch's parameters from
+    pinned host memory, renders on the compute stream and queues the bulk device-to-host
+    copy of all channels on a copy stream, so a batch renders while the previous one is
+    still being read back.  A slot is reused `depth` submissions later: read (or copy)
+    its host outputs before then.
+    """
+
+    def __init__(self, renderer: Renderer, batch, depth: int = 2, cfg: Optional[L.orrb_config] = None):
+        self.r = renderer
+        self.cfg = cfg or config()
+        self.shape = batch_shape(batch)
+        self.compute = torch.cuda.Stream(device=renderer.device)
+        self.copy = torch.cuda.Stream(device=renderer.device)
+        arrs = host_arrays(batch)
+        n_ws = L.orrb_workspace_size(renderer.ctx, self.shape, self.cfg)
+        self.slots = []
+        for _ in range(depth):
+            dev_in = {k: torch.empty(a.shape, dtype=_DTYPES[k], device=renderer.device) for k, a in arrs.items()}
+            out = renderer.alloc_outputs(int(self.shape.total_pixels))
+            self.slots.append(dict(
+                db=DeviceBatch(self.shape, dev_in), out=out,
+                host={k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items()},
+                ws=torch.empty(n_ws, dtype=torch.uint8, device=renderer.device),
+                rendered=torch.cuda.Event(), done=torch.cuda.Event()))
+        self.k = 0
+
+    @staticmethod
+    def pin(batch) -> Dict[str, torch.Tensor]:
+        """A batch's parameter arrays in pinned host memory (the form `submit` takes)."""
+        return {k: torch.from_numpy(a).pin_memory() for k, a in host_arrays(batch).items()}
+
+    def submit(self, pinned: Dict[str, torch.Tensor]):
+        slot = self.slots[self.k % len(self.slots)]
+        self.k += 1
+        self.compute.wait_event(slot["done"])          # its previous readback has finished
+        with torch.cuda.stream(self.compute):
+            for k, t in slot["db"].tensors.items():
+                t.copy_(pinned[k], non_blocking=True)
+            self.r.render(slot["db"], out=slot["out"], cfg=self.cfg, stream=self.compute, workspace=slot["ws"])
+            slot["rendered"].record(self.compute)
+        self.copy.wait_event(slot["rendered"])
+        with torch.cuda.stream(self.copy):
+            for k, v in slot["out"].items():
+                slot["host"][k].copy_(v, non_blocking=True)
+            slot["done"].record(self.copy)
+        return slot
+
+    @staticmethod
+    def result(slot) -> Dict[str, torch.Tensor]:
+        slot["done"].synchronize()
+        return slot["host"]
+
+
 class ShadeFn(torch.autograd.Function):
     """rgb_linear = shade(material, light, exposure_ev) at fixed visibility.
 

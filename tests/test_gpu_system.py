@@ -93,3 +93,18 @@ def test_served_requests_equal_their_solo_render():
         alone = solo.render(solo.upload(r.batch))
         torch.cuda.synchronize()
         _equal(r.result, alone)
+
+
+def test_capture_pipeline_results_match_direct_renders(renderer):
+    from paper_1906_11633_b300.render import CapturePipeline
+    batches = [sg.hand_batch(20 + k, np.arange(6), res=96) for k in range(3)]
+    pipe = CapturePipeline(renderer, batches[0], depth=2)
+    handles = [pipe.submit(CapturePipeline.pin(b)) for b in batches[:2]]
+    got0 = {k: v.clone() for k, v in CapturePipeline.result(handles[0]).items()}
+    handles.append(pipe.submit(CapturePipeline.pin(batches[2])))     # reuses slot 0 after its readback
+    got = [got0] + [{k: v.clone() for k, v in CapturePipeline.result(h).items()} for h in handles[1:]]
+    for b, g in zip(batches, got):
+        ref = renderer.render(renderer.upload(b))
+        torch.cuda.synchronize()
+        for k in ref:
+            np.testing.assert_array_equal(g[k].numpy(), ref[k].cpu().numpy(), err_msg=k)
