@@ -377,9 +377,10 @@ __device__ __noinline__ void cut_vertex(const ImageInfo& im, const float* pin, c
 // Near-plane clip of triangle (a, b, c) of the staged cluster; emits up to two
 // sub-triangles.  Vertex order follows Sutherland-Hodgman: for each edge
 // (v_k, v_k+1) emit v_k if inside, then the cut if the edge crosses.
-__device__ __noinline__ int clip_triangle(int t_max, Record* rec, const ImageInfo& im, const WarpG* wg,
-                                          const int vi[3], int prim, int mat, int seg, unsigned* keys, uint2* boxes,
+__device__ __noinline__ int clip_triangle(int t_max, Record* rec, const ImageInfo& im, const WarpG* wg, int v0,
+                                          int v1, int v2, int prim, int mat, int seg, unsigned* keys, uint2* boxes,
                                           unsigned* dropped) {
+  const int vi[3] = {v0, v1, v2};
   CutVert poly[4];
   int np = 0;
   for (int k = 0; k < 3; k++) {
@@ -478,8 +479,8 @@ __device__ void geometry_phase(const Params& p, CtaShared& sh, const int* mprefi
     const int seg = p.inst_seg[inst];
     for (int base = 0; base < nt; base += 32) {
       const int t = base + lane;
-      unsigned keys[2];
-      uint2 boxes[2];
+      unsigned key0 = 0, key1 = 0;   // registers: the clip path writes its own arrays
+      uint2 box0 = make_uint2(0, 0), box1 = make_uint2(0, 0);
       int cnt = 0;
       if (t < nt) {
         const uint32_t tri = p.tris[ml.tri_begin + t];
@@ -496,20 +497,28 @@ __device__ void geometry_phase(const Params& p, CtaShared& sh, const int* mprefi
             int X[3] = {wg->X[vi[0]], wg->X[vi[1]], wg->X[vi[2]]};
             int Y[3] = {wg->Y[vi[0]], wg->Y[vi[1]], wg->Y[vi[2]]};
             float fA;
-            if (setup_box(im, X, Y, boxes[0], fA)) {
+            if (setup_box(im, X, Y, box0, fA)) {
               float iw[3] = {wg->iw[vi[0]], wg->iw[vi[1]], wg->iw[vi[2]]};
               float n[3][3];
               for (int k = 0; k < 3; k++)
                 for (int d = 0; d < 3; d++) n[k][d] = wg->nv[vi[k] * 3 + d];
-              write_record(sc.rec + prim, X, Y, iw, n, mat, seg, boxes[0], fA);
-              keys[0] = 2u * prim;
+              write_record(sc.rec + prim, X, Y, iw, n, mat, seg, box0, fA);
+              key0 = 2u * prim;
               cnt = 1;
             }
           } else {
             dropped = 1;
           }
         } else if ((f0 | f1 | f2) & 1) {
-          cnt = clip_triangle(p.t_max, sc.rec, im, wg, vi, prim, mat, seg, keys, boxes, &dropped);
+          unsigned kk[2];
+          uint2 bb[2];
+          unsigned drop = 0;
+          cnt = clip_triangle(p.t_max, sc.rec, im, wg, vi[0], vi[1], vi[2], prim, mat, seg, kk, bb, &drop);
+          dropped |= drop;
+          key0 = kk[0];
+          box0 = bb[0];
+          key1 = kk[1];
+          box1 = bb[1];
         }
       }
       // warp prefix scan of the per-lane counts, one atomic per warp
@@ -523,9 +532,13 @@ __device__ void geometry_phase(const Params& p, CtaShared& sh, const int* mprefi
       if (lane == 31 && total) wbase = atomicAdd(&sh.n_vis, total);
       wbase = __shfl_sync(kFull, wbase, 31);
       int pos = wbase + incl - cnt;
-      for (int k = 0; k < cnt; k++) {
-        sc.vis_key[pos + k] = keys[k];
-        sc.vis_box[pos + k] = boxes[k];
+      if (cnt > 0) {
+        sc.vis_key[pos] = key0;
+        sc.vis_box[pos] = box0;
+      }
+      if (cnt > 1) {
+        sc.vis_key[pos + 1] = key1;
+        sc.vis_box[pos + 1] = box1;
       }
     }
     __syncwarp();
