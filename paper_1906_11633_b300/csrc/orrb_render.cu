@@ -9,7 +9,7 @@
 //      composes MV = V * M, transforms the cluster's vertices into view space,
 //      projects and snaps them to 8 fractional bits, clips triangles at the
 //      near plane (Sutherland-Hodgman, cut computed in fp64), sets up and
-//      culls them, writes one 80-byte record per visible (sub)triangle at a
+//      culls them, writes one 96-byte record per visible (sub)triangle at a
 //      slot fixed by its primitive id, and appends (key, pixel box) to the
 //      image's visible list with a warp prefix scan and one atomic per warp.
 //   B  binning: triangles that touch at most 64 screen tiles are counted per
@@ -66,7 +66,7 @@ struct ImageInfo {
 struct CtaShared {
   ImageInfo im;
   float mat[kMaxMaterials][5];
-  int n_vis, n_big, next_tile, img;
+  int n_vis, n_big, next_tile, next_job, img;
   int help_slot, help_cam;
   int scan_tmp[33];
 };
@@ -86,8 +86,8 @@ struct WarpTri {  // a binned triangle staged for the warp's fragment expansion 
   float iw[3];
   float fA;
   unsigned key;
-  int tl;
-  int px0, py0, bw, small;
+  int flags;  // bits 0-2: top-left edges; bit 3: small (32-bit relative arithmetic)
+  int px0, py0, bw, start;  // clamped box origin and width; index of its first candidate
 };
 
 struct Scratch {
@@ -106,8 +106,8 @@ struct Scratch {
 
 struct SmemLayout {
   size_t uni, g_size, b_size;
-  // phase R, per warp: depth keys of the tile, staged triangles and their offsets
-  size_t w_keys, w_tri, w_off, w_bytes, r_size;
+  // phase R, per warp: depth keys of the tile and the staged triangles
+  size_t w_keys, w_tri, w_bytes, r_size;
   size_t total;
 };
 
@@ -122,8 +122,7 @@ __host__ __device__ inline SmemLayout smem_layout(int threads, int tile_w, int t
   L.b_size = max_tiles > kSmemCountTiles ? 0 : al16(size_t(2) * (max_tiles + 2) * sizeof(int));
   L.w_keys = 0;
   L.w_tri = al16(tw * th * 8);
-  L.w_off = L.w_tri + al16(32 * sizeof(WarpTri));
-  L.w_bytes = L.w_off + al16(32 * sizeof(int));
+  L.w_bytes = L.w_tri + al16(32 * sizeof(WarpTri));
   L.r_size = size_t(threads / 32) * L.w_bytes;
   size_t u = L.g_size > L.b_size ? L.g_size : L.b_size;
   u = u > L.r_size ? u : L.r_size;
@@ -240,24 +239,29 @@ __device__ void setup_image(const Params& p, int cam, CtaShared& sh, int* mprefi
     }
     im.n_lights = nl;
     im.light_type = p.light_meta[s * 2 + 1];
-    for (int l = 0; l < nl; l++) {
-      const float* L4 = p.light + (s * kMaxLights + l) * 4;
-      for (int i = 0; i < 3; i++) {
-        float r = im.V[i * 4 + 0] * L4[0] + im.V[i * 4 + 1] * L4[1] + im.V[i * 4 + 2] * L4[2];
-        im.lv[l][i] = im.light_type == 0 ? r + im.V[i * 4 + 3] : -r;
-      }
-      im.lv[l][3] = L4[3];
-    }
-    im.scale = exp2f(p.exposure_ev[s]);
-    for (int k = 0; k < 3; k++) {
-      im.amb[k] = p.ambient[s * 3 + k];
-      im.bg[k] = p.background[s * 3 + k];
-    }
     sh.n_vis = 0;
     sh.n_big = 0;
     sh.next_tile = 0;
+    sh.next_job = 0;
   }
   __syncthreads();
+  // lights into view space, exposure, ambient and background: one thread each
+  if (tid < kMaxLights) {
+    if (tid < im.n_lights) {
+      const float* L4 = p.light + (im.s * kMaxLights + tid) * 4;
+      for (int i = 0; i < 3; i++) {
+        float r = im.V[i * 4 + 0] * L4[0] + im.V[i * 4 + 1] * L4[1] + im.V[i * 4 + 2] * L4[2];
+        im.lv[tid][i] = im.light_type == 0 ? r + im.V[i * 4 + 3] : -r;
+      }
+      im.lv[tid][3] = L4[3];
+    }
+  } else if (tid < kMaxLights + 3) {
+    im.amb[tid - kMaxLights] = p.ambient[im.s * 3 + tid - kMaxLights];
+  } else if (tid < kMaxLights + 6) {
+    im.bg[tid - kMaxLights - 3] = p.background[im.s * 3 + tid - kMaxLights - 3];
+  } else if (tid == kMaxLights + 6) {
+    im.scale = exp2f(p.exposure_ev[im.s]);
+  }
   for (int k = tid; k < kMaxMaterials * 5; k += blockDim.x)
     sh.mat[k / 5][k % 5] = p.material[(size_t)im.s * kMaxMaterials * 5 + k];
   if (!tables) {
@@ -429,11 +433,15 @@ __device__ __noinline__ int clip_triangle(int t_max, Record* rec, const ImageInf
 __device__ void geometry_phase(const Params& p, CtaShared& sh, const int* mprefix, const int* tprefix, WarpG* wgs,
                                const Scratch& sc) {
   const ImageInfo& im = sh.im;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   WarpG* wg = wgs + warp;
   const int jobs = mprefix[im.n_inst];
   unsigned dropped = 0, badmat = 0;
-  for (int j = warp; j < jobs; j += nw) {
+  while (true) {  // clusters are claimed one at a time: their cost varies with culling and clipping
+    int j = 0;
+    if (lane == 0) j = atomicAdd(&sh.next_job, 1);
+    j = __shfl_sync(kFull, j, 0);
+    if (j >= jobs) break;
     int lo = 0, hi = im.n_inst;  // mprefix[lo] <= j < mprefix[hi]
     while (hi - lo > 1) {
       int mid = (lo + hi) >> 1;
@@ -784,23 +792,24 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
   }
 
   // binned triangles: 32 at a time, their clamped boxes prefix-summed and the
-  // (triangle, pixel) candidates spread evenly over the lanes
+  // (triangle, pixel) candidates spread evenly over the lanes.  Triangles with candidates
+  // are staged compacted, so candidate m belongs to staged triangle (number of starts <= m) - 1;
+  // per chunk of 32 candidates that count is a ballot of the starts up to the chunk plus the
+  // bits of the starts inside it (distinct, since every staged triangle has a candidate).
   WarpTri* wt = reinterpret_cast<WarpTri*>(wbase + L.w_tri);
-  int* woff = reinterpret_cast<int*>(wbase + L.w_off);
   const int b0 = sc.tile_off[tile], b1 = sc.tile_off[tile + 1];
   for (int c = b0; c < b1; c += 32) {
     const int k = c + lane;
     int cnt = 0;
+    WarpTri T;
     if (k < b1) {
-      WarpTri T;
       T.key = sc.bins[k];
       const Record* rb = rec_of(p, sc, T.key);
       uint2 box;
       load_setup(rb, T.fA, box);
       load_tri(rb, T.X, T.Y, T.iw);
-      T.tl = (box.y >> 28) & 7;
-      T.small = box.y >> 31;
-      if (T.small) {  // relative to vertex 0 (exact 32-bit arithmetic)
+      T.flags = (box.y >> 28) & 15;
+      if (T.flags & 8) {  // small: relative to vertex 0 (exact 32-bit arithmetic)
         T.X[1] -= T.X[0];
         T.X[2] -= T.X[0];
         T.Y[1] -= T.Y[0];
@@ -812,33 +821,36 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
       const int bh = min(y0 + ch - 1, int((box.y >> 16) & 0xfff)) - T.py0 + 1;
       T.bw = bw;
       cnt = (bw > 0 && bh > 0) ? bw * bh : 0;
-      wt[lane] = T;
     }
+    const int slot = __popc(__ballot_sync(kFull, cnt > 0) & ((1u << lane) - 1u));
+    if (cnt > 0) wt[slot] = T;
     int incl = cnt;
     for (int o = 1; o < 32; o <<= 1) {
       const int v = __shfl_up_sync(kFull, incl, o);
       if (lane >= o) incl += v;
     }
-    woff[lane] = incl - cnt;
+    const int start = incl - cnt;
     const int total = __shfl_sync(kFull, incl, 31);
+    if (cnt > 0) wt[slot].start = start;
     __syncwarp();
-    for (int m = lane; m < total; m += 32) {
-      int lo = 0, hi = 31;  // largest t with woff[t] <= m: always a triangle with candidates
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (woff[mid] <= m) lo = mid;
-        else hi = mid - 1;
+    for (int base = 0; base < total; base += 32) {
+      const unsigned upto = __ballot_sync(kFull, cnt > 0 && start <= base);
+      const unsigned inside =
+          __reduce_or_sync(kFull, (cnt > 0 && start > base && start < base + 32) ? 1u << (start - base) : 0u);
+      const int m = base + lane;
+      if (m < total) {
+        const WarpTri& W = wt[__popc(upto) + __popc(inside & (0xffffffffu >> (31 - lane))) - 1];
+        const BoxWalk w(m - W.start, W.px0, W.py0, W.bw);
+        const int tl = W.flags & 7;
+        unsigned long long f;
+        if (W.flags & 8) {
+          const int Xr[3] = {0, W.X[1], W.X[2]}, Yr[3] = {0, W.Y[1], W.Y[2]};
+          f = fragment32(Xr, Yr, W.iw, W.fA, tl, W.key, im.ortho, 256 * w.px + 128 - W.X[0], 256 * w.py + 128 - W.Y[0]);
+        } else {
+          f = fragment(W.X, W.Y, W.iw, W.fA, tl, W.key, im.ortho, 256 * w.px + 128, 256 * w.py + 128);
+        }
+        if (f != kEmpty) atomicMin(&keys[(w.py - y0) * cw + (w.px - x0)], f);
       }
-      const WarpTri& T = wt[lo];
-      const BoxWalk w(m - woff[lo], T.px0, T.py0, T.bw);
-      unsigned long long f;
-      if (T.small) {
-        const int Xr[3] = {0, T.X[1], T.X[2]}, Yr[3] = {0, T.Y[1], T.Y[2]};
-        f = fragment32(Xr, Yr, T.iw, T.fA, T.tl, T.key, im.ortho, 256 * w.px + 128 - T.X[0], 256 * w.py + 128 - T.Y[0]);
-      } else {
-        f = fragment(T.X, T.Y, T.iw, T.fA, T.tl, T.key, im.ortho, 256 * w.px + 128, 256 * w.py + 128);
-      }
-      if (f != kEmpty) atomicMin(&keys[(w.py - y0) * cw + (w.px - x0)], f);
     }
     __syncwarp();
   }
