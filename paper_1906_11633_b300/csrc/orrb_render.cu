@@ -104,11 +104,22 @@ struct Scratch {
   __device__ unsigned long long* claim() const { return reinterpret_cast<unsigned long long*>(header); }
 };
 
+// Row spans of the large triangles (one 32-bit entry per triangle and image row) are kept
+// in shared memory when the image has at most this many (triangle, row) pairs.
+constexpr int kSpanCap = 1024;
+
 struct SmemLayout {
-  size_t uni, g_size, b_size;
+  size_t uni, g_size, b_size, spans;
   // phase R, per warp: depth keys of the tile and the staged triangles
   size_t w_keys, w_tri, w_bytes, r_size;
   size_t total;
+};
+
+struct SmemPtrs {
+  int* mprefix;
+  int* tprefix;
+  char* uni;
+  uint32_t* spans;
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -126,7 +137,8 @@ __host__ __device__ inline SmemLayout smem_layout(int threads, int tile_w, int t
   L.r_size = size_t(threads / 32) * L.w_bytes;
   size_t u = L.g_size > L.b_size ? L.g_size : L.b_size;
   u = u > L.r_size ? u : L.r_size;
-  L.total = L.uni + u;
+  L.spans = L.uni + al16(u);
+  L.total = L.spans + size_t(kSpanCap) * sizeof(uint32_t);
   return L;
 }
 
@@ -670,6 +682,64 @@ __device__ __forceinline__ const Record* rec_of(const Params& p, const Scratch& 
   return sc.rec + (size_t)(key & 1u) * p.t_max + (key >> 1);
 }
 
+// Covered pixels of a large triangle on image row py, within its box columns [bx0, bx1]:
+// edge e (vertex e+1 to vertex e+2) is w_e(px) = a * px + c with a = 256 dy, so its
+// half-plane test w_e + tl_e > 0 holds on a half-line of px.  The float quotient lands
+// within a pixel of the boundary (relative error ~2^-21 on values below 2^13 inside the
+// box), and exact 64-bit tests of the neighbouring pixels settle it.  Returns
+// lo | (hi + 1) << 16 (empty: lo > hi).
+__device__ uint32_t row_span(const int X[3], const int Y[3], int tl, int py, int bx0, int bx1) {
+  const int cy = 256 * py + 128;
+  int lo = bx0, hi = bx1;
+#pragma unroll
+  for (int e = 0; e < 3; e++) {
+    const int vs = e == 2 ? 0 : e + 1, ve = e == 0 ? 2 : e - 1;
+    const long long dy = Y[ve] - Y[vs], dx = X[ve] - X[vs];
+    const long long a = 256ll * dy;
+    const long long ct = (128ll - X[vs]) * dy - (long long)(cy - Y[vs]) * dx + ((tl >> e) & 1);  // c + tl
+    if (a > 0) {  // covered from the smallest px with a * px + ct > 0
+      const float t = floorf(__fdividef(__ll2float_rn(-ct), __ll2float_rn(a))) + 1.0f;
+      int q = int(fminf(fmaxf(t, float(bx0)), float(bx1 + 1)));
+      for (int it = 0; it < 4 && q > bx0 && a * (q - 1) + ct > 0; it++) q--;
+      for (int it = 0; it < 4 && q <= bx1 && !(a * q + ct > 0); it++) q++;
+      lo = max(lo, q);
+    } else if (a < 0) {  // covered up to the largest such px
+      const float t = ceilf(__fdividef(__ll2float_rn(ct), __ll2float_rn(-a))) - 1.0f;
+      int q = int(fminf(fmaxf(t, float(bx0 - 1)), float(bx1)));
+      for (int it = 0; it < 4 && q < bx1 && a * (q + 1) + ct > 0; it++) q++;
+      for (int it = 0; it < 4 && q >= bx0 && !(a * q + ct > 0); it++) q--;
+      hi = min(hi, q);
+    } else if (!(ct > 0)) {
+      lo = bx1 + 1;
+    }
+  }
+  if (lo > hi) lo = bx1 + 1, hi = bx1;
+  return unsigned(lo) | (unsigned(hi + 1) << 16);
+}
+
+// Fills the span table of the image's large triangles (block-wide; the caller synchronises).
+__device__ void big_spans(const Params& p, const CtaShared& sh, const Scratch& sc, uint32_t* spans) {
+  const int H = sh.im.H, nb = sh.n_big;
+  if ((long long)nb * H > kSpanCap) return;
+  for (int idx = threadIdx.x; idx < nb * H; idx += blockDim.x) {
+    const int b = idx / H, py = idx - b * H;
+    const Record* r = rec_of(p, sc, sc.big[b]);
+    float fA;
+    uint2 box;
+    load_setup(r, fA, box);
+    const int by0 = int(box.y & 0xffff), by1 = int((box.y >> 16) & 0xfff);
+    const int bx0 = int(box.x & 0xffff), bx1 = int(box.x >> 16);
+    uint32_t v = unsigned(bx1 + 1) | (unsigned(bx1 + 1) << 16);  // empty
+    if (py >= by0 && py <= by1) {
+      int X[3], Y[3];
+      float iw[3];
+      load_tri(r, X, Y, iw);
+      v = row_span(X, Y, (box.y >> 28) & 7, py, bx0, bx1);
+    }
+    spans[idx] = v;
+  }
+}
+
 __device__ void shade(const CtaShared& sh, const float P[3], const float n[3], int mat, float rgb[3]) {
   const ImageInfo& im = sh.im;
   const float* m = sh.mat[mat];
@@ -723,7 +793,8 @@ __device__ void shade(const CtaShared& sh, const float P[3], const float n[3], i
   rgb[2] = im.scale * (im.amb[2] * m[2] + c2);
 }
 
-__device__ __forceinline__ uint8_t quantise(float v) { return (uint8_t)floorf(fminf(fmaxf(v, 0.0f), 1.0f) * 255.0f + 0.5f); }
+// floor(clamp(v, 0, 1) * 255 + 0.5) with one rounding of the multiply-add (NaN -> 0)
+__device__ __forceinline__ uint8_t quantise(float v) { return (uint8_t)__float2uint_rd(fmaf(__saturatef(v), 255.0f, 0.5f)); }
 
 
 // Walks the pixels of a box (px0, py0, width bw) with index j = lane, lane+32, ...
@@ -738,7 +809,7 @@ struct BoxWalk {
 
 // Phase R for one tile, by one warp, in warp-private shared memory.
 __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scratch& sc, int tile, char* wbase,
-                                 const SmemLayout& L) {
+                                 const SmemLayout& L, const uint32_t* spans) {
   const ImageInfo& im = sh.im;
   const int lane = threadIdx.x & 31;
   const int tx = tile % im.ntx, ty = tile / im.ntx;
@@ -749,8 +820,11 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
   for (int i = lane; i < npx; i += 32) keys[i] = kEmpty;
   __syncwarp();
 
-  // large triangles: the lanes split the triangle's box within the tile, one pixel each
+  // large triangles: with the image's span table, the lanes walk only the covered pixels
+  // of each row, one each; without it (too many triangle rows), they split the triangle's
+  // box within the tile and test every pixel
   const int nbig = sh.n_big;
+  const bool with_spans = (long long)nbig * im.H <= kSpanCap;
   for (int b = 0; b < nbig; b++) {
     const unsigned key = sc.big[b];
     int X[3], Y[3];
@@ -764,19 +838,25 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
     if (bx0 > bx1 || by0 > by1) continue;
     load_tri(rb, X, Y, iw);
     const int tl = (box.y >> 28) & 7;
-    // per row: the lane's pixels are bx0 + lane + 32k, so each edge function advances by a
-    // constant 32 * 256 * dy between them (exact 64-bit integer steps)
+    // the lane's pixels are px0 + lane + 32k, so each edge function advances by a constant
+    // 32 * 256 * dy between them (exact 64-bit integer steps)
     const long long s0 = 8192ll * (Y[2] - Y[1]), s1 = 8192ll * (Y[0] - Y[2]), s2 = 8192ll * (Y[1] - Y[0]);
     for (int py = by0; py <= by1; py++) {
-      int px = bx0 + lane;
-      if (px > bx1) continue;
+      int lo = bx0, hi = bx1;
+      if (with_spans) {
+        const uint32_t v = spans[b * im.H + py];
+        lo = max(lo, int(v & 0xffff));
+        hi = min(hi, int(v >> 16) - 1);
+      }
+      int px = lo + lane;
+      if (px > hi) continue;
       const int cx = 256 * px + 128, cy = 256 * py + 128;
       long long w0 = (long long)(cx - X[1]) * (Y[2] - Y[1]) - (long long)(cy - Y[1]) * (X[2] - X[1]);
       long long w1 = (long long)(cx - X[2]) * (Y[0] - Y[2]) - (long long)(cy - Y[2]) * (X[0] - X[2]);
       long long w2 = (long long)(cx - X[0]) * (Y[1] - Y[0]) - (long long)(cy - Y[0]) * (X[1] - X[0]);
       unsigned long long* krow = keys + (py - y0) * cw - x0;
-      for (; px <= bx1; px += 32) {
-        if (w0 + (tl & 1) > 0 && w1 + ((tl >> 1) & 1) > 0 && w2 + ((tl >> 2) & 1) > 0) {
+      for (; px <= hi; px += 32) {
+        if (with_spans || (w0 + (tl & 1) > 0 && w1 + ((tl >> 1) & 1) > 0 && w2 + ((tl >> 2) & 1) > 0)) {
           const float f0 = __ll2float_rn(w0), f1 = __ll2float_rn(w1), f2 = __ll2float_rn(w2);
           const float sum = __fadd_rn(__fadd_rn(__fmul_rn(f0, iw[0]), __fmul_rn(f1, iw[1])), __fmul_rn(f2, iw[2]));
           const float depth = im.ortho ? __fdiv_rn(sum, fA) : __fdiv_rn(fA, sum);
@@ -963,25 +1043,19 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
 
 // Phase R for the current image: warps pull tiles first, first + stride, ... from the
 // CTA's counter until none is left.
-__device__ void raster_phase(const Params& p, CtaShared& sh, const Scratch& sc, char* uni, const SmemLayout& L,
+__device__ void raster_phase(const Params& p, CtaShared& sh, const Scratch& sc, const SmemPtrs& sp, const SmemLayout& L,
                              int first = 0, int stride = 1) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  char* wbase = uni + (size_t)warp * L.w_bytes;
+  char* wbase = sp.uni + (size_t)warp * L.w_bytes;
   while (true) {
     int k = 0;
     if (lane == 0) k = atomicAdd(&sh.next_tile, 1);
     const int t = first + stride * __shfl_sync(kFull, k, 0);
     if (t >= sh.im.n_tiles) break;
-    raster_tile_warp(p, sh, sc, t, wbase, L);
+    raster_tile_warp(p, sh, sc, t, wbase, L, sp.spans);
   }
   __syncthreads();
 }
-
-struct SmemPtrs {
-  int* mprefix;
-  int* tprefix;
-  char* uni;
-};
 
 __device__ inline SmemLayout layout_of(const Params& p) {
   return smem_layout(blockDim.x, p.tile_w, p.tile_h, p.inst_max, p.max_tiles, p.w_max);
@@ -992,6 +1066,7 @@ __device__ inline SmemPtrs carve(char* smem, const Params& p, const SmemLayout& 
   s.mprefix = reinterpret_cast<int*>(smem);
   s.tprefix = s.mprefix + (p.inst_max + 2);
   s.uni = smem + L.uni;
+  s.spans = reinterpret_cast<uint32_t*>(smem + L.spans);
   return s;
 }
 
@@ -1004,10 +1079,10 @@ constexpr long long kSpinBudget = 2000000000ll;
 // the records, so it needs no fence); a helper claims with compare-and-swap, so it never
 // takes a tile of a later image that reused the slot, and publishes each finished tile
 // in the slot's counter after a fence.
-__device__ void raster_claimed(const Params& p, CtaShared& sh, const Scratch& sc, char* uni, const SmemLayout& L,
+__device__ void raster_claimed(const Params& p, CtaShared& sh, const Scratch& sc, const SmemPtrs& sp, const SmemLayout& L,
                                int cam, bool owner) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  char* wbase = uni + (size_t)warp * L.w_bytes;
+  char* wbase = sp.uni + (size_t)warp * L.w_bytes;
   unsigned long long* word = sc.claim();
   const unsigned long long tag = (unsigned long long)(cam + 1) << 32;
   const int n_tiles = sh.im.n_tiles;
@@ -1032,7 +1107,7 @@ __device__ void raster_claimed(const Params& p, CtaShared& sh, const Scratch& sc
     }
     t = __shfl_sync(kFull, t, 0);
     if (t >= n_tiles) break;
-    raster_tile_warp(p, sh, sc, t, wbase, L);
+    raster_tile_warp(p, sh, sc, t, wbase, L, sp.spans);
     mine++;
     if (!owner && lane == 0) {
       __threadfence();
@@ -1064,6 +1139,7 @@ __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
       __syncthreads();
       int* counts = p.max_tiles > kSmemCountTiles ? sc.counts : reinterpret_cast<int*>(sp.uni);
       bin_phase(p, sh, counts, counts + (p.max_tiles + 2), sc);
+      big_spans(p, sh, sc, sp.spans);  // the barrier below publishes the table
       if (threadIdx.x == 0) {  // open the raster phase to helpers
         sc.header[3] = sh.n_big;
         sc.header[4] = 0;
@@ -1073,7 +1149,7 @@ __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
         atomicExch(sc.claim(), (unsigned long long)(cam + 1) << 32);
       }
       __syncthreads();
-      raster_claimed(p, sh, sc, sp.uni, L, cam, true);
+      raster_claimed(p, sh, sc, sp, L, cam, true);
       if (threadIdx.x == 0) {  // close it and wait for helpers still on its other tiles
         atomicExch(sc.claim(), 0ull);
         const unsigned helped = unsigned(sh.im.n_tiles - sh.next_tile);
@@ -1146,7 +1222,9 @@ __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
       setup_image(p, cam, sh, sp.mprefix, sp.tprefix, false);
       if (threadIdx.x == 0) sh.n_big = *reinterpret_cast<volatile int*>(o.header + 3);
       __syncthreads();
-      raster_claimed(p, sh, o, sp.uni, L, cam, false);
+      big_spans(p, sh, o, sp.spans);
+      __syncthreads();
+      raster_claimed(p, sh, o, sp, L, cam, false);
     }
     __syncthreads();
   }
@@ -1209,7 +1287,9 @@ __global__ void __launch_bounds__(512, 2) plain_raster_kernel(Params p) {
   setup_image(p, cam, sh, sp.mprefix, sp.tprefix, false);
   if (threadIdx.x == 0) sh.n_big = sc.header[3];
   __syncthreads();
-  raster_phase(p, sh, sc, sp.uni, L, blockIdx.y, gridDim.y);
+  big_spans(p, sh, sc, sp.spans);
+  __syncthreads();
+  raster_phase(p, sh, sc, sp, L, blockIdx.y, gridDim.y);
 }
 
 // Scratch of orrb_render_batch_noalloc: a file-scope device array, so that
