@@ -60,12 +60,12 @@ struct ImageInfo {
   int n_lights, light_type;
   float scale;
   float amb[3], bg[3];
-  float lv[kMaxLights][4];  // view-space light position (point) or direction to the light, intensity
+  alignas(16) float lv[kMaxLights][4];  // view-space light position (point) or direction to the light, intensity
 };
 
 struct CtaShared {
   ImageInfo im;
-  float mat[kMaxMaterials][5];
+  alignas(16) float mat[kMaxMaterials][8];  // albedo rgb, specular, shininess (padded: two vector loads)
   int n_vis, n_big, next_tile, next_job, img;
   int help_slot, help_cam;
   int scan_tmp[33];
@@ -275,7 +275,7 @@ __device__ void setup_image(const Params& p, int cam, CtaShared& sh, int* mprefi
     im.scale = exp2f(p.exposure_ev[im.s]);
   }
   for (int k = tid; k < kMaxMaterials * 5; k += blockDim.x)
-    sh.mat[k / 5][k % 5] = p.material[(size_t)im.s * kMaxMaterials * 5 + k];
+    sh.mat[k / 5][k % 5] = p.material[(size_t)im.s * kMaxMaterials * 5 + k];  // (columns 5-7 unused)
   if (!tables) {
     __syncthreads();
     return;
@@ -742,7 +742,8 @@ __device__ void big_spans(const Params& p, const CtaShared& sh, const Scratch& s
 
 __device__ void shade(const CtaShared& sh, const float P[3], const float n[3], int mat, float rgb[3]) {
   const ImageInfo& im = sh.im;
-  const float* m = sh.mat[mat];
+  const float4 ma = *reinterpret_cast<const float4*>(sh.mat[mat]);
+  const float m[5] = {ma.x, ma.y, ma.z, ma.w, sh.mat[mat][4]};
   float Vv[3];
   if (im.ortho) {
     Vv[0] = 0.0f;
@@ -760,13 +761,14 @@ __device__ void shade(const CtaShared& sh, const float P[3], const float n[3], i
     if (l >= im.n_lights) break;
     float L[3], E;
     if (im.light_type == 0) {
-      float Lv0 = im.lv[l][0] - P[0], Lv1 = im.lv[l][1] - P[1], Lv2 = im.lv[l][2] - P[2];
+      const float4 lq = *reinterpret_cast<const float4*>(im.lv[l]);
+      float Lv0 = lq.x - P[0], Lv1 = lq.y - P[1], Lv2 = lq.z - P[2];
       float d2 = Lv0 * Lv0 + Lv1 * Lv1 + Lv2 * Lv2;
       float r = rsqrtf(d2);
       L[0] = Lv0 * r;
       L[1] = Lv1 * r;
       L[2] = Lv2 * r;
-      E = im.lv[l][3] * (r * r);
+      E = lq.w * (r * r);
     } else {
       L[0] = im.lv[l][0];
       L[1] = im.lv[l][1];

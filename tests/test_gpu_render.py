@@ -173,3 +173,43 @@ def test_maximum_sizes(oracle):
     o = oracle.render(b, debug=True)
     st = compare(g, o, "max sizes")
     assert (o["seg"] > 2).sum() > 1000      # many of the 1023 small instances are visible
+
+
+def _fan_mesh(rim_px, centre_px=(100.5, 100.5), W=200, H=200, px_per_m=16.0):
+    """Coplanar fan (z = 0) whose vertices project exactly onto the given pixel centres of an
+    orthographic W x H camera at px_per_m (x_s = W/2 + f x, y_s = H/2 - f y); each triangle is
+    listed in both windings, so exactly one copy faces the camera."""
+    def world(u, v):
+        return ((u - 0.5 * W) / px_per_m, (0.5 * H - v) / px_per_m, 0.0)
+    pos = [world(*centre_px)] + [world(u, v) for u, v in rim_px]
+    tris = []
+    for k in range(len(rim_px)):
+        a, b = 1 + k, 1 + (k + 1) % len(rim_px)
+        tris += [(0, a, b), (0, b, a)]
+    return sg.Mesh(pos=np.asarray(pos, np.float32), nrm=np.tile(np.float32([0, 0, 1]), (len(pos), 1)),
+                   idx=np.asarray(tris, np.uint32), tri_mat=np.zeros(len(tris), np.uint8))
+
+
+@pytest.mark.parametrize("rim", [
+    # 4 large triangles: 4 x 200 (triangle, row) pairs fit the shared-memory span table
+    [(0.5, 0.5), (199.5, 50.5), (150.5, 199.5), (0.5, 199.5)],
+    # 10 large triangles: 2000 pairs, so every pixel is tested instead
+    [(0.5, 0.5), (57.5, 0.5), (199.5, 0.5), (199.5, 13.5), (199.5, 150.5), (199.5, 199.5), (120.5, 199.5),
+     (0.5, 199.5), (0.5, 160.5), (0.5, 50.5)],
+], ids=["span-table", "per-pixel"])
+def test_large_triangles_with_edges_through_pixel_centres(oracle, rim):
+    """Large (unbinned) triangles whose edges run through pixel centres at slopes 0, 1, 1/2, vertical
+    and co-prime ones, so the top-left rule decides every pixel on a shared edge: coverage must
+    equal the oracle's exactly with the per-row span table and with per-pixel tests."""
+    meshes = [_fan_mesh(rim)]
+    r = Renderer(meshes)
+    cam = scenes.camera_down((0.0, 0.0, 4.0), 200, 200, px_per_m=16.0)
+    b = scenes.single_sample(meshes, [0], [scenes.identity_pose()], [cam], seg=[1],
+                             lights=[((0.0, 0.0, 3.0), 2.0)], background=(0.2, 0.3, 0.4))
+    o = oracle.render(b, debug=True)
+    assert (o["seg"] == 1).sum() > 0.4 * 200 * 200
+    for cfg in (config(), config(tile_w=64, tile_h=4), config(tile_w=24, tile_h=8), config(mode=L.ORRB_MODE_PLAIN)):
+        g = render_np(r, b, cfg)
+        st = compare(g, o, f"fan {len(rim)} {cfg.tile_w}x{cfg.tile_h}")
+        assert st["flips"] == 0
+        np.testing.assert_array_equal(g["seg"], o["seg"])
