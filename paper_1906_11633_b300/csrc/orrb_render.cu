@@ -581,6 +581,9 @@ __device__ __forceinline__ bool binned_span(uint2 box, const ImageInfo& im, int&
   return (tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= kMaxSpanTiles;
 }
 
+// Neighbouring visible triangles come from the same cluster and mostly share tiles, so the
+// per-tile counter updates are aggregated per warp: the lanes that hit the same tile in a
+// step (match.any) add their number with one atomic by the lowest of them.
 __device__ void bin_phase(const Params& p, CtaShared& sh, int* counts, int* cursor, const Scratch& sc) {
   const ImageInfo& im = sh.im;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -588,24 +591,30 @@ __device__ void bin_phase(const Params& p, CtaShared& sh, int* counts, int* curs
   __syncthreads();
   const int n = sh.n_vis;
   const int lane = tid & 31;
+  const unsigned below = (1u << lane) - 1u;
   for (int e0 = 0; e0 < n; e0 += nt) {
     const int e = e0 + tid;
     bool big = false;
-    if (e < n) {
-      int tx0, tx1, ty0, ty1;
-      if (binned_span(sc.vis_box[e], im, tx0, tx1, ty0, ty1)) {
-        for (int ty = ty0; ty <= ty1; ty++)
-          for (int tx = tx0; tx <= tx1; tx++) atomicAdd(&counts[ty * im.ntx + tx], 1);
-      } else {
-        big = true;
-      }
+    int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = 0;
+    if (e < n && !binned_span(sc.vis_box[e], im, tx0, tx1, ty0, ty1)) {
+      big = true;
+      tx1 = -1;
+    }
+    const int w = tx1 - tx0 + 1, cnt = w > 0 ? w * (ty1 - ty0 + 1) : 0;
+    const int steps = __reduce_max_sync(kFull, cnt);
+    int tx = tx0, ty = ty0;
+    for (int j = 0; j < steps; j++) {
+      const int tile = j < cnt ? ty * im.ntx + tx : -1;
+      const unsigned peers = __match_any_sync(kFull, tile);
+      if (tile >= 0 && (peers & below) == 0) atomicAdd(&counts[tile], __popc(peers));
+      if (++tx > tx1) tx = tx0, ty++;
     }
     // ballot compaction of the large list: one atomic per warp
     const unsigned m = __ballot_sync(kFull, big);
     int wbase = 0;
     if (lane == 0 && m) wbase = atomicAdd(&sh.n_big, __popc(m));
     wbase = __shfl_sync(kFull, wbase, 0);
-    if (big) sc.big[wbase + __popc(m & ((1u << lane) - 1u))] = sc.vis_key[e];
+    if (big) sc.big[wbase + __popc(m & below)] = sc.vis_key[e];
   }
   __syncthreads();
   block_exclusive_scan(counts, im.n_tiles, sh.scan_tmp);
@@ -614,12 +623,26 @@ __device__ void bin_phase(const Params& p, CtaShared& sh, int* counts, int* curs
     cursor[t] = counts[t];
   }
   __syncthreads();
-  for (int e = tid; e < n; e += nt) {
-    int tx0, tx1, ty0, ty1;
-    if (binned_span(sc.vis_box[e], im, tx0, tx1, ty0, ty1)) {
-      const uint32_t key = sc.vis_key[e];
-      for (int ty = ty0; ty <= ty1; ty++)
-        for (int tx = tx0; tx <= tx1; tx++) sc.bins[atomicAdd(&cursor[ty * im.ntx + tx], 1)] = key;
+  for (int e0 = 0; e0 < n; e0 += nt) {
+    const int e = e0 + tid;
+    int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = 0;
+    uint32_t key = 0;
+    if (e < n) {
+      if (binned_span(sc.vis_box[e], im, tx0, tx1, ty0, ty1)) key = sc.vis_key[e];
+      else tx1 = -1;
+    }
+    const int w = tx1 - tx0 + 1, cnt = w > 0 ? w * (ty1 - ty0 + 1) : 0;
+    const int steps = __reduce_max_sync(kFull, cnt);
+    int tx = tx0, ty = ty0;
+    for (int j = 0; j < steps; j++) {
+      const int tile = j < cnt ? ty * im.ntx + tx : -1;
+      const unsigned peers = __match_any_sync(kFull, tile);
+      const int leader = __ffs(peers) - 1;
+      int base = 0;
+      if (tile >= 0 && lane == leader) base = atomicAdd(&cursor[tile], __popc(peers));
+      base = __shfl_sync(kFull, base, leader);
+      if (tile >= 0) sc.bins[base + __popc(peers & below)] = key;
+      if (++tx > tx1) tx = tx0, ty++;
     }
   }
   __syncthreads();
