@@ -118,6 +118,7 @@ struct SmemLayout {
 struct SmemPtrs {
   int* mprefix;
   int* tprefix;
+  int* mbegin;  // per instance: its mesh's first cluster
   char* uni;
   uint32_t* spans;
 };
@@ -128,7 +129,7 @@ __host__ __device__ inline SmemLayout smem_layout(int threads, int tile_w, int t
                                                   int w_max) {
   SmemLayout L;
   const size_t tw = size_t(tile_w < w_max ? tile_w : w_max), th = size_t(tile_h);
-  L.uni = al16(size_t(2) * (inst_max + 2) * sizeof(int));
+  L.uni = al16(size_t(3) * (inst_max + 2) * sizeof(int));
   L.g_size = size_t(threads / 32) * al16(sizeof(WarpG));
   L.b_size = max_tiles > kSmemCountTiles ? 0 : al16(size_t(2) * (max_tiles + 2) * sizeof(int));
   L.w_keys = 0;
@@ -199,7 +200,8 @@ __device__ void block_exclusive_scan(int* a, int n, int* tmp) {
 // ---------------------------------------------------------------------------
 // per-image set-up (camera, lights, materials, instance tables)
 // ---------------------------------------------------------------------------
-__device__ void setup_image(const Params& p, int cam, CtaShared& sh, int* mprefix, int* tprefix, bool tables) {
+__device__ void setup_image(const Params& p, int cam, CtaShared& sh, int* mprefix, int* tprefix, int* mbegin,
+                            bool tables) {
   ImageInfo& im = sh.im;
   const int tid = threadIdx.x;
   if (tid == 0) {
@@ -287,10 +289,12 @@ __device__ void setup_image(const Params& p, int cam, CtaShared& sh, int* mprefi
       flag_status(p, ORRB_DEV_BAD_INSTANCE);
       mprefix[i] = 0;
       tprefix[i] = 0;
+      mbegin[i] = 0;
     } else {
       MeshEntry me = p.meshes[mesh];
       mprefix[i] = me.meshlet_count;
       tprefix[i] = me.n_tris;
+      mbegin[i] = me.meshlet_begin;
     }
   }
   __syncthreads();
@@ -442,8 +446,8 @@ __device__ __noinline__ int clip_triangle(int t_max, Record* rec, const ImageInf
 // ---------------------------------------------------------------------------
 // phase G: geometry of one image
 // ---------------------------------------------------------------------------
-__device__ void geometry_phase(const Params& p, CtaShared& sh, const int* mprefix, const int* tprefix, WarpG* wgs,
-                               const Scratch& sc) {
+__device__ void geometry_phase(const Params& p, CtaShared& sh, const int* mprefix, const int* tprefix,
+                               const int* mbegin, WarpG* wgs, const Scratch& sc) {
   const ImageInfo& im = sh.im;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   WarpG* wg = wgs + warp;
@@ -461,8 +465,9 @@ __device__ void geometry_phase(const Params& p, CtaShared& sh, const int* mprefi
       else hi = mid;
     }
     const int inst = im.inst0 + lo;
-    const MeshEntry me = p.meshes[p.inst_mesh[inst]];
-    const MeshletEntry ml = p.meshlets[me.meshlet_begin + (j - mprefix[lo])];
+    const MeshletEntry ml = p.meshlets[mbegin[lo] + (j - mprefix[lo])];
+    const int mat_base = p.inst_mat_base[inst];  // loads issued before the transform that follows
+    const int seg = p.inst_seg[inst];
     if (lane < 12) {
       const int r = lane >> 2, c = lane & 3;
       const float* M = p.inst_pose + (size_t)inst * 12;
@@ -495,8 +500,6 @@ __device__ void geometry_phase(const Params& p, CtaShared& sh, const int* mprefi
     }
     __syncwarp();
     const int prim_base = tprefix[lo] + ml.mesh_tri_base;
-    const int mat_base = p.inst_mat_base[inst];
-    const int seg = p.inst_seg[inst];
     for (int base = 0; base < nt; base += 32) {
       const int t = base + lane;
       unsigned key0 = 0, key1 = 0;   // registers: the clip path writes its own arrays
@@ -1090,6 +1093,7 @@ __device__ inline SmemPtrs carve(char* smem, const Params& p, const SmemLayout& 
   SmemPtrs s;
   s.mprefix = reinterpret_cast<int*>(smem);
   s.tprefix = s.mprefix + (p.inst_max + 2);
+  s.mbegin = s.tprefix + (p.inst_max + 2);
   s.uni = smem + L.uni;
   s.spans = reinterpret_cast<uint32_t*>(smem + L.spans);
   return s;
@@ -1158,9 +1162,9 @@ __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
     __syncthreads();
     const int cam = sh.img;
     if (cam >= p.n_cams) break;
-    setup_image(p, cam, sh, sp.mprefix, sp.tprefix, true);
+    setup_image(p, cam, sh, sp.mprefix, sp.tprefix, sp.mbegin, true);
     if (sh.im.valid) {
-      geometry_phase(p, sh, sp.mprefix, sp.tprefix, reinterpret_cast<WarpG*>(sp.uni), sc);
+      geometry_phase(p, sh, sp.mprefix, sp.tprefix, sp.mbegin, reinterpret_cast<WarpG*>(sp.uni), sc);
       __syncthreads();
       int* counts = p.max_tiles > kSmemCountTiles ? sc.counts : reinterpret_cast<int*>(sp.uni);
       bin_phase(p, sh, counts, counts + (p.max_tiles + 2), sc);
@@ -1244,7 +1248,7 @@ __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
     if (slot >= 0 && cam >= 0) {
       const Scratch o = slot_scratch(p, slot);
       __threadfence();
-      setup_image(p, cam, sh, sp.mprefix, sp.tprefix, false);
+      setup_image(p, cam, sh, sp.mprefix, sp.tprefix, sp.mbegin, false);
       if (threadIdx.x == 0) sh.n_big = *reinterpret_cast<volatile int*>(o.header + 3);
       __syncthreads();
       big_spans(p, sh, o, sp.spans);
@@ -1272,12 +1276,12 @@ __global__ void __launch_bounds__(512, 2) plain_geometry_kernel(Params p) {
   const SmemLayout L = layout_of(p);
   SmemPtrs sp = carve(smem, p, L);
   const Scratch sc = slot_scratch(p, blockIdx.x);
-  setup_image(p, cam, sh, sp.mprefix, sp.tprefix, true);
+  setup_image(p, cam, sh, sp.mprefix, sp.tprefix, sp.mbegin, true);
   if (!sh.im.valid) {
     if (threadIdx.x == 0) sc.header[2] = -1;
     return;
   }
-  geometry_phase(p, sh, sp.mprefix, sp.tprefix, reinterpret_cast<WarpG*>(sp.uni), sc);
+  geometry_phase(p, sh, sp.mprefix, sp.tprefix, sp.mbegin, reinterpret_cast<WarpG*>(sp.uni), sc);
   __syncthreads();
   if (threadIdx.x == 0) sc.header[2] = sh.n_vis;
 }
@@ -1290,7 +1294,7 @@ __global__ void __launch_bounds__(512, 2) plain_bin_kernel(Params p) {
   const SmemLayout L = layout_of(p);
   SmemPtrs sp = carve(smem, p, L);
   const Scratch sc = slot_scratch(p, blockIdx.x);
-  setup_image(p, cam, sh, sp.mprefix, sp.tprefix, false);
+  setup_image(p, cam, sh, sp.mprefix, sp.tprefix, sp.mbegin, false);
   const int nvis = sc.header[2];
   if (nvis < 0) return;
   if (threadIdx.x == 0) sh.n_vis = nvis;
@@ -1309,7 +1313,7 @@ __global__ void __launch_bounds__(512, 2) plain_raster_kernel(Params p) {
   if (sc.header[2] < 0) return;
   const SmemLayout L = layout_of(p);
   SmemPtrs sp = carve(smem, p, L);
-  setup_image(p, cam, sh, sp.mprefix, sp.tprefix, false);
+  setup_image(p, cam, sh, sp.mprefix, sp.tprefix, sp.mbegin, false);
   if (threadIdx.x == 0) sh.n_big = sc.header[3];
   __syncthreads();
   big_spans(p, sh, sc, sp.spans);
