@@ -13,19 +13,22 @@
 //      slot fixed by its primitive id, and appends (key, pixel box) to the
 //      image's visible list with a warp prefix scan and one atomic per warp.
 //   B  binning: triangles that touch at most 64 screen tiles are counted per
-//      tile, the counts are prefix-summed and the keys scattered into
-//      per-tile bins; the rest go to a "large" list that every tile tests
-//      itself (in practice the table plane).
+//      tile (the lanes of a warp that hit the same tile share one atomic), the
+//      counts are prefix-summed and the keys scattered into per-tile bins; the
+//      rest go to a "large" list that every tile tests itself (in practice the
+//      table plane), whose exact covered interval per image row is tabulated in
+//      shared memory when it fits.
 //   R  raster + shade: each warp owns one tile at a time (default: one image
 //      row), claiming tiles from the image's counter, with its depth keys in
-//      warp-private shared memory, so the phase needs no CTA-wide barrier.  Large triangles: lanes split the triangle's box.
-//      Binned triangles: 32 at a time, their boxes prefix-summed and the
-//      (triangle, pixel) candidates spread evenly over the lanes, each
-//      covered centre folding (depth bits << 32 | key) into the tile's keys
-//      with a shared-memory 64-bit atomicMin.  Then every pixel resolves its
-//      winner, interpolates the normal, shades (Blinn-Phong, point or
-//      directional lights, exposure) and writes the four channels, consecutive
-//      lanes on consecutive pixels of a row.
+//      warp-private shared memory, so the phase needs no CTA-wide barrier.
+//      Large triangles: the lanes walk the covered pixels of each row.  Binned
+//      triangles: 32 at a time, their boxes prefix-summed and the (triangle,
+//      pixel) candidates spread evenly over the lanes (each finds its triangle
+//      from a ballot of the starts), each covered centre folding (depth bits
+//      << 32 | key) into the tile's keys with a shared-memory 64-bit atomicMin.
+//      Then every pixel resolves its winner, interpolates the normal, shades
+//      (Blinn-Phong, point or directional lights, exposure) and writes the
+//      four channels, consecutive lanes on consecutive pixels of a row.
 //
 // Everything that decides coverage, visibility or depth (transform, clip,
 // projection, snapping, edge functions, depth) uses explicitly rounded fp32
