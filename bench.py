@@ -46,6 +46,12 @@ CONFIG = {"workload": "hand-like scene: 256 samples x 3 cameras x 200x200, 24 ca
           "resolution": RES, "tris_per_sample": 24 * 320 + 14, "l2": "flushed between timed steps (256 MB write)"}
 
 
+def set_samples(n: int) -> None:
+    global N_SAMPLES, CONFIG
+    N_SAMPLES = n
+    CONFIG = dict(CONFIG, workload=CONFIG["workload"].replace("256 samples", f"{n} samples"), global_batch=n)
+
+
 def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
@@ -544,9 +550,13 @@ def main():
     ap.add_argument("--workload", choices=["hand", "uneven", "diff", "serve"], default="hand",
                     help="hand: the headline line; the others print supplementary lines")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--samples", type=int, default=N_SAMPLES,
+                    help="hand samples per step (smaller batches for profiler captures; the headline is 256)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.samples != N_SAMPLES:
+        set_samples(args.samples)
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
