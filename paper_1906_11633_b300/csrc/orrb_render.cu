@@ -928,8 +928,36 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
       }
       T.px0 = max(x0, int(box.x & 0xffff));
       T.py0 = max(y0, int(box.y & 0xffff));
-      const int bw = min(x0 + cw - 1, int(box.x >> 16)) - T.px0 + 1;
+      int bw = min(x0 + cw - 1, int(box.x >> 16)) - T.px0 + 1;
       const int bh = min(y0 + ch - 1, int((box.y >> 16) & 0xfff)) - T.py0 + 1;
+      if (ch == 1 && (T.flags & 8) && bw > 0 && bh > 0) {
+        // one-row tile, small triangle: keep only the columns whose centres lie within 2/256 px
+        // of the triangle's extent along the row (float, relative to vertex 0, where every
+        // coordinate is exact and each crossing is within 0.02/256 px); the exact edge test
+        // still decides every remaining candidate
+        const float cyr = float(256 * y0 + 128 - T.Y[0]);
+        const float vx[3] = {0.0f, float(T.X[1]), float(T.X[2])}, vy[3] = {0.0f, float(T.Y[1]), float(T.Y[2])};
+        float xl = 3.0e38f, xr = -3.0e38f;
+#pragma unroll
+        for (int e = 0; e < 3; e++) {
+          const int e2 = e == 2 ? 0 : e + 1;
+          const float ya = vy[e], yb = vy[e2], xa = vx[e], xb = vx[e2];
+          const bool cross = fminf(ya, yb) <= cyr && cyr <= fmaxf(ya, yb);
+          const float x = ya == yb ? xa : fmaf(cyr - ya, __fdividef(xb - xa, yb - ya), xa);
+          const float xo = ya == yb ? xb : x;
+          xl = cross ? fminf(xl, fminf(x, xo)) : xl;
+          xr = cross ? fmaxf(xr, fmaxf(x, xo)) : xr;
+        }
+        const float c0 = float(256 * T.px0 + 128 - T.X[0]);  // column bw's first centre, relative
+        const int jl = max(0, int(ceilf((xl - 2.0f - c0) * (1.0f / 256.0f))));
+        const int jr = min(bw - 1, int(floorf((xr + 2.0f - c0) * (1.0f / 256.0f))));
+        if (xl > xr || jl > jr) {
+          bw = 0;
+        } else {
+          T.px0 += jl;
+          bw = jr - jl + 1;
+        }
+      }
       T.bw = bw;
       cnt = (bw > 0 && bh > 0) ? bw * bh : 0;
     }
