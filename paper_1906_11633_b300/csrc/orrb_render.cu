@@ -1147,11 +1147,14 @@ __device__ void raster_claimed(const Params& p, CtaShared& sh, const Scratch& sc
   const unsigned long long tag = (unsigned long long)(cam + 1) << 32;
   const int n_tiles = sh.im.n_tiles;
   int mine = 0;
+  unsigned long long next = 0;  // the owner claims its next tile before rastering the current one
+  if (owner && lane == 0) next = atomicAdd(word, 1ull);
   while (true) {
     int t = 0;
     if (lane == 0) {
       if (owner) {
-        t = int(unsigned(atomicAdd(word, 1ull)));
+        t = int(unsigned(next));
+        if (t < n_tiles) next = atomicAdd(word, 1ull);
       } else {
         t = n_tiles;
         unsigned long long w = atomicAdd(word, 0ull);

@@ -213,3 +213,47 @@ def test_large_triangles_with_edges_through_pixel_centres(oracle, rim):
         st = compare(g, o, f"fan {len(rim)} {cfg.tile_w}x{cfg.tile_h}")
         assert st["flips"] == 0
         np.testing.assert_array_equal(g["seg"], o["seg"])
+
+
+def test_slivers_on_pixel_centre_rows(oracle):
+    """Small binned triangles on one-row tiles, where each row's candidate columns are narrowed
+    to the triangle's float extent along the row: slivers (nearly horizontal and nearly
+    vertical), vertices exactly on pixel-centre rows and columns, and sub-pixel triangles must
+    cover exactly the oracle's pixels."""
+    rng = np.random.default_rng(5)
+    W = H = 96
+    f = 16.0
+
+    def world(u, v, z):
+        return ((u - 0.5 * W) / f, (0.5 * H - v) / f, z)
+
+    pos, tris = [], []
+    for k in range(600):
+        cu, cv = rng.uniform(2, W - 2), rng.uniform(2, H - 2)
+        kind = k % 4
+        if kind == 0:      # on pixel-centre rows/columns
+            cu, cv = np.floor(cu) + 0.5, np.floor(cv) + 0.5
+            d = rng.integers(-6, 7, size=(2, 2)) + 0.0
+        elif kind == 1:    # nearly horizontal sliver
+            d = np.array([[rng.uniform(-8, 8), rng.uniform(-0.05, 0.05)], [rng.uniform(-8, 8), rng.uniform(-0.6, 0.6)]])
+        elif kind == 2:    # nearly vertical sliver
+            d = np.array([[rng.uniform(-0.05, 0.05), rng.uniform(-8, 8)], [rng.uniform(-0.6, 0.6), rng.uniform(-8, 8)]])
+        else:              # sub-pixel
+            d = rng.uniform(-0.8, 0.8, size=(2, 2))
+        z = -0.001 * k
+        i = len(pos)
+        pos += [world(cu, cv, z), world(cu + d[0, 0], cv + d[0, 1], z), world(cu + d[1, 0], cv + d[1, 1], z)]
+        tris += [(i, i + 1, i + 2), (i, i + 2, i + 1)]     # one winding faces the camera
+    mesh = sg.Mesh(pos=np.asarray(pos, np.float32), nrm=np.tile(np.float32([0, 0, 1]), (len(pos), 1)),
+                   idx=np.asarray(tris, np.uint32), tri_mat=np.zeros(len(tris), np.uint8))
+    r = Renderer([mesh])
+    cam = scenes.camera_down((0.0, 0.0, 4.0), W, H, px_per_m=f)
+    b = scenes.single_sample([mesh], [0], [scenes.identity_pose()], [cam], seg=[1],
+                             lights=[((0.0, 0.0, 3.0), 2.0)], background=(0.2, 0.3, 0.4))
+    o = oracle.render(b, debug=True)
+    assert (o["seg"] == 1).sum() > 500
+    for cfg in (config(), config(tile_w=64, tile_h=2)):
+        g = render_np(r, b, cfg)
+        compare(g, o, f"slivers {cfg.tile_w}x{cfg.tile_h}")
+        np.testing.assert_array_equal(g["seg"], o["seg"])
+        np.testing.assert_array_equal(g["depth"], o["depth"])
