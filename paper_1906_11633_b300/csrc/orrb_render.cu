@@ -784,44 +784,41 @@ __device__ void shade(const CtaShared& sh, const float P[3], const float n[3], i
     Vv[1] = -P[1] * rl;
     Vv[2] = -P[2] * rl;
   }
-  float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
+  // diffuse and specular irradiance summed over the lights, the albedo applied once:
+  // rgb_k = scale * (m_k * (ambient_k + sum E ndl) + sum E spec)
+  float D = 0.0f, S = 0.0f;
 #pragma unroll
   for (int l = 0; l < kMaxLights; l++) {
     if (l >= im.n_lights) break;
-    float L[3], E;
+    const float4 lq = *reinterpret_cast<const float4*>(im.lv[l]);
+    float Lx, Ly, Lz, r, E;  // (Lx, Ly, Lz) * r is the unit vector to the light
     if (im.light_type == 0) {
-      const float4 lq = *reinterpret_cast<const float4*>(im.lv[l]);
-      float Lv0 = lq.x - P[0], Lv1 = lq.y - P[1], Lv2 = lq.z - P[2];
-      float d2 = Lv0 * Lv0 + Lv1 * Lv1 + Lv2 * Lv2;
-      float r = rsqrtf(d2);
-      L[0] = Lv0 * r;
-      L[1] = Lv1 * r;
-      L[2] = Lv2 * r;
+      Lx = lq.x - P[0];
+      Ly = lq.y - P[1];
+      Lz = lq.z - P[2];
+      r = rsqrtf(Lx * Lx + Ly * Ly + Lz * Lz);
       E = lq.w * (r * r);
     } else {
-      L[0] = im.lv[l][0];
-      L[1] = im.lv[l][1];
-      L[2] = im.lv[l][2];
-      E = im.lv[l][3];
+      Lx = lq.x;
+      Ly = lq.y;
+      Lz = lq.z;
+      r = 1.0f;
+      E = lq.w;
     }
-    float ndl = fmaxf(0.0f, n[0] * L[0] + n[1] * L[1] + n[2] * L[2]);
-    float spec = 0.0f;
+    const float ndl = fmaxf(0.0f, (n[0] * Lx + n[1] * Ly + n[2] * Lz) * r);
+    D = fmaf(E, ndl, D);
     if (ndl > 0.0f && m[3] != 0.0f) {
-      float H0 = L[0] + Vv[0], H1 = L[1] + Vv[1], H2 = L[2] + Vv[2];
-      float h2 = H0 * H0 + H1 * H1 + H2 * H2;
+      const float H0 = fmaf(Lx, r, Vv[0]), H1 = fmaf(Ly, r, Vv[1]), H2 = fmaf(Lz, r, Vv[2]);
+      const float h2 = H0 * H0 + H1 * H1 + H2 * H2;
       if (h2 > 0.0f) {
-        float rh = rsqrtf(h2);
-        float ndh = fmaxf(0.0f, (n[0] * H0 + n[1] * H1 + n[2] * H2) * rh);
-        spec = m[3] * lobe_pow(ndh, m[4]);
+        const float ndh = fmaxf(0.0f, (n[0] * H0 + n[1] * H1 + n[2] * H2) * rsqrtf(h2));
+        S = fmaf(E, m[3] * lobe_pow(ndh, m[4]), S);
       }
     }
-    c0 += E * (m[0] * ndl + spec);
-    c1 += E * (m[1] * ndl + spec);
-    c2 += E * (m[2] * ndl + spec);
   }
-  rgb[0] = im.scale * (im.amb[0] * m[0] + c0);
-  rgb[1] = im.scale * (im.amb[1] * m[1] + c1);
-  rgb[2] = im.scale * (im.amb[2] * m[2] + c2);
+  rgb[0] = im.scale * fmaf(m[0], im.amb[0] + D, S);
+  rgb[1] = im.scale * fmaf(m[1], im.amb[1] + D, S);
+  rgb[2] = im.scale * fmaf(m[2], im.amb[2] + D, S);
 }
 
 // floor(clamp(v, 0, 1) * 255 + 0.5) with one rounding of the multiply-add (NaN -> 0)
