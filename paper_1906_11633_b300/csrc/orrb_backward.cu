@@ -48,7 +48,8 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-__global__ void __launch_bounds__(kBwdThreads) backward_partial_kernel(BackwardParams bp) {
+// 4 CTAs (32 warps) per SM: the per-pixel loads need the occupancy more than the adjoint needs registers
+__global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(BackwardParams bp) {
   const Params& p = bp.base;
   __shared__ BwdShared sh;
   const int cam = blockIdx.x, blk = blockIdx.y;
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(kBwdThreads) backward_partial_kernel(BackwardP
         }
         const float G = g[0] + g[1] + g[2];
         const float gr = g[0] * m[0] + g[1] * m[1] + g[2] * m[2];
-        float sum_endl = 0.0f, sum_epw = 0.0f, acc[3] = {0.0f, 0.0f, 0.0f};
+        float sum_endl = 0.0f, sum_epw = 0.0f;
 #pragma unroll
         for (int l = 0; l < kMaxLights; l++) {
           if (l >= sh.n_lights) break;
@@ -151,13 +152,12 @@ __global__ void __launch_bounds__(kBwdThreads) backward_partial_kernel(BackwardP
             }
           }
           const float spec = m[3] * pw;
-          for (int k = 0; k < 3; k++) acc[k] += E * (m[k] * ndl + spec);
           sum_endl += E * ndl;
           sum_epw += E * pw;
           const float dE = scale * (gr * ndl + G * spec);
           const float dndl = lit ? scale * E * gr : 0.0f;
-          // alpha * ndh^(alpha - 1) = alpha * pw / ndh for ndh > 0
-          const float dndh = (has_h && ndh > 0.0f) ? scale * E * G * m[3] * m[4] * (pw / ndh) : 0.0f;
+          // alpha * ndh^(alpha - 1) = alpha * pw / ndh for ndh > 0 (fast division: ~2 ulp)
+          const float dndh = (has_h && ndh > 0.0f) ? scale * E * G * m[3] * m[4] * __fdividef(pw, ndh) : 0.0f;
           float dL[3] = {dndl * n[0], dndl * n[1], dndl * n[2]};
           if (dndh != 0.0f) {
             float dH[3] = {dndh * n[0], dndh * n[1], dndh * n[2]};
@@ -176,9 +176,11 @@ __global__ void __launch_bounds__(kBwdThreads) backward_partial_kernel(BackwardP
         }
         for (int k = 0; k < 3; k++) dm[k] = g[k] * scale * (sh.amb[k] + sum_endl);
         dm[3] = scale * G * sum_epw;
-        float e = 0.0f;
-        for (int k = 0; k < 3; k++) e += g[k] * scale * (sh.amb[k] * m[k] + acc[k]);
-        dev += ln2 * e;
+        // d rgb_k / d ev = ln 2 * rgb_k, and sum_k g_k rgb_k / scale
+        //   = sum_k g_k amb_k m_k + (g . m) sum E ndl + (sum g) k_s sum E pw
+        const float e = g[0] * sh.amb[0] * m[0] + g[1] * sh.amb[1] * m[1] + g[2] * sh.amb[2] * m[2] +
+                        gr * sum_endl + G * m[3] * sum_epw;
+        dev += ln2 * scale * e;
       }
     }
     // segmented warp reduction over the materials present in these 32 pixels
