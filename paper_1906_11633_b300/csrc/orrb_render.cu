@@ -82,6 +82,7 @@ struct WarpG {  // per-warp cluster staging for phase G
   int Y[kMeshletVerts];
   float iw[kMeshletVerts];
   int flag[kMeshletVerts];  // bit 0: in front of the near plane; bit 1: inside the guard band
+  uint32_t tri[kMeshletTris];  // the cluster's packed triangles
 };
 
 struct WarpTri {  // a binned triangle staged for the warp's fragment expansion (64 B)
@@ -482,9 +483,26 @@ __device__ void geometry_phase(const Params& p, CtaShared& sh, const int* mprefi
     }
     __syncwarp();
     const int nv = ml.counts & 0xffff, nt = ml.counts >> 16;
-    for (int v = lane; v < nv; v += 32) {
-      const float4 P = p.vpos[ml.vert_begin + v];
-      const float4 N = p.vnrm[ml.vert_begin + v];
+    // the cluster's triangle words and its vertices are all requested before any is used
+    static_assert(kMeshletTris == 128 && kMeshletVerts == 64, "prefetch assumes 4 triangle and 2 vertex rounds");
+    uint32_t tq[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) tq[i] = i * 32 + lane < nt ? p.tris[ml.tri_begin + i * 32 + lane] : 0u;
+    float4 Pq[2], Nq[2];
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+      const int v = i * 32 + lane;
+      Pq[i] = v < nv ? p.vpos[ml.vert_begin + v] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      Nq[i] = v < nv ? p.vnrm[ml.vert_begin + v] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++) wg->tri[i * 32 + lane] = tq[i];
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+      const int v = i * 32 + lane;
+      if (v >= nv) break;
+      const float4 P = Pq[i];
+      const float4 N = Nq[i];
       float pc[3];
       for (int r = 0; r < 3; r++) {
         const float* m = &wg->mv[r * 4];
@@ -509,7 +527,7 @@ __device__ void geometry_phase(const Params& p, CtaShared& sh, const int* mprefi
       uint2 box0 = make_uint2(0, 0), box1 = make_uint2(0, 0);
       int cnt = 0;
       if (t < nt) {
-        const uint32_t tri = p.tris[ml.tri_begin + t];
+        const uint32_t tri = wg->tri[t];
         const int vi[3] = {int(tri & 0xff), int((tri >> 8) & 0xff), int((tri >> 16) & 0xff)};
         int mat = mat_base + int(tri >> 24);
         if (mat < 0 || mat >= kMaxMaterials) {
