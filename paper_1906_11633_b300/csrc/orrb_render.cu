@@ -1020,6 +1020,8 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
     float* depth_row = p.depth ? p.depth + orow : nullptr;
     uint8_t* seg_row = p.seg ? p.seg + orow : nullptr;
     const unsigned long long* krow = keys + ly * cw;
+    unsigned last = 0xffffffffu;  // the lane's previous winner and its material/segment/normal word
+    int4 last_q3 = make_int4(0, 0, 0, 0);
     for (int lx = lane; lx < cw; lx += 32) {
       const int px = x0 + lx;
       const unsigned long long kk = krow[lx];
@@ -1032,7 +1034,11 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
       } else {
         depth = __uint_as_float(unsigned(kk >> 32));
         const Record* r = rec_of(p, sc, unsigned(kk));
-        const int4 q3 = reinterpret_cast<const int4*>(r)[3];
+        if (unsigned(kk) != last) {  // 32 pixels apart, a lane often meets the same (large) triangle again
+          last = unsigned(kk);
+          last_q3 = reinterpret_cast<const int4*>(r)[3];
+        }
+        const int4 q3 = last_q3;
         mat = q3.x & 0xffff;
         seg = (q3.x >> 16) & 0xff;
         if (q3.x & (1 << 24)) {  // flat face: the normalised interpolated normal is the (unit) vertex normal
