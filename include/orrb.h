@@ -174,9 +174,9 @@ typedef struct {
 
 typedef struct {
   int32_t mode;          /* ORRB_MODE_FUSED or ORRB_MODE_PLAIN */
-  int32_t tile_w;        /* screen-tile width in pixels, multiple of 8 in [8, 512]; 0 = 512 */
-  int32_t tile_h;        /* screen-tile height in pixels, in [1, 64]; 0 = 8 */
-  int32_t threads;       /* threads per CTA: 256, 512 or 1024; 0 = 512 */
+  int32_t tile_w;        /* screen-tile width in pixels, multiple of 8 in [8, 512]; 0 = 256 (a narrower image uses its width) */
+  int32_t tile_h;        /* screen-tile height in pixels, in [1, 64], tile_w * tile_h <= 8192; 0 = 2 */
+  int32_t threads;       /* threads per CTA: 256 or 512; 0 = 512 */
   int32_t ctas_per_sm;   /* fused mode: resident CTAs per SM; 0 = as many as fit */
 } orrb_config;
 

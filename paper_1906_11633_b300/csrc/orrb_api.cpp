@@ -164,7 +164,7 @@ void resolve_config(const orrb_config* in, orrb_config* out) {
   orrb_config c{};
   if (in) c = *in;
   if (c.tile_w == 0) c.tile_w = 256;
-  if (c.tile_h == 0) c.tile_h = 1;
+  if (c.tile_h == 0) c.tile_h = 2;
   if (c.threads == 0) c.threads = 512;
   *out = c;
 }

@@ -18,8 +18,8 @@
 //      rest go to a "large" list that every tile tests itself (in practice the
 //      table plane), whose exact covered interval per image row is tabulated in
 //      shared memory when it fits.
-//   R  raster + shade: each warp owns one tile at a time (default: one image
-//      row), claiming tiles from the image's counter, with its depth keys in
+//   R  raster + shade: each warp owns one tile at a time (default: two image
+//      rows), claiming tiles from the image's counter, with its depth keys in
 //      warp-private shared memory, so the phase needs no CTA-wide barrier.
 //      Large triangles: the lanes walk the covered pixels of each row.  Binned
 //      triangles: 32 at a time, their boxes prefix-summed and the (triangle,
@@ -85,13 +85,15 @@ struct WarpG {  // per-warp cluster staging for phase G
   uint32_t tri[kMeshletTris];  // the cluster's packed triangles
 };
 
-struct WarpTri {  // a binned triangle staged for the warp's fragment expansion (64 B)
+struct WarpTri {  // a binned triangle staged for the warp's fragment expansion (80 B)
   int X[3], Y[3];
   float iw[3];
   float fA;
   unsigned key;
   int flags;  // bits 0-2: top-left edges; bit 3: small (32-bit relative arithmetic)
-  int px0, py0, bw, start;  // clamped box origin and width; index of its first candidate
+  int px0, py0, bw, start;  // first row's (or the box's) first column and width; index of its first candidate
+  int px1, bw1;             // tiles of at most two rows: the second row's first column and width
+  int pad[2];
 };
 
 struct Scratch {
@@ -945,36 +947,51 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
       T.py0 = max(y0, int(box.y & 0xffff));
       int bw = min(x0 + cw - 1, int(box.x >> 16)) - T.px0 + 1;
       const int bh = min(y0 + ch - 1, int((box.y >> 16) & 0xfff)) - T.py0 + 1;
-      if (ch == 1 && (T.flags & 8) && bw > 0 && bh > 0) {
-        // one-row tile, small triangle: keep only the columns whose centres lie within 2/256 px
-        // of the triangle's extent along the row (float, relative to vertex 0, where every
-        // coordinate is exact and each crossing is within 0.02/256 px); the exact edge test
-        // still decides every remaining candidate
-        const float cyr = float(256 * y0 + 128 - T.Y[0]);
-        const float vx[3] = {0.0f, float(T.X[1]), float(T.X[2])}, vy[3] = {0.0f, float(T.Y[1]), float(T.Y[2])};
-        float xl = 3.0e38f, xr = -3.0e38f;
+      if (ch <= 2 && bw > 0 && bh > 0) {
+        // tiles of one or two rows: each row's candidates form one run of columns; for a small
+        // triangle, only the columns whose centres lie within 2/256 px of its extent along the
+        // row (float, relative to vertex 0, where every coordinate is exact and each crossing is
+        // within 0.02/256 px); the exact edge test still decides every candidate
+        int a0 = T.px0, n0 = bw, a1 = T.px0, n1 = bh == 2 ? bw : 0;
+        if (T.flags & 8) {
+          const float cy0 = float(256 * T.py0 + 128 - T.Y[0]), cy1 = cy0 + 256.0f;
+          const float vx[3] = {0.0f, float(T.X[1]), float(T.X[2])}, vy[3] = {0.0f, float(T.Y[1]), float(T.Y[2])};
+          float xl0 = 3.0e38f, xr0 = -3.0e38f, xl1 = 3.0e38f, xr1 = -3.0e38f;
 #pragma unroll
-        for (int e = 0; e < 3; e++) {
-          const int e2 = e == 2 ? 0 : e + 1;
-          const float ya = vy[e], yb = vy[e2], xa = vx[e], xb = vx[e2];
-          const bool cross = fminf(ya, yb) <= cyr && cyr <= fmaxf(ya, yb);
-          const float x = ya == yb ? xa : fmaf(cyr - ya, __fdividef(xb - xa, yb - ya), xa);
-          const float xo = ya == yb ? xb : x;
-          xl = cross ? fminf(xl, fminf(x, xo)) : xl;
-          xr = cross ? fmaxf(xr, fmaxf(x, xo)) : xr;
+          for (int e = 0; e < 3; e++) {
+            const int e2 = e == 2 ? 0 : e + 1;
+            const float ya = vy[e], yb = vy[e2], xa = vx[e], xb = vx[e2];
+            const float ylo = fminf(ya, yb), yhi = fmaxf(ya, yb);
+            const bool flat = ya == yb;
+            const float slope = flat ? 0.0f : __fdividef(xb - xa, yb - ya);
+            const float x0e = fmaf(cy0 - ya, slope, xa), x1e = fmaf(cy1 - ya, slope, xa);
+            const float lo0 = flat ? fminf(xa, xb) : x0e, hi0 = flat ? fmaxf(xa, xb) : x0e;
+            const float lo1 = flat ? fminf(xa, xb) : x1e, hi1 = flat ? fmaxf(xa, xb) : x1e;
+            const bool c0 = ylo <= cy0 && cy0 <= yhi, c1 = ylo <= cy1 && cy1 <= yhi;
+            xl0 = c0 ? fminf(xl0, lo0) : xl0;
+            xr0 = c0 ? fmaxf(xr0, hi0) : xr0;
+            xl1 = c1 ? fminf(xl1, lo1) : xl1;
+            xr1 = c1 ? fmaxf(xr1, hi1) : xr1;
+          }
+          const float cx0 = float(256 * T.px0 + 128 - T.X[0]);  // the box's first column centre, relative
+          const int jl0 = max(0, int(ceilf((xl0 - 2.0f - cx0) * (1.0f / 256.0f))));
+          const int jr0 = min(bw - 1, int(floorf((xr0 + 2.0f - cx0) * (1.0f / 256.0f))));
+          const int jl1 = max(0, int(ceilf((xl1 - 2.0f - cx0) * (1.0f / 256.0f))));
+          const int jr1 = min(bw - 1, int(floorf((xr1 + 2.0f - cx0) * (1.0f / 256.0f))));
+          a0 = T.px0 + jl0;
+          n0 = xl0 <= xr0 ? max(0, jr0 - jl0 + 1) : 0;
+          a1 = T.px0 + jl1;
+          n1 = bh == 2 && xl1 <= xr1 ? max(0, jr1 - jl1 + 1) : 0;
         }
-        const float c0 = float(256 * T.px0 + 128 - T.X[0]);  // column bw's first centre, relative
-        const int jl = max(0, int(ceilf((xl - 2.0f - c0) * (1.0f / 256.0f))));
-        const int jr = min(bw - 1, int(floorf((xr + 2.0f - c0) * (1.0f / 256.0f))));
-        if (xl > xr || jl > jr) {
-          bw = 0;
-        } else {
-          T.px0 += jl;
-          bw = jr - jl + 1;
-        }
+        T.px0 = a0;
+        T.bw = n0;
+        T.px1 = a1;
+        T.bw1 = n1;
+        cnt = n0 + n1;
+      } else {
+        T.bw = bw;
+        cnt = (bw > 0 && bh > 0) ? bw * bh : 0;
       }
-      T.bw = bw;
-      cnt = (bw > 0 && bh > 0) ? bw * bh : 0;
     }
     const int slot = __popc(__ballot_sync(kFull, cnt > 0) & ((1u << lane) - 1u));
     if (cnt > 0) wt[slot] = T;
@@ -994,7 +1011,15 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
       const int m = base + lane;
       if (m < total) {
         const WarpTri& W = wt[__popc(upto) + __popc(inside & (0xffffffffu >> (31 - lane))) - 1];
-        const BoxWalk w(m - W.start, W.px0, W.py0, W.bw);
+        const int j = m - W.start;
+        BoxWalk w(0, 0, 0, 1);
+        if (ch <= 2) {  // the first row's run, then the second row's
+          const bool r1 = j >= W.bw;
+          w.px = r1 ? W.px1 + (j - W.bw) : W.px0 + j;
+          w.py = W.py0 + (r1 ? 1 : 0);
+        } else {
+          w = BoxWalk(j, W.px0, W.py0, W.bw);
+        }
         const int tl = W.flags & 7;
         unsigned long long f;
         if (W.flags & 8) {

@@ -20,7 +20,7 @@ ORRB_MAX_LIGHTS = 4
 ORRB_MAX_MATERIALS = 32
 ORRB_GBUFFER_PLANES = 7
 DEFAULT_TILE_W = 256    # the library's defaults for a zero orrb_config field
-DEFAULT_TILE_H = 1
+DEFAULT_TILE_H = 2
 DEFAULT_THREADS = 512
 DEV_BITS = {0x1: "bad camera", 0x2: "bad instance", 0x4: "too many triangles", 0x8: "bad material",
             0x10: "bad lights", 0x20: "triangle dropped by guard band"}

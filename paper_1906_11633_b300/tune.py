@@ -23,8 +23,8 @@ from . import lib as L
 from .render import DeviceBatch, Renderer, config
 
 DEFAULT_CANDIDATES: Tuple[Tuple[int, int, int], ...] = (
-    (256, 1, 512), (256, 1, 256), (128, 1, 512), (128, 2, 512), (64, 2, 512), (64, 4, 512),
-    (32, 4, 512), (32, 8, 256), (512, 1, 256), (200, 1, 512))
+    (256, 2, 512), (256, 1, 512), (256, 2, 256), (128, 2, 512), (128, 1, 512), (64, 2, 512), (64, 4, 512),
+    (32, 4, 512), (512, 1, 256), (512, 2, 256))
 
 _lock = threading.Lock()
 

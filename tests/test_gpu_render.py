@@ -216,7 +216,7 @@ def test_large_triangles_with_edges_through_pixel_centres(oracle, rim):
 
 
 def test_slivers_on_pixel_centre_rows(oracle):
-    """Small binned triangles on one-row tiles, where each row's candidate columns are narrowed
+    """Small binned triangles on one- and two-row tiles, where each row's candidate columns are narrowed
     to the triangle's float extent along the row: slivers (nearly horizontal and nearly
     vertical), vertices exactly on pixel-centre rows and columns, and sub-pixel triangles must
     cover exactly the oracle's pixels."""
@@ -252,7 +252,7 @@ def test_slivers_on_pixel_centre_rows(oracle):
                              lights=[((0.0, 0.0, 3.0), 2.0)], background=(0.2, 0.3, 0.4))
     o = oracle.render(b, debug=True)
     assert (o["seg"] == 1).sum() > 500
-    for cfg in (config(), config(tile_w=64, tile_h=2)):
+    for cfg in (config(), config(tile_w=256, tile_h=1), config(tile_w=64, tile_h=2), config(tile_w=32, tile_h=4)):
         g = render_np(r, b, cfg)
         compare(g, o, f"slivers {cfg.tile_w}x{cfg.tile_h}")
         np.testing.assert_array_equal(g["seg"], o["seg"])
