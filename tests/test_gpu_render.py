@@ -85,7 +85,7 @@ def test_ragged_wide_and_orthographic(oracle):
     b = scenes.single_sample(meshes, [0, 1, 2], poses, cams, seg=[1, 2, 3], mat_base=[0, 1, 7],
                              lights=[((0.5, -1.0, 2.0), 2.0), ((-1.0, 0.5, 1.5), 1.0)], albedo=(0.6, 0.4, 0.3),
                              specular=0.5, shininess=20.0, ambient=(0.05, 0.05, 0.05), background=(0.2, 0.3, 0.4))
-    for tw, th in ((256, 1), (64, 4), (24, 8), (512, 1)):
+    for tw, th in ((256, 2), (256, 1), (64, 4), (24, 8), (512, 1), (512, 2)):
         compare(render_np(r, b, config(tile_w=tw, tile_h=th, threads=256)), oracle.render(b, debug=True),
                 f"ragged tile={tw}x{th}")
 
@@ -257,3 +257,24 @@ def test_slivers_on_pixel_centre_rows(oracle):
         compare(g, o, f"slivers {cfg.tile_w}x{cfg.tile_h}")
         np.testing.assert_array_equal(g["seg"], o["seg"])
         np.testing.assert_array_equal(g["depth"], o["depth"])
+
+
+def test_hand_directional_lights_and_orthographic_cameras(hand_renderer, oracle):
+    """The hand scene with directional lights (unit directions) and every second camera
+    orthographic (the scene's 0.7 m span over the image), against the oracle."""
+    b = sg.hand_batch(9, np.arange(24))
+    light = b.light.copy()
+    d = light[:, :, :3].astype(np.float64)
+    d /= np.maximum(np.linalg.norm(d, axis=-1, keepdims=True), 1e-9)
+    light[:, :, :3] = d.astype(np.float32)
+    meta = b.light_meta.copy()
+    meta[:, 1] = sg.LIGHT_DIRECTIONAL
+    intr = b.cam_intr.copy()
+    ortho = np.arange(len(intr)) % 2 == 1
+    intr[ortho, 0] = intr[ortho, 1] = 200 / 0.7
+    intr[ortho, 5] = sg.CAM_ORTHOGRAPHIC
+    b = b.with_params(light=light, light_meta=meta, cam_intr=intr)
+    g = render_np(hand_renderer, b)
+    o = oracle.render(b, debug=True)
+    compare(g, o, "hand directional/ortho")
+    assert (o["seg"] >= 3).sum() > 1000          # the hand is in view
