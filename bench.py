@@ -61,8 +61,8 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on this kernel source."""
+def profiled_value(key: str):
+    """A figure (`key: value` line) of the committed ncu summary, if it was taken on this kernel source."""
     try:
         text = open(os.path.join(ROOT, "profiles", "render_fused_hand256.md")).read()
     except OSError:
@@ -70,9 +70,14 @@ def profiled_traffic():
     if kernel_source_hash() not in text:
         return None
     for line in text.splitlines():
-        if line.startswith("traffic_bytes_per_launch:"):
+        if line.startswith(key + ":"):
             return float(line.split(":")[1])
     return None
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this kernel source."""
+    return profiled_value("traffic_bytes_per_launch")
 
 
 def load_peaks():
@@ -343,6 +348,18 @@ def run_ours(args, world, rank, local):
             "t_roof_us": 1e6 * max(t_hbm, t_fp32), "t_hbm_us": 1e6 * t_hbm, "t_fp32_us": 1e6 * t_fp32,
             "roofline_frac_of_step": 1e3 * max(t_hbm, t_fp32) / kernel_ms,
             "kernel": "render_fused_kernel"}
+    # secondary (not the headline): the instruction-issue roofline, with the warp instructions
+    # per pixel that ncu counted on this kernel source (rasterisation is integer/issue work
+    # that the FP32 shading term does not count)
+    ipp = profiled_value("warp_instructions_per_pixel")
+    if ipp is not None:
+        issue_peak = props.multi_processor_count * 4 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6
+        inst = ipp * N
+        roof["secondary_issue"] = {"warp_inst_per_launch": inst, "achieved_ginst_s": inst / (kernel_ms / 1e3) / 1e9,
+                                   "peak_ginst_s": issue_peak / 1e9,
+                                   "frac": inst / (kernel_ms / 1e3) / issue_peak,
+                                   "source": "ncu smsp__inst_executed per pixel (profiles/render_fused_hand256.md); "
+                                             "peak = SMs x 4 schedulers x max SM clock"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded procedural hand scene)",
