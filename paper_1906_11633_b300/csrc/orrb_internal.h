@@ -120,7 +120,7 @@ ORRB_HD inline SlotLayout slot_layout(int t_max, int max_tiles) {
   L.vis_box = o;  o = align256(o + cap * 8);
   L.bins = o;     o = align256(o + cap * kMaxSpanTiles * 4);
   L.big = o;      o = align256(o + cap * 4);
-  L.tile_off = o; o = align256(o + (size_t(max_tiles) + 1) * 4);
+  L.tile_off = o; o = align256(o + 2 * size_t(max_tiles) * 4);  // per tile: first and end bin entry
   L.counts = o;   o = align256(o + (max_tiles > kSmemCountTiles ? 2 * (size_t(max_tiles) + 2) * 4 : 0));
   L.total = o;
   return L;

@@ -70,6 +70,7 @@ struct CtaShared {
   ImageInfo im;
   alignas(16) float mat[kMaxMaterials][8];  // albedo rgb, specular, shininess (padded: two vector loads)
   int n_vis, n_big, next_tile, next_job, img;
+  int bin_overflow;  // phase B: some tile got more keys than its share of the bin array
   int help_slot, help_cam;
   int scan_tmp[33];
 };
@@ -610,21 +611,30 @@ __device__ __forceinline__ bool binned_span(uint2 box, const ImageInfo& im, int&
 // Neighbouring visible triangles come from the same cluster and mostly share tiles, so the
 // per-tile counter updates are aggregated per warp: the lanes that hit the same tile in a
 // step (match.any) add their number with one atomic by the lowest of them.
+// One pass: tile t's keys go to bins[t * cap, t * cap + count_t), cap being the tile's equal share
+// of the bin array; only if some tile would exceed its share does a second pass redo the image
+// with exact offsets (counts, prefix sum, scatter).  tile_off holds each tile's (first, end).
 __device__ void bin_phase(const Params& p, CtaShared& sh, int* counts, int* cursor, const Scratch& sc) {
   const ImageInfo& im = sh.im;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int t = tid; t < im.n_tiles; t += nt) counts[t] = 0;
+  if (tid == 0) sh.bin_overflow = 0;
   __syncthreads();
   const int n = sh.n_vis;
   const int lane = tid & 31;
   const unsigned below = (1u << lane) - 1u;
+  const int cap = int(size_t(2 * p.t_max + 2) * kMaxSpanTiles / size_t(im.n_tiles));
   for (int e0 = 0; e0 < n; e0 += nt) {
     const int e = e0 + tid;
     bool big = false;
     int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = 0;
-    if (e < n && !binned_span(sc.vis_box[e], im, tx0, tx1, ty0, ty1)) {
-      big = true;
-      tx1 = -1;
+    uint32_t key = 0;
+    if (e < n) {
+      key = sc.vis_key[e];
+      if (!binned_span(sc.vis_box[e], im, tx0, tx1, ty0, ty1)) {
+        big = true;
+        tx1 = -1;
+      }
     }
     const int w = tx1 - tx0 + 1, cnt = w > 0 ? w * (ty1 - ty0 + 1) : 0;
     const int steps = __reduce_max_sync(kFull, cnt);
@@ -632,7 +642,14 @@ __device__ void bin_phase(const Params& p, CtaShared& sh, int* counts, int* curs
     for (int j = 0; j < steps; j++) {
       const int tile = j < cnt ? ty * im.ntx + tx : -1;
       const unsigned peers = __match_any_sync(kFull, tile);
-      if (tile >= 0 && (peers & below) == 0) atomicAdd(&counts[tile], __popc(peers));
+      const int leader = __ffs(peers) - 1;
+      int slot = 0;
+      if (tile >= 0 && lane == leader) slot = atomicAdd(&counts[tile], __popc(peers));
+      slot = __shfl_sync(kFull, slot, leader) + __popc(peers & below);
+      if (tile >= 0) {
+        if (slot < cap) sc.bins[size_t(tile) * cap + slot] = key;
+        else sh.bin_overflow = 1;
+      }
       if (++tx > tx1) tx = tx0, ty++;
     }
     // ballot compaction of the large list: one atomic per warp
@@ -640,12 +657,22 @@ __device__ void bin_phase(const Params& p, CtaShared& sh, int* counts, int* curs
     int wbase = 0;
     if (lane == 0 && m) wbase = atomicAdd(&sh.n_big, __popc(m));
     wbase = __shfl_sync(kFull, wbase, 0);
-    if (big) sc.big[wbase + __popc(m & below)] = sc.vis_key[e];
+    if (big) sc.big[wbase + __popc(m & below)] = key;
   }
   __syncthreads();
+  if (!sh.bin_overflow) {
+    for (int t = tid; t < im.n_tiles; t += nt) {
+      sc.tile_off[2 * t] = t * cap;
+      sc.tile_off[2 * t + 1] = t * cap + counts[t];
+    }
+    __syncthreads();
+    return;
+  }
+  // second pass: exact offsets from the counts (the counts are complete even where bins overflowed)
   block_exclusive_scan(counts, im.n_tiles, sh.scan_tmp);
-  for (int t = tid; t <= im.n_tiles; t += nt) {
-    sc.tile_off[t] = counts[t];
+  for (int t = tid; t < im.n_tiles; t += nt) {
+    sc.tile_off[2 * t] = counts[t];
+    sc.tile_off[2 * t + 1] = counts[t + 1];
     cursor[t] = counts[t];
   }
   __syncthreads();
@@ -925,7 +952,7 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
   // per chunk of 32 candidates that count is a ballot of the starts up to the chunk plus the
   // bits of the starts inside it (distinct, since every staged triangle has a candidate).
   WarpTri* wt = reinterpret_cast<WarpTri*>(wbase + L.w_tri);
-  const int b0 = sc.tile_off[tile], b1 = sc.tile_off[tile + 1];
+  const int b0 = sc.tile_off[2 * tile], b1 = sc.tile_off[2 * tile + 1];
   for (int c = b0; c < b1; c += 32) {
     const int k = c + lane;
     int cnt = 0;

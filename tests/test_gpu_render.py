@@ -278,3 +278,35 @@ def test_hand_directional_lights_and_orthographic_cameras(hand_renderer, oracle)
     o = oracle.render(b, debug=True)
     compare(g, o, "hand directional/ortho")
     assert (o["seg"] >= 3).sum() > 1000          # the hand is in view
+
+
+def test_bin_overflow_falls_back_to_exact_offsets(oracle):
+    """Each tile's bin holds an equal share of the bin array; a stack of 300 small triangles on
+    8x1 tiles of a 512x512 image overfills its tiles' shares, so phase B redoes the image with
+    exact per-tile offsets.  The result must equal the oracle's."""
+    rng = np.random.default_rng(3)
+    W = H = 512
+    f = 64.0
+
+    def world(u, v, z):
+        return ((u - 0.5 * W) / f, (0.5 * H - v) / f, z)
+
+    pos, tris = [], []
+    for k in range(300):
+        cu, cv = 200.0 + rng.uniform(-3, 3), 300.0 + rng.uniform(-3, 3)
+        d = rng.uniform(-6, 6, size=(3, 2))
+        z = -0.002 * k
+        i = len(pos)
+        pos += [world(cu + d[j, 0], cv + d[j, 1], z) for j in range(3)]
+        tris += [(i, i + 1, i + 2), (i, i + 2, i + 1)]
+    mesh = sg.Mesh(pos=np.asarray(pos, np.float32), nrm=np.tile(np.float32([0, 0, 1]), (len(pos), 1)),
+                   idx=np.asarray(tris, np.uint32), tri_mat=(np.arange(len(tris)) % 7).astype(np.uint8))
+    r = Renderer([mesh])
+    cam = scenes.camera_down((0.0, 0.0, 4.0), W, H, px_per_m=f)
+    b = scenes.single_sample([mesh], [0], [scenes.identity_pose()], [cam], seg=[1],
+                             lights=[((0.0, 0.0, 3.0), 2.0)], background=(0.2, 0.3, 0.4))
+    o = oracle.render(b, debug=True)
+    for cfg in (config(tile_w=8, tile_h=1), config(tile_w=8, tile_h=2), config()):
+        g = render_np(r, b, cfg)
+        compare(g, o, f"stack {cfg.tile_w}x{cfg.tile_h}")
+        np.testing.assert_array_equal(g["seg"], o["seg"])
