@@ -49,7 +49,7 @@ class _Batch(C.Structure):
     _fields_ = [("n_samples", C.c_int32)] + [(n, C.c_void_p) for n in (
         "inst_offset", "inst_mesh", "inst_pose", "inst_seg", "inst_mat_base",
         "cam_offset", "cam_sample", "cam_view", "cam_intr", "cam_wh", "img_offset",
-        "light", "light_meta", "material", "exposure_ev", "ambient", "background")]
+        "light", "light_meta", "material", "exposure_ev", "ambient", "background", "grading")]
 
 
 class _Outputs(C.Structure):
@@ -106,7 +106,8 @@ class _Pinned:
             img_offset=_c(batch.img_offset, np.int64), light=_c(batch.light, np.float32),
             light_meta=_c(batch.light_meta, np.int32), material=_c(batch.material, np.float32),
             exposure_ev=_c(batch.exposure_ev, np.float32), ambient=_c(batch.ambient, np.float32),
-            background=_c(batch.background, np.float32))
+            background=_c(batch.background, np.float32),
+            grading=None if getattr(batch, "grading", None) is None else _c(batch.grading, np.float32))
         self.batch = _Batch(batch.n_samples, *[_p(self.arrs[n]) for n, _ in _Batch._fields_[1:]])
 
 

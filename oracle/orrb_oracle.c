@@ -38,6 +38,22 @@
  *  11  rgb8 = floor(clamp(rgb,0,1)*255 + 1/2); normal -> binary16 (RNE);
  *      background: rgb = background colour, depth 0, normal 0, seg 0.
  *  12  the adjoint of step 10 at fixed visibility, in fp64.
+ *  13  optional colour grading of the rgb8 channel (the post-processing
+ *      randomizer, Sec. 4.3.1), per sample g = (hue h, saturation s, contrast
+ *      k, brightness b, temperature t, tint u, grain a, grain seed), applied to
+ *      the linear colour (pixels and background) before step 11's
+ *      quantisation, in this order and in fp32:
+ *        white balance  r *= 1 + t, g *= 1 + u, b *= 1 - t;
+ *        hue            rotation by h about the grey axis (1,1,1)/sqrt(3):
+ *                       c' = c cos h + (k x c) sin h + k (k . c)(1 - cos h);
+ *        saturation     c = Y + s (c - Y), Y = 0.2126 r + 0.7152 g + 0.0722 b;
+ *        contrast       c = (c - 1/2) k + 1/2;   brightness  c = c + b;
+ *        grain          c = c + a (n - 1/2) on all three channels, n in [0, 1)
+ *                       from the PCG hash (Jarzynski and Olano, "Hash
+ *                       Functions for GPU Rendering", 2020): n = pcg(pcg(seed
+ *                       + 0x9E3779B9 (j + 1)) ^ i) / 2^32, j the camera's
+ *                       index within its sample, i the pixel's within its
+ *                       image.  rgb_linear stays ungraded.
  */
 #include "orrb_oracle.h"
 
@@ -253,6 +269,33 @@ uint16_t orc_f32_to_f16(float f) {
   return (uint16_t)(sign | h);
 }
 
+/* step 13: the PCG hash, as published (one LCG step, a random xorshift, a multiply) */
+static uint32_t pcg_hash(uint32_t v) {
+  uint32_t state = v * 747796405u + 2891336453u;
+  uint32_t word = ((state >> ((state >> 28u) + 4u)) ^ state) * 277803737u;
+  return (word >> 22u) ^ word;
+}
+
+static void grade(const float* g, int32_t cam_local, int64_t pixel, float c[3]) {
+  float r = c[0] * (1.0f + g[4]), gr = c[1] * (1.0f + g[5]), bl = c[2] * (1.0f - g[4]);
+  const float ch = cosf(g[0]), sh = sinf(g[0]);
+  const float inv_sqrt3 = 0.57735026918962576f;
+  const float mean = (r + gr + bl) / 3.0f;
+  const float x0 = (bl - gr) * inv_sqrt3, x1 = (r - bl) * inv_sqrt3, x2 = (gr - r) * inv_sqrt3; /* k x c */
+  float h[3] = {r * ch + x0 * sh + mean * (1.0f - ch), gr * ch + x1 * sh + mean * (1.0f - ch),
+                bl * ch + x2 * sh + mean * (1.0f - ch)};
+  const float Y = 0.2126f * h[0] + 0.7152f * h[1] + 0.0722f * h[2];
+  const uint32_t seed = (uint32_t)g[7];
+  const uint32_t h1 = pcg_hash(seed + 0x9E3779B9u * (uint32_t)(cam_local + 1));
+  const float n = (float)pcg_hash(h1 ^ (uint32_t)pixel) * 2.3283064365386963e-10f; /* 2^-32 */
+  for (int k = 0; k < 3; k++) {
+    float v = Y + g[1] * (h[k] - Y);
+    v = (v - 0.5f) * g[2] + 0.5f;
+    v = v + g[3];
+    c[k] = v + g[6] * (n - 0.5f);
+  }
+}
+
 static uint8_t quantise(float v) {
   float c = v < 0.0f ? 0.0f : (v > 1.0f ? 1.0f : v);
   return (uint8_t)floorf(c * 255.0f + 0.5f);
@@ -391,8 +434,11 @@ static int render_image(const orc_meshes* me, const orc_batch* b, int32_t c, con
       if (out->prim) out->prim[o] = p->key;
       if (out->depth2) out->depth2[o] = p->depth2;
       if (p->key < 0) {
-        if (out->rgb)
-          for (int k = 0; k < 3; k++) out->rgb[o * 3 + k] = quantise(bg[k]);
+        if (out->rgb) {
+          float gc[3] = {bg[0], bg[1], bg[2]};
+          if (b->grading) grade(b->grading + (int64_t)s * 8, c - b->cam_offset[s], i, gc);
+          for (int k = 0; k < 3; k++) out->rgb[o * 3 + k] = quantise(gc[k]);
+        }
         if (out->rgb_linear)
           for (int k = 0; k < 3; k++) out->rgb_linear[o * 3 + k] = bg[k];
         if (out->depth) out->depth[o] = 0.0f;
@@ -435,8 +481,11 @@ static int render_image(const orc_meshes* me, const orc_batch* b, int32_t c, con
       }
       float rgb[3];
       shade_f32(b, s, V, ortho, P, n, p->mat, rgb);
-      if (out->rgb)
-        for (int k = 0; k < 3; k++) out->rgb[o * 3 + k] = quantise(rgb[k]);
+      if (out->rgb) {
+        float gc[3] = {rgb[0], rgb[1], rgb[2]};
+        if (b->grading) grade(b->grading + (int64_t)s * 8, c - b->cam_offset[s], i, gc);
+        for (int k = 0; k < 3; k++) out->rgb[o * 3 + k] = quantise(gc[k]);
+      }
       if (out->rgb_linear)
         for (int k = 0; k < 3; k++) out->rgb_linear[o * 3 + k] = rgb[k];
       if (out->depth) out->depth[o] = p->depth;

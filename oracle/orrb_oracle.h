@@ -65,6 +65,7 @@ typedef struct {
   const float* exposure_ev;     /* [S] */
   const float* ambient;         /* [S][3] */
   const float* background;      /* [S][3] */
+  const float* grading;         /* [S][8] colour-grading epilogue (step 13), or NULL */
 } orc_batch;
 
 typedef struct {                /* every pointer may be NULL */

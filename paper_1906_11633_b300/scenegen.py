@@ -27,7 +27,7 @@ from __future__ import annotations
 
 import math
 from dataclasses import dataclass, field, replace
-from typing import List, Sequence
+from typing import Optional, List, Sequence
 
 import numpy as np
 
@@ -49,6 +49,7 @@ STREAM_POST = 7
 STREAM_SCENE = 8
 STREAM_TARGET = 9
 STREAM_REQUESTS = 10
+STREAM_GRADING = 11
 
 # --------------------------------------------------------------------------
 # Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
@@ -230,6 +231,9 @@ class Batch:
     ambient: np.ndarray        # [B, 3] float32
     background: np.ndarray     # [B, 3] float32
     sample_ids: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))
+    # [B, 8] float32 colour-grading epilogue (hue, saturation, contrast, brightness, temperature,
+    # tint, grain amplitude, grain seed: an integer below 2^24), or None for none
+    grading: Optional[np.ndarray] = None
 
     @property
     def n_samples(self) -> int:
@@ -294,7 +298,14 @@ def concat_batches(batches: Sequence[Batch]) -> Batch:
         ambient=np.concatenate([b.ambient for b in batches]),
         background=np.concatenate([b.background for b in batches]),
         sample_ids=np.concatenate([b.sample_ids for b in batches]),
+        grading=_concat_grading(batches),
     )
+
+
+def _concat_grading(batches):
+    if all(b.grading is None for b in batches):
+        return None
+    return np.concatenate([b.grading if b.grading is not None else identity_grading(b.n_samples) for b in batches])
 
 
 def select_samples(batch: Batch, idx: Sequence[int]) -> Batch:
@@ -316,6 +327,7 @@ def select_samples(batch: Batch, idx: Sequence[int]) -> Batch:
             material=batch.material[s:s + 1], exposure_ev=batch.exposure_ev[s:s + 1],
             ambient=batch.ambient[s:s + 1], background=batch.background[s:s + 1],
             sample_ids=batch.sample_ids[s:s + 1] if len(batch.sample_ids) else np.array([s]),
+            grading=batch.grading[s:s + 1] if batch.grading is not None else None,
         ))
     return concat_batches(parts)
 
@@ -545,8 +557,34 @@ def _post(seed: int, ids: np.ndarray):
     return ev, ambient, background
 
 
+def identity_grading(n: int) -> np.ndarray:
+    """Grading parameters that leave the image unchanged."""
+    g = np.zeros((n, 8), np.float32)
+    g[:, 1] = 1.0   # saturation
+    g[:, 2] = 1.0   # contrast
+    return g
+
+
+def grading_params(seed: int, sample_ids) -> np.ndarray:
+    """Per-sample post-processing (the paper's post-processing randomizer, Sec. 4.3.1): hue shift
+    U(+-0.1) rad, saturation U[0.8, 1.2], contrast U[0.8, 1.2], brightness U(+-0.05), temperature
+    U(+-0.1), tint U(+-0.1), grain amplitude U[0, 0.05], and a grain seed (integer below 2^24)."""
+    ids = np.asarray(sample_ids, dtype=np.int64).reshape(-1)
+    u = uniform(seed, STREAM_GRADING, ids, 8)
+    g = np.empty((len(ids), 8), np.float32)
+    g[:, 0] = 0.1 * (2.0 * u[:, 0] - 1.0)
+    g[:, 1] = 0.8 + 0.4 * u[:, 1]
+    g[:, 2] = 0.8 + 0.4 * u[:, 2]
+    g[:, 3] = 0.05 * (2.0 * u[:, 3] - 1.0)
+    g[:, 4] = 0.1 * (2.0 * u[:, 4] - 1.0)
+    g[:, 5] = 0.1 * (2.0 * u[:, 5] - 1.0)
+    g[:, 6] = 0.05 * u[:, 6]
+    g[:, 7] = np.floor(u[:, 7] * 16777216.0)   # an integer below 2^24, exact in float32
+    return g
+
+
 def hand_batch(seed: int, sample_ids, res: int = 200, n_cams: int = 3, meshes=None, res_per_sample=None,
-               cams_per_sample=None) -> Batch:
+               cams_per_sample=None, grading: bool = False) -> Batch:
     """Hand-like scenes: table, block, 24 capsule links posed by hinge angles U(+-60 deg)."""
     ids = np.asarray(sample_ids, dtype=np.int64).reshape(-1)
     B = len(ids)
@@ -586,6 +624,7 @@ def hand_batch(seed: int, sample_ids, res: int = 200, n_cams: int = 3, meshes=No
         material=_materials(seed, ids),
         exposure_ev=ev, ambient=ambient, background=background,
         sample_ids=ids,
+        grading=grading_params(seed, ids) if grading else None,
     )
 
 
