@@ -155,6 +155,16 @@ typedef struct {
   const float* exposure_ev;      /* [n_samples] exposure in stops */
   const float* ambient;          /* [n_samples][3] */
   const float* background;       /* [n_samples][3] linear background colour */
+  const float* grading;          /* [n_samples][8] or NULL: colour grading of the rgb output (the
+                                    post-processing randomizer, Sec. 4.3.1), applied in fp32 to the
+                                    linear colour of every pixel before quantisation, in this order:
+                                    white balance r *= 1 + t, g *= 1 + u, b *= 1 - t; rotation by h
+                                    about the grey axis (1,1,1)/sqrt(3); saturation c = Y + s (c - Y),
+                                    Y the Rec. 709 luma; contrast c = (c - 1/2) k + 1/2; brightness
+                                    c += b; grain c += a (n - 1/2), n in [0, 1) from the PCG hash of
+                                    the seed, the camera's index within its sample and the pixel's
+                                    index within its image.  Row: h, s, k, b, t, u, a, seed (an
+                                    integer below 2^24).  rgb_linear is not graded. */
 } orrb_batch_desc;
 
 /* Caller-preallocated outputs, flat over all pixels of all images (image c

@@ -251,6 +251,7 @@ void fill_batch(Params& p, const orrb_batch_shape& s, const orrb_batch_desc& b) 
   p.exposure_ev = b.exposure_ev;
   p.ambient = b.ambient;
   p.background = b.background;
+  p.grading = b.grading;
   p.total_pixels = s.total_pixels;
   p.t_max = s.max_tris_per_sample;
   p.inst_max = s.max_inst_per_sample;

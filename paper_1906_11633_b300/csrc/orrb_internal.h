@@ -70,6 +70,7 @@ struct Params {
   const float* exposure_ev;
   const float* ambient;
   const float* background;
+  const float* grading;  // [n_samples][8] or null
   // outputs (device, any may be null)
   uint8_t* rgb;
   float* depth;

@@ -53,6 +53,14 @@ constexpr unsigned long long kEmpty = ~0ull;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kPlainRasterSplit = 8;  // plain mode: CTAs sharing one image's tiles
 
+// The PCG hash (Jarzynski and Olano, "Hash Functions for GPU Rendering", JCGT 2020): one LCG
+// step, a random xorshift and a multiply.
+__host__ __device__ inline unsigned pcg_hash(unsigned v) {
+  const unsigned state = v * 747796405u + 2891336453u;
+  const unsigned word = ((state >> ((state >> 28u) + 4u)) ^ state) * 277803737u;
+  return (word >> 22u) ^ word;
+}
+
 struct ImageInfo {
   int cam, s, W, H, inst0, n_inst, ortho, T, valid;
   int tw, th, ntx, n_tiles;
@@ -64,6 +72,12 @@ struct ImageInfo {
   float scale;
   float amb[3], bg[3];
   alignas(16) float lv[kMaxLights][4];  // view-space light position (point) or direction to the light, intensity
+  // colour grading of the rgb output (when the batch has it): the affine map of its white
+  // balance, hue, saturation, contrast and brightness (rows of A | t), the grain amplitude and
+  // the grain hash of (seed, camera within the sample)
+  float gm[3][4];
+  float grain;
+  unsigned grain_key;
 };
 
 struct CtaShared {
@@ -868,6 +882,46 @@ __device__ void shade(const CtaShared& sh, const float P[3], const float n[3], i
   rgb[2] = im.scale * fmaf(m[2], im.amb[2] + D, S);
 }
 
+// The image's grading (one thread, in the graded instances only, before a barrier that precedes
+// the raster phase).  White balance, the rotation about the grey axis, saturation, contrast and
+// brightness are each affine in the colour, so they compose into one map c -> A c + t, applied
+// per pixel; the grain stays per pixel.
+__device__ void grading_setup(const Params& p, ImageInfo& im) {
+  const float* g = p.grading + (size_t)im.s * 8;
+  float hs, hc;
+  sincosf(g[0], &hs, &hc);
+  const float k = 0.57735026918962576f;  // 1/sqrt(3): the grey axis (k, k, k)
+  // rotation R = cos I + sin [axis]x + (1 - cos) axis axis^T
+  const float a = hc + (1.0f - hc) / 3.0f, b = (1.0f - hc) / 3.0f - k * hs, c = (1.0f - hc) / 3.0f + k * hs;
+  const float R[3][3] = {{a, b, c}, {c, a, b}, {b, c, a}};
+  const float wb[3] = {1.0f + g[4], 1.0f + g[5], 1.0f - g[4]};
+  const float Yw[3] = {0.2126f, 0.7152f, 0.0722f};
+  const float sat = g[1], con = g[2];
+  // S = sat I + (1 - sat) 1 Yw^T; then contrast con and the offsets 0.5 (1 - con) + brightness
+  for (int i = 0; i < 3; i++) {
+    for (int j = 0; j < 3; j++) {
+      float rw = 0.0f;  // (S R)_ij
+      for (int m = 0; m < 3; m++) rw += ((i == m ? sat : 0.0f) + (1.0f - sat) * Yw[m]) * R[m][j];
+      im.gm[i][j] = con * rw * wb[j];
+    }
+    im.gm[i][3] = 0.5f * (1.0f - con) + g[3];
+  }
+  im.grain = g[6];
+  const unsigned cam_local = unsigned(im.cam - p.cam_offset[im.s]);
+  im.grain_key = pcg_hash(unsigned(g[7]) + 0x9E3779B9u * (cam_local + 1u));
+}
+
+// Colour grading of one pixel's linear colour (see orrb_batch_desc::grading); `pixel` is the
+// pixel's index within its image.  The grain is the PCG hash of the image's key and the
+// pixel index, scaled to [0, 1).
+__device__ __forceinline__ void grade(const ImageInfo& im, unsigned pixel, float c[3]) {
+  const float n = float(pcg_hash(im.grain_key ^ pixel)) * 2.3283064365386963e-10f - 0.5f;  // 2^-32
+  const float o = im.grain * n;
+  const float r = c[0], g = c[1], b = c[2];
+#pragma unroll
+  for (int i = 0; i < 3; i++) c[i] = fmaf(im.gm[i][0], r, fmaf(im.gm[i][1], g, fmaf(im.gm[i][2], b, im.gm[i][3] + o)));
+}
+
 // floor(clamp(v, 0, 1) * 255 + 0.5) with one rounding of the multiply-add (NaN -> 0)
 __device__ __forceinline__ uint8_t quantise(float v) { return (uint8_t)__float2uint_rd(fmaf(__saturatef(v), 255.0f, 0.5f)); }
 
@@ -883,6 +937,9 @@ struct BoxWalk {
 };
 
 // Phase R for one tile, by one warp, in warp-private shared memory.
+// kGrade: the batch has colour grading (a separate instance, so that the common case carries
+// none of its code).
+template <bool kGrade>
 __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scratch& sc, int tile, char* wbase,
                                  const SmemLayout& L, const uint32_t* spans) {
   const ImageInfo& im = sh.im;
@@ -1139,7 +1196,13 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
       // warp fill whole sectors of the row between them
       // (explicit global streaming stores: outputs are not re-read, and the compiler need not
       // assume they alias the shared-memory light and material tables)
-      if (rgb_row) {
+      if (kGrade && rgb_row) {
+        float gc[3] = {rgb[0], rgb[1], rgb[2]};
+        grade(im, unsigned(py * im.W + px), gc);
+        __stcs(rgb_row + 3 * lx + 0, quantise(gc[0]));
+        __stcs(rgb_row + 3 * lx + 1, quantise(gc[1]));
+        __stcs(rgb_row + 3 * lx + 2, quantise(gc[2]));
+      } else if (rgb_row) {
         __stcs(rgb_row + 3 * lx + 0, quantise(rgb[0]));
         __stcs(rgb_row + 3 * lx + 1, quantise(rgb[1]));
         __stcs(rgb_row + 3 * lx + 2, quantise(rgb[2]));
@@ -1175,6 +1238,7 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
 
 // Phase R for the current image: warps pull tiles first, first + stride, ... from the
 // CTA's counter until none is left.
+template <bool kGrade>
 __device__ void raster_phase(const Params& p, CtaShared& sh, const Scratch& sc, const SmemPtrs& sp, const SmemLayout& L,
                              int first = 0, int stride = 1) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1184,7 +1248,7 @@ __device__ void raster_phase(const Params& p, CtaShared& sh, const Scratch& sc, 
     if (lane == 0) k = atomicAdd(&sh.next_tile, 1);
     const int t = first + stride * __shfl_sync(kFull, k, 0);
     if (t >= sh.im.n_tiles) break;
-    raster_tile_warp(p, sh, sc, t, wbase, L, sp.spans);
+    raster_tile_warp<kGrade>(p, sh, sc, t, wbase, L, sp.spans);
   }
   __syncthreads();
 }
@@ -1212,6 +1276,7 @@ constexpr long long kSpinBudget = 2000000000ll;
 // the records, so it needs no fence); a helper claims with compare-and-swap, so it never
 // takes a tile of a later image that reused the slot, and publishes each finished tile
 // in the slot's counter after a fence.
+template <bool kGrade>
 __device__ void raster_claimed(const Params& p, CtaShared& sh, const Scratch& sc, const SmemPtrs& sp, const SmemLayout& L,
                                int cam, bool owner) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1243,7 +1308,7 @@ __device__ void raster_claimed(const Params& p, CtaShared& sh, const Scratch& sc
     }
     t = __shfl_sync(kFull, t, 0);
     if (t >= n_tiles) break;
-    raster_tile_warp(p, sh, sc, t, wbase, L, sp.spans);
+    raster_tile_warp<kGrade>(p, sh, sc, t, wbase, L, sp.spans);
     mine++;
     if (!owner && lane == 0) {
       __threadfence();
@@ -1258,6 +1323,7 @@ __device__ void raster_claimed(const Params& p, CtaShared& sh, const Scratch& sc
 // fused: one persistent launch.  CTAs pull whole images from a queue; once the
 // queue is empty they help finish the raster phase of images other CTAs still own.
 // ---------------------------------------------------------------------------
+template <bool kGrade>
 __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
   extern __shared__ __align__(16) char smem[];
   __shared__ CtaShared sh;
@@ -1270,6 +1336,7 @@ __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
     const int cam = sh.img;
     if (cam >= p.n_cams) break;
     setup_image(p, cam, sh, sp.mprefix, sp.tprefix, sp.mbegin, true);
+    if (kGrade && threadIdx.x == 0 && sh.im.valid) grading_setup(p, sh.im);  // (read after phase G's barrier)
     if (sh.im.valid) {
       geometry_phase(p, sh, sp.mprefix, sp.tprefix, sp.mbegin, reinterpret_cast<WarpG*>(sp.uni), sc);
       __syncthreads();
@@ -1285,7 +1352,7 @@ __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
         atomicExch(sc.claim(), (unsigned long long)(cam + 1) << 32);
       }
       __syncthreads();
-      raster_claimed(p, sh, sc, sp, L, cam, true);
+      raster_claimed<kGrade>(p, sh, sc, sp, L, cam, true);
       if (threadIdx.x == 0) {  // close it and wait for helpers still on its other tiles
         atomicExch(sc.claim(), 0ull);
         const unsigned helped = unsigned(sh.im.n_tiles - sh.next_tile);
@@ -1357,10 +1424,11 @@ __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
       __threadfence();
       setup_image(p, cam, sh, sp.mprefix, sp.tprefix, sp.mbegin, false);
       if (threadIdx.x == 0) sh.n_big = *reinterpret_cast<volatile int*>(o.header + 3);
+      if (kGrade && threadIdx.x == 0) grading_setup(p, sh.im);
       __syncthreads();
       big_spans(p, sh, o, sp.spans);
       __syncthreads();
-      raster_claimed(p, sh, o, sp, L, cam, false);
+      raster_claimed<kGrade>(p, sh, o, sp, L, cam, false);
     }
     __syncthreads();
   }
@@ -1411,6 +1479,7 @@ __global__ void __launch_bounds__(512, 2) plain_bin_kernel(Params p) {
   if (threadIdx.x == 0) sc.header[3] = sh.n_big;
 }
 
+template <bool kGrade>
 __global__ void __launch_bounds__(512, 2) plain_raster_kernel(Params p) {
   extern __shared__ __align__(16) char smem[];
   __shared__ CtaShared sh;
@@ -1422,10 +1491,11 @@ __global__ void __launch_bounds__(512, 2) plain_raster_kernel(Params p) {
   SmemPtrs sp = carve(smem, p, L);
   setup_image(p, cam, sh, sp.mprefix, sp.tprefix, sp.mbegin, false);
   if (threadIdx.x == 0) sh.n_big = sc.header[3];
+  if (kGrade && threadIdx.x == 0) grading_setup(p, sh.im);
   __syncthreads();
   big_spans(p, sh, sc, sp.spans);
   __syncthreads();
-  raster_phase(p, sh, sc, sp, L, blockIdx.y, gridDim.y);
+  raster_phase<kGrade>(p, sh, sc, sp, L, blockIdx.y, gridDim.y);
 }
 
 // Scratch of orrb_render_batch_noalloc: a file-scope device array, so that
@@ -1464,7 +1534,7 @@ namespace {
 // larger size is needed, so steady-state launches (and launches inside a stream capture)
 // make no attribute calls.
 std::mutex g_attr_mu;
-size_t g_attr_set[4][64] = {};
+size_t g_attr_set[6][64] = {};  // fused, plain geometry / bin / raster, then the graded fused and raster
 
 cudaError_t ensure_smem(const void* fn, int which, size_t smem) {
   int dev = 0;
@@ -1481,9 +1551,12 @@ cudaError_t ensure_smem(const void* fn, int which, size_t smem) {
 
 int render_max_ctas_per_sm(int threads, size_t smem) {
   int n = 0;
-  if (ensure_smem((const void*)render_fused_kernel, 0, smem) != cudaSuccess) return -1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_fused_kernel, threads, smem) != cudaSuccess) return -1;
-  return n;
+  int m = 0;  // both instances: the same launch bounds and shared memory
+  if (ensure_smem((const void*)render_fused_kernel<false>, 0, smem) != cudaSuccess) return -1;
+  if (ensure_smem((const void*)render_fused_kernel<true>, 4, smem) != cudaSuccess) return -1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_fused_kernel<false>, threads, smem) != cudaSuccess) return -1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, render_fused_kernel<true>, threads, smem) != cudaSuccess) return -1;
+  return n < m ? n : m;
 }
 
 int launch_render(const Params& p, int mode, int threads, int n_ctas, int max_cams_per_sample, void* stream,
@@ -1492,25 +1565,30 @@ int launch_render(const Params& p, int mode, int threads, int n_ctas, int max_ca
   const size_t smem = render_smem_bytes(threads, p.tile_w, p.tile_h, p.inst_max, p.max_tiles, p.w_max);
   cudaError_t e = cudaSuccess;
   if (mode == 0) {
-    e = ensure_smem((const void*)render_fused_kernel, 0, smem);
+    const bool graded = p.grading != nullptr;
+    e = graded ? ensure_smem((const void*)render_fused_kernel<true>, 4, smem)
+               : ensure_smem((const void*)render_fused_kernel<false>, 0, smem);
     if (e == cudaSuccess) {  // slot headers (claim words, counters) start at zero
       const SlotLayout SL = slot_layout(p.t_max, p.max_tiles);
       e = cudaMemset2DAsync(p.scratch + SL.header, p.slot_bytes, 0, 64, (size_t)n_ctas, st);
     }
     if (e == cudaSuccess) {
-      render_fused_kernel<<<n_ctas, threads, smem, st>>>(p);
+      if (graded) render_fused_kernel<true><<<n_ctas, threads, smem, st>>>(p);
+      else render_fused_kernel<false><<<n_ctas, threads, smem, st>>>(p);
       e = cudaGetLastError();
     }
   } else {
+    const bool graded = p.grading != nullptr;
     const void* ks[3] = {(const void*)plain_geometry_kernel, (const void*)plain_bin_kernel,
-                         (const void*)plain_raster_kernel};
-    for (int k = 0; k < 3 && e == cudaSuccess; k++) e = ensure_smem(ks[k], k + 1, smem);
+                         graded ? (const void*)plain_raster_kernel<true> : (const void*)plain_raster_kernel<false>};
+    for (int k = 0; k < 3 && e == cudaSuccess; k++) e = ensure_smem(ks[k], k == 2 && graded ? 5 : k + 1, smem);
     Params q = p;
     for (int s = 0; s < p.n_samples && e == cudaSuccess; s++) {
       q.plain_sample = s;
       plain_geometry_kernel<<<max_cams_per_sample, threads, smem, st>>>(q);
       plain_bin_kernel<<<max_cams_per_sample, threads, smem, st>>>(q);
-      plain_raster_kernel<<<dim3(max_cams_per_sample, kPlainRasterSplit), threads, smem, st>>>(q);
+      if (graded) plain_raster_kernel<true><<<dim3(max_cams_per_sample, kPlainRasterSplit), threads, smem, st>>>(q);
+      else plain_raster_kernel<false><<<dim3(max_cams_per_sample, kPlainRasterSplit), threads, smem, st>>>(q);
       e = cudaGetLastError();
     }
   }

@@ -44,7 +44,7 @@ class orrb_batch_shape(C.Structure):
 class orrb_batch_desc(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in (
         "inst_offset", "inst_mesh", "inst_pose", "inst_seg", "inst_mat_base", "cam_offset", "cam_sample", "cam_view",
-        "cam_intr", "cam_wh", "img_offset", "light", "light_meta", "material", "exposure_ev", "ambient", "background")]
+        "cam_intr", "cam_wh", "img_offset", "light", "light_meta", "material", "exposure_ev", "ambient", "background", "grading")]
 
 
 class orrb_outputs(C.Structure):

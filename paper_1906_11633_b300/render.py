@@ -24,7 +24,7 @@ _DTYPES = dict(inst_offset=torch.int32, inst_mesh=torch.int32, inst_pose=torch.f
                inst_mat_base=torch.int16, cam_offset=torch.int32, cam_sample=torch.int32, cam_view=torch.float32,
                cam_intr=torch.float32, cam_wh=torch.int32, img_offset=torch.int64, light=torch.float32,
                light_meta=torch.int32, material=torch.float32, exposure_ev=torch.float32, ambient=torch.float32,
-               background=torch.float32)
+               background=torch.float32, grading=torch.float32)
 _NP = {torch.int32: np.int32, torch.float32: np.float32, torch.uint8: np.uint8, torch.int16: np.int16,
        torch.int64: np.int64}
 
@@ -50,7 +50,9 @@ class DeviceBatch:
     desc: L.orrb_batch_desc = field(init=False)
 
     def __post_init__(self):
-        self.desc = L.orrb_batch_desc(*[self.tensors[n].data_ptr() for n in _DESC_FIELDS])
+        # an optional array (grading) that is absent or None passes a null pointer
+        self.desc = L.orrb_batch_desc(*[self.tensors[n].data_ptr() if self.tensors.get(n) is not None else None
+                                        for n in _DESC_FIELDS])
 
     @property
     def total_pixels(self) -> int:
@@ -63,8 +65,9 @@ class DeviceBatch:
 
 
 def host_arrays(batch) -> Dict[str, np.ndarray]:
-    """The batch's arrays in the C layout, contiguous, as numpy."""
-    return {n: np.ascontiguousarray(getattr(batch, n), dtype=_NP[_DTYPES[n]]) for n in _DESC_FIELDS}
+    """The batch's arrays in the C layout, contiguous, as numpy (an optional array that is None is left out)."""
+    return {n: np.ascontiguousarray(getattr(batch, n), dtype=_NP[_DTYPES[n]]) for n in _DESC_FIELDS
+            if getattr(batch, n, None) is not None}
 
 
 def _mesh_descs(meshes):

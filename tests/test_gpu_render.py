@@ -310,3 +310,22 @@ def test_bin_overflow_falls_back_to_exact_offsets(oracle):
         g = render_np(r, b, cfg)
         compare(g, o, f"stack {cfg.tile_w}x{cfg.tile_h}")
         np.testing.assert_array_equal(g["seg"], o["seg"])
+
+
+def test_colour_grading_matches_oracle(hand_renderer, oracle):
+    """The colour-grading epilogue of the rgb channel (random hue, saturation, contrast, brightness,
+    white balance and grain per sample) against the oracle, in fused and plain launches; identity
+    parameters leave every channel bit-identical, and the other channels never change."""
+    b = sg.hand_batch(13, np.arange(12), res=96, grading=True)
+    plain_b = b.with_params(grading=None)
+    o = oracle.render(b, debug=True)
+    ref = render_np(hand_renderer, plain_b)
+    for cfg in (config(), config(mode=L.ORRB_MODE_PLAIN)):
+        g = render_np(hand_renderer, b, cfg)
+        compare(g, o, "graded")
+        for k in ("depth", "normal", "seg", "rgb_linear"):
+            np.testing.assert_array_equal(g[k], ref[k], err_msg=k)
+    assert np.abs(g["rgb"].astype(int) - ref["rgb"].astype(int)).max() > 5     # the grading did something
+    ident = render_np(hand_renderer, b.with_params(grading=sg.identity_grading(b.n_samples)))
+    for k in ref:
+        np.testing.assert_array_equal(ident[k], ref[k], err_msg=k)
