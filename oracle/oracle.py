@@ -54,7 +54,8 @@ class _Batch(C.Structure):
 
 class _Outputs(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in (
-        "rgb", "depth", "normal", "seg", "rgb_linear", "gb_pos", "gb_nrm", "gb_mat", "prim", "depth2", "counters")]
+        "rgb", "depth", "normal", "seg", "rgb_linear", "gb_pos", "gb_nrm", "gb_mat", "prim", "depth2", "counters",
+        "tracker")] + [("tracker_stride", C.c_int32)]
 
 
 def lib():
@@ -124,10 +125,12 @@ def default_threads() -> int:
         return os.cpu_count() or 1
 
 
-def render(batch, threads: int | None = None, gbuffer: bool = False, debug: bool = False, cams=None):
+def render(batch, threads: int | None = None, gbuffer: bool = False, debug: bool = False, cams=None,
+           tracker: bool = False):
     """Oracle render of a batch.  Returns a dict of numpy channel arrays.
 
     `cams`: optional (begin, end) camera range; pixels of other images stay zero.
+    `tracker`: also the per (camera, instance) rows [n_cams, max instances per sample, 8] of step 14.
     """
     L = lib()
     pin = _Pinned(batch)
@@ -139,13 +142,17 @@ def render(batch, threads: int | None = None, gbuffer: bool = False, debug: bool
                    gb_mat=np.zeros(N, np.int32))
     if debug:
         out.update(prim=np.zeros(N, np.int64), depth2=np.zeros(N, np.float32))
+    stride = int(np.diff(batch.inst_offset).max()) if batch.n_samples else 0
+    if tracker:
+        out["tracker"] = np.zeros((batch.n_cams, stride, 8), np.int32)
     threads = threads or default_threads()
     c0, c1 = cams if cams is not None else (0, batch.n_cams)
     chunks = [(a + c0, b + c0) for a, b in _chunks(c1 - c0, threads)]
     counters = np.zeros((len(chunks), 4), np.int64)
 
     def run(i):
-        o = _Outputs(*[_p(out.get(n)) for n, _ in _Outputs._fields_[:-1]], _p(counters[i]))
+        o = _Outputs(*[_p(out.get(n)) for n, _ in _Outputs._fields_[:-3]], _p(counters[i]), _p(out.get("tracker")),
+                     stride)
         rc = L.orc_render(C.byref(pin.meshes), C.byref(pin.batch), chunks[i][0], chunks[i][1], C.byref(o))
         if rc != 0:
             raise MemoryError("oracle: allocation failed")

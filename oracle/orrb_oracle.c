@@ -54,9 +54,17 @@
  *                       + 0x9E3779B9 (j + 1)) ^ i) / 2^32, j the camera's
  *                       index within its sample, i the pixel's within its
  *                       image.  rgb_linear stays ungraded.
+ *  14  optional tracker rows (per camera and instance of its sample): the
+ *      8.8 fixed-point screen box (x0, y0, x1, y1) of the instance's mesh
+ *      vertices that lie in front of the near plane and inside the guard band,
+ *      snapped as in step 4 (empty: x0 = y0 = INT32_MAX, x1 = y1 = INT32_MIN);
+ *      the snapped projection (kx, ky) of the instance's origin (its pose
+ *      translation); flags bit 0: box not empty, bit 1: origin projected; and
+ *      the number of vertices in the box.
  */
 #include "orrb_oracle.h"
 
+#include <limits.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -378,6 +386,41 @@ static int render_image(const orc_meshes* me, const orc_batch* b, int32_t c, con
     int32_t mesh = (int32_t)b->inst_mesh[inst];
     float MV[12];
     compose_mv(V, b->inst_pose + (int64_t)inst * 12, MV);
+    if (out->tracker) { /* step 14 */
+      int32_t* row = out->tracker + ((int64_t)c * out->tracker_stride + (inst - b->inst_offset[s])) * 8;
+      int32_t x0 = INT32_MAX, y0 = INT32_MAX, x1 = INT32_MIN, y1 = INT32_MIN, nv = 0, flags = 0, kx = 0, ky = 0;
+      for (int32_t v = me->vert_offset[mesh]; v <= me->vert_offset[mesh + 1]; v++) {
+        const float origin[3] = {0.0f, 0.0f, 0.0f}, zero[3] = {0.0f, 0.0f, 0.0f};
+        const int is_origin = v == me->vert_offset[mesh + 1]; /* the last pass projects the origin */
+        vtx q = to_view(MV, is_origin ? origin : me->pos + (int64_t)v * 3, zero);
+        if (!(q.p[2] <= -near)) continue;
+        float xs, ys;
+        if (ortho) {
+          xs = cx + fx * q.p[0];
+          ys = cy - fy * q.p[1];
+        } else {
+          float iwv = 1.0f / (-q.p[2]);
+          xs = cx + fx * (q.p[0] * iwv);
+          ys = cy - fy * (q.p[1] * iwv);
+        }
+        if (!(fabsf(xs) < GUARD_PX) || !(fabsf(ys) < GUARD_PX)) continue;
+        int32_t X = (int32_t)rintf(xs * 256.0f), Y = (int32_t)rintf(ys * 256.0f);
+        if (is_origin) {
+          kx = X;
+          ky = Y;
+          flags |= 2;
+        } else {
+          if (X < x0) x0 = X;
+          if (Y < y0) y0 = Y;
+          if (X > x1) x1 = X;
+          if (Y > y1) y1 = Y;
+          nv++;
+          flags |= 1;
+        }
+      }
+      row[0] = x0; row[1] = y0; row[2] = x1; row[3] = y1;
+      row[4] = kx; row[5] = ky; row[6] = flags; row[7] = nv;
+    }
     int32_t v0 = me->vert_offset[mesh];
     int32_t t0 = me->tri_offset[mesh], t1 = me->tri_offset[mesh + 1];
     for (int32_t t = t0; t < t1; t++) {

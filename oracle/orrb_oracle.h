@@ -80,6 +80,8 @@ typedef struct {                /* every pointer may be NULL */
   int64_t* prim;                /* [N] winning key 2*prim_id + sub, -1 = background */
   float* depth2;                /* [N] depth of the nearest fragment of another key, +inf if none */
   int64_t* counters;            /* [4] fragments, triangles culled, clipped, dropped (accumulated) */
+  int32_t* tracker;             /* [C][tracker_stride][8] per (camera, instance of its sample), step 14 */
+  int32_t tracker_stride;
 } orc_outputs;
 
 /* Render images [cam_begin, cam_end).  Returns 0, or -1 on allocation failure. */
