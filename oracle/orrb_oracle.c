@@ -56,11 +56,11 @@
  *                       image.  rgb_linear stays ungraded.
  *  14  optional tracker rows (per camera and instance of its sample): the
  *      8.8 fixed-point screen box (x0, y0, x1, y1) of the instance's mesh
- *      vertices that lie in front of the near plane and inside the guard band,
- *      snapped as in step 4 (empty: x0 = y0 = INT32_MAX, x1 = y1 = INT32_MIN);
- *      the snapped projection (kx, ky) of the instance's origin (its pose
- *      translation); flags bit 0: box not empty, bit 1: origin projected; and
- *      the number of vertices in the box.
+ *      vertices (those its triangles use) that lie in front of the near plane
+ *      and inside the guard band, snapped as in step 4 (empty: x0 = y0 =
+ *      INT32_MAX, x1 = y1 = INT32_MIN); the snapped projection (kx, ky) of the
+ *      instance's origin (its pose translation); flags bit 0: box not empty,
+ *      bit 1: origin projected; a zero.
  */
 #include "orrb_oracle.h"
 
@@ -388,10 +388,17 @@ static int render_image(const orc_meshes* me, const orc_batch* b, int32_t c, con
     compose_mv(V, b->inst_pose + (int64_t)inst * 12, MV);
     if (out->tracker) { /* step 14 */
       int32_t* row = out->tracker + ((int64_t)c * out->tracker_stride + (inst - b->inst_offset[s])) * 8;
-      int32_t x0 = INT32_MAX, y0 = INT32_MAX, x1 = INT32_MIN, y1 = INT32_MIN, nv = 0, flags = 0, kx = 0, ky = 0;
-      for (int32_t v = me->vert_offset[mesh]; v <= me->vert_offset[mesh + 1]; v++) {
+      int32_t x0 = INT32_MAX, y0 = INT32_MAX, x1 = INT32_MIN, y1 = INT32_MIN, flags = 0, kx = 0, ky = 0;
+      const int32_t va = me->vert_offset[mesh], vb = me->vert_offset[mesh + 1];
+      unsigned char* used = (unsigned char*)calloc((size_t)(vb - va) + 1, 1);
+      if (!used) return -1;
+      for (int32_t t = me->tri_offset[mesh]; t < me->tri_offset[mesh + 1]; t++)
+        for (int k = 0; k < 3; k++) used[me->idx[(int64_t)t * 3 + k]] = 1;
+      used[vb - va] = 1;
+      for (int32_t v = va; v <= vb; v++) {
         const float origin[3] = {0.0f, 0.0f, 0.0f}, zero[3] = {0.0f, 0.0f, 0.0f};
-        const int is_origin = v == me->vert_offset[mesh + 1]; /* the last pass projects the origin */
+        const int is_origin = v == vb; /* the last pass projects the origin */
+        if (!used[v - va]) continue;
         vtx q = to_view(MV, is_origin ? origin : me->pos + (int64_t)v * 3, zero);
         if (!(q.p[2] <= -near)) continue;
         float xs, ys;
@@ -414,12 +421,12 @@ static int render_image(const orc_meshes* me, const orc_batch* b, int32_t c, con
           if (Y < y0) y0 = Y;
           if (X > x1) x1 = X;
           if (Y > y1) y1 = Y;
-          nv++;
           flags |= 1;
         }
       }
+      free(used);
       row[0] = x0; row[1] = y0; row[2] = x1; row[3] = y1;
-      row[4] = kx; row[5] = ky; row[6] = flags; row[7] = nv;
+      row[4] = kx; row[5] = ky; row[6] = flags; row[7] = 0;
     }
     int32_t v0 = me->vert_offset[mesh];
     int32_t t0 = me->tri_offset[mesh], t1 = me->tri_offset[mesh + 1];
@@ -560,9 +567,10 @@ int orc_render(const orc_meshes* m, const orc_batch* b, int32_t cam_begin, int32
   }
   pixel_winner* px = (pixel_winner*)malloc((size_t)(maxpx > 0 ? maxpx : 1) * sizeof(pixel_winner));
   if (!px) return -1;
-  for (int32_t c = cam_begin; c < cam_end; c++) render_image(m, b, c, out, px);
+  int rc = 0;
+  for (int32_t c = cam_begin; c < cam_end && rc == 0; c++) rc = render_image(m, b, c, out, px);
   free(px);
-  return 0;
+  return rc;
 }
 
 int orc_raster_fixed(int32_t W, int32_t H, int32_t n, const int32_t* X, const int32_t* Y, const float* iw,

@@ -1,9 +1,9 @@
 """Pins of the oracle's tracker rows (per camera and instance: the 8.8 fixed-point screen box of the
-instance's vertices in front of the near plane, the projected origin, flags, vertex count):
+instance's vertices in front of the near plane, the projected origin and flags):
 
   a quad whose corners project exactly onto known pixel positions (orthographic camera) has exactly
   those corners as its box, and its pose translation as its keypoint; an instance behind the camera
-  has an empty row; an instance cut by the near plane counts only its vertices in front; and every
+  has an empty row; an instance cut by the near plane boxes only its vertices in front; and every
   pixel an unclipped instance covers has its centre inside that instance's box.
 """
 
@@ -42,7 +42,7 @@ def test_box_and_keypoint_of_a_quad_are_exact(orc):
     want = [round(256 * (10.25 + du)), round(256 * (7.5 + dv)), round(256 * (41.75 + du)), round(256 * (30.0 + dv))]
     assert list(row[:4]) == want
     assert list(row[4:6]) == [round(256 * (0.5 * W + du)), round(256 * (0.5 * H + dv))]
-    assert row[6] == 3 and row[7] == 4
+    assert row[6] == 3 and row[7] == 0
 
 
 def test_instance_behind_the_camera_has_an_empty_row(orc):
@@ -51,21 +51,30 @@ def test_instance_behind_the_camera_has_an_empty_row(orc):
     b = scenes.single_sample([mesh], [0, 0], [scenes.pose(t=(0.0, 0.5, 1.0)), scenes.pose(t=(0.0, -3.0, 1.0))],
                              [cam], seg=[1, 2], lights=[((0, 0, 3), 1.0)])
     rows = orc.render(b, tracker=True)["tracker"][0]
-    assert rows[0, 6] == 3 and rows[0, 7] == mesh.n_verts
+    assert rows[0, 6] == 3 and rows[0, 0] <= rows[0, 2] and rows[0, 1] <= rows[0, 3]
     assert list(rows[1]) == [INT_MAX, INT_MAX, INT_MIN, INT_MIN, 0, 0, 0, 0]
 
 
-def test_near_plane_cut_counts_only_vertices_in_front(orc):
-    cam = scenes.camera_look((0.0, -2.0, 1.0), (0.0, 0.0, 1.0), 64, 64, 60.0)
-    mesh = sg.box_mesh(0.2)
-    # the box straddles the camera plane: its vertices at y = -2.2 are behind, those at y = -1.8 in front
-    b = scenes.single_sample([mesh], [0], [scenes.pose(t=(0.0, -2.0, 1.0))], [cam], seg=[1],
-                             lights=[((0, 0, 3), 1.0)])
+def _project(cam, pts):
+    """fp64 screen coordinates (8.8 units) and view depth of world points."""
+    view, intr, _ = cam
+    v = pts @ view[:, :3].T + view[:, 3]
+    fx, fy, cx, cy = intr[:4]
+    return 256 * (cx + fx * v[:, 0] / -v[:, 2]), 256 * (cy - fy * v[:, 1] / -v[:, 2]), -v[:, 2]
+
+
+def test_near_plane_cut_boxes_only_vertices_in_front(orc):
+    cam = scenes.camera_look((0.0, -2.0, 1.0), (0.3, 0.0, 1.2), 64, 64, 60.0)
+    mesh = sg.box_mesh(0.6)
+    t = np.array([0.1, -1.9, 1.05])              # the box straddles the camera plane
+    b = scenes.single_sample([mesh], [0], [scenes.pose(t=t)], [cam], seg=[1], lights=[((0, 0, 3), 1.0)])
     row = orc.render(b, tracker=True)["tracker"][0, 0]
-    view = mesh.pos.astype(np.float64) + np.array([0.0, -2.0, 1.0]) - np.array([0.0, -2.0, 1.0])
-    in_front = int((view[:, 1] > 0.01).sum())    # the camera looks along +y
-    assert row[7] == in_front and 0 < in_front < mesh.n_verts
-    assert row[6] & 2 == 0                        # the origin lies in the camera plane, behind the near plane
+    xs, ys, z = _project(cam, mesh.pos.astype(np.float64) + t)
+    front = z > 0.01 + 1e-6
+    assert 0 < front.sum() < len(z) and row[6] & 1
+    assert abs(row[0] - xs[front].min()) <= 2 and abs(row[2] - xs[front].max()) <= 2
+    assert abs(row[1] - ys[front].min()) <= 2 and abs(row[3] - ys[front].max()) <= 2
+    assert row[6] & 2 == 0 or _project(cam, t[None])[2][0] > 0.01
 
 
 def test_covered_pixels_lie_inside_the_box(orc):
@@ -80,7 +89,10 @@ def test_covered_pixels_lie_inside_the_box(orc):
             sid = int(b.inst_seg[b.inst_offset[s] + i])
             ys, xs = np.nonzero(seg[c] == sid)
             mesh = b.meshes[int(b.inst_mesh[b.inst_offset[s] + i])]
-            if len(xs) == 0 or row[7] != mesh.n_verts:   # unseen, or cut by the near plane
+            pose = b.inst_pose[b.inst_offset[s] + i].astype(np.float64)
+            world = mesh.pos.astype(np.float64) @ pose[:, :3].T + pose[:, 3]
+            view = world @ b.cam_view[c, :, :3].astype(np.float64).T + b.cam_view[c, :, 3]
+            if len(xs) == 0 or not (view[:, 2] < -0.011).all():   # unseen, or cut by the near plane
                 continue
             cx, cy = 256 * xs + 128, 256 * ys + 128
             assert (cx >= row[0]).all() and (cx <= row[2]).all() and (cy >= row[1]).all() and (cy <= row[3]).all()
