@@ -518,6 +518,27 @@ def run_diff(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def _timed_renders(r, db, args, world, **kw):
+    """Mean kernel time (ms, max over ranks) of one render of `db`, L2 flushed before each timed launch."""
+    import torch
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=r.device)
+    stream = torch.cuda.current_stream()
+    out = r.render(db, **kw)
+    for _ in range(args.warmup):
+        r.render(db, out=out)
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(max(10, args.steps // 10)):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r.render(db, out=out)
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    return max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in evs])), world)
+
+
 def run_grade(args, world, rank, local):
     """The hand batch with the colour-grading epilogue of the rgb channel (per-sample hue, saturation,
     contrast, brightness, white balance and grain): kernel time against the same batch ungraded."""
@@ -529,26 +550,7 @@ def run_grade(args, world, rank, local):
     r = Renderer(batch.meshes, device=local)
     graded = r.upload(batch)
     plain = graded.with_params(grading=None)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=r.device)
-    stream = torch.cuda.current_stream()
-
-    def timed(db):
-        out = r.render(db)
-        for _ in range(args.warmup):
-            r.render(db, out=out)
-        torch.cuda.synchronize()
-        evs = []
-        for _ in range(max(10, args.steps // 10)):
-            flush.fill_(1)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            r.render(db, out=out)
-            e1.record(stream)
-            evs.append((e0, e1))
-        torch.cuda.synchronize()
-        return max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in evs])), world)
-
-    gms, pms = timed(graded), timed(plain)
+    gms, pms = _timed_renders(r, graded, args, world), _timed_renders(r, plain, args, world)
     if rank != 0:
         return
     line = {"workload": "grade", "metric": "samples/s with the colour-grading epilogue",
@@ -557,6 +559,28 @@ def run_grade(args, world, rank, local):
             "config": {"samples": N_SAMPLES, "cameras": N_CAMS, "resolution": RES,
                        "grading": "hue U(+-0.1) rad, saturation and contrast U[0.8, 1.2], brightness U(+-0.05), "
                                   "temperature and tint U(+-0.1), grain U[0, 0.05]"}}
+    print(json.dumps(line), flush=True)
+
+
+def run_track(args, world, rank, local):
+    """The hand batch with the tracker rows (screen box and projected origin of every instance in every
+    image, folded in by the vertex stage): kernel time against the same batch without them."""
+    import torch
+    from paper_1906_11633_b300 import scenegen as sg
+    from paper_1906_11633_b300.render import Renderer
+    torch.cuda.set_device(local)
+    batch = sg.hand_batch(SEED, shard_samples(rank, world, N_SAMPLES), res=RES, n_cams=N_CAMS)
+    r = Renderer(batch.meshes, device=local)
+    db = r.upload(batch)
+    tms, pms = _timed_renders(r, db, args, world, tracker=True), _timed_renders(r, db, args, world)
+    if rank != 0:
+        return
+    line = {"workload": "track", "metric": "samples/s with the tracker rows",
+            "value": world * N_SAMPLES / (tms / 1e3), "unit": UNIT, "n_gpus": world, "ms_per_step": tms,
+            "untracked_ms_per_step": pms, "overhead": tms / pms - 1.0, "device_status": r.status(),
+            "config": {"samples": N_SAMPLES, "cameras": N_CAMS, "resolution": RES,
+                       "rows": f"one per camera and instance ({batch.n_inst // batch.n_samples} instances per sample), "
+                               "8 int32 each"}}
     print(json.dumps(line), flush=True)
 
 
@@ -606,7 +630,7 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the fused kernel from an ncu capture of this build")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["hand", "uneven", "diff", "serve", "grade"], default="hand",
+    ap.add_argument("--workload", choices=["hand", "uneven", "diff", "serve", "grade", "track"], default="hand",
                     help="hand: the headline line; the others print supplementary lines")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--samples", type=int, default=N_SAMPLES,
@@ -627,6 +651,8 @@ def main():
         run_serve(args, world, rank, local)
     elif args.workload == "grade":
         run_grade(args, world, rank, local)
+    elif args.workload == "track":
+        run_track(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

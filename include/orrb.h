@@ -177,6 +177,14 @@ typedef struct {
   float* rgb_linear;    /* device, [N][3] before clamp and quantisation */
   float* gbuffer;       /* device, [7][N] planes: position xyz, normal xyz (view space),
                            material slot as int32 bits (-1 background); input of the backward */
+  int32_t* tracker;     /* device, [n_cams][max_inst_per_sample][8] per camera and instance of its
+                           sample (the tracker output, Sec. 4.3): the 8.8 fixed-point screen box
+                           x0, y0, x1, y1 of the instance's vertices that its triangles use, that
+                           lie in front of the near plane and inside the guard band, snapped as the
+                           triangle vertices are (empty: INT32_MAX, INT32_MAX, INT32_MIN, INT32_MIN;
+                           a mesh without triangles keeps an empty row), the snapped
+                           projection kx, ky of its origin, flags (bit 0 box, bit 1 origin), 0.
+                           Rows past a sample's instance count are left as they were. */
 } orrb_outputs;
 
 #define ORRB_MODE_FUSED 0  /* one persistent launch over all images (work queue) */

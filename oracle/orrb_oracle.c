@@ -60,7 +60,8 @@
  *      and inside the guard band, snapped as in step 4 (empty: x0 = y0 =
  *      INT32_MAX, x1 = y1 = INT32_MIN); the snapped projection (kx, ky) of the
  *      instance's origin (its pose translation); flags bit 0: box not empty,
- *      bit 1: origin projected; a zero.
+ *      bit 1: origin projected; a zero.  An instance of a mesh without
+ *      triangles keeps an empty row.
  */
 #include "orrb_oracle.h"
 
@@ -394,7 +395,7 @@ static int render_image(const orc_meshes* me, const orc_batch* b, int32_t c, con
       if (!used) return -1;
       for (int32_t t = me->tri_offset[mesh]; t < me->tri_offset[mesh + 1]; t++)
         for (int k = 0; k < 3; k++) used[me->idx[(int64_t)t * 3 + k]] = 1;
-      used[vb - va] = 1;
+      used[vb - va] = me->tri_offset[mesh + 1] > me->tri_offset[mesh]; /* (a mesh without triangles: no row) */
       for (int32_t v = va; v <= vb; v++) {
         const float origin[3] = {0.0f, 0.0f, 0.0f}, zero[3] = {0.0f, 0.0f, 0.0f};
         const int is_origin = v == vb; /* the last pass projects the origin */

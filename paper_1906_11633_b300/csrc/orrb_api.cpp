@@ -418,6 +418,7 @@ orrb_status orrb_render_batch(orrb_ctx* ctx, const orrb_batch_shape* shape, cons
   p.seg = out->seg;
   p.rgb_linear = out->rgb_linear;
   p.gbuffer = out->gbuffer;
+  p.tracker = out->tracker;
   const ArenaLayout& A = ctx->arena;
   p.meshes = reinterpret_cast<const MeshEntry*>(ctx->arena_ptr + A.meshes);
   p.meshlets = reinterpret_cast<const MeshletEntry*>(ctx->arena_ptr + A.meshlets);
@@ -485,6 +486,7 @@ orrb_status orrb_render_batch_noalloc(orrb_ctx* ctx, const orrb_batch_shape* sha
   p.seg = out->seg;
   p.rgb_linear = out->rgb_linear;
   p.gbuffer = out->gbuffer;
+  p.tracker = out->tracker;
   const ArenaLayout& A = ctx->arena;
   p.meshes = reinterpret_cast<const MeshEntry*>(ctx->arena_ptr + A.meshes);
   p.meshlets = reinterpret_cast<const MeshletEntry*>(ctx->arena_ptr + A.meshlets);

@@ -78,6 +78,7 @@ struct Params {
   uint8_t* seg;
   float* rgb_linear;
   float* gbuffer;
+  int32_t* tracker;  // [n_cams][inst_max][8] or null
   int64_t total_pixels;
   // mesh set
   const MeshEntry* meshes;

@@ -40,6 +40,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <climits>
 #include <mutex>
 
 #include "orrb.h"
@@ -221,8 +222,9 @@ __device__ void block_exclusive_scan(int* a, int n, int* tmp) {
 // ---------------------------------------------------------------------------
 // per-image set-up (camera, lights, materials, instance tables)
 // ---------------------------------------------------------------------------
+// track: (with tables) also start this image's tracker rows empty.
 __device__ void setup_image(const Params& p, int cam, CtaShared& sh, int* mprefix, int* tprefix, int* mbegin,
-                            bool tables) {
+                            bool tables, bool track = false) {
   ImageInfo& im = sh.im;
   const int tid = threadIdx.x;
   if (tid == 0) {
@@ -305,6 +307,11 @@ __device__ void setup_image(const Params& p, int cam, CtaShared& sh, int* mprefi
   }
   const int n = im.n_inst;
   for (int i = tid; i < n; i += blockDim.x) {
+    if (track) {  // this image's tracker rows start empty (phase G folds its vertices in)
+      int4* row = reinterpret_cast<int4*>(p.tracker + ((size_t)im.cam * p.inst_max + i) * 8);
+      row[0] = make_int4(INT_MAX, INT_MAX, INT_MIN, INT_MIN);
+      row[1] = make_int4(0, 0, 0, 0);
+    }
     uint32_t mesh = p.inst_mesh[im.inst0 + i];
     if (mesh >= (uint32_t)p.n_meshes) {
       flag_status(p, ORRB_DEV_BAD_INSTANCE);
@@ -467,6 +474,9 @@ __device__ __noinline__ int clip_triangle(int t_max, Record* rec, const ImageInf
 // ---------------------------------------------------------------------------
 // phase G: geometry of one image
 // ---------------------------------------------------------------------------
+// kTrack: the launch writes tracker rows (a separate instance, so that the common case carries none
+// of that code).
+template <bool kTrack>
 __device__ void geometry_phase(const Params& p, CtaShared& sh, const int* mprefix, const int* tprefix,
                                const int* mbegin, WarpG* wgs, const Scratch& sc) {
   const ImageInfo& im = sh.im;
@@ -505,6 +515,7 @@ __device__ void geometry_phase(const Params& p, CtaShared& sh, const int* mprefi
     uint32_t tq[4];
 #pragma unroll
     for (int i = 0; i < 4; i++) tq[i] = i * 32 + lane < nt ? p.tris[ml.tri_begin + i * 32 + lane] : 0u;
+    int bx0 = INT_MAX, by0 = INT_MAX, bx1 = INT_MIN, by1 = INT_MIN;  // tracker box of the lane's vertices
     float4 Pq[2], Nq[2];
 #pragma unroll
     for (int i = 0; i < 2; i++) {
@@ -535,6 +546,36 @@ __device__ void geometry_phase(const Params& p, CtaShared& sh, const int* mprefi
       wg->Y[v] = Y;
       wg->iw[v] = iw;
       wg->flag[v] = inside | (ok << 1);
+      if (kTrack && inside && ok) {
+        bx0 = min(bx0, X);
+        by0 = min(by0, Y);
+        bx1 = max(bx1, X);
+        by1 = max(by1, Y);
+      }
+    }
+    if (kTrack) {  // the cluster's box into the instance's row; its first cluster also projects the origin
+      bx0 = __reduce_min_sync(kFull, bx0);
+      by0 = __reduce_min_sync(kFull, by0);
+      bx1 = __reduce_max_sync(kFull, bx1);
+      by1 = __reduce_max_sync(kFull, by1);
+      int* row = p.tracker + ((size_t)im.cam * p.inst_max + lo) * 8;
+      if (lane == 0 && bx0 <= bx1) {
+        atomicMin(row + 0, bx0);
+        atomicMin(row + 1, by0);
+        atomicMax(row + 2, bx1);
+        atomicMax(row + 3, by1);
+        atomicOr(row + 6, 1);
+      }
+      if (lane == 0 && j == mprefix[lo] && wg->mv[11] <= -im.near) {
+        int kx, ky, kok;
+        float kiw;
+        project(im, wg->mv[3], wg->mv[7], wg->mv[11], kx, ky, kiw, kok);
+        if (kok) {
+          row[4] = kx;
+          row[5] = ky;
+          atomicOr(row + 6, 2);
+        }
+      }
     }
     __syncwarp();
     const int prim_base = tprefix[lo] + ml.mesh_tri_base;
@@ -1323,7 +1364,7 @@ __device__ void raster_claimed(const Params& p, CtaShared& sh, const Scratch& sc
 // fused: one persistent launch.  CTAs pull whole images from a queue; once the
 // queue is empty they help finish the raster phase of images other CTAs still own.
 // ---------------------------------------------------------------------------
-template <bool kGrade>
+template <bool kGrade, bool kTrack>
 __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
   extern __shared__ __align__(16) char smem[];
   __shared__ CtaShared sh;
@@ -1335,10 +1376,10 @@ __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
     __syncthreads();
     const int cam = sh.img;
     if (cam >= p.n_cams) break;
-    setup_image(p, cam, sh, sp.mprefix, sp.tprefix, sp.mbegin, true);
+    setup_image(p, cam, sh, sp.mprefix, sp.tprefix, sp.mbegin, true, kTrack);
     if (kGrade && threadIdx.x == 0 && sh.im.valid) grading_setup(p, sh.im);  // (read after phase G's barrier)
     if (sh.im.valid) {
-      geometry_phase(p, sh, sp.mprefix, sp.tprefix, sp.mbegin, reinterpret_cast<WarpG*>(sp.uni), sc);
+      geometry_phase<kTrack>(p, sh, sp.mprefix, sp.tprefix, sp.mbegin, reinterpret_cast<WarpG*>(sp.uni), sc);
       __syncthreads();
       int* counts = p.max_tiles > kSmemCountTiles ? sc.counts : reinterpret_cast<int*>(sp.uni);
       bin_phase(p, sh, counts, counts + (p.max_tiles + 2), sc);
@@ -1443,6 +1484,7 @@ __device__ inline int plain_cam(const Params& p) {
   return c < p.cam_offset[s + 1] ? c : -1;
 }
 
+template <bool kTrack>
 __global__ void __launch_bounds__(512, 2) plain_geometry_kernel(Params p) {
   extern __shared__ __align__(16) char smem[];
   __shared__ CtaShared sh;
@@ -1451,12 +1493,12 @@ __global__ void __launch_bounds__(512, 2) plain_geometry_kernel(Params p) {
   const SmemLayout L = layout_of(p);
   SmemPtrs sp = carve(smem, p, L);
   const Scratch sc = slot_scratch(p, blockIdx.x);
-  setup_image(p, cam, sh, sp.mprefix, sp.tprefix, sp.mbegin, true);
+  setup_image(p, cam, sh, sp.mprefix, sp.tprefix, sp.mbegin, true, kTrack);
   if (!sh.im.valid) {
     if (threadIdx.x == 0) sc.header[2] = -1;
     return;
   }
-  geometry_phase(p, sh, sp.mprefix, sp.tprefix, sp.mbegin, reinterpret_cast<WarpG*>(sp.uni), sc);
+  geometry_phase<kTrack>(p, sh, sp.mprefix, sp.tprefix, sp.mbegin, reinterpret_cast<WarpG*>(sp.uni), sc);
   __syncthreads();
   if (threadIdx.x == 0) sc.header[2] = sh.n_vis;
 }
@@ -1534,7 +1576,7 @@ namespace {
 // larger size is needed, so steady-state launches (and launches inside a stream capture)
 // make no attribute calls.
 std::mutex g_attr_mu;
-size_t g_attr_set[6][64] = {};  // fused, plain geometry / bin / raster, then the graded fused and raster
+size_t g_attr_set[9][64] = {};  // per kernel instance (see fused_index and the plain launch)
 
 cudaError_t ensure_smem(const void* fn, int which, size_t smem) {
   int dev = 0;
@@ -1549,14 +1591,31 @@ cudaError_t ensure_smem(const void* fn, int which, size_t smem) {
 }
 }  // namespace
 
+// Fused kernel instance f: bit 0 colour grading, bit 1 tracker rows.
+static const void* fused_fn(int f) {
+  switch (f) {
+    case 0: return (const void*)render_fused_kernel<false, false>;
+    case 1: return (const void*)render_fused_kernel<true, false>;
+    case 2: return (const void*)render_fused_kernel<false, true>;
+    default: return (const void*)render_fused_kernel<true, true>;
+  }
+}
+// Its slot in the attribute cache (1-3 and 5, 8: the plain kernels).
+static int fused_index(int f) {
+  static const int slot[4] = {0, 4, 6, 7};
+  return slot[f & 3];
+}
+
 int render_max_ctas_per_sm(int threads, size_t smem) {
   int n = 0;
-  int m = 0;  // both instances: the same launch bounds and shared memory
-  if (ensure_smem((const void*)render_fused_kernel<false>, 0, smem) != cudaSuccess) return -1;
-  if (ensure_smem((const void*)render_fused_kernel<true>, 4, smem) != cudaSuccess) return -1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_fused_kernel<false>, threads, smem) != cudaSuccess) return -1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, render_fused_kernel<true>, threads, smem) != cudaSuccess) return -1;
-  return n < m ? n : m;
+  n = 1 << 30;  // every instance: the same launch bounds and shared memory; the least of their fits
+  for (int f = 0; f < 4; f++) {
+    int m = 0;
+    if (ensure_smem(fused_fn(f), fused_index(f), smem) != cudaSuccess) return -1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, fused_fn(f), threads, smem) != cudaSuccess) return -1;
+    n = m < n ? m : n;
+  }
+  return n;
 }
 
 int launch_render(const Params& p, int mode, int threads, int n_ctas, int max_cams_per_sample, void* stream,
@@ -1565,27 +1624,33 @@ int launch_render(const Params& p, int mode, int threads, int n_ctas, int max_ca
   const size_t smem = render_smem_bytes(threads, p.tile_w, p.tile_h, p.inst_max, p.max_tiles, p.w_max);
   cudaError_t e = cudaSuccess;
   if (mode == 0) {
-    const bool graded = p.grading != nullptr;
-    e = graded ? ensure_smem((const void*)render_fused_kernel<true>, 4, smem)
-               : ensure_smem((const void*)render_fused_kernel<false>, 0, smem);
+    const int f = (p.grading != nullptr ? 1 : 0) | (p.tracker != nullptr ? 2 : 0);
+    e = ensure_smem(fused_fn(f), fused_index(f), smem);
     if (e == cudaSuccess) {  // slot headers (claim words, counters) start at zero
       const SlotLayout SL = slot_layout(p.t_max, p.max_tiles);
       e = cudaMemset2DAsync(p.scratch + SL.header, p.slot_bytes, 0, 64, (size_t)n_ctas, st);
     }
     if (e == cudaSuccess) {
-      if (graded) render_fused_kernel<true><<<n_ctas, threads, smem, st>>>(p);
-      else render_fused_kernel<false><<<n_ctas, threads, smem, st>>>(p);
+      switch (f) {
+        case 0: render_fused_kernel<false, false><<<n_ctas, threads, smem, st>>>(p); break;
+        case 1: render_fused_kernel<true, false><<<n_ctas, threads, smem, st>>>(p); break;
+        case 2: render_fused_kernel<false, true><<<n_ctas, threads, smem, st>>>(p); break;
+        default: render_fused_kernel<true, true><<<n_ctas, threads, smem, st>>>(p); break;
+      }
       e = cudaGetLastError();
     }
   } else {
-    const bool graded = p.grading != nullptr;
-    const void* ks[3] = {(const void*)plain_geometry_kernel, (const void*)plain_bin_kernel,
+    const bool graded = p.grading != nullptr, tracked = p.tracker != nullptr;
+    const void* ks[3] = {tracked ? (const void*)plain_geometry_kernel<true> : (const void*)plain_geometry_kernel<false>,
+                         (const void*)plain_bin_kernel,
                          graded ? (const void*)plain_raster_kernel<true> : (const void*)plain_raster_kernel<false>};
-    for (int k = 0; k < 3 && e == cudaSuccess; k++) e = ensure_smem(ks[k], k == 2 && graded ? 5 : k + 1, smem);
+    const int which[3] = {tracked ? 8 : 1, 2, graded ? 5 : 3};
+    for (int k = 0; k < 3 && e == cudaSuccess; k++) e = ensure_smem(ks[k], which[k], smem);
     Params q = p;
     for (int s = 0; s < p.n_samples && e == cudaSuccess; s++) {
       q.plain_sample = s;
-      plain_geometry_kernel<<<max_cams_per_sample, threads, smem, st>>>(q);
+      if (tracked) plain_geometry_kernel<true><<<max_cams_per_sample, threads, smem, st>>>(q);
+      else plain_geometry_kernel<false><<<max_cams_per_sample, threads, smem, st>>>(q);
       plain_bin_kernel<<<max_cams_per_sample, threads, smem, st>>>(q);
       if (graded) plain_raster_kernel<true><<<dim3(max_cams_per_sample, kPlainRasterSplit), threads, smem, st>>>(q);
       else plain_raster_kernel<false><<<dim3(max_cams_per_sample, kPlainRasterSplit), threads, smem, st>>>(q);

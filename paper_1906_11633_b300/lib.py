@@ -48,7 +48,7 @@ class orrb_batch_desc(C.Structure):
 
 
 class orrb_outputs(C.Structure):
-    _fields_ = [(n, C.c_void_p) for n in ("rgb", "depth", "normal", "seg", "rgb_linear", "gbuffer")]
+    _fields_ = [(n, C.c_void_p) for n in ("rgb", "depth", "normal", "seg", "rgb_linear", "gbuffer", "tracker")]
 
 
 class orrb_config(C.Structure):

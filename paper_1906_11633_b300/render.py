@@ -146,13 +146,17 @@ class Renderer:
         return out
 
     def render(self, db: DeviceBatch, out=None, cfg: Optional[L.orrb_config] = None, rgb_linear: bool = False,
-               gbuffer: bool = False, stream=None, workspace: Optional[torch.Tensor] = None):
+               gbuffer: bool = False, stream=None, workspace: Optional[torch.Tensor] = None, tracker: bool = False):
+        """Render `db`; `tracker` adds the per (camera, instance) rows [n_cams, max instances, 8]."""
         cfg = cfg or config()
         if out is None:
             out = self.alloc_outputs(db.total_pixels, rgb_linear, gbuffer)
+            if tracker:
+                out["tracker"] = torch.empty((int(db.shape.n_cams), int(db.shape.max_inst_per_sample), 8),
+                                             dtype=torch.int32, device=self.device)
         ws = workspace if workspace is not None else self.workspace(db.shape, cfg)
         outs = L.orrb_outputs(*[out[k].data_ptr() if k in out else None
-                                for k in ("rgb", "depth", "normal", "seg", "rgb_linear", "gbuffer")])
+                                for k in ("rgb", "depth", "normal", "seg", "rgb_linear", "gbuffer", "tracker")])
         st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
         L.orrb_render_batch(self.ctx, db.shape, db.desc, outs, cfg, ws.data_ptr(), ws.numel(), st)
         self._last_ws = ws

@@ -329,3 +329,30 @@ def test_colour_grading_matches_oracle(hand_renderer, oracle):
     ident = render_np(hand_renderer, b.with_params(grading=sg.identity_grading(b.n_samples)))
     for k in ref:
         np.testing.assert_array_equal(ident[k], ref[k], err_msg=k)
+
+
+def test_tracker_rows_match_oracle(hand_renderer, oracle):
+    """Per (camera, instance) screen boxes and projected origins: integers from the bit-exact vertex
+    projection, so they must equal the oracle's exactly, in fused and plain launches and with the
+    near plane cutting instances (the camera near the table) and an instance behind the camera."""
+    b = sg.hand_batch(17, np.arange(10), res=128)
+    meshes = [sg.plane_mesh(3, 3), sg.box_mesh(0.5), sg.capsule_mesh(0.3, 0.8)]
+    near = scenes.single_sample(meshes, [0, 1, 2, 2],
+                                [scenes.identity_pose(), scenes.pose(t=(0.2, -0.1, 0.5)),
+                                 scenes.pose(R=sg._rot("z", np.array(0.7)), t=(-0.6, 0.3, 0.9)),
+                                 scenes.pose(t=(0.6, -0.4, -0.5))],                  # behind the first camera
+                                [scenes.camera_look((0.3, -0.2, 0.05), (0, 0, 0.6), 31, 29, 80.0),
+                                 scenes.camera_down((0.05, 0.02, 4.0), 53, 61, px_per_m=17.0)],
+                                lights=[((0.5, -1.0, 2.0), 2.0)])
+    for r, batch in ((hand_renderer, b), (Renderer(meshes), near)):
+        o = oracle.render(batch, tracker=True)["tracker"]
+        for cfg in (config(), config(mode=L.ORRB_MODE_PLAIN)):
+            db = r.upload(batch)
+            out = r.render(db, cfg=cfg, tracker=True)
+            out["tracker"].fill_(7)
+            out = r.render(db, cfg=cfg, out=out)
+            torch.cuda.synchronize()
+            assert r.status() == 0
+            g = out["tracker"].cpu().numpy()
+            np.testing.assert_array_equal(g, o)
+    assert (o[..., 6] & 1).any() and o[0, 3, 6] == 0 and o[1, 3, 6] == 3
