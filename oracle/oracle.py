@@ -49,7 +49,8 @@ class _Batch(C.Structure):
     _fields_ = [("n_samples", C.c_int32)] + [(n, C.c_void_p) for n in (
         "inst_offset", "inst_mesh", "inst_pose", "inst_seg", "inst_mat_base",
         "cam_offset", "cam_sample", "cam_view", "cam_intr", "cam_wh", "img_offset",
-        "light", "light_meta", "material", "exposure_ev", "ambient", "background", "grading")]
+        "light", "light_meta", "material", "exposure_ev", "ambient", "background", "grading", "light_spot",
+        "emission")]
 
 
 class _Outputs(C.Structure):
@@ -70,9 +71,9 @@ def lib():
             L.orc_raster_fixed.restype = C.c_int
             L.orc_f32_to_f16.argtypes = [C.c_float]
             L.orc_f32_to_f16.restype = C.c_uint16
-            L.orc_shade_f64.argtypes = [C.POINTER(_Batch), C.c_int32, C.c_int32] + [C.c_void_p] * 8
+            L.orc_shade_f64.argtypes = [C.POINTER(_Batch), C.c_int32, C.c_int32] + [C.c_void_p] * 9
             L.orc_shade_f64.restype = None
-            L.orc_shade_backward_f64.argtypes = [C.POINTER(_Batch), C.c_int32, C.c_int32] + [C.c_void_p] * 11
+            L.orc_shade_backward_f64.argtypes = [C.POINTER(_Batch), C.c_int32, C.c_int32] + [C.c_void_p] * 13
             L.orc_shade_backward_f64.restype = None
             _lib = L
     return _lib
@@ -84,6 +85,12 @@ def _p(a):
 
 def _c(a, dt):
     return np.ascontiguousarray(a, dtype=dt)
+
+
+def _opt(batch, name):
+    """An optional float32 parameter array of the batch, or None."""
+    a = getattr(batch, name, None)
+    return None if a is None else _c(a, np.float32)
 
 
 class _Pinned:
@@ -108,7 +115,7 @@ class _Pinned:
             light_meta=_c(batch.light_meta, np.int32), material=_c(batch.material, np.float32),
             exposure_ev=_c(batch.exposure_ev, np.float32), ambient=_c(batch.ambient, np.float32),
             background=_c(batch.background, np.float32),
-            grading=None if getattr(batch, "grading", None) is None else _c(batch.grading, np.float32))
+            grading=_opt(batch, "grading"), light_spot=_opt(batch, "light_spot"), emission=_opt(batch, "emission"))
         self.batch = _Batch(batch.n_samples, *[_p(self.arrs[n]) for n, _ in _Batch._fields_[1:]])
 
 
@@ -188,35 +195,40 @@ def f32_to_f16_bits(x) -> np.ndarray:
     return np.array([L.orc_f32_to_f16(float(v)) for v in x], np.uint16)
 
 
-def _params64(batch, material=None, light=None, exposure_ev=None, ambient=None):
+def _params64(batch, material=None, light=None, exposure_ev=None, ambient=None, emission=None):
     m = _c(batch.material if material is None else material, np.float64)
     l = _c(batch.light if light is None else light, np.float64)
     e = _c(batch.exposure_ev if exposure_ev is None else exposure_ev, np.float64)
     a = _c(batch.ambient if ambient is None else ambient, np.float64)
-    return m, l, e, a
+    em = getattr(batch, "emission", None) if emission is None else emission
+    return m, l, e, a, None if em is None else _c(em, np.float64)
 
 
-def shade_f64(batch, gb_pos, gb_nrm, gb_mat, material=None, light=None, exposure_ev=None, ambient=None):
+def shade_f64(batch, gb_pos, gb_nrm, gb_mat, material=None, light=None, exposure_ev=None, ambient=None,
+              emission=None):
     """fp64 shading of a fixed G-buffer (the function finite differences are taken of)."""
     pin = _Pinned(batch)
-    m, l, e, a = _params64(batch, material, light, exposure_ev, ambient)
+    m, l, e, a, em = _params64(batch, material, light, exposure_ev, ambient, emission)
     gp, gn, gm = _c(gb_pos, np.float32), _c(gb_nrm, np.float32), _c(gb_mat, np.int32)
     rgb = np.zeros((batch.total_pixels, 3), np.float64)
-    lib().orc_shade_f64(C.byref(pin.batch), 0, batch.n_cams, _p(gp), _p(gn), _p(gm), _p(m), _p(l), _p(e), _p(a), _p(rgb))
+    lib().orc_shade_f64(C.byref(pin.batch), 0, batch.n_cams, _p(gp), _p(gn), _p(gm), _p(m), _p(l), _p(e), _p(a),
+                        _p(em), _p(rgb))
     return rgb
 
 
 def shade_backward_f64(batch, gb_pos, gb_nrm, gb_mat, d_rgb, material=None, light=None, exposure_ev=None,
-                       ambient=None):
-    """fp64 adjoint: (d_material [S,32,4], d_light [S,4,4], d_ev [S])."""
+                       ambient=None, emission=None, return_emission=False):
+    """fp64 adjoint: (d_material [S,32,4], d_light [S,4,4], d_ev [S]), plus d_emission [S,32] last
+    when `return_emission`."""
     pin = _Pinned(batch)
-    m, l, e, a = _params64(batch, material, light, exposure_ev, ambient)
+    m, l, e, a, em = _params64(batch, material, light, exposure_ev, ambient, emission)
     gp, gn, gm = _c(gb_pos, np.float32), _c(gb_nrm, np.float32), _c(gb_mat, np.int32)
     g = _c(d_rgb, np.float64)
     S = batch.n_samples
     dm = np.zeros((S, 32, 4), np.float64)
     dl = np.zeros((S, 4, 4), np.float64)
     de = np.zeros(S, np.float64)
+    dem = np.zeros((S, 32), np.float64)
     lib().orc_shade_backward_f64(C.byref(pin.batch), 0, batch.n_cams, _p(gp), _p(gn), _p(gm), _p(m), _p(l), _p(e),
-                                 _p(a), _p(g), _p(dm), _p(dl), _p(de))
-    return dm, dl, de
+                                 _p(a), _p(em), _p(g), _p(dm), _p(dl), _p(de), _p(dem))
+    return (dm, dl, de, dem) if return_emission else (dm, dl, de)

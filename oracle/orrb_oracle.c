@@ -34,7 +34,16 @@
  *   9  G-buffer: P = depth*((x+1/2-cx)/fx, -(y+1/2-cy)/fy, -1); normal =
  *      sum_i (w_i*iw_i) n_i normalised; material = base + tri_mat; seg id.
  *  10  Blinn-Phong over the sample's lights, inverse-square falloff for
- *      point lights, white specular, times 2^EV, plus ambient*albedo.
+ *      point and spot lights, white specular, plus (ambient + emission) *
+ *      albedo, all times 2^EV.  Emission e is a scalar per material, the
+ *      emitted colour e * albedo (a MuJoCo material's emission, Sec. 4.2).
+ *      A spot light (type 2) is a point light times the cone factor
+ *      S = t^2 (3 - 2t), t = clamp((x - cos_o) / (cos_i - cos_o), 0, 1), x
+ *      the cosine between the spot axis and the direction from the light to
+ *      the point: 1 inside the inner cone, 0 outside the outer one (Sec.
+ *      4.3.1's spotlight angles).  A cone with cos_i <= cos_o, a type other
+ *      than 0 point, 1 directional, 2 spot, or a spot without its cone table
+ *      lights nothing.
  *  11  rgb8 = floor(clamp(rgb,0,1)*255 + 1/2); normal -> binary16 (RNE);
  *      background: rgb = background colour, depth 0, normal 0, seg 0.
  *  12  the adjoint of step 10 at fixed visibility, in fp64.
@@ -313,11 +322,27 @@ static uint8_t quantise(float v) {
 /* ------------------------------------------------------------------ */
 /* step 10: shading in fp32                                            */
 /* ------------------------------------------------------------------ */
+/* the number of lights that shine: 0 for an unknown type or a spot light without its cone table */
+static int32_t light_count(const orc_batch* b, int32_t s) {
+  int32_t count = b->light_meta[s * 2 + 0], type = b->light_meta[s * 2 + 1];
+  int ok = type == 0 || type == 1 || (type == 2 && b->light_spot != NULL);
+  return ok ? count : 0;
+}
+
+/* the spot cone factor of step 10 at cosine x, in fp32 */
+static float spot_f32(float x, float cos_o, float cos_i) {
+  if (!(cos_i > cos_o)) return 0.0f;
+  float t = (x - cos_o) / (cos_i - cos_o);
+  t = t < 0.0f ? 0.0f : (t > 1.0f ? 1.0f : t);
+  return t * t * (3.0f - 2.0f * t);
+}
+
 static void shade_f32(const orc_batch* b, int32_t s, const float* V, int ortho, const float P[3],
                       const float n[3], int32_t mat, float rgb[3]) {
   const float* m = b->material + ((int64_t)s * ORC_MAX_MATERIALS + mat) * 5;
   const float* amb = b->ambient + (int64_t)s * 3;
-  int32_t count = b->light_meta[s * 2 + 0];
+  const float e = b->emission ? b->emission[(int64_t)s * ORC_MAX_MATERIALS + mat] : 0.0f;
+  int32_t count = light_count(b, s);
   int32_t type = b->light_meta[s * 2 + 1];
   float c[3] = {0.0f, 0.0f, 0.0f};
   float Vv[3];
@@ -332,7 +357,7 @@ static void shade_f32(const orc_batch* b, int32_t s, const float* V, int ortho, 
   for (int l = 0; l < count; l++) {
     const float* L4 = b->light + ((int64_t)s * ORC_MAX_LIGHTS + l) * 4;
     float L[3], E;
-    if (type == 0) {
+    if (type != 1) {
       float Lv[3];
       for (int i = 0; i < 3; i++) {
         float lpv = ((V[i * 4 + 0] * L4[0] + V[i * 4 + 1] * L4[1]) + V[i * 4 + 2] * L4[2]) + V[i * 4 + 3];
@@ -342,6 +367,13 @@ static void shade_f32(const orc_batch* b, int32_t s, const float* V, int ortho, 
       float dl = sqrtf(d2);
       for (int i = 0; i < 3; i++) L[i] = Lv[i] / dl;
       E = L4[3] / d2;
+      if (type == 2) { /* the cone about the spot axis, taken to view space like a direction */
+        const float* sp = b->light_spot + ((int64_t)s * ORC_MAX_LIGHTS + l) * 5;
+        float av[3];
+        for (int i = 0; i < 3; i++) av[i] = (V[i * 4 + 0] * sp[0] + V[i * 4 + 1] * sp[1]) + V[i * 4 + 2] * sp[2];
+        float x = -((L[0] * av[0] + L[1] * av[1]) + L[2] * av[2]);
+        E = E * spot_f32(x, sp[3], sp[4]);
+      }
     } else {
       for (int i = 0; i < 3; i++) L[i] = -((V[i * 4 + 0] * L4[0] + V[i * 4 + 1] * L4[1]) + V[i * 4 + 2] * L4[2]);
       E = L4[3];
@@ -363,7 +395,7 @@ static void shade_f32(const orc_batch* b, int32_t s, const float* V, int ortho, 
     for (int k = 0; k < 3; k++) c[k] = c[k] + E * (m[k] * ndl + spec);
   }
   float scale = exp2f(b->exposure_ev[s]);
-  for (int k = 0; k < 3; k++) rgb[k] = scale * (amb[k] * m[k] + c[k]);
+  for (int k = 0; k < 3; k++) rgb[k] = scale * ((amb[k] * m[k] + e * m[k]) + c[k]);
 }
 
 /* ------------------------------------------------------------------ */
@@ -596,30 +628,56 @@ int orc_raster_fixed(int32_t W, int32_t H, int32_t n, const int32_t* X, const in
 typedef struct {
   double L[3], E, ndl, spec, ndh, pw; /* pw = ndh^alpha */
   double H[3], hl, Lv[3], dl, d2;
+  double S, dS; /* spot cone factor and its derivative in the cosine x (1 and 0 for other lights) */
   int lit, has_h;
 } light_term;
 
+/* view-space light positions (or directions to the light) and, for spot lights, view-space axes
+   with the cone cosines: spot[l] = (axis xyz, cos_o, cos_i) */
 static void view_lights_f64(const orc_batch* b, int32_t s, const float* V, const double* light,
-                            double out[ORC_MAX_LIGHTS][3]) {
-  int32_t count = b->light_meta[s * 2], type = b->light_meta[s * 2 + 1];
+                            double out[ORC_MAX_LIGHTS][3], double spot[ORC_MAX_LIGHTS][5]) {
+  int32_t count = light_count(b, s), type = b->light_meta[s * 2 + 1];
   for (int l = 0; l < count; l++) {
     const double* L4 = light + ((int64_t)s * ORC_MAX_LIGHTS + l) * 4;
     for (int i = 0; i < 3; i++) {
       double r = (double)V[i * 4 + 0] * L4[0] + (double)V[i * 4 + 1] * L4[1] + (double)V[i * 4 + 2] * L4[2];
-      out[l][i] = type == 0 ? r + (double)V[i * 4 + 3] : -r;
+      out[l][i] = type == 1 ? -r : r + (double)V[i * 4 + 3];
+    }
+    if (type == 2) {
+      const float* sp = b->light_spot + ((int64_t)s * ORC_MAX_LIGHTS + l) * 5;
+      for (int i = 0; i < 3; i++)
+        spot[l][i] = (double)V[i * 4 + 0] * sp[0] + (double)V[i * 4 + 1] * sp[1] + (double)V[i * 4 + 2] * sp[2];
+      spot[l][3] = sp[3];
+      spot[l][4] = sp[4];
     }
   }
 }
 
+/* spot: NULL, or (view-space axis, cos_o, cos_i) of a spot light */
 static void light_eval(int type, const double Lp[3], double I, const double P[3], const double n[3],
-                       const double Vv[3], double alpha, light_term* t) {
+                       const double Vv[3], double alpha, const double* spot, light_term* t) {
   memset(t, 0, sizeof(*t));
-  if (type == 0) {
+  t->S = 1.0;
+  if (type != 1) {
     for (int i = 0; i < 3; i++) t->Lv[i] = Lp[i] - P[i];
     t->d2 = t->Lv[0] * t->Lv[0] + t->Lv[1] * t->Lv[1] + t->Lv[2] * t->Lv[2];
     t->dl = sqrt(t->d2);
     for (int i = 0; i < 3; i++) t->L[i] = t->Lv[i] / t->dl;
-    t->E = I / t->d2;
+    if (spot) {
+      const double x = -(t->L[0] * spot[0] + t->L[1] * spot[1] + t->L[2] * spot[2]);
+      const double w = spot[4] - spot[3];
+      t->S = 0.0;
+      if (w > 0.0) {
+        double u = (x - spot[3]) / w;
+        if (u >= 1.0) {
+          t->S = 1.0;
+        } else if (u > 0.0) {
+          t->S = u * u * (3.0 - 2.0 * u);
+          t->dS = 6.0 * u * (1.0 - u) / w;
+        }
+      }
+    }
+    t->E = I * t->S / t->d2;
   } else {
     for (int i = 0; i < 3; i++) t->L[i] = Lp[i];
     t->E = I;
@@ -658,16 +716,16 @@ static void pixel_setup_f64(const float* gp, const float* gn, int ortho, double 
 
 void orc_shade_f64(const orc_batch* b, int32_t cam_begin, int32_t cam_end, const float* gb_pos,
                    const float* gb_nrm, const int32_t* gb_mat, const double* material, const double* light,
-                   const double* exposure_ev, const double* ambient, double* rgb) {
+                   const double* exposure_ev, const double* ambient, const double* emission, double* rgb) {
   for (int32_t c = cam_begin; c < cam_end; c++) {
     int32_t s = b->cam_sample[c];
     const float* V = b->cam_view + (int64_t)c * 12;
     int ortho = b->cam_intr[c * 6 + 5] != 0.0f;
     int64_t npx = (int64_t)b->cam_wh[c * 2] * b->cam_wh[c * 2 + 1];
     int64_t base = b->img_offset[c];
-    double Lp[ORC_MAX_LIGHTS][3];
-    view_lights_f64(b, s, V, light, Lp);
-    int32_t count = b->light_meta[s * 2], type = b->light_meta[s * 2 + 1];
+    double Lp[ORC_MAX_LIGHTS][3], sp[ORC_MAX_LIGHTS][5];
+    view_lights_f64(b, s, V, light, Lp, sp);
+    int32_t count = light_count(b, s), type = b->light_meta[s * 2 + 1];
     double scale = exp2(exposure_ev[s]);
     for (int64_t i = 0; i < npx; i++) {
       int64_t o = base + i;
@@ -682,11 +740,13 @@ void orc_shade_f64(const orc_batch* b, int32_t cam_begin, int32_t cam_end, const
       double acc[3] = {0, 0, 0};
       for (int l = 0; l < count; l++) {
         light_term t;
-        light_eval(type, Lp[l], light[((int64_t)s * ORC_MAX_LIGHTS + l) * 4 + 3], P, n, Vv, m[4], &t);
+        light_eval(type, Lp[l], light[((int64_t)s * ORC_MAX_LIGHTS + l) * 4 + 3], P, n, Vv, m[4],
+                   type == 2 ? sp[l] : NULL, &t);
         double spec = m[3] * t.pw;
         for (int k = 0; k < 3; k++) acc[k] += t.E * (m[k] * t.ndl + spec);
       }
-      for (int k = 0; k < 3; k++) rgb[o * 3 + k] = scale * (ambient[s * 3 + k] * m[k] + acc[k]);
+      const double e = emission ? emission[(int64_t)s * ORC_MAX_MATERIALS + mat] : 0.0;
+      for (int k = 0; k < 3; k++) rgb[o * 3 + k] = scale * ((ambient[s * 3 + k] + e) * m[k] + acc[k]);
     }
   }
 }
@@ -694,7 +754,8 @@ void orc_shade_f64(const orc_batch* b, int32_t cam_begin, int32_t cam_end, const
 void orc_shade_backward_f64(const orc_batch* b, int32_t cam_begin, int32_t cam_end, const float* gb_pos,
                             const float* gb_nrm, const int32_t* gb_mat, const double* material,
                             const double* light, const double* exposure_ev, const double* ambient,
-                            const double* d_rgb, double* d_material, double* d_light, double* d_ev) {
+                            const double* emission, const double* d_rgb, double* d_material, double* d_light,
+                            double* d_ev, double* d_emission) {
   const double ln2 = 0.69314718055994530942;
   for (int32_t c = cam_begin; c < cam_end; c++) {
     int32_t s = b->cam_sample[c];
@@ -702,9 +763,9 @@ void orc_shade_backward_f64(const orc_batch* b, int32_t cam_begin, int32_t cam_e
     int ortho = b->cam_intr[c * 6 + 5] != 0.0f;
     int64_t npx = (int64_t)b->cam_wh[c * 2] * b->cam_wh[c * 2 + 1];
     int64_t base = b->img_offset[c];
-    double Lp[ORC_MAX_LIGHTS][3];
-    view_lights_f64(b, s, V, light, Lp);
-    int32_t count = b->light_meta[s * 2], type = b->light_meta[s * 2 + 1];
+    double Lp[ORC_MAX_LIGHTS][3], sp[ORC_MAX_LIGHTS][5];
+    view_lights_f64(b, s, V, light, Lp, sp);
+    int32_t count = light_count(b, s), type = b->light_meta[s * 2 + 1];
     double scale = exp2(exposure_ev[s]);
     double dLp_view[ORC_MAX_LIGHTS][3];
     memset(dLp_view, 0, sizeof(dLp_view));
@@ -722,12 +783,13 @@ void orc_shade_backward_f64(const orc_batch* b, int32_t cam_begin, int32_t cam_e
       for (int l = 0; l < count; l++) {
         light_term t;
         double I = light[((int64_t)s * ORC_MAX_LIGHTS + l) * 4 + 3];
-        light_eval(type, Lp[l], I, P, n, Vv, m[4], &t);
+        light_eval(type, Lp[l], I, P, n, Vv, m[4], type == 2 ? sp[l] : NULL, &t);
         double spec = m[3] * t.pw;
         for (int k = 0; k < 3; k++) acc[k] += t.E * (m[k] * t.ndl + spec);
         sum_endl += t.E * t.ndl;
         sum_epw += t.E * t.pw;
-        /* rgb_k = scale*(amb_k*rho_k + sum_l E_l*(rho_k*ndl_l + ks*ndh_l^alpha)) */
+        /* rgb_k = scale*((amb_k + e)*rho_k + sum_l E_l*(rho_k*ndl_l + ks*ndh_l^alpha)),
+           E_l = I_l S_l / d2_l (S_l = 1 but for spot lights) or I_l (directional) */
         double dE = scale * (gr * t.ndl + G * spec);
         double dndl = t.lit ? scale * t.E * gr : 0.0;
         double dndh = (t.has_h && t.ndh > 0.0) ? scale * t.E * G * m[3] * m[4] * pow(t.ndh, m[4] - 1.0) : 0.0;
@@ -739,9 +801,11 @@ void orc_shade_backward_f64(const orc_batch* b, int32_t cam_begin, int32_t cam_e
           for (int k = 0; k < 3; k++) dLvec[k] += (dH[k] - t.H[k] * hd) / t.hl;
         }
         double* dl = d_light + ((int64_t)s * ORC_MAX_LIGHTS + l) * 4;
-        if (type == 0) {
-          dl[3] += dE / t.d2;
-          double dd2 = -dE * I / (t.d2 * t.d2);
+        if (type != 1) {
+          dl[3] += dE * t.S / t.d2;
+          double dd2 = -dE * I * t.S / (t.d2 * t.d2);
+          if (type == 2) /* x = -(L . axis): dE/dL = I/d2 * S'(x) * (-axis) */
+            for (int k = 0; k < 3; k++) dLvec[k] -= dE * I / t.d2 * t.dS * sp[l][k];
           double ld = t.L[0] * dLvec[0] + t.L[1] * dLvec[1] + t.L[2] * dLvec[2];
           for (int k = 0; k < 3; k++) dLp_view[l][k] += (dLvec[k] - t.L[k] * ld) / t.dl + 2.0 * dd2 * t.Lv[k];
         } else {
@@ -749,20 +813,22 @@ void orc_shade_backward_f64(const orc_batch* b, int32_t cam_begin, int32_t cam_e
           for (int k = 0; k < 3; k++) dLp_view[l][k] += dLvec[k];
         }
       }
+      const double e = emission ? emission[(int64_t)s * ORC_MAX_MATERIALS + mat] : 0.0;
       double* dm = d_material + ((int64_t)s * ORC_MAX_MATERIALS + mat) * 4;
-      for (int k = 0; k < 3; k++) dm[k] += g[k] * scale * (ambient[s * 3 + k] + sum_endl);
+      for (int k = 0; k < 3; k++) dm[k] += g[k] * scale * (ambient[s * 3 + k] + e + sum_endl);
       dm[3] += scale * G * sum_epw;
+      if (d_emission) d_emission[(int64_t)s * ORC_MAX_MATERIALS + mat] += scale * gr;
       double dev = 0.0;
-      for (int k = 0; k < 3; k++) dev += g[k] * scale * (ambient[s * 3 + k] * m[k] + acc[k]);
+      for (int k = 0; k < 3; k++) dev += g[k] * scale * ((ambient[s * 3 + k] + e) * m[k] + acc[k]);
       d_ev[s] += ln2 * dev;
     }
-    /* view-space light gradient back to world: point p_v = R p + t, direction L = -R d */
+    /* view-space light gradient back to world: point or spot p_v = R p + t, direction L = -R d */
     for (int l = 0; l < count; l++) {
       double* dl = d_light + ((int64_t)s * ORC_MAX_LIGHTS + l) * 4;
       for (int j = 0; j < 3; j++) {
         double r = 0.0;
         for (int i = 0; i < 3; i++) r += (double)V[i * 4 + j] * dLp_view[l][i];
-        dl[j] += type == 0 ? r : -r;
+        dl[j] += type == 1 ? -r : r;
       }
     }
   }

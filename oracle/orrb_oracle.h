@@ -20,8 +20,10 @@
  *   inst_pose      [I][3][4]      world-from-object
  *   cam_view       [C][3][4]      camera-from-world, camera looks down -z, +y up
  *   cam_intr       [C][6]         fx, fy, cx, cy, near, type (0 persp, 1 ortho)
- *   light          [S][4][4]      xyz (point position or direction), intensity
+ *   light          [S][4][4]      xyz (point or spot position, or direction), intensity
+ *   light_spot     [S][4][5]      spot axis xyz (unit, world), cos outer, cos inner
  *   material       [S][32][5]     albedo rgb, specular k_s, shininess alpha
+ *   emission       [S][32]        emission e (emitted colour e * albedo)
  *   outputs        flat over pixels; image c starts at pixel img_offset[c]
  */
 #ifndef ORRB_ORACLE_H
@@ -60,12 +62,14 @@ typedef struct {
   const int32_t* cam_wh;        /* [C][2] */
   const int64_t* img_offset;    /* [C] */
   const float* light;           /* [S][4][4] */
-  const int32_t* light_meta;    /* [S][2] count, type (0 point, 1 directional) */
+  const int32_t* light_meta;    /* [S][2] count, type (0 point, 1 directional, 2 spot) */
   const float* material;        /* [S][32][5] */
   const float* exposure_ev;     /* [S] */
   const float* ambient;         /* [S][3] */
   const float* background;      /* [S][3] */
   const float* grading;         /* [S][8] colour-grading epilogue (step 13), or NULL */
+  const float* light_spot;      /* [S][4][5] spot cones (step 10), or NULL */
+  const float* emission;        /* [S][32] material emission (step 10), or NULL for none */
 } orc_batch;
 
 typedef struct {                /* every pointer may be NULL */
@@ -101,21 +105,23 @@ int orc_raster_fixed(int32_t W, int32_t H, int32_t n, const int32_t* X, const in
 uint16_t orc_f32_to_f16(float f);
 
 /* fp64 shading of a G-buffer over images [cam_begin, cam_end), parameters in
- * fp64: material [S][32][5], light [S][4][4], exposure_ev [S], ambient [S][3].
+ * fp64: material [S][32][5], light [S][4][4], exposure_ev [S], ambient [S][3],
+ * emission [S][32] (or NULL); spot cones come from b.
  * Writes rgb [N][3] (background pixels get the background colour). */
 void orc_shade_f64(const orc_batch* b, int32_t cam_begin, int32_t cam_end,
                    const float* gb_pos, const float* gb_nrm, const int32_t* gb_mat,
                    const double* material, const double* light, const double* exposure_ev,
-                   const double* ambient, double* rgb);
+                   const double* ambient, const double* emission, double* rgb);
 
 /* fp64 adjoint of orc_shade_f64 at fixed visibility.  d_rgb [N][3] is dL/d rgb_linear.
  * Accumulates (+=) into d_material [S][32][4] (albedo rgb, specular),
- * d_light [S][4][4] (world position or direction xyz, intensity), d_ev [S]. */
+ * d_light [S][4][4] (world position or direction xyz, intensity), d_ev [S] and,
+ * unless NULL, d_emission [S][32].  The spot axis and cone are not differentiated. */
 void orc_shade_backward_f64(const orc_batch* b, int32_t cam_begin, int32_t cam_end,
                             const float* gb_pos, const float* gb_nrm, const int32_t* gb_mat,
                             const double* material, const double* light, const double* exposure_ev,
-                            const double* ambient, const double* d_rgb,
-                            double* d_material, double* d_light, double* d_ev);
+                            const double* ambient, const double* emission, const double* d_rgb,
+                            double* d_material, double* d_light, double* d_ev, double* d_emission);
 
 #ifdef __cplusplus
 }

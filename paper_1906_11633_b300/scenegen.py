@@ -18,6 +18,10 @@ Workload shapes (the paper's Shadow-Hand scene, Sec. 5, is not available; a
 procedural capsule hand of the same scale stands in for it):
   tiny_batch    -- unit cube on a 10 m plane, 64x64, 1 directional light
   hand_batch    -- 24 capsule links + 5 cm block + 1 m table, 3 cameras
+  benchmark_batch -- the hand scene lit and coloured the way the paper's benchmark
+                  configures it (Sec. 5): 3 spot lights placed by LightSetup with
+                  LightRandomizer levels and cones, FixedHue block materials with
+                  emission, camera jitter or orbit, post-processing grading
   uneven_batch  -- 1..156 capsule links per scene, mixed square resolutions
   perturb_params-- target parameters for the differentiation workload
   poisson_requests -- request stream for the serving loop
@@ -37,6 +41,7 @@ CAM_PERSPECTIVE = 0
 CAM_ORTHOGRAPHIC = 1
 LIGHT_POINT = 0
 LIGHT_DIRECTIONAL = 1
+LIGHT_SPOT = 2
 
 # One stream per randomizer, so the draws of one never shift another's.
 STREAM_MESHES = 1
@@ -50,6 +55,10 @@ STREAM_SCENE = 8
 STREAM_TARGET = 9
 STREAM_REQUESTS = 10
 STREAM_GRADING = 11
+STREAM_FIXED_HUE = 12
+STREAM_LIGHT_SETUP = 13
+STREAM_LIGHT_LEVELS = 14
+STREAM_ORBIT = 15
 
 # --------------------------------------------------------------------------
 # Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
@@ -234,6 +243,11 @@ class Batch:
     # [B, 8] float32 colour-grading epilogue (hue, saturation, contrast, brightness, temperature,
     # tint, grain amplitude, grain seed: an integer below 2^24), or None for none
     grading: Optional[np.ndarray] = None
+    # [B, 4, 5] float32 cones of spot lights (light type 2): world axis xyz (unit), cos of the outer
+    # and of the inner half-angle; or None
+    light_spot: Optional[np.ndarray] = None
+    # [B, 32] float32 material emission e (the emitted colour is e * albedo), or None for none
+    emission: Optional[np.ndarray] = None
 
     @property
     def n_samples(self) -> int:
@@ -298,14 +312,18 @@ def concat_batches(batches: Sequence[Batch]) -> Batch:
         ambient=np.concatenate([b.ambient for b in batches]),
         background=np.concatenate([b.background for b in batches]),
         sample_ids=np.concatenate([b.sample_ids for b in batches]),
-        grading=_concat_grading(batches),
+        grading=_concat_opt(batches, "grading", identity_grading),
+        light_spot=_concat_opt(batches, "light_spot", lambda n: np.zeros((n, MAX_LIGHTS, 5), np.float32)),
+        emission=_concat_opt(batches, "emission", lambda n: np.zeros((n, MAX_MATERIALS), np.float32)),
     )
 
 
-def _concat_grading(batches):
-    if all(b.grading is None for b in batches):
+def _concat_opt(batches, name, neutral):
+    """Concatenate an optional per-sample array; batches without it contribute `neutral(n_samples)`."""
+    if all(getattr(b, name) is None for b in batches):
         return None
-    return np.concatenate([b.grading if b.grading is not None else identity_grading(b.n_samples) for b in batches])
+    return np.concatenate([getattr(b, name) if getattr(b, name) is not None else neutral(b.n_samples)
+                           for b in batches])
 
 
 def select_samples(batch: Batch, idx: Sequence[int]) -> Batch:
@@ -328,6 +346,8 @@ def select_samples(batch: Batch, idx: Sequence[int]) -> Batch:
             ambient=batch.ambient[s:s + 1], background=batch.background[s:s + 1],
             sample_ids=batch.sample_ids[s:s + 1] if len(batch.sample_ids) else np.array([s]),
             grading=batch.grading[s:s + 1] if batch.grading is not None else None,
+            light_spot=batch.light_spot[s:s + 1] if batch.light_spot is not None else None,
+            emission=batch.emission[s:s + 1] if batch.emission is not None else None,
         ))
     return concat_batches(parts)
 
@@ -626,6 +646,142 @@ def hand_batch(seed: int, sample_ids, res: int = 200, n_cams: int = 3, meshes=No
         sample_ids=ids,
         grading=grading_params(seed, ids) if grading else None,
     )
+
+
+# --------------------------------------------------------------------------
+# The paper's randomizer and set-up components (Sec. 4.3.1, 4.3.2) as parameter samplers
+# --------------------------------------------------------------------------
+def hsv_to_rgb(hsv) -> np.ndarray:
+    """HSV in [0, 1]^3 (hue wraps) to RGB, the hexcone model (Smith, SIGGRAPH 1978)."""
+    hsv = np.asarray(hsv, np.float64)
+    h, sat, v = hsv[..., 0] % 1.0, hsv[..., 1], hsv[..., 2]
+    h6 = h * 6.0
+    sector = np.floor(h6)
+    f = h6 - sector
+    p, q, t = v * (1.0 - sat), v * (1.0 - sat * f), v * (1.0 - sat * (1.0 - f))
+    k = sector.astype(np.int64) % 6
+    r = np.choose(k, [v, q, p, p, t, v])
+    g = np.choose(k, [t, v, v, q, p, p])
+    b = np.choose(k, [p, p, t, v, v, q])
+    return np.stack([r, g, b], -1)
+
+
+def glossiness_to_shininess(g) -> np.ndarray:
+    """Glossiness in [0, 1] to the Blinn-Phong exponent 128^g in [1, 128]."""
+    return np.exp(np.asarray(g, np.float64) * math.log(128.0))
+
+
+def fixed_hue_materials(seed: int, sample_ids, hsv, radius=(0.03, 0.15, 0.15),
+                        clamp=((0.0, 1.0), (0.2, 1.0), (0.2, 1.0)), specular=(0.0, 0.6), glossiness=(0.3, 0.9),
+                        emissive_prob=0.15, emissive_power=(0.1, 0.6)):
+    """FixedHueMaterialRandomizer (Sec. 4.3.1): materials near calibrated HSV colours [K, 3].
+
+    Per sample and colour: each HSV component uniform within its radius of the calibrated value,
+    then clamped to its range (hue wraps instead); specular (the metallic level) and glossiness
+    uniform in their ranges; emissive with probability `emissive_prob`, at a power uniform in
+    `emissive_power`.  Returns albedo [B, K, 3], specular [B, K], shininess [B, K], emission [B, K].
+    """
+    ids = np.asarray(sample_ids, dtype=np.int64).reshape(-1)
+    hsv = np.asarray(hsv, np.float64).reshape(-1, 3)
+    K = len(hsv)
+    u = uniform(seed, STREAM_FIXED_HUE, ids, 7 * K).reshape(len(ids), K, 7)
+    h = hsv + np.asarray(radius) * (2.0 * u[..., :3] - 1.0)
+    h[..., 0] %= 1.0
+    for c in (1, 2):
+        h[..., c] = np.clip(h[..., c], clamp[c][0], clamp[c][1])
+    albedo = hsv_to_rgb(h)
+    ks = specular[0] + (specular[1] - specular[0]) * u[..., 3]
+    alpha = glossiness_to_shininess(glossiness[0] + (glossiness[1] - glossiness[0]) * u[..., 4])
+    emission = np.where(u[..., 5] < emissive_prob,
+                        emissive_power[0] + (emissive_power[1] - emissive_power[0]) * u[..., 6], 0.0)
+    return albedo, ks, alpha, emission
+
+
+def light_setup(seed: int, sample_ids, n_lights: int, target, distance=(0.35, 0.6), height=(0.4, 0.7)):
+    """LightSetup (Sec. 4.3.2): `n_lights` lights about `target`, each at a horizontal distance and
+    a height above it uniform in the ranges, spread evenly in azimuth from a uniform offset, and
+    each pointed at the target (LookAt).  Returns positions [B, n, 3] and unit axes [B, n, 3]."""
+    ids = np.asarray(sample_ids, dtype=np.int64).reshape(-1)
+    u = uniform(seed, STREAM_LIGHT_SETUP, ids, 1 + 2 * n_lights)
+    az = 2.0 * math.pi * (u[:, :1] + np.arange(n_lights)[None, :] / n_lights)
+    d = distance[0] + (distance[1] - distance[0]) * u[:, 1:1 + n_lights]
+    hgt = height[0] + (height[1] - height[0]) * u[:, 1 + n_lights:]
+    target = np.asarray(target, np.float64)
+    pos = target + np.stack([d * np.cos(az), d * np.sin(az), hgt], -1)
+    axis = target - pos
+    return pos, axis / np.linalg.norm(axis, axis=-1, keepdims=True)
+
+
+def light_levels(seed: int, sample_ids, n_lights: int, total=(0.5, 1.0), weight=(0.5, 1.0),
+                 outer_deg=(25.0, 45.0), softness=(0.1, 0.4)):
+    """LightRandomizer (Sec. 4.3.1): the total illumination uniform in `total`, split over the
+    lights in proportion to relative weights uniform in `weight`; spot cones with an outer
+    half-angle uniform in `outer_deg` and an inner one `1 - softness` times it.  Returns
+    intensities [B, n] (summing to the total), cos outer [B, n] and cos inner [B, n]."""
+    ids = np.asarray(sample_ids, dtype=np.int64).reshape(-1)
+    u = uniform(seed, STREAM_LIGHT_LEVELS, ids, 1 + 3 * n_lights)
+    T = total[0] + (total[1] - total[0]) * u[:, :1]
+    w = weight[0] + (weight[1] - weight[0]) * u[:, 1:1 + n_lights]
+    intensity = T * w / w.sum(axis=1, keepdims=True)
+    outer = np.radians(outer_deg[0] + (outer_deg[1] - outer_deg[0]) * u[:, 1 + n_lights:1 + 2 * n_lights])
+    inner = outer * (1.0 - (softness[0] + (softness[1] - softness[0]) * u[:, 1 + 2 * n_lights:]))
+    return intensity, np.cos(outer), np.cos(inner)
+
+
+def orbit_views(seed: int, sample_ids, n_cams: int, poi, radius=(0.4, 0.6), elevation_deg=(20.0, 70.0)):
+    """CameraRandomizer, Orbit mode (Sec. 4.3.1): every camera at a radius and elevation uniform in
+    the ranges and a uniform azimuth about the point of interest, looking at it.  Returns
+    camera-from-world matrices [B * n_cams, 3, 4] and their samples [B * n_cams]."""
+    ids = np.asarray(sample_ids, dtype=np.int64).reshape(-1)
+    u = uniform(seed, STREAM_ORBIT, ids, 3 * n_cams).reshape(len(ids), n_cams, 3)
+    r = radius[0] + (radius[1] - radius[0]) * u[..., 0]
+    el = np.radians(elevation_deg[0] + (elevation_deg[1] - elevation_deg[0]) * u[..., 1])
+    az = 2.0 * math.pi * u[..., 2]
+    poi = np.asarray(poi, np.float64)
+    eye = poi + r[..., None] * np.stack([np.cos(el) * np.cos(az), np.cos(el) * np.sin(az), np.sin(el)], -1)
+    eye = eye.reshape(-1, 3)
+    views = view_matrix(look_at(eye, np.broadcast_to(poi, eye.shape)), eye)
+    return views, np.repeat(np.arange(len(ids)), n_cams).astype(np.int32)
+
+
+# the block's six calibrated face colours (HSV): red, orange, yellow, green, blue, purple
+BLOCK_HSV = np.array([[0.00, 0.85, 0.80], [0.08, 0.85, 0.85], [0.15, 0.80, 0.85],
+                      [0.33, 0.70, 0.60], [0.60, 0.75, 0.70], [0.78, 0.60, 0.60]])
+N_SPOTS = 3
+
+
+def benchmark_batch(seed: int, sample_ids, res: int = 200, n_cams: int = 3, orbit: bool = False,
+                    grading: bool = True, meshes=None) -> Batch:
+    """The hand scene configured like the paper's benchmark (Sec. 5) where this renderer can: three
+    spot lights placed by LightSetup about the block with LightRandomizer levels and cones,
+    FixedHue materials (with emission) for the block's faces, the material randomizer for the
+    hand and the table, camera jitter (or orbit), post-processing grading.  Shadows are not
+    rendered."""
+    b = hand_batch(seed, sample_ids, res=res, n_cams=n_cams, meshes=meshes, grading=grading)
+    ids = b.sample_ids
+    B = len(ids)
+    pos, axis = light_setup(seed, ids, N_SPOTS, BLOCK_CENTRE)
+    inten, cos_o, cos_i = light_levels(seed, ids, N_SPOTS)
+    light = np.zeros((B, MAX_LIGHTS, 4))
+    light[:, :N_SPOTS, :3] = pos
+    light[:, :N_SPOTS, 3] = inten
+    spot = np.zeros((B, MAX_LIGHTS, 5))
+    spot[:, :N_SPOTS, :3] = axis
+    spot[:, :N_SPOTS, 3] = cos_o
+    spot[:, :N_SPOTS, 4] = cos_i
+    meta = np.tile([[N_SPOTS, LIGHT_SPOT]], (B, 1))
+    mat = b.material.astype(np.float64).copy()
+    albedo, ks, alpha, emis = fixed_hue_materials(seed, ids, BLOCK_HSV)
+    mat[:, 1:7, :3], mat[:, 1:7, 3], mat[:, 1:7, 4] = albedo, ks, alpha
+    emission = np.zeros((B, MAX_MATERIALS))
+    emission[:, 1:7] = emis
+    kw = dict(light=light.astype(np.float32), light_meta=meta.astype(np.int32),
+              light_spot=spot.astype(np.float32), material=mat.astype(np.float32),
+              emission=emission.astype(np.float32))
+    if orbit:
+        views, owner = orbit_views(seed, ids, n_cams, BLOCK_CENTRE)
+        kw.update(cam_view=views.astype(np.float32), cam_sample=owner)
+    return b.with_params(**kw)
 
 
 # --------------------------------------------------------------------------

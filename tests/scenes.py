@@ -31,7 +31,10 @@ def pose(R=None, t=(0, 0, 0)):
 
 
 def single_sample(meshes, inst_mesh, poses, cams, seg=None, mat_base=None, lights=(), light_type=sg.LIGHT_POINT,
-                  albedo=None, specular=0.0, shininess=1.0, ev=0.0, ambient=(0, 0, 0), background=(0, 0, 0)):
+                  albedo=None, specular=0.0, shininess=1.0, ev=0.0, ambient=(0, 0, 0), background=(0, 0, 0),
+                  spots=None, emission=None):
+    """One sample.  `spots`: per light (axis xyz, cos outer, cos inner) for spot lights;
+    `emission`: a scalar or [32] per-slot material emission."""
     n = len(inst_mesh)
     seg = np.arange(1, n + 1) if seg is None else np.asarray(seg)
     mat_base = np.zeros(n) if mat_base is None else np.asarray(mat_base)
@@ -64,4 +67,16 @@ def single_sample(meshes, inst_mesh, poses, cams, seg=None, mat_base=None, light
         ambient=np.asarray(ambient, np.float32).reshape(1, 3),
         background=np.asarray(background, np.float32).reshape(1, 3),
         sample_ids=np.zeros(1, np.int64),
+        light_spot=None if spots is None else _spot_table(spots),
+        emission=None if emission is None else np.broadcast_to(np.asarray(emission, np.float32),
+                                                               (1, sg.MAX_MATERIALS)).copy(),
     )
+
+
+def _spot_table(spots):
+    t = np.zeros((1, sg.MAX_LIGHTS, 5), np.float32)
+    for i, (axis, cos_o, cos_i) in enumerate(spots):
+        t[0, i, :3] = axis
+        t[0, i, 3] = cos_o
+        t[0, i, 4] = cos_i
+    return t

@@ -115,3 +115,51 @@ def test_unused_parameters_have_exactly_zero_gradient(oracle):
     assert len(unused) > 0
     assert (dm[0, unused] == 0).all()
     assert (dl[0, b.light_meta[0, 0]:] == 0).all()
+
+
+def test_spot_and_emission_adjoint_matches_central_differences(oracle):
+    """The benchmark-like scene: three spot lights (the cone factor depends on the light position)
+    and emissive block faces; light, exposure and emission gradients against fp64 differences."""
+    b = sg.benchmark_batch(5, np.arange(2), res=40, grading=False)
+    b = b.with_params(emission=b.emission + np.float32(0.05))     # every slot emissive
+    o = oracle.render(b, gbuffer=True)
+    gb = (o["gb_pos"], o["gb_nrm"], o["gb_mat"])
+    m, l = b.material.astype(np.float64), b.light.astype(np.float64)
+    e, em = b.exposure_ev.astype(np.float64), b.emission.astype(np.float64)
+    mat_t, light_t, ev_t = sg.perturb_params(b, 1)
+    tgt = oracle.shade_f64(b, *gb, material=mat_t, light=light_t, exposure_ev=ev_t, emission=em * 0.7)
+    fg = gb[2] >= 0
+
+    def loss(mm, ll, ee, emm):
+        rgb = oracle.shade_f64(b, *gb, material=mm, light=ll, exposure_ev=ee, emission=emm)
+        return ((rgb[fg] - tgt[fg]) ** 2).sum()
+
+    rgb = oracle.shade_f64(b, *gb, material=m, light=l, exposure_ev=e, emission=em)
+    g = 2.0 * (rgb - tgt)
+    g[~fg] = 0.0
+    dm, dl, de, dem = oracle.shade_backward_f64(b, *gb, g, material=m, light=l, exposure_ev=e, emission=em,
+                                                return_emission=True)
+    # the ramp of some cone crosses pixels of the scene, so the cone term is exercised
+    cams = np.repeat(b.cam_sample, b.cam_wh[:, 0] * b.cam_wh[:, 1])
+    checks = [("l", (s, li, k), dl[s, li, k]) for s in range(2) for li in range(3) for k in range(4)]
+    checks += [("e", (s,), de[s]) for s in range(2)]
+    for s in range(2):
+        used = np.unique(gb[2][fg & (cams == s)])
+        checks += [("em", (s, mat), dem[s, mat]) for mat in used[:6]]
+        checks += [("m", (s, mat, k), dm[s, mat, k]) for mat in used[:3] for k in range(3)]
+    fd, an = [], []
+    for kind_, idx, a in checks:
+        vals = []
+        for sgn in (1, -1):
+            arrs = {"m": m.copy(), "l": l.copy(), "e": e.copy(), "em": em.copy()}
+            arrs[kind_][idx] += sgn * H_FD
+            vals.append(loss(arrs["m"], arrs["l"], arrs["e"], arrs["em"]))
+        fd.append((vals[0] - vals[1]) / (2 * H_FD))
+        an.append(a)
+    fd, an = np.array(fd), np.array(an)
+    assert np.abs(an).max() > 0
+    assert _rel(an, fd).max() < 1e-4, (_rel(an, fd).max(), checks[int(np.argmax(_rel(an, fd)))])
+    # emission closed form: dL/de = 2^EV sum_px g . rho over the slot's pixels
+    s, mat = 0, int(np.unique(gb[2][fg & (cams == 0)])[0])
+    px = fg & (cams == s) & (gb[2] == mat)
+    np.testing.assert_allclose(dem[s, mat], 2.0 ** e[s] * (g[px] @ m[s, mat, :3]).sum(), rtol=1e-10)
