@@ -26,9 +26,12 @@
  *     triangles in mesh order) and sub the half of a near-clipped quad;
  *   - normal = perspective-correct interpolated view-space unit normal,
  *     stored as IEEE binary16; seg = the instance's id, 0 for background;
- *   - rgb = 2^EV * (ambient*albedo + sum_l E_l (albedo*max(0,n.L) +
- *     k_s*max(0,n.H)^alpha [n.L > 0])), E = I/d^2 for point lights and I for
- *     directional ones, quantised as floor(clamp(rgb,0,1)*255 + 1/2).
+ *   - rgb = 2^EV * ((ambient + e)*albedo + sum_l E_l (albedo*max(0,n.L) +
+ *     k_s*max(0,n.H)^alpha [n.L > 0])), e the material's emission, E = I/d^2
+ *     for point lights, I for directional ones and I S/d^2 for spot lights,
+ *     S = t^2 (3 - 2t), t = clamp((x - cos_o)/(cos_i - cos_o), 0, 1), x the
+ *     cosine between the spot axis and the direction from the light;
+ *     quantised as floor(clamp(rgb,0,1)*255 + 1/2).
  *
  * Conventions of every entry point.
  *   Memory:    every device buffer is allocated and owned by the caller; the
@@ -148,9 +151,11 @@ typedef struct {
   const float* cam_intr;         /* [n_cams][6] fx, fy, cx, cy (pixels), near (m), type (0 persp, 1 ortho) */
   const int32_t* cam_wh;         /* [n_cams][2] width, height */
   const int64_t* img_offset;     /* [n_cams] first pixel of each image in the flat outputs */
-  const float* light;            /* [n_samples][4][4] world position (point) or travel direction
+  const float* light;            /* [n_samples][4][4] world position (point, spot) or travel direction
                                     (directional) xyz, intensity */
-  const int32_t* light_meta;     /* [n_samples][2] light count (0..4), type (0 point, 1 directional) */
+  const int32_t* light_meta;     /* [n_samples][2] light count (0..4), type (0 point, 1 directional,
+                                    2 spot: needs light_spot).  Another type, or a spot type without
+                                    light_spot, sets ORRB_DEV_BAD_LIGHTS and lights nothing. */
   const float* material;         /* [n_samples][32][5] albedo rgb, specular k_s, shininess alpha */
   const float* exposure_ev;      /* [n_samples] exposure in stops */
   const float* ambient;          /* [n_samples][3] */
@@ -165,6 +170,13 @@ typedef struct {
                                     the seed, the camera's index within its sample and the pixel's
                                     index within its image.  Row: h, s, k, b, t, u, a, seed (an
                                     integer below 2^24).  rgb_linear is not graded. */
+  const float* light_spot;       /* [n_samples][4][5] or NULL: the cones of spot lights (the
+                                    LightRandomizer's spotlight angles, Sec. 4.3.1): world axis xyz
+                                    (unit length, the direction the spot points), cos of the outer
+                                    and of the inner half-angle.  A cone with cos_inner <= cos_outer
+                                    lights nothing.  Read only for samples of light type 2. */
+  const float* emission;         /* [n_samples][32] or NULL (none): material emission e, the emitted
+                                    colour being e * albedo (a MuJoCo material's emission, Sec. 4.2) */
 } orrb_batch_desc;
 
 /* Caller-preallocated outputs, flat over all pixels of all images (image c
@@ -245,6 +257,7 @@ typedef struct {
   float* d_material;   /* device, [n_samples][32][4]: d albedo rgb, d specular (overwritten) */
   float* d_light;      /* device, [n_samples][4][4]: d world position/direction xyz, d intensity */
   float* d_exposure;   /* device, [n_samples] */
+  float* d_emission;   /* device, [n_samples][32], or NULL: d emission (overwritten) */
 } orrb_param_grads;
 
 /* Workspace bytes of orrb_shade_backward for `shape` (partial sums). */
@@ -253,7 +266,8 @@ orrb_status orrb_backward_workspace_size(orrb_ctx* ctx, const orrb_batch_shape* 
 /* Gradients of a loss L w.r.t. the randomized material, light and exposure
  * parameters (Sec. 4.3.1), given d_rgb_linear = dL/d rgb_linear [N][3] and
  * the G-buffer a render wrote.  Visibility is held fixed (it does not depend
- * on these parameters).  The reduction over pixels runs in a fixed order, so
+ * on these parameters).  Spot axes and cones, shininess and the ambient term
+ * are not differentiated.  The reduction over pixels runs in a fixed order, so
  * results are bit-identical from run to run. */
 orrb_status orrb_shade_backward(orrb_ctx* ctx, const orrb_batch_shape* shape, const orrb_batch_desc* batch,
                                 const float* gbuffer, const float* d_rgb_linear, const orrb_param_grads* grads,

@@ -252,6 +252,8 @@ void fill_batch(Params& p, const orrb_batch_shape& s, const orrb_batch_desc& b) 
   p.ambient = b.ambient;
   p.background = b.background;
   p.grading = b.grading;
+  p.light_spot = b.light_spot;
+  p.emission = b.emission;
   p.total_pixels = s.total_pixels;
   p.t_max = s.max_tris_per_sample;
   p.inst_max = s.max_inst_per_sample;
@@ -569,6 +571,7 @@ orrb_status orrb_shade_backward(orrb_ctx* ctx, const orrb_batch_shape* shape, co
   bp.d_material = grads->d_material;
   bp.d_light = grads->d_light;
   bp.d_exposure = grads->d_exposure;
+  bp.d_emission = grads->d_emission;
   bp.partial = reinterpret_cast<float*>(static_cast<char*>(workspace) + 256);
   bp.blocks_per_img = bpi;
   char err[256] = {0};

@@ -3,8 +3,8 @@
 // Given the G-buffer a render wrote (view-space position, unit normal,
 // material slot per pixel) and dL/d rgb_linear, computes dL/d of the
 // randomized parameters the paper's randomizers draw (Sec. 4.3.1): per
-// material albedo (rgb) and specular k_s, per light position (or direction)
-// and intensity, and the exposure.  Visibility does not depend on these
+// material albedo (rgb), specular k_s and emission, per light position (or
+// direction) and intensity, and the exposure.  Visibility does not depend on these
 // parameters, so the gradient is exact, not an approximation.
 //
 // Pass 1 (grid = images x blocks_per_img): each CTA owns a fixed pixel range
@@ -35,11 +35,13 @@ constexpr int kBwdWarps = kBwdThreads / 32;
 struct BwdShared {
   float V[12];
   float lv[kMaxLights][4];
+  float la[kMaxLights][4];  // spot lights: view-space axis and -cos_o, over cos_i - cos_o
   float mat[kMaxMaterials][5];
+  float emis[kMaxMaterials];
   float amb[3];
   float scale;
   int n_lights, light_type, ortho, s;
-  float wmat[kBwdWarps][kMaxMaterials][4];      // per-warp material sums
+  float wmat[kBwdWarps][kMaxMaterials][5];      // per-warp material sums (albedo, specular, emission)
   float wred[kBwdWarps][kMaxLights * 4 + 1];    // per-warp light + exposure sums
 };
 
@@ -61,23 +63,35 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
     for (int k = 0; k < 12; k++) sh.V[k] = p.cam_view[cam * 12 + k];
     sh.ortho = p.cam_intr[cam * 6 + 5] != 0.0f;
     int nl = p.light_meta[s * 2];
+    const int lt = p.light_meta[s * 2 + 1];
+    if (!(lt == 0 || lt == 1 || (lt == 2 && p.light_spot))) nl = 0;  // lights nothing (as in the render)
     sh.n_lights = nl < 0 ? 0 : (nl > kMaxLights ? kMaxLights : nl);
-    sh.light_type = p.light_meta[s * 2 + 1];
+    sh.light_type = lt;
     for (int l = 0; l < sh.n_lights; l++) {
       const float* L4 = p.light + (s * kMaxLights + l) * 4;
       for (int i = 0; i < 3; i++) {
         float r = sh.V[i * 4 + 0] * L4[0] + sh.V[i * 4 + 1] * L4[1] + sh.V[i * 4 + 2] * L4[2];
-        sh.lv[l][i] = sh.light_type == 0 ? r + sh.V[i * 4 + 3] : -r;
+        sh.lv[l][i] = lt == 1 ? -r : r + sh.V[i * 4 + 3];
       }
       sh.lv[l][3] = L4[3];
+      if (lt == 2) {
+        const float* sp = p.light_spot + (s * kMaxLights + l) * 5;
+        const bool cone = sp[4] > sp[3];
+        const float w = cone ? 1.0f / (sp[4] - sp[3]) : 0.0f;
+        for (int i = 0; i < 3; i++)
+          sh.la[l][i] = (sh.V[i * 4 + 0] * sp[0] + sh.V[i * 4 + 1] * sp[1] + sh.V[i * 4 + 2] * sp[2]) * w;
+        sh.la[l][3] = cone ? -sp[3] * w : -1.0f;
+      }
     }
     sh.scale = exp2f(p.exposure_ev[s]);
     for (int k = 0; k < 3; k++) sh.amb[k] = p.ambient[s * 3 + k];
   }
-  for (int k = tid; k < kBwdWarps * kMaxMaterials * 4; k += kBwdThreads) (&sh.wmat[0][0][0])[k] = 0.0f;
+  for (int k = tid; k < kBwdWarps * kMaxMaterials * 5; k += kBwdThreads) (&sh.wmat[0][0][0])[k] = 0.0f;
   __syncthreads();
   for (int k = tid; k < kMaxMaterials * 5; k += kBwdThreads)
     sh.mat[k / 5][k % 5] = p.material[(size_t)sh.s * kMaxMaterials * 5 + k];
+  for (int k = tid; k < kMaxMaterials; k += kBwdThreads)
+    sh.emis[k] = p.emission ? p.emission[(size_t)sh.s * kMaxMaterials + k] : 0.0f;
   __syncthreads();
 
   const long long N = p.total_pixels;
@@ -96,7 +110,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
   for (long long r0 = i0; r0 < i1; r0 += kBwdThreads) {
     const long long i = r0 + tid;
     int mat = -1;
-    float dm[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    float dm[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
     if (i < i1) {
       const long long o = base + i;
       mat = __float_as_int(bp.gbuffer[6 * N + o]);
@@ -125,12 +139,19 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
           if (l >= sh.n_lights) break;
           float L[3], Lv[3] = {0.0f, 0.0f, 0.0f}, E, d2 = 1.0f, rinv = 1.0f;
           const float I = sh.lv[l][3];
-          if (sh.light_type == 0) {
+          float S = 1.0f, dS = 0.0f;  // spot cone factor, and its derivative in t
+          if (sh.light_type != 1) {
             for (int k = 0; k < 3; k++) Lv[k] = sh.lv[l][k] - P[k];
             d2 = Lv[0] * Lv[0] + Lv[1] * Lv[1] + Lv[2] * Lv[2];
             rinv = rsqrtf(d2);
             for (int k = 0; k < 3; k++) L[k] = Lv[k] * rinv;
-            E = I * (rinv * rinv);
+            if (sh.light_type == 2) {
+              const float t = __saturatef(L[0] * -sh.la[l][0] + L[1] * -sh.la[l][1] + L[2] * -sh.la[l][2] +
+                                          sh.la[l][3]);
+              S = t * t * (3.0f - 2.0f * t);
+              dS = 6.0f * t * (1.0f - t);  // zero where t is clamped
+            }
+            E = I * S * (rinv * rinv);
           } else {
             for (int k = 0; k < 3; k++) L[k] = sh.lv[l][k];
             E = I;
@@ -164,9 +185,14 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
             float hd = H[0] * dH[0] + H[1] * dH[1] + H[2] * dH[2];
             for (int k = 0; k < 3; k++) dL[k] += (dH[k] - H[k] * hd) * rh;
           }
-          if (sh.light_type == 0) {
-            dI[l] += dE * (rinv * rinv);
-            const float dd2 = -dE * I * (rinv * rinv) * (rinv * rinv);
+          if (sh.light_type != 1) {
+            dI[l] += dE * S * (rinv * rinv);
+            const float dd2 = -dE * I * S * (rinv * rinv) * (rinv * rinv);
+            // spot: t = -(L . a) / (cos_i - cos_o) + ..., so dE/dL = -I |Lv|^-2 S'(t) la_xyz
+            if (sh.light_type == 2) {
+              const float ds = dE * I * (rinv * rinv) * dS;
+              for (int k = 0; k < 3; k++) dL[k] -= ds * sh.la[l][k];
+            }
             const float ld = L[0] * dL[0] + L[1] * dL[1] + L[2] * dL[2];
             for (int k = 0; k < 3; k++) dlv[l][k] += (dL[k] - L[k] * ld) * rinv + 2.0f * dd2 * Lv[k];
           } else {
@@ -174,12 +200,14 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
             for (int k = 0; k < 3; k++) dlv[l][k] += dL[k];
           }
         }
-        for (int k = 0; k < 3; k++) dm[k] = g[k] * scale * (sh.amb[k] + sum_endl);
+        const float em = sh.emis[mat];
+        for (int k = 0; k < 3; k++) dm[k] = g[k] * scale * (sh.amb[k] + em + sum_endl);
         dm[3] = scale * G * sum_epw;
+        dm[4] = scale * gr;
         // d rgb_k / d ev = ln 2 * rgb_k, and sum_k g_k rgb_k / scale
-        //   = sum_k g_k amb_k m_k + (g . m) sum E ndl + (sum g) k_s sum E pw
+        //   = sum_k g_k amb_k m_k + (g . m) (emission + sum E ndl) + (sum g) k_s sum E pw
         const float e = g[0] * sh.amb[0] * m[0] + g[1] * sh.amb[1] * m[1] + g[2] * sh.amb[2] * m[2] +
-                        gr * sum_endl + G * m[3] * sum_epw;
+                        gr * (em + sum_endl) + G * m[3] * sum_epw;
         dev += ln2 * scale * e;
       }
     }
@@ -191,11 +219,13 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
       const bool mine = mat == mm;
       float v0 = warp_sum(mine ? dm[0] : 0.0f), v1 = warp_sum(mine ? dm[1] : 0.0f);
       float v2 = warp_sum(mine ? dm[2] : 0.0f), v3 = warp_sum(mine ? dm[3] : 0.0f);
+      float v4 = warp_sum(mine ? dm[4] : 0.0f);
       if (lane == 0) {
         sh.wmat[warp][mm][0] += v0;
         sh.wmat[warp][mm][1] += v1;
         sh.wmat[warp][mm][2] += v2;
         sh.wmat[warp][mm][3] += v3;
+        sh.wmat[warp][mm][4] += v4;
       }
       pending &= ~__ballot_sync(kFull, mine);
     }
@@ -215,10 +245,11 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
   }
   __syncthreads();
   float* out = bp.partial + ((size_t)cam * bp.blocks_per_img + blk) * kGradFloats;
-  for (int k = tid; k < kMaxMaterials * 4; k += kBwdThreads) {
+  for (int k = tid; k < kMaxMaterials * 5; k += kBwdThreads) {
     float v = 0.0f;
     for (int w = 0; w < kBwdWarps; w++) v += (&sh.wmat[w][0][0])[k];
-    out[k] = v;
+    const int mm = k / 5, c = k % 5;
+    out[c < 4 ? mm * 4 + c : kGradEmission + mm] = v;
   }
   if (tid < kMaxLights) {
     const int l = tid;
@@ -229,7 +260,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
     }
     for (int w = 0; w < kBwdWarps; w++) di += sh.wred[w][l * 4 + 3];
     // view -> world: point p_v = R p + t, so dp = R^T dp_v; direction L_v = -R d, so dd = -R^T dL_v
-    const float sgn = sh.light_type == 0 ? 1.0f : -1.0f;
+    const float sgn = sh.light_type == 1 ? -1.0f : 1.0f;
     for (int j = 0; j < 3; j++)
       out[kMaxMaterials * 4 + l * 4 + j] =
           sgn * (sh.V[0 * 4 + j] * dv[0] + sh.V[1 * 4 + j] * dv[1] + sh.V[2 * 4 + j] * dv[2]);
@@ -243,6 +274,8 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
 }
 
 // One thread per (sample, gradient float): sum the sample's partial rows in (camera, block) order.
+constexpr int kReduceThreads = 192;
+static_assert(kGradFloats <= kReduceThreads, "one thread per gradient float");
 __global__ void backward_reduce_kernel(BackwardParams bp) {
   const Params& p = bp.base;
   const int s = blockIdx.x, k = threadIdx.x;
@@ -254,8 +287,10 @@ __global__ void backward_reduce_kernel(BackwardParams bp) {
     if (bp.d_material) bp.d_material[(size_t)s * kMaxMaterials * 4 + k] = v;
   } else if (k < kMaxMaterials * 4 + kMaxLights * 4) {
     if (bp.d_light) bp.d_light[(size_t)s * kMaxLights * 4 + (k - kMaxMaterials * 4)] = v;
-  } else {
+  } else if (k < kGradEmission) {
     if (bp.d_exposure) bp.d_exposure[s] = v;
+  } else {
+    if (bp.d_emission) bp.d_emission[(size_t)s * kMaxMaterials + (k - kGradEmission)] = v;
   }
 }
 
@@ -267,7 +302,7 @@ int launch_backward(const BackwardParams& bp, int threads, void* stream, char* e
   backward_partial_kernel<<<dim3(bp.base.n_cams, bp.blocks_per_img), kBwdThreads, 0, st>>>(bp);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) {
-    backward_reduce_kernel<<<bp.base.n_samples, 160, 0, st>>>(bp);
+    backward_reduce_kernel<<<bp.base.n_samples, kReduceThreads, 0, st>>>(bp);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) {

@@ -71,6 +71,8 @@ struct Params {
   const float* ambient;
   const float* background;
   const float* grading;  // [n_samples][8] or null
+  const float* light_spot;  // [n_samples][4][5] or null
+  const float* emission;    // [n_samples][32] or null
   // outputs (device, any may be null)
   uint8_t* rgb;
   float* depth;
@@ -140,10 +142,13 @@ struct BackwardParams {
   float* d_material;
   float* d_light;
   float* d_exposure;
+  float* d_emission;     // or null
   float* partial;        // [n_cams][blocks_per_img][kGradFloats]
   int32_t blocks_per_img;
 };
-constexpr int kGradFloats = kMaxMaterials * 4 + kMaxLights * 4 + 1;  // 145
+// per partial row: material [32][4], light [4][4], exposure, emission [32]
+constexpr int kGradEmission = kMaxMaterials * 4 + kMaxLights * 4 + 1;
+constexpr int kGradFloats = kGradEmission + kMaxMaterials;  // 177
 int launch_backward(const BackwardParams& p, int threads, void* stream, char* err, size_t errlen);
 
 }  // namespace orrb

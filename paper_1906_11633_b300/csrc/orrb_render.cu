@@ -53,6 +53,10 @@ namespace {
 constexpr unsigned long long kEmpty = ~0ull;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kPlainRasterSplit = 8;  // plain mode: CTAs sharing one image's tiles
+// optional features of a batch, each compiled into kernel instances of its own
+constexpr int kFeatGrade = 1;  // colour grading of the rgb output
+constexpr int kFeatTrack = 2;  // tracker rows
+constexpr int kFeatLight = 4;  // a cone table (spot lights may occur) or material emission
 
 // The PCG hash (Jarzynski and Olano, "Hash Functions for GPU Rendering", JCGT 2020): one LCG
 // step, a random xorshift and a multiply.
@@ -72,7 +76,10 @@ struct ImageInfo {
   int n_lights, light_type;
   float scale;
   float amb[3], bg[3];
-  alignas(16) float lv[kMaxLights][4];  // view-space light position (point) or direction to the light, intensity
+  alignas(16) float lv[kMaxLights][4];  // view-space light position (point, spot) or direction to the light, intensity
+  // spot lights: the view-space axis a and -cos_o, both over cos_i - cos_o, so that the cone's
+  // t = (x - cos_o) / (cos_i - cos_o) = -(Lv . a) |Lv|^-1 + la[3] (a null cone: 0, 0, 0, -1)
+  alignas(16) float la[kMaxLights][4];
   // colour grading of the rgb output (when the batch has it): the affine map of its white
   // balance, hue, saturation, contrast and brightness (rows of A | t), the grain amplitude and
   // the grain hash of (seed, camera within the sample)
@@ -83,7 +90,7 @@ struct ImageInfo {
 
 struct CtaShared {
   ImageInfo im;
-  alignas(16) float mat[kMaxMaterials][8];  // albedo rgb, specular, shininess (padded: two vector loads)
+  alignas(16) float mat[kMaxMaterials][8];  // albedo rgb, specular, shininess, emission (padded: vector loads)
   int n_vis, n_big, next_tile, next_job, img;
   int bin_overflow;  // phase B: some tile got more keys than its share of the bin array
   int help_slot, help_cam;
@@ -274,8 +281,13 @@ __device__ void setup_image(const Params& p, int cam, CtaShared& sh, int* mprefi
       flag_status(p, ORRB_DEV_BAD_LIGHTS);
       nl = nl < 0 ? 0 : kMaxLights;
     }
+    const int lt = p.light_meta[s * 2 + 1];
+    if (!(lt == 0 || lt == 1 || (lt == 2 && p.light_spot))) {  // an unknown type lights nothing
+      flag_status(p, ORRB_DEV_BAD_LIGHTS);
+      nl = 0;
+    }
     im.n_lights = nl;
-    im.light_type = p.light_meta[s * 2 + 1];
+    im.light_type = lt;
     sh.n_vis = 0;
     sh.n_big = 0;
     sh.next_tile = 0;
@@ -288,7 +300,7 @@ __device__ void setup_image(const Params& p, int cam, CtaShared& sh, int* mprefi
       const float* L4 = p.light + (im.s * kMaxLights + tid) * 4;
       for (int i = 0; i < 3; i++) {
         float r = im.V[i * 4 + 0] * L4[0] + im.V[i * 4 + 1] * L4[1] + im.V[i * 4 + 2] * L4[2];
-        im.lv[tid][i] = im.light_type == 0 ? r + im.V[i * 4 + 3] : -r;
+        im.lv[tid][i] = im.light_type == 1 ? -r : r + im.V[i * 4 + 3];
       }
       im.lv[tid][3] = L4[3];
     }
@@ -300,7 +312,9 @@ __device__ void setup_image(const Params& p, int cam, CtaShared& sh, int* mprefi
     im.scale = exp2f(p.exposure_ev[im.s]);
   }
   for (int k = tid; k < kMaxMaterials * 5; k += blockDim.x)
-    sh.mat[k / 5][k % 5] = p.material[(size_t)im.s * kMaxMaterials * 5 + k];  // (columns 5-7 unused)
+    sh.mat[k / 5][k % 5] = p.material[(size_t)im.s * kMaxMaterials * 5 + k];
+  if (tid >= 32 && tid < 32 + kMaxMaterials)  // column 5: emission (columns 6-7 unused); blocks have >= 256 threads
+    sh.mat[tid - 32][5] = p.emission ? p.emission[(size_t)im.s * kMaxMaterials + tid - 32] : 0.0f;
   if (!tables) {
     __syncthreads();
     return;
@@ -871,10 +885,15 @@ __device__ void big_spans(const Params& p, const CtaShared& sh, const Scratch& s
   }
 }
 
+// kLight: the batch has a cone table (type-2, spot, lights can occur) or material emission.
+template <bool kLight>
 __device__ void shade(const CtaShared& sh, const float P[3], const float n[3], int mat, float rgb[3]) {
   const ImageInfo& im = sh.im;
   const float4 ma = *reinterpret_cast<const float4*>(sh.mat[mat]);
-  const float m[5] = {ma.x, ma.y, ma.z, ma.w, sh.mat[mat][4]};
+  float2 mb;  // shininess, emission
+  if (kLight) mb = *reinterpret_cast<const float2*>(&sh.mat[mat][4]);
+  else mb = make_float2(sh.mat[mat][4], 0.0f);
+  const float m[5] = {ma.x, ma.y, ma.z, ma.w, mb.x};
   float Vv[3];
   if (im.ortho) {
     Vv[0] = 0.0f;
@@ -887,19 +906,25 @@ __device__ void shade(const CtaShared& sh, const float P[3], const float n[3], i
     Vv[2] = -P[2] * rl;
   }
   // diffuse and specular irradiance summed over the lights, the albedo applied once:
-  // rgb_k = scale * (m_k * (ambient_k + sum E ndl) + sum E spec)
-  float D = 0.0f, S = 0.0f;
+  // rgb_k = scale * (m_k * (ambient_k + emission + sum E ndl) + sum E spec)
+  float D = mb.y, S = 0.0f;
 #pragma unroll
   for (int l = 0; l < kMaxLights; l++) {
     if (l >= im.n_lights) break;
     const float4 lq = *reinterpret_cast<const float4*>(im.lv[l]);
     float Lx, Ly, Lz, r, E;  // (Lx, Ly, Lz) * r is the unit vector to the light
-    if (im.light_type == 0) {
+    // point or spot (the other instances see only types 0 and 1: spot needs the cone table)
+    if (kLight ? im.light_type != 1 : im.light_type == 0) {
       Lx = lq.x - P[0];
       Ly = lq.y - P[1];
       Lz = lq.z - P[2];
       r = rsqrtf(Lx * Lx + Ly * Ly + Lz * Lz);
       E = lq.w * (r * r);
+      if (kLight && im.light_type == 2) {  // the spot cone: E *= t^2 (3 - 2t)
+        const float4 sq = *reinterpret_cast<const float4*>(im.la[l]);
+        const float t = __saturatef(fmaf(-(Lx * sq.x + Ly * sq.y + Lz * sq.z), r, sq.w));
+        E *= t * t * (3.0f - 2.0f * t);
+      }
     } else {
       Lx = lq.x;
       Ly = lq.y;
@@ -927,6 +952,19 @@ __device__ void shade(const CtaShared& sh, const float P[3], const float n[3], i
 // the raster phase).  White balance, the rotation about the grey axis, saturation, contrast and
 // brightness are each affine in the colour, so they compose into one map c -> A c + t, applied
 // per pixel; the grain stays per pixel.
+// The cone of spot light l in view space (its thread, in the spot instances only, after
+// setup_image and before a barrier that precedes the raster phase).
+__device__ void spot_setup(const Params& p, ImageInfo& im, int l) {
+  if (im.light_type != 2 || l >= im.n_lights) return;
+  const float* sp = p.light_spot + (im.s * kMaxLights + l) * 5;
+  const float cos_o = sp[3], cos_i = sp[4];
+  const bool cone = cos_i > cos_o;
+  const float w = cone ? 1.0f / (cos_i - cos_o) : 0.0f;
+  for (int i = 0; i < 3; i++)
+    im.la[l][i] = (im.V[i * 4 + 0] * sp[0] + im.V[i * 4 + 1] * sp[1] + im.V[i * 4 + 2] * sp[2]) * w;
+  im.la[l][3] = cone ? -cos_o * w : -1.0f;
+}
+
 __device__ void grading_setup(const Params& p, ImageInfo& im) {
   const float* g = p.grading + (size_t)im.s * 8;
   float hs, hc;
@@ -978,11 +1016,12 @@ struct BoxWalk {
 };
 
 // Phase R for one tile, by one warp, in warp-private shared memory.
-// kGrade: the batch has colour grading (a separate instance, so that the common case carries
-// none of its code).
-template <bool kGrade>
+// kF: the batch's optional features (kFeatGrade, kFeatTrack, kFeatLight); each combination is a
+// kernel instance of its own, so that the common case carries none of their code.
+template <int kF>
 __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scratch& sc, int tile, char* wbase,
                                  const SmemLayout& L, const uint32_t* spans) {
+  constexpr bool kGrade = (kF & kFeatGrade) != 0;
   const ImageInfo& im = sh.im;
   const int lane = threadIdx.x & 31;
   const int tx = tile % im.ntx, ty = tile / im.ntx;
@@ -1231,7 +1270,7 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
           P[1] = depth * uy;
           P[2] = -depth;
         }
-        shade(sh, P, n, mat, rgb);
+        shade<(kF & kFeatLight) != 0>(sh, P, n, mat, rgb);
       }
       // consecutive lanes write consecutive pixels: the three byte (or half) stores of a
       // warp fill whole sectors of the row between them
@@ -1279,7 +1318,7 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
 
 // Phase R for the current image: warps pull tiles first, first + stride, ... from the
 // CTA's counter until none is left.
-template <bool kGrade>
+template <int kF>
 __device__ void raster_phase(const Params& p, CtaShared& sh, const Scratch& sc, const SmemPtrs& sp, const SmemLayout& L,
                              int first = 0, int stride = 1) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1289,7 +1328,7 @@ __device__ void raster_phase(const Params& p, CtaShared& sh, const Scratch& sc, 
     if (lane == 0) k = atomicAdd(&sh.next_tile, 1);
     const int t = first + stride * __shfl_sync(kFull, k, 0);
     if (t >= sh.im.n_tiles) break;
-    raster_tile_warp<kGrade>(p, sh, sc, t, wbase, L, sp.spans);
+    raster_tile_warp<kF>(p, sh, sc, t, wbase, L, sp.spans);
   }
   __syncthreads();
 }
@@ -1317,7 +1356,7 @@ constexpr long long kSpinBudget = 2000000000ll;
 // the records, so it needs no fence); a helper claims with compare-and-swap, so it never
 // takes a tile of a later image that reused the slot, and publishes each finished tile
 // in the slot's counter after a fence.
-template <bool kGrade>
+template <int kF>
 __device__ void raster_claimed(const Params& p, CtaShared& sh, const Scratch& sc, const SmemPtrs& sp, const SmemLayout& L,
                                int cam, bool owner) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1349,7 +1388,7 @@ __device__ void raster_claimed(const Params& p, CtaShared& sh, const Scratch& sc
     }
     t = __shfl_sync(kFull, t, 0);
     if (t >= n_tiles) break;
-    raster_tile_warp<kGrade>(p, sh, sc, t, wbase, L, sp.spans);
+    raster_tile_warp<kF>(p, sh, sc, t, wbase, L, sp.spans);
     mine++;
     if (!owner && lane == 0) {
       __threadfence();
@@ -1364,8 +1403,9 @@ __device__ void raster_claimed(const Params& p, CtaShared& sh, const Scratch& sc
 // fused: one persistent launch.  CTAs pull whole images from a queue; once the
 // queue is empty they help finish the raster phase of images other CTAs still own.
 // ---------------------------------------------------------------------------
-template <bool kGrade, bool kTrack>
+template <int kF>
 __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
+  constexpr bool kGrade = (kF & kFeatGrade) != 0, kTrack = (kF & kFeatTrack) != 0, kLight = (kF & kFeatLight) != 0;
   extern __shared__ __align__(16) char smem[];
   __shared__ CtaShared sh;
   const SmemLayout L = layout_of(p);
@@ -1378,6 +1418,7 @@ __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
     if (cam >= p.n_cams) break;
     setup_image(p, cam, sh, sp.mprefix, sp.tprefix, sp.mbegin, true, kTrack);
     if (kGrade && threadIdx.x == 0 && sh.im.valid) grading_setup(p, sh.im);  // (read after phase G's barrier)
+    if (kLight && threadIdx.x < kMaxLights && sh.im.valid) spot_setup(p, sh.im, threadIdx.x);
     if (sh.im.valid) {
       geometry_phase<kTrack>(p, sh, sp.mprefix, sp.tprefix, sp.mbegin, reinterpret_cast<WarpG*>(sp.uni), sc);
       __syncthreads();
@@ -1393,7 +1434,7 @@ __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
         atomicExch(sc.claim(), (unsigned long long)(cam + 1) << 32);
       }
       __syncthreads();
-      raster_claimed<kGrade>(p, sh, sc, sp, L, cam, true);
+      raster_claimed<kF>(p, sh, sc, sp, L, cam, true);
       if (threadIdx.x == 0) {  // close it and wait for helpers still on its other tiles
         atomicExch(sc.claim(), 0ull);
         const unsigned helped = unsigned(sh.im.n_tiles - sh.next_tile);
@@ -1466,10 +1507,11 @@ __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
       setup_image(p, cam, sh, sp.mprefix, sp.tprefix, sp.mbegin, false);
       if (threadIdx.x == 0) sh.n_big = *reinterpret_cast<volatile int*>(o.header + 3);
       if (kGrade && threadIdx.x == 0) grading_setup(p, sh.im);
+      if (kLight && threadIdx.x < kMaxLights) spot_setup(p, sh.im, threadIdx.x);
       __syncthreads();
       big_spans(p, sh, o, sp.spans);
       __syncthreads();
-      raster_claimed<kGrade>(p, sh, o, sp, L, cam, false);
+      raster_claimed<kF>(p, sh, o, sp, L, cam, false);
     }
     __syncthreads();
   }
@@ -1521,8 +1563,9 @@ __global__ void __launch_bounds__(512, 2) plain_bin_kernel(Params p) {
   if (threadIdx.x == 0) sc.header[3] = sh.n_big;
 }
 
-template <bool kGrade>
+template <int kF>
 __global__ void __launch_bounds__(512, 2) plain_raster_kernel(Params p) {
+  constexpr bool kGrade = (kF & kFeatGrade) != 0, kLight = (kF & kFeatLight) != 0;
   extern __shared__ __align__(16) char smem[];
   __shared__ CtaShared sh;
   const int cam = plain_cam(p);
@@ -1534,10 +1577,11 @@ __global__ void __launch_bounds__(512, 2) plain_raster_kernel(Params p) {
   setup_image(p, cam, sh, sp.mprefix, sp.tprefix, sp.mbegin, false);
   if (threadIdx.x == 0) sh.n_big = sc.header[3];
   if (kGrade && threadIdx.x == 0) grading_setup(p, sh.im);
+  if (kLight && threadIdx.x < kMaxLights) spot_setup(p, sh.im, threadIdx.x);
   __syncthreads();
   big_spans(p, sh, sc, sp.spans);
   __syncthreads();
-  raster_phase<kGrade>(p, sh, sc, sp, L, blockIdx.y, gridDim.y);
+  raster_phase<kF>(p, sh, sc, sp, L, blockIdx.y, gridDim.y);
 }
 
 // Scratch of orrb_render_batch_noalloc: a file-scope device array, so that
@@ -1576,7 +1620,7 @@ namespace {
 // larger size is needed, so steady-state launches (and launches inside a stream capture)
 // make no attribute calls.
 std::mutex g_attr_mu;
-size_t g_attr_set[9][64] = {};  // per kernel instance (see fused_index and the plain launch)
+size_t g_attr_set[16][64] = {};  // per kernel instance: fused 0-7 (its feature bits), plain 8-14
 
 cudaError_t ensure_smem(const void* fn, int which, size_t smem) {
   int dev = 0;
@@ -1591,27 +1635,34 @@ cudaError_t ensure_smem(const void* fn, int which, size_t smem) {
 }
 }  // namespace
 
-// Fused kernel instance f: bit 0 colour grading, bit 1 tracker rows.
-static const void* fused_fn(int f) {
-  switch (f) {
-    case 0: return (const void*)render_fused_kernel<false, false>;
-    case 1: return (const void*)render_fused_kernel<true, false>;
-    case 2: return (const void*)render_fused_kernel<false, true>;
-    default: return (const void*)render_fused_kernel<true, true>;
-  }
+// The feature bits of a launch's batch and outputs.
+static int features(const Params& p) {
+  return (p.grading ? kFeatGrade : 0) | (p.tracker ? kFeatTrack : 0) | (p.light_spot || p.emission ? kFeatLight : 0);
 }
-// Its slot in the attribute cache (1-3 and 5, 8: the plain kernels).
-static int fused_index(int f) {
-  static const int slot[4] = {0, 4, 6, 7};
-  return slot[f & 3];
+
+// Fused kernel instance for feature bits f (attribute-cache slot f).
+static const void* fused_fn(int f) {
+  static const void* const fns[8] = {
+      (const void*)render_fused_kernel<0>, (const void*)render_fused_kernel<1>, (const void*)render_fused_kernel<2>,
+      (const void*)render_fused_kernel<3>, (const void*)render_fused_kernel<4>, (const void*)render_fused_kernel<5>,
+      (const void*)render_fused_kernel<6>, (const void*)render_fused_kernel<7>};
+  return fns[f & 7];
+}
+
+// Plain raster instance for feature bits f (grading and spot matter; slot 11 + index).
+static const void* plain_raster_fn(int f) {
+  static const void* const fns[4] = {(const void*)plain_raster_kernel<0>, (const void*)plain_raster_kernel<kFeatGrade>,
+                                     (const void*)plain_raster_kernel<kFeatLight>,
+                                     (const void*)plain_raster_kernel<kFeatGrade | kFeatLight>};
+  return fns[((f & kFeatGrade) ? 1 : 0) | ((f & kFeatLight) ? 2 : 0)];
 }
 
 int render_max_ctas_per_sm(int threads, size_t smem) {
   int n = 0;
   n = 1 << 30;  // every instance: the same launch bounds and shared memory; the least of their fits
-  for (int f = 0; f < 4; f++) {
+  for (int f = 0; f < 8; f++) {
     int m = 0;
-    if (ensure_smem(fused_fn(f), fused_index(f), smem) != cudaSuccess) return -1;
+    if (ensure_smem(fused_fn(f), f, smem) != cudaSuccess) return -1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, fused_fn(f), threads, smem) != cudaSuccess) return -1;
     n = m < n ? m : n;
   }
@@ -1623,28 +1674,32 @@ int launch_render(const Params& p, int mode, int threads, int n_ctas, int max_ca
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t smem = render_smem_bytes(threads, p.tile_w, p.tile_h, p.inst_max, p.max_tiles, p.w_max);
   cudaError_t e = cudaSuccess;
+  const int f = features(p);
   if (mode == 0) {
-    const int f = (p.grading != nullptr ? 1 : 0) | (p.tracker != nullptr ? 2 : 0);
-    e = ensure_smem(fused_fn(f), fused_index(f), smem);
+    e = ensure_smem(fused_fn(f), f, smem);
     if (e == cudaSuccess) {  // slot headers (claim words, counters) start at zero
       const SlotLayout SL = slot_layout(p.t_max, p.max_tiles);
       e = cudaMemset2DAsync(p.scratch + SL.header, p.slot_bytes, 0, 64, (size_t)n_ctas, st);
     }
     if (e == cudaSuccess) {
       switch (f) {
-        case 0: render_fused_kernel<false, false><<<n_ctas, threads, smem, st>>>(p); break;
-        case 1: render_fused_kernel<true, false><<<n_ctas, threads, smem, st>>>(p); break;
-        case 2: render_fused_kernel<false, true><<<n_ctas, threads, smem, st>>>(p); break;
-        default: render_fused_kernel<true, true><<<n_ctas, threads, smem, st>>>(p); break;
+        case 0: render_fused_kernel<0><<<n_ctas, threads, smem, st>>>(p); break;
+        case 1: render_fused_kernel<1><<<n_ctas, threads, smem, st>>>(p); break;
+        case 2: render_fused_kernel<2><<<n_ctas, threads, smem, st>>>(p); break;
+        case 3: render_fused_kernel<3><<<n_ctas, threads, smem, st>>>(p); break;
+        case 4: render_fused_kernel<4><<<n_ctas, threads, smem, st>>>(p); break;
+        case 5: render_fused_kernel<5><<<n_ctas, threads, smem, st>>>(p); break;
+        case 6: render_fused_kernel<6><<<n_ctas, threads, smem, st>>>(p); break;
+        default: render_fused_kernel<7><<<n_ctas, threads, smem, st>>>(p); break;
       }
       e = cudaGetLastError();
     }
   } else {
-    const bool graded = p.grading != nullptr, tracked = p.tracker != nullptr;
+    const bool tracked = (f & kFeatTrack) != 0;
+    const int rf = f & (kFeatGrade | kFeatLight);
     const void* ks[3] = {tracked ? (const void*)plain_geometry_kernel<true> : (const void*)plain_geometry_kernel<false>,
-                         (const void*)plain_bin_kernel,
-                         graded ? (const void*)plain_raster_kernel<true> : (const void*)plain_raster_kernel<false>};
-    const int which[3] = {tracked ? 8 : 1, 2, graded ? 5 : 3};
+                         (const void*)plain_bin_kernel, plain_raster_fn(f)};
+    const int which[3] = {tracked ? 9 : 8, 10, 11 + ((rf & kFeatGrade) ? 1 : 0) + ((rf & kFeatLight) ? 2 : 0)};
     for (int k = 0; k < 3 && e == cudaSuccess; k++) e = ensure_smem(ks[k], which[k], smem);
     Params q = p;
     for (int s = 0; s < p.n_samples && e == cudaSuccess; s++) {
@@ -1652,8 +1707,13 @@ int launch_render(const Params& p, int mode, int threads, int n_ctas, int max_ca
       if (tracked) plain_geometry_kernel<true><<<max_cams_per_sample, threads, smem, st>>>(q);
       else plain_geometry_kernel<false><<<max_cams_per_sample, threads, smem, st>>>(q);
       plain_bin_kernel<<<max_cams_per_sample, threads, smem, st>>>(q);
-      if (graded) plain_raster_kernel<true><<<dim3(max_cams_per_sample, kPlainRasterSplit), threads, smem, st>>>(q);
-      else plain_raster_kernel<false><<<dim3(max_cams_per_sample, kPlainRasterSplit), threads, smem, st>>>(q);
+      const dim3 grid(max_cams_per_sample, kPlainRasterSplit);
+      switch (rf) {
+        case 0: plain_raster_kernel<0><<<grid, threads, smem, st>>>(q); break;
+        case kFeatGrade: plain_raster_kernel<kFeatGrade><<<grid, threads, smem, st>>>(q); break;
+        case kFeatLight: plain_raster_kernel<kFeatLight><<<grid, threads, smem, st>>>(q); break;
+        default: plain_raster_kernel<kFeatGrade | kFeatLight><<<grid, threads, smem, st>>>(q); break;
+      }
       e = cudaGetLastError();
     }
   }

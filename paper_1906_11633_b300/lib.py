@@ -44,7 +44,8 @@ class orrb_batch_shape(C.Structure):
 class orrb_batch_desc(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in (
         "inst_offset", "inst_mesh", "inst_pose", "inst_seg", "inst_mat_base", "cam_offset", "cam_sample", "cam_view",
-        "cam_intr", "cam_wh", "img_offset", "light", "light_meta", "material", "exposure_ev", "ambient", "background", "grading")]
+        "cam_intr", "cam_wh", "img_offset", "light", "light_meta", "material", "exposure_ev", "ambient", "background", "grading",
+        "light_spot", "emission")]
 
 
 class orrb_outputs(C.Structure):
@@ -57,7 +58,8 @@ class orrb_config(C.Structure):
 
 
 class orrb_param_grads(C.Structure):
-    _fields_ = [("d_material", C.c_void_p), ("d_light", C.c_void_p), ("d_exposure", C.c_void_p)]
+    _fields_ = [("d_material", C.c_void_p), ("d_light", C.c_void_p), ("d_exposure", C.c_void_p),
+                ("d_emission", C.c_void_p)]
 
 
 class OrrbError(RuntimeError):

@@ -24,7 +24,7 @@ _DTYPES = dict(inst_offset=torch.int32, inst_mesh=torch.int32, inst_pose=torch.f
                inst_mat_base=torch.int16, cam_offset=torch.int32, cam_sample=torch.int32, cam_view=torch.float32,
                cam_intr=torch.float32, cam_wh=torch.int32, img_offset=torch.int64, light=torch.float32,
                light_meta=torch.int32, material=torch.float32, exposure_ev=torch.float32, ambient=torch.float32,
-               background=torch.float32, grading=torch.float32)
+               background=torch.float32, grading=torch.float32, light_spot=torch.float32, emission=torch.float32)
 _NP = {torch.int32: np.int32, torch.float32: np.float32, torch.uint8: np.uint8, torch.int16: np.int16,
        torch.int64: np.int64}
 
@@ -50,7 +50,7 @@ class DeviceBatch:
     desc: L.orrb_batch_desc = field(init=False)
 
     def __post_init__(self):
-        # an optional array (grading) that is absent or None passes a null pointer
+        # an optional array (grading, light_spot, emission) that is absent or None passes a null pointer
         self.desc = L.orrb_batch_desc(*[self.tensors[n].data_ptr() if self.tensors.get(n) is not None else None
                                         for n in _DESC_FIELDS])
 
@@ -166,7 +166,10 @@ class Renderer:
         st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
         return L.orrb_read_status(self.ctx, self._last_ws.data_ptr(), st)
 
-    def shade_backward(self, db: DeviceBatch, gbuffer: torch.Tensor, d_rgb: torch.Tensor, stream=None):
+    def shade_backward(self, db: DeviceBatch, gbuffer: torch.Tensor, d_rgb: torch.Tensor, stream=None,
+                       emission: bool = False):
+        """(d material [S,32,4], d light [S,4,4], d exposure [S]), plus d emission [S,32] last
+        when `emission`."""
         n = L.orrb_backward_workspace_size(self.ctx, db.shape)
         if self._bws is None or self._bws.numel() < n:
             self._bws = torch.empty(n, dtype=torch.uint8, device=self.device)
@@ -174,12 +177,14 @@ class Renderer:
         dm = torch.empty((S, L.ORRB_MAX_MATERIALS, 4), dtype=torch.float32, device=self.device)
         dl = torch.empty((S, L.ORRB_MAX_LIGHTS, 4), dtype=torch.float32, device=self.device)
         de = torch.empty(S, dtype=torch.float32, device=self.device)
-        grads = L.orrb_param_grads(dm.data_ptr(), dl.data_ptr(), de.data_ptr())
+        dem = torch.empty((S, L.ORRB_MAX_MATERIALS), dtype=torch.float32, device=self.device) if emission else None
+        grads = L.orrb_param_grads(dm.data_ptr(), dl.data_ptr(), de.data_ptr(),
+                                   dem.data_ptr() if emission else None)
         st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
         d_rgb = d_rgb.contiguous()
         L.orrb_shade_backward(self.ctx, db.shape, db.desc, gbuffer.data_ptr(), d_rgb.data_ptr(), grads,
                               self._bws.data_ptr(), self._bws.numel(), st)
-        return dm, dl, de
+        return (dm, dl, de, dem) if emission else (dm, dl, de)
 
 
 class GraphRender:
@@ -276,31 +281,37 @@ class CapturePipeline:
 
 
 class ShadeFn(torch.autograd.Function):
-    """rgb_linear = shade(material, light, exposure_ev) at fixed visibility.
+    """rgb_linear = shade(material, light, exposure_ev[, emission]) at fixed visibility.
 
     Forward renders the batch with the given parameter tensors (visibility does
     not depend on them); backward runs the hand-written shading adjoint kernel
     and returns d material [S,32,5] (albedo rgb and specular; shininess gets 0),
-    d light [S,4,4] and d exposure [S].
+    d light [S,4,4], d exposure [S] and, when an emission tensor [S,32] is
+    given, d emission.
     """
 
     @staticmethod
-    def forward(ctx, material, light, exposure_ev, renderer: Renderer, db: DeviceBatch):
-        dbp = db.with_params(material=material.detach().contiguous(), light=light.detach().contiguous(),
-                             exposure_ev=exposure_ev.detach().contiguous())
+    def forward(ctx, material, light, exposure_ev, renderer: Renderer, db: DeviceBatch, emission=None):
+        kw = dict(material=material.detach().contiguous(), light=light.detach().contiguous(),
+                  exposure_ev=exposure_ev.detach().contiguous())
+        if emission is not None:
+            kw["emission"] = emission.detach().contiguous()
+        dbp = db.with_params(**kw)
         out = renderer.render(dbp, rgb_linear=True, gbuffer=True)
         ctx.renderer = renderer
         ctx.db = dbp
+        ctx.emission = emission is not None
         ctx.save_for_backward(out["gbuffer"])
         return out["rgb_linear"]
 
     @staticmethod
     def backward(ctx, g):
         (gbuffer,) = ctx.saved_tensors
-        dm, dl, de = ctx.renderer.shade_backward(ctx.db, gbuffer, g.float())
+        grads = ctx.renderer.shade_backward(ctx.db, gbuffer, g.float(), emission=ctx.emission)
+        dm, dl, de = grads[:3]
         dmat = torch.zeros_like(ctx.db.tensors["material"])
         dmat[..., :4] = dm
-        return dmat, dl, de, None, None
+        return dmat, dl, de, None, None, (grads[3] if ctx.emission else None)
 
 
 def to_numpy(out) -> Dict[str, np.ndarray]:

@@ -112,3 +112,25 @@ def test_shadefn_autograd(renderer, oracle):
     assert torch.allclose(light.grad, dl, rtol=1e-5, atol=1e-6)
     assert torch.allclose(ev.grad, de, rtol=1e-5, atol=1e-6)
     assert (mat.grad[..., 4] == 0).all()
+
+
+def test_spot_and_emission_adjoint_matches_oracle(renderer, oracle):
+    """Three spot lights (the cone factor's dependence on the light position) and emissive
+    materials: every gradient, d emission included, against the oracle's fp64 adjoint; ShadeFn
+    returns d emission when given the emission tensor."""
+    b = sg.benchmark_batch(7, np.arange(12), res=96, grading=False)
+    b = b.with_params(emission=b.emission + np.float32(0.03))
+    db, out, gb, target, d_rgb = setup(renderer, oracle, b)
+    dm, dl, de, dem = [t.cpu().numpy() for t in
+                       renderer.shade_backward(db, out["gbuffer"], torch.from_numpy(d_rgb).cuda(), emission=True)]
+    rdm, rdl, rde, rdem = oracle.shade_backward_f64(b, *gb, d_rgb.astype(np.float64), return_emission=True)
+    assert rel_err(dm, rdm).max() < REL
+    assert rel_err(dl[:, :3], rdl[:, :3]).max() < REL
+    assert rel_err(de, rde).max() < REL
+    assert rel_err(dem, rdem).max() < REL
+    assert np.abs(rdem).max() > 0
+    emission = db.tensors["emission"].clone().requires_grad_(True)
+    mat = db.tensors["material"].clone().requires_grad_(True)
+    rgb = ShadeFn.apply(mat, db.tensors["light"], db.tensors["exposure_ev"], renderer, db, emission)
+    ((rgb - torch.from_numpy(target).float().cuda()) ** 2)[out["gbuffer"][6].view(torch.int32) >= 0].sum().backward()
+    assert torch.allclose(emission.grad.cpu(), torch.from_numpy(dem), rtol=1e-4, atol=1e-6)

@@ -356,3 +356,35 @@ def test_tracker_rows_match_oracle(hand_renderer, oracle):
             g = out["tracker"].cpu().numpy()
             np.testing.assert_array_equal(g, o)
     assert (o[..., 6] & 1).any() and o[0, 3, 6] == 0 and o[1, 3, 6] == 3
+
+
+def test_spot_lights_and_emission_match_oracle(hand_renderer, oracle):
+    """The benchmark-like scene (three spot lights with random cones aimed at the block, emissive
+    block faces, orbit cameras, grading) in fused and plain launches, and mixed in one batch with
+    point-lit samples (which pass a zero cone table and no emission)."""
+    spot = sg.benchmark_batch(21, np.arange(10), res=96, orbit=True)
+    spot = spot.with_params(emission=spot.emission + np.float32(0.02) * (np.arange(32) % 3 == 0))
+    point = sg.hand_batch(22, np.arange(10, 16), res=96, grading=True)
+    mixed = sg.concat_batches([sg.select_samples(spot, range(5)), point, sg.select_samples(spot, range(5, 10))])
+    for b in (spot, mixed):
+        o = oracle.render(b, debug=True)
+        for cfg in (config(), config(mode=L.ORRB_MODE_PLAIN)):
+            compare(render_np(hand_renderer, b, cfg), o, "spot")
+    lin = o["rgb_linear"].reshape(-1, 96 * 96, 3)
+    assert (lin[:5].max(axis=(1, 2)) > 0.2).all()           # the spots light the scene
+
+
+def test_lights_that_light_nothing_are_flagged(hand_renderer, oracle):
+    """A spot type without its cone table and an unknown type light nothing and set the light flag;
+    a null cone (cos_inner <= cos_outer) lights nothing and is valid input."""
+    b = sg.benchmark_batch(3, np.arange(3), res=64, grading=False)
+    null_cone = b.light_spot.copy()
+    null_cone[1, :, 4] = null_cone[1, :, 3]
+    meta = b.light_meta.copy()
+    meta[2, 1] = 7
+    for bad, flagged in ((b.with_params(light_spot=null_cone), False), (b.with_params(light_spot=None), True),
+                         (b.with_params(light_meta=meta), True)):
+        out = hand_renderer.render(hand_renderer.upload(bad), rgb_linear=True)
+        torch.cuda.synchronize()
+        assert bool(hand_renderer.status() & 0x10) == flagged
+        compare(to_numpy(out), oracle.render(bad, debug=True), "dark lights")
