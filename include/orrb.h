@@ -190,7 +190,7 @@ typedef struct {
   float* gbuffer;       /* device, [7][N] planes: position xyz, normal xyz (view space),
                            material slot as int32 bits (-1 background); input of the backward */
   int32_t* tracker;     /* device, [n_cams][max_inst_per_sample][8] per camera and instance of its
-                           sample (the tracker output, Sec. 4.3): the 8.8 fixed-point screen box
+                           sample (the tracker output, Sec. 4.3.2): the 8.8 fixed-point screen box
                            x0, y0, x1, y1 of the instance's vertices that its triangles use, that
                            lie in front of the near plane and inside the guard band, snapped as the
                            triangle vertices are (empty: INT32_MAX, INT32_MAX, INT32_MIN, INT32_MIN;

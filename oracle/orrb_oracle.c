@@ -63,7 +63,8 @@
  *                       + 0x9E3779B9 (j + 1)) ^ i) / 2^32, j the camera's
  *                       index within its sample, i the pixel's within its
  *                       image.  rgb_linear stays ungraded.
- *  14  optional tracker rows (per camera and instance of its sample): the
+ *  14  optional tracker rows (the Tracker component, Sec. 4.3.2; per camera
+ *      and instance of its sample): the
  *      8.8 fixed-point screen box (x0, y0, x1, y1) of the instance's mesh
  *      vertices (those its triangles use) that lie in front of the near plane
  *      and inside the guard band, snapped as in step 4 (empty: x0 = y0 =
