@@ -45,12 +45,14 @@ class _Meshes(C.Structure):
                 ("pos", C.c_void_p), ("nrm", C.c_void_p), ("idx", C.c_void_p), ("tri_mat", C.c_void_p)]
 
 
+_BATCH_ARRAYS = ("inst_offset", "inst_mesh", "inst_pose", "inst_seg", "inst_mat_base",
+                 "cam_offset", "cam_sample", "cam_view", "cam_intr", "cam_wh", "img_offset",
+                 "light", "light_meta", "material", "exposure_ev", "ambient", "background", "grading", "light_spot",
+                 "emission", "shadow_view", "shadow_intr", "shadow_map")
+
+
 class _Batch(C.Structure):
-    _fields_ = [("n_samples", C.c_int32)] + [(n, C.c_void_p) for n in (
-        "inst_offset", "inst_mesh", "inst_pose", "inst_seg", "inst_mat_base",
-        "cam_offset", "cam_sample", "cam_view", "cam_intr", "cam_wh", "img_offset",
-        "light", "light_meta", "material", "exposure_ev", "ambient", "background", "grading", "light_spot",
-        "emission")]
+    _fields_ = [("n_samples", C.c_int32)] + [(n, C.c_void_p) for n in _BATCH_ARRAYS] + [("shadow_res", C.c_int32)]
 
 
 class _Outputs(C.Structure):
@@ -75,6 +77,9 @@ def lib():
             L.orc_shade_f64.restype = None
             L.orc_shade_backward_f64.argtypes = [C.POINTER(_Batch), C.c_int32, C.c_int32] + [C.c_void_p] * 13
             L.orc_shade_backward_f64.restype = None
+            L.orc_render_shadow_maps.argtypes = [C.POINTER(_Meshes), C.POINTER(_Batch), C.c_int32, C.c_int32,
+                                                 C.c_void_p]
+            L.orc_render_shadow_maps.restype = C.c_int
             _lib = L
     return _lib
 
@@ -115,8 +120,15 @@ class _Pinned:
             light_meta=_c(batch.light_meta, np.int32), material=_c(batch.material, np.float32),
             exposure_ev=_c(batch.exposure_ev, np.float32), ambient=_c(batch.ambient, np.float32),
             background=_c(batch.background, np.float32),
-            grading=_opt(batch, "grading"), light_spot=_opt(batch, "light_spot"), emission=_opt(batch, "emission"))
-        self.batch = _Batch(batch.n_samples, *[_p(self.arrs[n]) for n, _ in _Batch._fields_[1:]])
+            grading=_opt(batch, "grading"), light_spot=_opt(batch, "light_spot"), emission=_opt(batch, "emission"),
+            shadow_view=_opt(batch, "shadow_view"), shadow_intr=_opt(batch, "shadow_intr"), shadow_map=None)
+        self.shadow_res = int(getattr(batch, "shadow_res", 0) or 0)
+        self.batch = _Batch(batch.n_samples, *[_p(self.arrs[n]) for n in _BATCH_ARRAYS], self.shadow_res)
+
+    def set_shadow_maps(self, maps):
+        """Point the lookups of step 16 at `maps` ([S, 4, R, R] float32, kept alive here)."""
+        self.arrs["shadow_map"] = maps
+        self.batch.shadow_map = _p(maps)
 
 
 def _chunks(n_cams: int, threads: int):
@@ -132,15 +144,43 @@ def default_threads() -> int:
         return os.cpu_count() or 1
 
 
+def shadow_maps(batch, threads: int | None = None, pin=None):
+    """The shadow maps of step 15, [n_samples, 4, R, R] float32 (zero for lights without shadow), or None."""
+    pin = pin or _Pinned(batch)
+    R = pin.shadow_res
+    if R <= 0 or pin.arrs["shadow_view"] is None or pin.arrs["shadow_intr"] is None:
+        return None
+    maps = np.zeros((batch.n_samples, 4, R, R), np.float32)
+    threads = threads or default_threads()
+    L = lib()
+
+    def run(rng):
+        if L.orc_render_shadow_maps(C.byref(pin.meshes), C.byref(pin.batch), rng[0], rng[1], _p(maps)) != 0:
+            raise MemoryError("oracle: allocation failed")
+
+    chunks = _chunks(batch.n_samples, threads)
+    if threads == 1 or len(chunks) == 1:
+        for c in chunks:
+            run(c)
+    else:
+        with ThreadPoolExecutor(threads) as ex:
+            list(ex.map(run, chunks))
+    return maps
+
+
 def render(batch, threads: int | None = None, gbuffer: bool = False, debug: bool = False, cams=None,
            tracker: bool = False):
     """Oracle render of a batch.  Returns a dict of numpy channel arrays.
 
     `cams`: optional (begin, end) camera range; pixels of other images stay zero.
     `tracker`: also the per (camera, instance) rows [n_cams, max instances per sample, 8] of step 14.
+    A batch with shadow cameras also returns its shadow maps (step 15) as "shadow_map".
     """
     L = lib()
     pin = _Pinned(batch)
+    maps = shadow_maps(batch, threads, pin)
+    if maps is not None:
+        pin.set_shadow_maps(maps)
     N = batch.total_pixels
     out = dict(rgb=np.zeros((N, 3), np.uint8), depth=np.zeros(N, np.float32), normal=np.zeros((N, 3), np.uint16),
                seg=np.zeros(N, np.uint8), rgb_linear=np.zeros((N, 3), np.float32))
@@ -171,6 +211,8 @@ def render(batch, threads: int | None = None, gbuffer: bool = False, debug: bool
         with ThreadPoolExecutor(threads) as ex:
             list(ex.map(run, range(len(chunks))))
     out["counters"] = counters.sum(0)
+    if maps is not None:
+        out["shadow_map"] = maps
     return out
 
 

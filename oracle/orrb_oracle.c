@@ -72,6 +72,26 @@
  *      instance's origin (its pose translation); flags bit 0: box not empty,
  *      bit 1: origin projected; a zero.  An instance of a mesh without
  *      triangles keeps an empty row.
+ *  15  optional shadow maps (soft shadows of the benchmark's lights, Sec. 5):
+ *      light l of sample s casts a shadow when l < its light count and its
+ *      shadow camera (view S, intrinsics fx, fy, cx, cy, near, bias) has
+ *      fx != 0.  Its R x R map holds, per pixel, the depth seen from the
+ *      shadow camera (steps 2-8 with that camera, perspective) of the nearest
+ *      BACK face -- each triangle's second and third vertices swapped before
+ *      step 5, so front faces are culled -- and 0 where there is none.
+ *  16  shadow lookup in step 10: for a camera pixel with surface and each
+ *      casting light, in fp32 with every operation rounded separately:
+ *        P as in step 9 (ux = ((x + 1/2) - cx) / fx, uy = -(((y + 1/2) - cy) /
+ *        fy), P = (depth ux, depth uy, -depth); orthographic: (ux, uy, -depth));
+ *        M = S V^-1 (V^-1 = [R^T | -R^T t], products summed in index order);
+ *        q = M P; z = -q_z; unless z > near the light is unshadowed; u = cx +
+ *        fx (q_x (1/z)), v = cy - fy (q_y (1/z)) (unshadowed beyond 2^20);
+ *        over the 3 x 3 texels (floor(u) + a, floor(v) + b), a, b in {-1, 0,
+ *        1}, inside the map, count k those with map depth d > 0 and z - bias
+ *        > d (percentage-closer filtering, Reeves, Salesin and Cook 1987);
+ *        E_l is multiplied by (9 - k) / 9.  The G-buffer's material word
+ *        carries k of light l in bits 8 + 4l .. 11 + 4l (the adjoint holds it
+ *        fixed: visibility does not depend on the shading parameters).
  */
 #include "orrb_oracle.h"
 
@@ -339,7 +359,7 @@ static float spot_f32(float x, float cos_o, float cos_i) {
 }
 
 static void shade_f32(const orc_batch* b, int32_t s, const float* V, int ortho, const float P[3],
-                      const float n[3], int32_t mat, float rgb[3]) {
+                      const float n[3], int32_t mat, const float vis[ORC_MAX_LIGHTS], float rgb[3]) {
   const float* m = b->material + ((int64_t)s * ORC_MAX_MATERIALS + mat) * 5;
   const float* amb = b->ambient + (int64_t)s * 3;
   const float e = b->emission ? b->emission[(int64_t)s * ORC_MAX_MATERIALS + mat] : 0.0f;
@@ -379,6 +399,7 @@ static void shade_f32(const orc_batch* b, int32_t s, const float* V, int ortho, 
       for (int i = 0; i < 3; i++) L[i] = -((V[i * 4 + 0] * L4[0] + V[i * 4 + 1] * L4[1]) + V[i * 4 + 2] * L4[2]);
       E = L4[3];
     }
+    E = E * vis[l]; /* step 16 */
     float ndl = (n[0] * L[0] + n[1] * L[1]) + n[2] * L[2];
     if (ndl < 0.0f) ndl = 0.0f;
     float spec = 0.0f;
@@ -400,7 +421,125 @@ static void shade_f32(const orc_batch* b, int32_t s, const float* V, int ortho, 
 }
 
 /* ------------------------------------------------------------------ */
-/* one image: steps 2-11                                               */
+/* steps 15-16: shadows                                                */
+/* ------------------------------------------------------------------ */
+/* light l of sample s casts a shadow (step 15) */
+static int casts_shadow(const orc_batch* b, int32_t s, int l) {
+  return b->shadow_view && b->shadow_intr && b->shadow_res > 0 && l < light_count(b, s) &&
+         b->shadow_intr[((int64_t)s * ORC_MAX_LIGHTS + l) * 6 + 0] != 0.0f;
+}
+
+/* M = S V^-1 for the rigid camera view V = [R | t] (step 16) */
+static void camera_to_shadow(const float* S, const float* V, float M[12]) {
+  float Wi[12];
+  for (int i = 0; i < 3; i++) {
+    for (int j = 0; j < 3; j++) Wi[i * 4 + j] = V[j * 4 + i];
+    Wi[i * 4 + 3] = -((V[0 * 4 + i] * V[3] + V[1 * 4 + i] * V[7]) + V[2 * 4 + i] * V[11]);
+  }
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 4; j++) {
+      float r = (S[i * 4 + 0] * Wi[0 * 4 + j] + S[i * 4 + 1] * Wi[1 * 4 + j]) + S[i * 4 + 2] * Wi[2 * 4 + j];
+      M[i * 4 + j] = j == 3 ? r + S[i * 4 + 3] : r;
+    }
+}
+
+/* the number of shadowed taps (0..9) at camera-space point P (step 16) */
+static int shadow_taps(const float M[12], const float* si, const float* map, int32_t R, const float P[3]) {
+  float q[3];
+  for (int i = 0; i < 3; i++) q[i] = ((M[i * 4 + 0] * P[0] + M[i * 4 + 1] * P[1]) + M[i * 4 + 2] * P[2]) + M[i * 4 + 3];
+  float z = -q[2];
+  if (!(z > si[4])) return 0;
+  float iw = 1.0f / z;
+  float u = si[2] + si[0] * (q[0] * iw);
+  float v = si[3] - si[1] * (q[1] * iw);
+  if (!(fabsf(u) < GUARD_PX) || !(fabsf(v) < GUARD_PX)) return 0;
+  int32_t i0 = (int32_t)floorf(u), j0 = (int32_t)floorf(v);
+  float zb = z - si[5];
+  int k = 0;
+  for (int bb = -1; bb <= 1; bb++)
+    for (int a = -1; a <= 1; a++) {
+      int32_t i = i0 + a, j = j0 + bb;
+      if (i < 0 || j < 0 || i >= R || j >= R) continue;
+      float d = map[(int64_t)j * R + i];
+      if (d > 0.0f && zb > d) k++;
+    }
+  return k;
+}
+
+/* ------------------------------------------------------------------ */
+/* steps 2-8 for one view of sample s                                 */
+/* ------------------------------------------------------------------ */
+/* in = fx, fy, cx, cy, near; back != 0 keeps back faces (step 15) */
+static void visibility(const orc_meshes* me, const orc_batch* b, int32_t s, const float* V, const float* in, int ortho,
+                       int32_t W, int32_t H, int back, pixel_winner* px, int64_t cnt[4]) {
+  float fx = in[0], fy = in[1], cx = in[2], cy = in[3], near = in[4];
+  int64_t frags = 0, culled = 0, clipped = 0, dropped = 0;
+  reset_winners(px, (int64_t)W * H);
+  int64_t prim_base = 0;
+  for (int32_t inst = b->inst_offset[s]; inst < b->inst_offset[s + 1]; inst++) {
+    int32_t mesh = (int32_t)b->inst_mesh[inst];
+    float MV[12];
+    compose_mv(V, b->inst_pose + (int64_t)inst * 12, MV);
+    int32_t v0 = me->vert_offset[mesh];
+    int32_t t0 = me->tri_offset[mesh], t1 = me->tri_offset[mesh + 1];
+    for (int32_t t = t0; t < t1; t++) {
+      vtx tri[3];
+      for (int k = 0; k < 3; k++) {
+        int64_t vi = (int64_t)v0 + me->idx[(int64_t)t * 3 + k];
+        tri[k] = to_view(MV, me->pos + vi * 3, me->nrm + vi * 3);
+      }
+      vtx poly[4];
+      int np = clip_near(tri, near, poly);
+      if (!(tri[0].p[2] <= -near && tri[1].p[2] <= -near && tri[2].p[2] <= -near)) clipped++;
+      int64_t prim = prim_base + (t - t0);
+      int32_t mat = (int32_t)b->inst_mat_base[inst] + me->tri_mat[t];
+      int32_t seg = b->inst_seg[inst];
+      for (int sub = 0; sub + 2 < np; sub++) {
+        const vtx* q[3] = {&poly[0], &poly[sub + 1], &poly[sub + 2]};
+        if (back) { /* reversed: the back faces pass the cull of step 5 */
+          const vtx* tmp = q[1];
+          q[1] = q[2];
+          q[2] = tmp;
+        }
+        int32_t X[3], Y[3];
+        float iw[3], nn[3][3];
+        int bad = 0;
+        for (int k = 0; k < 3; k++) {
+          float xs, ys;
+          if (ortho) {
+            iw[k] = -q[k]->p[2];
+            xs = cx + fx * q[k]->p[0];
+            ys = cy - fy * q[k]->p[1];
+          } else {
+            iw[k] = 1.0f / (-q[k]->p[2]);
+            xs = cx + fx * (q[k]->p[0] * iw[k]);
+            ys = cy - fy * (q[k]->p[1] * iw[k]);
+          }
+          if (!(fabsf(xs) < GUARD_PX) || !(fabsf(ys) < GUARD_PX)) bad = 1;
+          X[k] = bad ? 0 : (int32_t)rintf(xs * 256.0f);
+          Y[k] = bad ? 0 : (int32_t)rintf(ys * 256.0f);
+          for (int d = 0; d < 3; d++) nn[k][d] = q[k]->n[d];
+        }
+        if (bad) {
+          dropped++;
+          continue;
+        }
+        frags += raster_triangle(W, H, X, Y, iw, ortho, 2 * prim + sub, (const float(*)[3])nn, mat, seg, px,
+                                 &culled);
+      }
+    }
+    prim_base += t1 - t0;
+  }
+  if (cnt) {
+    cnt[0] += frags;
+    cnt[1] += culled;
+    cnt[2] += clipped;
+    cnt[3] += dropped;
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* one image: steps 2-11, 13, 14, 16                                   */
 /* ------------------------------------------------------------------ */
 static int render_image(const orc_meshes* me, const orc_batch* b, int32_t c, const orc_outputs* out,
                         pixel_winner* px) {
@@ -410,12 +549,8 @@ static int render_image(const orc_meshes* me, const orc_batch* b, int32_t c, con
   const float* in = b->cam_intr + (int64_t)c * 6;
   float fx = in[0], fy = in[1], cx = in[2], cy = in[3], near = in[4];
   int ortho = in[5] != 0.0f;
-  int64_t npx = (int64_t)W * H;
   int64_t base = b->img_offset[c];
-  int64_t frags = 0, culled = 0, clipped = 0, dropped = 0;
-  reset_winners(px, npx);
 
-  int64_t prim_base = 0;
   for (int32_t inst = b->inst_offset[s]; inst < b->inst_offset[s + 1]; inst++) {
     int32_t mesh = (int32_t)b->inst_mesh[inst];
     float MV[12];
@@ -462,50 +597,15 @@ static int render_image(const orc_meshes* me, const orc_batch* b, int32_t c, con
       row[0] = x0; row[1] = y0; row[2] = x1; row[3] = y1;
       row[4] = kx; row[5] = ky; row[6] = flags; row[7] = 0;
     }
-    int32_t v0 = me->vert_offset[mesh];
-    int32_t t0 = me->tri_offset[mesh], t1 = me->tri_offset[mesh + 1];
-    for (int32_t t = t0; t < t1; t++) {
-      vtx tri[3];
-      for (int k = 0; k < 3; k++) {
-        int64_t vi = (int64_t)v0 + me->idx[(int64_t)t * 3 + k];
-        tri[k] = to_view(MV, me->pos + vi * 3, me->nrm + vi * 3);
-      }
-      vtx poly[4];
-      int np = clip_near(tri, near, poly);
-      if (!(tri[0].p[2] <= -near && tri[1].p[2] <= -near && tri[2].p[2] <= -near)) clipped++;
-      int64_t prim = prim_base + (t - t0);
-      int32_t mat = (int32_t)b->inst_mat_base[inst] + me->tri_mat[t];
-      int32_t seg = b->inst_seg[inst];
-      for (int sub = 0; sub + 2 < np; sub++) {
-        const vtx* q[3] = {&poly[0], &poly[sub + 1], &poly[sub + 2]};
-        int32_t X[3], Y[3];
-        float iw[3], nn[3][3];
-        int bad = 0;
-        for (int k = 0; k < 3; k++) {
-          float xs, ys;
-          if (ortho) {
-            iw[k] = -q[k]->p[2];
-            xs = cx + fx * q[k]->p[0];
-            ys = cy - fy * q[k]->p[1];
-          } else {
-            iw[k] = 1.0f / (-q[k]->p[2]);
-            xs = cx + fx * (q[k]->p[0] * iw[k]);
-            ys = cy - fy * (q[k]->p[1] * iw[k]);
-          }
-          if (!(fabsf(xs) < GUARD_PX) || !(fabsf(ys) < GUARD_PX)) bad = 1;
-          X[k] = bad ? 0 : (int32_t)rintf(xs * 256.0f);
-          Y[k] = bad ? 0 : (int32_t)rintf(ys * 256.0f);
-          for (int d = 0; d < 3; d++) nn[k][d] = q[k]->n[d];
-        }
-        if (bad) {
-          dropped++;
-          continue;
-        }
-        frags += raster_triangle(W, H, X, Y, iw, ortho, 2 * prim + sub, (const float(*)[3])nn, mat, seg, px,
-                                 &culled);
-      }
-    }
-    prim_base += t1 - t0;
+  }
+  visibility(me, b, s, V, in, ortho, W, H, 0, px, out->counters);
+
+  /* step 16: the camera-to-shadow maps of the casting lights */
+  float Msh[ORC_MAX_LIGHTS][12];
+  int cast[ORC_MAX_LIGHTS];
+  for (int l = 0; l < ORC_MAX_LIGHTS; l++) {
+    cast[l] = casts_shadow(b, s, l);
+    if (cast[l]) camera_to_shadow(b->shadow_view + ((int64_t)s * ORC_MAX_LIGHTS + l) * 12, V, Msh[l]);
   }
 
   /* steps 9-11 per pixel */
@@ -563,8 +663,18 @@ static int render_image(const orc_meshes* me, const orc_batch* b, int32_t c, con
         P[1] = p->depth * uy;
         P[2] = -p->depth;
       }
+      float vis[ORC_MAX_LIGHTS] = {1.0f, 1.0f, 1.0f, 1.0f};
+      int32_t word = p->mat;
+      for (int l = 0; l < ORC_MAX_LIGHTS; l++) {
+        if (!cast[l]) continue;
+        const int64_t sl = (int64_t)s * ORC_MAX_LIGHTS + l;
+        int k = shadow_taps(Msh[l], b->shadow_intr + sl * 6, b->shadow_map + sl * b->shadow_res * b->shadow_res,
+                            b->shadow_res, P);
+        vis[l] = (float)(9 - k) / 9.0f;
+        word |= k << (8 + 4 * l);
+      }
       float rgb[3];
-      shade_f32(b, s, V, ortho, P, n, p->mat, rgb);
+      shade_f32(b, s, V, ortho, P, n, p->mat, vis, rgb);
       if (out->rgb) {
         float gc[3] = {rgb[0], rgb[1], rgb[2]};
         if (b->grading) grade(b->grading + (int64_t)s * 8, c - b->cam_offset[s], i, gc);
@@ -580,15 +690,26 @@ static int render_image(const orc_meshes* me, const orc_batch* b, int32_t c, con
         for (int k = 0; k < 3; k++) out->gb_pos[o * 3 + k] = P[k];
       if (out->gb_nrm)
         for (int k = 0; k < 3; k++) out->gb_nrm[o * 3 + k] = n[k];
-      if (out->gb_mat) out->gb_mat[o] = p->mat;
+      if (out->gb_mat) out->gb_mat[o] = word;
     }
   }
-  if (out->counters) {
-    out->counters[0] += frags;
-    out->counters[1] += culled;
-    out->counters[2] += clipped;
-    out->counters[3] += dropped;
-  }
+  return 0;
+}
+
+int orc_render_shadow_maps(const orc_meshes* m, const orc_batch* b, int32_t s_begin, int32_t s_end, float* maps) {
+  const int32_t R = b->shadow_res;
+  if (R <= 0 || !b->shadow_view || !b->shadow_intr) return 0;
+  pixel_winner* px = (pixel_winner*)malloc(sizeof(pixel_winner) * (size_t)R * (size_t)R);
+  if (!px) return -1;
+  for (int32_t s = s_begin; s < s_end; s++)
+    for (int l = 0; l < ORC_MAX_LIGHTS; l++) {
+      if (!casts_shadow(b, s, l)) continue;
+      const int64_t sl = (int64_t)s * ORC_MAX_LIGHTS + l;
+      visibility(m, b, s, b->shadow_view + sl * 12, b->shadow_intr + sl * 6, 0, R, R, 1, px, NULL);
+      float* map = maps + sl * R * R;
+      for (int64_t i = 0; i < (int64_t)R * R; i++) map[i] = px[i].key < 0 ? 0.0f : px[i].depth;
+    }
+  free(px);
   return 0;
 }
 
@@ -630,6 +751,7 @@ typedef struct {
   double L[3], E, ndl, spec, ndh, pw; /* pw = ndh^alpha */
   double H[3], hl, Lv[3], dl, d2;
   double S, dS; /* spot cone factor and its derivative in the cosine x (1 and 0 for other lights) */
+  double vis;   /* shadow factor (9 - k) / 9 of step 16, held fixed */
   int lit, has_h;
 } light_term;
 
@@ -654,11 +776,12 @@ static void view_lights_f64(const orc_batch* b, int32_t s, const float* V, const
   }
 }
 
-/* spot: NULL, or (view-space axis, cos_o, cos_i) of a spot light */
+/* spot: NULL, or (view-space axis, cos_o, cos_i) of a spot light; vis: the shadow factor */
 static void light_eval(int type, const double Lp[3], double I, const double P[3], const double n[3],
-                       const double Vv[3], double alpha, const double* spot, light_term* t) {
+                       const double Vv[3], double alpha, const double* spot, double vis, light_term* t) {
   memset(t, 0, sizeof(*t));
   t->S = 1.0;
+  t->vis = vis;
   if (type != 1) {
     for (int i = 0; i < 3; i++) t->Lv[i] = Lp[i] - P[i];
     t->d2 = t->Lv[0] * t->Lv[0] + t->Lv[1] * t->Lv[1] + t->Lv[2] * t->Lv[2];
@@ -678,10 +801,10 @@ static void light_eval(int type, const double Lp[3], double I, const double P[3]
         }
       }
     }
-    t->E = I * t->S / t->d2;
+    t->E = I * t->S * vis / t->d2;
   } else {
     for (int i = 0; i < 3; i++) t->L[i] = Lp[i];
-    t->E = I;
+    t->E = I * vis;
   }
   double ndl = n[0] * t->L[0] + n[1] * t->L[1] + n[2] * t->L[2];
   t->lit = ndl > 0.0;
@@ -730,8 +853,8 @@ void orc_shade_f64(const orc_batch* b, int32_t cam_begin, int32_t cam_end, const
     double scale = exp2(exposure_ev[s]);
     for (int64_t i = 0; i < npx; i++) {
       int64_t o = base + i;
-      int32_t mat = gb_mat[o];
-      if (mat < 0) {
+      int32_t word = gb_mat[o], mat = word & 0xff;
+      if (word < 0) {
         for (int k = 0; k < 3; k++) rgb[o * 3 + k] = b->background[s * 3 + k];
         continue;
       }
@@ -742,7 +865,7 @@ void orc_shade_f64(const orc_batch* b, int32_t cam_begin, int32_t cam_end, const
       for (int l = 0; l < count; l++) {
         light_term t;
         light_eval(type, Lp[l], light[((int64_t)s * ORC_MAX_LIGHTS + l) * 4 + 3], P, n, Vv, m[4],
-                   type == 2 ? sp[l] : NULL, &t);
+                   type == 2 ? sp[l] : NULL, (9 - ((word >> (8 + 4 * l)) & 15)) / 9.0, &t);
         double spec = m[3] * t.pw;
         for (int k = 0; k < 3; k++) acc[k] += t.E * (m[k] * t.ndl + spec);
       }
@@ -772,8 +895,8 @@ void orc_shade_backward_f64(const orc_batch* b, int32_t cam_begin, int32_t cam_e
     memset(dLp_view, 0, sizeof(dLp_view));
     for (int64_t i = 0; i < npx; i++) {
       int64_t o = base + i;
-      int32_t mat = gb_mat[o];
-      if (mat < 0) continue;
+      int32_t word = gb_mat[o], mat = word & 0xff;
+      if (word < 0) continue;
       const double* m = material + ((int64_t)s * ORC_MAX_MATERIALS + mat) * 5;
       const double* g = d_rgb + o * 3;
       double P[3], n[3], Vv[3];
@@ -784,7 +907,8 @@ void orc_shade_backward_f64(const orc_batch* b, int32_t cam_begin, int32_t cam_e
       for (int l = 0; l < count; l++) {
         light_term t;
         double I = light[((int64_t)s * ORC_MAX_LIGHTS + l) * 4 + 3];
-        light_eval(type, Lp[l], I, P, n, Vv, m[4], type == 2 ? sp[l] : NULL, &t);
+        light_eval(type, Lp[l], I, P, n, Vv, m[4], type == 2 ? sp[l] : NULL, (9 - ((word >> (8 + 4 * l)) & 15)) / 9.0,
+                   &t);
         double spec = m[3] * t.pw;
         for (int k = 0; k < 3; k++) acc[k] += t.E * (m[k] * t.ndl + spec);
         sum_endl += t.E * t.ndl;
@@ -803,14 +927,14 @@ void orc_shade_backward_f64(const orc_batch* b, int32_t cam_begin, int32_t cam_e
         }
         double* dl = d_light + ((int64_t)s * ORC_MAX_LIGHTS + l) * 4;
         if (type != 1) {
-          dl[3] += dE * t.S / t.d2;
-          double dd2 = -dE * I * t.S / (t.d2 * t.d2);
-          if (type == 2) /* x = -(L . axis): dE/dL = I/d2 * S'(x) * (-axis) */
-            for (int k = 0; k < 3; k++) dLvec[k] -= dE * I / t.d2 * t.dS * sp[l][k];
+          dl[3] += dE * t.S * t.vis / t.d2;
+          double dd2 = -dE * I * t.S * t.vis / (t.d2 * t.d2);
+          if (type == 2) /* x = -(L . axis): dE/dL = I vis/d2 * S'(x) * (-axis) */
+            for (int k = 0; k < 3; k++) dLvec[k] -= dE * I * t.vis / t.d2 * t.dS * sp[l][k];
           double ld = t.L[0] * dLvec[0] + t.L[1] * dLvec[1] + t.L[2] * dLvec[2];
           for (int k = 0; k < 3; k++) dLp_view[l][k] += (dLvec[k] - t.L[k] * ld) / t.dl + 2.0 * dd2 * t.Lv[k];
         } else {
-          dl[3] += dE;
+          dl[3] += dE * t.vis;
           for (int k = 0; k < 3; k++) dLp_view[l][k] += dLvec[k];
         }
       }

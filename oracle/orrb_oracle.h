@@ -70,6 +70,10 @@ typedef struct {
   const float* grading;         /* [S][8] colour-grading epilogue (step 13), or NULL */
   const float* light_spot;      /* [S][4][5] spot cones (step 10), or NULL */
   const float* emission;        /* [S][32] material emission (step 10), or NULL for none */
+  const float* shadow_view;     /* [S][4][3][4] shadow camera of each light (step 15), or NULL */
+  const float* shadow_intr;     /* [S][4][6] fx, fy, cx, cy, near, bias; fx == 0: no shadow */
+  const float* shadow_map;      /* [S][4][R][R] maps of step 15, read by step 16 (or NULL) */
+  int32_t shadow_res;           /* R, 0 for no shadows */
 } orc_batch;
 
 typedef struct {                /* every pointer may be NULL */
@@ -80,7 +84,7 @@ typedef struct {                /* every pointer may be NULL */
   float* rgb_linear;            /* [N][3] before clamping and quantisation */
   float* gb_pos;                /* [N][3] view-space position */
   float* gb_nrm;                /* [N][3] unit view-space normal, fp32 */
-  int32_t* gb_mat;              /* [N] material slot, -1 = background */
+  int32_t* gb_mat;              /* [N] material slot | shadowed taps of light l << (8 + 4l); -1 = background */
   int64_t* prim;                /* [N] winning key 2*prim_id + sub, -1 = background */
   float* depth2;                /* [N] depth of the nearest fragment of another key, +inf if none */
   int64_t* counters;            /* [4] fragments, triangles culled, clipped, dropped (accumulated) */
@@ -91,6 +95,10 @@ typedef struct {                /* every pointer may be NULL */
 /* Render images [cam_begin, cam_end).  Returns 0, or -1 on allocation failure. */
 int orc_render(const orc_meshes* m, const orc_batch* b, int32_t cam_begin, int32_t cam_end,
                const orc_outputs* out);
+
+/* Step 15: the shadow maps [S][4][R][R] of samples [s_begin, s_end) (maps of lights that cast
+ * no shadow are left as they were).  Returns 0, or -1 on allocation failure. */
+int orc_render_shadow_maps(const orc_meshes* m, const orc_batch* b, int32_t s_begin, int32_t s_end, float* maps);
 
 /* Rasterise already-snapped screen triangles (8 fractional bits) into one
  * W x H image: coverage, depth and the (depth, key) visibility test only.
@@ -106,7 +114,9 @@ uint16_t orc_f32_to_f16(float f);
 
 /* fp64 shading of a G-buffer over images [cam_begin, cam_end), parameters in
  * fp64: material [S][32][5], light [S][4][4], exposure_ev [S], ambient [S][3],
- * emission [S][32] (or NULL); spot cones come from b.
+ * emission [S][32] (or NULL); spot cones come from b.  gb_mat holds the
+ * G-buffer's material words: the slot in bits 0-7 and light l's shadowed
+ * taps (step 16) in bits 8 + 4l .. 11 + 4l, applied as the factor (9 - k) / 9.
  * Writes rgb [N][3] (background pixels get the background colour). */
 void orc_shade_f64(const orc_batch* b, int32_t cam_begin, int32_t cam_end,
                    const float* gb_pos, const float* gb_nrm, const int32_t* gb_mat,

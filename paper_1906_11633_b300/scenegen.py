@@ -248,6 +248,12 @@ class Batch:
     light_spot: Optional[np.ndarray] = None
     # [B, 32] float32 material emission e (the emitted colour is e * albedo), or None for none
     emission: Optional[np.ndarray] = None
+    # shadows: per light a perspective shadow camera, view [B, 4, 3, 4] (camera-from-world) and
+    # intrinsics [B, 4, 6] (fx, fy, cx, cy, near, depth bias; fx == 0: the light casts none),
+    # rendered into square maps of side shadow_res; None / 0 for no shadows
+    shadow_view: Optional[np.ndarray] = None
+    shadow_intr: Optional[np.ndarray] = None
+    shadow_res: int = 0
 
     @property
     def n_samples(self) -> int:
@@ -315,7 +321,16 @@ def concat_batches(batches: Sequence[Batch]) -> Batch:
         grading=_concat_opt(batches, "grading", identity_grading),
         light_spot=_concat_opt(batches, "light_spot", lambda n: np.zeros((n, MAX_LIGHTS, 5), np.float32)),
         emission=_concat_opt(batches, "emission", lambda n: np.zeros((n, MAX_MATERIALS), np.float32)),
+        shadow_view=_concat_opt(batches, "shadow_view", lambda n: np.zeros((n, MAX_LIGHTS, 3, 4), np.float32)),
+        shadow_intr=_concat_opt(batches, "shadow_intr", lambda n: np.zeros((n, MAX_LIGHTS, 6), np.float32)),
+        shadow_res=_shadow_res(batches),
     )
+
+
+def _shadow_res(batches):
+    res = {b.shadow_res for b in batches if b.shadow_view is not None}
+    assert len(res) <= 1, "batches with shadows must share one shadow-map size"
+    return res.pop() if res else 0
 
 
 def _concat_opt(batches, name, neutral):
@@ -348,6 +363,9 @@ def select_samples(batch: Batch, idx: Sequence[int]) -> Batch:
             grading=batch.grading[s:s + 1] if batch.grading is not None else None,
             light_spot=batch.light_spot[s:s + 1] if batch.light_spot is not None else None,
             emission=batch.emission[s:s + 1] if batch.emission is not None else None,
+            shadow_view=batch.shadow_view[s:s + 1] if batch.shadow_view is not None else None,
+            shadow_intr=batch.shadow_intr[s:s + 1] if batch.shadow_intr is not None else None,
+            shadow_res=batch.shadow_res,
         ))
     return concat_batches(parts)
 
@@ -744,6 +762,24 @@ def orbit_views(seed: int, sample_ids, n_cams: int, poi, radius=(0.4, 0.6), elev
     return views, np.repeat(np.arange(len(ids)), n_cams).astype(np.int32)
 
 
+def spot_shadow_cameras(pos, axis, cos_outer, res: int, near: float = 0.05, bias: float = 0.004,
+                        margin: float = 1.1):
+    """A perspective shadow camera per spot light: at the light, looking along its axis, with a
+    square field of view of `margin` times the outer cone.  Returns views [..., 3, 4] and
+    intrinsics [..., 6] (fx, fy, cx, cy, near, bias)."""
+    pos, axis = np.asarray(pos, np.float64), np.asarray(axis, np.float64)
+    up = np.where(np.abs(axis[..., 2:3]) > 0.99, np.array([0.0, 1.0, 0.0]), np.array([0.0, 0.0, 1.0]))
+    f = axis / np.linalg.norm(axis, axis=-1, keepdims=True)
+    r = np.cross(f, up)
+    r /= np.linalg.norm(r, axis=-1, keepdims=True)
+    R = np.stack([r, np.cross(r, f), -f], axis=-2)
+    half = np.minimum(np.arccos(np.clip(cos_outer, -1.0, 1.0)) * margin, np.radians(80.0))
+    fx = 0.5 * res / np.tan(half)
+    intr = np.stack([fx, fx, np.full_like(fx, 0.5 * res), np.full_like(fx, 0.5 * res), np.full_like(fx, near),
+                     np.full_like(fx, bias)], -1)
+    return view_matrix(R, pos), intr
+
+
 # the block's six calibrated face colours (HSV): red, orange, yellow, green, blue, purple
 BLOCK_HSV = np.array([[0.00, 0.85, 0.80], [0.08, 0.85, 0.85], [0.15, 0.80, 0.85],
                       [0.33, 0.70, 0.60], [0.60, 0.75, 0.70], [0.78, 0.60, 0.60]])
@@ -751,12 +787,12 @@ N_SPOTS = 3
 
 
 def benchmark_batch(seed: int, sample_ids, res: int = 200, n_cams: int = 3, orbit: bool = False,
-                    grading: bool = True, meshes=None) -> Batch:
-    """The hand scene configured like the paper's benchmark (Sec. 5) where this renderer can: three
-    spot lights placed by LightSetup about the block with LightRandomizer levels and cones,
-    FixedHue materials (with emission) for the block's faces, the material randomizer for the
-    hand and the table, camera jitter (or orbit), post-processing grading.  Shadows are not
-    rendered."""
+                    grading: bool = True, meshes=None, shadow_res: int = 0) -> Batch:
+    """The hand scene configured like the paper's benchmark (Sec. 5): three spot lights placed by
+    LightSetup about the block with LightRandomizer levels and cones, FixedHue materials (with
+    emission) for the block's faces, the material randomizer for the hand and the table, camera
+    jitter (or orbit), post-processing grading; with `shadow_res` > 0 every spot light casts
+    shadows from a shadow map of that side."""
     b = hand_batch(seed, sample_ids, res=res, n_cams=n_cams, meshes=meshes, grading=grading)
     ids = b.sample_ids
     B = len(ids)
@@ -781,6 +817,13 @@ def benchmark_batch(seed: int, sample_ids, res: int = 200, n_cams: int = 3, orbi
     if orbit:
         views, owner = orbit_views(seed, ids, n_cams, BLOCK_CENTRE)
         kw.update(cam_view=views.astype(np.float32), cam_sample=owner)
+    if shadow_res > 0:
+        sv, si = spot_shadow_cameras(pos, axis, cos_o, shadow_res)
+        shadow_view = np.zeros((B, MAX_LIGHTS, 3, 4))
+        shadow_intr = np.zeros((B, MAX_LIGHTS, 6))
+        shadow_view[:, :N_SPOTS], shadow_intr[:, :N_SPOTS] = sv, si
+        kw.update(shadow_view=shadow_view.astype(np.float32), shadow_intr=shadow_intr.astype(np.float32),
+                  shadow_res=int(shadow_res))
     return b.with_params(**kw)
 
 

@@ -117,10 +117,12 @@ def test_unused_parameters_have_exactly_zero_gradient(oracle):
     assert (dl[0, b.light_meta[0, 0]:] == 0).all()
 
 
-def test_spot_and_emission_adjoint_matches_central_differences(oracle):
+@pytest.mark.parametrize("shadow_res", [0, 64])
+def test_spot_and_emission_adjoint_matches_central_differences(oracle, shadow_res):
     """The benchmark-like scene: three spot lights (the cone factor depends on the light position)
-    and emissive block faces; light, exposure and emission gradients against fp64 differences."""
-    b = sg.benchmark_batch(5, np.arange(2), res=40, grading=False)
+    and emissive block faces, with and without shadow maps (the shadow factors, carried in the
+    G-buffer, stay fixed); light, exposure and emission gradients against fp64 differences."""
+    b = sg.benchmark_batch(5, np.arange(2), res=40, grading=False, shadow_res=shadow_res)
     b = b.with_params(emission=b.emission + np.float32(0.05))     # every slot emissive
     o = oracle.render(b, gbuffer=True)
     gb = (o["gb_pos"], o["gb_nrm"], o["gb_mat"])
@@ -141,10 +143,13 @@ def test_spot_and_emission_adjoint_matches_central_differences(oracle):
                                                 return_emission=True)
     # the ramp of some cone crosses pixels of the scene, so the cone term is exercised
     cams = np.repeat(b.cam_sample, b.cam_wh[:, 0] * b.cam_wh[:, 1])
+    if shadow_res:
+        k = (gb[2][fg] >> 8) & 15
+        assert ((k > 0) & (k < 9)).any()                               # partly shadowed pixels
     checks = [("l", (s, li, k), dl[s, li, k]) for s in range(2) for li in range(3) for k in range(4)]
     checks += [("e", (s,), de[s]) for s in range(2)]
     for s in range(2):
-        used = np.unique(gb[2][fg & (cams == s)])
+        used = np.unique(gb[2][fg & (cams == s)] & 0xff)
         checks += [("em", (s, mat), dem[s, mat]) for mat in used[:6]]
         checks += [("m", (s, mat, k), dm[s, mat, k]) for mat in used[:3] for k in range(3)]
     fd, an = [], []
@@ -160,6 +165,6 @@ def test_spot_and_emission_adjoint_matches_central_differences(oracle):
     assert np.abs(an).max() > 0
     assert _rel(an, fd).max() < 1e-4, (_rel(an, fd).max(), checks[int(np.argmax(_rel(an, fd)))])
     # emission closed form: dL/de = 2^EV sum_px g . rho over the slot's pixels
-    s, mat = 0, int(np.unique(gb[2][fg & (cams == 0)])[0])
-    px = fg & (cams == s) & (gb[2] == mat)
+    s, mat = 0, int(np.unique(gb[2][fg & (cams == 0)] & 0xff)[0])
+    px = fg & (cams == s) & ((gb[2] & 0xff) == mat)
     np.testing.assert_allclose(dem[s, mat], 2.0 ** e[s] * (g[px] @ m[s, mat, :3]).sum(), rtol=1e-10)
