@@ -40,6 +40,7 @@ N_SAMPLES = 256
 N_CAMS = 3
 RES = 200
 SEED = 0
+SHADOW_RES = 256    # side of the spot lights' shadow maps in the shadow workload
 BYTES_PER_PX = 3 + 4 + 6 + 1           # rgb u8x3, depth f32, normal f16x3, seg u8
 CONFIG = {"workload": "hand-like scene: 256 samples x 3 cameras x 200x200, 24 capsule links + block + table, "
                       "1-4 point lights, 4 channels", "global_batch": N_SAMPLES, "cameras": N_CAMS,
@@ -610,6 +611,33 @@ def run_spot(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_shadow(args, world, rank, local):
+    """The benchmark-like scene with its soft shadows: three shadow-casting spot lights, each with a
+    256 x 256 shadow map rendered every step (its own depth-only launch over the back faces) and a
+    3 x 3 percentage-closer lookup per pixel and light; kernel time of both launches against the
+    same scene without shadows."""
+    import torch
+    from paper_1906_11633_b300 import scenegen as sg
+    from paper_1906_11633_b300.render import Renderer
+    torch.cuda.set_device(local)
+    ids = shard_samples(rank, world, N_SAMPLES)
+    bench = sg.benchmark_batch(SEED, ids, res=RES, n_cams=N_CAMS, shadow_res=SHADOW_RES)
+    r = Renderer(bench.meshes, device=local)
+    db = r.upload(bench)
+    sms = _timed_renders(r, db, args, world)
+    nms = _timed_renders(r, r.upload(bench.with_params(shadow_view=None, shadow_intr=None, shadow_res=0)), args, world)
+    if rank != 0:
+        return
+    n_maps = int((bench.light_meta[:, 0]).sum())
+    line = {"workload": "shadow", "metric": "samples/s, benchmark-like scene with shadow-casting spot lights",
+            "value": world * N_SAMPLES / (sms / 1e3), "unit": UNIT, "n_gpus": world, "ms_per_step": sms,
+            "unshadowed_ms_per_step": nms, "overhead": sms / nms - 1.0, "device_status": r.status(),
+            "gpu_launches_per_step": 2,
+            "config": {"samples": N_SAMPLES, "cameras": N_CAMS, "resolution": RES, "shadow_maps": n_maps,
+                       "shadow_res": SHADOW_RES, "pcf": "3x3 taps", "lights": "3 spot lights", "grading": True}}
+    print(json.dumps(line), flush=True)
+
+
 def run_serve(args, world, rank, local):
     """Poisson arrivals at 2000 req/s of 1-64-sample hand requests at {64,128,200,256} px, 1-3 cameras."""
     import torch
@@ -656,7 +684,7 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the fused kernel from an ncu capture of this build")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["hand", "uneven", "diff", "serve", "grade", "track", "spot"], default="hand",
+    ap.add_argument("--workload", choices=["hand", "uneven", "diff", "serve", "grade", "track", "spot", "shadow"], default="hand",
                     help="hand: the headline line; the others print supplementary lines")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--samples", type=int, default=N_SAMPLES,
@@ -681,6 +709,8 @@ def main():
         run_track(args, world, rank, local)
     elif args.workload == "spot":
         run_spot(args, world, rank, local)
+    elif args.workload == "shadow":
+        run_shadow(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

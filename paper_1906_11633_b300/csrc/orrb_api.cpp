@@ -193,12 +193,21 @@ orrb_status check_shape(orrb_ctx* ctx, const orrb_batch_shape* s) {
     return fail(ctx, ORRB_ERR_INVALID_ARG, "max_tris_per_sample %d", s->max_tris_per_sample);
   if (s->max_cams_per_sample < 0 || s->total_pixels < 0)
     return fail(ctx, ORRB_ERR_INVALID_ARG, "bad camera or pixel count");
+  if (s->shadow_res < 0 || s->shadow_res > ORRB_MAX_RESOLUTION)
+    return fail(ctx, ORRB_ERR_INVALID_ARG, "shadow_res %d outside [0, %d]", s->shadow_res, ORRB_MAX_RESOLUTION);
   return ORRB_OK;
 }
 
+int tiles_of(int w, int h, const orrb_config& c) {
+  int tw = std::min(w, c.tile_w);
+  return ((w + tw - 1) / tw) * ((h + c.tile_h - 1) / c.tile_h);
+}
+
+// the camera images' tiling, or the shadow maps' when they need more tiles
 int max_tiles_of(const orrb_batch_shape& s, const orrb_config& c) {
-  int tw = std::min(s.max_width, c.tile_w);
-  return ((s.max_width + tw - 1) / tw) * ((s.max_height + c.tile_h - 1) / c.tile_h);
+  int t = tiles_of(s.max_width, s.max_height, c);
+  if (s.shadow_res > 0) t = std::max(t, tiles_of(s.shadow_res, s.shadow_res, c));
+  return t;
 }
 
 struct Plan {
@@ -210,7 +219,8 @@ orrb_status plan(orrb_ctx* ctx, const orrb_batch_shape& s, const orrb_config& c,
   P->max_tiles = max_tiles_of(s, c);
   SlotLayout L = slot_layout(s.max_tris_per_sample, P->max_tiles);
   P->slot_bytes = L.total;
-  P->smem = render_smem_bytes(c.threads, c.tile_w, c.tile_h, s.max_inst_per_sample, P->max_tiles, s.max_width);
+  P->smem = render_smem_bytes(c.threads, c.tile_w, c.tile_h, s.max_inst_per_sample, P->max_tiles,
+                              std::max(s.max_width, s.shadow_res), s.shadow_res > 0);
   if (P->smem > 227 * 1024) return fail(ctx, ORRB_ERR_INVALID_ARG, "tile / instance limits need %zu B of shared memory", P->smem);
   if (c.mode == ORRB_MODE_FUSED) {
     int fit = -1;
@@ -225,7 +235,7 @@ orrb_status plan(orrb_ctx* ctx, const orrb_batch_shape& s, const orrb_config& c,
     P->n_slots = ctx->sm_count * P->ctas_per_sm;
   } else {
     P->ctas_per_sm = 0;
-    P->n_slots = std::max(s.max_cams_per_sample, 1);
+    P->n_slots = std::max(std::max(s.max_cams_per_sample, 1), s.shadow_res > 0 ? kMaxLights : 1);
   }
   P->total = 256 + (size_t)P->n_slots * P->slot_bytes;
   return ORRB_OK;
@@ -254,6 +264,9 @@ void fill_batch(Params& p, const orrb_batch_shape& s, const orrb_batch_desc& b) 
   p.grading = b.grading;
   p.light_spot = b.light_spot;
   p.emission = b.emission;
+  p.shadow_view = b.shadow_view;
+  p.shadow_intr = b.shadow_intr;
+  p.shadow_res = s.shadow_res > 0 && b.shadow_view && b.shadow_intr ? s.shadow_res : 0;
   p.total_pixels = s.total_pixels;
   p.t_max = s.max_tris_per_sample;
   p.inst_max = s.max_inst_per_sample;
@@ -268,6 +281,42 @@ orrb_status check_desc(orrb_ctx* ctx, const orrb_batch_desc* b) {
                        b->light_meta,  b->material,  b->exposure_ev, b->ambient, b->background};
   for (size_t i = 0; i < sizeof(req) / sizeof(req[0]); i++)
     if (!req[i]) return fail(ctx, ORRB_ERR_INVALID_ARG, "batch array %zu is null", i);
+  return ORRB_OK;
+}
+
+// Enqueue one render: the shadow pass first when the batch has shadows (its own launch over
+// the images sample * 4 + light, depth only, into the shadow maps), then the camera images.
+// n_slots: the scratch slots the fused mode may use; ws: the status word and queue counters.
+orrb_status enqueue_render(orrb_ctx* ctx, Params& p, const orrb_batch_shape& s, int mode, int threads, int n_slots,
+                           char* ws, void* stream) {
+  char err[256] = {0};
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (p.shadow_res > 0) {
+    Params q = p;
+    q.shadow_pass = 1;
+    q.n_cams = s.n_samples * kMaxLights;
+    q.rgb = nullptr;
+    q.normal = nullptr;
+    q.seg = nullptr;
+    q.rgb_linear = nullptr;
+    q.gbuffer = nullptr;
+    q.tracker = nullptr;
+    q.grading = nullptr;
+    q.depth = p.shadow_map;
+    q.total_pixels = (int64_t)q.n_cams * s.shadow_res * s.shadow_res;
+    q.w_max = q.h_max = s.shadow_res;
+    const int n_ctas = mode == ORRB_MODE_FUSED ? std::min(n_slots, std::max(q.n_cams, 1)) : 0;
+    q.n_slots = n_ctas;
+    if (launch_render(q, mode, threads, n_ctas, kMaxLights, stream, err, sizeof(err)))
+      return fail(ctx, ORRB_ERR_CUDA, "%s", err);
+    // the camera launch's image queue starts again at zero (the status word carries over)
+    cudaError_t e = cudaMemsetAsync(ws + 4, 0, 8, st);
+    if (e != cudaSuccess) return fail(ctx, ORRB_ERR_CUDA, "queue reset: %s", cudaGetErrorString(e));
+  }
+  const int n_ctas = mode == ORRB_MODE_FUSED ? std::min(n_slots, std::max(s.n_cams, 1)) : 0;
+  p.n_slots = n_ctas;
+  if (launch_render(p, mode, threads, n_ctas, std::max(s.max_cams_per_sample, 1), stream, err, sizeof(err)))
+    return fail(ctx, ORRB_ERR_CUDA, "%s", err);
   return ORRB_OK;
 }
 
@@ -421,6 +470,8 @@ orrb_status orrb_render_batch(orrb_ctx* ctx, const orrb_batch_shape* shape, cons
   p.rgb_linear = out->rgb_linear;
   p.gbuffer = out->gbuffer;
   p.tracker = out->tracker;
+  p.shadow_map = out->shadow_map;
+  if (p.shadow_res > 0 && !p.shadow_map) return fail(ctx, ORRB_ERR_INVALID_ARG, "a batch with shadows needs out->shadow_map");
   const ArenaLayout& A = ctx->arena;
   p.meshes = reinterpret_cast<const MeshEntry*>(ctx->arena_ptr + A.meshes);
   p.meshlets = reinterpret_cast<const MeshletEntry*>(ctx->arena_ptr + A.meshlets);
@@ -443,12 +494,7 @@ orrb_status orrb_render_batch(orrb_ctx* ctx, const orrb_batch_shape* shape, cons
   cudaError_t e = cudaMemsetAsync(ws, 0, 16, s);
   if (e != cudaSuccess) return fail(ctx, ORRB_ERR_CUDA, "workspace clear: %s", cudaGetErrorString(e));
   if (shape->n_cams == 0 || shape->n_samples == 0) return ORRB_OK;
-  char err[256] = {0};
-  int n_ctas = c.mode == ORRB_MODE_FUSED ? std::min(P.n_slots, std::max(shape->n_cams, 1)) : 0;
-  p.n_slots = n_ctas;
-  if (launch_render(p, c.mode, c.threads, n_ctas, std::max(shape->max_cams_per_sample, 1), stream, err, sizeof(err)))
-    return fail(ctx, ORRB_ERR_CUDA, "%s", err);
-  return ORRB_OK;
+  return enqueue_render(ctx, p, *shape, c.mode, c.threads, P.n_slots, ws, stream);
 }
 
 orrb_status orrb_render_batch_noalloc(orrb_ctx* ctx, const orrb_batch_shape* shape, const orrb_batch_desc* batch,
@@ -489,6 +535,8 @@ orrb_status orrb_render_batch_noalloc(orrb_ctx* ctx, const orrb_batch_shape* sha
   p.rgb_linear = out->rgb_linear;
   p.gbuffer = out->gbuffer;
   p.tracker = out->tracker;
+  p.shadow_map = out->shadow_map;
+  if (p.shadow_res > 0 && !p.shadow_map) return fail(ctx, ORRB_ERR_INVALID_ARG, "a batch with shadows needs out->shadow_map");
   const ArenaLayout& A = ctx->arena;
   p.meshes = reinterpret_cast<const MeshEntry*>(ctx->arena_ptr + A.meshes);
   p.meshlets = reinterpret_cast<const MeshletEntry*>(ctx->arena_ptr + A.meshlets);
@@ -505,7 +553,6 @@ orrb_status orrb_render_batch_noalloc(orrb_ctx* ctx, const orrb_batch_shape* sha
   p.images_done = reinterpret_cast<uint32_t*>(ws + 8);
   p.scratch = ws + 256;
   p.slot_bytes = P.slot_bytes;
-  p.n_slots = std::min(n_slots, std::max(shape->n_cams, 1));  // one slot per launched CTA
   p.plain_sample = -1;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // the array keeps the previous call's contents: the status word and the queue counters restart at zero
@@ -513,11 +560,7 @@ orrb_status orrb_render_batch_noalloc(orrb_ctx* ctx, const orrb_batch_shape* sha
   if (e == cudaSuccess && device_status) e = cudaMemsetAsync(device_status, 0, 4, s);
   if (e != cudaSuccess) return fail(ctx, ORRB_ERR_CUDA, "scratch clear: %s", cudaGetErrorString(e));
   if (shape->n_cams == 0 || shape->n_samples == 0) return ORRB_OK;
-  char err[256] = {0};
-  if (launch_render(p, ORRB_MODE_FUSED, c.threads, p.n_slots, 1, stream, err,
-                    sizeof(err)))
-    return fail(ctx, ORRB_ERR_CUDA, "%s", err);
-  return ORRB_OK;
+  return enqueue_render(ctx, p, *shape, ORRB_MODE_FUSED, c.threads, n_slots, ws, stream);  // one slot per CTA
 }
 
 orrb_status orrb_read_status(orrb_ctx* ctx, const void* workspace, void* stream, uint32_t* status) {

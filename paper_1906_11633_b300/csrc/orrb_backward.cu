@@ -109,11 +109,13 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
   }
   for (long long r0 = i0; r0 < i1; r0 += kBwdThreads) {
     const long long i = r0 + tid;
-    int mat = -1;
+    int mat = -1, word = -1;
     float dm[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
     if (i < i1) {
       const long long o = base + i;
-      mat = __float_as_int(bp.gbuffer[6 * N + o]);
+      // the material word: slot in bits 0-7, light l's shadowed taps in bits 8 + 4l .. 11 + 4l
+      word = __float_as_int(bp.gbuffer[6 * N + o]);
+      mat = word < 0 ? -1 : (word & 0xff);
       if (mat >= kMaxMaterials) mat = -1;
       if (mat >= 0) {
         const float P[3] = {bp.gbuffer[o], bp.gbuffer[N + o], bp.gbuffer[2 * N + o]};
@@ -138,7 +140,9 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
         for (int l = 0; l < kMaxLights; l++) {
           if (l >= sh.n_lights) break;
           float L[3], Lv[3] = {0.0f, 0.0f, 0.0f}, E, d2 = 1.0f, rinv = 1.0f;
-          const float I = sh.lv[l][3];
+          // the shadow factor (9 - k) / 9 is held fixed: it scales the intensity
+          const float vis = __fdividef(float(9 - ((word >> (8 + 4 * l)) & 15)), 9.0f);
+          const float I = sh.lv[l][3] * vis;
           float S = 1.0f, dS = 0.0f;  // spot cone factor, and its derivative in t
           if (sh.light_type != 1) {
             for (int k = 0; k < 3; k++) Lv[k] = sh.lv[l][k] - P[k];
@@ -186,7 +190,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
             for (int k = 0; k < 3; k++) dL[k] += (dH[k] - H[k] * hd) * rh;
           }
           if (sh.light_type != 1) {
-            dI[l] += dE * S * (rinv * rinv);
+            dI[l] += dE * S * (rinv * rinv) * vis;
             const float dd2 = -dE * I * S * (rinv * rinv) * (rinv * rinv);
             // spot: t = -(L . a) / (cos_i - cos_o) + ..., so dE/dL = -I |Lv|^-2 S'(t) la_xyz
             if (sh.light_type == 2) {
@@ -196,7 +200,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
             const float ld = L[0] * dL[0] + L[1] * dL[1] + L[2] * dL[2];
             for (int k = 0; k < 3; k++) dlv[l][k] += (dL[k] - L[k] * ld) * rinv + 2.0f * dd2 * Lv[k];
           } else {
-            dI[l] += dE;
+            dI[l] += dE * vis;
             for (int k = 0; k < 3; k++) dlv[l][k] += dL[k];
           }
         }

@@ -57,6 +57,8 @@ constexpr int kPlainRasterSplit = 8;  // plain mode: CTAs sharing one image's ti
 constexpr int kFeatGrade = 1;  // colour grading of the rgb output
 constexpr int kFeatTrack = 2;  // tracker rows
 constexpr int kFeatLight = 4;  // a cone table (spot lights may occur) or material emission
+constexpr int kFeatShadow = 8;        // shadow-map lookups in the shading (implies kFeatLight)
+constexpr int kFeatShadowPass = 16;   // the depth-only pass that renders the shadow maps
 
 // The PCG hash (Jarzynski and Olano, "Hash Functions for GPU Rendering", JCGT 2020): one LCG
 // step, a random xorshift and a multiply.
@@ -86,6 +88,15 @@ struct ImageInfo {
   float gm[3][4];
   float grain;
   unsigned grain_key;
+};
+
+// Shadows of the current image (the lookup instances; in dynamic shared memory right after the
+// span table, present only in launches with shadow maps): per casting light the
+// camera-to-shadow-camera map S V^-1 and the shadow camera's fx, fy, cx, cy, near, bias.
+struct ShadowInfo {
+  int cast[kMaxLights];
+  float sm[kMaxLights][12];
+  float si[kMaxLights][6];
 };
 
 struct CtaShared {
@@ -154,8 +165,9 @@ struct SmemPtrs {
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
 
+// shadows: the launch looks up shadow maps (a ShadowInfo follows the span table)
 __host__ __device__ inline SmemLayout smem_layout(int threads, int tile_w, int tile_h, int inst_max, int max_tiles,
-                                                  int w_max) {
+                                                  int w_max, bool shadows) {
   SmemLayout L;
   const size_t tw = size_t(tile_w < w_max ? tile_w : w_max), th = size_t(tile_h);
   L.uni = al16(size_t(3) * (inst_max + 2) * sizeof(int));
@@ -168,7 +180,7 @@ __host__ __device__ inline SmemLayout smem_layout(int threads, int tile_w, int t
   size_t u = L.g_size > L.b_size ? L.g_size : L.b_size;
   u = u > L.r_size ? u : L.r_size;
   L.spans = L.uni + al16(u);
-  L.total = L.spans + size_t(kSpanCap) * sizeof(uint32_t);
+  L.total = L.spans + size_t(kSpanCap) * sizeof(uint32_t) + (shadows ? al16(sizeof(ShadowInfo)) : 0);
   return L;
 }
 
@@ -230,35 +242,39 @@ __device__ void block_exclusive_scan(int* a, int n, int* tmp) {
 // per-image set-up (camera, lights, materials, instance tables)
 // ---------------------------------------------------------------------------
 // track: (with tables) also start this image's tracker rows empty.
+// kPass: the shadow pass, whose image `cam` is the map of light cam % 4 of sample cam / 4.
+template <bool kPass = false>
 __device__ void setup_image(const Params& p, int cam, CtaShared& sh, int* mprefix, int* tprefix, int* mbegin,
                             bool tables, bool track = false) {
   ImageInfo& im = sh.im;
   const int tid = threadIdx.x;
   if (tid == 0) {
     im.cam = cam;
-    int s = p.cam_sample[cam];
+    int s = kPass ? cam / kMaxLights : p.cam_sample[cam];
     im.s = s;
-    im.W = p.cam_wh[cam * 2 + 0];
-    im.H = p.cam_wh[cam * 2 + 1];
+    im.W = kPass ? p.shadow_res : p.cam_wh[cam * 2 + 0];
+    im.H = kPass ? p.shadow_res : p.cam_wh[cam * 2 + 1];
     im.valid = 1;
-    const float* in = p.cam_intr + cam * 6;
+    const float* in = (kPass ? p.shadow_intr : p.cam_intr) + cam * 6;
     im.fx = in[0];
     im.fy = in[1];
     im.cx = in[2];
     im.cy = in[3];
     im.near = in[4];
-    im.ortho = in[5] != 0.0f;
+    im.ortho = kPass ? 0 : in[5] != 0.0f;
     im.inv_fx = 1.0f / im.fx;
     im.inv_fy = 1.0f / im.fy;
-    if (s < 0 || s >= p.n_samples || im.W < 1 || im.H < 1 || im.W > p.w_max || im.H > p.h_max ||
-        !(im.near > 0.0f) || !(im.fx != 0.0f) || !(im.fy != 0.0f)) {
+    if (kPass && in[0] == 0.0f) {  // the light casts no shadow: no map (not an error)
+      im.valid = 0;
+    } else if (s < 0 || s >= p.n_samples || im.W < 1 || im.H < 1 || im.W > p.w_max || im.H > p.h_max ||
+               !(im.near > 0.0f) || !(im.fx != 0.0f) || !(im.fy != 0.0f)) {
       flag_status(p, ORRB_DEV_BAD_CAMERA);
       im.valid = 0;
       s = 0;
       im.s = 0;
     }
-    for (int k = 0; k < 12; k++) im.V[k] = p.cam_view[cam * 12 + k];
-    im.px_off = p.img_offset[cam];
+    for (int k = 0; k < 12; k++) im.V[k] = (kPass ? p.shadow_view : p.cam_view)[cam * 12 + k];
+    im.px_off = kPass ? (long long)cam * p.shadow_res * p.shadow_res : p.img_offset[cam];
     if (im.valid && (im.px_off < 0 || im.px_off + (long long)im.W * im.H > p.total_pixels)) {
       flag_status(p, ORRB_DEV_BAD_CAMERA);  // the image would not fit in the output arrays
       im.valid = 0;
@@ -288,6 +304,7 @@ __device__ void setup_image(const Params& p, int cam, CtaShared& sh, int* mprefi
     }
     im.n_lights = nl;
     im.light_type = lt;
+    if (kPass && cam % kMaxLights >= nl) im.valid = 0;  // no such light: no map
     sh.n_vis = 0;
     sh.n_big = 0;
     sh.next_tile = 0;
@@ -439,6 +456,8 @@ __device__ __noinline__ void cut_vertex(const ImageInfo& im, const float* pin, c
 // Near-plane clip of triangle (a, b, c) of the staged cluster; emits up to two
 // sub-triangles.  Vertex order follows Sutherland-Hodgman: for each edge
 // (v_k, v_k+1) emit v_k if inside, then the cut if the edge crosses.
+// kBack: emit each sub-triangle reversed (the shadow pass keeps back faces).
+template <int kBack>
 __device__ __noinline__ int clip_triangle(int t_max, Record* rec, const ImageInfo& im, const WarpG* wg, int v0,
                                           int v1, int v2, int prim, int mat, int seg, unsigned* keys, uint2* boxes,
                                           unsigned* dropped) {
@@ -464,7 +483,7 @@ __device__ __noinline__ int clip_triangle(int t_max, Record* rec, const ImageInf
   }
   int emitted = 0;
   for (int sub = 0; sub + 2 < np; sub++) {
-    const CutVert* q[3] = {&poly[0], &poly[sub + 1], &poly[sub + 2]};
+    const CutVert* q[3] = {&poly[0], &poly[sub + 1 + kBack], &poly[sub + 2 - kBack]};
     if (!(q[0]->ok && q[1]->ok && q[2]->ok)) {
       *dropped = 1;
       continue;
@@ -489,8 +508,9 @@ __device__ __noinline__ int clip_triangle(int t_max, Record* rec, const ImageInf
 // phase G: geometry of one image
 // ---------------------------------------------------------------------------
 // kTrack: the launch writes tracker rows (a separate instance, so that the common case carries none
-// of that code).
-template <bool kTrack>
+// of that code).  kBack: keep back faces instead of front faces (the shadow pass): every triangle
+// is taken with its second and third vertices swapped.
+template <bool kTrack, bool kBack = false>
 __device__ void geometry_phase(const Params& p, CtaShared& sh, const int* mprefix, const int* tprefix,
                                const int* mbegin, WarpG* wgs, const Scratch& sc) {
   const ImageInfo& im = sh.im;
@@ -600,7 +620,8 @@ __device__ void geometry_phase(const Params& p, CtaShared& sh, const int* mprefi
       int cnt = 0;
       if (t < nt) {
         const uint32_t tri = wg->tri[t];
-        const int vi[3] = {int(tri & 0xff), int((tri >> 8) & 0xff), int((tri >> 16) & 0xff)};
+        const int ia = int((tri >> 8) & 0xff), ib = int((tri >> 16) & 0xff);
+        const int vi[3] = {int(tri & 0xff), kBack ? ib : ia, kBack ? ia : ib};
         int mat = mat_base + int(tri >> 24);
         if (mat < 0 || mat >= kMaxMaterials) {
           badmat = 1;
@@ -629,7 +650,9 @@ __device__ void geometry_phase(const Params& p, CtaShared& sh, const int* mprefi
           unsigned kk[2];
           uint2 bb[2];
           unsigned drop = 0;
-          cnt = clip_triangle(p.t_max, sc.rec, im, wg, vi[0], vi[1], vi[2], prim, mat, seg, kk, bb, &drop);
+          // (the shadow pass clips the triangle in its own order and reverses what comes out)
+          cnt = kBack ? clip_triangle<1>(p.t_max, sc.rec, im, wg, vi[0], vi[2], vi[1], prim, mat, seg, kk, bb, &drop)
+                      : clip_triangle<0>(p.t_max, sc.rec, im, wg, vi[0], vi[1], vi[2], prim, mat, seg, kk, bb, &drop);
           dropped |= drop;
           key0 = kk[0];
           box0 = bb[0];
@@ -886,8 +909,10 @@ __device__ void big_spans(const Params& p, const CtaShared& sh, const Scratch& s
 }
 
 // kLight: the batch has a cone table (type-2, spot, lights can occur) or material emission.
-template <bool kLight>
-__device__ void shade(const CtaShared& sh, const float P[3], const float n[3], int mat, float rgb[3]) {
+// kShadow: vis[l] is light l's shadow factor.
+template <bool kLight, bool kShadow = false>
+__device__ void shade(const CtaShared& sh, const float P[3], const float n[3], int mat, float rgb[3],
+                      const float* vis = nullptr) {
   const ImageInfo& im = sh.im;
   const float4 ma = *reinterpret_cast<const float4*>(sh.mat[mat]);
   float2 mb;  // shininess, emission
@@ -932,6 +957,7 @@ __device__ void shade(const CtaShared& sh, const float P[3], const float n[3], i
       r = 1.0f;
       E = lq.w;
     }
+    if (kShadow) E *= vis[l];
     const float ndl = fmaxf(0.0f, (n[0] * Lx + n[1] * Ly + n[2] * Lz) * r);
     D = fmaf(E, ndl, D);
     if (ndl > 0.0f && m[3] != 0.0f) {
@@ -952,6 +978,69 @@ __device__ void shade(const CtaShared& sh, const float P[3], const float n[3], i
 // the raster phase).  White balance, the rotation about the grey axis, saturation, contrast and
 // brightness are each affine in the colour, so they compose into one map c -> A c + t, applied
 // per pixel; the grain stays per pixel.
+// Light l's shadow camera for this image (its thread, in the shadow instances only, after
+// setup_image and before a barrier that precedes the raster phase): M = S V^-1 with
+// V^-1 = [R^T | -R^T t], every product and sum rounded to nearest in index order, so the
+// lookup below is the same fp32 computation wherever it runs.
+__device__ void shadow_setup(const Params& p, const ImageInfo& im, ShadowInfo& sd, int l) {
+  const float* si = p.shadow_intr + ((size_t)im.s * kMaxLights + l) * 6;
+  sd.cast[l] = l < im.n_lights && si[0] != 0.0f;
+  if (!sd.cast[l]) return;
+  const float* S = p.shadow_view + ((size_t)im.s * kMaxLights + l) * 12;
+  const float* V = im.V;
+  float Wi[12];
+  for (int i = 0; i < 3; i++) {
+    for (int j = 0; j < 3; j++) Wi[i * 4 + j] = V[j * 4 + i];
+    Wi[i * 4 + 3] = -__fadd_rn(__fadd_rn(__fmul_rn(V[0 * 4 + i], V[3]), __fmul_rn(V[1 * 4 + i], V[7])),
+                               __fmul_rn(V[2 * 4 + i], V[11]));
+  }
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 4; j++) {
+      float r = __fadd_rn(__fadd_rn(__fmul_rn(S[i * 4 + 0], Wi[0 * 4 + j]), __fmul_rn(S[i * 4 + 1], Wi[1 * 4 + j])),
+                          __fmul_rn(S[i * 4 + 2], Wi[2 * 4 + j]));
+      sd.sm[l][j + 4 * i] = j == 3 ? __fadd_rn(r, S[i * 4 + 3]) : r;
+    }
+  for (int k = 0; k < 6; k++) sd.si[l][k] = si[k];
+}
+
+// The shadowed taps (0..9) of light l at the pixel (px, py) of depth `depth`: its G-buffer
+// position, projected into the light's map with round-to-nearest operations in a fixed order,
+// then the 3 x 3 texels around it compared with its depth less the bias.
+__device__ __noinline__ int shadow_taps(const Params& p, const ImageInfo& im, const ShadowInfo& sd, int l, int px,
+                                        int py, float depth) {
+  const float ux = __fdiv_rn(__fsub_rn(__fadd_rn(float(px), 0.5f), im.cx), im.fx);
+  const float uy = -__fdiv_rn(__fsub_rn(__fadd_rn(float(py), 0.5f), im.cy), im.fy);
+  const float P0 = im.ortho ? ux : __fmul_rn(depth, ux), P1 = im.ortho ? uy : __fmul_rn(depth, uy), P2 = -depth;
+  const float* M = sd.sm[l];
+  float q[3];
+  for (int i = 0; i < 3; i++)
+    q[i] = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[i * 4 + 0], P0), __fmul_rn(M[i * 4 + 1], P1)),
+                               __fmul_rn(M[i * 4 + 2], P2)),
+                     M[i * 4 + 3]);
+  const float* si = sd.si[l];
+  const float z = -q[2];
+  if (!(z > si[4])) return 0;
+  const float iw = __fdiv_rn(1.0f, z);
+  const float u = __fadd_rn(si[2], __fmul_rn(si[0], __fmul_rn(q[0], iw)));
+  const float v = __fsub_rn(si[3], __fmul_rn(si[1], __fmul_rn(q[1], iw)));
+  if (!(fabsf(u) < kGuardPx) || !(fabsf(v) < kGuardPx)) return 0;
+  const int i0 = int(floorf(u)), j0 = int(floorf(v)), R = p.shadow_res;
+  const float zb = __fsub_rn(z, si[5]);
+  const float* map = p.shadow_map + ((size_t)im.s * kMaxLights + l) * R * R;
+  int k = 0;
+  for (int b = -1; b <= 1; b++) {
+    const int j = j0 + b;
+    if (j < 0 || j >= R) continue;
+    for (int a = -1; a <= 1; a++) {
+      const int i = i0 + a;
+      if (i < 0 || i >= R) continue;
+      const float d = __ldg(map + (size_t)j * R + i);
+      k += d > 0.0f && zb > d;
+    }
+  }
+  return k;
+}
+
 // The cone of spot light l in view space (its thread, in the spot instances only, after
 // setup_image and before a barrier that precedes the raster phase).
 __device__ void spot_setup(const Params& p, ImageInfo& im, int l) {
@@ -1021,7 +1110,8 @@ struct BoxWalk {
 template <int kF>
 __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scratch& sc, int tile, char* wbase,
                                  const SmemLayout& L, const uint32_t* spans) {
-  constexpr bool kGrade = (kF & kFeatGrade) != 0;
+  constexpr bool kGrade = (kF & kFeatGrade) != 0, kShadow = (kF & kFeatShadow) != 0;
+  constexpr bool kPass = (kF & kFeatShadowPass) != 0;
   const ImageInfo& im = sh.im;
   const int lane = threadIdx.x & 31;
   const int tx = tile % im.ntx, ty = tile / im.ntx;
@@ -1214,8 +1304,13 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
     for (int lx = lane; lx < cw; lx += 32) {
       const int px = x0 + lx;
       const unsigned long long kk = krow[lx];
+      if (kPass) {  // the shadow pass: the map's depth only
+        if (depth_row) __stcs(depth_row + lx, kk == kEmpty ? 0.0f : __uint_as_float(unsigned(kk >> 32)));
+        continue;
+      }
       float rgb[3], depth = 0.0f, n[3] = {0.0f, 0.0f, 0.0f}, P[3] = {0.0f, 0.0f, 0.0f};
       int mat = -1, seg = 0;
+      int word = -1;  // the G-buffer's material word
       if (kk == kEmpty) {
         rgb[0] = im.bg[0];
         rgb[1] = im.bg[1];
@@ -1270,7 +1365,21 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
           P[1] = depth * uy;
           P[2] = -depth;
         }
-        shade<(kF & kFeatLight) != 0>(sh, P, n, mat, rgb);
+        if (kShadow) {
+          const ShadowInfo& sd = *reinterpret_cast<const ShadowInfo*>(spans + kSpanCap);
+          float vis[kMaxLights];
+          word = mat;
+          for (int l = 0; l < kMaxLights; l++) {
+            vis[l] = 1.0f;
+            if (!sd.cast[l]) continue;
+            const int k = shadow_taps(p, im, sd, l, px, py, depth);
+            vis[l] = __fdiv_rn(float(9 - k), 9.0f);
+            word |= k << (8 + 4 * l);
+          }
+          shade<true, true>(sh, P, n, mat, rgb, vis);
+        } else {
+          shade<(kF & kFeatLight) != 0>(sh, P, n, mat, rgb);
+        }
       }
       // consecutive lanes write consecutive pixels: the three byte (or half) stores of a
       // warp fill whole sectors of the row between them
@@ -1309,7 +1418,7 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
         __stcs(p.gbuffer + 3 * N + o, n[0]);
         __stcs(p.gbuffer + 4 * N + o, n[1]);
         __stcs(p.gbuffer + 5 * N + o, n[2]);
-        __stcs(p.gbuffer + 6 * N + o, __int_as_float(mat));
+        __stcs(p.gbuffer + 6 * N + o, __int_as_float(kShadow ? word : mat));
       }
     }
   }
@@ -1334,7 +1443,8 @@ __device__ void raster_phase(const Params& p, CtaShared& sh, const Scratch& sc, 
 }
 
 __device__ inline SmemLayout layout_of(const Params& p) {
-  return smem_layout(blockDim.x, p.tile_w, p.tile_h, p.inst_max, p.max_tiles, p.w_max);
+  return smem_layout(blockDim.x, p.tile_w, p.tile_h, p.inst_max, p.max_tiles, p.w_max,
+                     p.shadow_res > 0 && !p.shadow_pass);
 }
 
 __device__ inline SmemPtrs carve(char* smem, const Params& p, const SmemLayout& L) {
@@ -1406,6 +1516,7 @@ __device__ void raster_claimed(const Params& p, CtaShared& sh, const Scratch& sc
 template <int kF>
 __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
   constexpr bool kGrade = (kF & kFeatGrade) != 0, kTrack = (kF & kFeatTrack) != 0, kLight = (kF & kFeatLight) != 0;
+  constexpr bool kShadow = (kF & kFeatShadow) != 0, kPass = (kF & kFeatShadowPass) != 0;
   extern __shared__ __align__(16) char smem[];
   __shared__ CtaShared sh;
   const SmemLayout L = layout_of(p);
@@ -1416,11 +1527,13 @@ __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
     __syncthreads();
     const int cam = sh.img;
     if (cam >= p.n_cams) break;
-    setup_image(p, cam, sh, sp.mprefix, sp.tprefix, sp.mbegin, true, kTrack);
+    setup_image<kPass>(p, cam, sh, sp.mprefix, sp.tprefix, sp.mbegin, true, kTrack);
     if (kGrade && threadIdx.x == 0 && sh.im.valid) grading_setup(p, sh.im);  // (read after phase G's barrier)
     if (kLight && threadIdx.x < kMaxLights && sh.im.valid) spot_setup(p, sh.im, threadIdx.x);
+    if (kShadow && threadIdx.x < kMaxLights && sh.im.valid)
+      shadow_setup(p, sh.im, *reinterpret_cast<ShadowInfo*>(sp.spans + kSpanCap), threadIdx.x);
     if (sh.im.valid) {
-      geometry_phase<kTrack>(p, sh, sp.mprefix, sp.tprefix, sp.mbegin, reinterpret_cast<WarpG*>(sp.uni), sc);
+      geometry_phase<kTrack, kPass>(p, sh, sp.mprefix, sp.tprefix, sp.mbegin, reinterpret_cast<WarpG*>(sp.uni), sc);
       __syncthreads();
       int* counts = p.max_tiles > kSmemCountTiles ? sc.counts : reinterpret_cast<int*>(sp.uni);
       bin_phase(p, sh, counts, counts + (p.max_tiles + 2), sc);
@@ -1504,10 +1617,12 @@ __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
     if (slot >= 0 && cam >= 0) {
       const Scratch o = slot_scratch(p, slot);
       __threadfence();
-      setup_image(p, cam, sh, sp.mprefix, sp.tprefix, sp.mbegin, false);
+      setup_image<kPass>(p, cam, sh, sp.mprefix, sp.tprefix, sp.mbegin, false);
       if (threadIdx.x == 0) sh.n_big = *reinterpret_cast<volatile int*>(o.header + 3);
       if (kGrade && threadIdx.x == 0) grading_setup(p, sh.im);
       if (kLight && threadIdx.x < kMaxLights) spot_setup(p, sh.im, threadIdx.x);
+      if (kShadow && threadIdx.x < kMaxLights)
+        shadow_setup(p, sh.im, *reinterpret_cast<ShadowInfo*>(sp.spans + kSpanCap), threadIdx.x);
       __syncthreads();
       big_spans(p, sh, o, sp.spans);
       __syncthreads();
@@ -1520,14 +1635,18 @@ __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
 // ---------------------------------------------------------------------------
 // plain: three launches per sample; scratch slot = camera index within the sample
 // ---------------------------------------------------------------------------
+// (in the shadow pass: the map of light blockIdx.x of the sample)
 __device__ inline int plain_cam(const Params& p) {
   const int s = p.plain_sample;
+  if (p.shadow_pass) return blockIdx.x < unsigned(kMaxLights) ? s * kMaxLights + int(blockIdx.x) : -1;
   const int c = p.cam_offset[s] + blockIdx.x;
   return c < p.cam_offset[s + 1] ? c : -1;
 }
 
-template <bool kTrack>
+// kG: bit 0 tracker rows, bit 1 the shadow pass
+template <int kG>
 __global__ void __launch_bounds__(512, 2) plain_geometry_kernel(Params p) {
+  constexpr bool kTrack = (kG & 1) != 0, kPass = (kG & 2) != 0;
   extern __shared__ __align__(16) char smem[];
   __shared__ CtaShared sh;
   const int cam = plain_cam(p);
@@ -1535,12 +1654,12 @@ __global__ void __launch_bounds__(512, 2) plain_geometry_kernel(Params p) {
   const SmemLayout L = layout_of(p);
   SmemPtrs sp = carve(smem, p, L);
   const Scratch sc = slot_scratch(p, blockIdx.x);
-  setup_image(p, cam, sh, sp.mprefix, sp.tprefix, sp.mbegin, true, kTrack);
+  setup_image<kPass>(p, cam, sh, sp.mprefix, sp.tprefix, sp.mbegin, true, kTrack);
   if (!sh.im.valid) {
     if (threadIdx.x == 0) sc.header[2] = -1;
     return;
   }
-  geometry_phase<kTrack>(p, sh, sp.mprefix, sp.tprefix, sp.mbegin, reinterpret_cast<WarpG*>(sp.uni), sc);
+  geometry_phase<kTrack, kPass>(p, sh, sp.mprefix, sp.tprefix, sp.mbegin, reinterpret_cast<WarpG*>(sp.uni), sc);
   __syncthreads();
   if (threadIdx.x == 0) sc.header[2] = sh.n_vis;
 }
@@ -1553,7 +1672,8 @@ __global__ void __launch_bounds__(512, 2) plain_bin_kernel(Params p) {
   const SmemLayout L = layout_of(p);
   SmemPtrs sp = carve(smem, p, L);
   const Scratch sc = slot_scratch(p, blockIdx.x);
-  setup_image(p, cam, sh, sp.mprefix, sp.tprefix, sp.mbegin, false);
+  if (p.shadow_pass) setup_image<true>(p, cam, sh, sp.mprefix, sp.tprefix, sp.mbegin, false);
+  else setup_image(p, cam, sh, sp.mprefix, sp.tprefix, sp.mbegin, false);
   const int nvis = sc.header[2];
   if (nvis < 0) return;
   if (threadIdx.x == 0) sh.n_vis = nvis;
@@ -1566,6 +1686,7 @@ __global__ void __launch_bounds__(512, 2) plain_bin_kernel(Params p) {
 template <int kF>
 __global__ void __launch_bounds__(512, 2) plain_raster_kernel(Params p) {
   constexpr bool kGrade = (kF & kFeatGrade) != 0, kLight = (kF & kFeatLight) != 0;
+  constexpr bool kShadow = (kF & kFeatShadow) != 0, kPass = (kF & kFeatShadowPass) != 0;
   extern __shared__ __align__(16) char smem[];
   __shared__ CtaShared sh;
   const int cam = plain_cam(p);
@@ -1574,10 +1695,12 @@ __global__ void __launch_bounds__(512, 2) plain_raster_kernel(Params p) {
   if (sc.header[2] < 0) return;
   const SmemLayout L = layout_of(p);
   SmemPtrs sp = carve(smem, p, L);
-  setup_image(p, cam, sh, sp.mprefix, sp.tprefix, sp.mbegin, false);
+  setup_image<kPass>(p, cam, sh, sp.mprefix, sp.tprefix, sp.mbegin, false);
   if (threadIdx.x == 0) sh.n_big = sc.header[3];
   if (kGrade && threadIdx.x == 0) grading_setup(p, sh.im);
   if (kLight && threadIdx.x < kMaxLights) spot_setup(p, sh.im, threadIdx.x);
+  if (kShadow && threadIdx.x < kMaxLights)
+    shadow_setup(p, sh.im, *reinterpret_cast<ShadowInfo*>(sp.spans + kSpanCap), threadIdx.x);
   __syncthreads();
   big_spans(p, sh, sc, sp.spans);
   __syncthreads();
@@ -1611,8 +1734,8 @@ int noalloc_scratch(int device, void** ptr, size_t* bytes) {
   return 0;
 }
 
-size_t render_smem_bytes(int threads, int tile_w, int tile_h, int inst_max, int max_tiles, int w_max) {
-  return smem_layout(threads, tile_w, tile_h, inst_max, max_tiles, w_max).total;
+size_t render_smem_bytes(int threads, int tile_w, int tile_h, int inst_max, int max_tiles, int w_max, bool shadows) {
+  return smem_layout(threads, tile_w, tile_h, inst_max, max_tiles, w_max, shadows).total;
 }
 
 namespace {
@@ -1620,7 +1743,7 @@ namespace {
 // larger size is needed, so steady-state launches (and launches inside a stream capture)
 // make no attribute calls.
 std::mutex g_attr_mu;
-size_t g_attr_set[16][64] = {};  // per kernel instance: fused 0-7 (its feature bits), plain 8-14
+size_t g_attr_set[32][64] = {};  // per kernel instance: fused 0-12, plain geometry 13-15, bin 16, raster 20-26
 
 cudaError_t ensure_smem(const void* fn, int which, size_t smem) {
   int dev = 0;
@@ -1637,33 +1760,54 @@ cudaError_t ensure_smem(const void* fn, int which, size_t smem) {
 
 // The feature bits of a launch's batch and outputs.
 static int features(const Params& p) {
-  return (p.grading ? kFeatGrade : 0) | (p.tracker ? kFeatTrack : 0) | (p.light_spot || p.emission ? kFeatLight : 0);
+  if (p.shadow_pass) return kFeatShadowPass;
+  int f = (p.grading ? kFeatGrade : 0) | (p.tracker ? kFeatTrack : 0) | (p.light_spot || p.emission ? kFeatLight : 0);
+  if (p.shadow_res > 0) f |= kFeatShadow | kFeatLight;
+  return f;
 }
 
-// Fused kernel instance for feature bits f (attribute-cache slot f).
+// The fused instances: feature sets 0-7, 12-15 (shadow lookups) and 16 (the shadow pass); slot k of
+// the attribute cache is the k-th of kFusedSets.
+constexpr int kFusedSets[13] = {0, 1, 2, 3, 4, 5, 6, 7, 12, 13, 14, 15, 16};
+static int fused_slot(int f) {
+  for (int k = 0; k < 13; k++)
+    if (kFusedSets[k] == f) return k;
+  return 0;
+}
 static const void* fused_fn(int f) {
-  static const void* const fns[8] = {
-      (const void*)render_fused_kernel<0>, (const void*)render_fused_kernel<1>, (const void*)render_fused_kernel<2>,
-      (const void*)render_fused_kernel<3>, (const void*)render_fused_kernel<4>, (const void*)render_fused_kernel<5>,
-      (const void*)render_fused_kernel<6>, (const void*)render_fused_kernel<7>};
-  return fns[f & 7];
+  static const void* const fns[13] = {
+      (const void*)render_fused_kernel<0>,  (const void*)render_fused_kernel<1>,  (const void*)render_fused_kernel<2>,
+      (const void*)render_fused_kernel<3>,  (const void*)render_fused_kernel<4>,  (const void*)render_fused_kernel<5>,
+      (const void*)render_fused_kernel<6>,  (const void*)render_fused_kernel<7>,  (const void*)render_fused_kernel<12>,
+      (const void*)render_fused_kernel<13>, (const void*)render_fused_kernel<14>, (const void*)render_fused_kernel<15>,
+      (const void*)render_fused_kernel<16>};
+  return fns[fused_slot(f)];
 }
 
-// Plain raster instance for feature bits f (grading and spot matter; slot 11 + index).
+// The plain raster instances (grading, light, shadow lookups, the shadow pass; slots 20 + k).
+constexpr int kPlainRasterSets[7] = {0, 1, 4, 5, 12, 13, 16};
+static int plain_raster_slot(int f) {
+  const int g = f & (kFeatGrade | kFeatLight | kFeatShadow | kFeatShadowPass);
+  for (int k = 0; k < 7; k++)
+    if (kPlainRasterSets[k] == g) return k;
+  return 0;
+}
 static const void* plain_raster_fn(int f) {
-  static const void* const fns[4] = {(const void*)plain_raster_kernel<0>, (const void*)plain_raster_kernel<kFeatGrade>,
-                                     (const void*)plain_raster_kernel<kFeatLight>,
-                                     (const void*)plain_raster_kernel<kFeatGrade | kFeatLight>};
-  return fns[((f & kFeatGrade) ? 1 : 0) | ((f & kFeatLight) ? 2 : 0)];
+  static const void* const fns[7] = {
+      (const void*)plain_raster_kernel<0>,  (const void*)plain_raster_kernel<1>,  (const void*)plain_raster_kernel<4>,
+      (const void*)plain_raster_kernel<5>,  (const void*)plain_raster_kernel<12>, (const void*)plain_raster_kernel<13>,
+      (const void*)plain_raster_kernel<16>};
+  return fns[plain_raster_slot(f)];
 }
 
 int render_max_ctas_per_sm(int threads, size_t smem) {
   int n = 0;
   n = 1 << 30;  // every instance: the same launch bounds and shared memory; the least of their fits
-  for (int f = 0; f < 8; f++) {
+  for (int k = 0; k < 13; k++) {
     int m = 0;
-    if (ensure_smem(fused_fn(f), f, smem) != cudaSuccess) return -1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, fused_fn(f), threads, smem) != cudaSuccess) return -1;
+    if (ensure_smem(fused_fn(kFusedSets[k]), k, smem) != cudaSuccess) return -1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, fused_fn(kFusedSets[k]), threads, smem) != cudaSuccess)
+      return -1;
     n = m < n ? m : n;
   }
   return n;
@@ -1672,11 +1816,12 @@ int render_max_ctas_per_sm(int threads, size_t smem) {
 int launch_render(const Params& p, int mode, int threads, int n_ctas, int max_cams_per_sample, void* stream,
                   char* err, size_t errlen) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const size_t smem = render_smem_bytes(threads, p.tile_w, p.tile_h, p.inst_max, p.max_tiles, p.w_max);
+  const size_t smem = render_smem_bytes(threads, p.tile_w, p.tile_h, p.inst_max, p.max_tiles, p.w_max,
+                                       p.shadow_res > 0 && !p.shadow_pass);
   cudaError_t e = cudaSuccess;
   const int f = features(p);
   if (mode == 0) {
-    e = ensure_smem(fused_fn(f), f, smem);
+    e = ensure_smem(fused_fn(f), fused_slot(f), smem);
     if (e == cudaSuccess) {  // slot headers (claim words, counters) start at zero
       const SlotLayout SL = slot_layout(p.t_max, p.max_tiles);
       e = cudaMemset2DAsync(p.scratch + SL.header, p.slot_bytes, 0, 64, (size_t)n_ctas, st);
@@ -1690,29 +1835,40 @@ int launch_render(const Params& p, int mode, int threads, int n_ctas, int max_ca
         case 4: render_fused_kernel<4><<<n_ctas, threads, smem, st>>>(p); break;
         case 5: render_fused_kernel<5><<<n_ctas, threads, smem, st>>>(p); break;
         case 6: render_fused_kernel<6><<<n_ctas, threads, smem, st>>>(p); break;
-        default: render_fused_kernel<7><<<n_ctas, threads, smem, st>>>(p); break;
+        case 7: render_fused_kernel<7><<<n_ctas, threads, smem, st>>>(p); break;
+        case 12: render_fused_kernel<12><<<n_ctas, threads, smem, st>>>(p); break;
+        case 13: render_fused_kernel<13><<<n_ctas, threads, smem, st>>>(p); break;
+        case 14: render_fused_kernel<14><<<n_ctas, threads, smem, st>>>(p); break;
+        case 15: render_fused_kernel<15><<<n_ctas, threads, smem, st>>>(p); break;
+        default: render_fused_kernel<16><<<n_ctas, threads, smem, st>>>(p); break;
       }
       e = cudaGetLastError();
     }
   } else {
-    const bool tracked = (f & kFeatTrack) != 0;
-    const int rf = f & (kFeatGrade | kFeatLight);
-    const void* ks[3] = {tracked ? (const void*)plain_geometry_kernel<true> : (const void*)plain_geometry_kernel<false>,
-                         (const void*)plain_bin_kernel, plain_raster_fn(f)};
-    const int which[3] = {tracked ? 9 : 8, 10, 11 + ((rf & kFeatGrade) ? 1 : 0) + ((rf & kFeatLight) ? 2 : 0)};
+    const int g = ((f & kFeatTrack) ? 1 : 0) | ((f & kFeatShadowPass) ? 2 : 0);
+    const void* geo = g == 1 ? (const void*)plain_geometry_kernel<1>
+                             : (g == 2 ? (const void*)plain_geometry_kernel<2> : (const void*)plain_geometry_kernel<0>);
+    const void* ks[3] = {geo, (const void*)plain_bin_kernel, plain_raster_fn(f)};
+    const int which[3] = {13 + g, 16, 20 + plain_raster_slot(f)};
     for (int k = 0; k < 3 && e == cudaSuccess; k++) e = ensure_smem(ks[k], which[k], smem);
     Params q = p;
+    const dim3 grid(max_cams_per_sample, kPlainRasterSplit);
     for (int s = 0; s < p.n_samples && e == cudaSuccess; s++) {
       q.plain_sample = s;
-      if (tracked) plain_geometry_kernel<true><<<max_cams_per_sample, threads, smem, st>>>(q);
-      else plain_geometry_kernel<false><<<max_cams_per_sample, threads, smem, st>>>(q);
+      switch (g) {
+        case 1: plain_geometry_kernel<1><<<max_cams_per_sample, threads, smem, st>>>(q); break;
+        case 2: plain_geometry_kernel<2><<<max_cams_per_sample, threads, smem, st>>>(q); break;
+        default: plain_geometry_kernel<0><<<max_cams_per_sample, threads, smem, st>>>(q); break;
+      }
       plain_bin_kernel<<<max_cams_per_sample, threads, smem, st>>>(q);
-      const dim3 grid(max_cams_per_sample, kPlainRasterSplit);
-      switch (rf) {
+      switch (kPlainRasterSets[plain_raster_slot(f)]) {
         case 0: plain_raster_kernel<0><<<grid, threads, smem, st>>>(q); break;
-        case kFeatGrade: plain_raster_kernel<kFeatGrade><<<grid, threads, smem, st>>>(q); break;
-        case kFeatLight: plain_raster_kernel<kFeatLight><<<grid, threads, smem, st>>>(q); break;
-        default: plain_raster_kernel<kFeatGrade | kFeatLight><<<grid, threads, smem, st>>>(q); break;
+        case 1: plain_raster_kernel<1><<<grid, threads, smem, st>>>(q); break;
+        case 4: plain_raster_kernel<4><<<grid, threads, smem, st>>>(q); break;
+        case 5: plain_raster_kernel<5><<<grid, threads, smem, st>>>(q); break;
+        case 12: plain_raster_kernel<12><<<grid, threads, smem, st>>>(q); break;
+        case 13: plain_raster_kernel<13><<<grid, threads, smem, st>>>(q); break;
+        default: plain_raster_kernel<16><<<grid, threads, smem, st>>>(q); break;
       }
       e = cudaGetLastError();
     }

@@ -38,18 +38,19 @@ class orrb_mesh_desc(C.Structure):
 class orrb_batch_shape(C.Structure):
     _fields_ = [("n_samples", C.c_int32), ("n_cams", C.c_int32), ("max_tris_per_sample", C.c_int32),
                 ("max_inst_per_sample", C.c_int32), ("max_cams_per_sample", C.c_int32), ("max_width", C.c_int32),
-                ("max_height", C.c_int32), ("total_pixels", C.c_int64)]
+                ("max_height", C.c_int32), ("total_pixels", C.c_int64), ("shadow_res", C.c_int32)]
 
 
 class orrb_batch_desc(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in (
         "inst_offset", "inst_mesh", "inst_pose", "inst_seg", "inst_mat_base", "cam_offset", "cam_sample", "cam_view",
         "cam_intr", "cam_wh", "img_offset", "light", "light_meta", "material", "exposure_ev", "ambient", "background", "grading",
-        "light_spot", "emission")]
+        "light_spot", "emission", "shadow_view", "shadow_intr")]
 
 
 class orrb_outputs(C.Structure):
-    _fields_ = [(n, C.c_void_p) for n in ("rgb", "depth", "normal", "seg", "rgb_linear", "gbuffer", "tracker")]
+    _fields_ = [(n, C.c_void_p) for n in ("rgb", "depth", "normal", "seg", "rgb_linear", "gbuffer", "tracker",
+                                          "shadow_map")]
 
 
 class orrb_config(C.Structure):

@@ -24,7 +24,8 @@ _DTYPES = dict(inst_offset=torch.int32, inst_mesh=torch.int32, inst_pose=torch.f
                inst_mat_base=torch.int16, cam_offset=torch.int32, cam_sample=torch.int32, cam_view=torch.float32,
                cam_intr=torch.float32, cam_wh=torch.int32, img_offset=torch.int64, light=torch.float32,
                light_meta=torch.int32, material=torch.float32, exposure_ev=torch.float32, ambient=torch.float32,
-               background=torch.float32, grading=torch.float32, light_spot=torch.float32, emission=torch.float32)
+               background=torch.float32, grading=torch.float32, light_spot=torch.float32, emission=torch.float32,
+               shadow_view=torch.float32, shadow_intr=torch.float32)
 _NP = {torch.int32: np.int32, torch.float32: np.float32, torch.uint8: np.uint8, torch.int16: np.int16,
        torch.int64: np.int64}
 
@@ -39,7 +40,8 @@ def batch_shape(batch) -> L.orrb_batch_shape:
         max_cams_per_sample=int(np.diff(batch.cam_offset).max()) if batch.n_samples else 0,
         max_width=int(batch.cam_wh[:, 0].max()) if batch.n_cams else 1,
         max_height=int(batch.cam_wh[:, 1].max()) if batch.n_cams else 1,
-        total_pixels=batch.total_pixels)
+        total_pixels=batch.total_pixels,
+        shadow_res=int(getattr(batch, "shadow_res", 0) or 0) if getattr(batch, "shadow_view", None) is not None else 0)
 
 
 @dataclass
@@ -50,13 +52,19 @@ class DeviceBatch:
     desc: L.orrb_batch_desc = field(init=False)
 
     def __post_init__(self):
-        # an optional array (grading, light_spot, emission) that is absent or None passes a null pointer
+        # an optional array (grading, light_spot, emission, shadow cameras) that is absent or None passes
+        # a null pointer
         self.desc = L.orrb_batch_desc(*[self.tensors[n].data_ptr() if self.tensors.get(n) is not None else None
                                         for n in _DESC_FIELDS])
 
     @property
     def total_pixels(self) -> int:
         return int(self.shape.total_pixels)
+
+    @property
+    def has_shadows(self) -> bool:
+        return int(self.shape.shadow_res) > 0 and self.tensors.get("shadow_view") is not None \
+            and self.tensors.get("shadow_intr") is not None
 
     def with_params(self, **kw) -> "DeviceBatch":
         t = dict(self.tensors)
@@ -145,18 +153,27 @@ class Renderer:
             out["gbuffer"] = torch.empty((L.ORRB_GBUFFER_PLANES, n_pixels), dtype=torch.float32, device=d)
         return out
 
+    def alloc_shadow_maps(self, db: DeviceBatch) -> torch.Tensor:
+        """The shadow-map output [n_samples, 4, R, R] of a batch with shadows."""
+        R = int(db.shape.shadow_res)
+        return torch.empty((int(db.shape.n_samples), L.ORRB_MAX_LIGHTS, R, R), dtype=torch.float32, device=self.device)
+
     def render(self, db: DeviceBatch, out=None, cfg: Optional[L.orrb_config] = None, rgb_linear: bool = False,
                gbuffer: bool = False, stream=None, workspace: Optional[torch.Tensor] = None, tracker: bool = False):
-        """Render `db`; `tracker` adds the per (camera, instance) rows [n_cams, max instances, 8]."""
+        """Render `db`; `tracker` adds the per (camera, instance) rows [n_cams, max instances, 8]; a batch
+        with shadows also writes (and returns) its shadow maps as "shadow_map"."""
         cfg = cfg or config()
         if out is None:
             out = self.alloc_outputs(db.total_pixels, rgb_linear, gbuffer)
             if tracker:
                 out["tracker"] = torch.empty((int(db.shape.n_cams), int(db.shape.max_inst_per_sample), 8),
                                              dtype=torch.int32, device=self.device)
+        if db.has_shadows and "shadow_map" not in out:
+            out["shadow_map"] = self.alloc_shadow_maps(db)
         ws = workspace if workspace is not None else self.workspace(db.shape, cfg)
         outs = L.orrb_outputs(*[out[k].data_ptr() if k in out else None
-                                for k in ("rgb", "depth", "normal", "seg", "rgb_linear", "gbuffer", "tracker")])
+                                for k in ("rgb", "depth", "normal", "seg", "rgb_linear", "gbuffer", "tracker",
+                                          "shadow_map")])
         st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
         L.orrb_render_batch(self.ctx, db.shape, db.desc, outs, cfg, ws.data_ptr(), ws.numel(), st)
         self._last_ws = ws

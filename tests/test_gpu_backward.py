@@ -134,3 +134,18 @@ def test_spot_and_emission_adjoint_matches_oracle(renderer, oracle):
     rgb = ShadeFn.apply(mat, db.tensors["light"], db.tensors["exposure_ev"], renderer, db, emission)
     ((rgb - torch.from_numpy(target).float().cuda()) ** 2)[out["gbuffer"][6].view(torch.int32) >= 0].sum().backward()
     assert torch.allclose(emission.grad.cpu(), torch.from_numpy(dem), rtol=1e-4, atol=1e-6)
+
+
+def test_shadowed_adjoint_matches_oracle(renderer, oracle):
+    """With shadow maps the G-buffer's material words carry the shadowed taps, which the adjoint
+    holds fixed: every gradient against the oracle's fp64 adjoint of the same G-buffer."""
+    b = sg.benchmark_batch(8, np.arange(8), res=96, grading=False, shadow_res=128)
+    db, out, gb, target, d_rgb = setup(renderer, oracle, b)
+    assert (gb[2][gb[2] >= 0] > 0xff).any()
+    dm, dl, de, dem = [t.cpu().numpy() for t in
+                       renderer.shade_backward(db, out["gbuffer"], torch.from_numpy(d_rgb).cuda(), emission=True)]
+    rdm, rdl, rde, rdem = oracle.shade_backward_f64(b, *gb, d_rgb.astype(np.float64), return_emission=True)
+    assert rel_err(dm, rdm).max() < REL
+    assert rel_err(dl[:, :3], rdl[:, :3]).max() < REL
+    assert rel_err(de, rde).max() < REL
+    assert rel_err(dem, rdem).max() < REL

@@ -388,3 +388,31 @@ def test_lights_that_light_nothing_are_flagged(hand_renderer, oracle):
         torch.cuda.synchronize()
         assert bool(hand_renderer.status() & 0x10) == flagged
         compare(to_numpy(out), oracle.render(bad, debug=True), "dark lights")
+
+
+@pytest.mark.parametrize("mode", [L.ORRB_MODE_FUSED, L.ORRB_MODE_PLAIN])
+def test_shadow_maps_and_lookups_match_oracle(hand_renderer, oracle, mode):
+    """The benchmark-like scene with shadow maps: every map of a casting light bit-identical to the
+    oracle's (the same rasterisation, back faces), every G-buffer material word (slot and shadowed
+    taps per light) identical, and the channels within the contract; maps of lights that cast
+    none are left untouched."""
+    b = sg.benchmark_batch(31, np.arange(8), res=96, shadow_res=128)
+    b = b.with_params(light_meta=b.light_meta.copy())
+    b.light_meta[5, 0] = 2                              # a sample with one light fewer
+    o = oracle.render(b, debug=True, gbuffer=True)
+    r = hand_renderer
+    db = r.upload(b)
+    out = r.render(db, cfg=config(mode=mode), rgb_linear=True, gbuffer=True)
+    out["shadow_map"].fill_(-1.0)
+    out = r.render(db, cfg=config(mode=mode), out=out)
+    torch.cuda.synchronize()
+    assert r.status() == 0
+    g = to_numpy(out)
+    cast = np.arange(4)[None, :] < b.light_meta[:, :1]
+    np.testing.assert_array_equal(g["shadow_map"][cast], o["shadow_map"][cast])
+    assert (g["shadow_map"][~cast] == -1.0).all()
+    assert (o["shadow_map"][cast] > 0).mean() > 0.005
+    np.testing.assert_array_equal(g["gbuffer"][6].view(np.int32), o["gb_mat"])
+    k = (o["gb_mat"][o["gb_mat"] >= 0] >> 8) & 0xfff
+    assert (k > 0).mean() > 0.05                        # shadows fall on a good share of the pixels
+    compare(g, o, "shadows")
