@@ -59,6 +59,9 @@ constexpr int kFeatTrack = 2;  // tracker rows
 constexpr int kFeatLight = 4;  // a cone table (spot lights may occur) or material emission
 constexpr int kFeatShadow = 8;        // shadow-map lookups in the shading (implies kFeatLight)
 constexpr int kFeatShadowPass = 16;   // the depth-only pass that renders the shadow maps
+// (9 - k) / 9 for k shadowed taps of 9, each the correctly rounded fp32 quotient
+__constant__ float kPcfFactor[10] = {1.0f,        0.8888889f, 0.7777778f, 0.6666667f, 0.5555556f,
+                                     0.44444445f, 0.33333334f, 0.22222222f, 0.11111111f, 0.0f};
 
 // The PCG hash (Jarzynski and Olano, "Hash Functions for GPU Rendering", JCGT 2020): one LCG
 // step, a random xorshift and a multiply.
@@ -1003,42 +1006,53 @@ __device__ void shadow_setup(const Params& p, const ImageInfo& im, ShadowInfo& s
   for (int k = 0; k < 6; k++) sd.si[l][k] = si[k];
 }
 
-// The shadowed taps (0..9) of light l at the pixel (px, py) of depth `depth`: its G-buffer
-// position, projected into the light's map with round-to-nearest operations in a fixed order,
-// then the 3 x 3 texels around it compared with its depth less the bias.
-__device__ __noinline__ int shadow_taps(const Params& p, const ImageInfo& im, const ShadowInfo& sd, int l, int px,
-                                        int py, float depth) {
+// The shadow factors of the casting lights at the pixel (px, py) of depth `depth`, and the
+// G-buffer word (slot | shadowed taps of light l << (8 + 4l)).  The pixel's G-buffer position is
+// projected into each light's map with round-to-nearest operations in a fixed order (the
+// reciprocal is correctly rounded, so it equals 1 / z), then the 3 x 3 texels around it are
+// compared with its depth less the bias; the factor (9 - k) / 9 comes from a table.
+__device__ __forceinline__ int shadow_lookup(const Params& p, const ImageInfo& im, const ShadowInfo& sd, int px,
+                                             int py, float depth, int mat, float vis[kMaxLights]) {
   const float ux = __fdiv_rn(__fsub_rn(__fadd_rn(float(px), 0.5f), im.cx), im.fx);
   const float uy = -__fdiv_rn(__fsub_rn(__fadd_rn(float(py), 0.5f), im.cy), im.fy);
   const float P0 = im.ortho ? ux : __fmul_rn(depth, ux), P1 = im.ortho ? uy : __fmul_rn(depth, uy), P2 = -depth;
-  const float* M = sd.sm[l];
-  float q[3];
-  for (int i = 0; i < 3; i++)
-    q[i] = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[i * 4 + 0], P0), __fmul_rn(M[i * 4 + 1], P1)),
-                               __fmul_rn(M[i * 4 + 2], P2)),
-                     M[i * 4 + 3]);
-  const float* si = sd.si[l];
-  const float z = -q[2];
-  if (!(z > si[4])) return 0;
-  const float iw = __fdiv_rn(1.0f, z);
-  const float u = __fadd_rn(si[2], __fmul_rn(si[0], __fmul_rn(q[0], iw)));
-  const float v = __fsub_rn(si[3], __fmul_rn(si[1], __fmul_rn(q[1], iw)));
-  if (!(fabsf(u) < kGuardPx) || !(fabsf(v) < kGuardPx)) return 0;
-  const int i0 = int(floorf(u)), j0 = int(floorf(v)), R = p.shadow_res;
-  const float zb = __fsub_rn(z, si[5]);
-  const float* map = p.shadow_map + ((size_t)im.s * kMaxLights + l) * R * R;
-  int k = 0;
-  for (int b = -1; b <= 1; b++) {
-    const int j = j0 + b;
-    if (j < 0 || j >= R) continue;
-    for (int a = -1; a <= 1; a++) {
-      const int i = i0 + a;
-      if (i < 0 || i >= R) continue;
-      const float d = __ldg(map + (size_t)j * R + i);
-      k += d > 0.0f && zb > d;
+  const int R = p.shadow_res;
+  int word = mat;
+#pragma unroll
+  for (int l = 0; l < kMaxLights; l++) {
+    vis[l] = 1.0f;
+    if (!sd.cast[l]) continue;
+    const float* M = sd.sm[l];
+    const float* si = sd.si[l];
+    const float q2 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[8], P0), __fmul_rn(M[9], P1)), __fmul_rn(M[10], P2)), M[11]);
+    const float z = -q2;
+    if (!(z > si[4])) continue;
+    const float q0 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[0], P0), __fmul_rn(M[1], P1)), __fmul_rn(M[2], P2)), M[3]);
+    const float q1 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[4], P0), __fmul_rn(M[5], P1)), __fmul_rn(M[6], P2)), M[7]);
+    const float iw = __frcp_rn(z);
+    const float u = __fadd_rn(si[2], __fmul_rn(si[0], __fmul_rn(q0, iw)));
+    const float v = __fsub_rn(si[3], __fmul_rn(si[1], __fmul_rn(q1, iw)));
+    if (!(fabsf(u) < kGuardPx) || !(fabsf(v) < kGuardPx)) continue;
+    const int i0 = int(floorf(u)), j0 = int(floorf(v));
+    const float zb = __fsub_rn(z, si[5]);
+    const float* map = p.shadow_map + ((size_t)im.s * kMaxLights + l) * R * R;
+    int k = 0;
+#pragma unroll
+    for (int b = -1; b <= 1; b++) {
+      const int j = j0 + b;
+      if (j < 0 || j >= R) continue;
+#pragma unroll
+      for (int a = -1; a <= 1; a++) {
+        const int i = i0 + a;
+        if (i < 0 || i >= R) continue;
+        const float d = __ldg(map + (size_t)j * R + i);
+        k += d > 0.0f && zb > d;
+      }
     }
+    vis[l] = kPcfFactor[k];
+    word |= k << (8 + 4 * l);
   }
-  return k;
+  return word;
 }
 
 // The cone of spot light l in view space (its thread, in the spot instances only, after
@@ -1368,14 +1382,7 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
         if (kShadow) {
           const ShadowInfo& sd = *reinterpret_cast<const ShadowInfo*>(spans + kSpanCap);
           float vis[kMaxLights];
-          word = mat;
-          for (int l = 0; l < kMaxLights; l++) {
-            vis[l] = 1.0f;
-            if (!sd.cast[l]) continue;
-            const int k = shadow_taps(p, im, sd, l, px, py, depth);
-            vis[l] = __fdiv_rn(float(9 - k), 9.0f);
-            word |= k << (8 + 4 * l);
-          }
+          word = shadow_lookup(p, im, sd, px, py, depth, mat, vis);
           shade<true, true>(sh, P, n, mat, rgb, vis);
         } else {
           shade<(kF & kFeatLight) != 0>(sh, P, n, mat, rgb);
