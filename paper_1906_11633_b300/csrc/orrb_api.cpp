@@ -213,6 +213,7 @@ int max_tiles_of(const orrb_batch_shape& s, const orrb_config& c) {
 struct Plan {
   int n_slots, ctas_per_sm, max_tiles;
   size_t slot_bytes, smem, total;
+  size_t nb_offset;  // the shadow maps' neighbourhood table (after the slots), 0 without shadows
 };
 
 orrb_status plan(orrb_ctx* ctx, const orrb_batch_shape& s, const orrb_config& c, Plan* P) {
@@ -238,6 +239,11 @@ orrb_status plan(orrb_ctx* ctx, const orrb_batch_shape& s, const orrb_config& c,
     P->n_slots = std::max(std::max(s.max_cams_per_sample, 1), s.shadow_res > 0 ? kMaxLights : 1);
   }
   P->total = 256 + (size_t)P->n_slots * P->slot_bytes;
+  P->nb_offset = 0;
+  if (s.shadow_res > 0) {
+    P->nb_offset = align256(P->total);
+    P->total = P->nb_offset + (size_t)s.n_samples * kMaxLights * s.shadow_res * s.shadow_res * sizeof(float2);
+  }
   return ORRB_OK;
 }
 
@@ -308,6 +314,8 @@ orrb_status enqueue_render(orrb_ctx* ctx, Params& p, const orrb_batch_shape& s, 
     const int n_ctas = mode == ORRB_MODE_FUSED ? std::min(n_slots, std::max(q.n_cams, 1)) : 0;
     q.n_slots = n_ctas;
     if (launch_render(q, mode, threads, n_ctas, kMaxLights, stream, err, sizeof(err)))
+      return fail(ctx, ORRB_ERR_CUDA, "%s", err);
+    if (p.shadow_nb && launch_shadow_neighbourhoods(q, stream, err, sizeof(err)))
       return fail(ctx, ORRB_ERR_CUDA, "%s", err);
     // the camera launch's image queue starts again at zero (the status word carries over)
     cudaError_t e = cudaMemsetAsync(ws + 4, 0, 8, st);
@@ -489,6 +497,7 @@ orrb_status orrb_render_batch(orrb_ctx* ctx, const orrb_batch_shape* shape, cons
   p.scratch = ws + 256;
   p.slot_bytes = P.slot_bytes;
   p.n_slots = P.n_slots;
+  p.shadow_nb = p.shadow_res > 0 ? reinterpret_cast<float2*>(ws + P.nb_offset) : nullptr;
   p.plain_sample = -1;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(ws, 0, 16, s);

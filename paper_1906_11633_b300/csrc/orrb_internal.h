@@ -76,6 +76,8 @@ struct Params {
   const float* shadow_view;  // [n_samples][4][12] (with shadow_res > 0)
   const float* shadow_intr;  // [n_samples][4][6]
   float* shadow_map;         // [n_samples][4][R][R]: written by the shadow pass, read by the shading
+  float2* shadow_nb;         // [n_samples][4][R][R] or null: per texel over its 3 x 3 neighbourhood, the least
+                             // depth > 0 (+inf if none) and, if all nine are inside and > 0, the largest (+inf)
   int32_t shadow_res;        // R, 0 without shadows
   int32_t shadow_pass;       // this launch renders the shadow maps (images: sample * 4 + light)
   // outputs (device, any may be null)
@@ -138,6 +140,7 @@ ORRB_HD inline SlotLayout slot_layout(int t_max, int max_tiles) {
 // Host entry points implemented in the .cu files.
 int launch_render(const Params& p, int mode, int threads, int ctas_per_sm, int max_cams_per_sample,
                   void* stream, char* err, size_t errlen);
+int launch_shadow_neighbourhoods(const Params& p, void* stream, char* err, size_t errlen);
 size_t render_smem_bytes(int threads, int tile_w, int tile_h, int inst_max, int max_tiles, int w_max, bool shadows);
 
 struct BackwardParams {

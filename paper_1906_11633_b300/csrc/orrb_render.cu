@@ -1035,19 +1035,30 @@ __device__ __forceinline__ int shadow_lookup(const Params& p, const ImageInfo& i
     if (!(fabsf(u) < kGuardPx) || !(fabsf(v) < kGuardPx)) continue;
     const int i0 = int(floorf(u)), j0 = int(floorf(v));
     const float zb = __fsub_rn(z, si[5]);
-    const float* map = p.shadow_map + ((size_t)im.s * kMaxLights + l) * R * R;
-    int k = 0;
+    const size_t m0 = ((size_t)im.s * kMaxLights + l) * R * R;
+    int k = -1;
+    if (p.shadow_nb && i0 >= 0 && j0 >= 0 && i0 < R && j0 < R) {  // one load settles lit and umbra points
+      const float2 e = __ldg(p.shadow_nb + m0 + (size_t)j0 * R + i0);
+      if (!(zb > e.x)) k = 0;  // no occupied tap is nearer than the point
+      else if (zb > e.y) k = 9;  // all nine occupied and nearer
+    }
+    if (k == 0) continue;
+    if (k < 0) {
+    k = 0;
+    const float* map = p.shadow_map + m0;
+    const bool col[3] = {i0 - 1 >= 0 && i0 - 1 < R, i0 >= 0 && i0 < R, i0 + 1 >= 0 && i0 + 1 < R};
 #pragma unroll
     for (int b = -1; b <= 1; b++) {
       const int j = j0 + b;
       if (j < 0 || j >= R) continue;
+      const float* row = map + j * R + i0;  // (within a map, offsets fit 32 bits)
 #pragma unroll
       for (int a = -1; a <= 1; a++) {
-        const int i = i0 + a;
-        if (i < 0 || i >= R) continue;
-        const float d = __ldg(map + (size_t)j * R + i);
+        if (!col[a + 1]) continue;
+        const float d = __ldg(row + a);
         k += d > 0.0f && zb > d;
       }
+    }
     }
     vis[l] = kPcfFactor[k];
     word |= k << (8 + 4 * l);
@@ -1714,6 +1725,44 @@ __global__ void __launch_bounds__(512, 2) plain_raster_kernel(Params p) {
   raster_phase<kF>(p, sh, sc, sp, L, blockIdx.y, gridDim.y);
 }
 
+// The neighbourhood table of the shadow maps (after the shadow pass, before the camera launch):
+// per texel over its 3 x 3 neighbourhood (texels outside the map count as empty), the least
+// depth > 0 (+inf if none) and, when all nine are inside and occupied, the largest (+inf
+// otherwise).  A point with depth-less-bias zb is then unshadowed by every tap when zb <= the
+// least, and shadowed by all nine when zb > the largest; only the others count taps.
+// One block per map row (blockIdx.x) and map (blockIdx.y, striding by gridDim.y); threads
+// stride along the row.
+__global__ void __launch_bounds__(256) shadow_neighbourhood_kernel(Params p) {
+  const int R = p.shadow_res, y = blockIdx.x, n_maps = p.n_samples * kMaxLights;
+  const float inf = __int_as_float(0x7f800000);
+  for (int m = blockIdx.y; m < n_maps; m += gridDim.y) {
+    if (m % kMaxLights >= p.light_meta[(m / kMaxLights) * 2]) continue;  // no such light: no map
+    const float* map = p.shadow_map + (size_t)m * R * R;
+    const float* rows[3] = {map + (y > 0 ? y - 1 : 0) * R, map + y * R, map + (y + 1 < R ? y + 1 : y) * R};
+    const bool row_in[3] = {y > 0, true, y + 1 < R};
+    float2* out = p.shadow_nb + (size_t)m * R * R + (size_t)y * R;
+    for (int x = threadIdx.x; x < R; x += blockDim.x) {
+      float lo = inf, hi = 0.0f;
+      bool full = row_in[0] && row_in[2] && x > 0 && x + 1 < R;
+      for (int b = 0; b < 3; b++) {
+        if (!row_in[b]) continue;
+        for (int a = -1; a <= 1; a++) {
+          const int xx = x + a;
+          if (xx < 0 || xx >= R) continue;
+          const float d = __ldg(rows[b] + xx);
+          if (d > 0.0f) {
+            lo = fminf(lo, d);
+            hi = fmaxf(hi, d);
+          } else {
+            full = false;
+          }
+        }
+      }
+      out[x] = make_float2(lo, full ? hi : inf);
+    }
+  }
+}
+
 // Scratch of orrb_render_batch_noalloc: a file-scope device array, so that
 // entry point never allocates.  Host code must not pass the symbol itself to
 // a kernel (on the host it names a stand-in, not device memory); it passes
@@ -1738,6 +1787,18 @@ int noalloc_scratch(int device, void** ptr, size_t* bytes) {
   }
   *ptr = cache[device];
   *bytes = ORRB_NOALLOC_SCRATCH_BYTES;
+  return 0;
+}
+
+int launch_shadow_neighbourhoods(const Params& p, void* stream, char* err, size_t errlen) {
+  const int n_maps = p.n_samples * kMaxLights;
+  const dim3 grid(unsigned(p.shadow_res), unsigned(n_maps < 65535 ? n_maps : 65535));
+  shadow_neighbourhood_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(p);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    snprintf(err, errlen, "shadow neighbourhood launch failed: %s", cudaGetErrorString(e));
+    return 1;
+  }
   return 0;
 }
 

@@ -67,3 +67,30 @@ def test_noalloc_rejects_shapes_beyond_its_static_scratch():
                                     torch.cuda.current_stream().cuda_stream)
     assert e.value.status == 2
     assert "static scratch" in str(e.value)
+
+
+def test_noalloc_shadows_count_every_tap_like_the_shortcut():
+    """With shadows the workspace entry point settles lit and umbra points from the maps'
+    neighbourhood table; the allocation-free one has no room for it and counts all nine taps every
+    time.  Maps, G-buffer words (the tap counts) and channels must agree exactly."""
+    r = Renderer(sg.hand_meshes())
+    stream = torch.cuda.current_stream().cuda_stream
+    status = torch.full((1,), 0xFF, dtype=torch.int32, device="cuda")
+    b = sg.benchmark_batch(14, np.arange(4), res=96, shadow_res=128)
+    db = r.upload(b)
+    ref = to_numpy(r.render(db, rgb_linear=True, gbuffer=True))
+    out = r.alloc_outputs(db.total_pixels, rgb_linear=True, gbuffer=True)
+    out["shadow_map"] = r.alloc_shadow_maps(db)
+    outs = _outs(out)
+    outs.shadow_map = out["shadow_map"].data_ptr()
+    L.orrb_render_batch_noalloc(r.ctx, db.shape, db.desc, outs, config(), status.data_ptr(), stream)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    got = to_numpy(out)
+    cast = np.arange(4)[None, :] < b.light_meta[:, :1]
+    np.testing.assert_array_equal(got["shadow_map"][cast], ref["shadow_map"][cast])
+    words = got["gbuffer"][6].view(np.int32)
+    np.testing.assert_array_equal(words, ref["gbuffer"][6].view(np.int32))
+    assert (words[words >= 0] > 0xff).mean() > 0.05
+    for k in ("rgb", "rgb_linear", "depth", "seg", "normal"):
+        np.testing.assert_array_equal(got[k], ref[k], err_msg=k)
