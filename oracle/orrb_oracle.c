@@ -31,8 +31,11 @@
  *      float and summed left to right (orthographic: (w0*d0+w1*d1+w2*d2)/A).
  *   8  the nearest fragment wins by (depth, key) ascending, key = 2*prim+sub,
  *      prim = triangle index in the sample's concatenated triangle list.
- *   9  G-buffer: P = depth*((x+1/2-cx)/fx, -(y+1/2-cy)/fy, -1); normal =
- *      sum_i (w_i*iw_i) n_i normalised; material = base + tri_mat; seg id.
+ *   9  G-buffer: P = (depth ux, depth uy, -depth) with ux = ((x + 1/2) - cx)
+ *      * (1/fx), uy = -(((y + 1/2) - cy) * (1/fy)), each operation rounded
+ *      separately, 1/fx the correctly rounded reciprocal (orthographic: (ux,
+ *      uy, -depth)); normal = sum_i (w_i*iw_i) n_i normalised; material =
+ *      base + tri_mat; seg id.
  *  10  Blinn-Phong over the sample's lights, inverse-square falloff for
  *      point and spot lights, white specular, plus (ambient + emission) *
  *      albedo, all times 2^EV.  Emission e is a scalar per material, the
@@ -81,8 +84,7 @@
  *      step 5, so front faces are culled -- and 0 where there is none.
  *  16  shadow lookup in step 10: for a camera pixel with surface and each
  *      casting light, in fp32 with every operation rounded separately:
- *        P as in step 9 (ux = ((x + 1/2) - cx) / fx, uy = -(((y + 1/2) - cy) /
- *        fy), P = (depth ux, depth uy, -depth); orthographic: (ux, uy, -depth));
+ *        P as in step 9;
  *        M = S V^-1 (V^-1 = [R^T | -R^T t], products summed in index order);
  *        q = M P; z = -q_z; unless z > near the light is unshadowed; u = cx +
  *        fx (q_x (1/z)), v = cy - fy (q_y (1/z)) (unshadowed beyond 2^20);
@@ -548,6 +550,7 @@ static int render_image(const orc_meshes* me, const orc_batch* b, int32_t c, con
   const float* V = b->cam_view + (int64_t)c * 12;
   const float* in = b->cam_intr + (int64_t)c * 6;
   float fx = in[0], fy = in[1], cx = in[2], cy = in[3], near = in[4];
+  float inv_fx = 1.0f / fx, inv_fy = 1.0f / fy;
   int ortho = in[5] != 0.0f;
   int64_t base = b->img_offset[c];
 
@@ -651,8 +654,8 @@ static int render_image(const orc_meshes* me, const orc_batch* b, int32_t c, con
       float len = sqrtf((n[0] * n[0] + n[1] * n[1]) + n[2] * n[2]);
       if (len > 0.0f)
         for (int k = 0; k < 3; k++) n[k] = n[k] / len;
-      float ux = ((float)x + 0.5f - cx) / fx;
-      float uy = -(((float)y + 0.5f - cy) / fy);
+      float ux = ((float)x + 0.5f - cx) * inv_fx;
+      float uy = -(((float)y + 0.5f - cy) * inv_fy);
       float P[3];
       if (ortho) {
         P[0] = ux;

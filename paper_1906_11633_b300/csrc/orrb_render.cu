@@ -265,8 +265,8 @@ __device__ void setup_image(const Params& p, int cam, CtaShared& sh, int* mprefi
     im.cy = in[3];
     im.near = in[4];
     im.ortho = kPass ? 0 : in[5] != 0.0f;
-    im.inv_fx = 1.0f / im.fx;
-    im.inv_fy = 1.0f / im.fy;
+    im.inv_fx = __frcp_rn(im.fx);  // correctly rounded: the G-buffer position uses it
+    im.inv_fy = __frcp_rn(im.fy);
     if (kPass && in[0] == 0.0f) {  // the light casts no shadow: no map (not an error)
       im.valid = 0;
     } else if (s < 0 || s >= p.n_samples || im.W < 1 || im.H < 1 || im.W > p.w_max || im.H > p.h_max ||
@@ -1006,16 +1006,15 @@ __device__ void shadow_setup(const Params& p, const ImageInfo& im, ShadowInfo& s
   for (int k = 0; k < 6; k++) sd.si[l][k] = si[k];
 }
 
-// The shadow factors of the casting lights at the pixel (px, py) of depth `depth`, and the
-// G-buffer word (slot | shadowed taps of light l << (8 + 4l)).  The pixel's G-buffer position is
-// projected into each light's map with round-to-nearest operations in a fixed order (the
-// reciprocal is correctly rounded, so it equals 1 / z), then the 3 x 3 texels around it are
-// compared with its depth less the bias; the factor (9 - k) / 9 comes from a table.
-__device__ __forceinline__ int shadow_lookup(const Params& p, const ImageInfo& im, const ShadowInfo& sd, int px,
-                                             int py, float depth, int mat, float vis[kMaxLights]) {
-  const float ux = __fdiv_rn(__fsub_rn(__fadd_rn(float(px), 0.5f), im.cx), im.fx);
-  const float uy = -__fdiv_rn(__fsub_rn(__fadd_rn(float(py), 0.5f), im.cy), im.fy);
-  const float P0 = im.ortho ? ux : __fmul_rn(depth, ux), P1 = im.ortho ? uy : __fmul_rn(depth, uy), P2 = -depth;
+// The shadow factors of the casting lights at the G-buffer position P (whose three coordinates
+// the resolve computes with separately rounded operations), and the G-buffer word (slot |
+// shadowed taps of light l << (8 + 4l)).  P is projected into each light's map with
+// round-to-nearest operations in a fixed order (the reciprocal is correctly rounded, so it
+// equals 1 / z), then the 3 x 3 texels around it are compared with its depth less the bias; the
+// factor (9 - k) / 9 comes from a table.
+__device__ __forceinline__ int shadow_lookup(const Params& p, const ImageInfo& im, const ShadowInfo& sd,
+                                             const float P[3], int mat, float vis[kMaxLights]) {
+  const float P0 = P[0], P1 = P[1], P2 = P[2];
   const int R = p.shadow_res;
   int word = mat;
 #pragma unroll
@@ -1318,7 +1317,7 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
   for (int ly = 0; ly < ch; ly++) {
     const long long orow = im.px_off + (long long)(y0 + ly) * im.W + x0;
     const int py = y0 + ly;
-    const float uy = -((float(py) + 0.5f - im.cy) * im.inv_fy);
+    const float uy = -__fmul_rn(__fsub_rn(__fadd_rn(float(py), 0.5f), im.cy), im.inv_fy);  // (no contraction)
     uint8_t* rgb_row = p.rgb ? p.rgb + 3 * orow : nullptr;
     uint16_t* nrm_row = p.normal ? p.normal + 3 * orow : nullptr;
     float* depth_row = p.depth ? p.depth + orow : nullptr;
@@ -1380,20 +1379,21 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
             n[2] *= rl;
           }
         }
-        const float ux = (float(px) + 0.5f - im.cx) * im.inv_fx;
+        // the G-buffer position, each operation rounded separately (the shadow lookup relies on it)
+        const float ux = __fmul_rn(__fsub_rn(__fadd_rn(float(px), 0.5f), im.cx), im.inv_fx);
         if (im.ortho) {
           P[0] = ux;
           P[1] = uy;
           P[2] = -depth;
         } else {
-          P[0] = depth * ux;
-          P[1] = depth * uy;
+          P[0] = __fmul_rn(depth, ux);
+          P[1] = __fmul_rn(depth, uy);
           P[2] = -depth;
         }
         if (kShadow) {
           const ShadowInfo& sd = *reinterpret_cast<const ShadowInfo*>(spans + kSpanCap);
           float vis[kMaxLights];
-          word = shadow_lookup(p, im, sd, px, py, depth, mat, vis);
+          word = shadow_lookup(p, im, sd, P, mat, vis);
           shade<true, true>(sh, P, n, mat, rgb, vis);
         } else {
           shade<(kF & kFeatLight) != 0>(sh, P, n, mat, rgb);

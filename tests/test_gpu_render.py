@@ -413,6 +413,8 @@ def test_shadow_maps_and_lookups_match_oracle(hand_renderer, oracle, mode):
     assert (g["shadow_map"][~cast] == -1.0).all()
     assert (o["shadow_map"][cast] > 0).mean() > 0.005
     np.testing.assert_array_equal(g["gbuffer"][6].view(np.int32), o["gb_mat"])
+    same = g["depth"] == o["depth"]                     # the lookup's input: the G-buffer position, bit for bit
+    np.testing.assert_array_equal(g["gbuffer"][0:3].T[same], o["gb_pos"][same])
     k = (o["gb_mat"][o["gb_mat"] >= 0] >> 8) & 0xfff
     assert (k > 0).mean() > 0.05                        # shadows fall on a good share of the pixels
     compare(g, o, "shadows")
