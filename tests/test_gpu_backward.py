@@ -47,7 +47,8 @@ def setup(renderer, oracle, batch, seed=0):
 
 @pytest.mark.parametrize("res", [64, 200])
 def test_adjoint_matches_oracle(renderer, oracle, res):
-    b = sg.hand_batch(4, np.arange(8 if res == 64 else 16), res=res)
+    """At 200 px the full differentiation batch: 256 hand samples x 3 cameras."""
+    b = sg.hand_batch(4, np.arange(8 if res == 64 else 256), res=res)
     db, out, gb, target, d_rgb = setup(renderer, oracle, b)
     dm, dl, de = renderer.shade_backward(db, out["gbuffer"], torch.from_numpy(d_rgb).cuda())
     rdm, rdl, rde = oracle.shade_backward_f64(b, *gb, d_rgb.astype(np.float64))
