@@ -52,7 +52,8 @@ _BATCH_ARRAYS = ("inst_offset", "inst_mesh", "inst_pose", "inst_seg", "inst_mat_
 
 
 class _Batch(C.Structure):
-    _fields_ = [("n_samples", C.c_int32)] + [(n, C.c_void_p) for n in _BATCH_ARRAYS] + [("shadow_res", C.c_int32)]
+    _fields_ = [("n_samples", C.c_int32)] + [(n, C.c_void_p) for n in _BATCH_ARRAYS] + [("shadow_res", C.c_int32),
+                                                                                        ("shadow_faces", C.c_int32)]
 
 
 class _Outputs(C.Structure):
@@ -123,10 +124,12 @@ class _Pinned:
             grading=_opt(batch, "grading"), light_spot=_opt(batch, "light_spot"), emission=_opt(batch, "emission"),
             shadow_view=_opt(batch, "shadow_view"), shadow_intr=_opt(batch, "shadow_intr"), shadow_map=None)
         self.shadow_res = int(getattr(batch, "shadow_res", 0) or 0)
-        self.batch = _Batch(batch.n_samples, *[_p(self.arrs[n]) for n in _BATCH_ARRAYS], self.shadow_res)
+        self.shadow_faces = int(getattr(batch, "shadow_faces", 1) or 1)
+        self.batch = _Batch(batch.n_samples, *[_p(self.arrs[n]) for n in _BATCH_ARRAYS], self.shadow_res,
+                            self.shadow_faces)
 
     def set_shadow_maps(self, maps):
-        """Point the lookups of step 16 at `maps` ([S, 4, R, R] float32, kept alive here)."""
+        """Point the lookups of step 16 at `maps` ([S, 4, F, R, R] float32, kept alive here)."""
         self.arrs["shadow_map"] = maps
         self.batch.shadow_map = _p(maps)
 
@@ -145,12 +148,12 @@ def default_threads() -> int:
 
 
 def shadow_maps(batch, threads: int | None = None, pin=None):
-    """The shadow maps of step 15, [n_samples, 4, R, R] float32 (zero for lights without shadow), or None."""
+    """The shadow maps of step 15, [n_samples, 4, F, R, R] float32 (zero for faces without shadow), or None."""
     pin = pin or _Pinned(batch)
     R = pin.shadow_res
     if R <= 0 or pin.arrs["shadow_view"] is None or pin.arrs["shadow_intr"] is None:
         return None
-    maps = np.zeros((batch.n_samples, 4, R, R), np.float32)
+    maps = np.zeros((batch.n_samples, 4, pin.shadow_faces, R, R), np.float32)
     threads = threads or default_threads()
     L = lib()
 

@@ -76,22 +76,23 @@
  *      bit 1: origin projected; a zero.  An instance of a mesh without
  *      triangles keeps an empty row.
  *  15  optional shadow maps (soft shadows of the benchmark's lights, Sec. 5):
- *      light l of sample s casts a shadow when l < its light count and its
- *      shadow camera (view S, intrinsics fx, fy, cx, cy, near, bias) has
- *      fx != 0.  Its R x R map holds, per pixel, the depth seen from the
- *      shadow camera (steps 2-8 with that camera, perspective) of the nearest
- *      BACK face -- each triangle's second and third vertices swapped before
- *      step 5, so front faces are culled -- and 0 where there is none.
+ *      each light has F shadow cameras ("faces": one for a spot light, six
+ *      cube faces for a point light); face f of light l of sample s casts
+ *      when l < the light count and its camera (view S, intrinsics fx, fy,
+ *      cx, cy, near, bias) has fx != 0.  Its R x R map holds, per pixel, the
+ *      depth seen from that camera (steps 2-8 with it, perspective) of the
+ *      nearest BACK face -- each triangle's second and third vertices swapped
+ *      before step 5, so front faces are culled -- and 0 where there is none.
  *  16  shadow lookup in step 10: for a camera pixel with surface and each
- *      casting light, in fp32 with every operation rounded separately:
- *        P as in step 9;
- *        M = S V^-1 (V^-1 = [R^T | -R^T t], products summed in index order);
- *        q = M P; z = -q_z; unless z > near the light is unshadowed; u = cx +
- *        fx (q_x (1/z)), v = cy - fy (q_y (1/z)) (unshadowed beyond 2^20);
- *        over the 3 x 3 texels (floor(u) + a, floor(v) + b), a, b in {-1, 0,
- *        1}, inside the map, count k those with map depth d > 0 and z - bias
- *        > d (percentage-closer filtering, Reeves, Salesin and Cook 1987);
- *        E_l is multiplied by (9 - k) / 9.  The G-buffer's material word
+ *      light with a casting face, in fp32 with every operation rounded
+ *      separately: P as in step 9; for the faces in order, M = S V^-1 (V^-1 =
+ *      [R^T | -R^T t], products summed in index order), q = M P, z = -q_z,
+ *      u = cx + fx (q_x (1/z)), v = cy - fy (q_y (1/z)); the first face with
+ *      z > near and (floor(u), floor(v)) inside its map decides (none: the
+ *      light is unshadowed): over the 3 x 3 texels (floor(u) + a, floor(v) +
+ *      b), a, b in {-1, 0, 1}, inside the map, count k those with map depth
+ *      d > 0 and z - bias > d (percentage-closer filtering, Reeves, Salesin
+ *      and Cook 1987); E_l is multiplied by (9 - k) / 9.  The G-buffer's material word
  *        carries k of light l in bits 8 + 4l .. 11 + 4l (the adjoint holds it
  *        fixed: visibility does not depend on the shading parameters).
  */
@@ -425,10 +426,18 @@ static void shade_f32(const orc_batch* b, int32_t s, const float* V, int ortho, 
 /* ------------------------------------------------------------------ */
 /* steps 15-16: shadows                                                */
 /* ------------------------------------------------------------------ */
-/* light l of sample s casts a shadow (step 15) */
-static int casts_shadow(const orc_batch* b, int32_t s, int l) {
+/* faces per light (step 15) */
+static int32_t shadow_faces(const orc_batch* b) { return b->shadow_faces > 0 ? b->shadow_faces : 1; }
+
+/* index of face f of light l of sample s in the shadow arrays */
+static int64_t shadow_index(const orc_batch* b, int32_t s, int l, int f) {
+  return ((int64_t)s * ORC_MAX_LIGHTS + l) * shadow_faces(b) + f;
+}
+
+/* face f of light l of sample s casts a shadow (step 15) */
+static int casts_shadow(const orc_batch* b, int32_t s, int l, int f) {
   return b->shadow_view && b->shadow_intr && b->shadow_res > 0 && l < light_count(b, s) &&
-         b->shadow_intr[((int64_t)s * ORC_MAX_LIGHTS + l) * 6 + 0] != 0.0f;
+         b->shadow_intr[shadow_index(b, s, l, f) * 6 + 0] != 0.0f;
 }
 
 /* M = S V^-1 for the rigid camera view V = [R | t] (step 16) */
@@ -445,17 +454,19 @@ static void camera_to_shadow(const float* S, const float* V, float M[12]) {
     }
 }
 
-/* the number of shadowed taps (0..9) at camera-space point P (step 16) */
+/* the number of shadowed taps (0..9) at camera-space point P on one face, or -1 when the face's
+   map does not contain P's projection (step 16) */
 static int shadow_taps(const float M[12], const float* si, const float* map, int32_t R, const float P[3]) {
   float q[3];
   for (int i = 0; i < 3; i++) q[i] = ((M[i * 4 + 0] * P[0] + M[i * 4 + 1] * P[1]) + M[i * 4 + 2] * P[2]) + M[i * 4 + 3];
   float z = -q[2];
-  if (!(z > si[4])) return 0;
+  if (!(z > si[4])) return -1;
   float iw = 1.0f / z;
   float u = si[2] + si[0] * (q[0] * iw);
   float v = si[3] - si[1] * (q[1] * iw);
-  if (!(fabsf(u) < GUARD_PX) || !(fabsf(v) < GUARD_PX)) return 0;
+  if (!(fabsf(u) < GUARD_PX) || !(fabsf(v) < GUARD_PX)) return -1;
   int32_t i0 = (int32_t)floorf(u), j0 = (int32_t)floorf(v);
+  if (i0 < 0 || j0 < 0 || i0 >= R || j0 >= R) return -1;
   float zb = z - si[5];
   int k = 0;
   for (int bb = -1; bb <= 1; bb++)
@@ -603,13 +614,20 @@ static int render_image(const orc_meshes* me, const orc_batch* b, int32_t c, con
   }
   visibility(me, b, s, V, in, ortho, W, H, 0, px, out->counters);
 
-  /* step 16: the camera-to-shadow maps of the casting lights */
-  float Msh[ORC_MAX_LIGHTS][12];
-  int cast[ORC_MAX_LIGHTS];
-  for (int l = 0; l < ORC_MAX_LIGHTS; l++) {
-    cast[l] = casts_shadow(b, s, l);
-    if (cast[l]) camera_to_shadow(b->shadow_view + ((int64_t)s * ORC_MAX_LIGHTS + l) * 12, V, Msh[l]);
+  /* step 16: the camera-to-shadow maps of the casting faces */
+  const int32_t F = shadow_faces(b);
+  float (*Msh)[12] = (float (*)[12])malloc(sizeof(float) * 12 * ORC_MAX_LIGHTS * (size_t)F);
+  int* cast = (int*)malloc(sizeof(int) * ORC_MAX_LIGHTS * (size_t)F);
+  if (!Msh || !cast) {
+    free(Msh);
+    free(cast);
+    return -1;
   }
+  for (int l = 0; l < ORC_MAX_LIGHTS; l++)
+    for (int f = 0; f < F; f++) {
+      cast[l * F + f] = casts_shadow(b, s, l, f);
+      if (cast[l * F + f]) camera_to_shadow(b->shadow_view + shadow_index(b, s, l, f) * 12, V, Msh[l * F + f]);
+    }
 
   /* steps 9-11 per pixel */
   const float* bg = b->background + (int64_t)s * 3;
@@ -669,10 +687,14 @@ static int render_image(const orc_meshes* me, const orc_batch* b, int32_t c, con
       float vis[ORC_MAX_LIGHTS] = {1.0f, 1.0f, 1.0f, 1.0f};
       int32_t word = p->mat;
       for (int l = 0; l < ORC_MAX_LIGHTS; l++) {
-        if (!cast[l]) continue;
-        const int64_t sl = (int64_t)s * ORC_MAX_LIGHTS + l;
-        int k = shadow_taps(Msh[l], b->shadow_intr + sl * 6, b->shadow_map + sl * b->shadow_res * b->shadow_res,
-                            b->shadow_res, P);
+        int k = -1;
+        for (int f = 0; f < F && k < 0; f++) { /* the first face whose map contains the point */
+          if (!cast[l * F + f]) continue;
+          const int64_t si = shadow_index(b, s, l, f);
+          k = shadow_taps(Msh[l * F + f], b->shadow_intr + si * 6,
+                          b->shadow_map + si * b->shadow_res * b->shadow_res, b->shadow_res, P);
+        }
+        if (k <= 0) continue;
         vis[l] = (float)(9 - k) / 9.0f;
         word |= k << (8 + 4 * l);
       }
@@ -696,6 +718,8 @@ static int render_image(const orc_meshes* me, const orc_batch* b, int32_t c, con
       if (out->gb_mat) out->gb_mat[o] = word;
     }
   }
+  free(Msh);
+  free(cast);
   return 0;
 }
 
@@ -705,13 +729,14 @@ int orc_render_shadow_maps(const orc_meshes* m, const orc_batch* b, int32_t s_be
   pixel_winner* px = (pixel_winner*)malloc(sizeof(pixel_winner) * (size_t)R * (size_t)R);
   if (!px) return -1;
   for (int32_t s = s_begin; s < s_end; s++)
-    for (int l = 0; l < ORC_MAX_LIGHTS; l++) {
-      if (!casts_shadow(b, s, l)) continue;
-      const int64_t sl = (int64_t)s * ORC_MAX_LIGHTS + l;
-      visibility(m, b, s, b->shadow_view + sl * 12, b->shadow_intr + sl * 6, 0, R, R, 1, px, NULL);
-      float* map = maps + sl * R * R;
-      for (int64_t i = 0; i < (int64_t)R * R; i++) map[i] = px[i].key < 0 ? 0.0f : px[i].depth;
-    }
+    for (int l = 0; l < ORC_MAX_LIGHTS; l++)
+      for (int f = 0; f < shadow_faces(b); f++) {
+        if (!casts_shadow(b, s, l, f)) continue;
+        const int64_t si = shadow_index(b, s, l, f);
+        visibility(m, b, s, b->shadow_view + si * 12, b->shadow_intr + si * 6, 0, R, R, 1, px, NULL);
+        float* map = maps + si * R * R;
+        for (int64_t i = 0; i < (int64_t)R * R; i++) map[i] = px[i].key < 0 ? 0.0f : px[i].depth;
+      }
   free(px);
   return 0;
 }

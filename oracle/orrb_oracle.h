@@ -70,10 +70,11 @@ typedef struct {
   const float* grading;         /* [S][8] colour-grading epilogue (step 13), or NULL */
   const float* light_spot;      /* [S][4][5] spot cones (step 10), or NULL */
   const float* emission;        /* [S][32] material emission (step 10), or NULL for none */
-  const float* shadow_view;     /* [S][4][3][4] shadow camera of each light (step 15), or NULL */
-  const float* shadow_intr;     /* [S][4][6] fx, fy, cx, cy, near, bias; fx == 0: no shadow */
-  const float* shadow_map;      /* [S][4][R][R] maps of step 15, read by step 16 (or NULL) */
+  const float* shadow_view;     /* [S][4][F][3][4] shadow cameras of each light (step 15), or NULL */
+  const float* shadow_intr;     /* [S][4][F][6] fx, fy, cx, cy, near, bias; fx == 0: no shadow */
+  const float* shadow_map;      /* [S][4][F][R][R] maps of step 15, read by step 16 (or NULL) */
   int32_t shadow_res;           /* R, 0 for no shadows */
+  int32_t shadow_faces;         /* F, shadow cameras per light (1 spot, 6 cube); 0 is read as 1 */
 } orc_batch;
 
 typedef struct {                /* every pointer may be NULL */
@@ -96,7 +97,7 @@ typedef struct {                /* every pointer may be NULL */
 int orc_render(const orc_meshes* m, const orc_batch* b, int32_t cam_begin, int32_t cam_end,
                const orc_outputs* out);
 
-/* Step 15: the shadow maps [S][4][R][R] of samples [s_begin, s_end) (maps of lights that cast
+/* Step 15: the shadow maps [S][4][F][R][R] of samples [s_begin, s_end) (maps of faces that cast
  * no shadow are left as they were).  Returns 0, or -1 on allocation failure. */
 int orc_render_shadow_maps(const orc_meshes* m, const orc_batch* b, int32_t s_begin, int32_t s_end, float* maps);
 

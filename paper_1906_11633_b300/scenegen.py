@@ -248,12 +248,14 @@ class Batch:
     light_spot: Optional[np.ndarray] = None
     # [B, 32] float32 material emission e (the emitted colour is e * albedo), or None for none
     emission: Optional[np.ndarray] = None
-    # shadows: per light a perspective shadow camera, view [B, 4, 3, 4] (camera-from-world) and
-    # intrinsics [B, 4, 6] (fx, fy, cx, cy, near, depth bias; fx == 0: the light casts none),
-    # rendered into square maps of side shadow_res; None / 0 for no shadows
+    # shadows: per light shadow_faces perspective shadow cameras (one for a spot light, six cube
+    # faces for a point light), views [B, 4, F, 3, 4] (camera-from-world) and intrinsics
+    # [B, 4, F, 6] (fx, fy, cx, cy, near, depth bias; fx == 0: that face casts none), rendered
+    # into square maps of side shadow_res; None / 0 for no shadows
     shadow_view: Optional[np.ndarray] = None
     shadow_intr: Optional[np.ndarray] = None
     shadow_res: int = 0
+    shadow_faces: int = 1
 
     @property
     def n_samples(self) -> int:
@@ -321,16 +323,20 @@ def concat_batches(batches: Sequence[Batch]) -> Batch:
         grading=_concat_opt(batches, "grading", identity_grading),
         light_spot=_concat_opt(batches, "light_spot", lambda n: np.zeros((n, MAX_LIGHTS, 5), np.float32)),
         emission=_concat_opt(batches, "emission", lambda n: np.zeros((n, MAX_MATERIALS), np.float32)),
-        shadow_view=_concat_opt(batches, "shadow_view", lambda n: np.zeros((n, MAX_LIGHTS, 3, 4), np.float32)),
-        shadow_intr=_concat_opt(batches, "shadow_intr", lambda n: np.zeros((n, MAX_LIGHTS, 6), np.float32)),
-        shadow_res=_shadow_res(batches),
+        shadow_view=_concat_opt(batches, "shadow_view",
+                                lambda n: np.zeros((n, MAX_LIGHTS, _shadow_kind(batches)[1], 3, 4), np.float32)),
+        shadow_intr=_concat_opt(batches, "shadow_intr",
+                                lambda n: np.zeros((n, MAX_LIGHTS, _shadow_kind(batches)[1], 6), np.float32)),
+        shadow_res=_shadow_kind(batches)[0],
+        shadow_faces=_shadow_kind(batches)[1],
     )
 
 
-def _shadow_res(batches):
-    res = {b.shadow_res for b in batches if b.shadow_view is not None}
-    assert len(res) <= 1, "batches with shadows must share one shadow-map size"
-    return res.pop() if res else 0
+def _shadow_kind(batches):
+    """(shadow_res, shadow_faces) shared by the batches with shadows."""
+    kinds = {(b.shadow_res, b.shadow_faces) for b in batches if b.shadow_view is not None}
+    assert len(kinds) <= 1, "batches with shadows must share one shadow-map size and face count"
+    return kinds.pop() if kinds else (0, 1)
 
 
 def _concat_opt(batches, name, neutral):
@@ -366,6 +372,7 @@ def select_samples(batch: Batch, idx: Sequence[int]) -> Batch:
             shadow_view=batch.shadow_view[s:s + 1] if batch.shadow_view is not None else None,
             shadow_intr=batch.shadow_intr[s:s + 1] if batch.shadow_intr is not None else None,
             shadow_res=batch.shadow_res,
+            shadow_faces=batch.shadow_faces,
         ))
     return concat_batches(parts)
 
@@ -622,8 +629,9 @@ def grading_params(seed: int, sample_ids) -> np.ndarray:
 
 
 def hand_batch(seed: int, sample_ids, res: int = 200, n_cams: int = 3, meshes=None, res_per_sample=None,
-               cams_per_sample=None, grading: bool = False) -> Batch:
-    """Hand-like scenes: table, block, 24 capsule links posed by hinge angles U(+-60 deg)."""
+               cams_per_sample=None, grading: bool = False, shadow_res: int = 0) -> Batch:
+    """Hand-like scenes: table, block, 24 capsule links posed by hinge angles U(+-60 deg); with
+    `shadow_res` > 0 every point light casts shadows from six cube-face maps of that side."""
     ids = np.asarray(sample_ids, dtype=np.int64).reshape(-1)
     B = len(ids)
     meshes = meshes if meshes is not None else hand_meshes(0)
@@ -663,7 +671,19 @@ def hand_batch(seed: int, sample_ids, res: int = 200, n_cams: int = 3, meshes=No
         exposure_ev=ev, ambient=ambient, background=background,
         sample_ids=ids,
         grading=grading_params(seed, ids) if grading else None,
+        **(_cube_shadows(light, meta, shadow_res) if shadow_res > 0 else {}),
     )
+
+
+def _cube_shadows(light, meta, res):
+    """Cube-face shadow cameras for every point light of every sample (zero rows elsewhere)."""
+    B = len(light)
+    sv, si = point_shadow_cameras(light[..., :3].astype(np.float64), res)     # [B, 4, 6, ...]
+    on = (np.arange(MAX_LIGHTS)[None, :] < meta[:, :1]) & (meta[:, 1:2] == LIGHT_POINT)
+    sv = np.where(on[..., None, None, None], sv, 0.0)
+    si = np.where(on[..., None, None], si, 0.0)
+    return dict(shadow_view=sv.reshape(B, MAX_LIGHTS, 6, 3, 4).astype(np.float32),
+                shadow_intr=si.reshape(B, MAX_LIGHTS, 6, 6).astype(np.float32), shadow_res=int(res), shadow_faces=6)
 
 
 # --------------------------------------------------------------------------
@@ -780,6 +800,26 @@ def spot_shadow_cameras(pos, axis, cos_outer, res: int, near: float = 0.05, bias
     return view_matrix(R, pos), intr
 
 
+CUBE_FACES = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]], np.float64)
+
+
+def point_shadow_cameras(pos, res: int, near: float = 0.02, bias: float = 0.004):
+    """Six cube-face shadow cameras per point light (looking along +x, -x, +y, -y, +z, -z with
+    90 deg fields of view).  pos [..., 3] -> views [..., 6, 3, 4], intrinsics [..., 6, 6]."""
+    pos = np.asarray(pos, np.float64)
+    views, intr = [], []
+    for d in CUBE_FACES:
+        up = np.array([0.0, 1.0, 0.0]) if abs(d[2]) > 0 else np.array([0.0, 0.0, 1.0])
+        f = np.broadcast_to(d, pos.shape)
+        r = np.cross(f, up)
+        r = r / np.linalg.norm(r, axis=-1, keepdims=True)
+        R = np.stack([r, np.cross(r, f), -f], axis=-2)
+        views.append(view_matrix(R, pos))
+        intr.append(np.broadcast_to(np.array([0.5 * res, 0.5 * res, 0.5 * res, 0.5 * res, near, bias]),
+                                    pos.shape[:-1] + (6,)))
+    return np.stack(views, axis=-3), np.stack(intr, axis=-2)
+
+
 # the block's six calibrated face colours (HSV): red, orange, yellow, green, blue, purple
 BLOCK_HSV = np.array([[0.00, 0.85, 0.80], [0.08, 0.85, 0.85], [0.15, 0.80, 0.85],
                       [0.33, 0.70, 0.60], [0.60, 0.75, 0.70], [0.78, 0.60, 0.60]])
@@ -819,11 +859,11 @@ def benchmark_batch(seed: int, sample_ids, res: int = 200, n_cams: int = 3, orbi
         kw.update(cam_view=views.astype(np.float32), cam_sample=owner)
     if shadow_res > 0:
         sv, si = spot_shadow_cameras(pos, axis, cos_o, shadow_res)
-        shadow_view = np.zeros((B, MAX_LIGHTS, 3, 4))
-        shadow_intr = np.zeros((B, MAX_LIGHTS, 6))
-        shadow_view[:, :N_SPOTS], shadow_intr[:, :N_SPOTS] = sv, si
+        shadow_view = np.zeros((B, MAX_LIGHTS, 1, 3, 4))
+        shadow_intr = np.zeros((B, MAX_LIGHTS, 1, 6))
+        shadow_view[:, :N_SPOTS, 0], shadow_intr[:, :N_SPOTS, 0] = sv, si
         kw.update(shadow_view=shadow_view.astype(np.float32), shadow_intr=shadow_intr.astype(np.float32),
-                  shadow_res=int(shadow_res))
+                  shadow_res=int(shadow_res), shadow_faces=1)
     return b.with_params(**kw)
 
 

@@ -25,11 +25,11 @@ def _down_camera(eye, R, half_deg, bias=0.0, near=0.05):
 
 
 def _shadowed(batch, views, intrs, R):
-    sv = np.zeros((batch.n_samples, 4, 3, 4), np.float32)
-    si = np.zeros((batch.n_samples, 4, 6), np.float32)
+    sv = np.zeros((batch.n_samples, 4, 1, 3, 4), np.float32)
+    si = np.zeros((batch.n_samples, 4, 1, 6), np.float32)
     for l, (v, i) in enumerate(zip(views, intrs)):
-        sv[:, l], si[:, l] = v, i
-    return batch.with_params(shadow_view=sv, shadow_intr=si, shadow_res=R)
+        sv[:, l, 0], si[:, l, 0] = v, i
+    return batch.with_params(shadow_view=sv, shadow_intr=si, shadow_res=R, shadow_faces=1)
 
 
 def test_shadow_map_holds_the_nearest_back_faces(oracle):
@@ -37,7 +37,7 @@ def test_shadow_map_holds_the_nearest_back_faces(oracle):
     b = scenes.single_sample([sg.box_mesh(a, per_face_material=False)], [0], [scenes.pose(t=(0.0, 0.0, zc))],
                              [scenes.camera_down((0.0, 0.0, 3.0), 8, 8, fovy_deg=40)], lights=[((0, 0, H), 1.0)])
     view, intr = _down_camera((0.0, 0.0, H), R, half)
-    m = oracle.render(_shadowed(b, [view], [intr], R))["shadow_map"][0, 0].astype(np.float64)
+    m = oracle.render(_shadowed(b, [view], [intr], R))["shadow_map"][0, 0, 0].astype(np.float64)
     f = intr[0]
     u = (np.arange(R) + 0.5 - 0.5 * R) / f                  # pixel-centre ray slopes
     ux, uy = np.meshgrid(u, -u)
@@ -84,7 +84,7 @@ def test_lights_without_a_shadow_camera_are_unshadowed(oracle):
     b = sg.benchmark_batch(2, np.arange(2), res=48, shadow_res=64, grading=False)
     plain = oracle.render(b.with_params(shadow_view=None, shadow_intr=None, shadow_res=0), gbuffer=True)
     off = b.shadow_intr.copy()
-    off[:, :, 0] = 0.0                                      # fx = 0: no shadow camera
+    off[..., 0] = 0.0                                       # fx = 0: no shadow camera
     got = oracle.render(b.with_params(shadow_intr=off), gbuffer=True)
     for k in ("rgb", "rgb_linear", "depth", "normal", "seg", "gb_mat"):
         np.testing.assert_array_equal(got[k], plain[k], err_msg=k)
@@ -133,20 +133,67 @@ def test_pcf_taps_match_the_plane_geometry(oracle):
     H, bias, R = 1.2, 0.004, 96
     b, intr = _floating_box(bias, R=R)
     o = oracle.render(b, gbuffer=True)
-    m = o["shadow_map"][0, 0].astype(np.float64)
+    m = o["shadow_map"][0, 0, 0].astype(np.float64)
     k = (o["gb_mat"] >> 8) & 15
     P = o["gb_pos"].astype(np.float64)
     sel = np.nonzero(o["seg"] == 1)[0]
     f, c = intr[0], intr[2]
     u, v = c + f * P[sel, 0] / H, c - f * P[sel, 1] / H
     i0, j0 = np.floor(u).astype(int), np.floor(v).astype(int)
+    inside = (i0 >= 0) & (j0 >= 0) & (i0 < R) & (j0 < R)       # else no face contains the point: lit
     want = np.zeros(len(sel), int)
     for dj in (-1, 0, 1):
         for di in (-1, 0, 1):
             i, j = i0 + di, j0 + dj
             ok = (i >= 0) & (j >= 0) & (i < R) & (j < R)
             d = np.where(ok, m[np.clip(j, 0, R - 1), np.clip(i, 0, R - 1)], 0.0)
-            want += ((d > 0) & (H - bias > d)).astype(int)
+            want += ((d > 0) & (H - bias > d) & inside).astype(int)
     safe = (np.abs(u - np.round(u)) > 1e-3) & (np.abs(v - np.round(v)) > 1e-3)
     assert safe.mean() > 0.99 and (want[safe] == 9).sum() > 50 and ((want[safe] > 0) & (want[safe] < 9)).sum() > 20
     np.testing.assert_array_equal(k[sel][safe], want[safe])
+
+
+def _ray_hits_box(L, p, c, half, grow):
+    """Does the segment L -> p (rows of p) pass through the box centred at c (half-sizes `half` grown
+    by `grow`)?  Slab test in fp64."""
+    d = p - L
+    lo, hi = c - half - grow, c + half + grow
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t1, t2 = (lo - L) / d, (hi - L) / d
+    tmin = np.nanmax(np.minimum(t1, t2), axis=1)
+    tmax = np.nanmin(np.maximum(t1, t2), axis=1)
+    return (tmax >= np.maximum(tmin, 0.0)) & (tmin <= 1.0)
+
+
+def test_cube_faces_shadow_a_point_light_in_every_direction(oracle):
+    """A point light with six 90-degree cube-face cameras over a plane with boxes below it and to
+    its sides: every plane point whose ray to the light passes well inside a box is fully shadowed
+    (whichever face sees it), every point whose ray misses all boxes by a margin is lit."""
+    H, R, a = 0.5, 128, 0.06
+    boxes = [np.array([0.0, 0.0, 0.25]), np.array([0.55, 0.0, 0.2]), np.array([0.0, -0.6, 0.2])]
+    plane, box = sg.plane_mesh(2.0, 2.0), sg.box_mesh(a, per_face_material=False)
+    cam = scenes.camera_down((0.0, 0.0, 4.0), 240, 240, fovy_deg=40)
+    b = scenes.single_sample([plane, box], [0, 1, 1, 1], [scenes.identity_pose()] + [scenes.pose(t=c) for c in boxes],
+                             [cam], seg=[1, 2, 3, 4], lights=[((0.0, 0.0, H), 1.0)])
+    sv, si = sg.point_shadow_cameras(np.array([[0.0, 0.0, H]]), R, near=0.02, bias=0.004)
+    b = b.with_params(shadow_view=np.pad(sv[None], ((0, 0), (0, 3), (0, 0), (0, 0), (0, 0))).astype(np.float32),
+                      shadow_intr=np.pad(si[None], ((0, 0), (0, 3), (0, 0), (0, 0))).astype(np.float32),
+                      shadow_res=R, shadow_faces=6)
+    o = oracle.render(b, gbuffer=True)
+    assert (o["shadow_map"][0, 0] > 0).any(axis=(1, 2)).sum() >= 3       # boxes seen by three faces
+    k = (o["gb_mat"] >> 8) & 15
+    on_plane = np.nonzero(o["seg"] == 1)[0]
+    P = o["gb_pos"][on_plane].astype(np.float64)
+    world = np.stack([P[:, 0], P[:, 1], np.zeros(len(P))], 1)            # camera R = identity, plane z = 0
+    L = np.array([0.0, 0.0, H])
+    margin = 3 * 2.0 / R * 0.7                                           # three texels at 0.7 m
+    hit = np.zeros(len(P), bool)
+    miss = np.ones(len(P), bool)
+    for c in boxes:
+        hit |= _ray_hits_box(L, world, c, a, -margin)
+        miss &= ~_ray_hits_box(L, world, c, a, margin)
+    faces = np.argmax(np.abs(world - L) * np.array([1, 1, 1]), axis=1)
+    assert hit.sum() > 300 and miss.sum() > 1000
+    assert len(np.unique(faces[hit])) >= 2                              # shadows through different faces
+    assert (k[on_plane][hit] == 9).all(), np.bincount(k[on_plane][hit])
+    assert (k[on_plane][miss] == 0).all(), np.bincount(k[on_plane][miss])
