@@ -137,6 +137,7 @@ typedef struct {
   int32_t max_width, max_height;/* <= ORRB_MAX_RESOLUTION */
   int64_t total_pixels;         /* sum of width*height over cameras */
   int32_t shadow_res;           /* side of the square shadow maps, <= ORRB_MAX_RESOLUTION; 0: no shadows */
+  int32_t shadow_faces;         /* F, shadow cameras per light in [1, 6] (1: spot, 6: cube map); 0 means 1 */
 } orrb_batch_shape;
 
 /* Per-sample state and randomization parameters; all device pointers. */
@@ -178,26 +179,28 @@ typedef struct {
                                     lights nothing.  Read only for samples of light type 2. */
   const float* emission;         /* [n_samples][32] or NULL (none): material emission e, the emitted
                                     colour being e * albedo (a MuJoCo material's emission, Sec. 4.2) */
-  const float* shadow_view;      /* [n_samples][4][3][4] or NULL: per light a perspective shadow camera
-                                    (camera-from-world, OpenGL axes, rigid) for the soft shadows of the
-                                    benchmark's lights (Sec. 5); used when shape.shadow_res > 0 */
-  const float* shadow_intr;      /* [n_samples][4][6] or NULL: its fx, fy, cx, cy (pixels of the
-                                    shadow_res square map), near (m) and depth bias (m); fx == 0: the
-                                    light casts no shadow.  A light l < the sample's light count with
-                                    fx != 0 casts: its map holds the depth from the shadow camera of
-                                    the nearest back face of the sample's triangles (front faces are
-                                    culled), rendered with the camera rules above, 0 where none.  A
-                                    visible surface point is then tested against the 3 x 3 map texels
-                                    around its projection (percentage-closer filtering): k of them
-                                    shadow it when their depth d > 0 and (its depth - bias) > d, and
-                                    the light's E is multiplied by (9 - k) / 9.  The projection is
-                                    computed in fp32 with every operation rounded to nearest: P as
-                                    the G-buffer position (x_v = depth ((x + 1/2 - cx) / fx), y_v =
-                                    -depth ((y + 1/2 - cy) / fy), z_v = -depth), q = (S V^-1) P with
-                                    V^-1 = [R^T | -R^T t] and products summed in index order, z =
-                                    -q_z (no shadow unless z > near), u = cx + fx (q_x (1 / z)), v =
-                                    cy - fy (q_y (1 / z)), taps (floor(u) + a, floor(v) + b) for a, b
-                                    in {-1, 0, 1}. */
+  const float* shadow_view;      /* [n_samples][4][F][3][4] or NULL: per light F perspective shadow
+                                    cameras ("faces": one for a spot light, six cube faces for a point
+                                    light; camera-from-world, OpenGL axes, rigid) for the soft shadows
+                                    of the benchmark's lights (Sec. 5); used when shape.shadow_res > 0 */
+  const float* shadow_intr;      /* [n_samples][4][F][6] or NULL: each face's fx, fy, cx, cy (pixels
+                                    of the shadow_res square map), near (m) and depth bias (m); fx ==
+                                    0: the face casts no shadow.  A face of a light l < the sample's
+                                    light count with fx != 0 casts: its map holds the depth from its
+                                    camera of the nearest back face of the sample's triangles (front
+                                    faces are culled), rendered with the camera rules above, 0 where
+                                    none.  A visible surface point is projected, for the light's
+                                    casting faces in order, in fp32 with every operation rounded to
+                                    nearest: P the G-buffer position (x_v = depth ((x + 1/2 - cx) *
+                                    (1/fx)), y_v = -depth ((y + 1/2 - cy) * (1/fy)), z_v = -depth,
+                                    1/fx rounded once), q = (S V^-1) P with V^-1 = [R^T | -R^T t] and
+                                    products summed in index order, z = -q_z, u = cx + fx (q_x (1 /
+                                    z)), v = cy - fy (q_y (1 / z)); the first face with z > near and
+                                    (floor(u), floor(v)) inside its map decides (none: unshadowed):
+                                    k of the 3 x 3 texels (floor(u) + a, floor(v) + b), a, b in {-1,
+                                    0, 1}, shadow it when inside the map with depth d > 0 and (z -
+                                    bias) > d (percentage-closer filtering), and the light's E is
+                                    multiplied by (9 - k) / 9. */
 } orrb_batch_desc;
 
 /* Caller-preallocated outputs, flat over all pixels of all images (image c
@@ -220,10 +223,10 @@ typedef struct {
                            a mesh without triangles keeps an empty row), the snapped
                            projection kx, ky of its origin, flags (bit 0 box, bit 1 origin), 0.
                            Rows past a sample's instance count are left as they were. */
-  float* shadow_map;    /* device, [n_samples][4][shadow_res][shadow_res] depth (0: none); needed when
-                           shape.shadow_res > 0 and the batch has shadow cameras.  Written for the
-                           lights that cast, first (its own launch), then read by the shading.
-                           Maps of lights that cast none are left as they were. */
+  float* shadow_map;    /* device, [n_samples][4][F][shadow_res][shadow_res] depth (0: none); needed
+                           when shape.shadow_res > 0 and the batch has shadow cameras.  Written for
+                           the faces that cast, first (its own launch), then read by the shading.
+                           Maps of faces that cast none are left as they were. */
 } orrb_outputs;
 
 #define ORRB_MODE_FUSED 0  /* one persistent launch over all images (work queue) */

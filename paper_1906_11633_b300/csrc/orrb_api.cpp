@@ -195,8 +195,12 @@ orrb_status check_shape(orrb_ctx* ctx, const orrb_batch_shape* s) {
     return fail(ctx, ORRB_ERR_INVALID_ARG, "bad camera or pixel count");
   if (s->shadow_res < 0 || s->shadow_res > ORRB_MAX_RESOLUTION)
     return fail(ctx, ORRB_ERR_INVALID_ARG, "shadow_res %d outside [0, %d]", s->shadow_res, ORRB_MAX_RESOLUTION);
+  if (s->shadow_faces < 0 || s->shadow_faces > kMaxShadowFaces)
+    return fail(ctx, ORRB_ERR_INVALID_ARG, "shadow_faces %d outside [0, %d]", s->shadow_faces, kMaxShadowFaces);
   return ORRB_OK;
 }
+
+int faces_of(const orrb_batch_shape& s) { return s.shadow_faces > 0 ? s.shadow_faces : 1; }
 
 int tiles_of(int w, int h, const orrb_config& c) {
   int tw = std::min(w, c.tile_w);
@@ -236,13 +240,13 @@ orrb_status plan(orrb_ctx* ctx, const orrb_batch_shape& s, const orrb_config& c,
     P->n_slots = ctx->sm_count * P->ctas_per_sm;
   } else {
     P->ctas_per_sm = 0;
-    P->n_slots = std::max(std::max(s.max_cams_per_sample, 1), s.shadow_res > 0 ? kMaxLights : 1);
+    P->n_slots = std::max(std::max(s.max_cams_per_sample, 1), s.shadow_res > 0 ? kMaxLights * faces_of(s) : 1);
   }
   P->total = 256 + (size_t)P->n_slots * P->slot_bytes;
   P->nb_offset = 0;
   if (s.shadow_res > 0) {
     P->nb_offset = align256(P->total);
-    P->total = P->nb_offset + (size_t)s.n_samples * kMaxLights * s.shadow_res * s.shadow_res * sizeof(float2);
+    P->total = P->nb_offset + (size_t)s.n_samples * kMaxLights * faces_of(s) * s.shadow_res * s.shadow_res * sizeof(float2);
   }
   return ORRB_OK;
 }
@@ -273,6 +277,7 @@ void fill_batch(Params& p, const orrb_batch_shape& s, const orrb_batch_desc& b) 
   p.shadow_view = b.shadow_view;
   p.shadow_intr = b.shadow_intr;
   p.shadow_res = s.shadow_res > 0 && b.shadow_view && b.shadow_intr ? s.shadow_res : 0;
+  p.shadow_faces = faces_of(s);
   p.total_pixels = s.total_pixels;
   p.t_max = s.max_tris_per_sample;
   p.inst_max = s.max_inst_per_sample;
@@ -300,7 +305,7 @@ orrb_status enqueue_render(orrb_ctx* ctx, Params& p, const orrb_batch_shape& s, 
   if (p.shadow_res > 0) {
     Params q = p;
     q.shadow_pass = 1;
-    q.n_cams = s.n_samples * kMaxLights;
+    q.n_cams = s.n_samples * kMaxLights * p.shadow_faces;
     q.rgb = nullptr;
     q.normal = nullptr;
     q.seg = nullptr;
@@ -313,7 +318,7 @@ orrb_status enqueue_render(orrb_ctx* ctx, Params& p, const orrb_batch_shape& s, 
     q.w_max = q.h_max = s.shadow_res;
     const int n_ctas = mode == ORRB_MODE_FUSED ? std::min(n_slots, std::max(q.n_cams, 1)) : 0;
     q.n_slots = n_ctas;
-    if (launch_render(q, mode, threads, n_ctas, kMaxLights, stream, err, sizeof(err)))
+    if (launch_render(q, mode, threads, n_ctas, kMaxLights * p.shadow_faces, stream, err, sizeof(err)))
       return fail(ctx, ORRB_ERR_CUDA, "%s", err);
     if (p.shadow_nb && launch_shadow_neighbourhoods(q, stream, err, sizeof(err)))
       return fail(ctx, ORRB_ERR_CUDA, "%s", err);

@@ -14,6 +14,7 @@
 namespace orrb {
 
 constexpr int kMaxLights = 4;
+constexpr int kMaxShadowFaces = 6;  // shadow cameras per light (a cube map)
 constexpr int kMaxMaterials = 32;
 constexpr int kMeshletVerts = 64;
 constexpr int kMeshletTris = 128;
@@ -79,7 +80,8 @@ struct Params {
   float2* shadow_nb;         // [n_samples][4][R][R] or null: per texel over its 3 x 3 neighbourhood, the least
                              // depth > 0 (+inf if none) and, if all nine are inside and > 0, the largest (+inf)
   int32_t shadow_res;        // R, 0 without shadows
-  int32_t shadow_pass;       // this launch renders the shadow maps (images: sample * 4 + light)
+  int32_t shadow_faces;      // F, shadow cameras per light
+  int32_t shadow_pass;       // this launch renders the shadow maps (images: (sample * 4 + light) * F + face)
   // outputs (device, any may be null)
   uint8_t* rgb;
   float* depth;

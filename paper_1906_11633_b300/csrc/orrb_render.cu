@@ -94,12 +94,12 @@ struct ImageInfo {
 };
 
 // Shadows of the current image (the lookup instances; in dynamic shared memory right after the
-// span table, present only in launches with shadow maps): per casting light the
+// span table, present only in launches with shadow maps): per casting face of each light the
 // camera-to-shadow-camera map S V^-1 and the shadow camera's fx, fy, cx, cy, near, bias.
 struct ShadowInfo {
-  int cast[kMaxLights];
-  float sm[kMaxLights][12];
-  float si[kMaxLights][6];
+  int cast[kMaxLights][kMaxShadowFaces];
+  float sm[kMaxLights][kMaxShadowFaces][12];
+  float si[kMaxLights][kMaxShadowFaces][6];
 };
 
 struct CtaShared {
@@ -245,7 +245,8 @@ __device__ void block_exclusive_scan(int* a, int n, int* tmp) {
 // per-image set-up (camera, lights, materials, instance tables)
 // ---------------------------------------------------------------------------
 // track: (with tables) also start this image's tracker rows empty.
-// kPass: the shadow pass, whose image `cam` is the map of light cam % 4 of sample cam / 4.
+// kPass: the shadow pass, whose image `cam` is the map of face cam % F of light (cam / F) % 4 of
+// sample cam / (4 F).
 template <bool kPass = false>
 __device__ void setup_image(const Params& p, int cam, CtaShared& sh, int* mprefix, int* tprefix, int* mbegin,
                             bool tables, bool track = false) {
@@ -253,7 +254,7 @@ __device__ void setup_image(const Params& p, int cam, CtaShared& sh, int* mprefi
   const int tid = threadIdx.x;
   if (tid == 0) {
     im.cam = cam;
-    int s = kPass ? cam / kMaxLights : p.cam_sample[cam];
+    int s = kPass ? cam / (kMaxLights * p.shadow_faces) : p.cam_sample[cam];
     im.s = s;
     im.W = kPass ? p.shadow_res : p.cam_wh[cam * 2 + 0];
     im.H = kPass ? p.shadow_res : p.cam_wh[cam * 2 + 1];
@@ -307,7 +308,7 @@ __device__ void setup_image(const Params& p, int cam, CtaShared& sh, int* mprefi
     }
     im.n_lights = nl;
     im.light_type = lt;
-    if (kPass && cam % kMaxLights >= nl) im.valid = 0;  // no such light: no map
+    if (kPass && (cam / p.shadow_faces) % kMaxLights >= nl) im.valid = 0;  // no such light: no map
     sh.n_vis = 0;
     sh.n_big = 0;
     sh.next_tile = 0;
@@ -986,10 +987,6 @@ __device__ void shade(const CtaShared& sh, const float P[3], const float n[3], i
 // V^-1 = [R^T | -R^T t], every product and sum rounded to nearest in index order, so the
 // lookup below is the same fp32 computation wherever it runs.
 __device__ void shadow_setup(const Params& p, const ImageInfo& im, ShadowInfo& sd, int l) {
-  const float* si = p.shadow_intr + ((size_t)im.s * kMaxLights + l) * 6;
-  sd.cast[l] = l < im.n_lights && si[0] != 0.0f;
-  if (!sd.cast[l]) return;
-  const float* S = p.shadow_view + ((size_t)im.s * kMaxLights + l) * 12;
   const float* V = im.V;
   float Wi[12];
   for (int i = 0; i < 3; i++) {
@@ -997,13 +994,20 @@ __device__ void shadow_setup(const Params& p, const ImageInfo& im, ShadowInfo& s
     Wi[i * 4 + 3] = -__fadd_rn(__fadd_rn(__fmul_rn(V[0 * 4 + i], V[3]), __fmul_rn(V[1 * 4 + i], V[7])),
                                __fmul_rn(V[2 * 4 + i], V[11]));
   }
-  for (int i = 0; i < 3; i++)
-    for (int j = 0; j < 4; j++) {
-      float r = __fadd_rn(__fadd_rn(__fmul_rn(S[i * 4 + 0], Wi[0 * 4 + j]), __fmul_rn(S[i * 4 + 1], Wi[1 * 4 + j])),
-                          __fmul_rn(S[i * 4 + 2], Wi[2 * 4 + j]));
-      sd.sm[l][j + 4 * i] = j == 3 ? __fadd_rn(r, S[i * 4 + 3]) : r;
-    }
-  for (int k = 0; k < 6; k++) sd.si[l][k] = si[k];
+  for (int f = 0; f < kMaxShadowFaces; f++) {
+    const size_t c = ((size_t)im.s * kMaxLights + l) * p.shadow_faces + f;
+    const float* si = p.shadow_intr + c * 6;
+    sd.cast[l][f] = f < p.shadow_faces && l < im.n_lights && si[0] != 0.0f;
+    if (!sd.cast[l][f]) continue;
+    const float* S = p.shadow_view + c * 12;
+    for (int i = 0; i < 3; i++)
+      for (int j = 0; j < 4; j++) {
+        float r = __fadd_rn(__fadd_rn(__fmul_rn(S[i * 4 + 0], Wi[0 * 4 + j]), __fmul_rn(S[i * 4 + 1], Wi[1 * 4 + j])),
+                            __fmul_rn(S[i * 4 + 2], Wi[2 * 4 + j]));
+        sd.sm[l][f][j + 4 * i] = j == 3 ? __fadd_rn(r, S[i * 4 + 3]) : r;
+      }
+    for (int k = 0; k < 6; k++) sd.si[l][f][k] = si[k];
+  }
 }
 
 // The shadow factors of the casting lights at the G-buffer position P (whose three coordinates
@@ -1015,52 +1019,55 @@ __device__ void shadow_setup(const Params& p, const ImageInfo& im, ShadowInfo& s
 __device__ __forceinline__ int shadow_lookup(const Params& p, const ImageInfo& im, const ShadowInfo& sd,
                                              const float P[3], int mat, float vis[kMaxLights]) {
   const float P0 = P[0], P1 = P[1], P2 = P[2];
-  const int R = p.shadow_res;
+  const int R = p.shadow_res, F = p.shadow_faces;
   int word = mat;
 #pragma unroll
   for (int l = 0; l < kMaxLights; l++) {
     vis[l] = 1.0f;
-    if (!sd.cast[l]) continue;
-    const float* M = sd.sm[l];
-    const float* si = sd.si[l];
-    const float q2 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[8], P0), __fmul_rn(M[9], P1)), __fmul_rn(M[10], P2)), M[11]);
-    const float z = -q2;
-    if (!(z > si[4])) continue;
-    const float q0 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[0], P0), __fmul_rn(M[1], P1)), __fmul_rn(M[2], P2)), M[3]);
-    const float q1 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[4], P0), __fmul_rn(M[5], P1)), __fmul_rn(M[6], P2)), M[7]);
-    const float iw = __frcp_rn(z);
-    const float u = __fadd_rn(si[2], __fmul_rn(si[0], __fmul_rn(q0, iw)));
-    const float v = __fsub_rn(si[3], __fmul_rn(si[1], __fmul_rn(q1, iw)));
-    if (!(fabsf(u) < kGuardPx) || !(fabsf(v) < kGuardPx)) continue;
-    const int i0 = int(floorf(u)), j0 = int(floorf(v));
-    const float zb = __fsub_rn(z, si[5]);
-    const size_t m0 = ((size_t)im.s * kMaxLights + l) * R * R;
-    int k = -1;
-    if (p.shadow_nb && i0 >= 0 && j0 >= 0 && i0 < R && j0 < R) {  // one load settles lit and umbra points
-      const float2 e = __ldg(p.shadow_nb + m0 + (size_t)j0 * R + i0);
-      if (!(zb > e.x)) k = 0;  // no occupied tap is nearer than the point
-      else if (zb > e.y) k = 9;  // all nine occupied and nearer
-    }
-    if (k == 0) continue;
-    if (k < 0) {
-    k = 0;
-    const float* map = p.shadow_map + m0;
-    const bool col[3] = {i0 - 1 >= 0 && i0 - 1 < R, i0 >= 0 && i0 < R, i0 + 1 >= 0 && i0 + 1 < R};
-#pragma unroll
-    for (int b = -1; b <= 1; b++) {
-      const int j = j0 + b;
-      if (j < 0 || j >= R) continue;
-      const float* row = map + j * R + i0;  // (within a map, offsets fit 32 bits)
-#pragma unroll
-      for (int a = -1; a <= 1; a++) {
-        if (!col[a + 1]) continue;
-        const float d = __ldg(row + a);
-        k += d > 0.0f && zb > d;
+    for (int f = 0; f < F; f++) {  // the first casting face whose map contains the point decides
+      if (!sd.cast[l][f]) continue;
+      const float* M = sd.sm[l][f];
+      const float* si = sd.si[l][f];
+      const float q2 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[8], P0), __fmul_rn(M[9], P1)), __fmul_rn(M[10], P2)), M[11]);
+      const float z = -q2;
+      if (!(z > si[4])) continue;
+      const float q0 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[0], P0), __fmul_rn(M[1], P1)), __fmul_rn(M[2], P2)), M[3]);
+      const float q1 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[4], P0), __fmul_rn(M[5], P1)), __fmul_rn(M[6], P2)), M[7]);
+      const float iw = __frcp_rn(z);
+      const float u = __fadd_rn(si[2], __fmul_rn(si[0], __fmul_rn(q0, iw)));
+      const float v = __fsub_rn(si[3], __fmul_rn(si[1], __fmul_rn(q1, iw)));
+      if (!(fabsf(u) < kGuardPx) || !(fabsf(v) < kGuardPx)) continue;
+      const int i0 = int(floorf(u)), j0 = int(floorf(v));
+      if (i0 < 0 || j0 < 0 || i0 >= R || j0 >= R) continue;
+      const float zb = __fsub_rn(z, si[5]);
+      const size_t m0 = (((size_t)im.s * kMaxLights + l) * F + f) * R * R;
+      int k = -1;
+      if (p.shadow_nb) {  // one load settles lit and umbra points
+        const float2 e = __ldg(p.shadow_nb + m0 + (size_t)j0 * R + i0);
+        if (!(zb > e.x)) k = 0;  // no occupied tap is nearer than the point
+        else if (zb > e.y) k = 9;  // all nine occupied and nearer
       }
+      if (k < 0) {
+        k = 0;
+        const float* map = p.shadow_map + m0;
+        const bool col[3] = {i0 - 1 >= 0, true, i0 + 1 < R};
+#pragma unroll
+        for (int b = -1; b <= 1; b++) {
+          const int jj = j0 + b;
+          if (jj < 0 || jj >= R) continue;
+          const float* row = map + jj * R + i0;  // (within a map, offsets fit 32 bits)
+#pragma unroll
+          for (int a = -1; a <= 1; a++) {
+            if (!col[a + 1]) continue;
+            const float d = __ldg(row + a);
+            k += d > 0.0f && zb > d;
+          }
+        }
+      }
+      vis[l] = kPcfFactor[k];
+      word |= k << (8 + 4 * l);
+      break;
     }
-    }
-    vis[l] = kPcfFactor[k];
-    word |= k << (8 + 4 * l);
   }
   return word;
 }
@@ -1653,10 +1660,13 @@ __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
 // ---------------------------------------------------------------------------
 // plain: three launches per sample; scratch slot = camera index within the sample
 // ---------------------------------------------------------------------------
-// (in the shadow pass: the map of light blockIdx.x of the sample)
+// (in the shadow pass: the sample's map blockIdx.x, light-major then face)
 __device__ inline int plain_cam(const Params& p) {
   const int s = p.plain_sample;
-  if (p.shadow_pass) return blockIdx.x < unsigned(kMaxLights) ? s * kMaxLights + int(blockIdx.x) : -1;
+  if (p.shadow_pass) {
+    const int per = kMaxLights * p.shadow_faces;
+    return int(blockIdx.x) < per ? s * per + int(blockIdx.x) : -1;
+  }
   const int c = p.cam_offset[s] + blockIdx.x;
   return c < p.cam_offset[s + 1] ? c : -1;
 }
@@ -1733,10 +1743,12 @@ __global__ void __launch_bounds__(512, 2) plain_raster_kernel(Params p) {
 // One block per map row (blockIdx.x) and map (blockIdx.y, striding by gridDim.y); threads
 // stride along the row.
 __global__ void __launch_bounds__(256) shadow_neighbourhood_kernel(Params p) {
-  const int R = p.shadow_res, y = blockIdx.x, n_maps = p.n_samples * kMaxLights;
+  const int R = p.shadow_res, y = blockIdx.x, F = p.shadow_faces, n_maps = p.n_samples * kMaxLights * F;
   const float inf = __int_as_float(0x7f800000);
   for (int m = blockIdx.y; m < n_maps; m += gridDim.y) {
-    if (m % kMaxLights >= p.light_meta[(m / kMaxLights) * 2]) continue;  // no such light: no map
+    const int sl = m / F;  // sample * 4 + light
+    if (sl % kMaxLights >= p.light_meta[(sl / kMaxLights) * 2] || p.shadow_intr[(size_t)m * 6] == 0.0f)
+      continue;  // no such light, or a face that casts none: no map
     const float* map = p.shadow_map + (size_t)m * R * R;
     const float* rows[3] = {map + (y > 0 ? y - 1 : 0) * R, map + y * R, map + (y + 1 < R ? y + 1 : y) * R};
     const bool row_in[3] = {y > 0, true, y + 1 < R};
@@ -1791,7 +1803,7 @@ int noalloc_scratch(int device, void** ptr, size_t* bytes) {
 }
 
 int launch_shadow_neighbourhoods(const Params& p, void* stream, char* err, size_t errlen) {
-  const int n_maps = p.n_samples * kMaxLights;
+  const int n_maps = p.n_samples * kMaxLights * p.shadow_faces;
   const dim3 grid(unsigned(p.shadow_res), unsigned(n_maps < 65535 ? n_maps : 65535));
   shadow_neighbourhood_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(p);
   const cudaError_t e = cudaGetLastError();

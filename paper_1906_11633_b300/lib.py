@@ -38,7 +38,8 @@ class orrb_mesh_desc(C.Structure):
 class orrb_batch_shape(C.Structure):
     _fields_ = [("n_samples", C.c_int32), ("n_cams", C.c_int32), ("max_tris_per_sample", C.c_int32),
                 ("max_inst_per_sample", C.c_int32), ("max_cams_per_sample", C.c_int32), ("max_width", C.c_int32),
-                ("max_height", C.c_int32), ("total_pixels", C.c_int64), ("shadow_res", C.c_int32)]
+                ("max_height", C.c_int32), ("total_pixels", C.c_int64), ("shadow_res", C.c_int32),
+                ("shadow_faces", C.c_int32)]
 
 
 class orrb_batch_desc(C.Structure):

@@ -41,7 +41,8 @@ def batch_shape(batch) -> L.orrb_batch_shape:
         max_width=int(batch.cam_wh[:, 0].max()) if batch.n_cams else 1,
         max_height=int(batch.cam_wh[:, 1].max()) if batch.n_cams else 1,
         total_pixels=batch.total_pixels,
-        shadow_res=int(getattr(batch, "shadow_res", 0) or 0) if getattr(batch, "shadow_view", None) is not None else 0)
+        shadow_res=int(getattr(batch, "shadow_res", 0) or 0) if getattr(batch, "shadow_view", None) is not None else 0,
+        shadow_faces=int(getattr(batch, "shadow_faces", 1) or 1))
 
 
 @dataclass
@@ -154,9 +155,10 @@ class Renderer:
         return out
 
     def alloc_shadow_maps(self, db: DeviceBatch) -> torch.Tensor:
-        """The shadow-map output [n_samples, 4, R, R] of a batch with shadows."""
-        R = int(db.shape.shadow_res)
-        return torch.empty((int(db.shape.n_samples), L.ORRB_MAX_LIGHTS, R, R), dtype=torch.float32, device=self.device)
+        """The shadow-map output [n_samples, 4, F, R, R] of a batch with shadows."""
+        R, F = int(db.shape.shadow_res), max(1, int(db.shape.shadow_faces))
+        return torch.empty((int(db.shape.n_samples), L.ORRB_MAX_LIGHTS, F, R, R), dtype=torch.float32,
+                           device=self.device)
 
     def render(self, db: DeviceBatch, out=None, cfg: Optional[L.orrb_config] = None, rgb_linear: bool = False,
                gbuffer: bool = False, stream=None, workspace: Optional[torch.Tensor] = None, tracker: bool = False):

@@ -390,15 +390,20 @@ def test_lights_that_light_nothing_are_flagged(hand_renderer, oracle):
         compare(to_numpy(out), oracle.render(bad, debug=True), "dark lights")
 
 
-@pytest.mark.parametrize("mode", [L.ORRB_MODE_FUSED, L.ORRB_MODE_PLAIN])
-def test_shadow_maps_and_lookups_match_oracle(hand_renderer, oracle, mode):
-    """The benchmark-like scene with shadow maps: every map of a casting light bit-identical to the
-    oracle's (the same rasterisation, back faces), every G-buffer material word (slot and shadowed
-    taps per light) identical, and the channels within the contract; maps of lights that cast
-    none are left untouched."""
-    b = sg.benchmark_batch(31, np.arange(8), res=96, shadow_res=128)
+@pytest.mark.parametrize("mode,kind", [(L.ORRB_MODE_FUSED, "spot"), (L.ORRB_MODE_PLAIN, "spot"),
+                                       (L.ORRB_MODE_FUSED, "cube"), (L.ORRB_MODE_PLAIN, "cube")])
+def test_shadow_maps_and_lookups_match_oracle(hand_renderer, oracle, mode, kind):
+    """Shadow maps of the benchmark-like scene's spot lights (one face each) and of the hand scene's
+    point lights (six cube faces each): every map of a casting face bit-identical to the oracle's
+    (the same rasterisation, back faces), every G-buffer material word (slot and shadowed taps per
+    light) identical, and the channels within the contract; maps of lights that cast none are
+    left untouched."""
+    if kind == "spot":
+        b = sg.benchmark_batch(31, np.arange(8), res=96, shadow_res=128)
+    else:
+        b = sg.hand_batch(32, np.arange(8), res=96, shadow_res=64)
     b = b.with_params(light_meta=b.light_meta.copy())
-    b.light_meta[5, 0] = 2                              # a sample with one light fewer
+    b.light_meta[5, 0] = max(1, b.light_meta[5, 0] - 1)   # a sample with one light fewer
     o = oracle.render(b, debug=True, gbuffer=True)
     r = hand_renderer
     db = r.upload(b)
@@ -411,10 +416,10 @@ def test_shadow_maps_and_lookups_match_oracle(hand_renderer, oracle, mode):
     cast = np.arange(4)[None, :] < b.light_meta[:, :1]
     np.testing.assert_array_equal(g["shadow_map"][cast], o["shadow_map"][cast])
     assert (g["shadow_map"][~cast] == -1.0).all()
-    assert (o["shadow_map"][cast] > 0).mean() > 0.005
+    assert (o["shadow_map"][cast] > 0).mean() > 0.001
     np.testing.assert_array_equal(g["gbuffer"][6].view(np.int32), o["gb_mat"])
     same = g["depth"] == o["depth"]                     # the lookup's input: the G-buffer position, bit for bit
     np.testing.assert_array_equal(g["gbuffer"][0:3].T[same], o["gb_pos"][same])
     k = (o["gb_mat"][o["gb_mat"] >= 0] >> 8) & 0xfff
-    assert (k > 0).mean() > 0.05                        # shadows fall on a good share of the pixels
+    assert (k > 0).mean() > 0.01                        # shadows fall on a share of the pixels
     compare(g, o, "shadows")
