@@ -41,6 +41,7 @@ N_CAMS = 3
 RES = 200
 SEED = 0
 SHADOW_RES = 256    # side of the spot lights' shadow maps in the shadow workload
+CUBE_RES = 128      # side of the point lights' cube-map faces in the cube workload
 BYTES_PER_PX = 3 + 4 + 6 + 1           # rgb u8x3, depth f32, normal f16x3, seg u8
 CONFIG = {"workload": "hand-like scene: 256 samples x 3 cameras x 200x200, 24 capsule links + block + table, "
                       "1-4 point lights, 4 channels", "global_batch": N_SAMPLES, "cameras": N_CAMS,
@@ -642,9 +643,33 @@ def run_shadow(args, world, rank, local):
     line = {"workload": "shadow", "metric": "samples/s, benchmark-like scene with shadow-casting spot lights",
             "value": world * N_SAMPLES / (sms / 1e3), "unit": UNIT, "n_gpus": world, "ms_per_step": sms,
             "unshadowed_ms_per_step": nms, "overhead": sms / nms - 1.0, "device_status": r.status(),
-            "gpu_launches_per_step": 2,
+            "gpu_launches_per_step": 3,
             "config": {"samples": N_SAMPLES, "cameras": N_CAMS, "resolution": RES, "shadow_maps": n_maps,
                        "shadow_res": SHADOW_RES, "pcf": "3x3 taps", "lights": "3 spot lights", "grading": True}}
+    print(json.dumps(line), flush=True)
+
+
+def run_cube(args, world, rank, local):
+    """The hand scene with its 1-4 point lights casting cube-map shadows (six 128 x 128 faces per
+    light, rendered every step); kernel time against the same batch without shadows."""
+    import torch
+    from paper_1906_11633_b300 import scenegen as sg
+    from paper_1906_11633_b300.render import Renderer
+    torch.cuda.set_device(local)
+    ids = shard_samples(rank, world, N_SAMPLES)
+    batch = sg.hand_batch(SEED, ids, res=RES, n_cams=N_CAMS, shadow_res=CUBE_RES)
+    r = Renderer(batch.meshes, device=local)
+    sms = _timed_renders(r, r.upload(batch), args, world)
+    nms = _timed_renders(r, r.upload(batch.with_params(shadow_view=None, shadow_intr=None, shadow_res=0)), args, world)
+    if rank != 0:
+        return
+    n_maps = int(batch.light_meta[:, 0].sum()) * 6
+    line = {"workload": "cube", "metric": "samples/s, hand scene with cube-map shadows of its point lights",
+            "value": world * N_SAMPLES / (sms / 1e3), "unit": UNIT, "n_gpus": world, "ms_per_step": sms,
+            "unshadowed_ms_per_step": nms, "overhead": sms / nms - 1.0, "device_status": r.status(),
+            "gpu_launches_per_step": 3,
+            "config": {"samples": N_SAMPLES, "cameras": N_CAMS, "resolution": RES, "shadow_maps": n_maps,
+                       "shadow_res": CUBE_RES, "faces_per_light": 6, "pcf": "3x3 taps"}}
     print(json.dumps(line), flush=True)
 
 
@@ -694,7 +719,7 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the fused kernel from an ncu capture of this build")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["hand", "uneven", "diff", "serve", "grade", "track", "spot", "shadow"], default="hand",
+    ap.add_argument("--workload", choices=["hand", "uneven", "diff", "serve", "grade", "track", "spot", "shadow", "cube"], default="hand",
                     help="hand: the headline line; the others print supplementary lines")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--samples", type=int, default=N_SAMPLES,
@@ -721,6 +746,8 @@ def main():
         run_spot(args, world, rank, local)
     elif args.workload == "shadow":
         run_shadow(args, world, rank, local)
+    elif args.workload == "cube":
+        run_cube(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:
