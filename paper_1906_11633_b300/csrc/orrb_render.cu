@@ -1740,37 +1740,54 @@ __global__ void __launch_bounds__(512, 2) plain_raster_kernel(Params p) {
 // depth > 0 (+inf if none) and, when all nine are inside and occupied, the largest (+inf
 // otherwise).  A point with depth-less-bias zb is then unshadowed by every tap when zb <= the
 // least, and shadowed by all nine when zb > the largest; only the others count taps.
-// One block per map row (blockIdx.x) and map (blockIdx.y, striding by gridDim.y); threads
-// stride along the row.
-__global__ void __launch_bounds__(256) shadow_neighbourhood_kernel(Params p) {
-  const int R = p.shadow_res, y = blockIdx.x, F = p.shadow_faces, n_maps = p.n_samples * kMaxLights * F;
+// Each thread owns one column x of one map and walks down it, keeping the 3-texel summaries
+// (least occupied depth, largest depth, all three occupied) of the rows above, at and below in
+// registers: three loads per texel.  A block covers 128 columns of one map (blocks stride over
+// (map, column block) pairs).
+struct RowTriple {
+  float lo, hi;
+  bool full;
+};
+
+__device__ __forceinline__ RowTriple row_triple(const float* map, int R, int x, int y) {
+  RowTriple t{__int_as_float(0x7f800000), 0.0f, y >= 0 && y < R && x > 0 && x + 1 < R};
+  if (y < 0 || y >= R) return t;
+  const float* row = map + (size_t)y * R;
+#pragma unroll
+  for (int a = -1; a <= 1; a++) {
+    const int xx = x + a;
+    if (xx < 0 || xx >= R) continue;
+    const float d = __ldg(row + xx);
+    if (d > 0.0f) {
+      t.lo = fminf(t.lo, d);
+      t.hi = fmaxf(t.hi, d);
+    } else {
+      t.full = false;
+    }
+  }
+  return t;
+}
+
+__global__ void __launch_bounds__(128) shadow_neighbourhood_kernel(Params p) {
+  const int R = p.shadow_res, F = p.shadow_faces, n_maps = p.n_samples * kMaxLights * F;
+  const int col_blocks = (R + 127) / 128;
   const float inf = __int_as_float(0x7f800000);
-  for (int m = blockIdx.y; m < n_maps; m += gridDim.y) {
+  for (long long w = blockIdx.x; w < (long long)n_maps * col_blocks; w += gridDim.x) {
+    const int m = int(w / col_blocks), x = int(w % col_blocks) * 128 + int(threadIdx.x);
     const int sl = m / F;  // sample * 4 + light
     if (sl % kMaxLights >= p.light_meta[(sl / kMaxLights) * 2] || p.shadow_intr[(size_t)m * 6] == 0.0f)
       continue;  // no such light, or a face that casts none: no map
+    if (x >= R) continue;
     const float* map = p.shadow_map + (size_t)m * R * R;
-    const float* rows[3] = {map + (y > 0 ? y - 1 : 0) * R, map + y * R, map + (y + 1 < R ? y + 1 : y) * R};
-    const bool row_in[3] = {y > 0, true, y + 1 < R};
-    float2* out = p.shadow_nb + (size_t)m * R * R + (size_t)y * R;
-    for (int x = threadIdx.x; x < R; x += blockDim.x) {
-      float lo = inf, hi = 0.0f;
-      bool full = row_in[0] && row_in[2] && x > 0 && x + 1 < R;
-      for (int b = 0; b < 3; b++) {
-        if (!row_in[b]) continue;
-        for (int a = -1; a <= 1; a++) {
-          const int xx = x + a;
-          if (xx < 0 || xx >= R) continue;
-          const float d = __ldg(rows[b] + xx);
-          if (d > 0.0f) {
-            lo = fminf(lo, d);
-            hi = fmaxf(hi, d);
-          } else {
-            full = false;
-          }
-        }
-      }
-      out[x] = make_float2(lo, full ? hi : inf);
+    float2* out = p.shadow_nb + (size_t)m * R * R + x;
+    RowTriple a = row_triple(map, R, x, -1), b = row_triple(map, R, x, 0);
+#pragma unroll 4
+    for (int y = 0; y < R; y++) {
+      const RowTriple c = row_triple(map, R, x, y + 1);
+      const float lo = fminf(fminf(a.lo, b.lo), c.lo), hi = fmaxf(fmaxf(a.hi, b.hi), c.hi);
+      out[(size_t)y * R] = make_float2(lo, a.full && b.full && c.full ? hi : inf);
+      a = b;
+      b = c;
     }
   }
 }
@@ -1804,8 +1821,9 @@ int noalloc_scratch(int device, void** ptr, size_t* bytes) {
 
 int launch_shadow_neighbourhoods(const Params& p, void* stream, char* err, size_t errlen) {
   const int n_maps = p.n_samples * kMaxLights * p.shadow_faces;
-  const dim3 grid(unsigned(p.shadow_res), unsigned(n_maps < 65535 ? n_maps : 65535));
-  shadow_neighbourhood_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(p);
+  const long long work = (long long)n_maps * ((p.shadow_res + 127) / 128);
+  shadow_neighbourhood_kernel<<<unsigned(work < (1 << 30) ? work : (1 << 30)), 128, 0,
+                                static_cast<cudaStream_t>(stream)>>>(p);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     snprintf(err, errlen, "shadow neighbourhood launch failed: %s", cudaGetErrorString(e));
