@@ -423,3 +423,30 @@ def test_shadow_maps_and_lookups_match_oracle(hand_renderer, oracle, mode, kind)
     k = (o["gb_mat"][o["gb_mat"] >= 0] >> 8) & 0xfff
     assert (k > 0).mean() > 0.01                        # shadows fall on a share of the pixels
     compare(g, o, "shadows")
+
+
+@pytest.mark.parametrize("grading", [True, False])
+@pytest.mark.parametrize("shadows", [True, False])
+def test_option_combinations_with_tracker_rows_match_oracle(hand_renderer, oracle, grading, shadows):
+    """Tracker rows together with spot lights, emission, colour grading and shadow maps, each
+    combination its own kernel instance, fused and plain: channels, G-buffer words, maps and
+    tracker rows against the oracle."""
+    b = sg.benchmark_batch(41, np.arange(6), res=80, grading=grading, shadow_res=96 if shadows else 0)
+    o = oracle.render(b, debug=True, gbuffer=True, tracker=True)
+    cast = np.arange(4)[None, :] < b.light_meta[:, :1]
+    for cfg in (config(), config(mode=L.ORRB_MODE_PLAIN)):
+        g = render_np(hand_renderer, b, cfg, gbuffer=True, tracker=True)
+        compare(g, o, "options")
+        np.testing.assert_array_equal(g["tracker"], o["tracker"])
+        np.testing.assert_array_equal(g["gbuffer"][6].view(np.int32), o["gb_mat"])
+        if shadows:
+            np.testing.assert_array_equal(g["shadow_map"][cast], o["shadow_map"][cast])
+
+
+def test_graded_tracked_point_lit_batch_matches_oracle(hand_renderer, oracle):
+    """Colour grading with tracker rows and plain point lights (the grading-and-tracker instance)."""
+    b = sg.hand_batch(43, np.arange(4), res=80, grading=True)
+    o = oracle.render(b, debug=True, tracker=True)
+    g = render_np(hand_renderer, b, tracker=True)
+    compare(g, o, "graded and tracked")
+    np.testing.assert_array_equal(g["tracker"], o["tracker"])
