@@ -97,8 +97,10 @@ def fp32_peak_tflops(sms: int, mhz: float) -> float:
 
 def shading_flops(n_visible: int, n_lit: int, n_light_terms: int) -> float:
     """Algorithmic FP32 operations of the shading step over visible pixels, counted from the defined
-    arithmetic (each +, -, x, /, sqrt, max, floor, conversion, exp2, log2 = 1; enumeration in DESIGN.md):
-    76 per visible pixel + 31 per (pixel, light) + 20 per (pixel, light) with n.L > 0 (specular lobe)."""
+    arithmetic (each +, -, x, /, sqrt, max, floor, conversion, exp2, log2 = 1): 76 per visible pixel
+    (view vector, normal, ambient and exposure terms, clamp and quantisation of three channels),
+    31 per (pixel, light) (light vector, distance, falloff, n.L, diffuse sum) and 20 more per
+    (pixel, light) with n.L > 0 (half vector, n.H and the specular lobe)."""
     return float(76 * n_visible + 31 * n_light_terms + 20 * n_lit)
 
 
@@ -717,7 +719,7 @@ def main():
     ap.add_argument("--tile-h", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--traffic", type=float, default=None,
-                    help="DRAM bytes per launch of the fused kernel from an ncu capture of this build")
+                    help="DRAM bytes per launch of the fused kernel from an ncu capture of the same kernel source")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["hand", "uneven", "diff", "serve", "grade", "track", "spot", "shadow", "cube"], default="hand",
                     help="hand: the headline line; the others print supplementary lines")
