@@ -450,3 +450,18 @@ def test_graded_tracked_point_lit_batch_matches_oracle(hand_renderer, oracle):
     g = render_np(hand_renderer, b, tracker=True)
     compare(g, o, "graded and tracked")
     np.testing.assert_array_equal(g["tracker"], o["tracker"])
+
+
+@pytest.mark.parametrize("mode", [L.ORRB_MODE_FUSED, L.ORRB_MODE_PLAIN])
+def test_ragged_shadow_maps_match_oracle(hand_renderer, oracle, mode):
+    """Shadow maps of a ragged side (257: a partial tile column in the shadow pass and a one-column
+    block in the neighbourhood table) with camera images of a ragged width, against the oracle."""
+    b = sg.benchmark_batch(47, np.arange(3), res=72, grading=False, shadow_res=257)
+    o = oracle.render(b, debug=True, gbuffer=True)
+    g = render_np(hand_renderer, b, config(mode=mode, tile_w=64, tile_h=2), gbuffer=True)
+    cast = np.arange(4)[None, :] < b.light_meta[:, :1]
+    np.testing.assert_array_equal(g["shadow_map"][cast], o["shadow_map"][cast])
+    np.testing.assert_array_equal(g["gbuffer"][6].view(np.int32), o["gb_mat"])
+    k = (o["gb_mat"][o["gb_mat"] >= 0] >> 8) & 0xfff
+    assert ((k & 15) % 9 != 0).any()                   # partly shadowed points: the taps were counted
+    compare(g, o, "ragged shadows")
