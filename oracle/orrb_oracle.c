@@ -79,15 +79,17 @@
  *      each light has F shadow cameras ("faces": one for a spot light, six
  *      cube faces for a point light); face f of light l of sample s casts
  *      when l < the light count and its camera (view S, intrinsics fx, fy,
- *      cx, cy, near, bias) has fx != 0.  Its R x R map holds, per pixel, the
- *      depth seen from that camera (steps 2-8 with it, perspective) of the
- *      nearest BACK face -- each triangle's second and third vertices swapped
+ *      cx, cy, near, bias, type: 0 perspective, 1 orthographic as for a
+ *      directional light) has fx != 0.  Its R x R map holds, per pixel, the
+ *      depth seen from that camera (steps 2-8 with it) of the nearest BACK
+ *      face -- each triangle's second and third vertices swapped
  *      before step 5, so front faces are culled -- and 0 where there is none.
  *  16  shadow lookup in step 10: for a camera pixel with surface and each
  *      light with a casting face, in fp32 with every operation rounded
  *      separately: P as in step 9; for the faces in order, M = S V^-1 (V^-1 =
  *      [R^T | -R^T t], products summed in index order), q = M P, z = -q_z,
- *      u = cx + fx (q_x (1/z)), v = cy - fy (q_y (1/z)); the first face with
+ *      u = cx + fx (q_x (1/z)), v = cy - fy (q_y (1/z)) (orthographic: u =
+ *      cx + fx q_x, v = cy - fy q_y); the first face with
  *      z > near and (floor(u), floor(v)) inside its map decides (none: the
  *      light is unshadowed): over the 3 x 3 texels (floor(u) + a, floor(v) +
  *      b), a, b in {-1, 0, 1}, inside the map, count k those with map depth
@@ -437,7 +439,7 @@ static int64_t shadow_index(const orc_batch* b, int32_t s, int l, int f) {
 /* face f of light l of sample s casts a shadow (step 15) */
 static int casts_shadow(const orc_batch* b, int32_t s, int l, int f) {
   return b->shadow_view && b->shadow_intr && b->shadow_res > 0 && l < light_count(b, s) &&
-         b->shadow_intr[shadow_index(b, s, l, f) * 6 + 0] != 0.0f;
+         b->shadow_intr[shadow_index(b, s, l, f) * 7 + 0] != 0.0f;
 }
 
 /* M = S V^-1 for the rigid camera view V = [R | t] (step 16) */
@@ -461,9 +463,15 @@ static int shadow_taps(const float M[12], const float* si, const float* map, int
   for (int i = 0; i < 3; i++) q[i] = ((M[i * 4 + 0] * P[0] + M[i * 4 + 1] * P[1]) + M[i * 4 + 2] * P[2]) + M[i * 4 + 3];
   float z = -q[2];
   if (!(z > si[4])) return -1;
-  float iw = 1.0f / z;
-  float u = si[2] + si[0] * (q[0] * iw);
-  float v = si[3] - si[1] * (q[1] * iw);
+  float u, v;
+  if (si[6] != 0.0f) { /* orthographic */
+    u = si[2] + si[0] * q[0];
+    v = si[3] - si[1] * q[1];
+  } else {
+    float iw = 1.0f / z;
+    u = si[2] + si[0] * (q[0] * iw);
+    v = si[3] - si[1] * (q[1] * iw);
+  }
   if (!(fabsf(u) < GUARD_PX) || !(fabsf(v) < GUARD_PX)) return -1;
   int32_t i0 = (int32_t)floorf(u), j0 = (int32_t)floorf(v);
   if (i0 < 0 || j0 < 0 || i0 >= R || j0 >= R) return -1;
@@ -691,7 +699,7 @@ static int render_image(const orc_meshes* me, const orc_batch* b, int32_t c, con
         for (int f = 0; f < F && k < 0; f++) { /* the first face whose map contains the point */
           if (!cast[l * F + f]) continue;
           const int64_t si = shadow_index(b, s, l, f);
-          k = shadow_taps(Msh[l * F + f], b->shadow_intr + si * 6,
+          k = shadow_taps(Msh[l * F + f], b->shadow_intr + si * 7,
                           b->shadow_map + si * b->shadow_res * b->shadow_res, b->shadow_res, P);
         }
         if (k <= 0) continue;
@@ -733,7 +741,8 @@ int orc_render_shadow_maps(const orc_meshes* m, const orc_batch* b, int32_t s_be
       for (int f = 0; f < shadow_faces(b); f++) {
         if (!casts_shadow(b, s, l, f)) continue;
         const int64_t si = shadow_index(b, s, l, f);
-        visibility(m, b, s, b->shadow_view + si * 12, b->shadow_intr + si * 6, 0, R, R, 1, px, NULL);
+        const float* in = b->shadow_intr + si * 7;
+        visibility(m, b, s, b->shadow_view + si * 12, in, in[6] != 0.0f, R, R, 1, px, NULL);
         float* map = maps + si * R * R;
         for (int64_t i = 0; i < (int64_t)R * R; i++) map[i] = px[i].key < 0 ? 0.0f : px[i].depth;
       }

@@ -71,7 +71,8 @@ typedef struct {
   const float* light_spot;      /* [S][4][5] spot cones (step 10), or NULL */
   const float* emission;        /* [S][32] material emission (step 10), or NULL for none */
   const float* shadow_view;     /* [S][4][F][3][4] shadow cameras of each light (step 15), or NULL */
-  const float* shadow_intr;     /* [S][4][F][6] fx, fy, cx, cy, near, bias; fx == 0: no shadow */
+  const float* shadow_intr;     /* [S][4][F][7] fx, fy, cx, cy, near, bias, type (0 persp, 1 ortho);
+                                   fx == 0: no shadow */
   const float* shadow_map;      /* [S][4][F][R][R] maps of step 15, read by step 16 (or NULL) */
   int32_t shadow_res;           /* R, 0 for no shadows */
   int32_t shadow_faces;         /* F, shadow cameras per light (1 spot, 6 cube); 0 is read as 1 */

@@ -248,9 +248,10 @@ class Batch:
     light_spot: Optional[np.ndarray] = None
     # [B, 32] float32 material emission e (the emitted colour is e * albedo), or None for none
     emission: Optional[np.ndarray] = None
-    # shadows: per light shadow_faces perspective shadow cameras (one for a spot light, six cube
-    # faces for a point light), views [B, 4, F, 3, 4] (camera-from-world) and intrinsics
-    # [B, 4, F, 6] (fx, fy, cx, cy, near, depth bias; fx == 0: that face casts none), rendered
+    # shadows: per light shadow_faces shadow cameras (one for a spot light, six cube faces for a
+    # point light, one orthographic for a directional light), views [B, 4, F, 3, 4]
+    # (camera-from-world) and intrinsics [B, 4, F, 7] (fx, fy, cx, cy, near, depth bias, type:
+    # 0 perspective, 1 orthographic; fx == 0: that face casts none), rendered
     # into square maps of side shadow_res; None / 0 for no shadows
     shadow_view: Optional[np.ndarray] = None
     shadow_intr: Optional[np.ndarray] = None
@@ -326,7 +327,7 @@ def concat_batches(batches: Sequence[Batch]) -> Batch:
         shadow_view=_concat_opt(batches, "shadow_view",
                                 lambda n: np.zeros((n, MAX_LIGHTS, _shadow_kind(batches)[1], 3, 4), np.float32)),
         shadow_intr=_concat_opt(batches, "shadow_intr",
-                                lambda n: np.zeros((n, MAX_LIGHTS, _shadow_kind(batches)[1], 6), np.float32)),
+                                lambda n: np.zeros((n, MAX_LIGHTS, _shadow_kind(batches)[1], 7), np.float32)),
         shadow_res=_shadow_kind(batches)[0],
         shadow_faces=_shadow_kind(batches)[1],
     )
@@ -449,7 +450,9 @@ def tiny_meshes() -> List[Mesh]:
     return [plane_mesh(5.0, 5.0), box_mesh(0.5, per_face_material=False)]
 
 
-def tiny_batch(seed: int, n_samples: int = 8, res: int = 64, meshes=None) -> Batch:
+def tiny_batch(seed: int, n_samples: int = 8, res: int = 64, meshes=None, shadow_res: int = 0) -> Batch:
+    """The tiny workload; with `shadow_res` > 0 its directional light casts shadows from an
+    orthographic map of that side over the central 6 x 6 m of the plane."""
     meshes = meshes if meshes is not None else tiny_meshes()
     ids = np.arange(n_samples, dtype=np.int64)
     B = n_samples
@@ -489,7 +492,19 @@ def tiny_batch(seed: int, n_samples: int = 8, res: int = 64, meshes=None) -> Bat
         ambient=np.zeros((B, 3), np.float32),
         background=np.zeros((B, 3), np.float32),
         sample_ids=ids,
+        **(_directional_shadows(light, shadow_res) if shadow_res > 0 else {}),
     )
+
+
+def _directional_shadows(light, res):
+    """An orthographic shadow camera for light 0 (directional) of every tiny sample."""
+    B = len(light)
+    view, intr = directional_shadow_camera(light[0, 0, :3], (0.0, 0.0, 0.5), 3.0, res)
+    sv = np.zeros((B, MAX_LIGHTS, 1, 3, 4))
+    si = np.zeros((B, MAX_LIGHTS, 1, 7))
+    sv[:, 0, 0], si[:, 0, 0] = view, intr
+    return dict(shadow_view=sv.astype(np.float32), shadow_intr=si.astype(np.float32), shadow_res=int(res),
+                shadow_faces=1)
 
 
 # --------------------------------------------------------------------------
@@ -683,7 +698,7 @@ def _cube_shadows(light, meta, res):
     sv = np.where(on[..., None, None, None], sv, 0.0)
     si = np.where(on[..., None, None], si, 0.0)
     return dict(shadow_view=sv.reshape(B, MAX_LIGHTS, 6, 3, 4).astype(np.float32),
-                shadow_intr=si.reshape(B, MAX_LIGHTS, 6, 6).astype(np.float32), shadow_res=int(res), shadow_faces=6)
+                shadow_intr=si.reshape(B, MAX_LIGHTS, 6, 7).astype(np.float32), shadow_res=int(res), shadow_faces=6)
 
 
 # --------------------------------------------------------------------------
@@ -796,7 +811,7 @@ def spot_shadow_cameras(pos, axis, cos_outer, res: int, near: float = 0.05, bias
     half = np.minimum(np.arccos(np.clip(cos_outer, -1.0, 1.0)) * margin, np.radians(80.0))
     fx = 0.5 * res / np.tan(half)
     intr = np.stack([fx, fx, np.full_like(fx, 0.5 * res), np.full_like(fx, 0.5 * res), np.full_like(fx, near),
-                     np.full_like(fx, bias)], -1)
+                     np.full_like(fx, bias), np.zeros_like(fx)], -1)
     return view_matrix(R, pos), intr
 
 
@@ -805,7 +820,7 @@ CUBE_FACES = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], 
 
 def point_shadow_cameras(pos, res: int, near: float = 0.02, bias: float = 0.004):
     """Six cube-face shadow cameras per point light (looking along +x, -x, +y, -y, +z, -z with
-    90 deg fields of view).  pos [..., 3] -> views [..., 6, 3, 4], intrinsics [..., 6, 6]."""
+    90 deg fields of view).  pos [..., 3] -> views [..., 6, 3, 4], intrinsics [..., 6, 7]."""
     pos = np.asarray(pos, np.float64)
     views, intr = [], []
     for d in CUBE_FACES:
@@ -815,9 +830,25 @@ def point_shadow_cameras(pos, res: int, near: float = 0.02, bias: float = 0.004)
         r = r / np.linalg.norm(r, axis=-1, keepdims=True)
         R = np.stack([r, np.cross(r, f), -f], axis=-2)
         views.append(view_matrix(R, pos))
-        intr.append(np.broadcast_to(np.array([0.5 * res, 0.5 * res, 0.5 * res, 0.5 * res, near, bias]),
-                                    pos.shape[:-1] + (6,)))
+        intr.append(np.broadcast_to(np.array([0.5 * res, 0.5 * res, 0.5 * res, 0.5 * res, near, bias, 0.0]),
+                                    pos.shape[:-1] + (7,)))
     return np.stack(views, axis=-3), np.stack(intr, axis=-2)
+
+
+def directional_shadow_camera(direction, target, half_extent: float, res: int, distance: float = 5.0,
+                              near: float = 0.05, bias: float = 0.01):
+    """An orthographic shadow camera for a directional light travelling along `direction`: placed
+    `distance` back from `target` and looking along the light, its square map covering
+    +-half_extent metres.  Returns the view [3, 4] and intrinsics [7]."""
+    d = np.asarray(direction, np.float64)
+    d = d / np.linalg.norm(d)
+    up = np.array([0.0, 1.0, 0.0]) if abs(d[2]) > 0.99 else np.array([0.0, 0.0, 1.0])
+    r = np.cross(d, up)
+    r /= np.linalg.norm(r)
+    R = np.stack([r, np.cross(r, d), -d])
+    eye = np.asarray(target, np.float64) - distance * d
+    f = 0.5 * res / half_extent
+    return view_matrix(R, eye), np.array([f, f, 0.5 * res, 0.5 * res, near, bias, 1.0])
 
 
 # the block's six calibrated face colours (HSV): red, orange, yellow, green, blue, purple
@@ -860,7 +891,7 @@ def benchmark_batch(seed: int, sample_ids, res: int = 200, n_cams: int = 3, orbi
     if shadow_res > 0:
         sv, si = spot_shadow_cameras(pos, axis, cos_o, shadow_res)
         shadow_view = np.zeros((B, MAX_LIGHTS, 1, 3, 4))
-        shadow_intr = np.zeros((B, MAX_LIGHTS, 1, 6))
+        shadow_intr = np.zeros((B, MAX_LIGHTS, 1, 7))
         shadow_view[:, :N_SPOTS, 0], shadow_intr[:, :N_SPOTS, 0] = sv, si
         kw.update(shadow_view=shadow_view.astype(np.float32), shadow_intr=shadow_intr.astype(np.float32),
                   shadow_res=int(shadow_res), shadow_faces=1)

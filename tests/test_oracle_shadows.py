@@ -21,12 +21,12 @@ from tests import scenes
 def _down_camera(eye, R, half_deg, bias=0.0, near=0.05):
     view = sg.view_matrix(np.eye(3), np.asarray(eye, np.float64))
     f = 0.5 * R / math.tan(math.radians(half_deg))
-    return view, np.array([f, f, 0.5 * R, 0.5 * R, near, bias])
+    return view, np.array([f, f, 0.5 * R, 0.5 * R, near, bias, 0.0])
 
 
 def _shadowed(batch, views, intrs, R):
     sv = np.zeros((batch.n_samples, 4, 1, 3, 4), np.float32)
-    si = np.zeros((batch.n_samples, 4, 1, 6), np.float32)
+    si = np.zeros((batch.n_samples, 4, 1, 7), np.float32)
     for l, (v, i) in enumerate(zip(views, intrs)):
         sv[:, l, 0], si[:, l, 0] = v, i
     return batch.with_params(shadow_view=sv, shadow_intr=si, shadow_res=R, shadow_faces=1)
@@ -197,3 +197,30 @@ def test_cube_faces_shadow_a_point_light_in_every_direction(oracle):
     assert len(np.unique(faces[hit])) >= 2                              # shadows through different faces
     assert (k[on_plane][hit] == 9).all(), np.bincount(k[on_plane][hit])
     assert (k[on_plane][miss] == 0).all(), np.bincount(k[on_plane][miss])
+
+
+def test_directional_light_shadows_by_parallel_projection(oracle):
+    """A directional light 30 degrees off vertical with an orthographic shadow camera: a floating
+    box shadows exactly the plane points whose ray towards the light passes through it (all nine
+    taps well inside, none well outside)."""
+    th = math.radians(30.0)
+    d = np.array([math.sin(th), 0.0, -math.cos(th)])        # the direction the light travels
+    a, c, R, half = 0.15, np.array([0.0, 0.0, 0.3]), 192, 1.0
+    plane, box = sg.plane_mesh(2.0, 2.0), sg.box_mesh(a, per_face_material=False)
+    cam = scenes.camera_down((0.0, 0.0, 4.0), 200, 200, fovy_deg=25)
+    b = scenes.single_sample([plane, box], [0, 1], [scenes.identity_pose(), scenes.pose(t=c)], [cam], seg=[1, 2],
+                             lights=[(d, 1.0)], light_type=sg.LIGHT_DIRECTIONAL)
+    view, intr = sg.directional_shadow_camera(d, (0.0, 0.0, 0.3), half, R, bias=0.004)
+    o = oracle.render(_shadowed(b, [view], [intr], R), gbuffer=True)
+    k = (o["gb_mat"] >> 8) & 15
+    sel = np.nonzero(o["seg"] == 1)[0]
+    P = o["gb_pos"][sel].astype(np.float64)
+    world = np.stack([P[:, 0], P[:, 1], np.zeros(len(P))], 1)
+    far = world - 10.0 * d                                   # a point far along the ray towards the light
+    margin = 3 * half / (0.5 * R)                            # three texels
+    hit = _ray_hits_box(far, world, c, a, -margin)
+    miss = ~_ray_hits_box(far, world, c, a, margin)
+    assert hit.sum() > 200 and miss.sum() > 1000
+    assert (k[sel][hit] == 9).all(), np.bincount(k[sel][hit])
+    assert (k[sel][miss] == 0).all(), np.bincount(k[sel][miss])
+    assert (world[hit, 0] > 0.2).mean() > 0.5                 # cast away from the light, along +x
