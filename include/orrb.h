@@ -183,9 +183,10 @@ typedef struct {
                                     cameras ("faces": one for a spot light, six cube faces for a point
                                     light; camera-from-world, OpenGL axes, rigid) for the soft shadows
                                     of the benchmark's lights (Sec. 5); used when shape.shadow_res > 0 */
-  const float* shadow_intr;      /* [n_samples][4][F][6] or NULL: each face's fx, fy, cx, cy (pixels
-                                    of the shadow_res square map), near (m) and depth bias (m); fx ==
-                                    0: the face casts no shadow.  A face of a light l < the sample's
+  const float* shadow_intr;      /* [n_samples][4][F][7] or NULL: each face's fx, fy, cx, cy (pixels
+                                    of the shadow_res square map; pixels per metre when orthographic),
+                                    near (m), depth bias (m) and type (0 perspective, 1 orthographic,
+                                    as for a directional light); fx == 0: the face casts no shadow.  A face of a light l < the sample's
                                     light count with fx != 0 casts: its map holds the depth from its
                                     camera of the nearest back face of the sample's triangles (front
                                     faces are culled), rendered with the camera rules above, 0 where
@@ -195,7 +196,8 @@ typedef struct {
                                     (1/fx)), y_v = -depth ((y + 1/2 - cy) * (1/fy)), z_v = -depth,
                                     1/fx rounded once), q = (S V^-1) P with V^-1 = [R^T | -R^T t] and
                                     products summed in index order, z = -q_z, u = cx + fx (q_x (1 /
-                                    z)), v = cy - fy (q_y (1 / z)); the first face with z > near and
+                                    z)), v = cy - fy (q_y (1 / z)) (orthographic: u = cx + fx q_x, v
+                                    = cy - fy q_y); the first face with z > near and
                                     (floor(u), floor(v)) inside its map decides (none: unshadowed):
                                     k of the 3 x 3 texels (floor(u) + a, floor(v) + b), a, b in {-1,
                                     0, 1}, shadow it when inside the map with depth d > 0 and (z -

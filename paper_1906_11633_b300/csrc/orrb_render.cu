@@ -99,7 +99,7 @@ struct ImageInfo {
 struct ShadowInfo {
   int cast[kMaxLights][kMaxShadowFaces];
   float sm[kMaxLights][kMaxShadowFaces][12];
-  float si[kMaxLights][kMaxShadowFaces][6];
+  float si[kMaxLights][kMaxShadowFaces][7];
 };
 
 struct CtaShared {
@@ -259,13 +259,13 @@ __device__ void setup_image(const Params& p, int cam, CtaShared& sh, int* mprefi
     im.W = kPass ? p.shadow_res : p.cam_wh[cam * 2 + 0];
     im.H = kPass ? p.shadow_res : p.cam_wh[cam * 2 + 1];
     im.valid = 1;
-    const float* in = (kPass ? p.shadow_intr : p.cam_intr) + cam * 6;
+    const float* in = kPass ? p.shadow_intr + cam * 7 : p.cam_intr + cam * 6;
     im.fx = in[0];
     im.fy = in[1];
     im.cx = in[2];
     im.cy = in[3];
     im.near = in[4];
-    im.ortho = kPass ? 0 : in[5] != 0.0f;
+    im.ortho = (kPass ? in[6] : in[5]) != 0.0f;
     im.inv_fx = __frcp_rn(im.fx);  // correctly rounded: the G-buffer position uses it
     im.inv_fy = __frcp_rn(im.fy);
     if (kPass && in[0] == 0.0f) {  // the light casts no shadow: no map (not an error)
@@ -996,7 +996,7 @@ __device__ void shadow_setup(const Params& p, const ImageInfo& im, ShadowInfo& s
   }
   for (int f = 0; f < kMaxShadowFaces; f++) {
     const size_t c = ((size_t)im.s * kMaxLights + l) * p.shadow_faces + f;
-    const float* si = p.shadow_intr + c * 6;
+    const float* si = p.shadow_intr + c * 7;
     sd.cast[l][f] = f < p.shadow_faces && l < im.n_lights && si[0] != 0.0f;
     if (!sd.cast[l][f]) continue;
     const float* S = p.shadow_view + c * 12;
@@ -1006,7 +1006,7 @@ __device__ void shadow_setup(const Params& p, const ImageInfo& im, ShadowInfo& s
                             __fmul_rn(S[i * 4 + 2], Wi[2 * 4 + j]));
         sd.sm[l][f][j + 4 * i] = j == 3 ? __fadd_rn(r, S[i * 4 + 3]) : r;
       }
-    for (int k = 0; k < 6; k++) sd.si[l][f][k] = si[k];
+    for (int k = 0; k < 7; k++) sd.si[l][f][k] = si[k];
   }
 }
 
@@ -1033,9 +1033,10 @@ __device__ __forceinline__ int shadow_lookup(const Params& p, const ImageInfo& i
       if (!(z > si[4])) continue;
       const float q0 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[0], P0), __fmul_rn(M[1], P1)), __fmul_rn(M[2], P2)), M[3]);
       const float q1 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[4], P0), __fmul_rn(M[5], P1)), __fmul_rn(M[6], P2)), M[7]);
-      const float iw = __frcp_rn(z);
-      const float u = __fadd_rn(si[2], __fmul_rn(si[0], __fmul_rn(q0, iw)));
-      const float v = __fsub_rn(si[3], __fmul_rn(si[1], __fmul_rn(q1, iw)));
+      const bool ortho = si[6] != 0.0f;  // (orthographic: a directional light's camera)
+      const float iw = ortho ? 1.0f : __frcp_rn(z);
+      const float u = __fadd_rn(si[2], __fmul_rn(si[0], ortho ? q0 : __fmul_rn(q0, iw)));
+      const float v = __fsub_rn(si[3], __fmul_rn(si[1], ortho ? q1 : __fmul_rn(q1, iw)));
       if (!(fabsf(u) < kGuardPx) || !(fabsf(v) < kGuardPx)) continue;
       const int i0 = int(floorf(u)), j0 = int(floorf(v));
       if (i0 < 0 || j0 < 0 || i0 >= R || j0 >= R) continue;
@@ -1775,7 +1776,7 @@ __global__ void __launch_bounds__(128) shadow_neighbourhood_kernel(Params p) {
   for (long long w = blockIdx.x; w < (long long)n_maps * col_blocks; w += gridDim.x) {
     const int m = int(w / col_blocks), x = int(w % col_blocks) * 128 + int(threadIdx.x);
     const int sl = m / F;  // sample * 4 + light
-    if (sl % kMaxLights >= p.light_meta[(sl / kMaxLights) * 2] || p.shadow_intr[(size_t)m * 6] == 0.0f)
+    if (sl % kMaxLights >= p.light_meta[(sl / kMaxLights) * 2] || p.shadow_intr[(size_t)m * 7] == 0.0f)
       continue;  // no such light, or a face that casts none: no map
     if (x >= R) continue;
     const float* map = p.shadow_map + (size_t)m * R * R;

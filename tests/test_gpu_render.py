@@ -465,3 +465,18 @@ def test_ragged_shadow_maps_match_oracle(hand_renderer, oracle, mode):
     k = (o["gb_mat"][o["gb_mat"] >= 0] >> 8) & 0xfff
     assert ((k & 15) % 9 != 0).any()                   # partly shadowed points: the taps were counted
     compare(g, o, "ragged shadows")
+
+
+@pytest.mark.parametrize("mode", [L.ORRB_MODE_FUSED, L.ORRB_MODE_PLAIN])
+def test_directional_light_shadows_match_oracle(tiny_renderer, oracle, mode):
+    """The tiny scene's directional light casting the cube's shadow from an orthographic map: maps,
+    G-buffer words and channels against the oracle."""
+    b = sg.tiny_batch(5, n_samples=8, shadow_res=128)
+    o = oracle.render(b, debug=True, gbuffer=True)
+    g = render_np(tiny_renderer, b, config(mode=mode), gbuffer=True)
+    cast = np.arange(4)[None, :] < b.light_meta[:, :1]
+    np.testing.assert_array_equal(g["shadow_map"][cast], o["shadow_map"][cast])
+    np.testing.assert_array_equal(g["gbuffer"][6].view(np.int32), o["gb_mat"])
+    k = (o["gb_mat"][o["gb_mat"] >= 0] >> 8) & 15
+    assert (k == 9).mean() > 0.02 and ((k > 0) & (k < 9)).any()
+    compare(g, o, "directional shadows")
