@@ -37,6 +37,7 @@ class ServeRequest:
     arrival: float = 0.0            # perf_counter() at submission
     done: float = 0.0               # perf_counter() when the outputs were ready
     result: Optional[Dict[str, Any]] = None
+    error: Optional[str] = None     # set (and `event` signalled) when the request failed
     batch_id: int = -1
     event: threading.Event = field(default_factory=threading.Event)
 
@@ -72,6 +73,7 @@ class Server:
         self.per_stream: List[collections.deque] = [collections.deque() for _ in range(n_streams)]
         self.stream_cv = [threading.Condition() for _ in range(n_streams)]
         self.completed: List[ServeRequest] = []
+        self.failed: List[ServeRequest] = []   # requests whose batch failed to launch or to render
         self.max_concurrent = 0
         self.batches_launched = 0
         self.rejected_for_memory = 0
@@ -138,7 +140,13 @@ class Server:
                 k = self._next_stream
                 self._next_stream = (k + 1) % self.n_streams
                 self.inflight_bytes += need
-            handle = self.backend.launch([r.batch for r in take], k)
+            try:
+                handle = self.backend.launch([r.batch for r in take], k)
+            except Exception as e:  # the batch never started: fail its requests, free its budget
+                with self.lock:
+                    self.inflight_bytes -= need
+                self._fail(take, f"launch failed: {e}")
+                continue
             fl = InFlight(bid, take, handle, need, k)
             for r in take:
                 r.batch_id = bid
@@ -160,18 +168,34 @@ class Server:
                 if not q:
                     return
                 fl = q.popleft()
-            results = self.backend.wait(fl.handle)
+            try:
+                results, error = self.backend.wait(fl.handle), None
+            except Exception as e:  # the batch ran but its results cannot be trusted
+                results, error = [None] * len(fl.requests), f"render failed: {e}"
             now = time.perf_counter()
             for r, res in zip(fl.requests, results):
                 r.result = res
+                r.error = error
                 r.done = now
-            self.backend.release(fl.handle)
-            with self.lock:
-                self.inflight.pop(fl.batch_id, None)
-                self.inflight_bytes -= fl.nbytes
-                self.completed.extend(fl.requests)
-            for r in fl.requests:      # signal only once the bookkeeping is visible to stats()
-                r.event.set()
+            try:
+                self.backend.release(fl.handle)
+            finally:
+                with self.lock:
+                    self.inflight.pop(fl.batch_id, None)
+                    self.inflight_bytes -= fl.nbytes
+                    (self.failed if error else self.completed).extend(fl.requests)
+                for r in fl.requests:      # signal only once the bookkeeping is visible to stats()
+                    r.event.set()
+
+    def _fail(self, reqs, error: str) -> None:
+        now = time.perf_counter()
+        for r in reqs:
+            r.error = error
+            r.done = now
+        with self.lock:
+            self.failed.extend(reqs)
+        for r in reqs:
+            r.event.set()
 
     # -- report ----------------------------------------------------------------------
     def stats(self, wall_s: float) -> Dict[str, float]:
@@ -179,7 +203,7 @@ class Server:
         samples = sum(r.batch.n_samples for r in self.completed)
         return {"requests": len(self.completed), "samples": samples, "samples_per_s": samples / wall_s,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "max_ms": float(lat.max()), "batches": self.batches_launched,
+                "max_ms": float(lat.max()), "batches": self.batches_launched, "failed": len(self.failed),
                 "max_concurrent_batches": self.max_concurrent, "memory_waits": self.rejected_for_memory}
 
 
@@ -248,6 +272,9 @@ class GpuBackend:
 
     def wait(self, h):
         h["event"].synchronize()
+        status = self.L.orrb_read_status(self.r.ctx, h["ws"].data_ptr(), h["stream"].cuda_stream)
+        if status:  # a content check or a bounded wait on the device gave up: the outputs are not trusted
+            raise RuntimeError(f"device status {status:#x}")
         res, p0 = [], 0
         src = h["host"] if h["host"] is not None else h["out"]
         for b in h["batches"]:

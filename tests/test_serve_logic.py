@@ -84,3 +84,46 @@ def test_memory_budget_serialises_large_batches():
         assert r.event.wait(10.0)
     srv.close()
     assert be.peak_bytes <= one and be.peak_active == 1
+
+
+class FaultyBackend(FakeBackend):
+    """Fails the launch of batch `launch_fail` and the wait of batch `wait_fail` (counting from 0),
+    as a render call that returns an error code or a device status word would."""
+
+    def __init__(self, launch_fail, wait_fail, **kw):
+        super().__init__(**kw)
+        self.launch_fail, self.wait_fail, self.n = launch_fail, wait_fail, 0
+
+    def launch(self, batches, k):
+        i, self.n = self.n, self.n + 1
+        if i == self.launch_fail:
+            raise RuntimeError("launch error code")
+        h = super().launch(batches, k)
+        h["i"] = i
+        return h
+
+    def wait(self, h):
+        res = super().wait(h)
+        if h["i"] == self.wait_fail:
+            raise RuntimeError("device status 0x40")
+        return res
+
+
+def test_failed_batches_fail_their_requests_and_the_server_goes_on():
+    be = FaultyBackend(launch_fail=1, wait_fail=3, gpu_ms=2.0)
+    srv = Server(be, n_streams=2, max_inflight=2, tick_ms=1.0, max_batch_samples=4)
+    reqs = []
+    for i in range(24):
+        reqs.append(srv.submit(ServeRequest(i, _req_batch(i, 2, 32))))
+        time.sleep(0.002)
+    for r in reqs:
+        assert r.event.wait(10.0), f"request {r.rid} never finished"
+    srv.close()
+    failed = [r for r in reqs if r.error]
+    ok = [r for r in reqs if not r.error]
+    assert failed and any("launch" in r.error for r in failed) and any("render" in r.error for r in failed)
+    assert all(r.result is None for r in failed) and all(r.result is not None for r in ok)
+    assert len(ok) + len(failed) == 24 and len(ok) >= 16         # later batches still ran
+    assert srv.inflight_bytes == 0 and be.active_bytes == 0
+    st = srv.stats(1.0)
+    assert st["failed"] == len(failed) and st["requests"] == len(ok)
