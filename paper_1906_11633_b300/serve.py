@@ -127,10 +127,20 @@ class Server:
                         break
                     take.append(req)
                     n += req.batch.n_samples
-                need = self.backend.bytes_needed([r.batch for r in take])
-                while len(take) > 1 and self.inflight_bytes + need > self.budget:
-                    take.pop()                       # admit a smaller prefix that fits
+                try:
                     need = self.backend.bytes_needed([r.batch for r in take])
+                    while len(take) > 1 and self.inflight_bytes + need > self.budget:
+                        take.pop()                       # admit a smaller prefix that fits
+                        need = self.backend.bytes_needed([r.batch for r in take])
+                    invalid = None
+                except Exception as e:  # a request the host cannot even size: fail what was taken
+                    for _ in take:
+                        self.pending.popleft()
+                    invalid = e
+            if invalid is not None:
+                self._fail(take, f"invalid request: {invalid}")
+                continue
+            with self.lock:
                 if self.inflight_bytes + need > self.budget:
                     self.rejected_for_memory += 1
                     return                           # wait for an in-flight batch to free memory

@@ -108,3 +108,32 @@ def test_capture_pipeline_results_match_direct_renders(renderer):
         torch.cuda.synchronize()
         for k in ref:
             np.testing.assert_array_equal(g[k].numpy(), ref[k].cpu().numpy(), err_msg=k)
+
+
+def test_served_requests_with_bad_input_fail_alone():
+    """Two bad requests among good ones, each in a batch of its own: one names a mesh that does not
+    exist (the host cannot size it: it fails before launch), one has a light count beyond the
+    maximum (the kernel clamps it and flags the status word, and the loop fails the batch with
+    that status).  The requests around them are rendered as usual."""
+    from paper_1906_11633_b300.serve import GpuBackend, Server, ServeRequest
+    meshes = sg.hand_meshes()
+    be = GpuBackend(meshes, n_streams=2)
+    srv = Server(be, n_streams=2, max_inflight=2, tick_ms=1.0, max_batch_samples=2)
+    batches = [sg.hand_batch(9, np.arange(2 * i, 2 * i + 2), res=64, n_cams=2, meshes=meshes) for i in range(6)]
+    bad_mesh = batches[1].inst_mesh.copy()
+    bad_mesh[5] = 999
+    batches[1] = batches[1].with_params(inst_mesh=bad_mesh)
+    bad_lights = batches[3].light_meta.copy()
+    bad_lights[0, 0] = 9
+    batches[3] = batches[3].with_params(light_meta=bad_lights)
+    reqs = [srv.submit(ServeRequest(i, b)) for i, b in enumerate(batches)]
+    for r in reqs:
+        assert r.event.wait(60.0)
+    srv.close()
+    assert reqs[1].error is not None and reqs[1].error.startswith("invalid request")
+    assert reqs[3].error is not None and "device status 0x10" in reqs[3].error and reqs[3].result is None
+    assert all(r.error is None and r.result is not None for i, r in enumerate(reqs) if i not in (1, 3))
+    solo = Renderer(meshes)
+    alone = solo.render(solo.upload(batches[4]))
+    torch.cuda.synchronize()
+    _equal(reqs[4].result, alone)
