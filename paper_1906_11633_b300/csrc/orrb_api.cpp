@@ -129,6 +129,8 @@ ArenaLayout arena_layout(int n_meshes, int n_meshlets, int n_verts, int n_tris) 
   o = align256(o + sizeof(MeshEntry) * (size_t)std::max(n_meshes, 1));
   L.meshlets = o;
   o = align256(o + sizeof(MeshletEntry) * (size_t)std::max(n_meshlets, 1));
+  L.bounds = o;
+  o = align256(o + 16 * (size_t)std::max(n_meshlets, 1));
   L.vpos = o;
   o = align256(o + 16 * (size_t)std::max(n_verts, 1));
   L.vnrm = o;
@@ -412,6 +414,29 @@ orrb_status orrb_upload_meshes(orrb_ctx* ctx, const orrb_mesh_desc* meshes, int3
   for (size_t i = 0; i < cl.size(); i++)
     ml[i] = MeshletEntry{cl[i].vert_begin, cl[i].tri_begin, cl[i].n_verts | (cl[i].n_tris << 16), cl[i].mesh_tri_base};
   if (!ml.empty()) std::memcpy(host.data() + L.meshlets, ml.data(), sizeof(MeshletEntry) * ml.size());
+  // per cluster a bounding sphere: the centre of its vertices' box and the largest distance to it,
+  // in double, rounded outwards (the shadow pass skips clusters wholly outside a shadow camera's view)
+  std::vector<float4> bounds(cl.size());
+  for (size_t i = 0; i < cl.size(); i++) {
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int v = 0; v < cl[i].n_verts; v++) {
+      const float4 q = vpos[cl[i].vert_begin + v];
+      const double c[3] = {q.x, q.y, q.z};
+      for (int k = 0; k < 3; k++) {
+        lo[k] = std::min(lo[k], c[k]);
+        hi[k] = std::max(hi[k], c[k]);
+      }
+    }
+    double mid[3], r2 = 0.0;
+    for (int k = 0; k < 3; k++) mid[k] = cl[i].n_verts ? 0.5 * (lo[k] + hi[k]) : 0.0;
+    for (int v = 0; v < cl[i].n_verts; v++) {
+      const float4 q = vpos[cl[i].vert_begin + v];
+      const double d[3] = {q.x - mid[0], q.y - mid[1], q.z - mid[2]};
+      r2 = std::max(r2, d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    }
+    bounds[i] = make_float4((float)mid[0], (float)mid[1], (float)mid[2], (float)(std::sqrt(r2) * (1.0 + 1e-6) + 1e-6));
+  }
+  if (!bounds.empty()) std::memcpy(host.data() + L.bounds, bounds.data(), 16 * bounds.size());
   if (!vpos.empty()) {
     std::memcpy(host.data() + L.vpos, vpos.data(), 16 * vpos.size());
     std::memcpy(host.data() + L.vnrm, vnrm.data(), 16 * vnrm.size());
@@ -488,6 +513,7 @@ orrb_status orrb_render_batch(orrb_ctx* ctx, const orrb_batch_shape* shape, cons
   const ArenaLayout& A = ctx->arena;
   p.meshes = reinterpret_cast<const MeshEntry*>(ctx->arena_ptr + A.meshes);
   p.meshlets = reinterpret_cast<const MeshletEntry*>(ctx->arena_ptr + A.meshlets);
+  p.cbounds = reinterpret_cast<const float4*>(ctx->arena_ptr + A.bounds);
   p.vpos = reinterpret_cast<const float4*>(ctx->arena_ptr + A.vpos);
   p.vnrm = reinterpret_cast<const float4*>(ctx->arena_ptr + A.vnrm);
   p.tris = reinterpret_cast<const uint32_t*>(ctx->arena_ptr + A.tris);
@@ -554,6 +580,7 @@ orrb_status orrb_render_batch_noalloc(orrb_ctx* ctx, const orrb_batch_shape* sha
   const ArenaLayout& A = ctx->arena;
   p.meshes = reinterpret_cast<const MeshEntry*>(ctx->arena_ptr + A.meshes);
   p.meshlets = reinterpret_cast<const MeshletEntry*>(ctx->arena_ptr + A.meshlets);
+  p.cbounds = reinterpret_cast<const float4*>(ctx->arena_ptr + A.bounds);
   p.vpos = reinterpret_cast<const float4*>(ctx->arena_ptr + A.vpos);
   p.vnrm = reinterpret_cast<const float4*>(ctx->arena_ptr + A.vnrm);
   p.tris = reinterpret_cast<const uint32_t*>(ctx->arena_ptr + A.tris);

@@ -37,7 +37,7 @@ struct MeshletEntry {     // 16 B
 };
 
 struct ArenaLayout {      // byte offsets inside the arena, all 256-aligned
-  size_t meshes, meshlets, vpos, vnrm, tris, total;
+  size_t meshes, meshlets, bounds, vpos, vnrm, tris, total;
   int32_t n_meshes, n_meshlets, n_verts, n_tris;
 };
 
@@ -94,6 +94,7 @@ struct Params {
   // mesh set
   const MeshEntry* meshes;
   const MeshletEntry* meshlets;
+  const float4* cbounds;  // per cluster: object-space bounding sphere (centre xyz, radius)
   const float4* vpos;
   const float4* vnrm;
   const uint32_t* tris;  // 3 local vertex indices (u8) | tri_mat << 24

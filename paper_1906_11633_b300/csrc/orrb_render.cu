@@ -511,9 +511,34 @@ __device__ __noinline__ int clip_triangle(int t_max, Record* rec, const ImageInf
 // ---------------------------------------------------------------------------
 // phase G: geometry of one image
 // ---------------------------------------------------------------------------
+// True when the bounding sphere b (object space) of a cluster, moved to view space by mv, lies
+// wholly behind the near plane or wholly beyond one of the image's four edges (for a perspective
+// view: in the half-space beyond the plane through the eye and that edge).  Every triangle of such
+// a cluster is then clipped away or covers no pixel centre, so skipping it changes nothing.  The
+// radius is widened by a millimetre and a thousandth, far beyond the fp32 error of the test.
+__device__ __forceinline__ bool cluster_outside(const ImageInfo& im, const float* mv, float4 b) {
+  const float x = mv[0] * b.x + mv[1] * b.y + mv[2] * b.z + mv[3];
+  const float y = mv[4] * b.x + mv[5] * b.y + mv[6] * b.z + mv[7];
+  const float z = mv[8] * b.x + mv[9] * b.y + mv[10] * b.z + mv[11];
+  const float r = b.w * 1.001f + 1e-3f;
+  if (z - r > -im.near) return true;
+  const float W = float(im.W), H = float(im.H);
+  if (im.ortho) {  // x_s = cx + fx x, y_s = cy - fy y
+    return x + r < -im.cx / im.fx || x - r > (W - im.cx) / im.fx || y - r > im.cy / im.fy ||
+           y + r < (im.cy - H) / im.fy;
+  }
+  // x_s < 0: fx x - cx z < 0;  x_s > W: fx x + (W - cx) z > 0;  y_s < 0: fy y + cy z > 0;
+  // y_s > H: (H - cy) z - fy y > 0   (each side's normal length scales the radius)
+  return im.fx * x - im.cx * z + r * sqrtf(im.fx * im.fx + im.cx * im.cx) < 0.0f ||
+         im.fx * x + (W - im.cx) * z - r * sqrtf(im.fx * im.fx + (W - im.cx) * (W - im.cx)) > 0.0f ||
+         im.fy * y + im.cy * z - r * sqrtf(im.fy * im.fy + im.cy * im.cy) > 0.0f ||
+         (H - im.cy) * z - im.fy * y - r * sqrtf(im.fy * im.fy + (H - im.cy) * (H - im.cy)) > 0.0f;
+}
+
 // kTrack: the launch writes tracker rows (a separate instance, so that the common case carries none
 // of that code).  kBack: keep back faces instead of front faces (the shadow pass): every triangle
-// is taken with its second and third vertices swapped.
+// is taken with its second and third vertices swapped; clusters wholly outside the shadow camera's
+// view are skipped (a cube face sees about a sixth of the scene).
 template <bool kTrack, bool kBack = false>
 __device__ void geometry_phase(const Params& p, CtaShared& sh, const int* mprefix, const int* tprefix,
                                const int* mbegin, WarpG* wgs, const Scratch& sc) {
@@ -547,6 +572,8 @@ __device__ void geometry_phase(const Params& p, CtaShared& sh, const int* mprefi
       wg->mv[lane] = s;
     }
     __syncwarp();
+    if (kBack && cluster_outside(im, wg->mv, __ldg(p.cbounds + mbegin[lo] + (j - mprefix[lo]))))
+      continue;  // (warp-uniform: every lane tests the same sphere)
     const int nv = ml.counts & 0xffff, nt = ml.counts >> 16;
     // the cluster's triangle words and its vertices are all requested before any is used
     static_assert(kMeshletTris == 128 && kMeshletVerts == 64, "prefetch assumes 4 triangle and 2 vertex rounds");
