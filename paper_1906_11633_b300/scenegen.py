@@ -815,11 +815,12 @@ def spot_shadow_cameras(pos, axis, cos_outer, res: int, near: float = 0.05, bias
     return view_matrix(R, pos), intr
 
 
-CUBE_FACES = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]], np.float64)
+# the face looking down first: lights hang above the scene, and the lookup tries faces in order
+CUBE_FACES = np.array([[0, 0, -1], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1]], np.float64)
 
 
 def point_shadow_cameras(pos, res: int, near: float = 0.02, bias: float = 0.004):
-    """Six cube-face shadow cameras per point light (looking along +x, -x, +y, -y, +z, -z with
+    """Six cube-face shadow cameras per point light (looking along -z, +x, -x, +y, -y, +z with
     90 deg fields of view).  pos [..., 3] -> views [..., 6, 3, 4], intrinsics [..., 6, 7]."""
     pos = np.asarray(pos, np.float64)
     views, intr = [], []
