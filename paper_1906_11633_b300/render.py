@@ -207,7 +207,8 @@ class Renderer:
 
 
 class GraphRender:
-    """One fused render captured in a CUDA graph and replayed with new batch contents.
+    """One fused render captured in a CUDA graph and replayed with new batch contents (with shadow
+    maps the render is its three launches and a queue reset, all captured).
 
     The kernel reads every descriptor from device memory, so a batch with the
     same array shapes (a capacity bucket) renders by copying its parameters into

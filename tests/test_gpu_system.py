@@ -42,6 +42,22 @@ def test_graph_replay_matches_direct_render_and_takes_new_contents(renderer):
     _equal(out, renderer.render(renderer.upload(b2)))
 
 
+def test_graph_replay_with_shadow_maps(renderer):
+    """A shadowed batch is several launches (shadow pass, the maps' neighbourhood table, cameras)
+    and a queue reset; its captured graph replays them, maps included, and takes new contents."""
+    b1 = sg.benchmark_batch(3, np.arange(6), res=96, shadow_res=128)
+    b2 = sg.benchmark_batch(4, np.arange(6), res=96, shadow_res=128)
+    g = GraphRender(renderer, renderer.upload(b1))
+    assert "shadow_map" in g.out
+    out = g.replay()
+    torch.cuda.synchronize()
+    _equal(out, renderer.render(renderer.upload(b1)))
+    g.update(b2)
+    out = g.replay()
+    torch.cuda.synchronize()
+    _equal(out, renderer.render(renderer.upload(b2)))
+
+
 def test_uneven_batch_in_one_launch_matches_plain_launches(renderer):
     b = sg.uneven_batch(3, np.arange(48))
     db = renderer.upload(b)
