@@ -265,9 +265,12 @@ class CapturePipeline:
         self.slots = []
         for _ in range(depth):
             dev_in = {k: torch.empty(a.shape, dtype=_DTYPES[k], device=renderer.device) for k, a in arrs.items()}
+            db = DeviceBatch(self.shape, dev_in)
             out = renderer.alloc_outputs(int(self.shape.total_pixels))
+            if db.has_shadows:  # the shadow maps are an output too, read back with the channels
+                out["shadow_map"] = renderer.alloc_shadow_maps(db)
             self.slots.append(dict(
-                db=DeviceBatch(self.shape, dev_in), out=out,
+                db=db, out=out,
                 host={k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items()},
                 ws=torch.empty(n_ws, dtype=torch.uint8, device=renderer.device),
                 rendered=torch.cuda.Event(), done=torch.cuda.Event()))
