@@ -256,8 +256,10 @@ class GpuBackend:
     def bytes_needed(self, batches) -> int:
         px = sum(b.total_pixels for b in batches)
         tris = max(int(b.tris_per_sample().max()) for b in batches)
-        # outputs (14 B per pixel) + workspace + parameters
-        return int(px * 14 + self.ws_a + self.ws_b * tris + sum(b.n_samples for b in batches) * 4096)
+        # outputs (14 B per pixel) + workspace + parameters, + shadow maps and their neighbourhood table
+        maps = sum(b.n_samples * 4 * b.shadow_faces * b.shadow_res ** 2 * 12
+                   for b in batches if getattr(b, "shadow_view", None) is not None)
+        return int(px * 14 + self.ws_a + self.ws_b * tris + sum(b.n_samples for b in batches) * 4096 + maps)
 
     def launch(self, batches, k: int):
         torch = self.torch
@@ -285,12 +287,14 @@ class GpuBackend:
         status = self.L.orrb_read_status(self.r.ctx, h["ws"].data_ptr(), h["stream"].cuda_stream)
         if status:  # a content check or a bounded wait on the device gave up: the outputs are not trusted
             raise RuntimeError(f"device status {status:#x}")
-        res, p0 = [], 0
+        res, p0, s0 = [], 0, 0
         src = h["host"] if h["host"] is not None else h["out"]
         for b in h["batches"]:
-            n = b.total_pixels
-            res.append({k: v[p0:p0 + n] for k, v in src.items()})
+            n, ns = b.total_pixels, b.n_samples
+            # channels are flat over pixels; shadow maps are per sample
+            res.append({k: (v[s0:s0 + ns] if k == "shadow_map" else v[p0:p0 + n]) for k, v in src.items()})
             p0 += n
+            s0 += ns
         return res
 
     def release(self, h):

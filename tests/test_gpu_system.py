@@ -134,6 +134,32 @@ def test_capture_pipeline_results_match_direct_renders(renderer, shadows):
             np.testing.assert_array_equal(g[k].numpy()[keep], ref[k].cpu().numpy()[keep], err_msg=k)
 
 
+def test_served_shadowed_requests_equal_their_solo_render():
+    """Requests with shadow maps batched together: each one's channels and the maps of its own
+    samples equal its render alone."""
+    from paper_1906_11633_b300.serve import GpuBackend, Server, ServeRequest
+    meshes = sg.hand_meshes()
+    be = GpuBackend(meshes, n_streams=2)
+    srv = Server(be, n_streams=2, max_inflight=2, tick_ms=5.0)
+    batches = [sg.benchmark_batch(11, np.arange(3 * i, 3 * i + 1 + i % 3), res=64, n_cams=2, meshes=meshes,
+                                  shadow_res=64) for i in range(6)]
+    reqs = [srv.submit(ServeRequest(i, b)) for i, b in enumerate(batches)]
+    for r in reqs:
+        assert r.event.wait(60.0)
+    st = srv.stats(1.0)
+    srv.close()
+    assert st["requests"] == 6 and st["batches"] < 6
+    solo = Renderer(meshes)
+    for r in reqs:
+        alone = solo.render(solo.upload(r.batch))
+        torch.cuda.synchronize()
+        cast = np.arange(4)[None, :] < r.batch.light_meta[:, :1]
+        for k in alone:
+            keep = cast if k == "shadow_map" else slice(None)
+            np.testing.assert_array_equal(to_numpy({k: r.result[k]})[k][keep], to_numpy({k: alone[k]})[k][keep],
+                                          err_msg=k)
+
+
 def test_served_requests_with_bad_input_fail_alone():
     """Two bad requests among good ones, each in a batch of its own: one names a mesh that does not
     exist (the host cannot size it: it fails before launch), one has a light count beyond the
