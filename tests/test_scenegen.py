@@ -1,8 +1,30 @@
 """The seeded input generator: a sample's parameters do not depend on its batch (Sec. 4.3 seeding)."""
 
+from pathlib import Path
+
 import numpy as np
 
 from paper_1906_11633_b300 import scenegen as sg
+
+GOLDEN = Path(__file__).parent / "golden"
+
+
+def test_philox_matches_the_published_known_answer_vectors():
+    """The block function every draw comes from, against the Philox4x32-10 vectors published with
+    the generator (Salmon et al., SC 2011): all-zero, all-one and pi-digit counters and keys."""
+    rows = [ln.split() for ln in (GOLDEN / "philox4x32_10_kat.txt").read_text().splitlines()
+            if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for row in rows:
+        c, k, want = [int(v, 16) for v in row[:4]], [int(v, 16) for v in row[4:6]], [int(v, 16) for v in row[6:]]
+        got = sg.philox4x32_10(*[np.uint32(v) for v in c], *k)
+        assert [int(v) for v in got] == want, row
+    # broadcast over a counter array gives the same words as one call per counter
+    ctr = np.array([0, 0xFFFFFFFF], np.uint32)
+    many = sg.philox4x32_10(ctr, ctr, ctr, ctr, 0, 0)
+    for i, v in enumerate(ctr):
+        one = sg.philox4x32_10(v, v, v, v, 0, 0)
+        assert [int(w[i]) for w in many] == [int(w) for w in one]
 
 
 def test_sample_identical_alone_and_in_batch():
