@@ -57,7 +57,7 @@ def set_samples(n: int) -> None:
 def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("orrb_render.cu", "orrb_internal.h"):
+    for f in ("orrb_render.cu", "orrb_internal.h", "orrb_shading.cuh"):
         with open(os.path.join(ROOT, "paper_1906_11633_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
