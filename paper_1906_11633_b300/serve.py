@@ -141,9 +141,17 @@ class Server:
                 self._fail(take, f"invalid request: {invalid}")
                 continue
             with self.lock:
-                if self.inflight_bytes + need > self.budget:
+                too_big = not self.inflight and need > self.budget
+                if too_big:                          # (a single request) it can never fit: fail it, serve the rest
+                    for _ in take:
+                        self.pending.popleft()
+                elif self.inflight_bytes + need > self.budget:
                     self.rejected_for_memory += 1
                     return                           # wait for an in-flight batch to free memory
+            if too_big:
+                self._fail(take, f"does not fit in device memory: needs {need} bytes of a {self.budget}-byte budget")
+                continue
+            with self.lock:
                 for _ in take:
                     self.pending.popleft()
                 bid = next(self._ids)

@@ -3,7 +3,8 @@
 Checks: every request completes exactly once, in-flight batches never exceed
 the slot count or the memory budget, batches overlap (more than one in flight)
 when requests keep arriving, and a request larger than the budget is never
-admitted alongside others that would overflow it.
+admitted alongside others that would overflow it, and a request that could never
+fit the budget fails alone instead of blocking the queue behind it.
 """
 
 import threading
@@ -127,3 +128,18 @@ def test_failed_batches_fail_their_requests_and_the_server_goes_on():
     assert srv.inflight_bytes == 0 and be.active_bytes == 0
     st = srv.stats(1.0)
     assert st["failed"] == len(failed) and st["requests"] == len(ok)
+
+
+def test_request_larger_than_the_whole_budget_fails_and_the_queue_moves_on():
+    small = 64 * 64 * 14                      # one 64 x 64 image
+    be = FakeBackend(gpu_ms=2.0, budget=4 * small)
+    srv = Server(be, n_streams=2, max_inflight=2, tick_ms=1.0)
+    big = srv.submit(ServeRequest(0, _req_batch(0, 8, 64)))        # 8 images: twice the budget
+    rest = [srv.submit(ServeRequest(i, _req_batch(i, 1, 64))) for i in range(1, 9)]
+    for r in [big] + rest:
+        assert r.event.wait(10.0), f"request {r.rid} never finished"
+    srv.close()
+    assert big.error and "does not fit" in big.error and big.result is None
+    assert all(r.error is None and r.result is not None for r in rest)
+    assert be.peak_bytes <= 4 * small and srv.inflight_bytes == 0
+    assert srv.stats(1.0)["failed"] == 1
