@@ -217,12 +217,15 @@ class Server:
 
     # -- report ----------------------------------------------------------------------
     def stats(self, wall_s: float) -> Dict[str, float]:
-        lat = np.array([r.latency_ms for r in self.completed]) if self.completed else np.zeros(1)
-        samples = sum(r.batch.n_samples for r in self.completed)
-        return {"requests": len(self.completed), "samples": samples, "samples_per_s": samples / wall_s,
+        with self.lock:  # a consistent snapshot while batches may still complete
+            done, n_failed = list(self.completed), len(self.failed)
+            batches, conc, waits = self.batches_launched, self.max_concurrent, self.rejected_for_memory
+        lat = np.array([r.latency_ms for r in done]) if done else np.zeros(1)
+        samples = sum(r.batch.n_samples for r in done)
+        return {"requests": len(done), "samples": samples, "samples_per_s": samples / wall_s,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "max_ms": float(lat.max()), "batches": self.batches_launched, "failed": len(self.failed),
-                "max_concurrent_batches": self.max_concurrent, "memory_waits": self.rejected_for_memory}
+                "max_ms": float(lat.max()), "batches": batches, "failed": n_failed,
+                "max_concurrent_batches": conc, "memory_waits": waits}
 
 
 class GpuBackend:
