@@ -219,7 +219,8 @@ int max_tiles_of(const orrb_batch_shape& s, const orrb_config& c) {
 struct Plan {
   int n_slots, ctas_per_sm, max_tiles;
   size_t slot_bytes, smem, total;
-  size_t nb_offset;  // the shadow maps' neighbourhood table (after the slots), 0 without shadows
+  size_t nb_offset;   // the shadow maps' neighbourhood table (after the slots), 0 without shadows
+  size_t cnt_offset;  // its occupied-texel counts (after the table)
 };
 
 orrb_status plan(orrb_ctx* ctx, const orrb_batch_shape& s, const orrb_config& c, Plan* P) {
@@ -246,9 +247,12 @@ orrb_status plan(orrb_ctx* ctx, const orrb_batch_shape& s, const orrb_config& c,
   }
   P->total = 256 + (size_t)P->n_slots * P->slot_bytes;
   P->nb_offset = 0;
+  P->cnt_offset = 0;
   if (s.shadow_res > 0) {
+    const size_t texels = (size_t)s.n_samples * kMaxLights * faces_of(s) * s.shadow_res * s.shadow_res;
     P->nb_offset = align256(P->total);
-    P->total = P->nb_offset + (size_t)s.n_samples * kMaxLights * faces_of(s) * s.shadow_res * s.shadow_res * sizeof(float2);
+    P->cnt_offset = align256(P->nb_offset + texels * sizeof(uint32_t));
+    P->total = P->cnt_offset + texels;
   }
   return ORRB_OK;
 }
@@ -528,7 +532,8 @@ orrb_status orrb_render_batch(orrb_ctx* ctx, const orrb_batch_shape* shape, cons
   p.scratch = ws + 256;
   p.slot_bytes = P.slot_bytes;
   p.n_slots = P.n_slots;
-  p.shadow_nb = p.shadow_res > 0 ? reinterpret_cast<float2*>(ws + P.nb_offset) : nullptr;
+  p.shadow_nb = p.shadow_res > 0 ? reinterpret_cast<uint32_t*>(ws + P.nb_offset) : nullptr;
+  p.shadow_cnt = p.shadow_res > 0 ? reinterpret_cast<uint8_t*>(ws + P.cnt_offset) : nullptr;
   p.plain_sample = -1;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(ws, 0, 16, s);

@@ -77,8 +77,10 @@ struct Params {
   const float* shadow_view;  // [n_samples][4][12] (with shadow_res > 0)
   const float* shadow_intr;  // [n_samples][4][6]
   float* shadow_map;         // [n_samples][4][R][R]: written by the shadow pass, read by the shading
-  float2* shadow_nb;         // [n_samples][4][R][R] or null: per texel over its 3 x 3 neighbourhood, the least
-                             // depth > 0 (+inf if none) and, if all nine are inside and > 0, the largest (+inf)
+  uint32_t* shadow_nb;       // [n_samples][4][R][R] or null: per texel over its 3 x 3 neighbourhood, the least
+                             // depth > 0 (+inf if none, binary16 rounded down) | the largest (0 if none,
+                             // binary16 rounded up) << 16
+  uint8_t* shadow_cnt;       // [n_samples][4][R][R] (with shadow_nb): occupied texels (depth > 0) among the nine
   int32_t shadow_res;        // R, 0 without shadows
   int32_t shadow_faces;      // F, shadow cameras per light
   int32_t shadow_pass;       // this launch renders the shadow maps (images: (sample * 4 + light) * F + face)

@@ -1070,10 +1070,13 @@ __device__ __forceinline__ int shadow_lookup(const Params& p, const ImageInfo& i
       const float zb = __fsub_rn(z, si[5]);
       const size_t m0 = (((size_t)im.s * kMaxLights + l) * F + f) * R * R;
       int k = -1;
-      if (p.shadow_nb) {  // one load settles lit and umbra points
-        const float2 e = __ldg(p.shadow_nb + m0 + (size_t)j0 * R + i0);
-        if (!(zb > e.x)) k = 0;  // no occupied tap is nearer than the point
-        else if (zb > e.y) k = 9;  // all nine occupied and nearer
+      if (p.shadow_nb) {  // one entry settles lit points and those behind every occupied tap
+        const size_t t = m0 + (size_t)j0 * R + i0;
+        const unsigned e = __ldg(p.shadow_nb + t);
+        const float lo = __half2float(__ushort_as_half((unsigned short)(e & 0xffffu)));
+        const float hi = __half2float(__ushort_as_half((unsigned short)(e >> 16)));
+        if (!(zb > lo)) k = 0;  // no occupied tap is nearer than the point
+        else if (zb > hi) k = __ldg(p.shadow_cnt + t);  // every occupied tap is nearer
       }
       if (k < 0) {
         k = 0;
@@ -1765,20 +1768,25 @@ __global__ void __launch_bounds__(512, 2) plain_raster_kernel(Params p) {
 
 // The neighbourhood table of the shadow maps (after the shadow pass, before the camera launch):
 // per texel over its 3 x 3 neighbourhood (texels outside the map count as empty), the least
-// depth > 0 (+inf if none) and, when all nine are inside and occupied, the largest (+inf
-// otherwise).  A point with depth-less-bias zb is then unshadowed by every tap when zb <= the
-// least, and shadowed by all nine when zb > the largest; only the others count taps.
-// Each thread owns one column x of one map and walks down it, keeping the 3-texel summaries
-// (least occupied depth, largest depth, all three occupied) of the rows above, at and below in
-// registers: three loads per texel.  A block covers 128 columns of one map (blocks stride over
-// (map, column block) pairs).
+// occupied depth (depth > 0; +inf if none), the largest (0 if none) and the number of occupied
+// texels c.  A point with depth-less-bias zb is then unshadowed by every tap when zb <= the
+// least, and shadowed by exactly the c occupied taps when zb > the largest (the empty ones
+// light); only the others count taps.  The two depths are stored as binary16 rounded outward
+// (the least down, the largest up), which keeps both shortcuts exact: what they cannot settle
+// takes the nine taps.
+// Each thread owns one column x of one map and walks down kNbRows rows of it, keeping the
+// 3-texel summaries (least and largest occupied depth, occupied count) of the rows above, at
+// and below in registers: three loads per texel.  A block covers 128 columns and kNbRows rows
+// of one map (blocks stride over (map, column block, row block) triples).
+constexpr int kNbRows = 32;
+
 struct RowTriple {
   float lo, hi;
-  bool full;
+  int n;  // occupied texels among the three
 };
 
 __device__ __forceinline__ RowTriple row_triple(const float* map, int R, int x, int y) {
-  RowTriple t{__int_as_float(0x7f800000), 0.0f, y >= 0 && y < R && x > 0 && x + 1 < R};
+  RowTriple t{__int_as_float(0x7f800000), 0.0f, 0};
   if (y < 0 || y >= R) return t;
   const float* row = map + (size_t)y * R;
 #pragma unroll
@@ -1789,8 +1797,7 @@ __device__ __forceinline__ RowTriple row_triple(const float* map, int R, int x, 
     if (d > 0.0f) {
       t.lo = fminf(t.lo, d);
       t.hi = fmaxf(t.hi, d);
-    } else {
-      t.full = false;
+      t.n++;
     }
   }
   return t;
@@ -1798,22 +1805,27 @@ __device__ __forceinline__ RowTriple row_triple(const float* map, int R, int x, 
 
 __global__ void __launch_bounds__(128) shadow_neighbourhood_kernel(Params p) {
   const int R = p.shadow_res, F = p.shadow_faces, n_maps = p.n_samples * kMaxLights * F;
-  const int col_blocks = (R + 127) / 128;
-  const float inf = __int_as_float(0x7f800000);
-  for (long long w = blockIdx.x; w < (long long)n_maps * col_blocks; w += gridDim.x) {
-    const int m = int(w / col_blocks), x = int(w % col_blocks) * 128 + int(threadIdx.x);
+  const int col_blocks = (R + 127) / 128, row_blocks = (R + kNbRows - 1) / kNbRows;
+  const long long per_map = (long long)col_blocks * row_blocks;
+  for (long long w = blockIdx.x; w < (long long)n_maps * per_map; w += gridDim.x) {
+    const int m = int(w / per_map), wr = int(w % per_map);
+    const int x = (wr % col_blocks) * 128 + int(threadIdx.x);
+    const int y0 = (wr / col_blocks) * kNbRows, y1 = min(R, y0 + kNbRows);
     const int sl = m / F;  // sample * 4 + light
     if (sl % kMaxLights >= p.light_meta[(sl / kMaxLights) * 2] || p.shadow_intr[(size_t)m * 7] == 0.0f)
       continue;  // no such light, or a face that casts none: no map
     if (x >= R) continue;
     const float* map = p.shadow_map + (size_t)m * R * R;
-    float2* out = p.shadow_nb + (size_t)m * R * R + x;
-    RowTriple a = row_triple(map, R, x, -1), b = row_triple(map, R, x, 0);
+    uint32_t* out = p.shadow_nb + (size_t)m * R * R + x;
+    uint8_t* cnt = p.shadow_cnt + (size_t)m * R * R + x;
+    RowTriple a = row_triple(map, R, x, y0 - 1), b = row_triple(map, R, x, y0);
 #pragma unroll 4
-    for (int y = 0; y < R; y++) {
+    for (int y = y0; y < y1; y++) {
       const RowTriple c = row_triple(map, R, x, y + 1);
       const float lo = fminf(fminf(a.lo, b.lo), c.lo), hi = fmaxf(fmaxf(a.hi, b.hi), c.hi);
-      out[(size_t)y * R] = make_float2(lo, a.full && b.full && c.full ? hi : inf);
+      out[(size_t)y * R] = unsigned(__half_as_ushort(__float2half_rd(lo))) |
+                           (unsigned(__half_as_ushort(__float2half_ru(hi))) << 16);
+      cnt[(size_t)y * R] = uint8_t(a.n + b.n + c.n);
       a = b;
       b = c;
     }
@@ -1849,7 +1861,7 @@ int noalloc_scratch(int device, void** ptr, size_t* bytes) {
 
 int launch_shadow_neighbourhoods(const Params& p, void* stream, char* err, size_t errlen) {
   const int n_maps = p.n_samples * kMaxLights * p.shadow_faces;
-  const long long work = (long long)n_maps * ((p.shadow_res + 127) / 128);
+  const long long work = (long long)n_maps * ((p.shadow_res + 127) / 128) * ((p.shadow_res + kNbRows - 1) / kNbRows);
   shadow_neighbourhood_kernel<<<unsigned(work < (1 << 30) ? work : (1 << 30)), 128, 0,
                                 static_cast<cudaStream_t>(stream)>>>(p);
   const cudaError_t e = cudaGetLastError();

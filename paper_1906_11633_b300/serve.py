@@ -267,8 +267,9 @@ class GpuBackend:
     def bytes_needed(self, batches) -> int:
         px = sum(b.total_pixels for b in batches)
         tris = max(int(b.tris_per_sample().max()) for b in batches)
-        # outputs (14 B per pixel) + workspace + parameters, + shadow maps and their neighbourhood table
-        maps = sum(b.n_samples * 4 * b.shadow_faces * b.shadow_res ** 2 * 12
+        # outputs (14 B per pixel) + workspace + parameters, + shadow maps (4 B per texel) and their
+        # neighbourhood table (4 B + a 1-byte count per texel)
+        maps = sum(b.n_samples * 4 * b.shadow_faces * b.shadow_res ** 2 * 9
                    for b in batches if getattr(b, "shadow_view", None) is not None)
         return int(px * 14 + self.ws_a + self.ws_b * tris + sum(b.n_samples for b in batches) * 4096 + maps)
 

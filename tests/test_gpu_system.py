@@ -24,9 +24,15 @@ def renderer():
     return Renderer(sg.hand_meshes())
 
 
-def _equal(a, b):
+def _equal(a, b, batch=None):
+    """Channel by channel; shadow maps only where a light casts (the others are left as they were)."""
     for k in a:
-        np.testing.assert_array_equal(to_numpy({k: a[k]})[k], to_numpy({k: b[k]})[k], err_msg=k)
+        x, y = to_numpy({k: a[k]})[k], to_numpy({k: b[k]})[k]
+        if k == "shadow_map":
+            cast = (np.arange(4)[None, :, None] < batch.light_meta[:, :1, None]) & (batch.shadow_intr[..., 0] != 0)
+            assert cast.any()
+            x, y = x[cast], y[cast]
+        np.testing.assert_array_equal(x, y, err_msg=k)
 
 
 def test_graph_replay_matches_direct_render_and_takes_new_contents(renderer):
@@ -51,11 +57,11 @@ def test_graph_replay_with_shadow_maps(renderer):
     assert "shadow_map" in g.out
     out = g.replay()
     torch.cuda.synchronize()
-    _equal(out, renderer.render(renderer.upload(b1)))
+    _equal(out, renderer.render(renderer.upload(b1)), b1)
     g.update(b2)
     out = g.replay()
     torch.cuda.synchronize()
-    _equal(out, renderer.render(renderer.upload(b2)))
+    _equal(out, renderer.render(renderer.upload(b2)), b2)
 
 
 def test_uneven_batch_in_one_launch_matches_plain_launches(renderer):
