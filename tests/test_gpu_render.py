@@ -454,8 +454,9 @@ def test_graded_tracked_point_lit_batch_matches_oracle(hand_renderer, oracle):
 
 @pytest.mark.parametrize("mode", [L.ORRB_MODE_FUSED, L.ORRB_MODE_PLAIN])
 def test_ragged_shadow_maps_match_oracle(hand_renderer, oracle, mode):
-    """Shadow maps of a ragged side (257: a partial tile column in the shadow pass and a one-column
-    block in the neighbourhood table) with camera images of a ragged width, against the oracle."""
+    """Shadow maps of a ragged side (257: a partial tile column in the shadow pass, and a one-column
+    block and a one-row walk in the neighbourhood table) with camera images of a ragged width,
+    against the oracle."""
     b = sg.benchmark_batch(47, np.arange(3), res=72, grading=False, shadow_res=257)
     o = oracle.render(b, debug=True, gbuffer=True)
     g = render_np(hand_renderer, b, config(mode=mode, tile_w=64, tile_h=2), gbuffer=True)
