@@ -940,10 +940,9 @@ __device__ void big_spans(const Params& p, const CtaShared& sh, const Scratch& s
 }
 
 // kLight: the batch has a cone table (type-2, spot, lights can occur) or material emission.
-// kShadow: vis[l] is light l's shadow factor.
-template <bool kLight, bool kShadow = false>
-__device__ void shade(const CtaShared& sh, const float P[3], const float n[3], int mat, float rgb[3],
-                      const float* vis = nullptr) {
+// (The shadowed instances shade with shade_shadowed, below.)
+template <bool kLight>
+__device__ void shade(const CtaShared& sh, const float P[3], const float n[3], int mat, float rgb[3]) {
   const ImageInfo& im = sh.im;
   const float4 ma = *reinterpret_cast<const float4*>(sh.mat[mat]);
   float2 mb;  // shininess, emission
@@ -988,7 +987,6 @@ __device__ void shade(const CtaShared& sh, const float P[3], const float n[3], i
       r = 1.0f;
       E = lq.w;
     }
-    if (kShadow) E *= vis[l];
     const float ndl = fmaxf(0.0f, (n[0] * Lx + n[1] * Ly + n[2] * Lz) * r);
     D = fmaf(E, ndl, D);
     if (ndl > 0.0f && m[3] != 0.0f) {
@@ -1037,70 +1035,63 @@ __device__ void shadow_setup(const Params& p, const ImageInfo& im, ShadowInfo& s
   }
 }
 
-// The shadow factors of the casting lights at the G-buffer position P (whose three coordinates
-// the resolve computes with separately rounded operations), and the G-buffer word (slot |
-// shadowed taps of light l << (8 + 4l)).  P is projected into each light's map with
-// round-to-nearest operations in a fixed order (the reciprocal is correctly rounded, so it
-// equals 1 / z), then the 3 x 3 texels around it are compared with its depth less the bias; the
-// factor (9 - k) / 9 comes from a table.
-__device__ __forceinline__ int shadow_lookup(const Params& p, const ImageInfo& im, const ShadowInfo& sd,
-                                             const float P[3], int mat, float vis[kMaxLights]) {
-  const float P0 = P[0], P1 = P[1], P2 = P[2];
+// The shadowed taps k (0..9) of light l at the G-buffer position P (whose three coordinates the
+// resolve computes with separately rounded operations).  P is projected into the light's maps
+// with round-to-nearest operations in a fixed order (the reciprocal is correctly rounded, so it
+// equals 1 / z); the first casting face whose map contains the projection decides, and the 3 x 3
+// texels around it are compared with the point's depth less the bias.  The neighbourhood table
+// settles lit points and points behind every occupied tap in one or two loads; the others count
+// the taps.  A point that no face contains has k = 0.
+__device__ __forceinline__ int shadow_lookup_one(const Params& p, const ImageInfo& im, const ShadowInfo& sd,
+                                                 float P0, float P1, float P2, int l) {
   const int R = p.shadow_res, F = p.shadow_faces;
-  int word = mat;
+  for (int f = 0; f < F; f++) {  // the first casting face whose map contains the point decides
+    if (!sd.cast[l][f]) continue;
+    const float* M = sd.sm[l][f];
+    const float* si = sd.si[l][f];
+    const float q2 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[8], P0), __fmul_rn(M[9], P1)), __fmul_rn(M[10], P2)), M[11]);
+    const float z = -q2;
+    if (!(z > si[4])) continue;
+    const float q0 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[0], P0), __fmul_rn(M[1], P1)), __fmul_rn(M[2], P2)), M[3]);
+    const float q1 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[4], P0), __fmul_rn(M[5], P1)), __fmul_rn(M[6], P2)), M[7]);
+    const bool ortho = si[6] != 0.0f;  // (orthographic: a directional light's camera)
+    const float iw = ortho ? 1.0f : __frcp_rn(z);
+    const float u = __fadd_rn(si[2], __fmul_rn(si[0], ortho ? q0 : __fmul_rn(q0, iw)));
+    const float v = __fsub_rn(si[3], __fmul_rn(si[1], ortho ? q1 : __fmul_rn(q1, iw)));
+    if (!(fabsf(u) < kGuardPx) || !(fabsf(v) < kGuardPx)) continue;
+    const int i0 = int(floorf(u)), j0 = int(floorf(v));
+    if (i0 < 0 || j0 < 0 || i0 >= R || j0 >= R) continue;
+    const float zb = __fsub_rn(z, si[5]);
+    const size_t m0 = (((size_t)im.s * kMaxLights + l) * F + f) * R * R;
+    int k = -1;
+    if (p.shadow_nb) {  // one entry settles lit points and those behind every occupied tap
+      const size_t t = m0 + (size_t)j0 * R + i0;
+      const unsigned e = __ldg(p.shadow_nb + t);
+      const float lo = __half2float(__ushort_as_half((unsigned short)(e & 0xffffu)));
+      const float hi = __half2float(__ushort_as_half((unsigned short)(e >> 16)));
+      if (!(zb > lo)) k = 0;  // no occupied tap is nearer than the point
+      else if (zb > hi) k = __ldg(p.shadow_cnt + t);  // every occupied tap is nearer
+    }
+    if (k < 0) {
+      k = 0;
+      const float* map = p.shadow_map + m0;
+      const bool col[3] = {i0 - 1 >= 0, true, i0 + 1 < R};
 #pragma unroll
-  for (int l = 0; l < kMaxLights; l++) {
-    vis[l] = 1.0f;
-    for (int f = 0; f < F; f++) {  // the first casting face whose map contains the point decides
-      if (!sd.cast[l][f]) continue;
-      const float* M = sd.sm[l][f];
-      const float* si = sd.si[l][f];
-      const float q2 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[8], P0), __fmul_rn(M[9], P1)), __fmul_rn(M[10], P2)), M[11]);
-      const float z = -q2;
-      if (!(z > si[4])) continue;
-      const float q0 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[0], P0), __fmul_rn(M[1], P1)), __fmul_rn(M[2], P2)), M[3]);
-      const float q1 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[4], P0), __fmul_rn(M[5], P1)), __fmul_rn(M[6], P2)), M[7]);
-      const bool ortho = si[6] != 0.0f;  // (orthographic: a directional light's camera)
-      const float iw = ortho ? 1.0f : __frcp_rn(z);
-      const float u = __fadd_rn(si[2], __fmul_rn(si[0], ortho ? q0 : __fmul_rn(q0, iw)));
-      const float v = __fsub_rn(si[3], __fmul_rn(si[1], ortho ? q1 : __fmul_rn(q1, iw)));
-      if (!(fabsf(u) < kGuardPx) || !(fabsf(v) < kGuardPx)) continue;
-      const int i0 = int(floorf(u)), j0 = int(floorf(v));
-      if (i0 < 0 || j0 < 0 || i0 >= R || j0 >= R) continue;
-      const float zb = __fsub_rn(z, si[5]);
-      const size_t m0 = (((size_t)im.s * kMaxLights + l) * F + f) * R * R;
-      int k = -1;
-      if (p.shadow_nb) {  // one entry settles lit points and those behind every occupied tap
-        const size_t t = m0 + (size_t)j0 * R + i0;
-        const unsigned e = __ldg(p.shadow_nb + t);
-        const float lo = __half2float(__ushort_as_half((unsigned short)(e & 0xffffu)));
-        const float hi = __half2float(__ushort_as_half((unsigned short)(e >> 16)));
-        if (!(zb > lo)) k = 0;  // no occupied tap is nearer than the point
-        else if (zb > hi) k = __ldg(p.shadow_cnt + t);  // every occupied tap is nearer
-      }
-      if (k < 0) {
-        k = 0;
-        const float* map = p.shadow_map + m0;
-        const bool col[3] = {i0 - 1 >= 0, true, i0 + 1 < R};
+      for (int bb = -1; bb <= 1; bb++) {
+        const int jj = j0 + bb;
+        if (jj < 0 || jj >= R) continue;
+        const float* row = map + jj * R + i0;  // (within a map, offsets fit 32 bits)
 #pragma unroll
-        for (int b = -1; b <= 1; b++) {
-          const int jj = j0 + b;
-          if (jj < 0 || jj >= R) continue;
-          const float* row = map + jj * R + i0;  // (within a map, offsets fit 32 bits)
-#pragma unroll
-          for (int a = -1; a <= 1; a++) {
-            if (!col[a + 1]) continue;
-            const float d = __ldg(row + a);
-            k += d > 0.0f && zb > d;
-          }
+        for (int aa = -1; aa <= 1; aa++) {
+          if (!col[aa + 1]) continue;
+          const float d = __ldg(row + aa);
+          k += d > 0.0f && zb > d;
         }
       }
-      vis[l] = kPcfFactor[k];
-      word |= k << (8 + 4 * l);
-      break;
     }
+    return k;
   }
-  return word;
+  return 0;
 }
 
 // The cone of spot light l in view space (its thread, in the spot instances only, after
@@ -1157,6 +1148,71 @@ __device__ __forceinline__ uint8_t quantise(float v) { return (uint8_t)__float2u
 
 
 // Walks the pixels of a box (px0, py0, width bw) with index j = lane, lane+32, ...
+// Shading in the shadowed instances, returning the G-buffer word (slot | k of light l << (8 + 4l)).
+// Each light's lookup sits inside the light loop, and the loop is not unrolled: unrolled over four
+// lights, the inlined lookups made the kernel's code large enough for instruction fetch to stall
+// warps.  The arithmetic is that of shade<true>, with E scaled by the factor (9 - k) / 9 from a table.
+__device__ int shade_shadowed(const Params& p, const CtaShared& sh, const ShadowInfo& sd, const float P[3],
+                              const float n[3], int mat, float rgb[3]) {
+  const ImageInfo& im = sh.im;
+  const float4 ma = *reinterpret_cast<const float4*>(sh.mat[mat]);
+  const float2 mb = *reinterpret_cast<const float2*>(&sh.mat[mat][4]);
+  const float m[5] = {ma.x, ma.y, ma.z, ma.w, mb.x};
+  float Vv[3];
+  if (im.ortho) {
+    Vv[0] = 0.0f;
+    Vv[1] = 0.0f;
+    Vv[2] = 1.0f;
+  } else {
+    float rl = rsqrtf(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
+    Vv[0] = -P[0] * rl;
+    Vv[1] = -P[1] * rl;
+    Vv[2] = -P[2] * rl;
+  }
+  int word = mat;
+  float D = mb.y, S = 0.0f;
+#pragma unroll 1
+  for (int l = 0; l < im.n_lights && l < kMaxLights; l++) {
+    const int k = shadow_lookup_one(p, im, sd, P[0], P[1], P[2], l);
+    word |= k << (8 + 4 * l);
+    const float4 lq = *reinterpret_cast<const float4*>(im.lv[l]);
+    float Lx, Ly, Lz, r, E;
+    if (im.light_type != 1) {
+      Lx = lq.x - P[0];
+      Ly = lq.y - P[1];
+      Lz = lq.z - P[2];
+      r = rsqrtf(Lx * Lx + Ly * Ly + Lz * Lz);
+      E = lq.w * (r * r);
+      if (im.light_type == 2) {
+        const float4 sq = *reinterpret_cast<const float4*>(im.la[l]);
+        const float t = __saturatef(fmaf(-(Lx * sq.x + Ly * sq.y + Lz * sq.z), r, sq.w));
+        E *= t * t * (3.0f - 2.0f * t);
+      }
+    } else {
+      Lx = lq.x;
+      Ly = lq.y;
+      Lz = lq.z;
+      r = 1.0f;
+      E = lq.w;
+    }
+    E *= kPcfFactor[k];
+    const float ndl = fmaxf(0.0f, (n[0] * Lx + n[1] * Ly + n[2] * Lz) * r);
+    D = fmaf(E, ndl, D);
+    if (ndl > 0.0f && m[3] != 0.0f) {
+      const float H0 = fmaf(Lx, r, Vv[0]), H1 = fmaf(Ly, r, Vv[1]), H2 = fmaf(Lz, r, Vv[2]);
+      const float h2 = H0 * H0 + H1 * H1 + H2 * H2;
+      if (h2 > 0.0f) {
+        const float ndh = fmaxf(0.0f, (n[0] * H0 + n[1] * H1 + n[2] * H2) * rsqrtf(h2));
+        S = fmaf(E, m[3] * lobe_pow(ndh, m[4]), S);
+      }
+    }
+  }
+  rgb[0] = im.scale * fmaf(m[0], im.amb[0] + D, S);
+  rgb[1] = im.scale * fmaf(m[1], im.amb[1] + D, S);
+  rgb[2] = im.scale * fmaf(m[2], im.amb[2] + D, S);
+  return word;
+}
+
 struct BoxWalk {
   int px, py;
   __device__ __forceinline__ BoxWalk(int j, int px0, int py0, int bw) {
@@ -1430,9 +1486,7 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
         }
         if (kShadow) {
           const ShadowInfo& sd = *reinterpret_cast<const ShadowInfo*>(spans + kSpanCap);
-          float vis[kMaxLights];
-          word = shadow_lookup(p, im, sd, P, mat, vis);
-          shade<true, true>(sh, P, n, mat, rgb, vis);
+          word = shade_shadowed(p, sh, sd, P, n, mat, rgb);
         } else {
           shade<(kF & kFeatLight) != 0>(sh, P, n, mat, rgb);
         }
