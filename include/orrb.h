@@ -240,6 +240,12 @@ typedef struct {
   int32_t tile_h;        /* screen-tile height in pixels, in [1, 64], tile_w * tile_h <= 8192; 0 = 2 */
   int32_t threads;       /* threads per CTA: 256 or 512; 0 = 512 */
   int32_t ctas_per_sm;   /* fused mode: resident CTAs per SM; 0 = as many as fit */
+  int32_t reserved;      /* must be 0 */
+  int64_t wait_cycles;   /* fused mode: a wait between CTAs (a CTA looking for raster tiles to help
+                            with, an image's owner waiting for its helpers) gives up after this many
+                            SM clock cycles, sets ORRB_DEV_TIMEOUT and leaves the launch (the
+                            outputs may then be incomplete); 0 = 2e9, about a second.  A small value
+                            makes the waits run out on purpose. */
 } orrb_config;
 
 /* Workspace bytes for `shape` under `cfg`.  The workspace is caller-owned
@@ -271,6 +277,9 @@ orrb_status orrb_render_batch(orrb_ctx* ctx, const orrb_batch_shape* shape, cons
  *     ORRB_DEV_* bits (cleared by this call); NULL discards them.
  * The first call on a device looks up the static array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * The address is kept for the life of the process: after a device reset
+ * (cudaDeviceReset, or a reset of the primary context) it is stale, and the
+ * entry point must not be called again until the library is reloaded.
  * All calls share the one array: calls whose GPU work overlaps (different
  * streams, threads or contexts on the same device) race and corrupt each
  * other's results; serialise them on one stream. */

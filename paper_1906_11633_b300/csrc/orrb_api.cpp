@@ -168,6 +168,7 @@ void resolve_config(const orrb_config* in, orrb_config* out) {
   if (c.tile_w == 0) c.tile_w = 256;
   if (c.tile_h == 0) c.tile_h = 2;
   if (c.threads == 0) c.threads = 512;
+  if (c.wait_cycles == 0) c.wait_cycles = 2000000000ll;
   *out = c;
 }
 
@@ -178,6 +179,8 @@ orrb_status check_config(orrb_ctx* ctx, const orrb_config& c) {
   if (c.tile_w * c.tile_h > 8192) return fail(ctx, ORRB_ERR_INVALID_ARG, "tile larger than 8192 px");
   if (c.threads != 256 && c.threads != 512) return fail(ctx, ORRB_ERR_INVALID_ARG, "threads %d", c.threads);
   if (c.ctas_per_sm < 0) return fail(ctx, ORRB_ERR_INVALID_ARG, "ctas_per_sm %d", c.ctas_per_sm);
+  if (c.reserved != 0) return fail(ctx, ORRB_ERR_INVALID_ARG, "reserved config field must be 0");
+  if (c.wait_cycles < 0) return fail(ctx, ORRB_ERR_INVALID_ARG, "wait_cycles %lld", (long long)c.wait_cycles);
   return ORRB_OK;
 }
 
@@ -532,6 +535,7 @@ orrb_status orrb_render_batch(orrb_ctx* ctx, const orrb_batch_shape* shape, cons
   p.scratch = ws + 256;
   p.slot_bytes = P.slot_bytes;
   p.n_slots = P.n_slots;
+  p.wait_cycles = c.wait_cycles;
   p.shadow_nb = p.shadow_res > 0 ? reinterpret_cast<uint32_t*>(ws + P.nb_offset) : nullptr;
   p.shadow_cnt = p.shadow_res > 0 ? reinterpret_cast<uint8_t*>(ws + P.cnt_offset) : nullptr;
   p.plain_sample = -1;
@@ -599,6 +603,7 @@ orrb_status orrb_render_batch_noalloc(orrb_ctx* ctx, const orrb_batch_shape* sha
   p.images_done = reinterpret_cast<uint32_t*>(ws + 8);
   p.scratch = ws + 256;
   p.slot_bytes = P.slot_bytes;
+  p.wait_cycles = c.wait_cycles;
   p.plain_sample = -1;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // the array keeps the previous call's contents: the status word and the queue counters restart at zero

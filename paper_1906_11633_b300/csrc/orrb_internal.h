@@ -112,6 +112,7 @@ struct Params {
   char* scratch;
   size_t slot_bytes;
   int32_t n_slots;
+  long long wait_cycles;  // bounded waits between CTAs give up after this many SM cycles
   // plain mode: the sample this launch renders (-1 in fused mode)
   int32_t plain_sample;
 };

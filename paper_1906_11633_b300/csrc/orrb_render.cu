@@ -108,6 +108,7 @@ struct CtaShared {
   int n_vis, n_big, next_tile, next_job, img;
   int bin_overflow;  // phase B: some tile got more keys than its share of the bin array
   int help_slot, help_cam;
+  int stop;  // a wait for helpers timed out: the CTA takes no further work
   int scan_tmp[33];
 };
 
@@ -1567,9 +1568,8 @@ __device__ inline SmemPtrs carve(char* smem, const Params& p, const SmemLayout& 
   return s;
 }
 
-// Bounded waits: a spin that exceeds this many SM cycles (about a second) sets
+// Bounded waits: a spin that exceeds p.wait_cycles SM cycles (by default about a second) sets
 // ORRB_DEV_TIMEOUT and gives up instead of hanging.
-constexpr long long kSpinBudget = 2000000000ll;
 
 // Raster tiles of the image whose claim word is `claim`, for camera `cam`.  The owner of
 // the slot claims with atomicAdd and counts its own tiles in shared memory (its CTA wrote
@@ -1632,6 +1632,7 @@ __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
   const SmemLayout L = layout_of(p);
   SmemPtrs sp = carve(smem, p, L);
   const Scratch sc = slot_scratch(p, blockIdx.x);
+  if (threadIdx.x == 0) sh.stop = 0;
   while (true) {
     if (threadIdx.x == 0) sh.img = atomicAdd(p.work_counter, 1);
     __syncthreads();
@@ -1663,8 +1664,11 @@ __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
         const unsigned helped = unsigned(sh.im.n_tiles - sh.next_tile);
         const long long t0 = clock64();
         while (atomicAdd(reinterpret_cast<unsigned*>(sc.header + 4), 0u) < helped) {
-          if (clock64() - t0 > kSpinBudget) {
+          if (clock64() - t0 > p.wait_cycles) {
+            // a helper may still be reading this slot: the CTA leaves the launch, so that the
+            // slot is never rewritten under it
             flag_status(p, ORRB_DEV_TIMEOUT);
+            sh.stop = 1;
             break;
           }
           __nanosleep(200);
@@ -1676,6 +1680,7 @@ __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
       atomicAdd(p.images_done, 1u);
     }
     __syncthreads();
+    if (sh.stop) return;
   }
   // helper mode: join the open raster phase with the most tiles left, until every image is done
   long long t0 = clock64();  // start of the current search (thread 0); reset whenever work is found
@@ -1710,7 +1715,7 @@ __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
           t0 = clock64();
         } else {
           if (*reinterpret_cast<volatile unsigned*>(p.images_done) >= unsigned(p.n_cams)) cam = -2;
-          else if (clock64() - t0 > kSpinBudget) {
+          else if (clock64() - t0 > p.wait_cycles) {
             flag_status(p, ORRB_DEV_TIMEOUT);
             cam = -2;
           } else {

@@ -22,8 +22,15 @@ ORRB_GBUFFER_PLANES = 7
 DEFAULT_TILE_W = 256    # the library's defaults for a zero orrb_config field
 DEFAULT_TILE_H = 2
 DEFAULT_THREADS = 512
+ORRB_DEV_BAD_CAMERA = 0x1     # device status word bits (ORRB_DEV_* of include/orrb.h)
+ORRB_DEV_BAD_INSTANCE = 0x2
+ORRB_DEV_TOO_MANY_TRIS = 0x4
+ORRB_DEV_BAD_MATERIAL = 0x8
+ORRB_DEV_BAD_LIGHTS = 0x10
+ORRB_DEV_DROPPED = 0x20
+ORRB_DEV_TIMEOUT = 0x40
 DEV_BITS = {0x1: "bad camera", 0x2: "bad instance", 0x4: "too many triangles", 0x8: "bad material",
-            0x10: "bad lights", 0x20: "triangle dropped by guard band"}
+            0x10: "bad lights", 0x20: "triangle dropped by guard band", 0x40: "a bounded wait between CTAs gave up"}
 
 EXPORTS = ["orrb_create", "orrb_destroy", "orrb_status_string", "orrb_last_error", "orrb_mesh_arena_size",
            "orrb_upload_meshes", "orrb_release_meshes", "orrb_workspace_size", "orrb_render_batch",
@@ -56,7 +63,7 @@ class orrb_outputs(C.Structure):
 
 class orrb_config(C.Structure):
     _fields_ = [("mode", C.c_int32), ("tile_w", C.c_int32), ("tile_h", C.c_int32), ("threads", C.c_int32),
-                ("ctas_per_sm", C.c_int32)]
+                ("ctas_per_sm", C.c_int32), ("reserved", C.c_int32), ("wait_cycles", C.c_int64)]
 
 
 class orrb_param_grads(C.Structure):

@@ -93,8 +93,9 @@ def _mesh_descs(meshes):
 
 
 def config(mode: int = L.ORRB_MODE_FUSED, tile_w: int = 0, tile_h: int = 0, threads: int = 0,
-           ctas_per_sm: int = 0) -> L.orrb_config:
-    return L.orrb_config(mode, tile_w, tile_h, threads, ctas_per_sm)
+           ctas_per_sm: int = 0, wait_cycles: int = 0) -> L.orrb_config:
+    """Launch configuration; 0 picks each default (see orrb_config in include/orrb.h)."""
+    return L.orrb_config(mode, tile_w, tile_h, threads, ctas_per_sm, 0, wait_cycles)
 
 
 class Renderer:

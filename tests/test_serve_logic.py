@@ -143,3 +143,25 @@ def test_request_larger_than_the_whole_budget_fails_and_the_queue_moves_on():
     assert all(r.error is None and r.result is not None for r in rest)
     assert be.peak_bytes <= 4 * small and srv.inflight_bytes == 0
     assert srv.stats(1.0)["failed"] == 1
+
+
+class SlowLaunchBackend(FakeBackend):
+    """A launch that takes long on the host (packing, copies): the request is out of the pending
+    queue but not yet in flight while it runs."""
+
+    def launch(self, batches, k):
+        time.sleep(0.2)
+        return super().launch(batches, k)
+
+
+def test_close_waits_for_a_batch_that_is_still_launching():
+    be = SlowLaunchBackend(gpu_ms=1.0)
+    srv = Server(be, n_streams=2, max_inflight=2, tick_ms=1.0)
+    req = srv.submit(ServeRequest(0, _req_batch(0, 2, 32)))
+    deadline = time.perf_counter() + 5.0
+    while srv.pending and time.perf_counter() < deadline:   # the scheduler has taken it ...
+        time.sleep(0.001)
+    assert not srv.pending and not req.event.is_set()        # ... and is inside the launch
+    srv.close()
+    assert req.event.is_set() and req.error is None and req.result == {"n": 2}
+    assert be.active == 0
