@@ -119,8 +119,12 @@ struct Params {
 
 // Per-slot scratch (one image at a time): sizes in elements, from t_max.
 struct SlotLayout {
-  size_t rec, vis_key, vis_box, bins, big, tile_off, counts, header, total;
+  size_t rec, vis_key, vis_box, bins, big, tile_off, counts, header, pub, total;
 };
+
+// The image state an owner publishes in its slot for helpers (camera, lights, materials, the
+// large triangles' row spans, shadow cameras): at most this many bytes.
+constexpr size_t kPubBytes = 8192;
 
 // Binning keeps its per-tile counters in shared memory up to this many tiles, else in the slot.
 constexpr int kSmemCountTiles = 4094;
@@ -132,6 +136,7 @@ ORRB_HD inline SlotLayout slot_layout(int t_max, int max_tiles) {
   size_t cap = 2 * size_t(t_max) + 2;
   size_t o = 0;
   L.header = o;   o = align256(o + 64);
+  L.pub = o;      o = align256(o + kPubBytes);
   L.rec = o;      o = align256(o + cap * sizeof(Record));
   L.vis_key = o;  o = align256(o + cap * 4);
   L.vis_box = o;  o = align256(o + cap * 8);

@@ -109,6 +109,8 @@ struct CtaShared {
   int bin_overflow;  // phase B: some tile got more keys than its share of the bin array
   int help_slot, help_cam;
   int stop;  // a wait for helpers timed out: the CTA takes no further work
+  float red_score[32];  // helper search: per-warp best score and slot
+  int red_slot[32];
   int scan_tmp[33];
 };
 
@@ -135,6 +137,7 @@ struct WarpTri {  // a binned triangle staged for the warp's fragment expansion 
 };
 
 struct Scratch {
+  char* pub;  // the image state the owner publishes for helpers (PubImage)
   Record* rec;
   uint32_t* vis_key;
   uint2* vis_box;
@@ -142,7 +145,8 @@ struct Scratch {
   uint32_t* big;
   uint32_t* tile_off;
   // header: [0..1] claim word (camera + 1) << 32 | next tile, 0 while no raster phase is
-  // open; [2] n_vis; [3] n_big; [4] tiles finished; [5] tiles of the open image
+  // open; [2] n_vis; [3] n_big; [4] tiles finished; [5] tiles of the open image; [6] helper CTAs
+  // that joined the open image
   int* counts;  // per-tile counters and cursors when they do not fit in shared memory
   int* header;
   __device__ unsigned long long* claim() const { return reinterpret_cast<unsigned long long*>(header); }
@@ -166,6 +170,19 @@ struct SmemPtrs {
   char* uni;
   uint32_t* spans;
 };
+
+// What an owner publishes in its slot when it opens the raster phase, so that a helper takes
+// the image's prepared state with one copy instead of setting the image up again.
+struct PubImage {
+  ImageInfo im;
+  alignas(16) float mat[kMaxMaterials][8];
+  int n_big, pad[3];
+  uint32_t spans[kSpanCap];
+  ShadowInfo sd;
+};
+static_assert(sizeof(PubImage) <= kPubBytes, "published image state exceeds its slot region");
+static_assert(sizeof(PubImage) % 16 == 0 && alignof(PubImage) <= 16 && sizeof(ImageInfo) % 16 == 0 &&
+                  sizeof(ShadowInfo) % 16 == 0, "published image state is copied in 16-byte words");
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
 
@@ -193,6 +210,7 @@ __device__ inline Scratch slot_scratch(const Params& p, int slot) {
   char* b = p.scratch + size_t(slot) * p.slot_bytes;
   Scratch s;
   s.header = reinterpret_cast<int*>(b + L.header);
+  s.pub = b + L.pub;
   s.rec = reinterpret_cast<Record*>(b + L.rec);
   s.vis_key = reinterpret_cast<uint32_t*>(b + L.vis_key);
   s.vis_box = reinterpret_cast<uint2*>(b + L.vis_box);
@@ -1536,6 +1554,42 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
   __syncwarp();
 }
 
+// The owner's prepared image state (camera, lights, materials, grading, spot cones, the large
+// triangles' row spans, shadow cameras) into its slot, every thread a share of the 16-byte words,
+// each fencing its own writes before the barrier that precedes the opening of the raster phase.
+template <bool kShadow>
+__device__ void publish_image(const CtaShared& sh, const SmemPtrs& sp, char* pub) {
+  PubImage* g = reinterpret_cast<PubImage*>(pub);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  auto copy = [&](int4* dst, const int4* src, int n) {
+    for (int i = tid; i < n; i += nt) dst[i] = src[i];
+  };
+  copy(reinterpret_cast<int4*>(&g->im), reinterpret_cast<const int4*>(&sh.im), int(sizeof(ImageInfo) / 16));
+  copy(reinterpret_cast<int4*>(g->mat), reinterpret_cast<const int4*>(sh.mat), int(sizeof(g->mat) / 16));
+  copy(reinterpret_cast<int4*>(g->spans), reinterpret_cast<const int4*>(sp.spans), kSpanCap / 4);
+  if (kShadow)
+    copy(reinterpret_cast<int4*>(&g->sd), reinterpret_cast<const int4*>(sp.spans + kSpanCap), int(sizeof(ShadowInfo) / 16));
+  if (tid == 0) g->n_big = sh.n_big;
+  __threadfence();
+}
+
+// A helper takes the published state of the image it joins (loads that bypass L1: the slot was
+// written by another SM and may have held an earlier image).
+template <bool kShadow>
+__device__ void take_published(CtaShared& sh, const SmemPtrs& sp, const char* pub) {
+  const PubImage* g = reinterpret_cast<const PubImage*>(pub);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  auto copy = [&](int4* dst, const int4* src, int n) {
+    for (int i = tid; i < n; i += nt) dst[i] = __ldcg(src + i);
+  };
+  copy(reinterpret_cast<int4*>(&sh.im), reinterpret_cast<const int4*>(&g->im), int(sizeof(ImageInfo) / 16));
+  copy(reinterpret_cast<int4*>(sh.mat), reinterpret_cast<const int4*>(g->mat), int(sizeof(g->mat) / 16));
+  copy(reinterpret_cast<int4*>(sp.spans), reinterpret_cast<const int4*>(g->spans), kSpanCap / 4);
+  if (kShadow)
+    copy(reinterpret_cast<int4*>(sp.spans + kSpanCap), reinterpret_cast<const int4*>(&g->sd), int(sizeof(ShadowInfo) / 16));
+  if (tid == 0) sh.n_big = __ldcg(&g->n_big);
+}
+
 // Phase R for the current image: warps pull tiles first, first + stride, ... from the
 // CTA's counter until none is left.
 template <int kF>
@@ -1648,12 +1702,18 @@ __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
       __syncthreads();
       int* counts = p.max_tiles > kSmemCountTiles ? sc.counts : reinterpret_cast<int*>(sp.uni);
       bin_phase(p, sh, counts, counts + (p.max_tiles + 2), sc);
-      big_spans(p, sh, sc, sp.spans);  // the barrier below publishes the table
-      if (threadIdx.x == 0) {  // open the raster phase to helpers
+      big_spans(p, sh, sc, sp.spans);
+      __syncthreads();  // (the span table is complete)
+      publish_image<kShadow>(sh, sp, sc.pub);
+      if (threadIdx.x == 0) {
         sc.header[3] = sh.n_big;
         sc.header[4] = 0;
         sc.header[5] = sh.im.n_tiles;
+        sc.header[6] = 0;
         sh.next_tile = 0;
+      }
+      __syncthreads();  // (every thread fenced its part of the published state)
+      if (threadIdx.x == 0) {  // open the raster phase to helpers
         __threadfence();
         atomicExch(sc.claim(), (unsigned long long)(cam + 1) << 32);
       }
@@ -1682,49 +1742,68 @@ __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
     __syncthreads();
     if (sh.stop) return;
   }
-  // helper mode: join the open raster phase with the most tiles left, until every image is done
+  // helper mode: join an open raster phase, until every image is done.  Every thread scores a
+  // share of the slots by the tiles left per helper that already joined, so idle CTAs spread over
+  // the open images instead of all choosing the same one.
   long long t0 = clock64();  // start of the current search (thread 0); reset whenever work is found
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   while (true) {
-    if (threadIdx.x < 32) {  // warp 0 scans the slots, one per lane at a time
-      int best = -1, best_left = 0;
-      for (int s = threadIdx.x; s < p.n_slots; s += 32) {
-        const Scratch o = slot_scratch(p, s);
-        const unsigned long long w = *reinterpret_cast<volatile unsigned long long*>(o.header);
-        if (w == 0ull) continue;
-        const int left = *reinterpret_cast<volatile int*>(o.header + 5) - int(unsigned(w));
-        if (left > best_left) {
-          best_left = left;
-          best = s;
-        }
+    float best_score = 0.0f;
+    int best = -1;
+    for (int s = threadIdx.x; s < p.n_slots; s += blockDim.x) {
+      const int* h = reinterpret_cast<const int*>(p.scratch + size_t(s) * p.slot_bytes);  // (the header leads the slot)
+      const unsigned long long w = *reinterpret_cast<const volatile unsigned long long*>(h);
+      if (w == 0ull) continue;
+      const int left = *reinterpret_cast<const volatile int*>(h + 5) - int(unsigned(w));
+      if (left <= 0) continue;
+      const float score = float(left) / float(1 + *reinterpret_cast<const volatile int*>(h + 6));
+      if (score > best_score) {
+        best_score = score;
+        best = s;
       }
-      for (int off = 16; off > 0; off >>= 1) {
-        const int ol = __shfl_down_sync(kFull, best_left, off), ob = __shfl_down_sync(kFull, best, off);
-        if (ol > best_left) {
-          best_left = ol;
-          best = ob;
-        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      const float os = __shfl_down_sync(kFull, best_score, off);
+      const int ob = __shfl_down_sync(kFull, best, off);
+      if (os > best_score) {
+        best_score = os;
+        best = ob;
       }
+    }
+    if (lane == 0) {
+      sh.red_score[warp] = best_score;
+      sh.red_slot[warp] = best;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      best_score = 0.0f;
+      best = -1;
+      for (int k = 0; k < int(blockDim.x >> 5); k++)
+        if (sh.red_score[k] > best_score) {
+          best_score = sh.red_score[k];
+          best = sh.red_slot[k];
+        }
       int cam = -1;
       if (best >= 0) {
-        const unsigned long long w = *reinterpret_cast<volatile unsigned long long*>(slot_scratch(p, best).header);
-        cam = int(w >> 32) - 1;   // 0 -> -1: closed meanwhile, search again
+        int* h = reinterpret_cast<int*>(p.scratch + size_t(best) * p.slot_bytes);
+        const unsigned long long w = *reinterpret_cast<volatile unsigned long long*>(h);
+        cam = int(w >> 32) - 1;  // 0 -> -1: closed meanwhile, search again
         if (cam < 0) best = -1;
+        else atomicAdd(h + 6, 1);
       }
-      if (threadIdx.x == 0) {
-        if (best >= 0) {
-          t0 = clock64();
+      if (best >= 0) {
+        t0 = clock64();
+      } else {
+        if (*reinterpret_cast<volatile unsigned*>(p.images_done) >= unsigned(p.n_cams)) cam = -2;
+        else if (clock64() - t0 > p.wait_cycles) {
+          flag_status(p, ORRB_DEV_TIMEOUT);
+          cam = -2;
         } else {
-          if (*reinterpret_cast<volatile unsigned*>(p.images_done) >= unsigned(p.n_cams)) cam = -2;
-          else if (clock64() - t0 > p.wait_cycles) {
-            flag_status(p, ORRB_DEV_TIMEOUT);
-            cam = -2;
-          } else {
-            __nanosleep(500);
-          }
+          __nanosleep(500);
         }
-        sh.help_slot = best;
-        sh.help_cam = cam;
       }
+      sh.help_slot = best;
+      sh.help_cam = cam;
     }
     __syncthreads();
     const int slot = sh.help_slot, cam = sh.help_cam;
@@ -1732,14 +1811,7 @@ __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
     if (slot >= 0 && cam >= 0) {
       const Scratch o = slot_scratch(p, slot);
       __threadfence();
-      setup_image<kPass>(p, cam, sh, sp.mprefix, sp.tprefix, sp.mbegin, false);
-      if (threadIdx.x == 0) sh.n_big = *reinterpret_cast<volatile int*>(o.header + 3);
-      if (kGrade && threadIdx.x == 0) grading_setup(p, sh.im);
-      if (kLight && threadIdx.x < kMaxLights) spot_setup(p, sh.im, threadIdx.x);
-      if (kShadow && threadIdx.x < kMaxLights)
-        shadow_setup(p, sh.im, *reinterpret_cast<ShadowInfo*>(sp.spans + kSpanCap), threadIdx.x);
-      __syncthreads();
-      big_spans(p, sh, o, sp.spans);
+      take_published<kShadow>(sh, sp, o.pub);
       __syncthreads();
       raster_claimed<kF>(p, sh, o, sp, L, cam, false);
     }
