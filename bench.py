@@ -95,13 +95,70 @@ def fp32_peak_tflops(sms: int, mhz: float) -> float:
     return sms * 128 * 2 * mhz * 1e6 / 1e12
 
 
-def shading_flops(n_visible: int, n_lit: int, n_light_terms: int) -> float:
-    """Algorithmic FP32 operations of the shading step over visible pixels, counted from the defined
-    arithmetic (each +, -, x, /, sqrt, max, floor, conversion, exp2, log2 = 1): 76 per visible pixel
-    (view vector, normal, ambient and exposure terms, clamp and quantisation of three channels),
-    31 per (pixel, light) (light vector, distance, falloff, n.L, diffuse sum) and 20 more per
-    (pixel, light) with n.L > 0 (half vector, n.H and the specular lobe)."""
-    return float(76 * n_visible + 31 * n_light_terms + 20 * n_lit)
+# Algorithmic FP32 operations of the per-pixel steps (G-buffer interpolation, shading, grading,
+# quantisation), with the per-term counts that the oracle tallies beside its own arithmetic
+# (oracle/orrb_oracle.c, render_image and shade_f32; each +, -, *, /, sqrt, pow, negation,
+# comparison and clamp counts once; work that depends on the image only, such as moving the lights
+# to view space, counts once per image).  tests/test_oracle_flops.py checks this function against
+# the oracle's count on the same G-buffer.  Shadow-map lookups are not counted (a lower bound for
+# the shadowed workloads).
+FLOP_PIXEL = {False: 91, True: 74}        # per visible pixel: perspective, orthographic camera
+FLOP_LIGHT = {0: 33, 1: 20, 2: 33}        # per (visible pixel, light) by light type
+FLOP_SPOT_CONE, FLOP_SPOT_NULL = 16, 8    # more per (pixel, spot light): a cone, a null cone
+FLOP_LIT = 21                             # more per (pixel, light) with n . L > 0
+FLOP_GRADE, FLOP_GRADE_BG = 64, 64 + 18   # per graded visible pixel, per graded background pixel
+
+
+def alg_flops(batch, gb_pos, gb_nrm, gb_mat) -> float:
+    """The algorithmic FP32 operations of one render of `batch`, from its G-buffer (positions
+    [N, 3], normals [N, 3], material words [N], -1 background)."""
+    total = 0
+    start = 0
+    for c in range(batch.n_cams):
+        n = int(batch.cam_wh[c, 0]) * int(batch.cam_wh[c, 1])
+        sl = slice(start, start + n)
+        start += n
+        s = int(batch.cam_sample[c])
+        ortho = bool(batch.cam_intr[c, 5] != 0)
+        fg = gb_mat[sl] >= 0
+        nv = int(fg.sum())
+        count, typ = int(batch.light_meta[s, 0]), int(batch.light_meta[s, 1])
+        if not (typ in (0, 1) or (typ == 2 and batch.light_spot is not None)):
+            count = 0
+        graded = batch.grading is not None
+        total += 2 + count * (18 + (16 if typ == 2 else 0)) + 1 + (6 if graded else 0)   # per image
+        total += nv * FLOP_PIXEL[ortho] + (n - nv) * (FLOP_GRADE_BG if graded else 0) + (nv * FLOP_GRADE if graded else 0)
+        if nv == 0 or count == 0:
+            continue
+        V = batch.cam_view[c].astype(np.float64)
+        P = gb_pos[sl][fg].astype(np.float64)
+        nrm = gb_nrm[sl][fg].astype(np.float64)
+        for l in range(count):
+            total += nv * FLOP_LIGHT[typ]
+            if typ == 2:
+                sp = batch.light_spot[s, l]
+                total += nv * (FLOP_SPOT_CONE if sp[4] > sp[3] else FLOP_SPOT_NULL)
+            if typ == 1:
+                Ld = np.broadcast_to(-(V[:, :3] @ batch.light[s, l, :3]), P.shape)
+            else:
+                Ld = V[:, :3] @ batch.light[s, l, :3] + V[:, 3] - P
+            total += FLOP_LIT * int((np.einsum("ij,ij->i", nrm, Ld) > 0).sum())
+    return float(total)
+
+
+def measured_fp32_peak(reps: int = 3):
+    """FP32 multiply-add throughput measured on this device by the probe library (scalar FFMA and
+    packed FFMA2 chains, CUDA events): (best TFLOP/s, scalar, packed), or None if unavailable."""
+    import ctypes
+    path = os.path.join(ROOT, "paper_1906_11633_b300", "libfp32peak.so")
+    try:
+        lib = ctypes.CDLL(path)
+    except OSError:
+        return None
+    a, b = ctypes.c_double(), ctypes.c_double()
+    if lib.orrb_measure_fp32_peak(reps, ctypes.byref(a), ctypes.byref(b)) != 0:
+        return None
+    return max(a.value, b.value) / 1e12, a.value / 1e12, b.value / 1e12
 
 
 class ClockSampler:
@@ -335,16 +392,13 @@ def run_ours(args, world, rank, local):
     alg_bytes = BYTES_PER_PX * N + param_bytes + mesh_bytes
     # algorithmic shading FLOPs from this batch's visible pixels and lights
     o = r.render(db, cfg=cfg, rgb_linear=True, gbuffer=True)
-    gmat = o["gbuffer"][6].view(torch.int32).cpu().numpy()
-    fg = gmat >= 0
-    per_img_px = (batch.cam_wh[:, 0] * batch.cam_wh[:, 1]).astype(np.int64)
-    nl_px = np.repeat(batch.light_meta[batch.cam_sample, 0], per_img_px)
     gb = o["gbuffer"].cpu().numpy()
-    lit = _lit_lights(batch, gb, fg, per_img_px)
-    flops = shading_flops(int(fg.sum()), lit, int(nl_px[fg].sum()))
+    flops = alg_flops(batch, gb[0:3].T, gb[3:6].T, gb[6].view(np.int32))
     props = torch.cuda.get_device_properties(dev)
     clk_sum = clk.summary()
-    fp32_peak = fp32_peak_tflops(props.multi_processor_count, float(peaks.get("sm_max_mhz", 2032.0)))
+    nominal = fp32_peak_tflops(props.multi_processor_count, float(peaks.get("sm_max_mhz", 2032.0)))
+    probe = measured_fp32_peak()
+    fp32_peak = probe[0] if probe is not None else nominal
     t_hbm = alg_bytes / (hbm * 1e9)
     t_fp32 = flops / (fp32_peak * 1e12)
     bound = "hbm" if t_hbm >= t_fp32 else "alu"
@@ -357,7 +411,11 @@ def run_ours(args, world, rank, local):
             "frac": (achieved_gbs / hbm) if bound == "hbm" else (achieved_tf / fp32_peak),
             "traffic": args.traffic if args.traffic is not None else profiled_traffic(),
             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if bound == "hbm" else
-                           "nominal: SMs x 128 x 2 x max SM clock",
+                           ("measured FP32 FMA-chain probe" if probe is not None else
+                            "nominal: SMs x 128 x 2 x max SM clock"),
+            "fp32_peak_tflops": {"measured_scalar_ffma": probe[1] if probe else None,
+                                 "measured_packed_ffma2": probe[2] if probe else None,
+                                 "nominal": nominal, "used": fp32_peak},
             "alg_bytes_per_launch": alg_bytes, "alg_fp32_flop_per_launch": flops,
             "t_roof_us": 1e6 * max(t_hbm, t_fp32), "t_hbm_us": 1e6 * t_hbm, "t_fp32_us": 1e6 * t_fp32,
             "roofline_frac_of_step": 1e3 * max(t_hbm, t_fp32) / kernel_ms,
@@ -394,31 +452,6 @@ def run_ours(args, world, rank, local):
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_baseline(batch)
     print(json.dumps(line), flush=True)
-
-
-def _lit_lights(batch, gb, fg, per_img_px):
-    """Number of (pixel, light) pairs with n.L > 0 (they evaluate the specular lobe)."""
-    total = 0
-    start = 0
-    for c in range(batch.n_cams):
-        n = int(per_img_px[c])
-        sl = slice(start, start + n)
-        start += n
-        m = fg[sl]
-        if not m.any():
-            continue
-        s = batch.cam_sample[c]
-        V = batch.cam_view[c].astype(np.float64)
-        P = gb[0:3, sl][:, m].T
-        nrm = gb[3:6, sl][:, m].T
-        for l in range(batch.light_meta[s, 0]):
-            lp = V[:, :3] @ batch.light[s, l, :3] + V[:, 3]
-            if batch.light_meta[s, 1] != 1:          # point and spot lights; 1 is directional
-                Ld = lp - P
-            else:
-                Ld = np.broadcast_to(-(V[:, :3] @ batch.light[s, l, :3]), P.shape)
-            total += int((np.einsum("ij,ij->i", nrm, Ld) > 0).sum())
-    return total
 
 
 def run_uneven(args, world, rank, local):

@@ -59,7 +59,7 @@ class _Batch(C.Structure):
 class _Outputs(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in (
         "rgb", "depth", "normal", "seg", "rgb_linear", "gb_pos", "gb_nrm", "gb_mat", "prim", "depth2", "counters",
-        "tracker")] + [("tracker_stride", C.c_int32)]
+        "tracker")] + [("tracker_stride", C.c_int32), ("flops", C.c_void_p)]
 
 
 def lib():
@@ -172,12 +172,15 @@ def shadow_maps(batch, threads: int | None = None, pin=None):
 
 
 def render(batch, threads: int | None = None, gbuffer: bool = False, debug: bool = False, cams=None,
-           tracker: bool = False):
+           tracker: bool = False, flops: bool = False):
     """Oracle render of a batch.  Returns a dict of numpy channel arrays.
 
     `cams`: optional (begin, end) camera range; pixels of other images stay zero.
     `tracker`: also the per (camera, instance) rows [n_cams, max instances per sample, 8] of step 14.
     A batch with shadow cameras also returns its shadow maps (step 15) as "shadow_map".
+    `flops`: also the number of fp32 operations of steps 9-13 and 16 (the oracle's own per-block
+    tallies: per visible pixel what depends on the pixel, once per image what depends on the image
+    only), as "flops".
     """
     L = lib()
     pin = _Pinned(batch)
@@ -199,10 +202,11 @@ def render(batch, threads: int | None = None, gbuffer: bool = False, debug: bool
     c0, c1 = cams if cams is not None else (0, batch.n_cams)
     chunks = [(a + c0, b + c0) for a, b in _chunks(c1 - c0, threads)]
     counters = np.zeros((len(chunks), 4), np.int64)
+    nflops = np.zeros((len(chunks), 1), np.int64)
 
     def run(i):
-        o = _Outputs(*[_p(out.get(n)) for n, _ in _Outputs._fields_[:-3]], _p(counters[i]), _p(out.get("tracker")),
-                     stride)
+        o = _Outputs(*[_p(out.get(n)) for n, _ in _Outputs._fields_[:-4]], _p(counters[i]), _p(out.get("tracker")),
+                     stride, _p(nflops[i]) if flops else None)
         rc = L.orc_render(C.byref(pin.meshes), C.byref(pin.batch), chunks[i][0], chunks[i][1], C.byref(o))
         if rc != 0:
             raise MemoryError("oracle: allocation failed")
@@ -214,6 +218,8 @@ def render(batch, threads: int | None = None, gbuffer: bool = False, debug: bool
         with ThreadPoolExecutor(threads) as ex:
             list(ex.map(run, range(len(chunks))))
     out["counters"] = counters.sum(0)
+    if flops:
+        out["flops"] = int(nflops.sum())
     if maps is not None:
         out["shadow_map"] = maps
     return out

@@ -320,6 +320,11 @@ static uint32_t pcg_hash(uint32_t v) {
   return (word >> 22u) ^ word;
 }
 
+/* fp32 operations of one call that depend on the pixel: 3 white-balance products, the mean (3),
+   the cross product (6), the rotation (15), the luma (5), the grain value (2) and 10 per channel
+   (30); the per-sample factors 1 +- t, 1 + u, cos, sin and 1 - cos (6) are counted once per image */
+#define ORC_GRADE_OPS 64
+#define ORC_GRADE_IMAGE_OPS 6
 static void grade(const float* g, int32_t cam_local, int64_t pixel, float c[3]) {
   float r = c[0] * (1.0f + g[4]), gr = c[1] * (1.0f + g[5]), bl = c[2] * (1.0f - g[4]);
   const float ch = cosf(g[0]), sh = sinf(g[0]);
@@ -363,8 +368,13 @@ static float spot_f32(float x, float cos_o, float cos_i) {
   return t * t * (3.0f - 2.0f * t);
 }
 
+/* ops: the fp32 operations of the call that depend on the pixel are added (each +, -, *, /, sqrt,
+   powf, negation, comparison and clamp counts once); the light's move to view space (18 per light),
+   the spot axis's (15) and its cone width cos_i - cos_o (1), and 2^EV (1) depend on the image only
+   and are counted once per image by the caller (orc_shade_image_ops). */
 static void shade_f32(const orc_batch* b, int32_t s, const float* V, int ortho, const float P[3],
-                      const float n[3], int32_t mat, const float vis[ORC_MAX_LIGHTS], float rgb[3]) {
+                      const float n[3], int32_t mat, const float vis[ORC_MAX_LIGHTS], float rgb[3], int64_t* ops) {
+  int64_t k_ops = 0;
   const float* m = b->material + ((int64_t)s * ORC_MAX_MATERIALS + mat) * 5;
   const float* amb = b->ambient + (int64_t)s * 3;
   const float e = b->emission ? b->emission[(int64_t)s * ORC_MAX_MATERIALS + mat] : 0.0f;
@@ -379,6 +389,7 @@ static void shade_f32(const orc_batch* b, int32_t s, const float* V, int ortho, 
   } else {
     float lp = sqrtf((P[0] * P[0] + P[1] * P[1]) + P[2] * P[2]);
     for (int k = 0; k < 3; k++) Vv[k] = -P[k] / lp;
+    k_ops += 6 + 6;
   }
   for (int l = 0; l < count; l++) {
     const float* L4 = b->light + ((int64_t)s * ORC_MAX_LIGHTS + l) * 4;
@@ -393,12 +404,16 @@ static void shade_f32(const orc_batch* b, int32_t s, const float* V, int ortho, 
       float dl = sqrtf(d2);
       for (int i = 0; i < 3; i++) L[i] = Lv[i] / dl;
       E = L4[3] / d2;
+      k_ops += 3 + 5 + 1 + 3 + 1; /* L - P, d^2, d, the unit vector, the falloff */
       if (type == 2) { /* the cone about the spot axis, taken to view space like a direction */
         const float* sp = b->light_spot + ((int64_t)s * ORC_MAX_LIGHTS + l) * 5;
         float av[3];
         for (int i = 0; i < 3; i++) av[i] = (V[i * 4 + 0] * sp[0] + V[i * 4 + 1] * sp[1]) + V[i * 4 + 2] * sp[2];
         float x = -((L[0] * av[0] + L[1] * av[1]) + L[2] * av[2]);
         E = E * spot_f32(x, sp[3], sp[4]);
+        /* x (6), the cone test (1), then (x - cos_o) / width with its clamp (4) and the smoothstep
+           (4) when the cone is not null, and the product (1) */
+        k_ops += 6 + 1 + (sp[4] > sp[3] ? 8 : 0) + 1;
       }
     } else {
       for (int i = 0; i < 3; i++) L[i] = -((V[i * 4 + 0] * L4[0] + V[i * 4 + 1] * L4[1]) + V[i * 4 + 2] * L4[2]);
@@ -408,21 +423,35 @@ static void shade_f32(const orc_batch* b, int32_t s, const float* V, int ortho, 
     float ndl = (n[0] * L[0] + n[1] * L[1]) + n[2] * L[2];
     if (ndl < 0.0f) ndl = 0.0f;
     float spec = 0.0f;
+    k_ops += 1 + 6 + 1; /* the shadow factor, n . L with its clamp, the test below */
     if (ndl > 0.0f) {
       float Hv[3] = {L[0] + Vv[0], L[1] + Vv[1], L[2] + Vv[2]};
       float h2 = (Hv[0] * Hv[0] + Hv[1] * Hv[1]) + Hv[2] * Hv[2];
+      k_ops += 3 + 5 + 1; /* L + V, its squared length, the test below */
       if (h2 > 0.0f) {
         float hl = sqrtf(h2);
         float H[3] = {Hv[0] / hl, Hv[1] / hl, Hv[2] / hl};
         float ndh = (n[0] * H[0] + n[1] * H[1]) + n[2] * H[2];
         if (ndh < 0.0f) ndh = 0.0f;
         spec = m[3] * powf(ndh, m[4]);
+        k_ops += 1 + 3 + 5 + 1 + 2; /* |H|, H, n . H with its clamp, the lobe */
       }
     }
     for (int k = 0; k < 3; k++) c[k] = c[k] + E * (m[k] * ndl + spec);
+    k_ops += 12;
   }
   float scale = exp2f(b->exposure_ev[s]);
   for (int k = 0; k < 3; k++) rgb[k] = scale * ((amb[k] * m[k] + e * m[k]) + c[k]);
+  k_ops += 15;
+  *ops += k_ops;
+}
+
+/* The fp32 operations of steps 10 and 13 that depend only on the image of sample s (counted once
+   per image): each light moved to view space (18), each spot axis (15) and cone width (1), 2^EV (1),
+   and the grading factors when the batch is graded. */
+static int64_t orc_shade_image_ops(const orc_batch* b, int32_t s) {
+  int32_t count = light_count(b, s), type = b->light_meta[s * 2 + 1];
+  return (int64_t)count * (18 + (type == 2 ? 16 : 0)) + 1 + (b->grading ? ORC_GRADE_IMAGE_OPS : 0);
 }
 
 /* ------------------------------------------------------------------ */
@@ -458,30 +487,38 @@ static void camera_to_shadow(const float* S, const float* V, float M[12]) {
 
 /* the number of shadowed taps (0..9) at camera-space point P on one face, or -1 when the face's
    map does not contain P's projection (step 16) */
-static int shadow_taps(const float M[12], const float* si, const float* map, int32_t R, const float P[3]) {
+static int shadow_taps(const float M[12], const float* si, const float* map, int32_t R, const float P[3],
+                       int64_t* ops) {
   float q[3];
   for (int i = 0; i < 3; i++) q[i] = ((M[i * 4 + 0] * P[0] + M[i * 4 + 1] * P[1]) + M[i * 4 + 2] * P[2]) + M[i * 4 + 3];
   float z = -q[2];
+  *ops += 18 + 1 + 1; /* the projection, z, the near test */
   if (!(z > si[4])) return -1;
   float u, v;
   if (si[6] != 0.0f) { /* orthographic */
     u = si[2] + si[0] * q[0];
     v = si[3] - si[1] * q[1];
+    *ops += 4;
   } else {
     float iw = 1.0f / z;
     u = si[2] + si[0] * (q[0] * iw);
     v = si[3] - si[1] * (q[1] * iw);
+    *ops += 7;
   }
+  *ops += 4; /* the guard-band tests */
   if (!(fabsf(u) < GUARD_PX) || !(fabsf(v) < GUARD_PX)) return -1;
   int32_t i0 = (int32_t)floorf(u), j0 = (int32_t)floorf(v);
+  *ops += 4; /* floor and conversion of u and v */
   if (i0 < 0 || j0 < 0 || i0 >= R || j0 >= R) return -1;
   float zb = z - si[5];
+  *ops += 1;
   int k = 0;
   for (int bb = -1; bb <= 1; bb++)
     for (int a = -1; a <= 1; a++) {
       int32_t i = i0 + a, j = j0 + bb;
       if (i < 0 || j < 0 || i >= R || j >= R) continue;
       float d = map[(int64_t)j * R + i];
+      *ops += d > 0.0f ? 2 : 1; /* the occupancy test, then the depth test */
       if (d > 0.0f && zb > d) k++;
     }
   return k;
@@ -637,7 +674,12 @@ static int render_image(const orc_meshes* me, const orc_batch* b, int32_t c, con
       if (cast[l * F + f]) camera_to_shadow(b->shadow_view + shadow_index(b, s, l, f) * 12, V, Msh[l * F + f]);
     }
 
-  /* steps 9-11 per pixel */
+  /* steps 9-11 per pixel.  ops counts the fp32 operations of steps 9-13 and 16 (out->flops): per
+     visible pixel those that depend on the pixel, as the comments beside the code tally them; per
+     background pixel only the grading and quantisation of a graded background colour (an ungraded
+     one is the same for the whole image); once per image the set-up of the lights, the exposure,
+     the grading factors and the reciprocal focal lengths (2). */
+  int64_t ops = 2 + orc_shade_image_ops(b, s);
   const float* bg = b->background + (int64_t)s * 3;
   for (int32_t y = 0; y < H; y++) {
     for (int32_t x = 0; x < W; x++) {
@@ -652,6 +694,7 @@ static int render_image(const orc_meshes* me, const orc_batch* b, int32_t c, con
           if (b->grading) grade(b->grading + (int64_t)s * 8, c - b->cam_offset[s], i, gc);
           for (int k = 0; k < 3; k++) out->rgb[o * 3 + k] = quantise(gc[k]);
         }
+        if (b->grading) ops += ORC_GRADE_OPS + 3 * 6; /* the grading and the three quantisations */
         if (out->rgb_linear)
           for (int k = 0; k < 3; k++) out->rgb_linear[o * 3 + k] = bg[k];
         if (out->depth) out->depth[o] = 0.0f;
@@ -670,27 +713,35 @@ static int render_image(const orc_meshes* me, const orc_batch* b, int32_t c, con
       int64_t w1 = edge(p->X[2], p->Y[2], p->X[0], p->Y[0], cxp, cyp);
       int64_t w2 = edge(p->X[0], p->Y[0], p->X[1], p->Y[1], cxp, cyp);
       float a0 = (float)w0, a1 = (float)w1, a2 = (float)w2;
+      ops += 3;
       if (!ortho) {
         a0 = a0 * p->iw[0];
         a1 = a1 * p->iw[1];
         a2 = a2 * p->iw[2];
+        ops += 3;
       }
       float n[3];
       for (int k = 0; k < 3; k++) n[k] = (a0 * p->n[0][k] + a1 * p->n[1][k]) + a2 * p->n[2][k];
       float len = sqrtf((n[0] * n[0] + n[1] * n[1]) + n[2] * n[2]);
-      if (len > 0.0f)
+      ops += 15 + 6 + 1; /* the interpolated normal, its length, the test below */
+      if (len > 0.0f) {
         for (int k = 0; k < 3; k++) n[k] = n[k] / len;
+        ops += 3;
+      }
       float ux = ((float)x + 0.5f - cx) * inv_fx;
       float uy = -(((float)y + 0.5f - cy) * inv_fy);
       float P[3];
+      ops += 4 + 5;
       if (ortho) {
         P[0] = ux;
         P[1] = uy;
         P[2] = -p->depth;
+        ops += 1;
       } else {
         P[0] = p->depth * ux;
         P[1] = p->depth * uy;
         P[2] = -p->depth;
+        ops += 3;
       }
       float vis[ORC_MAX_LIGHTS] = {1.0f, 1.0f, 1.0f, 1.0f};
       int32_t word = p->mat;
@@ -700,19 +751,23 @@ static int render_image(const orc_meshes* me, const orc_batch* b, int32_t c, con
           if (!cast[l * F + f]) continue;
           const int64_t si = shadow_index(b, s, l, f);
           k = shadow_taps(Msh[l * F + f], b->shadow_intr + si * 7,
-                          b->shadow_map + si * b->shadow_res * b->shadow_res, b->shadow_res, P);
+                          b->shadow_map + si * b->shadow_res * b->shadow_res, b->shadow_res, P, &ops);
         }
         if (k <= 0) continue;
         vis[l] = (float)(9 - k) / 9.0f;
+        ops += 2;
         word |= k << (8 + 4 * l);
       }
       float rgb[3];
-      shade_f32(b, s, V, ortho, P, n, p->mat, vis, rgb);
+      shade_f32(b, s, V, ortho, P, n, p->mat, vis, rgb, &ops);
       if (out->rgb) {
         float gc[3] = {rgb[0], rgb[1], rgb[2]};
         if (b->grading) grade(b->grading + (int64_t)s * 8, c - b->cam_offset[s], i, gc);
         for (int k = 0; k < 3; k++) out->rgb[o * 3 + k] = quantise(gc[k]);
       }
+      /* the grading, three quantisations (clamp 2, scale, offset, floor, conversion) and three
+         binary16 conversions of the normal */
+      ops += (b->grading ? ORC_GRADE_OPS : 0) + 3 * 6 + 3;
       if (out->rgb_linear)
         for (int k = 0; k < 3; k++) out->rgb_linear[o * 3 + k] = rgb[k];
       if (out->depth) out->depth[o] = p->depth;
@@ -728,6 +783,7 @@ static int render_image(const orc_meshes* me, const orc_batch* b, int32_t c, con
   }
   free(Msh);
   free(cast);
+  if (out->flops) out->flops[0] += ops;
   return 0;
 }
 

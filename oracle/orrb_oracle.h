@@ -92,6 +92,7 @@ typedef struct {                /* every pointer may be NULL */
   int64_t* counters;            /* [4] fragments, triangles culled, clipped, dropped (accumulated) */
   int32_t* tracker;             /* [C][tracker_stride][8] per (camera, instance of its sample), step 14 */
   int32_t tracker_stride;
+  int64_t* flops;               /* [1] fp32 operations of steps 9-13 and 16 (accumulated; see render_image) */
 } orc_outputs;
 
 /* Render images [cam_begin, cam_end).  Returns 0, or -1 on allocation failure. */
