@@ -8,7 +8,8 @@
 // parameters, so the gradient is exact, not an approximation.
 //
 // Pass 1 (grid = images x blocks_per_img): each CTA owns a fixed pixel range
-// of one image.  Light and exposure terms accumulate per thread; material
+// of one image, which its threads stream through shared memory (cp.async,
+// three chunks of 256 pixels ahead, each thread its own pixels' words).  Light and exposure terms accumulate per thread; material
 // terms accumulate per warp with a segmented reduction: for every material
 // present in the warp's 32 pixels the lanes with that material are summed by
 // a fixed shuffle tree.  The CTA then combines its warps in warp order,
@@ -32,6 +33,20 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kBwdThreads = 256;
 constexpr int kBwdWarps = kBwdThreads / 32;
 
+// Pixel data are staged through shared memory kStages chunks ahead: each thread copies the ten
+// words of the pixels it will shade (seven G-buffer planes, three dL/drgb) with cp.async, so the
+// loads of later chunks are in flight while it shades the current one.
+constexpr int kStages = 3;
+constexpr int kWords = 10;
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int kN>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(kN) : "memory"); }
+
 struct BwdShared {
   float V[12];
   float lv[kMaxLights][4];
@@ -43,6 +58,7 @@ struct BwdShared {
   int n_lights, light_type, ortho, s;
   float wmat[kBwdWarps][kMaxMaterials][5];      // per-warp material sums (albedo, specular, emission)
   float wred[kBwdWarps][kMaxLights * 4 + 1];    // per-warp light + exposure sums
+  float stage[kStages][kWords][kBwdThreads];    // each thread's own staged pixel words
 };
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -107,20 +123,34 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
     dlv[l][0] = dlv[l][1] = dlv[l][2] = 0.0f;
     dI[l] = 0.0f;
   }
-  for (long long r0 = i0; r0 < i1; r0 += kBwdThreads) {
+  // the ten words of pixel r0 + tid into stage `st` (nothing past the range: its copies are skipped)
+  auto stage_pixel = [&](long long r0, int st) {
+    const long long i = r0 + tid;
+    if (i < i1) {
+      const long long o = base + i;
+      for (int k = 0; k < 7; k++) cp_async4(&sh.stage[st][k][tid], bp.gbuffer + k * N + o);
+      for (int k = 0; k < 3; k++) cp_async4(&sh.stage[st][7 + k][tid], bp.d_rgb + 3 * o + k);
+    }
+    cp_async_commit();  // (an empty group where the range has ended keeps the group count aligned)
+  };
+  for (int k = 0; k < kStages - 1; k++) stage_pixel(i0 + (long long)k * kBwdThreads, k);
+  int st = 0;
+  for (long long r0 = i0; r0 < i1; r0 += kBwdThreads, st = st == kStages - 1 ? 0 : st + 1) {
+    stage_pixel(r0 + (long long)(kStages - 1) * kBwdThreads, st == 0 ? kStages - 1 : st - 1);
+    cp_async_wait<kStages - 1>();  // this thread's copies of chunk r0 have landed
     const long long i = r0 + tid;
     int mat = -1, word = -1;
     float dm[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
     if (i < i1) {
-      const long long o = base + i;
+      const float* w = &sh.stage[st][0][tid];
       // the material word: slot in bits 0-7, light l's shadowed taps in bits 8 + 4l .. 11 + 4l
-      word = __float_as_int(bp.gbuffer[6 * N + o]);
+      word = __float_as_int(w[6 * kBwdThreads]);
       mat = word < 0 ? -1 : (word & 0xff);
       if (mat >= kMaxMaterials) mat = -1;
       if (mat >= 0) {
-        const float P[3] = {bp.gbuffer[o], bp.gbuffer[N + o], bp.gbuffer[2 * N + o]};
-        const float n[3] = {bp.gbuffer[3 * N + o], bp.gbuffer[4 * N + o], bp.gbuffer[5 * N + o]};
-        const float g[3] = {bp.d_rgb[3 * o], bp.d_rgb[3 * o + 1], bp.d_rgb[3 * o + 2]};
+        const float P[3] = {w[0], w[kBwdThreads], w[2 * kBwdThreads]};
+        const float n[3] = {w[3 * kBwdThreads], w[4 * kBwdThreads], w[5 * kBwdThreads]};
+        const float g[3] = {w[7 * kBwdThreads], w[8 * kBwdThreads], w[9 * kBwdThreads]};
         const float* m = sh.mat[mat];
         float Vv[3];
         if (sh.ortho) {
