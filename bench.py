@@ -382,6 +382,9 @@ def run_ours(args, world, rank, local):
     e2e_value = world * N_SAMPLES / (e2e_ms / 1e3)
     ok = bool((CapturePipeline.result(last)["seg"].numpy() == out["seg"].cpu().numpy()).all())
 
+    # -- the differentiation pattern on the same batch: forward with G-buffer + shading adjoint ---
+    dfms, dbms, dbytes = time_diff(r, db, batch, reps=10, warmup=3)
+
     if rank != 0:
         return
     # -- roofline -----------------------------------------------------------------
@@ -447,6 +450,12 @@ def run_ours(args, world, rank, local):
                            "channels on a copy stream; D2H is capped near 57 GB/s on this host link"},
             "gpu_launches": args.steps,
             "roofline": roof,
+            "diff": {"forward_gbuffer_ms": dfms, "adjoint_ms": dbms,
+                     "adjoint_achieved_gbs": dbytes / (dbms / 1e3) / 1e9,
+                     "adjoint_frac_of_hbm": dbytes / (dbms / 1e3) / 1e9 / hbm,
+                     "adjoint_alg_bytes": dbytes,
+                     "how": "L2 loss against a target rendered with perturbed parameters; adjoint = "
+                            "backward_partial_kernel + backward_reduce_kernel; 40 B per pixel read"},
             "clocks": clk_sum,
             "device_status": status}
     if not args.no_cpu_baseline:
@@ -511,33 +520,24 @@ def run_uneven(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
-def run_diff(args, world, rank, local):
-    """Forward with G-buffer + shading adjoint for 256 hand samples (L2 loss against perturbed-parameter targets)."""
+def time_diff(r, db, batch, reps: int, warmup: int):
+    """Forward with G-buffer and shading adjoint of `db` (L2 loss against a target rendered with
+    perturbed parameters): (forward ms, adjoint ms, algorithmic adjoint bytes), CUDA events."""
     import torch
     from paper_1906_11633_b300 import scenegen as sg
-    from paper_1906_11633_b300.render import Renderer
-    torch.cuda.set_device(local)
-    batch = sg.hand_batch(SEED, shard_samples(rank, world, N_SAMPLES), res=RES, n_cams=N_CAMS)
-    r = Renderer(batch.meshes, device=local)
-    db = r.upload(batch)
     mat_t, light_t, ev_t = sg.perturb_params(batch, SEED)
-    dbt = db.with_params(material=torch.from_numpy(mat_t).cuda(), light=torch.from_numpy(light_t).cuda(),
-                         exposure_ev=torch.from_numpy(ev_t).cuda())
+    dbt = db.with_params(material=torch.from_numpy(mat_t).to(r.device), light=torch.from_numpy(light_t).to(r.device),
+                         exposure_ev=torch.from_numpy(ev_t).to(r.device))
     target = r.render(dbt, rgb_linear=True)["rgb_linear"].clone()
     out = r.render(db, rgb_linear=True, gbuffer=True)
-    stream = torch.cuda.current_stream()
-
-    def step():
+    stream = torch.cuda.current_stream(r.device)
+    d = 2.0 * (out["rgb_linear"] - target)
+    for _ in range(warmup):
         r.render(db, out=out, rgb_linear=True, gbuffer=True)
-        d = 2.0 * (out["rgb_linear"] - target)
-        return r.shade_backward(db, out["gbuffer"], d)
-
-    for _ in range(args.warmup):
-        step()
+        r.shade_backward(db, out["gbuffer"], d)
     torch.cuda.synchronize()
     fw, bw = [], []
-    d = 2.0 * (out["rgb_linear"] - target)
-    for _ in range(max(5, args.steps // 10)):
+    for _ in range(reps):
         e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         e[0].record(stream)
         r.render(db, out=out, rgb_linear=True, gbuffer=True)
@@ -549,11 +549,24 @@ def run_diff(args, world, rank, local):
     torch.cuda.synchronize()
     fms = float(np.mean([a.elapsed_time(b) for a, b in fw]))
     bms = float(np.mean([a.elapsed_time(b) for a, b in bw]))
+    # 40 B per pixel read (G-buffer 28 B + dL/drgb 12 B), the gradient rows written
+    bw_bytes = batch.total_pixels * (7 * 4 + 12) + batch.n_samples * (128 + 16 + 1) * 4
+    return fms, bms, bw_bytes
+
+
+def run_diff(args, world, rank, local):
+    """Forward with G-buffer + shading adjoint for 256 hand samples (L2 loss against perturbed-parameter targets)."""
+    import torch
+    from paper_1906_11633_b300 import scenegen as sg
+    from paper_1906_11633_b300.render import Renderer
+    torch.cuda.set_device(local)
+    batch = sg.hand_batch(SEED, shard_samples(rank, world, N_SAMPLES), res=RES, n_cams=N_CAMS)
+    r = Renderer(batch.meshes, device=local)
+    db = r.upload(batch)
+    fms, bms, bw_bytes = time_diff(r, db, batch, max(5, args.steps // 10), args.warmup)
     if rank != 0:
         return
     peaks, _ = load_peaks()
-    N = batch.total_pixels
-    bw_bytes = N * (7 * 4 + 12) + N_SAMPLES * (128 + 16 + 1) * 4
     line = {"workload": "diff", "metric": "samples/s, forward with G-buffer + shading adjoint",
             "value": world * N_SAMPLES / ((fms + bms) / 1e3), "unit": UNIT, "n_gpus": world,
             "forward_ms": fms, "backward_ms": bms, "backward_samples_per_s": N_SAMPLES / (bms / 1e3),

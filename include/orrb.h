@@ -176,7 +176,12 @@ typedef struct {
                                     LightRandomizer's spotlight angles, Sec. 4.3.1): world axis xyz
                                     (unit length, the direction the spot points), cos of the outer
                                     and of the inner half-angle.  A cone with cos_inner <= cos_outer
-                                    lights nothing.  Read only for samples of light type 2. */
+                                    lights nothing.  The kernels fold 1 / (cos_inner - cos_outer) into
+                                    the axis, which scales the rounding of the cone's cosine by that
+                                    factor: the rgb_linear contract (1e-4 against the oracle) is held
+                                    for cos_inner - cos_outer >= 0.01 (tested at 0.01); a narrower
+                                    ramp renders, but its pixels on the ramp may differ by more.
+                                    Read only for samples of light type 2. */
   const float* emission;         /* [n_samples][32] or NULL (none): material emission e, the emitted
                                     colour being e * albedo (a MuJoCo material's emission, Sec. 4.2) */
   const float* shadow_view;      /* [n_samples][4][F][3][4] or NULL: per light F perspective shadow
