@@ -234,6 +234,9 @@ typedef struct {
                            when shape.shadow_res > 0 and the batch has shadow cameras.  Written for
                            the faces that cast, first (its own launch), then read by the shading.
                            Maps of faces that cast none are left as they were. */
+  float* rgb_graded;    /* device, [N][3] or NULL: the colour after the colour grading (batch.grading)
+                           and before clamping and quantisation, the input of a loss on the graded
+                           image (see orrb_param_grads.d_grading); for an ungraded batch, rgb_linear */
 } orrb_outputs;
 
 #define ORRB_MODE_FUSED 0  /* one persistent launch over all images (work queue) */
@@ -304,6 +307,14 @@ typedef struct {
   float* d_light;      /* device, [n_samples][4][4]: d world position/direction xyz, d intensity */
   float* d_exposure;   /* device, [n_samples] */
   float* d_emission;   /* device, [n_samples][32], or NULL: d emission (overwritten) */
+  float* d_grading;    /* device, [n_samples][8], or NULL.  When given (the batch must be graded),
+                          the loss is on the graded colour: the d_rgb_linear argument of
+                          orrb_shade_backward holds dL/d rgb_graded instead, the adjoint goes back
+                          through the grading (Sec. 4.3.1 post-processing randomizer) to every
+                          parameter, and d_grading receives d hue, saturation, contrast,
+                          brightness, temperature, tint, grain amplitude, and 0 for the seed.  The
+                          background's colour is graded too: its pixels count for the grading
+                          parameters (the background colour itself is not differentiated). */
 } orrb_param_grads;
 
 /* Workspace bytes of orrb_shade_backward for `shape` (partial sums). */

@@ -78,6 +78,10 @@ def lib():
             L.orc_shade_f64.restype = None
             L.orc_shade_backward_f64.argtypes = [C.POINTER(_Batch), C.c_int32, C.c_int32] + [C.c_void_p] * 13
             L.orc_shade_backward_f64.restype = None
+            L.orc_grade_f64.argtypes = [C.POINTER(_Batch), C.c_int32, C.c_int32] + [C.c_void_p] * 3
+            L.orc_grade_f64.restype = None
+            L.orc_grade_backward_f64.argtypes = [C.POINTER(_Batch), C.c_int32, C.c_int32] + [C.c_void_p] * 5
+            L.orc_grade_backward_f64.restype = None
             L.orc_render_shadow_maps.argtypes = [C.POINTER(_Meshes), C.POINTER(_Batch), C.c_int32, C.c_int32,
                                                  C.c_void_p]
             L.orc_render_shadow_maps.restype = C.c_int
@@ -283,3 +287,32 @@ def shade_backward_f64(batch, gb_pos, gb_nrm, gb_mat, d_rgb, material=None, ligh
     lib().orc_shade_backward_f64(C.byref(pin.batch), 0, batch.n_cams, _p(gp), _p(gn), _p(gm), _p(m), _p(l), _p(e),
                                  _p(a), _p(em), _p(g), _p(dm), _p(dl), _p(de), _p(dem))
     return (dm, dl, de, dem) if return_emission else (dm, dl, de)
+
+
+def grade_f64(batch, rgb_in, grading=None):
+    """Step 13 in fp64: the graded colour [N, 3] of the linear colour `rgb_in` [N, 3] (grading
+    parameters [S, 8], default the batch's)."""
+    pin = _Pinned(batch)
+    g = _c(batch.grading if grading is None else grading, np.float64)
+    x = _c(rgb_in, np.float64)
+    out = np.zeros((batch.total_pixels, 3), np.float64)
+    lib().orc_grade_f64(C.byref(pin.batch), 0, batch.n_cams, _p(g), _p(x), _p(out))
+    return out
+
+
+def graded_shade_f64(batch, gb_pos, gb_nrm, gb_mat, grading=None, **params):
+    """The graded colour of a fixed G-buffer in fp64 (shading of step 10, then step 13)."""
+    return grade_f64(batch, shade_f64(batch, gb_pos, gb_nrm, gb_mat, **params), grading)
+
+
+def graded_backward_f64(batch, gb_pos, gb_nrm, gb_mat, d_graded, grading=None, **params):
+    """fp64 adjoint of a loss on the graded colour: (d_material, d_light, d_ev, d_grading [S, 8])."""
+    pin = _Pinned(batch)
+    g = _c(batch.grading if grading is None else grading, np.float64)
+    lin = _c(shade_f64(batch, gb_pos, gb_nrm, gb_mat, **params), np.float64)
+    dO = _c(d_graded, np.float64)
+    d_lin = np.zeros((batch.total_pixels, 3), np.float64)
+    dg = np.zeros((batch.n_samples, 8), np.float64)
+    lib().orc_grade_backward_f64(C.byref(pin.batch), 0, batch.n_cams, _p(g), _p(lin), _p(dO), _p(d_lin), _p(dg))
+    dm, dl, de = shade_backward_f64(batch, gb_pos, gb_nrm, gb_mat, d_lin, **params)
+    return dm, dl, de, dg

@@ -1051,3 +1051,108 @@ void orc_shade_backward_f64(const orc_batch* b, int32_t cam_begin, int32_t cam_e
     }
   }
 }
+
+/* ------------------------------------------------------------------ */
+/* step 13 in fp64 and its adjoint (a loss on the graded colour)       */
+/* ------------------------------------------------------------------ */
+/* The graded colour of every pixel of images [cam_begin, cam_end) from its linear colour rgb_in
+   (the shading, or the background), the steps of grade() in fp64 and the same order, with the
+   grading parameters taken from `grading` ([S][8], fp64 so that differences can perturb them). */
+void orc_grade_f64(const orc_batch* b, int32_t cam_begin, int32_t cam_end, const double* grading,
+                   const double* rgb_in, double* rgb_out) {
+  const double k = 0.57735026918962576;
+  const double Yw[3] = {0.2126, 0.7152, 0.0722};
+  for (int32_t c = cam_begin; c < cam_end; c++) {
+    const int32_t s = b->cam_sample[c];
+    const double* g = grading + (int64_t)s * 8;
+    const int64_t npx = (int64_t)b->cam_wh[c * 2] * b->cam_wh[c * 2 + 1], base = b->img_offset[c];
+    const uint32_t h1 = pcg_hash((uint32_t)b->grading[(int64_t)s * 8 + 7] + 0x9E3779B9u * (uint32_t)(c - b->cam_offset[s] + 1));
+    const double ch = cos(g[0]), sh = sin(g[0]);
+    for (int64_t i = 0; i < npx; i++) {
+      const double* in = rgb_in + (base + i) * 3;
+      double* out = rgb_out + (base + i) * 3;
+      const double r = in[0] * (1.0 + g[4]), gr = in[1] * (1.0 + g[5]), bl = in[2] * (1.0 - g[4]);
+      const double mean = (r + gr + bl) / 3.0;
+      const double x[3] = {(bl - gr) * k, (r - bl) * k, (gr - r) * k};
+      const double c1[3] = {r, gr, bl};
+      double h[3];
+      for (int j = 0; j < 3; j++) h[j] = c1[j] * ch + x[j] * sh + mean * (1.0 - ch);
+      const double Y = Yw[0] * h[0] + Yw[1] * h[1] + Yw[2] * h[2];
+      const double n = (double)pcg_hash(h1 ^ (uint32_t)i) * 2.3283064365386963e-10;
+      for (int j = 0; j < 3; j++) {
+        double v = Y + g[1] * (h[j] - Y);
+        v = (v - 0.5) * g[2] + 0.5;
+        v = v + g[3];
+        out[j] = v + g[6] * (n - 0.5);
+      }
+    }
+  }
+}
+
+/* The adjoint of orc_grade_f64: given d_out = dL/d graded colour, the gradient dL/d rgb_in
+   (written) and dL/d grading parameters (accumulated into d_grading [S][8]: hue, saturation,
+   contrast, brightness, temperature, tint, grain amplitude; the seed gets none), each step of the
+   grading taken back in reverse order. */
+void orc_grade_backward_f64(const orc_batch* b, int32_t cam_begin, int32_t cam_end, const double* grading,
+                            const double* rgb_in, const double* d_out, double* d_in, double* d_grading) {
+  const double k = 0.57735026918962576;
+  const double Yw[3] = {0.2126, 0.7152, 0.0722};
+  for (int32_t c = cam_begin; c < cam_end; c++) {
+    const int32_t s = b->cam_sample[c];
+    const double* g = grading + (int64_t)s * 8;
+    double* dg = d_grading + (int64_t)s * 8;
+    const int64_t npx = (int64_t)b->cam_wh[c * 2] * b->cam_wh[c * 2 + 1], base = b->img_offset[c];
+    const uint32_t h1 = pcg_hash((uint32_t)b->grading[(int64_t)s * 8 + 7] + 0x9E3779B9u * (uint32_t)(c - b->cam_offset[s] + 1));
+    const double ch = cos(g[0]), sh = sin(g[0]);
+    for (int64_t i = 0; i < npx; i++) {
+      const double* in = rgb_in + (base + i) * 3;
+      const double* dO = d_out + (base + i) * 3;
+      /* the forward values the adjoint needs */
+      const double r = in[0] * (1.0 + g[4]), gr = in[1] * (1.0 + g[5]), bl = in[2] * (1.0 - g[4]);
+      const double mean = (r + gr + bl) / 3.0;
+      const double x[3] = {(bl - gr) * k, (r - bl) * k, (gr - r) * k};
+      const double c1[3] = {r, gr, bl};
+      double h[3], v1[3];
+      for (int j = 0; j < 3; j++) h[j] = c1[j] * ch + x[j] * sh + mean * (1.0 - ch);
+      const double Y = Yw[0] * h[0] + Yw[1] * h[1] + Yw[2] * h[2];
+      for (int j = 0; j < 3; j++) v1[j] = Y + g[1] * (h[j] - Y);
+      const double n = (double)pcg_hash(h1 ^ (uint32_t)i) * 2.3283064365386963e-10;
+      /* grain, brightness, contrast */
+      double dv1[3], dh[3] = {0.0, 0.0, 0.0}, dY = 0.0;
+      for (int j = 0; j < 3; j++) {
+        dg[6] += dO[j] * (n - 0.5);
+        dg[3] += dO[j];
+        dg[2] += dO[j] * (v1[j] - 0.5);
+        dv1[j] = dO[j] * g[2];
+      }
+      /* saturation v1 = Y + s (h - Y) */
+      for (int j = 0; j < 3; j++) {
+        dg[1] += dv1[j] * (h[j] - Y);
+        dh[j] += dv1[j] * g[1];
+        dY += dv1[j] * (1.0 - g[1]);
+      }
+      for (int j = 0; j < 3; j++) dh[j] += Yw[j] * dY;
+      /* rotation h = c1 cos + x sin + mean (1 - cos) */
+      double dc1[3], dx[3], dmean = 0.0, dch = 0.0, dsh = 0.0;
+      for (int j = 0; j < 3; j++) {
+        dch += dh[j] * (c1[j] - mean);
+        dsh += dh[j] * x[j];
+        dc1[j] = dh[j] * ch;
+        dx[j] = dh[j] * sh;
+        dmean += dh[j] * (1.0 - ch);
+      }
+      dg[0] += -sh * dch + ch * dsh;
+      /* x = (bl - gr, r - bl, gr - r) k and mean = (r + gr + bl) / 3 */
+      const double dr = dc1[0] + k * (dx[1] - dx[2]) + dmean / 3.0;
+      const double dgr = dc1[1] + k * (dx[2] - dx[0]) + dmean / 3.0;
+      const double dbl = dc1[2] + k * (dx[0] - dx[1]) + dmean / 3.0;
+      /* white balance r = c0 (1 + t), gr = c1 (1 + u), bl = c2 (1 - t) */
+      dg[4] += dr * in[0] - dbl * in[2];
+      dg[5] += dgr * in[1];
+      double* dI = d_in + (base + i) * 3;
+      dI[0] = dr * (1.0 + g[4]);
+      dI[1] = dgr * (1.0 + g[5]);
+      dI[2] = dbl * (1.0 - g[4]);
+    }
+  }
+}

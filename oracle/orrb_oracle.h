@@ -136,6 +136,18 @@ void orc_shade_backward_f64(const orc_batch* b, int32_t cam_begin, int32_t cam_e
                             const double* ambient, const double* emission, const double* d_rgb,
                             double* d_material, double* d_light, double* d_ev, double* d_emission);
 
+/* Step 13 (colour grading) in fp64 on a linear colour rgb_in [N][3] (shading or background),
+ * with the grading parameters `grading` [S][8]: writes the graded colour rgb_out [N][3] (the
+ * grain's seed is taken from the batch). */
+void orc_grade_f64(const orc_batch* b, int32_t cam_begin, int32_t cam_end, const double* grading,
+                   const double* rgb_in, double* rgb_out);
+
+/* Adjoint of orc_grade_f64: d_out = dL/d graded colour [N][3]; writes d_in = dL/d rgb_in [N][3]
+ * and accumulates (+=) d_grading [S][8] (hue, saturation, contrast, brightness, temperature,
+ * tint, grain amplitude; 0 for the seed). */
+void orc_grade_backward_f64(const orc_batch* b, int32_t cam_begin, int32_t cam_end, const double* grading,
+                            const double* rgb_in, const double* d_out, double* d_in, double* d_grading);
+
 #ifdef __cplusplus
 }
 #endif

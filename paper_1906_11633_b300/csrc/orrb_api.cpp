@@ -319,6 +319,7 @@ orrb_status enqueue_render(orrb_ctx* ctx, Params& p, const orrb_batch_shape& s, 
     q.normal = nullptr;
     q.seg = nullptr;
     q.rgb_linear = nullptr;
+    q.rgb_graded = nullptr;
     q.gbuffer = nullptr;
     q.tracker = nullptr;
     q.grading = nullptr;
@@ -513,6 +514,7 @@ orrb_status orrb_render_batch(orrb_ctx* ctx, const orrb_batch_shape* shape, cons
   p.normal = out->normal;
   p.seg = out->seg;
   p.rgb_linear = out->rgb_linear;
+  p.rgb_graded = out->rgb_graded;
   p.gbuffer = out->gbuffer;
   p.tracker = out->tracker;
   p.shadow_map = out->shadow_map;
@@ -582,6 +584,7 @@ orrb_status orrb_render_batch_noalloc(orrb_ctx* ctx, const orrb_batch_shape* sha
   p.normal = out->normal;
   p.seg = out->seg;
   p.rgb_linear = out->rgb_linear;
+  p.rgb_graded = out->rgb_graded;
   p.gbuffer = out->gbuffer;
   p.tracker = out->tracker;
   p.shadow_map = out->shadow_map;
@@ -666,6 +669,9 @@ orrb_status orrb_shade_backward(orrb_ctx* ctx, const orrb_batch_shape* shape, co
   bp.d_light = grads->d_light;
   bp.d_exposure = grads->d_exposure;
   bp.d_emission = grads->d_emission;
+  bp.d_grading = grads->d_grading;
+  if (bp.d_grading && !batch->grading)
+    return fail(ctx, ORRB_ERR_INVALID_ARG, "d_grading (a loss on the graded colour) needs a graded batch");
   bp.partial = reinterpret_cast<float*>(static_cast<char*>(workspace) + 256);
   bp.blocks_per_img = bpi;
   char err[256] = {0};

@@ -58,6 +58,10 @@ struct BwdShared {
   int n_lights, light_type, ortho, s;
   float wmat[kBwdWarps][kMaxMaterials][5];      // per-warp material sums (albedo, specular, emission)
   float wred[kBwdWarps][kMaxLights * 4 + 1];    // per-warp light + exposure sums
+  float wgrade[kBwdWarps][kGradeSums];          // per-warp grading sums (graded loss)
+  float gm[3][4];                               // the image's grading map c' = A c + t
+  float bg[3];
+  unsigned gkey;                                // the image's grain key
   float stage[kStages][kWords][kBwdThreads];    // each thread's own staged pixel words
 };
 
@@ -66,7 +70,11 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-// 4 CTAs (32 warps) per SM: the per-pixel loads need the occupancy more than the adjoint needs registers
+// 4 CTAs (32 warps) per SM: the per-pixel loads need the occupancy more than the adjoint needs registers.
+// kGraded: the loss is on the graded colour c' = A c + t + grain: d_rgb holds dL/dc', the adjoint
+// of the shading takes A^T dL/dc', and the image's sums sum dc' c^T, sum dc' and the grain term
+// are written for the grading parameters' gradients (formed in the reduce kernel).
+template <bool kGraded>
 __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(BackwardParams bp) {
   const Params& p = bp.base;
   __shared__ BwdShared sh;
@@ -101,6 +109,11 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
     }
     sh.scale = exp2f(p.exposure_ev[s]);
     for (int k = 0; k < 3; k++) sh.amb[k] = p.ambient[s * 3 + k];
+    if (kGraded) {
+      grading_map(p.grading + (size_t)s * 8, sh.gm);
+      sh.gkey = grain_key(p.grading + (size_t)s * 8, unsigned(cam - p.cam_offset[s]));
+      for (int k = 0; k < 3; k++) sh.bg[k] = p.background[s * 3 + k];
+    }
   }
   for (int k = tid; k < kBwdWarps * kMaxMaterials * 5; k += kBwdThreads) (&sh.wmat[0][0][0])[k] = 0.0f;
   __syncthreads();
@@ -118,6 +131,8 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
   const float ln2 = 0.69314718055994530942f;
   const float scale = sh.scale;
 
+  float gsum[kGradeSums];  // graded loss: sum dc' c^T (row-major), sum dc', sum (sum dc') grain
+  for (int k = 0; k < kGradeSums; k++) gsum[k] = 0.0f;
   float dlv[kMaxLights][3], dI[kMaxLights], dev = 0.0f;
   for (int l = 0; l < kMaxLights; l++) {
     dlv[l][0] = dlv[l][1] = dlv[l][2] = 0.0f;
@@ -147,10 +162,17 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
       word = __float_as_int(w[6 * kBwdThreads]);
       mat = word < 0 ? -1 : (word & 0xff);
       if (mat >= kMaxMaterials) mat = -1;
+      // dL/d rgb_linear: the input itself, or for a graded loss A^T dL/dc'
+      const float gp[3] = {w[7 * kBwdThreads], w[8 * kBwdThreads], w[9 * kBwdThreads]};
+      float g[3] = {gp[0], gp[1], gp[2]};
+      if (kGraded)
+        for (int k = 0; k < 3; k++) g[k] = sh.gm[0][k] * gp[0] + sh.gm[1][k] * gp[1] + sh.gm[2][k] * gp[2];
+      float c[3];  // the ungraded colour (graded loss only)
+      if (kGraded && mat < 0)
+        for (int k = 0; k < 3; k++) c[k] = sh.bg[k];
       if (mat >= 0) {
         const float P[3] = {w[0], w[kBwdThreads], w[2 * kBwdThreads]};
         const float n[3] = {w[3 * kBwdThreads], w[4 * kBwdThreads], w[5 * kBwdThreads]};
-        const float g[3] = {w[7 * kBwdThreads], w[8 * kBwdThreads], w[9 * kBwdThreads]};
         const float* m = sh.mat[mat];
         float Vv[3];
         if (sh.ortho) {
@@ -243,6 +265,15 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
         const float e = g[0] * sh.amb[0] * m[0] + g[1] * sh.amb[1] * m[1] + g[2] * sh.amb[2] * m[2] +
                         gr * (em + sum_endl) + G * m[3] * sum_epw;
         dev += ln2 * scale * e;
+        if (kGraded)
+          for (int k = 0; k < 3; k++) c[k] = scale * (m[k] * (sh.amb[k] + em + sum_endl) + m[3] * sum_epw);
+      }
+      if (kGraded) {
+        for (int a = 0; a < 3; a++) {
+          for (int b = 0; b < 3; b++) gsum[a * 3 + b] += gp[a] * c[b];
+          gsum[9 + a] += gp[a];
+        }
+        gsum[12] += (gp[0] + gp[1] + gp[2]) * grain_centred(sh.gkey, unsigned(i));
       }
     }
     // segmented warp reduction over the materials present in these 32 pixels
@@ -277,6 +308,11 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
     float v = warp_sum(dev);
     if (lane == 0) sh.wred[warp][kMaxLights * 4] = v;
   }
+  if (kGraded)
+    for (int k = 0; k < kGradeSums; k++) {
+      const float v = warp_sum(gsum[k]);
+      if (lane == 0) sh.wgrade[warp][k] = v;
+    }
   __syncthreads();
   float* out = bp.partial + ((size_t)cam * bp.blocks_per_img + blk) * kGradFloats;
   for (int k = tid; k < kMaxMaterials * 5; k += kBwdThreads) {
@@ -305,27 +341,88 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
     for (int w = 0; w < kBwdWarps; w++) v += sh.wred[w][kMaxLights * 4];
     out[kMaxMaterials * 4 + kMaxLights * 4] = v;
   }
+  if (tid >= 32 && tid < 32 + kGradeSums) {
+    float v = 0.0f;
+    if (kGraded)
+      for (int w = 0; w < kBwdWarps; w++) v += sh.wgrade[w][tid - 32];
+    out[kGradGrade + tid - 32] = v;
+  }
 }
 
-// One thread per (sample, gradient float): sum the sample's partial rows in (camera, block) order.
+// The gradients of the grading parameters from an image-summed graded loss: with c' = A c + t +
+// a n per pixel, A = k S R W (contrast k, saturation S, rotation R by h about the grey axis, white
+// balance W = diag(1 + t, 1 + u, 1 - t)) and t = (1 - k) / 2 + b, dL/dtheta = sum_ij dA_ij/dtheta
+// M_ij + sum_i dt_i/dtheta s_i with M = sum dc' c^T and s = sum dc' (the partial rows' sums); the
+// grain amplitude's is sum (sum_k dc'_k) n.  Out: d hue, saturation, contrast, brightness,
+// temperature, tint, grain amplitude, 0 (the seed).
+__device__ void grading_grads(const float* g, const float* sums, float* out) {
+  float hs, hc;
+  sincosf(g[0], &hs, &hc);
+  const float kx = 0.57735026918962576f;
+  const float a = hc + (1.0f - hc) / 3.0f, b = (1.0f - hc) / 3.0f - kx * hs, c = (1.0f - hc) / 3.0f + kx * hs;
+  const float da = -2.0f * hs / 3.0f, db = hs / 3.0f - kx * hc, dc = hs / 3.0f + kx * hc;  // d/dh
+  const float R[3][3] = {{a, b, c}, {c, a, b}, {b, c, a}};
+  const float dR[3][3] = {{da, db, dc}, {dc, da, db}, {db, dc, da}};
+  const float wb[3] = {1.0f + g[4], 1.0f + g[5], 1.0f - g[4]};
+  const float Yw[3] = {0.2126f, 0.7152f, 0.0722f};
+  const float sat = g[1], con = g[2];
+  const float* M = sums;
+  const float* sv = sums + 9;
+  float d_h = 0.0f, d_sat = 0.0f, d_con = 0.0f, d_t = 0.0f, d_u = 0.0f;
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) {
+      float sr = 0.0f, sdr = 0.0f, dsr = 0.0f;  // (S R)_ij, (S dR/dh)_ij, (dS/dsat R)_ij
+      for (int m = 0; m < 3; m++) {
+        const float S_im = (i == m ? sat : 0.0f) + (1.0f - sat) * Yw[m];
+        const float dS_im = (i == m ? 1.0f : 0.0f) - Yw[m];
+        sr += S_im * R[m][j];
+        sdr += S_im * dR[m][j];
+        dsr += dS_im * R[m][j];
+      }
+      const float Mij = M[i * 3 + j];
+      d_h += con * sdr * wb[j] * Mij;
+      d_sat += con * dsr * wb[j] * Mij;
+      d_con += sr * wb[j] * Mij;
+      d_t += con * sr * (j == 0 ? 1.0f : (j == 2 ? -1.0f : 0.0f)) * Mij;
+      d_u += con * sr * (j == 1 ? 1.0f : 0.0f) * Mij;
+    }
+  const float ssum = sv[0] + sv[1] + sv[2];
+  out[0] = d_h;
+  out[1] = d_sat;
+  out[2] = d_con - 0.5f * ssum;
+  out[3] = ssum;
+  out[4] = d_t;
+  out[5] = d_u;
+  out[6] = sums[12];
+  out[7] = 0.0f;
+}
+
+// One thread per (sample, gradient float): sum the sample's partial rows in (camera, block) order;
+// for a graded loss one thread then forms the grading gradients from the summed grading sums.
 constexpr int kReduceThreads = 192;
 static_assert(kGradFloats <= kReduceThreads, "one thread per gradient float");
-__global__ void backward_reduce_kernel(BackwardParams bp) {
+__global__ void __launch_bounds__(kReduceThreads) backward_reduce_kernel(BackwardParams bp) {
   const Params& p = bp.base;
   const int s = blockIdx.x, k = threadIdx.x;
-  if (k >= kGradFloats) return;
+  __shared__ float gsums[kGradeSums];
   float v = 0.0f;
-  for (int c = p.cam_offset[s]; c < p.cam_offset[s + 1]; c++)
-    for (int b = 0; b < bp.blocks_per_img; b++) v += bp.partial[((size_t)c * bp.blocks_per_img + b) * kGradFloats + k];
+  if (k < kGradFloats)
+    for (int c = p.cam_offset[s]; c < p.cam_offset[s + 1]; c++)
+      for (int b = 0; b < bp.blocks_per_img; b++) v += bp.partial[((size_t)c * bp.blocks_per_img + b) * kGradFloats + k];
   if (k < kMaxMaterials * 4) {
     if (bp.d_material) bp.d_material[(size_t)s * kMaxMaterials * 4 + k] = v;
   } else if (k < kMaxMaterials * 4 + kMaxLights * 4) {
     if (bp.d_light) bp.d_light[(size_t)s * kMaxLights * 4 + (k - kMaxMaterials * 4)] = v;
   } else if (k < kGradEmission) {
     if (bp.d_exposure) bp.d_exposure[s] = v;
-  } else {
+  } else if (k < kGradGrade) {
     if (bp.d_emission) bp.d_emission[(size_t)s * kMaxMaterials + (k - kGradEmission)] = v;
+  } else if (k < kGradFloats) {
+    gsums[k - kGradGrade] = v;
   }
+  __syncthreads();
+  if (k == 0 && bp.d_grading && p.grading)
+    grading_grads(p.grading + (size_t)s * 8, gsums, bp.d_grading + (size_t)s * 8);
 }
 
 }  // namespace
@@ -333,7 +430,10 @@ __global__ void backward_reduce_kernel(BackwardParams bp) {
 int launch_backward(const BackwardParams& bp, int threads, void* stream, char* err, size_t errlen) {
   (void)threads;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  backward_partial_kernel<<<dim3(bp.base.n_cams, bp.blocks_per_img), kBwdThreads, 0, st>>>(bp);
+  if (bp.d_grading && bp.base.grading)
+    backward_partial_kernel<true><<<dim3(bp.base.n_cams, bp.blocks_per_img), kBwdThreads, 0, st>>>(bp);
+  else
+    backward_partial_kernel<false><<<dim3(bp.base.n_cams, bp.blocks_per_img), kBwdThreads, 0, st>>>(bp);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) {
     backward_reduce_kernel<<<bp.base.n_samples, kReduceThreads, 0, st>>>(bp);

@@ -90,6 +90,7 @@ struct Params {
   uint16_t* normal;
   uint8_t* seg;
   float* rgb_linear;
+  float* rgb_graded;  // [N][3] or null: the graded colour before clamping
   float* gbuffer;
   int32_t* tracker;  // [n_cams][inst_max][8] or null
   int64_t total_pixels;
@@ -162,12 +163,16 @@ struct BackwardParams {
   float* d_light;
   float* d_exposure;
   float* d_emission;     // or null
+  float* d_grading;      // [n_samples][8] or null: the loss is on the graded colour (d_rgb = dL/d graded)
   float* partial;        // [n_cams][blocks_per_img][kGradFloats]
   int32_t blocks_per_img;
 };
-// per partial row: material [32][4], light [4][4], exposure, emission [32]
+// per partial row: material [32][4], light [4][4], exposure, emission [32], and for a graded loss
+// the sums sum dc' c^T [3][3], sum dc' [3] and sum (sum_k dc'_k) * grain over the image's pixels
 constexpr int kGradEmission = kMaxMaterials * 4 + kMaxLights * 4 + 1;
-constexpr int kGradFloats = kGradEmission + kMaxMaterials;  // 177
+constexpr int kGradGrade = kGradEmission + kMaxMaterials;
+constexpr int kGradeSums = 13;
+constexpr int kGradFloats = kGradGrade + kGradeSums;  // 190
 int launch_backward(const BackwardParams& p, int threads, void* stream, char* err, size_t errlen);
 
 }  // namespace orrb

@@ -63,13 +63,6 @@ constexpr int kFeatShadowPass = 16;   // the depth-only pass that renders the sh
 __constant__ float kPcfFactor[10] = {1.0f,        0.8888889f, 0.7777778f, 0.6666667f, 0.5555556f,
                                      0.44444445f, 0.33333334f, 0.22222222f, 0.11111111f, 0.0f};
 
-// The PCG hash (Jarzynski and Olano, "Hash Functions for GPU Rendering", JCGT 2020): one LCG
-// step, a random xorshift and a multiply.
-__host__ __device__ inline unsigned pcg_hash(unsigned v) {
-  const unsigned state = v * 747796405u + 2891336453u;
-  const unsigned word = ((state >> ((state >> 28u) + 4u)) ^ state) * 277803737u;
-  return (word >> 22u) ^ word;
-}
 
 struct ImageInfo {
   int cam, s, W, H, inst0, n_inst, ortho, T, valid;
@@ -1128,35 +1121,16 @@ __device__ void spot_setup(const Params& p, ImageInfo& im, int l) {
 
 __device__ void grading_setup(const Params& p, ImageInfo& im) {
   const float* g = p.grading + (size_t)im.s * 8;
-  float hs, hc;
-  sincosf(g[0], &hs, &hc);
-  const float k = 0.57735026918962576f;  // 1/sqrt(3): the grey axis (k, k, k)
-  // rotation R = cos I + sin [axis]x + (1 - cos) axis axis^T
-  const float a = hc + (1.0f - hc) / 3.0f, b = (1.0f - hc) / 3.0f - k * hs, c = (1.0f - hc) / 3.0f + k * hs;
-  const float R[3][3] = {{a, b, c}, {c, a, b}, {b, c, a}};
-  const float wb[3] = {1.0f + g[4], 1.0f + g[5], 1.0f - g[4]};
-  const float Yw[3] = {0.2126f, 0.7152f, 0.0722f};
-  const float sat = g[1], con = g[2];
-  // S = sat I + (1 - sat) 1 Yw^T; then contrast con and the offsets 0.5 (1 - con) + brightness
-  for (int i = 0; i < 3; i++) {
-    for (int j = 0; j < 3; j++) {
-      float rw = 0.0f;  // (S R)_ij
-      for (int m = 0; m < 3; m++) rw += ((i == m ? sat : 0.0f) + (1.0f - sat) * Yw[m]) * R[m][j];
-      im.gm[i][j] = con * rw * wb[j];
-    }
-    im.gm[i][3] = 0.5f * (1.0f - con) + g[3];
-  }
+  grading_map(g, im.gm);
   im.grain = g[6];
-  const unsigned cam_local = unsigned(im.cam - p.cam_offset[im.s]);
-  im.grain_key = pcg_hash(unsigned(g[7]) + 0x9E3779B9u * (cam_local + 1u));
+  im.grain_key = grain_key(g, unsigned(im.cam - p.cam_offset[im.s]));
 }
 
 // Colour grading of one pixel's linear colour (see orrb_batch_desc::grading); `pixel` is the
 // pixel's index within its image.  The grain is the PCG hash of the image's key and the
 // pixel index, scaled to [0, 1).
 __device__ __forceinline__ void grade(const ImageInfo& im, unsigned pixel, float c[3]) {
-  const float n = float(pcg_hash(im.grain_key ^ pixel)) * 2.3283064365386963e-10f - 0.5f;  // 2^-32
-  const float o = im.grain * n;
+  const float o = im.grain * grain_centred(im.grain_key, pixel);
   const float r = c[0], g = c[1], b = c[2];
 #pragma unroll
   for (int i = 0; i < 3; i++) c[i] = fmaf(im.gm[i][0], r, fmaf(im.gm[i][1], g, fmaf(im.gm[i][2], b, im.gm[i][3] + o)));
@@ -1514,16 +1488,32 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
       // warp fill whole sectors of the row between them
       // (explicit global streaming stores: outputs are not re-read, and the compiler need not
       // assume they alias the shared-memory light and material tables)
-      if (kGrade && rgb_row) {
+      if (kGrade && (rgb_row || p.rgb_graded)) {
         float gc[3] = {rgb[0], rgb[1], rgb[2]};
         grade(im, unsigned(py * im.W + px), gc);
-        __stcs(rgb_row + 3 * lx + 0, quantise(gc[0]));
-        __stcs(rgb_row + 3 * lx + 1, quantise(gc[1]));
-        __stcs(rgb_row + 3 * lx + 2, quantise(gc[2]));
-      } else if (rgb_row) {
-        __stcs(rgb_row + 3 * lx + 0, quantise(rgb[0]));
-        __stcs(rgb_row + 3 * lx + 1, quantise(rgb[1]));
-        __stcs(rgb_row + 3 * lx + 2, quantise(rgb[2]));
+        if (rgb_row) {
+          __stcs(rgb_row + 3 * lx + 0, quantise(gc[0]));
+          __stcs(rgb_row + 3 * lx + 1, quantise(gc[1]));
+          __stcs(rgb_row + 3 * lx + 2, quantise(gc[2]));
+        }
+        if (p.rgb_graded) {  // the graded colour before clamping (the input of a graded loss)
+          float* o3 = p.rgb_graded + 3 * (orow + lx);
+          __stcs(o3 + 0, gc[0]);
+          __stcs(o3 + 1, gc[1]);
+          __stcs(o3 + 2, gc[2]);
+        }
+      } else {
+        if (rgb_row) {
+          __stcs(rgb_row + 3 * lx + 0, quantise(rgb[0]));
+          __stcs(rgb_row + 3 * lx + 1, quantise(rgb[1]));
+          __stcs(rgb_row + 3 * lx + 2, quantise(rgb[2]));
+        }
+        if (p.rgb_graded) {  // (an ungraded batch: the graded colour is the linear colour)
+          float* o3 = p.rgb_graded + 3 * (orow + lx);
+          __stcs(o3 + 0, rgb[0]);
+          __stcs(o3 + 1, rgb[1]);
+          __stcs(o3 + 2, rgb[2]);
+        }
       }
       if (nrm_row) {
         const __half2 h01 = __floats2half2_rn(n[0], n[1]);

@@ -36,4 +36,46 @@ __device__ __forceinline__ float lobe_pow(float ndh, float alpha) {
   return exp2f_approx(alpha * lg);
 }
 
+// The PCG hash (Jarzynski and Olano, "Hash Functions for GPU Rendering", JCGT 2020): one LCG
+// step, a random xorshift and a multiply.
+__host__ __device__ inline unsigned pcg_hash(unsigned v) {
+  const unsigned state = v * 747796405u + 2891336453u;
+  const unsigned word = ((state >> ((state >> 28u) + 4u)) ^ state) * 277803737u;
+  return (word >> 22u) ^ word;
+}
+
+// The grain key of an image: the hash of the sample's grain seed and the camera's index within
+// its sample.  A pixel's grain value is the hash of (key ^ pixel index within the image) scaled
+// to [0, 1), minus 1/2.
+__device__ __forceinline__ unsigned grain_key(const float* g, unsigned cam_local) {
+  return pcg_hash(unsigned(g[7]) + 0x9E3779B9u * (cam_local + 1u));
+}
+__device__ __forceinline__ float grain_centred(unsigned key, unsigned pixel) {
+  return float(pcg_hash(key ^ pixel)) * 2.3283064365386963e-10f - 0.5f;  // 2^-32
+}
+
+// Colour grading of a sample (g = hue, saturation, contrast, brightness, temperature, tint, grain,
+// seed): white balance, the rotation about the grey axis, saturation, contrast and brightness are
+// each affine in the colour, so they compose into one map c -> A c + t (rows of gm = A | t).
+__device__ __forceinline__ void grading_map(const float* g, float gm[3][4]) {
+  float hs, hc;
+  sincosf(g[0], &hs, &hc);
+  const float k = 0.57735026918962576f;  // 1/sqrt(3): the grey axis (k, k, k)
+  // rotation R = cos I + sin [axis]x + (1 - cos) axis axis^T
+  const float a = hc + (1.0f - hc) / 3.0f, b = (1.0f - hc) / 3.0f - k * hs, c = (1.0f - hc) / 3.0f + k * hs;
+  const float R[3][3] = {{a, b, c}, {c, a, b}, {b, c, a}};
+  const float wb[3] = {1.0f + g[4], 1.0f + g[5], 1.0f - g[4]};
+  const float Yw[3] = {0.2126f, 0.7152f, 0.0722f};
+  const float sat = g[1], con = g[2];
+  // S = sat I + (1 - sat) 1 Yw^T; then contrast con and the offsets 0.5 (1 - con) + brightness
+  for (int i = 0; i < 3; i++) {
+    for (int j = 0; j < 3; j++) {
+      float rw = 0.0f;  // (S R)_ij
+      for (int m = 0; m < 3; m++) rw += ((i == m ? sat : 0.0f) + (1.0f - sat) * Yw[m]) * R[m][j];
+      gm[i][j] = con * rw * wb[j];
+    }
+    gm[i][3] = 0.5f * (1.0f - con) + g[3];
+  }
+}
+
 }  // namespace orrb

@@ -58,7 +58,7 @@ class orrb_batch_desc(C.Structure):
 
 class orrb_outputs(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in ("rgb", "depth", "normal", "seg", "rgb_linear", "gbuffer", "tracker",
-                                          "shadow_map")]
+                                          "shadow_map", "rgb_graded")]
 
 
 class orrb_config(C.Structure):
@@ -68,7 +68,7 @@ class orrb_config(C.Structure):
 
 class orrb_param_grads(C.Structure):
     _fields_ = [("d_material", C.c_void_p), ("d_light", C.c_void_p), ("d_exposure", C.c_void_p),
-                ("d_emission", C.c_void_p)]
+                ("d_emission", C.c_void_p), ("d_grading", C.c_void_p)]
 
 
 class OrrbError(RuntimeError):

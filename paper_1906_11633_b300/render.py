@@ -143,7 +143,8 @@ class Renderer:
             self._ws = torch.empty(n, dtype=torch.uint8, device=self.device)
         return self._ws
 
-    def alloc_outputs(self, n_pixels: int, rgb_linear: bool = False, gbuffer: bool = False):
+    def alloc_outputs(self, n_pixels: int, rgb_linear: bool = False, gbuffer: bool = False,
+                      rgb_graded: bool = False):
         d = self.device
         out = dict(rgb=torch.empty((n_pixels, 3), dtype=torch.uint8, device=d),
                    depth=torch.empty(n_pixels, dtype=torch.float32, device=d),
@@ -153,6 +154,8 @@ class Renderer:
             out["rgb_linear"] = torch.empty((n_pixels, 3), dtype=torch.float32, device=d)
         if gbuffer:
             out["gbuffer"] = torch.empty((L.ORRB_GBUFFER_PLANES, n_pixels), dtype=torch.float32, device=d)
+        if rgb_graded:
+            out["rgb_graded"] = torch.empty((n_pixels, 3), dtype=torch.float32, device=d)
         return out
 
     def alloc_shadow_maps(self, db: DeviceBatch) -> torch.Tensor:
@@ -162,12 +165,13 @@ class Renderer:
                            device=self.device)
 
     def render(self, db: DeviceBatch, out=None, cfg: Optional[L.orrb_config] = None, rgb_linear: bool = False,
-               gbuffer: bool = False, stream=None, workspace: Optional[torch.Tensor] = None, tracker: bool = False):
+               gbuffer: bool = False, stream=None, workspace: Optional[torch.Tensor] = None, tracker: bool = False,
+               rgb_graded: bool = False):
         """Render `db`; `tracker` adds the per (camera, instance) rows [n_cams, max instances, 8]; a batch
         with shadows also writes (and returns) its shadow maps as "shadow_map"."""
         cfg = cfg or config()
         if out is None:
-            out = self.alloc_outputs(db.total_pixels, rgb_linear, gbuffer)
+            out = self.alloc_outputs(db.total_pixels, rgb_linear, gbuffer, rgb_graded)
             if tracker:
                 out["tracker"] = torch.empty((int(db.shape.n_cams), int(db.shape.max_inst_per_sample), 8),
                                              dtype=torch.int32, device=self.device)
@@ -176,7 +180,7 @@ class Renderer:
         ws = workspace if workspace is not None else self.workspace(db.shape, cfg)
         outs = L.orrb_outputs(*[out[k].data_ptr() if k in out else None
                                 for k in ("rgb", "depth", "normal", "seg", "rgb_linear", "gbuffer", "tracker",
-                                          "shadow_map")])
+                                          "shadow_map", "rgb_graded")])
         st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
         L.orrb_render_batch(self.ctx, db.shape, db.desc, outs, cfg, ws.data_ptr(), ws.numel(), st)
         self._last_ws = ws
@@ -187,9 +191,10 @@ class Renderer:
         return L.orrb_read_status(self.ctx, self._last_ws.data_ptr(), st)
 
     def shade_backward(self, db: DeviceBatch, gbuffer: torch.Tensor, d_rgb: torch.Tensor, stream=None,
-                       emission: bool = False):
-        """(d material [S,32,4], d light [S,4,4], d exposure [S]), plus d emission [S,32] last
-        when `emission`."""
+                       emission: bool = False, grading: bool = False):
+        """(d material [S,32,4], d light [S,4,4], d exposure [S]), plus d emission [S,32] when
+        `emission`, plus d grading [S,8] last when `grading` (then d_rgb is dL/d rgb_graded, the
+        loss being on the graded colour)."""
         n = L.orrb_backward_workspace_size(self.ctx, db.shape)
         if self._bws is None or self._bws.numel() < n:
             self._bws = torch.empty(n, dtype=torch.uint8, device=self.device)
@@ -198,13 +203,15 @@ class Renderer:
         dl = torch.empty((S, L.ORRB_MAX_LIGHTS, 4), dtype=torch.float32, device=self.device)
         de = torch.empty(S, dtype=torch.float32, device=self.device)
         dem = torch.empty((S, L.ORRB_MAX_MATERIALS), dtype=torch.float32, device=self.device) if emission else None
+        dg = torch.empty((S, 8), dtype=torch.float32, device=self.device) if grading else None
         grads = L.orrb_param_grads(dm.data_ptr(), dl.data_ptr(), de.data_ptr(),
-                                   dem.data_ptr() if emission else None)
+                                   dem.data_ptr() if emission else None, dg.data_ptr() if grading else None)
         st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
         d_rgb = d_rgb.contiguous()
         L.orrb_shade_backward(self.ctx, db.shape, db.desc, gbuffer.data_ptr(), d_rgb.data_ptr(), grads,
                               self._bws.data_ptr(), self._bws.numel(), st)
-        return (dm, dl, de, dem) if emission else (dm, dl, de)
+        r = (dm, dl, de) + ((dem,) if emission else ()) + ((dg,) if grading else ())
+        return r
 
 
 class GraphRender:

@@ -150,3 +150,33 @@ def test_shadowed_adjoint_matches_oracle(renderer, oracle):
     assert rel_err(dl[:, :3], rdl[:, :3]).max() < REL
     assert rel_err(de, rde).max() < REL
     assert rel_err(dem, rdem).max() < REL
+
+
+def test_graded_loss_adjoint_matches_oracle(renderer, oracle):
+    """A loss on the graded colour (colour grading, Sec. 4.3.1 post-processing randomizer): the
+    GPU's rgb_graded equals the oracle's fp64 grading of its linear colour, and the adjoint through
+    the grading (material, light, exposure and the seven grading parameters) matches the oracle's
+    fp64 adjoint of its step-by-step grading."""
+    b = sg.benchmark_batch(8, np.arange(6), res=64)
+    assert b.grading is not None
+    db = renderer.upload(b)
+    out = renderer.render(db, rgb_linear=True, gbuffer=True, rgb_graded=True)
+    o = to_numpy(out)
+    gb = o["gbuffer"]
+    gpos, gnrm = np.ascontiguousarray(gb[0:3].T), np.ascontiguousarray(gb[3:6].T)
+    gmat = gb[6].view(np.int32).copy()
+    graded = oracle.grade_f64(b, o["rgb_linear"].astype(np.float64))
+    assert np.abs(o["rgb_graded"] - graded).max() < 1e-4
+    rng = np.random.default_rng(8)
+    target = graded + rng.normal(0.0, 0.05, graded.shape)
+    d = (2.0 * (o["rgb_graded"].astype(np.float64) - target)).astype(np.float32)
+    dm, dl, de, dg = renderer.shade_backward(db, out["gbuffer"], torch.from_numpy(d).cuda(), grading=True)
+    rdm, rdl, rde, rdg = oracle.graded_backward_f64(b, gpos, gnrm, gmat, d.astype(np.float64))
+    assert rel_err(dm.cpu().numpy(), rdm).max() < REL
+    act = np.arange(4)[None, :] < b.light_meta[:, :1]
+    assert rel_err(dl.cpu().numpy()[act], rdl[act]).max() < REL
+    assert rel_err(de.cpu().numpy(), rde).max() < REL
+    got = dg.cpu().numpy()
+    for j in range(7):   # per parameter kind, relative to that kind's largest gradient
+        assert rel_err(got[:, j], rdg[:, j]).max() < REL, (j, got[:, j], rdg[:, j])
+    assert np.all(got[:, 7] == 0.0)
