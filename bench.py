@@ -384,6 +384,11 @@ def run_ours(args, world, rank, local):
 
     # -- the differentiation pattern on the same batch: forward with G-buffer + shading adjoint ---
     dfms, dbms, dbytes = time_diff(r, db, batch, reps=10, warmup=3)
+    # -- the batching and serving patterns, briefly (their own workloads measure them at length) --
+    uneven = serve = None
+    if not args.no_patterns:
+        uneven = measure_uneven(args, world, rank, local)
+        serve = measure_serve(1.0, world, rank, local)
 
     if rank != 0:
         return
@@ -450,6 +455,13 @@ def run_ours(args, world, rank, local):
                            "channels on a copy stream; D2H is capped near 57 GB/s on this host link"},
             "gpu_launches": args.steps,
             "roofline": roof,
+            "uneven": None if uneven is None else {
+                k: uneven[k] for k in ("value", "ms_per_step", "fused_over_plain", "plain", "device_status")} | {
+                "config": {k: uneven["config"][k] for k in ("scenes", "images", "pixels", "triangles_per_scene", "tile",
+                                                             "threads")}},
+            "serve": None if serve is None else {
+                k: serve[k] for k in ("value", "p50_ms", "p99_ms", "max_ms", "requests", "batches",
+                                      "max_concurrent_batches")} | {"seconds": 1.0, "rate_hz": 2000.0},
             "diff": {"forward_gbuffer_ms": dfms, "adjoint_ms": dbms,
                      "adjoint_achieved_gbs": dbytes / (dbms / 1e3) / 1e9,
                      "adjoint_frac_of_hbm": dbytes / (dbms / 1e3) / 1e9 / hbm,
@@ -466,6 +478,13 @@ def run_ours(args, world, rank, local):
 def run_uneven(args, world, rank, local):
     """1024 scenes with log-uniform [1k, 50k] triangles, square resolutions U{64..512}, 1-3 cameras: one
     persistent launch replayed from a CUDA graph with the autotuned tiling, vs per-scene plain launches."""
+    line = measure_uneven(args, world, rank, local)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+def measure_uneven(args, world, rank, local):
+    """The uneven workload's JSON line (rank 0; None on the others)."""
     import torch
     from paper_1906_11633_b300 import scenegen as sg
     from paper_1906_11633_b300 import lib as L
@@ -502,7 +521,7 @@ def run_uneven(args, world, rank, local):
     torch.cuda.synchronize()
     plain_ms = max_over_ranks(e0.elapsed_time(e1), world)
     if rank != 0:
-        return
+        return None
     peaks, _ = load_peaks()
     alg_bytes = BYTES_PER_PX * batch.total_pixels
     line = {"workload": "uneven", "metric": "samples/s, uneven batch in one persistent launch (CUDA graph)",
@@ -517,7 +536,7 @@ def run_uneven(args, world, rank, local):
                          "unit": "GB/s", "frac": alg_bytes / (ms / 1e3) / 1e9 / float(peaks["hbm_gbs"]),
                          "alg_bytes_per_launch": alg_bytes},
             "device_status": r.status()}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def time_diff(r, db, batch, reps: int, warmup: int):
@@ -723,11 +742,18 @@ def run_cube(args, world, rank, local):
 
 def run_serve(args, world, rank, local):
     """Poisson arrivals at 2000 req/s of 1-64-sample hand requests at {64,128,200,256} px, 1-3 cameras."""
+    line = measure_serve(args.serve_seconds, world, rank, local)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+def measure_serve(seconds, world, rank, local):
+    """The serving workload's JSON line for `seconds` of arrivals (rank 0; None on the others)."""
     import torch
     from paper_1906_11633_b300 import scenegen as sg
     from paper_1906_11633_b300.serve import GpuBackend, Server, run_poisson
     torch.cuda.set_device(local)
-    rate, dur = 2000.0, args.serve_seconds
+    rate, dur = 2000.0, seconds
     reqs = sg.poisson_requests(SEED + rank, rate, dur)
     meshes = sg.hand_meshes()
     t0 = time.perf_counter()
@@ -743,7 +769,7 @@ def run_serve(args, world, rank, local):
     st = srv.stats(wall)
     srv.close()
     if rank != 0:
-        return
+        return None
     line = {"workload": "serve", "metric": "samples/s and request latency under Poisson arrivals",
             "value": st["samples_per_s"], "unit": UNIT, "n_gpus": world,
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
@@ -752,7 +778,7 @@ def run_serve(args, world, rank, local):
             "config": {"rate_hz": rate, "seconds": dur, "tick_ms": 2.0, "streams": 2, "max_inflight": 4,
                        "request_samples": "U{1..64}", "resolution": list(sg.SERVE_RES), "cameras": "U{1..3}",
                        "host_generation_s": gen_s}}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def main():
@@ -767,6 +793,8 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the fused kernel from an ncu capture of the same kernel source")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-patterns", action="store_true",
+                    help="headline: skip the short uneven-batch and serving measurements")
     ap.add_argument("--workload", choices=["hand", "uneven", "diff", "serve", "grade", "track", "spot", "shadow", "cube"], default="hand",
                     help="hand: the headline line; the others print supplementary lines")
     ap.add_argument("--serve-seconds", type=float, default=3.0)

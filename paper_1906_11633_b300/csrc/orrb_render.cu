@@ -91,8 +91,10 @@ struct ImageInfo {
 // camera-to-shadow-camera map S V^-1 and the shadow camera's fx, fy, cx, cy, near, bias.
 struct ShadowInfo {
   int cast[kMaxLights][kMaxShadowFaces];
-  float sm[kMaxLights][kMaxShadowFaces][12];
-  float si[kMaxLights][kMaxShadowFaces][7];
+  alignas(16) float sm[kMaxLights][kMaxShadowFaces][12];  // (rows of 16-byte vector loads)
+  alignas(16) float si[kMaxLights][kMaxShadowFaces][8];   // the seven intrinsics, padded
+  unsigned long long map_off[kMaxLights][kMaxShadowFaces];  // first texel of the face's map
+  float pcf[12];  // (9 - k) / 9 for k = 0..9 (a shared-memory copy: lanes index it divergently)
 };
 
 struct CtaShared {
@@ -1044,7 +1046,11 @@ __device__ void shadow_setup(const Params& p, const ImageInfo& im, ShadowInfo& s
         sd.sm[l][f][j + 4 * i] = j == 3 ? __fadd_rn(r, S[i * 4 + 3]) : r;
       }
     for (int k = 0; k < 7; k++) sd.si[l][f][k] = si[k];
+    sd.si[l][f][7] = 0.0f;
+    sd.map_off[l][f] = (unsigned long long)c * p.shadow_res * p.shadow_res;
   }
+  if (l == 0)
+    for (int k = 0; k < 10; k++) sd.pcf[k] = kPcfFactor[k];
 }
 
 // The shadowed taps k (0..9) of light l at the G-buffer position P (whose three coordinates the
@@ -1059,22 +1065,24 @@ __device__ __forceinline__ int shadow_lookup_one(const Params& p, const ImageInf
   const int R = p.shadow_res, F = p.shadow_faces;
   for (int f = 0; f < F; f++) {  // the first casting face whose map contains the point decides
     if (!sd.cast[l][f]) continue;
-    const float* M = sd.sm[l][f];
-    const float* si = sd.si[l][f];
-    const float q2 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[8], P0), __fmul_rn(M[9], P1)), __fmul_rn(M[10], P2)), M[11]);
+    const float4* M4 = reinterpret_cast<const float4*>(sd.sm[l][f]);
+    const float4 ma = M4[0], mb = M4[1], mc = M4[2];
+    const float4 sa = reinterpret_cast<const float4*>(sd.si[l][f])[0];  // fx, fy, cx, cy
+    const float4 sb = reinterpret_cast<const float4*>(sd.si[l][f])[1];  // near, bias, type
+    const float q2 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(mc.x, P0), __fmul_rn(mc.y, P1)), __fmul_rn(mc.z, P2)), mc.w);
     const float z = -q2;
-    if (!(z > si[4])) continue;
-    const float q0 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[0], P0), __fmul_rn(M[1], P1)), __fmul_rn(M[2], P2)), M[3]);
-    const float q1 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[4], P0), __fmul_rn(M[5], P1)), __fmul_rn(M[6], P2)), M[7]);
-    const bool ortho = si[6] != 0.0f;  // (orthographic: a directional light's camera)
+    if (!(z > sb.x)) continue;
+    const float q0 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(ma.x, P0), __fmul_rn(ma.y, P1)), __fmul_rn(ma.z, P2)), ma.w);
+    const float q1 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(mb.x, P0), __fmul_rn(mb.y, P1)), __fmul_rn(mb.z, P2)), mb.w);
+    const bool ortho = sb.z != 0.0f;  // (orthographic: a directional light's camera)
     const float iw = ortho ? 1.0f : __frcp_rn(z);
-    const float u = __fadd_rn(si[2], __fmul_rn(si[0], ortho ? q0 : __fmul_rn(q0, iw)));
-    const float v = __fsub_rn(si[3], __fmul_rn(si[1], ortho ? q1 : __fmul_rn(q1, iw)));
+    const float u = __fadd_rn(sa.z, __fmul_rn(sa.x, ortho ? q0 : __fmul_rn(q0, iw)));
+    const float v = __fsub_rn(sa.w, __fmul_rn(sa.y, ortho ? q1 : __fmul_rn(q1, iw)));
     if (!(fabsf(u) < kGuardPx) || !(fabsf(v) < kGuardPx)) continue;
     const int i0 = int(floorf(u)), j0 = int(floorf(v));
     if (i0 < 0 || j0 < 0 || i0 >= R || j0 >= R) continue;
-    const float zb = __fsub_rn(z, si[5]);
-    const size_t m0 = (((size_t)im.s * kMaxLights + l) * F + f) * R * R;
+    const float zb = __fsub_rn(z, sb.y);
+    const size_t m0 = sd.map_off[l][f];
     int k = -1;
     if (p.shadow_nb) {  // one entry settles lit points and those behind every occupied tap
       const size_t t = m0 + (size_t)j0 * R + i0;
@@ -1188,7 +1196,7 @@ __device__ int shade_shadowed(const Params& p, const CtaShared& sh, const Shadow
       r = 1.0f;
       E = lq.w;
     }
-    E *= kPcfFactor[k];
+    E *= sd.pcf[k];
     const float ndl = fmaxf(0.0f, (n[0] * Lx + n[1] * Ly + n[2] * Lz) * r);
     D = fmaf(E, ndl, D);
     if (ndl > 0.0f && m[3] != 0.0f) {
