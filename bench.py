@@ -283,7 +283,7 @@ def run_reference(args, world, rank):
     from oracle import oracle as orc
     batch = sg.hand_batch(SEED, np.arange(N_SAMPLES), res=RES, n_cams=N_CAMS)
     threads = orc.default_threads()
-    n = 8                                  # samples per step: a bounded slice of the batch
+    n = max(8, threads)                    # samples per step: a bounded slice of the batch, three images a thread
     per = []
     for i in range(args.warmup + args.steps):
         ids = [(i * n + k) % N_SAMPLES for k in range(n)]
