@@ -232,48 +232,6 @@ class Server:
                 "max_concurrent_batches": conc, "memory_waits": waits}
 
 
-class StagingPool:
-    """Reusable parameter staging for one stream: pinned host buffers and device buffers that a
-    batch's arrays are packed into (256-byte aligned), so that a launch makes one host-to-device
-    copy into memory allocated once instead of page-locking and allocating every array.  A buffer
-    pair is reused once the copy that last read its host side has completed (its event)."""
-
-    def __init__(self, torch, device):
-        self.torch, self.device = torch, device
-        self.slots = []   # [host (pinned uint8), device (uint8), event or None]
-
-    def _slot(self, nbytes: int):
-        torch = self.torch
-        for sl in self.slots:
-            if sl[1].numel() >= nbytes and (sl[2] is None or sl[2].query()):
-                return sl
-        cap = 1 << max(16, int(nbytes - 1).bit_length())
-        sl = [torch.empty(cap, dtype=torch.uint8, pin_memory=True), torch.empty(cap, dtype=torch.uint8, device=self.device),
-              None]
-        self.slots.append(sl)
-        return sl
-
-    def pack(self, arrs, stream):
-        """Device tensors holding `arrs` (name -> contiguous numpy array), copied on `stream`."""
-        torch = self.torch
-        offs, o = {}, 0
-        for n, a in arrs.items():
-            offs[n] = o
-            o = (o + a.nbytes + 255) & ~255
-        sl = self._slot(max(o, 256))
-        host = sl[0].numpy()
-        for n, a in arrs.items():
-            host[offs[n]:offs[n] + a.nbytes] = a.reshape(-1).view(np.uint8)
-        sl[1][:o].copy_(sl[0][:o], non_blocking=True)
-        ev = torch.cuda.Event()
-        ev.record(stream)
-        sl[2] = ev
-        out = {}
-        for n, a in arrs.items():
-            out[n] = sl[1][offs[n]:offs[n] + a.nbytes].view(getattr(torch, str(a.dtype))).view(a.shape)
-        return out
-
-
 class GpuBackend:
     """Packs requests into one batch and renders it on a per-slot CUDA stream.
 
@@ -292,7 +250,6 @@ class GpuBackend:
         self.r = Renderer(meshes, device=device)
         self.cfg = cfg or config()
         self.streams = [torch.cuda.Stream(device=self.r.device) for _ in range(n_streams)]
-        self.staging = [StagingPool(torch, self.r.device) for _ in range(n_streams)]
         self.readback = readback
         self.reserve = reserve_bytes
         # workspace bytes ~ a + b * (triangles of the largest sample), fitted from two library queries
@@ -326,7 +283,11 @@ class GpuBackend:
         packed, shape = self._shape(batches)
         s = self.streams[k]
         with torch.cuda.stream(s):
-            t = self.staging[k].pack(host_arrays(packed), s)
+            # (pinned copies come from torch's caching host allocator, which reuses its blocks once
+            # the copies that read them have run: a pool of per-stream staging buffers measured
+            # worse, its buffers waiting behind the stream's previous render)
+            arrs = host_arrays(packed)
+            t = {n: torch.from_numpy(a).pin_memory().to(self.r.device, non_blocking=True) for n, a in arrs.items()}
             db = DeviceBatch(shape, t)
             n_ws = self.L.orrb_workspace_size(self.r.ctx, shape, self.cfg)
             ws = torch.empty(n_ws, dtype=torch.uint8, device=self.r.device)
