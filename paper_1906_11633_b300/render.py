@@ -312,37 +312,45 @@ class CapturePipeline:
 
 
 class ShadeFn(torch.autograd.Function):
-    """rgb_linear = shade(material, light, exposure_ev[, emission]) at fixed visibility.
+    """rgb = shade(material, light, exposure_ev[, emission][, grading]) at fixed visibility.
 
-    Forward renders the batch with the given parameter tensors (visibility does
-    not depend on them); backward runs the hand-written shading adjoint kernel
-    and returns d material [S,32,5] (albedo rgb and specular; shininess gets 0),
-    d light [S,4,4], d exposure [S] and, when an emission tensor [S,32] is
-    given, d emission.
+    Forward renders the batch with the given parameter tensors (visibility does not depend on
+    them) and returns rgb_linear, or with a grading tensor [S,8] the graded colour before
+    quantisation (rgb_graded); backward runs the hand-written shading adjoint kernel and returns
+    d material [S,32,5] (albedo rgb and specular; shininess gets 0), d light [S,4,4], d exposure
+    [S], d emission [S,32] when an emission tensor is given, and d grading [S,8] (hue,
+    saturation, contrast, brightness, temperature, tint, grain amplitude; the seed gets 0) when a
+    grading tensor is given.
     """
 
     @staticmethod
-    def forward(ctx, material, light, exposure_ev, renderer: Renderer, db: DeviceBatch, emission=None):
+    def forward(ctx, material, light, exposure_ev, renderer: Renderer, db: DeviceBatch, emission=None, grading=None):
         kw = dict(material=material.detach().contiguous(), light=light.detach().contiguous(),
                   exposure_ev=exposure_ev.detach().contiguous())
         if emission is not None:
             kw["emission"] = emission.detach().contiguous()
+        if grading is not None:
+            kw["grading"] = grading.detach().contiguous()
         dbp = db.with_params(**kw)
-        out = renderer.render(dbp, rgb_linear=True, gbuffer=True)
+        out = renderer.render(dbp, rgb_linear=True, gbuffer=True, rgb_graded=grading is not None)
         ctx.renderer = renderer
         ctx.db = dbp
         ctx.emission = emission is not None
+        ctx.graded = grading is not None
         ctx.save_for_backward(out["gbuffer"])
-        return out["rgb_linear"]
+        return out["rgb_graded"] if ctx.graded else out["rgb_linear"]
 
     @staticmethod
     def backward(ctx, g):
         (gbuffer,) = ctx.saved_tensors
-        grads = ctx.renderer.shade_backward(ctx.db, gbuffer, g.float(), emission=ctx.emission)
+        grads = ctx.renderer.shade_backward(ctx.db, gbuffer, g.float(), emission=ctx.emission, grading=ctx.graded)
         dm, dl, de = grads[:3]
+        rest = list(grads[3:])
+        dem = rest.pop(0) if ctx.emission else None
+        dg = rest.pop(0) if ctx.graded else None
         dmat = torch.zeros_like(ctx.db.tensors["material"])
         dmat[..., :4] = dm
-        return dmat, dl, de, None, None, (grads[3] if ctx.emission else None)
+        return dmat, dl, de, None, None, dem, dg
 
 
 def to_numpy(out) -> Dict[str, np.ndarray]:

@@ -180,3 +180,11 @@ def test_graded_loss_adjoint_matches_oracle(renderer, oracle):
     for j in range(7):   # per parameter kind, relative to that kind's largest gradient
         assert rel_err(got[:, j], rdg[:, j]).max() < REL, (j, got[:, j], rdg[:, j])
     assert np.all(got[:, 7] == 0.0)
+    # ShadeFn with a grading tensor returns rgb_graded and back-propagates into it
+    grading = db.tensors["grading"].clone().requires_grad_(True)
+    ev = db.tensors["exposure_ev"].clone().requires_grad_(True)
+    c = ShadeFn.apply(db.tensors["material"], db.tensors["light"], ev, renderer, db, None, grading)
+    assert torch.equal(c, out["rgb_graded"])
+    ((c.double() - torch.from_numpy(target).cuda()) ** 2).sum().backward()
+    assert torch.allclose(grading.grad, dg, rtol=1e-5, atol=1e-6)
+    assert torch.allclose(ev.grad, de, rtol=1e-5, atol=1e-6)
