@@ -232,6 +232,53 @@ class Server:
                 "max_concurrent_batches": conc, "memory_waits": waits}
 
 
+_TD: Dict[Any, Any] = {}
+
+
+def _torch_dtypes(torch) -> Dict[Any, Any]:
+    """numpy dtype -> torch dtype for the parameter arrays' types."""
+    if not _TD:
+        for n in ("int16", "int32", "int64", "uint8", "float32"):
+            _TD[np.dtype(n)] = getattr(torch, n)
+    return _TD
+
+
+class ParamStage:
+    """One batch's parameters in one pinned host buffer and one device buffer, each array at a
+    256-byte aligned offset, so a launch makes one host-to-device copy instead of page-locking and
+    copying every array.  A stage belongs to one in-flight batch from its launch to its release
+    (after the batch has finished on the GPU), so neither buffer is rewritten while a copy or the
+    render can still read it, and no launch waits for one."""
+
+    def __init__(self, torch, device, nbytes: int):
+        self.host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+        self.dev = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.host_np = self.host.numpy()
+
+    @property
+    def capacity(self) -> int:
+        return int(self.host.numel())
+
+    @staticmethod
+    def layout(arrs) -> tuple:
+        offs, o = {}, 0
+        for n, a in arrs.items():
+            offs[n] = o
+            o = (o + a.nbytes + 255) & ~255
+        return offs, max(o, 256)
+
+    def upload(self, torch, arrs, offs, nbytes: int, stream):
+        """Device tensors holding `arrs` (name -> contiguous numpy array), copied on `stream`."""
+        h = self.host_np
+        for n, a in arrs.items():
+            h[offs[n]:offs[n] + a.nbytes] = a.reshape(-1).view(np.uint8)
+        with torch.cuda.stream(stream):
+            self.dev[:nbytes].copy_(self.host[:nbytes], non_blocking=True)
+        # (flat views: the renderer reads only each array's address)
+        td = _torch_dtypes(torch)
+        return {n: self.dev[offs[n]:offs[n] + a.nbytes].view(td[a.dtype]) for n, a in arrs.items()}
+
+
 class GpuBackend:
     """Packs requests into one batch and renders it on a per-slot CUDA stream.
 
@@ -241,7 +288,7 @@ class GpuBackend:
     """
 
     def __init__(self, meshes, device: int = 0, n_streams: int = 2, cfg=None, readback: bool = False,
-                 reserve_bytes: int = 8 << 30):
+                 reserve_bytes: int = 8 << 30, n_stages: int = 4, stage_bytes: int = 8 << 20):
         import torch
 
         from . import lib as L
@@ -257,6 +304,11 @@ class GpuBackend:
              for t in (10000, 20000)]
         self.ws_b = (w[1] - w[0]) / 10000.0
         self.ws_a = w[0] - 10000 * self.ws_b
+        # parameter stages, allocated up front (one per batch in flight; 8 MB holds the parameters of
+        # about 2,000 samples with shadow cameras); a batch larger than a stage gets a bigger one
+        self.stage_bytes = stage_bytes
+        self._stage_lock = threading.Lock()
+        self._stages = [ParamStage(torch, self.r.device, stage_bytes) for _ in range(n_stages)]
 
     def memory_budget(self) -> int:
         free, _ = self.torch.cuda.mem_get_info(self.r.device)
@@ -277,29 +329,46 @@ class GpuBackend:
                    for b in batches if getattr(b, "shadow_view", None) is not None)
         return int(px * 14 + self.ws_a + self.ws_b * tris + sum(b.n_samples for b in batches) * 4096 + maps)
 
+    def _take_stage(self, nbytes: int) -> ParamStage:
+        with self._stage_lock:
+            for i, st in enumerate(self._stages):
+                if st.capacity >= nbytes:
+                    return self._stages.pop(i)
+        return ParamStage(self.torch, self.r.device, max(self.stage_bytes, 1 << int(nbytes - 1).bit_length()))
+
     def launch(self, batches, k: int):
         torch = self.torch
         from .render import DeviceBatch, host_arrays
         packed, shape = self._shape(batches)
         s = self.streams[k]
-        with torch.cuda.stream(s):
-            # (pinned copies come from torch's caching host allocator, which reuses its blocks once
-            # the copies that read them have run: a pool of per-stream staging buffers measured
-            # worse, its buffers waiting behind the stream's previous render)
-            arrs = host_arrays(packed)
-            t = {n: torch.from_numpy(a).pin_memory().to(self.r.device, non_blocking=True) for n, a in arrs.items()}
-            db = DeviceBatch(shape, t)
-            n_ws = self.L.orrb_workspace_size(self.r.ctx, shape, self.cfg)
-            ws = torch.empty(n_ws, dtype=torch.uint8, device=self.r.device)
-            out = self.r.render(db, cfg=self.cfg, stream=s, workspace=ws)
-            host = None
-            if self.readback:
-                host = {k2: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k2, v in out.items()}
-                for k2 in out:
-                    host[k2].copy_(out[k2], non_blocking=True)
-            ev = torch.cuda.Event()
-            ev.record(s)
-        return {"db": db, "ws": ws, "out": out, "host": host, "event": ev, "batches": batches, "stream": s}
+        arrs = host_arrays(packed)
+        offs, nbytes = ParamStage.layout(arrs)
+        stage = self._take_stage(nbytes)
+        try:
+            t = stage.upload(torch, arrs, offs, nbytes, s)
+            with torch.cuda.stream(s):
+                db = DeviceBatch(shape, t)
+                n_ws = self.L.orrb_workspace_size(self.r.ctx, shape, self.cfg)
+                ws = torch.empty(n_ws, dtype=torch.uint8, device=self.r.device)
+                out = self.r.render(db, cfg=self.cfg, stream=s, workspace=ws)
+                host = None
+                if self.readback:
+                    host = {k2: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k2, v in out.items()}
+                    for k2 in out:
+                        host[k2].copy_(out[k2], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(s)
+        except Exception:
+            # the copy may be queued: the stage is not reused before the stream has drained
+            s.synchronize()
+            self._put_stage(stage)
+            raise
+        return {"db": db, "ws": ws, "out": out, "host": host, "event": ev, "batches": batches, "stream": s,
+                "stage": stage}
+
+    def _put_stage(self, stage: ParamStage) -> None:
+        with self._stage_lock:
+            self._stages.append(stage)
 
     def wait(self, h):
         h["event"].synchronize()
@@ -317,9 +386,14 @@ class GpuBackend:
         return res
 
     def release(self, h):
-        # tensors return to torch's caching allocator once the stream's work is done
+        # tensors return to torch's caching allocator once the stream's work is done; the batch has
+        # finished (wait() synchronised on its event, or the launch failed and drained), so its
+        # stage is free again
         h["ws"].record_stream(h["stream"])
+        stage = h.get("stage")
         h.clear()
+        if stage is not None:
+            self._put_stage(stage)
 
 
 def run_poisson(server: Server, requests, batches, duration_s: float, warmup_s: float = 0.0):

@@ -90,10 +90,13 @@ def test_autotuner_result_is_valid_and_cached(renderer, tmp_path):
     _equal(renderer.render(db, cfg=cfg), renderer.render(db))
 
 
-def test_served_requests_equal_their_solo_render():
+@pytest.mark.parametrize("n_stages,stage_bytes", [(4, 8 << 20), (1, 16 << 10)])
+def test_served_requests_equal_their_solo_render(n_stages, stage_bytes):
+    """Requests batched together equal their solo renders; with one 16 KB parameter stage the
+    backend makes larger stages as batches need them, and every stage is back after the run."""
     from paper_1906_11633_b300.serve import GpuBackend, Server, ServeRequest
     meshes = sg.hand_meshes()
-    be = GpuBackend(meshes, n_streams=2)
+    be = GpuBackend(meshes, n_streams=2, n_stages=n_stages, stage_bytes=stage_bytes)
     srv = Server(be, n_streams=2, max_inflight=4, tick_ms=2.0)
     rng = np.random.default_rng(0)
     batches = []
@@ -110,6 +113,11 @@ def test_served_requests_equal_their_solo_render():
     srv.close()
     assert st["requests"] == 40
     assert st["batches"] < 40                       # requests were batched together
+    caps = sorted(stg.capacity for stg in be._stages)
+    if n_stages == 4:
+        assert caps == [8 << 20] * 4                # the preallocated stages sufficed and all came back
+    else:
+        assert len(caps) >= 2 and caps[-1] > 16 << 10
     solo = Renderer(meshes)
     for r in reqs[::7]:
         alone = solo.render(solo.upload(r.batch))

@@ -165,3 +165,31 @@ def test_close_waits_for_a_batch_that_is_still_launching():
     srv.close()
     assert req.event.is_set() and req.error is None and req.result == {"n": 2}
     assert be.active == 0
+
+
+def test_param_stage_packs_every_array_at_aligned_offsets():
+    """The serving backend's parameter stage: every array of a packed batch (optional arrays
+    included) lands at a 256-byte aligned offset of one buffer and comes back as a view holding
+    exactly its bytes (CPU tensors stand in for the pinned and device buffers)."""
+    import numpy as np
+    import torch
+    from paper_1906_11633_b300.render import host_arrays
+    from paper_1906_11633_b300.serve import ParamStage
+    meshes = sg.hand_meshes()
+    parts = [sg.hand_batch(3, np.arange(0, 2), res=64, meshes=meshes),
+             sg.benchmark_batch(4, np.arange(2, 5), res=64, n_cams=2, meshes=meshes, shadow_res=32)]
+    arrs = host_arrays(sg.concat_batches(parts))
+    assert {"grading", "light_spot", "emission", "shadow_view", "shadow_intr"} <= set(arrs)
+    offs, nbytes = ParamStage.layout(arrs)
+    assert all(o % 256 == 0 for o in offs.values()) and nbytes % 256 == 0
+    spans = sorted((offs[n], offs[n] + a.nbytes) for n, a in arrs.items())
+    assert all(e <= b for (_, e), (b, _) in zip(spans, spans[1:]))      # no overlap
+    stage = ParamStage.__new__(ParamStage)
+    stage.host = torch.zeros(nbytes + 512, dtype=torch.uint8)
+    stage.dev = torch.full((nbytes + 512,), 0xAB, dtype=torch.uint8)
+    stage.host_np = stage.host.numpy()
+    t = stage.upload(torch, arrs, offs, nbytes, None)
+    for n, a in arrs.items():
+        assert t[n].numel() == a.size and t[n].numpy().dtype == a.dtype, n
+        assert t[n].numpy().tobytes() == a.tobytes(), n
+    assert (stage.dev[nbytes:] == 0xAB).all()                            # nothing written past the layout
