@@ -1895,72 +1895,6 @@ __global__ void __launch_bounds__(512, 2) plain_raster_kernel(Params p) {
   raster_phase<kF>(p, sh, sc, sp, L, blockIdx.y, gridDim.y);
 }
 
-// The neighbourhood table of the shadow maps (after the shadow pass, before the camera launch):
-// per texel over its 3 x 3 neighbourhood (texels outside the map count as empty), the least
-// occupied depth (depth > 0; +inf if none), the largest (0 if none) and the number of occupied
-// texels c.  A point with depth-less-bias zb is then unshadowed by every tap when zb <= the
-// least, and shadowed by exactly the c occupied taps when zb > the largest (the empty ones
-// light); only the others count taps.  The two depths are stored as binary16 rounded outward
-// (the least down, the largest up), which keeps both shortcuts exact: what they cannot settle
-// takes the nine taps.
-// Each thread owns one column x of one map and walks down kNbRows rows of it, keeping the
-// 3-texel summaries (least and largest occupied depth, occupied count) of the rows above, at
-// and below in registers: three loads per texel.  A block covers 128 columns and kNbRows rows
-// of one map (blocks stride over (map, column block, row block) triples).
-constexpr int kNbRows = 32;
-
-struct RowTriple {
-  float lo, hi;
-  int n;  // occupied texels among the three
-};
-
-__device__ __forceinline__ RowTriple row_triple(const float* map, int R, int x, int y) {
-  RowTriple t{__int_as_float(0x7f800000), 0.0f, 0};
-  if (y < 0 || y >= R) return t;
-  const float* row = map + (size_t)y * R;
-#pragma unroll
-  for (int a = -1; a <= 1; a++) {
-    const int xx = x + a;
-    if (xx < 0 || xx >= R) continue;
-    const float d = __ldg(row + xx);
-    if (d > 0.0f) {
-      t.lo = fminf(t.lo, d);
-      t.hi = fmaxf(t.hi, d);
-      t.n++;
-    }
-  }
-  return t;
-}
-
-__global__ void __launch_bounds__(128) shadow_neighbourhood_kernel(Params p) {
-  const int R = p.shadow_res, F = p.shadow_faces, n_maps = p.n_samples * kMaxLights * F;
-  const int col_blocks = (R + 127) / 128, row_blocks = (R + kNbRows - 1) / kNbRows;
-  const long long per_map = (long long)col_blocks * row_blocks;
-  for (long long w = blockIdx.x; w < (long long)n_maps * per_map; w += gridDim.x) {
-    const int m = int(w / per_map), wr = int(w % per_map);
-    const int x = (wr % col_blocks) * 128 + int(threadIdx.x);
-    const int y0 = (wr / col_blocks) * kNbRows, y1 = min(R, y0 + kNbRows);
-    const int sl = m / F;  // sample * 4 + light
-    if (sl % kMaxLights >= p.light_meta[(sl / kMaxLights) * 2] || p.shadow_intr[(size_t)m * 7] == 0.0f)
-      continue;  // no such light, or a face that casts none: no map
-    if (x >= R) continue;
-    const float* map = p.shadow_map + (size_t)m * R * R;
-    uint32_t* out = p.shadow_nb + (size_t)m * R * R + x;
-    uint8_t* cnt = p.shadow_cnt + (size_t)m * R * R + x;
-    RowTriple a = row_triple(map, R, x, y0 - 1), b = row_triple(map, R, x, y0);
-#pragma unroll 4
-    for (int y = y0; y < y1; y++) {
-      const RowTriple c = row_triple(map, R, x, y + 1);
-      const float lo = fminf(fminf(a.lo, b.lo), c.lo), hi = fmaxf(fmaxf(a.hi, b.hi), c.hi);
-      out[(size_t)y * R] = unsigned(__half_as_ushort(__float2half_rd(lo))) |
-                           (unsigned(__half_as_ushort(__float2half_ru(hi))) << 16);
-      cnt[(size_t)y * R] = uint8_t(a.n + b.n + c.n);
-      a = b;
-      b = c;
-    }
-  }
-}
-
 // Scratch of orrb_render_batch_noalloc: a file-scope device array, so that
 // entry point never allocates.  Host code must not pass the symbol itself to
 // a kernel (on the host it names a stand-in, not device memory); it passes
@@ -1985,19 +1919,6 @@ int noalloc_scratch(int device, void** ptr, size_t* bytes) {
   }
   *ptr = cache[device];
   *bytes = ORRB_NOALLOC_SCRATCH_BYTES;
-  return 0;
-}
-
-int launch_shadow_neighbourhoods(const Params& p, void* stream, char* err, size_t errlen) {
-  const int n_maps = p.n_samples * kMaxLights * p.shadow_faces;
-  const long long work = (long long)n_maps * ((p.shadow_res + 127) / 128) * ((p.shadow_res + kNbRows - 1) / kNbRows);
-  shadow_neighbourhood_kernel<<<unsigned(work < (1 << 30) ? work : (1 << 30)), 128, 0,
-                                static_cast<cudaStream_t>(stream)>>>(p);
-  const cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) {
-    snprintf(err, errlen, "shadow neighbourhood launch failed: %s", cudaGetErrorString(e));
-    return 1;
-  }
   return 0;
 }
 
