@@ -54,6 +54,11 @@ def set_samples(n: int) -> None:
     CONFIG = dict(CONFIG, workload=CONFIG["workload"].replace("256 samples", f"{n} samples"), global_batch=n)
 
 
+def parallelism(world: int) -> str:
+    """How the job splits over its ranks (the same words in both arms' config)."""
+    return f"replicas x{world}" if world > 1 else "single GPU"
+
+
 def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
@@ -296,7 +301,8 @@ def run_reference(args, world, rank):
     value = n / (ms / 1e3)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": CONFIG,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(CONFIG, parallelism=parallelism(args.gpus)),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"{n} samples ({n * N_CAMS} images) per step of the same workload"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -443,9 +449,9 @@ def run_ours(args, world, rank, local):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded procedural hand scene)",
-            "config": dict(CONFIG, parallelism=f"replicas x{world}" if world > 1 else "single GPU",
-                           tile=[min(args.tile_w or L.DEFAULT_TILE_W, RES), args.tile_h or L.DEFAULT_TILE_H],
-                           threads=args.threads or L.DEFAULT_THREADS),
+            "config": dict(CONFIG, parallelism=parallelism(world)),
+            "launch": {"tile": [min(args.tile_w or L.DEFAULT_TILE_W, RES), args.tile_h or L.DEFAULT_TILE_H],
+                       "threads": args.threads or L.DEFAULT_THREADS},
             "plain": {"value": plain_value, "ms_per_step": plain_ms, "steps": psteps,
                       "launches_per_step": 3 * N_SAMPLES},
             "fused_over_plain": value / plain_value,
