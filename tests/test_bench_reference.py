@@ -20,6 +20,6 @@ def test_reference_arm_prints_one_contract_line():
     sys.path.insert(0, ROOT)
     import bench
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
-    assert d["config"] == bench.CONFIG and d["higher_is_better"] is True and d["steps"] == 1
+    assert d["config"] == dict(bench.CONFIG, parallelism=bench.parallelism(1)) and d["higher_is_better"] is True and d["steps"] == 1
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
