@@ -53,13 +53,14 @@ _BATCH_ARRAYS = ("inst_offset", "inst_mesh", "inst_pose", "inst_seg", "inst_mat_
 
 class _Batch(C.Structure):
     _fields_ = [("n_samples", C.c_int32)] + [(n, C.c_void_p) for n in _BATCH_ARRAYS] + [("shadow_res", C.c_int32),
-                                                                                        ("shadow_faces", C.c_int32)]
+                                                                                        ("shadow_faces", C.c_int32),
+                                                                                        ("post", C.c_void_p)]
 
 
 class _Outputs(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in (
         "rgb", "depth", "normal", "seg", "rgb_linear", "gb_pos", "gb_nrm", "gb_mat", "prim", "depth2", "counters",
-        "tracker")] + [("tracker_stride", C.c_int32), ("flops", C.c_void_p)]
+        "tracker")] + [("tracker_stride", C.c_int32), ("flops", C.c_void_p), ("rgb_final", C.c_void_p)]
 
 
 def lib():
@@ -73,6 +74,8 @@ def lib():
                                            C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
             L.orc_raster_fixed.restype = C.c_int
             L.orc_f32_to_f16.argtypes = [C.c_float]
+            L.orc_post_image.argtypes = [C.c_int32, C.c_int32] + [C.c_void_p] * 5
+            L.orc_post_image.restype = C.c_int
             L.orc_f32_to_f16.restype = C.c_uint16
             L.orc_shade_f64.argtypes = [C.POINTER(_Batch), C.c_int32, C.c_int32] + [C.c_void_p] * 9
             L.orc_shade_f64.restype = None
@@ -129,8 +132,9 @@ class _Pinned:
             shadow_view=_opt(batch, "shadow_view"), shadow_intr=_opt(batch, "shadow_intr"), shadow_map=None)
         self.shadow_res = int(getattr(batch, "shadow_res", 0) or 0)
         self.shadow_faces = int(getattr(batch, "shadow_faces", 1) or 1)
+        self.post = _opt(batch, "post")
         self.batch = _Batch(batch.n_samples, *[_p(self.arrs[n]) for n in _BATCH_ARRAYS], self.shadow_res,
-                            self.shadow_faces)
+                            self.shadow_faces, _p(self.post))
 
     def set_shadow_maps(self, maps):
         """Point the lookups of step 16 at `maps` ([S, 4, F, R, R] float32, kept alive here)."""
@@ -193,7 +197,8 @@ def render(batch, threads: int | None = None, gbuffer: bool = False, debug: bool
         pin.set_shadow_maps(maps)
     N = batch.total_pixels
     out = dict(rgb=np.zeros((N, 3), np.uint8), depth=np.zeros(N, np.float32), normal=np.zeros((N, 3), np.uint16),
-               seg=np.zeros(N, np.uint8), rgb_linear=np.zeros((N, 3), np.float32))
+               seg=np.zeros(N, np.uint8), rgb_linear=np.zeros((N, 3), np.float32),
+               rgb_final=np.zeros((N, 3), np.float32))
     if gbuffer:
         out.update(gb_pos=np.zeros((N, 3), np.float32), gb_nrm=np.zeros((N, 3), np.float32),
                    gb_mat=np.zeros(N, np.int32))
@@ -209,8 +214,8 @@ def render(batch, threads: int | None = None, gbuffer: bool = False, debug: bool
     nflops = np.zeros((len(chunks), 1), np.int64)
 
     def run(i):
-        o = _Outputs(*[_p(out.get(n)) for n, _ in _Outputs._fields_[:-4]], _p(counters[i]), _p(out.get("tracker")),
-                     stride, _p(nflops[i]) if flops else None)
+        o = _Outputs(*[_p(out.get(n)) for n, _ in _Outputs._fields_[:-5]], _p(counters[i]), _p(out.get("tracker")),
+                     stride, _p(nflops[i]) if flops else None, _p(out["rgb_final"]))
         rc = L.orc_render(C.byref(pin.meshes), C.byref(pin.batch), chunks[i][0], chunks[i][1], C.byref(o))
         if rc != 0:
             raise MemoryError("oracle: allocation failed")
@@ -227,6 +232,22 @@ def render(batch, threads: int | None = None, gbuffer: bool = False, debug: bool
     if maps is not None:
         out["shadow_map"] = maps
     return out
+
+
+def post_image(W: int, H: int, intr, q, col, depth, normal):
+    """Step 17 on one W x H image: returns the post-processed colour [W*H, 3] float32 of the linear
+    colour `col` [W*H, 3], given the depth channel [W*H], the normal channel's binary16 bits
+    [W*H, 3], the camera's (fx, fy, cx, cy, near, type) and q = (AO intensity, bloom intensity,
+    bloom radius in pixels, 0)."""
+    c = _c(col, np.float32).reshape(-1, 3).copy()
+    d = _c(depth, np.float32).reshape(-1)
+    n = _c(normal, np.uint16).reshape(-1, 3)
+    i = _c(intr, np.float32).reshape(6)
+    qq = _c(q, np.float32).reshape(4)
+    assert len(c) == len(d) == len(n) == W * H
+    if lib().orc_post_image(W, H, _p(i), _p(qq), _p(c), _p(d), _p(n)) != 0:
+        raise MemoryError("oracle: allocation failed")
+    return c
 
 
 def raster_fixed(W: int, H: int, X, Y, iw, ortho: bool = False):

@@ -97,6 +97,27 @@
  *      and Cook 1987); E_l is multiplied by (9 - k) / 9.  The G-buffer's material word
  *        carries k of light l in bits 8 + 4l .. 11 + 4l (the adjoint holds it
  *        fixed: visibility does not depend on the shading parameters).
+ *  17  optional post-processing of a sample's images (the rest of the
+ *      post-processing randomizer, Sec. 4.3.1: ambient-occlusion intensity a,
+ *      bloom intensity beta and bloom radius sigma in pixels, per sample),
+ *      applied to the linear colour c of every pixel (step 10, or the
+ *      background) before step 13's grading and step 11's quantisation; it
+ *      reads only the image's depth channel and its binary16 normals (n, as
+ *      decoded), and is computed here in fp64, rounded to fp32 once at the end:
+ *        ambient occlusion: for a pixel with surface, P its position as in
+ *          step 9 from its depth, and each of eight offsets (dx, dy) =
+ *          (2, 1), (-1, 3), (-4, -1), (1, -4), (5, 2), (-2, 5), (-5, -3), (3, -6)
+ *          whose pixel lies in the image and has a surface, v = P' - P, L = |v|:
+ *          o = max(0, (n . v) / L - 0.1) / (1 + L^2 / 0.05^2) (0 where L = 0);
+ *          O = (sum of o) / 8 over all eight; c = c * max(0, 1 - a O).
+ *          Pixels without surface keep c.
+ *        bloom (where beta != 0 and sigma > 0): the bright part
+ *          b = max(c - 1, 0) per channel is blurred by the Gaussian
+ *          w_i = exp(-i^2 / (2 sigma^2)) / sum_j exp(-j^2 / (2 sigma^2)),
+ *          |i|, |j| <= R = min(ceil(3 sigma), 16), first along rows, then along
+ *          columns, pixel indices clamped to the image:
+ *          B(x, y) = sum_j w_j sum_i w_i b(clamp(x + i), clamp(y + j));
+ *          c = c + beta B.
  */
 #include "orrb_oracle.h"
 
@@ -348,6 +369,109 @@ static void grade(const float* g, int32_t cam_local, int64_t pixel, float c[3]) 
 static uint8_t quantise(float v) {
   float c = v < 0.0f ? 0.0f : (v > 1.0f ? 1.0f : v);
   return (uint8_t)floorf(c * 255.0f + 0.5f);
+}
+
+/* ------------------------------------------------------------------ */
+/* step 17: ambient occlusion and bloom, fp64                          */
+/* ------------------------------------------------------------------ */
+/* binary16 bits -> value (IEEE 754: sign, 5 exponent bits biased by 15, 10 fraction bits;
+   exponent 0 holds the subnormals m * 2^-24) */
+static double f16_value(uint16_t h) {
+  const int sign = h >> 15, e = (h >> 10) & 31, m = h & 1023;
+  double v;
+  if (e == 0) v = ldexp((double)m, -24);
+  else if (e == 31) v = m ? NAN : INFINITY;
+  else v = ldexp(1024.0 + (double)m, e - 25);
+  return sign ? -v : v;
+}
+
+static const int POST_DX[8] = {2, -1, -4, 1, 5, -2, -5, 3};
+static const int POST_DY[8] = {1, 3, -1, -4, 2, 5, -3, -6};
+
+int orc_post_image(int32_t W, int32_t H, const float* in, const float* q, float* col, const float* depth,
+                   const uint16_t* normal) {
+  const double a = q[0], beta = q[1], sigma = q[2];
+  const int64_t N = (int64_t)W * H;
+  double* c = (double*)malloc(sizeof(double) * 3 * (size_t)(N > 0 ? N : 1));
+  if (!c) return -1;
+  for (int64_t i = 0; i < 3 * N; i++) c[i] = col[i];
+  if (a != 0.0) {
+    /* positions as in step 9, from the depth */
+    const double fx = in[0], fy = in[1], cx = in[2], cy = in[3];
+    const int ortho = in[5] != 0.0f;
+    for (int32_t y = 0; y < H; y++)
+      for (int32_t x = 0; x < W; x++) {
+        const int64_t i = (int64_t)y * W + x;
+        if (!(depth[i] > 0.0f)) continue;
+        double P[3], n[3];
+        const double ux = ((x + 0.5) - cx) / fx, uy = -(((y + 0.5) - cy) / fy), d = depth[i];
+        P[0] = ortho ? ux : d * ux;
+        P[1] = ortho ? uy : d * uy;
+        P[2] = -d;
+        for (int k = 0; k < 3; k++) n[k] = f16_value(normal[i * 3 + k]);
+        double O = 0.0;
+        for (int k = 0; k < 8; k++) {
+          const int32_t qx = x + POST_DX[k], qy = y + POST_DY[k];
+          if (qx < 0 || qy < 0 || qx >= W || qy >= H) continue;
+          const int64_t j = (int64_t)qy * W + qx;
+          if (!(depth[j] > 0.0f)) continue;
+          const double uxq = ((qx + 0.5) - cx) / fx, uyq = -(((qy + 0.5) - cy) / fy), dq = depth[j];
+          const double v[3] = {(ortho ? uxq : dq * uxq) - P[0], (ortho ? uyq : dq * uyq) - P[1], -dq - P[2]};
+          const double L2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+          if (!(L2 > 0.0)) continue;
+          const double L = sqrt(L2);
+          const double cosine = (n[0] * v[0] + n[1] * v[1] + n[2] * v[2]) / L - 0.1;
+          if (cosine > 0.0) O += cosine / (1.0 + L2 / (0.05 * 0.05));
+        }
+        O /= 8.0;
+        double f = 1.0 - a * O;
+        if (f < 0.0) f = 0.0;
+        for (int k = 0; k < 3; k++) c[i * 3 + k] *= f;
+      }
+  }
+  if (beta != 0.0 && sigma > 0.0) {
+    int R = (int)ceil(3.0 * sigma);
+    if (R > 16) R = 16;
+    double w[33], sw = 0.0;
+    for (int i = -R; i <= R; i++) {
+      w[i + 16] = exp(-(double)(i * i) / (2.0 * sigma * sigma));
+      sw += w[i + 16];
+    }
+    for (int i = -R; i <= R; i++) w[i + 16] /= sw;
+    double* h = (double*)malloc(sizeof(double) * 3 * (size_t)N);
+    if (!h) {
+      free(c);
+      return -1;
+    }
+    for (int32_t y = 0; y < H; y++) /* along rows */
+      for (int32_t x = 0; x < W; x++)
+        for (int k = 0; k < 3; k++) {
+          double acc = 0.0;
+          for (int i = -R; i <= R; i++) {
+            int32_t xx = x + i;
+            xx = xx < 0 ? 0 : (xx >= W ? W - 1 : xx);
+            const double v = c[((int64_t)y * W + xx) * 3 + k] - 1.0;
+            acc += w[i + 16] * (v > 0.0 ? v : 0.0);
+          }
+          h[((int64_t)y * W + x) * 3 + k] = acc;
+        }
+    for (int32_t y = 0; y < H; y++) /* then along columns, added to the colour */
+      for (int32_t x = 0; x < W; x++)
+        for (int k = 0; k < 3; k++) {
+          double acc = 0.0;
+          for (int j = -R; j <= R; j++) {
+            int32_t yy = y + j;
+            yy = yy < 0 ? 0 : (yy >= H ? H - 1 : yy);
+            acc += w[j + 16] * h[((int64_t)yy * W + x) * 3 + k];
+          }
+          col[((int64_t)y * W + x) * 3 + k] = (float)(c[((int64_t)y * W + x) * 3 + k] + beta * acc);
+        }
+    free(h);
+  } else {
+    for (int64_t i = 0; i < 3 * N; i++) col[i] = (float)c[i];
+  }
+  free(c);
+  return 0;
 }
 
 /* ------------------------------------------------------------------ */
@@ -681,6 +805,26 @@ static int render_image(const orc_meshes* me, const orc_batch* b, int32_t c, con
      the grading factors and the reciprocal focal lengths (2). */
   int64_t ops = 2 + orc_shade_image_ops(b, s);
   const float* bg = b->background + (int64_t)s * 3;
+  /* step 17: with post-processing the image's linear colour, depth and normals are kept until
+     every pixel is shaded, then post-processed, graded and quantised */
+  const float* post = b->post ? b->post + (int64_t)s * 4 : NULL;
+  float* pcol = NULL;
+  float* pdep = NULL;
+  uint16_t* pnrm = NULL;
+  if (post) {
+    const size_t np = (size_t)W * (size_t)H + 1;
+    pcol = (float*)malloc(sizeof(float) * 3 * np);
+    pdep = (float*)malloc(sizeof(float) * np);
+    pnrm = (uint16_t*)malloc(sizeof(uint16_t) * 3 * np);
+    if (!pcol || !pdep || !pnrm) {
+      free(pcol);
+      free(pdep);
+      free(pnrm);
+      free(Msh);
+      free(cast);
+      return -1;
+    }
+  }
   for (int32_t y = 0; y < H; y++) {
     for (int32_t x = 0; x < W; x++) {
       int64_t i = (int64_t)y * W + x;
@@ -689,10 +833,19 @@ static int render_image(const orc_meshes* me, const orc_batch* b, int32_t c, con
       if (out->prim) out->prim[o] = p->key;
       if (out->depth2) out->depth2[o] = p->depth2;
       if (p->key < 0) {
-        if (out->rgb) {
+        if (post) {
+          for (int k = 0; k < 3; k++) {
+            pcol[i * 3 + k] = bg[k];
+            pnrm[i * 3 + k] = 0;
+          }
+          pdep[i] = 0.0f;
+        } else if (out->rgb || out->rgb_final) {
           float gc[3] = {bg[0], bg[1], bg[2]};
           if (b->grading) grade(b->grading + (int64_t)s * 8, c - b->cam_offset[s], i, gc);
-          for (int k = 0; k < 3; k++) out->rgb[o * 3 + k] = quantise(gc[k]);
+          for (int k = 0; k < 3; k++) {
+            if (out->rgb) out->rgb[o * 3 + k] = quantise(gc[k]);
+            if (out->rgb_final) out->rgb_final[o * 3 + k] = gc[k];
+          }
         }
         if (b->grading) ops += ORC_GRADE_OPS + 3 * 6; /* the grading and the three quantisations */
         if (out->rgb_linear)
@@ -760,10 +913,19 @@ static int render_image(const orc_meshes* me, const orc_batch* b, int32_t c, con
       }
       float rgb[3];
       shade_f32(b, s, V, ortho, P, n, p->mat, vis, rgb, &ops);
-      if (out->rgb) {
+      if (post) {
+        for (int k = 0; k < 3; k++) {
+          pcol[i * 3 + k] = rgb[k];
+          pnrm[i * 3 + k] = orc_f32_to_f16(n[k]);
+        }
+        pdep[i] = p->depth;
+      } else if (out->rgb || out->rgb_final) {
         float gc[3] = {rgb[0], rgb[1], rgb[2]};
         if (b->grading) grade(b->grading + (int64_t)s * 8, c - b->cam_offset[s], i, gc);
-        for (int k = 0; k < 3; k++) out->rgb[o * 3 + k] = quantise(gc[k]);
+        for (int k = 0; k < 3; k++) {
+          if (out->rgb) out->rgb[o * 3 + k] = quantise(gc[k]);
+          if (out->rgb_final) out->rgb_final[o * 3 + k] = gc[k];
+        }
       }
       /* the grading, three quantisations (clamp 2, scale, offset, floor, conversion) and three
          binary16 conversions of the normal */
@@ -781,10 +943,25 @@ static int render_image(const orc_meshes* me, const orc_batch* b, int32_t c, con
       if (out->gb_mat) out->gb_mat[o] = word;
     }
   }
+  int rc = 0;
+  if (post) {
+    rc = orc_post_image(W, H, in, post, pcol, pdep, pnrm);
+    for (int64_t i = 0; rc == 0 && i < (int64_t)W * H; i++) {
+      float gc[3] = {pcol[i * 3 + 0], pcol[i * 3 + 1], pcol[i * 3 + 2]};
+      if (b->grading) grade(b->grading + (int64_t)s * 8, c - b->cam_offset[s], i, gc);
+      for (int k = 0; k < 3; k++) {
+        if (out->rgb) out->rgb[(base + i) * 3 + k] = quantise(gc[k]);
+        if (out->rgb_final) out->rgb_final[(base + i) * 3 + k] = gc[k];
+      }
+    }
+    free(pcol);
+    free(pdep);
+    free(pnrm);
+  }
   free(Msh);
   free(cast);
   if (out->flops) out->flops[0] += ops;
-  return 0;
+  return rc;
 }
 
 int orc_render_shadow_maps(const orc_meshes* m, const orc_batch* b, int32_t s_begin, int32_t s_end, float* maps) {

@@ -24,6 +24,7 @@
  *   light_spot     [S][4][5]      spot axis xyz (unit, world), cos outer, cos inner
  *   material       [S][32][5]     albedo rgb, specular k_s, shininess alpha
  *   emission       [S][32]        emission e (emitted colour e * albedo)
+ *   post           [S][4]         step 17: AO intensity, bloom intensity, bloom radius (px), 0
  *   outputs        flat over pixels; image c starts at pixel img_offset[c]
  */
 #ifndef ORRB_ORACLE_H
@@ -76,6 +77,7 @@ typedef struct {
   const float* shadow_map;      /* [S][4][F][R][R] maps of step 15, read by step 16 (or NULL) */
   int32_t shadow_res;           /* R, 0 for no shadows */
   int32_t shadow_faces;         /* F, shadow cameras per light (1 spot, 6 cube); 0 is read as 1 */
+  const float* post;            /* [S][4] post-processing of step 17, or NULL for none */
 } orc_batch;
 
 typedef struct {                /* every pointer may be NULL */
@@ -93,6 +95,7 @@ typedef struct {                /* every pointer may be NULL */
   int32_t* tracker;             /* [C][tracker_stride][8] per (camera, instance of its sample), step 14 */
   int32_t tracker_stride;
   int64_t* flops;               /* [1] fp32 operations of steps 9-13 and 16 (accumulated; see render_image) */
+  float* rgb_final;             /* [N][3] the colour step 11 quantises: after steps 17 and 13 */
 } orc_outputs;
 
 /* Render images [cam_begin, cam_end).  Returns 0, or -1 on allocation failure. */
@@ -112,6 +115,13 @@ int orc_raster_fixed(int32_t W, int32_t H, int32_t n, const int32_t* X, const in
                      const float* iw, int32_t ortho, int64_t* prim_out, float* depth_out,
                      int32_t* count_out);
 
+/* Step 17 on one W x H image (the post-processing randomizer's ambient occlusion and bloom,
+ * Sec. 4.3.1): col [W*H][3] the linear colour, replaced by the post-processed colour; depth [W*H]
+ * the depth channel (0: no surface); normal [W*H][3] the normal channel's binary16 bits; in the
+ * camera's fx, fy, cx, cy, near, type; q the sample's AO intensity, bloom intensity, bloom radius
+ * (px) and a 0.  Returns 0, or -1 on allocation failure. */
+int orc_post_image(int32_t W, int32_t H, const float* in, const float* q, float* col, const float* depth,
+                   const uint16_t* normal);
 /* float -> binary16 bits, round to nearest even (the normal channel's encoding). */
 uint16_t orc_f32_to_f16(float f);
 

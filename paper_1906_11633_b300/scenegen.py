@@ -59,6 +59,7 @@ STREAM_FIXED_HUE = 12
 STREAM_LIGHT_SETUP = 13
 STREAM_LIGHT_LEVELS = 14
 STREAM_ORBIT = 15
+STREAM_POST_EFFECTS = 16
 
 # --------------------------------------------------------------------------
 # Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
@@ -248,6 +249,9 @@ class Batch:
     light_spot: Optional[np.ndarray] = None
     # [B, 32] float32 material emission e (the emitted colour is e * albedo), or None for none
     emission: Optional[np.ndarray] = None
+    # [B, 4] float32 post-processing: ambient-occlusion intensity, bloom intensity, bloom radius
+    # (pixels), 0; or None for none
+    post: Optional[np.ndarray] = None
     # shadows: per light shadow_faces shadow cameras (one for a spot light, six cube faces for a
     # point light, one orthographic for a directional light), views [B, 4, F, 3, 4]
     # (camera-from-world) and intrinsics [B, 4, F, 7] (fx, fy, cx, cy, near, depth bias, type:
@@ -324,6 +328,7 @@ def concat_batches(batches: Sequence[Batch]) -> Batch:
         grading=_concat_opt(batches, "grading", identity_grading),
         light_spot=_concat_opt(batches, "light_spot", lambda n: np.zeros((n, MAX_LIGHTS, 5), np.float32)),
         emission=_concat_opt(batches, "emission", lambda n: np.zeros((n, MAX_MATERIALS), np.float32)),
+        post=_concat_opt(batches, "post", lambda n: np.zeros((n, 4), np.float32)),
         shadow_view=_concat_opt(batches, "shadow_view",
                                 lambda n: np.zeros((n, MAX_LIGHTS, _shadow_kind(batches)[1], 3, 4), np.float32)),
         shadow_intr=_concat_opt(batches, "shadow_intr",
@@ -370,6 +375,7 @@ def select_samples(batch: Batch, idx: Sequence[int]) -> Batch:
             grading=batch.grading[s:s + 1] if batch.grading is not None else None,
             light_spot=batch.light_spot[s:s + 1] if batch.light_spot is not None else None,
             emission=batch.emission[s:s + 1] if batch.emission is not None else None,
+            post=batch.post[s:s + 1] if batch.post is not None else None,
             shadow_view=batch.shadow_view[s:s + 1] if batch.shadow_view is not None else None,
             shadow_intr=batch.shadow_intr[s:s + 1] if batch.shadow_intr is not None else None,
             shadow_res=batch.shadow_res,
@@ -643,6 +649,18 @@ def grading_params(seed: int, sample_ids) -> np.ndarray:
     return g
 
 
+def post_params(seed: int, sample_ids) -> np.ndarray:
+    """Per-sample ambient occlusion and bloom (the rest of the post-processing randomizer, Sec.
+    4.3.1): AO intensity U[0, 1.5], bloom intensity U[0, 1], bloom radius U[1, 6] pixels."""
+    ids = np.asarray(sample_ids, dtype=np.int64).reshape(-1)
+    u = uniform(seed, STREAM_POST_EFFECTS, ids, 3)
+    q = np.zeros((len(ids), 4), np.float32)
+    q[:, 0] = 1.5 * u[:, 0]
+    q[:, 1] = u[:, 1]
+    q[:, 2] = 1.0 + 5.0 * u[:, 2]
+    return q
+
+
 def hand_batch(seed: int, sample_ids, res: int = 200, n_cams: int = 3, meshes=None, res_per_sample=None,
                cams_per_sample=None, grading: bool = False, shadow_res: int = 0) -> Batch:
     """Hand-like scenes: table, block, 24 capsule links posed by hinge angles U(+-60 deg); with
@@ -859,12 +877,12 @@ N_SPOTS = 3
 
 
 def benchmark_batch(seed: int, sample_ids, res: int = 200, n_cams: int = 3, orbit: bool = False,
-                    grading: bool = True, meshes=None, shadow_res: int = 0) -> Batch:
+                    grading: bool = True, meshes=None, shadow_res: int = 0, post: bool = False) -> Batch:
     """The hand scene configured like the paper's benchmark (Sec. 5): three spot lights placed by
     LightSetup about the block with LightRandomizer levels and cones, FixedHue materials (with
     emission) for the block's faces, the material randomizer for the hand and the table, camera
     jitter (or orbit), post-processing grading; with `shadow_res` > 0 every spot light casts
-    shadows from a shadow map of that side."""
+    shadows from a shadow map of that side; with `post` ambient occlusion and bloom too."""
     b = hand_batch(seed, sample_ids, res=res, n_cams=n_cams, meshes=meshes, grading=grading)
     ids = b.sample_ids
     B = len(ids)
@@ -886,6 +904,8 @@ def benchmark_batch(seed: int, sample_ids, res: int = 200, n_cams: int = 3, orbi
     kw = dict(light=light.astype(np.float32), light_meta=meta.astype(np.int32),
               light_spot=spot.astype(np.float32), material=mat.astype(np.float32),
               emission=emission.astype(np.float32))
+    if post:
+        kw.update(post=post_params(seed, ids))
     if orbit:
         views, owner = orbit_views(seed, ids, n_cams, BLOCK_CENTRE)
         kw.update(cam_view=views.astype(np.float32), cam_sample=owner)

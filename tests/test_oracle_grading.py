@@ -46,7 +46,10 @@ def test_identity_changes_nothing(orc, batch):
     plain = orc.render(batch)
     got = orc.render(batch.with_params(grading=sg.identity_grading(batch.n_samples)))
     for k in plain:
-        np.testing.assert_array_equal(got[k], plain[k], err_msg=k)
+        if k == "rgb_final":  # (the identity's fp32 steps, e.g. Y + 1 * (c - Y), may move the last bit)
+            np.testing.assert_allclose(got[k], plain[k], rtol=0, atol=1e-6, err_msg=k)
+        else:
+            np.testing.assert_array_equal(got[k], plain[k], err_msg=k)
 
 
 def test_hue_third_turn_permutes_channels(orc, batch):
