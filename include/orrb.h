@@ -138,6 +138,8 @@ typedef struct {
   int64_t total_pixels;         /* sum of width*height over cameras */
   int32_t shadow_res;           /* side of the square shadow maps, <= ORRB_MAX_RESOLUTION; 0: no shadows */
   int32_t shadow_faces;         /* F, shadow cameras per light in [1, 6] (1: spot, 6: cube map); 0 means 1 */
+  int32_t post_effects;         /* 1: the batch may carry post-processing parameters (batch.post), and
+                                   the workspace holds the post pass's images (46 B per pixel); 0: none */
 } orrb_batch_shape;
 
 /* Per-sample state and randomization parameters; all device pointers. */
@@ -208,6 +210,22 @@ typedef struct {
                                     0, 1}, shadow it when inside the map with depth d > 0 and (z -
                                     bias) > d (percentage-closer filtering), and the light's E is
                                     multiplied by (9 - k) / 9. */
+  const float* post;             /* [n_samples][4] or NULL: ambient occlusion and bloom of the rgb output
+                                    (the rest of the post-processing randomizer, Sec. 4.3.1): AO
+                                    intensity a, bloom intensity beta, bloom radius sigma (pixels), 0.
+                                    Needs shape.post_effects = 1.  Applied to the linear colour of every
+                                    pixel after the shading and before the grading, in fp32, from the
+                                    image's depth channel and binary16 normals only.  AO: for a pixel
+                                    with surface, P its G-buffer position (as for the shadow lookup),
+                                    n its decoded normal, over the eight offsets (2, 1), (-1, 3),
+                                    (-4, -1), (1, -4), (5, 2), (-2, 5), (-5, -3), (3, -6) whose pixel is
+                                    in the image and has a surface, v = P' - P, L = |v|:
+                                    o = max(0, n.v / L - 0.1) / (1 + L^2 / 0.05^2); O = sum(o) / 8;
+                                    c *= max(0, 1 - a O).  Bloom (beta != 0, sigma > 0): the bright part
+                                    max(c - 1, 0) blurred by the normalised Gaussian of standard
+                                    deviation sigma truncated at min(ceil(3 sigma), 16) pixels, rows
+                                    then columns, indices clamped to the image, times beta, is added.
+                                    rgb_linear stays the shading's colour.  Not differentiated. */
 } orrb_batch_desc;
 
 /* Caller-preallocated outputs, flat over all pixels of all images (image c
@@ -234,9 +252,11 @@ typedef struct {
                            when shape.shadow_res > 0 and the batch has shadow cameras.  Written for
                            the faces that cast, first (its own launch), then read by the shading.
                            Maps of faces that cast none are left as they were. */
-  float* rgb_graded;    /* device, [N][3] or NULL: the colour after the colour grading (batch.grading)
-                           and before clamping and quantisation, the input of a loss on the graded
-                           image (see orrb_param_grads.d_grading); for an ungraded batch, rgb_linear */
+  float* rgb_graded;    /* device, [N][3] or NULL: the colour after ambient occlusion and bloom
+                           (batch.post) and the colour grading (batch.grading), before clamping and
+                           quantisation, the input of a loss on the graded image (see
+                           orrb_param_grads.d_grading, which needs a batch without post); for an
+                           ungraded batch without post, rgb_linear */
 } orrb_outputs;
 
 #define ORRB_MODE_FUSED 0  /* one persistent launch over all images (work queue) */
@@ -280,7 +300,9 @@ orrb_status orrb_render_batch(orrb_ctx* ctx, const orrb_batch_shape* shape, cons
  * the process exits.  Fewer CTAs run when a sample's scratch slot is large;
  * a shape whose slot (about 740 bytes per triangle of the largest sample)
  * does not fit even once is rejected with ORRB_ERR_WORKSPACE.  The entry
- * point calls no cudaMalloc, cudaFree or allocating library routine.
+ * point calls no cudaMalloc, cudaFree or allocating library routine.  A batch
+ * with post-processing parameters (batch.post) is rejected with
+ * ORRB_ERR_UNSUPPORTED: its images need the workspace.
  *   device_status: optional device pointer to one uint32 that receives the
  *     ORRB_DEV_* bits (cleared by this call); NULL discards them.
  * The first call on a device looks up the static array's device address
@@ -314,7 +336,9 @@ typedef struct {
                           parameter, and d_grading receives d hue, saturation, contrast,
                           brightness, temperature, tint, grain amplitude, and 0 for the seed.  The
                           background's colour is graded too: its pixels count for the grading
-                          parameters (the background colour itself is not differentiated). */
+                          parameters (the background colour itself is not differentiated).  A
+                          batch with post-processing (batch.post) is rejected with
+                          ORRB_ERR_UNSUPPORTED: ambient occlusion and bloom are not differentiated. */
 } orrb_param_grads;
 
 /* Workspace bytes of orrb_shade_backward for `shape` (partial sums). */

@@ -10,7 +10,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-SOURCES = ["orrb_api.cpp", "orrb_render.cu", "orrb_shadow_table.cu", "orrb_backward.cu"]
+SOURCES = ["orrb_api.cpp", "orrb_render.cu", "orrb_shadow_table.cu", "orrb_post.cu", "orrb_backward.cu"]
 HEADERS = [os.path.join(CSRC, "orrb_internal.h"), os.path.join(CSRC, "orrb_shading.cuh"), os.path.join(ROOT, "include", "orrb.h")]
 LIB = os.path.join(HERE, "liborrb.so")
 PEAK_SRC = os.path.join(CSRC, "orrb_fp32_peak.cu")

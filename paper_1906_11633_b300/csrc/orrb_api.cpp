@@ -202,6 +202,8 @@ orrb_status check_shape(orrb_ctx* ctx, const orrb_batch_shape* s) {
     return fail(ctx, ORRB_ERR_INVALID_ARG, "shadow_res %d outside [0, %d]", s->shadow_res, ORRB_MAX_RESOLUTION);
   if (s->shadow_faces < 0 || s->shadow_faces > kMaxShadowFaces)
     return fail(ctx, ORRB_ERR_INVALID_ARG, "shadow_faces %d outside [0, %d]", s->shadow_faces, kMaxShadowFaces);
+  if (s->post_effects != 0 && s->post_effects != 1)
+    return fail(ctx, ORRB_ERR_INVALID_ARG, "post_effects %d is neither 0 nor 1", s->post_effects);
   return ORRB_OK;
 }
 
@@ -224,6 +226,9 @@ struct Plan {
   size_t slot_bytes, smem, total;
   size_t nb_offset;   // the shadow maps' neighbourhood table (after the slots), 0 without shadows
   size_t cnt_offset;  // its occupied-texel counts (after the table)
+  // the post pass's images (with shape.post_effects): linear colour, depth, normals, occluded
+  // colour, row blur
+  size_t post_lin, post_depth, post_normal, post_cao, post_hblur;
 };
 
 orrb_status plan(orrb_ctx* ctx, const orrb_batch_shape& s, const orrb_config& c, Plan* P) {
@@ -256,6 +261,16 @@ orrb_status plan(orrb_ctx* ctx, const orrb_batch_shape& s, const orrb_config& c,
     P->nb_offset = align256(P->total);
     P->cnt_offset = align256(P->nb_offset + texels * sizeof(uint32_t));
     P->total = P->cnt_offset + texels;
+  }
+  P->post_lin = P->post_depth = P->post_normal = P->post_cao = P->post_hblur = 0;
+  if (s.post_effects) {
+    const size_t n = (size_t)s.total_pixels;
+    P->post_lin = align256(P->total);
+    P->post_depth = align256(P->post_lin + 12 * n);
+    P->post_normal = align256(P->post_depth + 4 * n);
+    P->post_cao = align256(P->post_normal + 6 * n);
+    P->post_hblur = align256(P->post_cao + 12 * n);
+    P->total = P->post_hblur + 12 * n;
   }
   return ORRB_OK;
 }
@@ -541,11 +556,47 @@ orrb_status orrb_render_batch(orrb_ctx* ctx, const orrb_batch_shape* shape, cons
   p.shadow_nb = p.shadow_res > 0 ? reinterpret_cast<uint32_t*>(ws + P.nb_offset) : nullptr;
   p.shadow_cnt = p.shadow_res > 0 ? reinterpret_cast<uint8_t*>(ws + P.cnt_offset) : nullptr;
   p.plain_sample = -1;
+  // ambient occlusion and bloom: the camera launch writes the linear colour, depth and normals
+  // (the caller's outputs where given, else the workspace's) and neither grades nor quantises; the
+  // post pass then writes rgb and the graded colour
+  PostParams pq{};
+  const bool post = batch->post != nullptr;
+  if (post) {
+    if (!shape->post_effects)
+      return fail(ctx, ORRB_ERR_INVALID_ARG, "batch.post needs shape.post_effects = 1 (it sizes the workspace)");
+    pq.cam_wh = batch->cam_wh;
+    pq.img_offset = batch->img_offset;
+    pq.cam_intr = batch->cam_intr;
+    pq.cam_sample = batch->cam_sample;
+    pq.cam_offset = batch->cam_offset;
+    pq.post = batch->post;
+    pq.grading = batch->grading;
+    pq.n_cams = shape->n_cams;
+    pq.n_samples = shape->n_samples;
+    pq.lin = out->rgb_linear ? out->rgb_linear : reinterpret_cast<float*>(ws + P.post_lin);
+    pq.depth = out->depth ? out->depth : reinterpret_cast<float*>(ws + P.post_depth);
+    pq.normal = out->normal ? out->normal : reinterpret_cast<uint16_t*>(ws + P.post_normal);
+    pq.cao = reinterpret_cast<float*>(ws + P.post_cao);
+    pq.hblur = reinterpret_cast<float*>(ws + P.post_hblur);
+    pq.rgb = out->rgb;
+    pq.rgb_graded = out->rgb_graded;
+    p.rgb_linear = const_cast<float*>(pq.lin);
+    p.depth = const_cast<float*>(pq.depth);
+    p.normal = const_cast<uint16_t*>(pq.normal);
+    p.rgb = nullptr;
+    p.rgb_graded = nullptr;
+    p.grading = nullptr;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(ws, 0, 16, s);
   if (e != cudaSuccess) return fail(ctx, ORRB_ERR_CUDA, "workspace clear: %s", cudaGetErrorString(e));
   if (shape->n_cams == 0 || shape->n_samples == 0) return ORRB_OK;
-  return enqueue_render(ctx, p, *shape, c.mode, c.threads, P.n_slots, ws, stream);
+  st = enqueue_render(ctx, p, *shape, c.mode, c.threads, P.n_slots, ws, stream);
+  if (st != ORRB_OK || !post) return st;
+  char err[256] = {0};
+  if (launch_post(pq, shape->max_width, shape->max_height, stream, err, sizeof(err)))
+    return fail(ctx, ORRB_ERR_CUDA, "%s", err);
+  return ORRB_OK;
 }
 
 orrb_status orrb_render_batch_noalloc(orrb_ctx* ctx, const orrb_batch_shape* shape, const orrb_batch_desc* batch,
@@ -561,6 +612,8 @@ orrb_status orrb_render_batch_noalloc(orrb_ctx* ctx, const orrb_batch_shape* sha
   if (st == ORRB_OK) st = check_desc(ctx, batch);
   if (st != ORRB_OK) return st;
   if (c.mode != ORRB_MODE_FUSED) return fail(ctx, ORRB_ERR_INVALID_ARG, "the allocation-free entry point runs the fused mode only");
+  if (batch->post)
+    return fail(ctx, ORRB_ERR_UNSUPPORTED, "the allocation-free entry point has no room for the post-processing images");
   if (!out) return fail(ctx, ORRB_ERR_INVALID_ARG, "null outputs");
   DeviceGuard dg(ctx->device);
   if (!dg.ok) return fail(ctx, ORRB_ERR_CUDA, "cudaSetDevice(%d) failed", ctx->device);
@@ -672,6 +725,8 @@ orrb_status orrb_shade_backward(orrb_ctx* ctx, const orrb_batch_shape* shape, co
   bp.d_grading = grads->d_grading;
   if (bp.d_grading && !batch->grading)
     return fail(ctx, ORRB_ERR_INVALID_ARG, "d_grading (a loss on the graded colour) needs a graded batch");
+  if (bp.d_grading && batch->post)
+    return fail(ctx, ORRB_ERR_UNSUPPORTED, "a loss on the graded colour is not differentiated through ambient occlusion and bloom");
   bp.partial = reinterpret_cast<float*>(static_cast<char*>(workspace) + 256);
   bp.blocks_per_img = bpi;
   char err[256] = {0};

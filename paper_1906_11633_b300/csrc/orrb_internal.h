@@ -175,4 +175,24 @@ constexpr int kGradeSums = 13;
 constexpr int kGradFloats = kGradGrade + kGradeSums;  // 190
 int launch_backward(const BackwardParams& p, int threads, void* stream, char* err, size_t errlen);
 
+// The post-processing pass (ambient occlusion and bloom) after the camera launch.
+struct PostParams {
+  const int32_t* cam_wh;
+  const int64_t* img_offset;
+  const float* cam_intr;
+  const int32_t* cam_sample;
+  const int32_t* cam_offset;
+  const float* post;     // [n_samples][4] AO intensity, bloom intensity, bloom radius, 0
+  const float* grading;  // [n_samples][8] or null
+  int32_t n_cams, n_samples;
+  const float* lin;         // [N][3] linear colour (the camera launch's rgb_linear)
+  const float* depth;       // [N]
+  const uint16_t* normal;   // [N][3] binary16
+  float* cao;               // [N][3] scratch: the occluded colour
+  float* hblur;             // [N][3] scratch: the bright parts blurred along rows
+  uint8_t* rgb;             // [N][3] or null
+  float* rgb_graded;        // [N][3] or null
+};
+int launch_post(const PostParams& q, int w_max, int h_max, void* stream, char* err, size_t errlen);
+
 }  // namespace orrb

@@ -14,6 +14,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liborrb.so")
 
 ORRB_OK = 0
+ORRB_ERR_INVALID_ARG = 1   # status codes (ORRB_ERR_* of include/orrb.h)
+ORRB_ERR_WORKSPACE = 2
+ORRB_ERR_CUDA = 3
+ORRB_ERR_TIMEOUT = 4
+ORRB_ERR_NOT_FOUND = 5
+ORRB_ERR_UNSUPPORTED = 6
+ORRB_ERR_DEVICE = 7
 ORRB_MODE_FUSED = 0
 ORRB_MODE_PLAIN = 1
 ORRB_MAX_LIGHTS = 4
@@ -46,14 +53,14 @@ class orrb_batch_shape(C.Structure):
     _fields_ = [("n_samples", C.c_int32), ("n_cams", C.c_int32), ("max_tris_per_sample", C.c_int32),
                 ("max_inst_per_sample", C.c_int32), ("max_cams_per_sample", C.c_int32), ("max_width", C.c_int32),
                 ("max_height", C.c_int32), ("total_pixels", C.c_int64), ("shadow_res", C.c_int32),
-                ("shadow_faces", C.c_int32)]
+                ("shadow_faces", C.c_int32), ("post_effects", C.c_int32)]
 
 
 class orrb_batch_desc(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in (
         "inst_offset", "inst_mesh", "inst_pose", "inst_seg", "inst_mat_base", "cam_offset", "cam_sample", "cam_view",
         "cam_intr", "cam_wh", "img_offset", "light", "light_meta", "material", "exposure_ev", "ambient", "background", "grading",
-        "light_spot", "emission", "shadow_view", "shadow_intr")]
+        "light_spot", "emission", "shadow_view", "shadow_intr", "post")]
 
 
 class orrb_outputs(C.Structure):

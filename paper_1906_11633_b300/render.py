@@ -25,7 +25,7 @@ _DTYPES = dict(inst_offset=torch.int32, inst_mesh=torch.int32, inst_pose=torch.f
                cam_intr=torch.float32, cam_wh=torch.int32, img_offset=torch.int64, light=torch.float32,
                light_meta=torch.int32, material=torch.float32, exposure_ev=torch.float32, ambient=torch.float32,
                background=torch.float32, grading=torch.float32, light_spot=torch.float32, emission=torch.float32,
-               shadow_view=torch.float32, shadow_intr=torch.float32)
+               shadow_view=torch.float32, shadow_intr=torch.float32, post=torch.float32)
 _NP = {torch.int32: np.int32, torch.float32: np.float32, torch.uint8: np.uint8, torch.int16: np.int16,
        torch.int64: np.int64}
 
@@ -42,7 +42,8 @@ def batch_shape(batch) -> L.orrb_batch_shape:
         max_height=int(batch.cam_wh[:, 1].max()) if batch.n_cams else 1,
         total_pixels=batch.total_pixels,
         shadow_res=int(getattr(batch, "shadow_res", 0) or 0) if getattr(batch, "shadow_view", None) is not None else 0,
-        shadow_faces=int(getattr(batch, "shadow_faces", 1) or 1))
+        shadow_faces=int(getattr(batch, "shadow_faces", 1) or 1),
+        post_effects=int(getattr(batch, "post", None) is not None))
 
 
 @dataclass

@@ -324,10 +324,12 @@ class GpuBackend:
         px = sum(b.total_pixels for b in batches)
         tris = max(int(b.tris_per_sample().max()) for b in batches)
         # outputs (14 B per pixel) + workspace + parameters, + shadow maps (4 B per texel) and their
-        # neighbourhood table (4 B + a 1-byte count per texel)
+        # neighbourhood table (4 B + a 1-byte count per texel), + the post pass's images (46 B per
+        # pixel) when a request carries ambient occlusion and bloom
         maps = sum(b.n_samples * 4 * b.shadow_faces * b.shadow_res ** 2 * 9
                    for b in batches if getattr(b, "shadow_view", None) is not None)
-        return int(px * 14 + self.ws_a + self.ws_b * tris + sum(b.n_samples for b in batches) * 4096 + maps)
+        post = px * 46 + 256 * 5 if any(getattr(b, "post", None) is not None for b in batches) else 0
+        return int(px * 14 + self.ws_a + self.ws_b * tris + sum(b.n_samples for b in batches) * 4096 + maps + post)
 
     def _take_stage(self, nbytes: int) -> ParamStage:
         with self._stage_lock:
