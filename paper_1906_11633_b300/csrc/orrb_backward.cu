@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
           Vv[1] = 0.0f;
           Vv[2] = 1.0f;
         } else {
-          float rl = rsqrtf(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
+          float rl = rsqrt_approx(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
           Vv[0] = -P[0] * rl;
           Vv[1] = -P[1] * rl;
           Vv[2] = -P[2] * rl;
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
           if (sh.light_type != 1) {
             for (int k = 0; k < 3; k++) Lv[k] = sh.lv[l][k] - P[k];
             d2 = Lv[0] * Lv[0] + Lv[1] * Lv[1] + Lv[2] * Lv[2];
-            rinv = rsqrtf(d2);
+            rinv = rsqrt_approx(d2);
             for (int k = 0; k < 3; k++) L[k] = Lv[k] * rinv;
             if (sh.light_type == 2) {
               const float t = __saturatef(L[0] * -sh.la[l][0] + L[1] * -sh.la[l][1] + L[2] * -sh.la[l][2] +
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
             float h2 = Hv[0] * Hv[0] + Hv[1] * Hv[1] + Hv[2] * Hv[2];
             if (h2 > 0.0f) {
               has_h = true;
-              rh = rsqrtf(h2);
+              rh = rsqrt_approx(h2);
               for (int k = 0; k < 3; k++) H[k] = Hv[k] * rh;
               ndh = fmaxf(0.0f, n[0] * H[0] + n[1] * H[1] + n[2] * H[2]);
               pw = lobe_pow(ndh, m[4]);

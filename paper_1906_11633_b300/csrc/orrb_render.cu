@@ -969,7 +969,7 @@ __device__ void shade(const CtaShared& sh, const float P[3], const float n[3], i
     Vv[1] = 0.0f;
     Vv[2] = 1.0f;
   } else {
-    float rl = rsqrtf(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
+    float rl = rsqrt_approx(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
     Vv[0] = -P[0] * rl;
     Vv[1] = -P[1] * rl;
     Vv[2] = -P[2] * rl;
@@ -987,7 +987,7 @@ __device__ void shade(const CtaShared& sh, const float P[3], const float n[3], i
       Lx = lq.x - P[0];
       Ly = lq.y - P[1];
       Lz = lq.z - P[2];
-      r = rsqrtf(Lx * Lx + Ly * Ly + Lz * Lz);
+      r = rsqrt_approx(Lx * Lx + Ly * Ly + Lz * Lz);
       E = lq.w * (r * r);
       if (kLight && im.light_type == 2) {  // the spot cone: E *= t^2 (3 - 2t)
         const float4 sq = *reinterpret_cast<const float4*>(im.la[l]);
@@ -1007,7 +1007,7 @@ __device__ void shade(const CtaShared& sh, const float P[3], const float n[3], i
       const float H0 = fmaf(Lx, r, Vv[0]), H1 = fmaf(Ly, r, Vv[1]), H2 = fmaf(Lz, r, Vv[2]);
       const float h2 = H0 * H0 + H1 * H1 + H2 * H2;
       if (h2 > 0.0f) {
-        const float ndh = fmaxf(0.0f, (n[0] * H0 + n[1] * H1 + n[2] * H2) * rsqrtf(h2));
+        const float ndh = fmaxf(0.0f, (n[0] * H0 + n[1] * H1 + n[2] * H2) * rsqrt_approx(h2));
         S = fmaf(E, m[3] * lobe_pow(ndh, m[4]), S);
       }
     }
@@ -1165,7 +1165,7 @@ __device__ int shade_shadowed(const Params& p, const CtaShared& sh, const Shadow
     Vv[1] = 0.0f;
     Vv[2] = 1.0f;
   } else {
-    float rl = rsqrtf(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
+    float rl = rsqrt_approx(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
     Vv[0] = -P[0] * rl;
     Vv[1] = -P[1] * rl;
     Vv[2] = -P[2] * rl;
@@ -1182,7 +1182,7 @@ __device__ int shade_shadowed(const Params& p, const CtaShared& sh, const Shadow
       Lx = lq.x - P[0];
       Ly = lq.y - P[1];
       Lz = lq.z - P[2];
-      r = rsqrtf(Lx * Lx + Ly * Ly + Lz * Lz);
+      r = rsqrt_approx(Lx * Lx + Ly * Ly + Lz * Lz);
       E = lq.w * (r * r);
       if (im.light_type == 2) {
         const float4 sq = *reinterpret_cast<const float4*>(im.la[l]);
@@ -1203,7 +1203,7 @@ __device__ int shade_shadowed(const Params& p, const CtaShared& sh, const Shadow
       const float H0 = fmaf(Lx, r, Vv[0]), H1 = fmaf(Ly, r, Vv[1]), H2 = fmaf(Lz, r, Vv[2]);
       const float h2 = H0 * H0 + H1 * H1 + H2 * H2;
       if (h2 > 0.0f) {
-        const float ndh = fmaxf(0.0f, (n[0] * H0 + n[1] * H1 + n[2] * H2) * rsqrtf(h2));
+        const float ndh = fmaxf(0.0f, (n[0] * H0 + n[1] * H1 + n[2] * H2) * rsqrt_approx(h2));
         S = fmaf(E, m[3] * lobe_pow(ndh, m[4]), S);
       }
     }
@@ -1468,7 +1468,7 @@ __device__ void raster_tile_warp(const Params& p, const CtaShared& sh, const Scr
           n[2] = a0 * __int_as_float(q3.w) + a1 * q4.z + a2 * q5.y;
           const float l2 = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
           if (l2 > 0.0f) {
-            const float rl = rsqrtf(l2);
+            const float rl = rsqrt_approx(l2);
             n[0] *= rl;
             n[1] *= rl;
             n[2] *= rl;

@@ -9,6 +9,15 @@ __device__ __forceinline__ float exp2f_approx(float x) {
   return y;
 }
 
+// 1/sqrt(x) by the hardware approximation (PTX rsqrt.approx, relative error below 2^-22.9) with
+// subnormal inputs flushed to zero.  The inputs here are squared lengths; only a vector shorter
+// than about 1e-19 would read as zero.
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ float log2f_approx(float x) {
   float y;
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
