@@ -1664,7 +1664,8 @@ __device__ void raster_claimed(const Params& p, CtaShared& sh, const Scratch& sc
     mine++;
     if (!owner && lane == 0) {
       __threadfence();
-      atomicAdd(reinterpret_cast<unsigned*>(sc.header + 4), 1u);
+      if (atomicAdd(reinterpret_cast<unsigned*>(sc.header + 4), 1u) + 1u == unsigned(n_tiles))
+        atomicAdd(p.images_done, 1u);  // the image's last tile (the owner has added its own)
     }
   }
   if (owner && lane == 0) atomicAdd(&sh.next_tile, mine);  // the owner's own count (shared memory)
@@ -1684,9 +1685,11 @@ __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
   const SmemLayout L = layout_of(p);
   SmemPtrs sp = carve(smem, p, L);
   const Scratch sc = slot_scratch(p, blockIdx.x);
-  if (threadIdx.x == 0) sh.stop = 0;
+  if (threadIdx.x == 0) {
+    sh.stop = 0;
+    sh.img = atomicAdd(p.work_counter, 1);
+  }
   while (true) {
-    if (threadIdx.x == 0) sh.img = atomicAdd(p.work_counter, 1);
     __syncthreads();
     const int cam = sh.img;
     if (cam >= p.n_cams) break;
@@ -1717,11 +1720,21 @@ __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
       }
       __syncthreads();
       raster_claimed<kF>(p, sh, sc, sp, L, cam, true);
-      if (threadIdx.x == 0) {  // close it and wait for helpers still on its other tiles
+      if (threadIdx.x == 0) {
+        // close the raster phase and add the own tiles to the slot's finished-tile count; whoever
+        // brings that count to the image's tile count (owner or helper) counts the image done
         atomicExch(sc.claim(), 0ull);
-        const unsigned helped = unsigned(sh.im.n_tiles - sh.next_tile);
+        const unsigned n_tiles = unsigned(sh.im.n_tiles), mine = unsigned(sh.next_tile);
+        __threadfence();
+        // (with no own tile, helpers took every tile and the last of them counted the image)
+        if (mine > 0 && atomicAdd(reinterpret_cast<unsigned*>(sc.header + 4), mine) + mine == n_tiles)
+          atomicAdd(p.images_done, 1u);
+        // the next image, popped before deciding whether to wait: only a CTA that reuses its slot
+        // waits for the helpers still on its other tiles; once the queue is empty it goes on to
+        // help other images at once (helpers exist only after the queue has emptied)
+        sh.img = atomicAdd(p.work_counter, 1);
         const long long t0 = clock64();
-        while (atomicAdd(reinterpret_cast<unsigned*>(sc.header + 4), 0u) < helped) {
+        while (sh.img < p.n_cams && atomicAdd(reinterpret_cast<unsigned*>(sc.header + 4), 0u) < n_tiles) {
           if (clock64() - t0 > p.wait_cycles) {
             // a helper may still be reading this slot: the CTA leaves the launch, so that the
             // slot is never rewritten under it
@@ -1732,10 +1745,10 @@ __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
           __nanosleep(200);
         }
       }
-    }
-    if (threadIdx.x == 0) {
+    } else if (threadIdx.x == 0) {  // an image that is not rendered (its status bits are set)
       __threadfence();
       atomicAdd(p.images_done, 1u);
+      sh.img = atomicAdd(p.work_counter, 1);
     }
     __syncthreads();
     if (sh.stop) return;
