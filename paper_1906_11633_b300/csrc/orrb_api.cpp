@@ -4,6 +4,7 @@
 // arena and the last error message.  Every device buffer (mesh arena,
 // workspace, outputs, batch arrays) belongs to the caller.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -36,6 +37,21 @@ struct orrb_ctx {
 namespace {
 
 using namespace orrb;
+
+// An NVTX range over one host-side step (a no-op unless a profiler is attached), so that a
+// timeline shows which entry point and which launch of a render enqueued the kernels.
+// A null name opens no range (the allocation-free entry point calls nothing it need not).
+struct Range {
+  explicit Range(const char* name) : on(name != nullptr) {
+    if (on) nvtxRangePushA(name);
+  }
+  ~Range() {
+    if (on) nvtxRangePop();
+  }
+  bool on;
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 orrb_status fail(orrb_ctx* ctx, orrb_status s, const char* fmt, ...) {
   if (ctx) {
@@ -323,10 +339,11 @@ orrb_status check_desc(orrb_ctx* ctx, const orrb_batch_desc* b) {
 // the images sample * 4 + light, depth only, into the shadow maps), then the camera images.
 // n_slots: the scratch slots the fused mode may use; ws: the status word and queue counters.
 orrb_status enqueue_render(orrb_ctx* ctx, Params& p, const orrb_batch_shape& s, int mode, int threads, int n_slots,
-                           char* ws, void* stream) {
+                           char* ws, void* stream, bool trace = true) {
   char err[256] = {0};
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (p.shadow_res > 0) {
+    Range r(trace ? "orrb shadow pass + neighbourhood table" : nullptr);
     Params q = p;
     q.shadow_pass = 1;
     q.n_cams = s.n_samples * kMaxLights * p.shadow_faces;
@@ -351,6 +368,7 @@ orrb_status enqueue_render(orrb_ctx* ctx, Params& p, const orrb_batch_shape& s, 
     cudaError_t e = cudaMemsetAsync(ws + 4, 0, 8, st);
     if (e != cudaSuccess) return fail(ctx, ORRB_ERR_CUDA, "queue reset: %s", cudaGetErrorString(e));
   }
+  Range r(!trace ? nullptr : mode == ORRB_MODE_FUSED ? "orrb camera launch (fused)" : "orrb camera launches (plain)");
   const int n_ctas = mode == ORRB_MODE_FUSED ? std::min(n_slots, std::max(s.n_cams, 1)) : 0;
   p.n_slots = n_ctas;
   if (launch_render(p, mode, threads, n_ctas, std::max(s.max_cams_per_sample, 1), stream, err, sizeof(err)))
@@ -419,6 +437,7 @@ orrb_status orrb_mesh_arena_size(const orrb_mesh_desc* meshes, int32_t n, size_t
 orrb_status orrb_upload_meshes(orrb_ctx* ctx, const orrb_mesh_desc* meshes, int32_t n, void* dev_arena,
                                size_t arena_bytes, void* stream) {
   if (!ctx) return ORRB_ERR_INVALID_ARG;
+  Range range("orrb_upload_meshes");
   std::lock_guard<std::mutex> g(ctx->mu);
   orrb_status st = check_meshes(ctx, meshes, n);
   if (st != ORRB_OK) return st;
@@ -505,6 +524,7 @@ orrb_status orrb_render_batch(orrb_ctx* ctx, const orrb_batch_shape* shape, cons
                               const orrb_outputs* out, const orrb_config* cfg, void* workspace, size_t ws_bytes,
                               void* stream) {
   if (!ctx) return ORRB_ERR_INVALID_ARG;
+  Range range("orrb_render_batch");
   std::lock_guard<std::mutex> g(ctx->mu);
   if (!ctx->has_meshes) return fail(ctx, ORRB_ERR_NOT_FOUND, "upload meshes before rendering");
   orrb_config c;
@@ -594,6 +614,7 @@ orrb_status orrb_render_batch(orrb_ctx* ctx, const orrb_batch_shape* shape, cons
   st = enqueue_render(ctx, p, *shape, c.mode, c.threads, P.n_slots, ws, stream);
   if (st != ORRB_OK || !post) return st;
   char err[256] = {0};
+  Range post_range("orrb post pass (ambient occlusion, bloom)");
   if (launch_post(pq, shape->max_width, shape->max_height, stream, err, sizeof(err)))
     return fail(ctx, ORRB_ERR_CUDA, "%s", err);
   return ORRB_OK;
@@ -667,7 +688,7 @@ orrb_status orrb_render_batch_noalloc(orrb_ctx* ctx, const orrb_batch_shape* sha
   if (e == cudaSuccess && device_status) e = cudaMemsetAsync(device_status, 0, 4, s);
   if (e != cudaSuccess) return fail(ctx, ORRB_ERR_CUDA, "scratch clear: %s", cudaGetErrorString(e));
   if (shape->n_cams == 0 || shape->n_samples == 0) return ORRB_OK;
-  return enqueue_render(ctx, p, *shape, ORRB_MODE_FUSED, c.threads, n_slots, ws, stream);  // one slot per CTA
+  return enqueue_render(ctx, p, *shape, ORRB_MODE_FUSED, c.threads, n_slots, ws, stream, false);  // one slot per CTA
 }
 
 orrb_status orrb_read_status(orrb_ctx* ctx, const void* workspace, void* stream, uint32_t* status) {
@@ -701,6 +722,7 @@ orrb_status orrb_shade_backward(orrb_ctx* ctx, const orrb_batch_shape* shape, co
                                 const float* gbuffer, const float* d_rgb_linear, const orrb_param_grads* grads,
                                 void* workspace, size_t ws_bytes, void* stream) {
   if (!ctx) return ORRB_ERR_INVALID_ARG;
+  Range range("orrb_shade_backward");
   std::lock_guard<std::mutex> g(ctx->mu);
   orrb_status st = check_shape(ctx, shape);
   if (st == ORRB_OK) st = check_desc(ctx, batch);

@@ -341,10 +341,11 @@ class GpuBackend:
     def launch(self, batches, k: int):
         torch = self.torch
         from .render import DeviceBatch, host_arrays
-        packed, shape = self._shape(batches)
+        with torch.cuda.nvtx.range("serve: pack batch"):  # (a timeline range; no-op without a profiler)
+            packed, shape = self._shape(batches)
+            arrs = host_arrays(packed)
+            offs, nbytes = ParamStage.layout(arrs)
         s = self.streams[k]
-        arrs = host_arrays(packed)
-        offs, nbytes = ParamStage.layout(arrs)
         stage = self._take_stage(nbytes)
         try:
             t = stage.upload(torch, arrs, offs, nbytes, s)
