@@ -70,6 +70,20 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// Four sums over the warp at once (a fixed order, so the result is the same every run): the
+// half-warps exchange two of the four values, the quarter-warps one of the remaining two, and the
+// last three steps sum one value.  Lane l returns the sum of value (l >> 3) & 3, so lanes 0, 8, 16
+// and 24 hold the four sums; six shuffles instead of twenty.
+__device__ __forceinline__ float warp_sum4(float a0, float a1, float a2, float a3, int lane) {
+  const bool h16 = (lane & 16) != 0, h8 = (lane & 8) != 0;
+  const float r0 = __shfl_xor_sync(kFull, h16 ? a0 : a2, 16);
+  const float r1 = __shfl_xor_sync(kFull, h16 ? a1 : a3, 16);
+  const float b0 = (h16 ? a2 : a0) + r0, b1 = (h16 ? a3 : a1) + r1;
+  float c = (h8 ? b1 : b0) + __shfl_xor_sync(kFull, h8 ? b0 : b1, 8);
+  for (int o = 4; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+  return c;
+}
+
 // 4 CTAs (32 warps) per SM: the per-pixel loads need the occupancy more than the adjoint needs registers.
 // kGraded: the loss is on the graded colour c' = A c + t + grain: d_rgb holds dL/dc', the adjoint
 // of the shading takes A^T dL/dc', and the image's sums sum dc' c^T, sum dc' and the grain term
@@ -282,27 +296,18 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
       const int leader = __ffs(pending) - 1;
       const int mm = __shfl_sync(kFull, mat, leader);
       const bool mine = mat == mm;
-      float v0 = warp_sum(mine ? dm[0] : 0.0f), v1 = warp_sum(mine ? dm[1] : 0.0f);
-      float v2 = warp_sum(mine ? dm[2] : 0.0f), v3 = warp_sum(mine ? dm[3] : 0.0f);
-      float v4 = warp_sum(mine ? dm[4] : 0.0f);
-      if (lane == 0) {
-        sh.wmat[warp][mm][0] += v0;
-        sh.wmat[warp][mm][1] += v1;
-        sh.wmat[warp][mm][2] += v2;
-        sh.wmat[warp][mm][3] += v3;
-        sh.wmat[warp][mm][4] += v4;
-      }
+      const float v = warp_sum4(mine ? dm[0] : 0.0f, mine ? dm[1] : 0.0f, mine ? dm[2] : 0.0f,
+                                mine ? dm[3] : 0.0f, lane);
+      const float v4 = warp_sum(mine ? dm[4] : 0.0f);
+      if ((lane & 7) == 0) sh.wmat[warp][mm][lane >> 3] += v;
+      if (lane == 0) sh.wmat[warp][mm][4] += v4;
       pending &= ~__ballot_sync(kFull, mine);
     }
   }
   // per-thread light and exposure sums -> per warp (fixed tree) -> per CTA (warp order)
   for (int l = 0; l < kMaxLights; l++) {
-    for (int k = 0; k < 3; k++) {
-      float v = warp_sum(dlv[l][k]);
-      if (lane == 0) sh.wred[warp][l * 4 + k] = v;
-    }
-    float v = warp_sum(dI[l]);
-    if (lane == 0) sh.wred[warp][l * 4 + 3] = v;
+    const float v = warp_sum4(dlv[l][0], dlv[l][1], dlv[l][2], dI[l], lane);
+    if ((lane & 7) == 0) sh.wred[warp][l * 4 + (lane >> 3)] = v;
   }
   {
     float v = warp_sum(dev);
