@@ -85,11 +85,13 @@
  *      face -- each triangle's second and third vertices swapped
  *      before step 5, so front faces are culled -- and 0 where there is none.
  *  16  shadow lookup in step 10: for a camera pixel with surface and each
- *      light with a casting face, in fp32 with every operation rounded
- *      separately: P as in step 9; for the faces in order, M = S V^-1 (V^-1 =
- *      [R^T | -R^T t], products summed in index order), q = M P, z = -q_z,
- *      u = cx + fx (q_x (1/z)), v = cy - fy (q_y (1/z)) (orthographic: u =
- *      cx + fx q_x, v = cy - fy q_y); the first face with
+ *      light with a casting face, in fp32, every operation rounded to nearest:
+ *      P as in step 9; for the faces in order, M = S V^-1 (V^-1 = [R^T | -R^T t],
+ *      products summed in index order, each operation rounded separately),
+ *      q_i = fma(M_i2, P_z, fma(M_i1, P_y, fma(M_i0, P_x, M_i3))) (fused
+ *      multiply-adds, one rounding each), z = -q_z, u = fma(fx, q_x (1/z), cx),
+ *      v = fma(-fy, q_y (1/z), cy) (orthographic: u = fma(fx, q_x, cx),
+ *      v = fma(-fy, q_y, cy)); the first face with
  *      z > near and (floor(u), floor(v)) inside its map decides (none: the
  *      light is unshadowed): over the 3 x 3 texels (floor(u) + a, floor(v) +
  *      b), a, b in {-1, 0, 1}, inside the map, count k those with map depth
@@ -614,19 +616,20 @@ static void camera_to_shadow(const float* S, const float* V, float M[12]) {
 static int shadow_taps(const float M[12], const float* si, const float* map, int32_t R, const float P[3],
                        int64_t* ops) {
   float q[3];
-  for (int i = 0; i < 3; i++) q[i] = ((M[i * 4 + 0] * P[0] + M[i * 4 + 1] * P[1]) + M[i * 4 + 2] * P[2]) + M[i * 4 + 3];
+  /* each row as three fused multiply-adds (one rounding each), the translation first */
+  for (int i = 0; i < 3; i++) q[i] = fmaf(M[i * 4 + 2], P[2], fmaf(M[i * 4 + 1], P[1], fmaf(M[i * 4 + 0], P[0], M[i * 4 + 3])));
   float z = -q[2];
-  *ops += 18 + 1 + 1; /* the projection, z, the near test */
+  *ops += 18 + 1 + 1; /* the projection (nine fused multiply-adds, two operations each), z, the near test */
   if (!(z > si[4])) return -1;
   float u, v;
   if (si[6] != 0.0f) { /* orthographic */
-    u = si[2] + si[0] * q[0];
-    v = si[3] - si[1] * q[1];
+    u = fmaf(si[0], q[0], si[2]);
+    v = fmaf(-si[1], q[1], si[3]);
     *ops += 4;
   } else {
     float iw = 1.0f / z;
-    u = si[2] + si[0] * (q[0] * iw);
-    v = si[3] - si[1] * (q[1] * iw);
+    u = fmaf(si[0], q[0] * iw, si[2]);
+    v = fmaf(-si[1], q[1] * iw, si[3]);
     *ops += 7;
   }
   *ops += 4; /* the guard-band tests */

@@ -1055,7 +1055,8 @@ __device__ void shadow_setup(const Params& p, const ImageInfo& im, ShadowInfo& s
 
 // The shadowed taps k (0..9) of light l at the G-buffer position P (whose three coordinates the
 // resolve computes with separately rounded operations).  P is projected into the light's maps
-// with round-to-nearest operations in a fixed order (the reciprocal is correctly rounded, so it
+// with round-to-nearest operations in a fixed order: each row of the projection and each image
+// coordinate as fused multiply-adds, one rounding each (the reciprocal is correctly rounded, so it
 // equals 1 / z); the first casting face whose map contains the projection decides, and the 3 x 3
 // texels around it are compared with the point's depth less the bias.  The neighbourhood table
 // settles lit points and points behind every occupied tap in one or two loads; the others count
@@ -1069,15 +1070,16 @@ __device__ __forceinline__ int shadow_lookup_one(const Params& p, const ImageInf
     const float4 ma = M4[0], mb = M4[1], mc = M4[2];
     const float4 sa = reinterpret_cast<const float4*>(sd.si[l][f])[0];  // fx, fy, cx, cy
     const float4 sb = reinterpret_cast<const float4*>(sd.si[l][f])[1];  // near, bias, type
-    const float q2 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(mc.x, P0), __fmul_rn(mc.y, P1)), __fmul_rn(mc.z, P2)), mc.w);
+    // each row as three fused multiply-adds, the translation first (one rounding each)
+    const float q2 = __fmaf_rn(mc.z, P2, __fmaf_rn(mc.y, P1, __fmaf_rn(mc.x, P0, mc.w)));
     const float z = -q2;
     if (!(z > sb.x)) continue;
-    const float q0 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(ma.x, P0), __fmul_rn(ma.y, P1)), __fmul_rn(ma.z, P2)), ma.w);
-    const float q1 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(mb.x, P0), __fmul_rn(mb.y, P1)), __fmul_rn(mb.z, P2)), mb.w);
+    const float q0 = __fmaf_rn(ma.z, P2, __fmaf_rn(ma.y, P1, __fmaf_rn(ma.x, P0, ma.w)));
+    const float q1 = __fmaf_rn(mb.z, P2, __fmaf_rn(mb.y, P1, __fmaf_rn(mb.x, P0, mb.w)));
     const bool ortho = sb.z != 0.0f;  // (orthographic: a directional light's camera)
     const float iw = ortho ? 1.0f : __frcp_rn(z);
-    const float u = __fadd_rn(sa.z, __fmul_rn(sa.x, ortho ? q0 : __fmul_rn(q0, iw)));
-    const float v = __fsub_rn(sa.w, __fmul_rn(sa.y, ortho ? q1 : __fmul_rn(q1, iw)));
+    const float u = __fmaf_rn(sa.x, ortho ? q0 : __fmul_rn(q0, iw), sa.z);
+    const float v = __fmaf_rn(-sa.y, ortho ? q1 : __fmul_rn(q1, iw), sa.w);
     if (!(fabsf(u) < kGuardPx) || !(fabsf(v) < kGuardPx)) continue;
     const int i0 = int(floorf(u)), j0 = int(floorf(v));
     if (i0 < 0 || j0 < 0 || i0 >= R || j0 >= R) continue;
