@@ -270,7 +270,8 @@ typedef struct {
   int32_t ctas_per_sm;   /* fused mode: resident CTAs per SM; 0 = as many as fit */
   int32_t reserved;      /* must be 0 */
   int64_t wait_cycles;   /* fused mode: a wait between CTAs (a CTA looking for raster tiles to help
-                            with, an image's owner waiting for its helpers) gives up after this many
+                            with, an image's owner waiting for its helpers before it reuses its
+                            scratch for the next image) gives up after this many
                             SM clock cycles, sets ORRB_DEV_TIMEOUT and leaves the launch (the
                             outputs may then be incomplete); 0 = 2e9, about a second.  A small value
                             makes the waits run out on purpose. */
