@@ -57,7 +57,7 @@ struct BwdShared {
   float scale;
   int n_lights, light_type, ortho, s;
   float wmat[kBwdWarps][kMaxMaterials][5];      // per-warp material sums (albedo, specular, emission)
-  float wred[kBwdWarps][kMaxLights * 4 + 1];    // per-warp light + exposure sums
+  float wred[kBwdWarps][kMaxLights * 4];        // per-warp light sums
   float wgrade[kBwdWarps][kGradeSums];          // per-warp grading sums (graded loss)
   float gm[3][4];                               // the image's grading map c' = A c + t
   float bg[3];
@@ -142,12 +142,11 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
   const long long chunk = (npx + bp.blocks_per_img - 1) / bp.blocks_per_img;
   const long long i0 = blk * chunk, i1 = min(npx, i0 + chunk);
   const long long base = p.img_offset[cam];
-  const float ln2 = 0.69314718055994530942f;
   const float scale = sh.scale;
 
   float gsum[kGradeSums];  // graded loss: sum dc' c^T (row-major), sum dc', sum (sum dc') grain
   for (int k = 0; k < kGradeSums; k++) gsum[k] = 0.0f;
-  float dlv[kMaxLights][3], dI[kMaxLights], dev = 0.0f;
+  float dlv[kMaxLights][3], dI[kMaxLights];
   for (int l = 0; l < kMaxLights; l++) {
     dlv[l][0] = dlv[l][1] = dlv[l][2] = 0.0f;
     dI[l] = 0.0f;
@@ -274,11 +273,6 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
         for (int k = 0; k < 3; k++) dm[k] = g[k] * scale * (sh.amb[k] + em + sum_endl);
         dm[3] = scale * G * sum_epw;
         dm[4] = scale * gr;
-        // d rgb_k / d ev = ln 2 * rgb_k, and sum_k g_k rgb_k / scale
-        //   = sum_k g_k amb_k m_k + (g . m) (emission + sum E ndl) + (sum g) k_s sum E pw
-        const float e = g[0] * sh.amb[0] * m[0] + g[1] * sh.amb[1] * m[1] + g[2] * sh.amb[2] * m[2] +
-                        gr * (em + sum_endl) + G * m[3] * sum_epw;
-        dev += ln2 * scale * e;
         if (kGraded)
           for (int k = 0; k < 3; k++) c[k] = scale * (m[k] * (sh.amb[k] + em + sum_endl) + m[3] * sum_epw);
       }
@@ -309,10 +303,6 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
     const float v = warp_sum4(dlv[l][0], dlv[l][1], dlv[l][2], dI[l], lane);
     if ((lane & 7) == 0) sh.wred[warp][l * 4 + (lane >> 3)] = v;
   }
-  {
-    float v = warp_sum(dev);
-    if (lane == 0) sh.wred[warp][kMaxLights * 4] = v;
-  }
   if (kGraded)
     for (int k = 0; k < kGradeSums; k++) {
       const float v = warp_sum(gsum[k]);
@@ -341,11 +331,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
           sgn * (sh.V[0 * 4 + j] * dv[0] + sh.V[1 * 4 + j] * dv[1] + sh.V[2 * 4 + j] * dv[2]);
     out[kMaxMaterials * 4 + l * 4 + 3] = di;
   }
-  if (tid == 0) {
-    float v = 0.0f;
-    for (int w = 0; w < kBwdWarps; w++) v += sh.wred[w][kMaxLights * 4];
-    out[kMaxMaterials * 4 + kMaxLights * 4] = v;
-  }
+  if (tid == 0) out[kMaxMaterials * 4 + kMaxLights * 4] = 0.0f;  // (the exposure: formed by the reduce kernel)
   if (tid >= 32 && tid < 32 + kGradeSums) {
     float v = 0.0f;
     if (kGraded)
@@ -410,22 +396,36 @@ __global__ void __launch_bounds__(kReduceThreads) backward_reduce_kernel(Backwar
   const Params& p = bp.base;
   const int s = blockIdx.x, k = threadIdx.x;
   __shared__ float gsums[kGradeSums];
+  __shared__ float dmat[kMaxMaterials * 4];
   float v = 0.0f;
   if (k < kGradFloats)
     for (int c = p.cam_offset[s]; c < p.cam_offset[s + 1]; c++)
       for (int b = 0; b < bp.blocks_per_img; b++) v += bp.partial[((size_t)c * bp.blocks_per_img + b) * kGradFloats + k];
   if (k < kMaxMaterials * 4) {
+    dmat[k] = v;
     if (bp.d_material) bp.d_material[(size_t)s * kMaxMaterials * 4 + k] = v;
   } else if (k < kMaxMaterials * 4 + kMaxLights * 4) {
     if (bp.d_light) bp.d_light[(size_t)s * kMaxLights * 4 + (k - kMaxMaterials * 4)] = v;
   } else if (k < kGradEmission) {
-    if (bp.d_exposure) bp.d_exposure[s] = v;
+    // (the exposure slot of the partial rows is zero)
   } else if (k < kGradGrade) {
     if (bp.d_emission) bp.d_emission[(size_t)s * kMaxMaterials + (k - kGradEmission)] = v;
   } else if (k < kGradFloats) {
     gsums[k - kGradGrade] = v;
   }
   __syncthreads();
+  // The linear colour is linear in each material's (albedo rgb, specular) with no constant term,
+  // and the exposure scales all of it: d rgb / d ev = ln 2 rgb = ln 2 sum_m m . d rgb / d m.  So
+  // dL/d ev = ln 2 sum over materials of m . dL/dm, formed here from the material gradients
+  // instead of per pixel (materials in index order).
+  if (k == 32 && bp.d_exposure) {
+    const float* ms = p.material + (size_t)s * kMaxMaterials * 5;
+    float e = 0.0f;
+    for (int m = 0; m < kMaxMaterials; m++)
+      e += ms[m * 5 + 0] * dmat[m * 4 + 0] + ms[m * 5 + 1] * dmat[m * 4 + 1] + ms[m * 5 + 2] * dmat[m * 4 + 2] +
+           ms[m * 5 + 3] * dmat[m * 4 + 3];
+    bp.d_exposure[s] = 0.69314718055994530942f * e;
+  }
   if (k == 0 && bp.d_grading && p.grading)
     grading_grads(p.grading + (size_t)s * 8, gsums, bp.d_grading + (size_t)s * 8);
 }
