@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
           if (l >= sh.n_lights) break;
           float L[3], Lv[3] = {0.0f, 0.0f, 0.0f}, E, d2 = 1.0f, rinv = 1.0f;
           // the shadow factor (9 - k) / 9 is held fixed: it scales the intensity
-          const float vis = __fdividef(float(9 - ((word >> (8 + 4 * l)) & 15)), 9.0f);
+          const float vis = float(9 - ((word >> (8 + 4 * l)) & 15)) * (1.0f / 9.0f);
           const float I = sh.lv[l][3] * vis;
           float S = 1.0f, dS = 0.0f;  // spot cone factor, and its derivative in t
           if (sh.light_type != 1) {
@@ -248,12 +248,11 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
           const float dndl = lit ? scale * E * gr : 0.0f;
           // alpha * ndh^(alpha - 1) = alpha * pw / ndh for ndh > 0 (fast division: ~2 ulp)
           const float dndh = (has_h && ndh > 0.0f) ? scale * E * G * m[3] * m[4] * __fdividef(pw, ndh) : 0.0f;
-          float dL[3] = {dndl * n[0], dndl * n[1], dndl * n[2]};
-          if (dndh != 0.0f) {
-            float dH[3] = {dndh * n[0], dndh * n[1], dndh * n[2]};
-            float hd = H[0] * dH[0] + H[1] * dH[1] + H[2] * dH[2];
-            for (int k = 0; k < 3; k++) dL[k] += (dH[k] - H[k] * hd) * rh;
-          }
+          // through the half vector's normalisation, dL = dndl n + (dH - H (H . dH)) rh with dH = dndh n;
+          // dndh is non-zero only where ndh = n . H > 0, so H . dH = dndh ndh and
+          // dL = (dndl + dndh rh) n - (dndh ndh rh) H
+          const float cn = dndl + dndh * rh, ch = dndh * ndh * rh;
+          float dL[3] = {cn * n[0] - ch * H[0], cn * n[1] - ch * H[1], cn * n[2] - ch * H[2]};
           if (sh.light_type != 1) {
             dI[l] += dE * S * (rinv * rinv) * vis;
             const float dd2 = -dE * I * S * (rinv * rinv) * (rinv * rinv);
@@ -262,8 +261,11 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
               const float ds = dE * I * (rinv * rinv) * dS;
               for (int k = 0; k < 3; k++) dL[k] -= ds * sh.la[l][k];
             }
+            // through L = Lv / |Lv|: (dL - L (L . dL)) rinv = dL rinv - Lv (L . dL) rinv^2, plus the
+            // inverse-square law's 2 dd2 Lv
             const float ld = L[0] * dL[0] + L[1] * dL[1] + L[2] * dL[2];
-            for (int k = 0; k < 3; k++) dlv[l][k] += (dL[k] - L[k] * ld) * rinv + 2.0f * dd2 * Lv[k];
+            const float cl = 2.0f * dd2 - ld * (rinv * rinv);
+            for (int k = 0; k < 3; k++) dlv[l][k] += dL[k] * rinv + cl * Lv[k];
           } else {
             dI[l] += dE * vis;
             for (int k = 0; k < 3; k++) dlv[l][k] += dL[k];
