@@ -228,16 +228,16 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
           const float ndl_raw = n[0] * L[0] + n[1] * L[1] + n[2] * L[2];
           const bool lit = ndl_raw > 0.0f;
           const float ndl = lit ? ndl_raw : 0.0f;
-          float pw = 0.0f, ndh = 0.0f, H[3] = {0.0f, 0.0f, 0.0f}, rh = 0.0f;
+          // the half vector Hv = L + V and its reciprocal length rh (H = Hv rh is not formed)
+          float pw = 0.0f, ndh = 0.0f, Hv[3] = {0.0f, 0.0f, 0.0f}, rh = 0.0f;
           bool has_h = false;
           if (lit) {
-            float Hv[3] = {L[0] + Vv[0], L[1] + Vv[1], L[2] + Vv[2]};
-            float h2 = Hv[0] * Hv[0] + Hv[1] * Hv[1] + Hv[2] * Hv[2];
+            for (int k = 0; k < 3; k++) Hv[k] = L[k] + Vv[k];
+            const float h2 = Hv[0] * Hv[0] + Hv[1] * Hv[1] + Hv[2] * Hv[2];
             if (h2 > 0.0f) {
               has_h = true;
               rh = rsqrt_approx(h2);
-              for (int k = 0; k < 3; k++) H[k] = Hv[k] * rh;
-              ndh = fmaxf(0.0f, n[0] * H[0] + n[1] * H[1] + n[2] * H[2]);
+              ndh = fmaxf(0.0f, (n[0] * Hv[0] + n[1] * Hv[1] + n[2] * Hv[2]) * rh);
               pw = lobe_pow(ndh, m[4]);
             }
           }
@@ -250,12 +250,13 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
           const float dndh = (has_h && ndh > 0.0f) ? scale * E * G * m[3] * m[4] * __fdividef(pw, ndh) : 0.0f;
           // through the half vector's normalisation, dL = dndl n + (dH - H (H . dH)) rh with dH = dndh n;
           // dndh is non-zero only where ndh = n . H > 0, so H . dH = dndh ndh and
-          // dL = (dndl + dndh rh) n - (dndh ndh rh) H
-          const float cn = dndl + dndh * rh, ch = dndh * ndh * rh;
-          float dL[3] = {cn * n[0] - ch * H[0], cn * n[1] - ch * H[1], cn * n[2] - ch * H[2]};
+          // dL = (dndl + dndh rh) n - (dndh ndh rh) H = (dndl + dndh rh) n - (dndh ndh rh^2) Hv
+          const float cn = dndl + dndh * rh, ch = dndh * ndh * (rh * rh);
+          float dL[3] = {cn * n[0] - ch * Hv[0], cn * n[1] - ch * Hv[1], cn * n[2] - ch * Hv[2]};
           if (sh.light_type != 1) {
-            dI[l] += dE * S * (rinv * rinv) * vis;
-            const float dd2 = -dE * I * S * (rinv * rinv) * (rinv * rinv);
+            const float r2 = rinv * rinv;
+            dI[l] += dE * S * r2 * vis;
+            const float dd2 = -dE * E * r2;  // (E = I S r2)
             // spot: t = -(L . a) / (cos_i - cos_o) + ..., so dE/dL = -I |Lv|^-2 S'(t) la_xyz
             if (sh.light_type == 2) {
               const float ds = dE * I * (rinv * rinv) * dS;
