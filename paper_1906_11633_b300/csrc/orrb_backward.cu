@@ -295,7 +295,8 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
       const bool mine = mat == mm;
       const float v = warp_sum4(mine ? dm[0] : 0.0f, mine ? dm[1] : 0.0f, mine ? dm[2] : 0.0f,
                                 mine ? dm[3] : 0.0f, lane);
-      const float v4 = warp_sum(mine ? dm[4] : 0.0f);
+      // (the emission sums only when the caller asked for their gradients)
+      const float v4 = bp.d_emission ? warp_sum(mine ? dm[4] : 0.0f) : 0.0f;
       if ((lane & 7) == 0) sh.wmat[warp][mm][lane >> 3] += v;
       if (lane == 0) sh.wmat[warp][mm][4] += v4;
       pending &= ~__ballot_sync(kFull, mine);
