@@ -361,6 +361,16 @@ def run_ours(args, world, rank, local):
     plain_ms = max_over_ranks(float(np.sum(pper)), world) / psteps
     plain_value = world * N_SAMPLES / (plain_ms / 1e3)
 
+    # -- staged: the same three kernels launched once each over the whole batch (a non-fused
+    # comparison without the per-sample launch overhead of the plain mode) ----------------------
+    scfg = config(mode=L.ORRB_MODE_STAGED, tile_w=args.tile_w, tile_h=args.tile_h, threads=args.threads)
+    ssteps = max(3, args.steps // 10)
+    sper = timed(lambda: r.render(db, out=out, cfg=scfg), ssteps, min(args.warmup, 3))
+    staged_ms = max_over_ranks(float(np.sum(sper)), world) / ssteps
+    staged_value = world * N_SAMPLES / (staged_ms / 1e3)
+    staged_ok = bool(all(torch.equal(a, b) for a, b in zip(
+        r.render(db, cfg=scfg).values(), r.render(db, cfg=cfg).values())))
+
     # -- e2e through host buffers: the capture pipeline (Sec. 4.4) -------------------
     # every step copies its parameters from pinned host memory, renders, and reads all
     # four channels back to pinned host memory; consecutive steps overlap (render of
@@ -455,6 +465,11 @@ def run_ours(args, world, rank, local):
             "plain": {"value": plain_value, "ms_per_step": plain_ms, "steps": psteps,
                       "launches_per_step": 3 * N_SAMPLES},
             "fused_over_plain": value / plain_value,
+            "staged": {"value": staged_value, "ms_per_step": staged_ms, "steps": ssteps,
+                       "launches_per_step": 3, "outputs_equal_fused": staged_ok,
+                       "how": "every image's geometry, then every image's binning, then the raster: "
+                              "three batch-wide launches of the plain kernels, one scratch slot per image"},
+            "fused_over_staged": value / staged_value,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "ms_per_step": e2e_ms, "steps": esteps, "readback_ok": bool(ok),
                     "how": "CapturePipeline: 2 round-robin slots, H2D + render on one stream, bulk D2H of all "

@@ -261,9 +261,14 @@ typedef struct {
 
 #define ORRB_MODE_FUSED 0  /* one persistent launch over all images (work queue) */
 #define ORRB_MODE_PLAIN 1  /* three launches (setup, bin, raster+shade) per sample */
+#define ORRB_MODE_STAGED 2 /* the same three kernels, each launched once over a chunk of the batch's
+                              images (every image's geometry, then binning, then raster+shade); a
+                              chunk holds as many images as fit in 8 GiB of scratch, at least two
+                              per SM.  Same outputs as the other modes; for comparison with the
+                              fused launch */
 
 typedef struct {
-  int32_t mode;          /* ORRB_MODE_FUSED or ORRB_MODE_PLAIN */
+  int32_t mode;          /* ORRB_MODE_FUSED, ORRB_MODE_PLAIN or ORRB_MODE_STAGED */
   int32_t tile_w;        /* screen-tile width in pixels, multiple of 8 in [8, 512]; 0 = 256 (a narrower image uses its width) */
   int32_t tile_h;        /* screen-tile height in pixels, in [1, 64], tile_w * tile_h <= 8192; 0 = 2 */
   int32_t threads;       /* threads per CTA: 256 or 512; 0 = 512 */

@@ -189,7 +189,8 @@ void resolve_config(const orrb_config* in, orrb_config* out) {
 }
 
 orrb_status check_config(orrb_ctx* ctx, const orrb_config& c) {
-  if (c.mode != ORRB_MODE_FUSED && c.mode != ORRB_MODE_PLAIN) return fail(ctx, ORRB_ERR_INVALID_ARG, "bad mode %d", c.mode);
+  if (c.mode != ORRB_MODE_FUSED && c.mode != ORRB_MODE_PLAIN && c.mode != ORRB_MODE_STAGED)
+    return fail(ctx, ORRB_ERR_INVALID_ARG, "bad mode %d", c.mode);
   if (c.tile_w < 8 || c.tile_w > 512 || c.tile_w % 8) return fail(ctx, ORRB_ERR_INVALID_ARG, "tile_w %d", c.tile_w);
   if (c.tile_h < 1 || c.tile_h > 64) return fail(ctx, ORRB_ERR_INVALID_ARG, "tile_h %d", c.tile_h);
   if (c.tile_w * c.tile_h > 8192) return fail(ctx, ORRB_ERR_INVALID_ARG, "tile larger than 8192 px");
@@ -265,6 +266,14 @@ orrb_status plan(orrb_ctx* ctx, const orrb_batch_shape& s, const orrb_config& c,
     if (fit <= 0) return fail(ctx, ORRB_ERR_CUDA, "occupancy query failed for %zu B shared memory", P->smem);
     P->ctas_per_sm = c.ctas_per_sm > 0 ? std::min(c.ctas_per_sm, fit) : fit;
     P->n_slots = ctx->sm_count * P->ctas_per_sm;
+  } else if (c.mode == ORRB_MODE_STAGED) {
+    // one slot per image of a chunk: every image of the launch (and every shadow map of the shadow
+    // pass) while the slots fit in 8 GiB, else chunks of that many, at least two images per SM
+    P->ctas_per_sm = 0;
+    const long long images = std::max<long long>(
+        std::max(s.n_cams, 1), s.shadow_res > 0 ? (long long)s.n_samples * kMaxLights * faces_of(s) : 1);
+    const long long fit = (long long)((size_t(8) << 30) / std::max<size_t>(P->slot_bytes, 1));
+    P->n_slots = (int)std::min(images, std::max(fit, 2LL * ctx->sm_count));
   } else {
     P->ctas_per_sm = 0;
     P->n_slots = std::max(std::max(s.max_cams_per_sample, 1), s.shadow_res > 0 ? kMaxLights * faces_of(s) : 1);
@@ -358,7 +367,7 @@ orrb_status enqueue_render(orrb_ctx* ctx, Params& p, const orrb_batch_shape& s, 
     q.depth = p.shadow_map;
     q.total_pixels = (int64_t)q.n_cams * s.shadow_res * s.shadow_res;
     q.w_max = q.h_max = s.shadow_res;
-    const int n_ctas = mode == ORRB_MODE_FUSED ? std::min(n_slots, std::max(q.n_cams, 1)) : 0;
+    const int n_ctas = mode != ORRB_MODE_PLAIN ? std::min(n_slots, std::max(q.n_cams, 1)) : 0;
     q.n_slots = n_ctas;
     if (launch_render(q, mode, threads, n_ctas, kMaxLights * p.shadow_faces, stream, err, sizeof(err)))
       return fail(ctx, ORRB_ERR_CUDA, "%s", err);
@@ -368,8 +377,10 @@ orrb_status enqueue_render(orrb_ctx* ctx, Params& p, const orrb_batch_shape& s, 
     cudaError_t e = cudaMemsetAsync(ws + 4, 0, 8, st);
     if (e != cudaSuccess) return fail(ctx, ORRB_ERR_CUDA, "queue reset: %s", cudaGetErrorString(e));
   }
-  Range r(!trace ? nullptr : mode == ORRB_MODE_FUSED ? "orrb camera launch (fused)" : "orrb camera launches (plain)");
-  const int n_ctas = mode == ORRB_MODE_FUSED ? std::min(n_slots, std::max(s.n_cams, 1)) : 0;
+  Range r(!trace ? nullptr
+                 : mode == ORRB_MODE_FUSED ? "orrb camera launch (fused)"
+                 : mode == ORRB_MODE_STAGED ? "orrb camera launches (staged)" : "orrb camera launches (plain)");
+  const int n_ctas = mode != ORRB_MODE_PLAIN ? std::min(n_slots, std::max(s.n_cams, 1)) : 0;
   p.n_slots = n_ctas;
   if (launch_render(p, mode, threads, n_ctas, std::max(s.max_cams_per_sample, 1), stream, err, sizeof(err)))
     return fail(ctx, ORRB_ERR_CUDA, "%s", err);
@@ -576,6 +587,7 @@ orrb_status orrb_render_batch(orrb_ctx* ctx, const orrb_batch_shape* shape, cons
   p.shadow_nb = p.shadow_res > 0 ? reinterpret_cast<uint32_t*>(ws + P.nb_offset) : nullptr;
   p.shadow_cnt = p.shadow_res > 0 ? reinterpret_cast<uint8_t*>(ws + P.cnt_offset) : nullptr;
   p.plain_sample = -1;
+  p.stage_base = 0;
   // ambient occlusion and bloom: the camera launch writes the linear colour, depth and normals
   // (the caller's outputs where given, else the workspace's) and neither grades nor quantises; the
   // post pass then writes rgb and the graded colour
@@ -682,6 +694,7 @@ orrb_status orrb_render_batch_noalloc(orrb_ctx* ctx, const orrb_batch_shape* sha
   p.slot_bytes = P.slot_bytes;
   p.wait_cycles = c.wait_cycles;
   p.plain_sample = -1;
+  p.stage_base = 0;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // the array keeps the previous call's contents: the status word and the queue counters restart at zero
   cudaError_t e = cudaMemsetAsync(ws, 0, 16, s);

@@ -114,9 +114,13 @@ struct Params {
   size_t slot_bytes;
   int32_t n_slots;
   long long wait_cycles;  // bounded waits between CTAs give up after this many SM cycles
-  // plain mode: the sample this launch renders (-1 in fused mode)
+  // plain mode: the sample this launch renders (-1 in fused mode, kStagedLaunch in staged mode)
   int32_t plain_sample;
+  int32_t stage_base;  // staged mode: the first image of this launch's chunk
 };
+
+// plain_sample of a staged launch: its CTAs take images stage_base + blockIdx.x.
+constexpr int32_t kStagedLaunch = -2;
 
 // Per-slot scratch (one image at a time): sizes in elements, from t_max.
 struct SlotLayout {

@@ -53,6 +53,7 @@ namespace {
 constexpr unsigned long long kEmpty = ~0ull;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kPlainRasterSplit = 8;  // plain mode: CTAs sharing one image's tiles
+constexpr int kStagedRasterSplit = 2;  // staged mode (measured: 1, 2, 4, 8 -> 2 fastest)
 // optional features of a batch, each compiled into kernel instances of its own
 constexpr int kFeatGrade = 1;  // colour grading of the rgb output
 constexpr int kFeatTrack = 2;  // tracker rows
@@ -1834,10 +1835,16 @@ __global__ void __launch_bounds__(512, 2) render_fused_kernel(Params p) {
 
 // ---------------------------------------------------------------------------
 // plain: three launches per sample; scratch slot = camera index within the sample
+// (in the shadow pass: the sample's map blockIdx.x, light-major then face).
+// staged: the same three kernels, each launched once over a chunk of the batch's images
+// (image stage_base + blockIdx.x; scratch slot = blockIdx.x).
 // ---------------------------------------------------------------------------
-// (in the shadow pass: the sample's map blockIdx.x, light-major then face)
 __device__ inline int plain_cam(const Params& p) {
   const int s = p.plain_sample;
+  if (s == kStagedLaunch) {
+    const int c = p.stage_base + int(blockIdx.x);
+    return c < p.n_cams ? c : -1;
+  }
   if (p.shadow_pass) {
     const int per = kMaxLights * p.shadow_faces;
     return int(blockIdx.x) < per ? s * per + int(blockIdx.x) : -1;
@@ -2055,15 +2062,20 @@ int launch_render(const Params& p, int mode, int threads, int n_ctas, int max_ca
     const int which[3] = {13 + g, 16, 20 + plain_raster_slot(f)};
     for (int k = 0; k < 3 && e == cudaSuccess; k++) e = ensure_smem(ks[k], which[k], smem);
     Params q = p;
-    const dim3 grid(max_cams_per_sample, kPlainRasterSplit);
-    for (int s = 0; s < p.n_samples && e == cudaSuccess; s++) {
-      q.plain_sample = s;
+    // plain: one sample's images per launch; staged: a chunk of n_ctas images per launch
+    const bool staged = mode == 2;
+    const int per = staged ? n_ctas : max_cams_per_sample;
+    const int n_launches = staged ? (p.n_cams + n_ctas - 1) / n_ctas : p.n_samples;
+    const dim3 grid(per, staged ? kStagedRasterSplit : kPlainRasterSplit);
+    for (int s = 0; s < n_launches && e == cudaSuccess; s++) {
+      q.plain_sample = staged ? kStagedLaunch : s;
+      q.stage_base = staged ? s * n_ctas : 0;
       switch (g) {
-        case 1: plain_geometry_kernel<1><<<max_cams_per_sample, threads, smem, st>>>(q); break;
-        case 2: plain_geometry_kernel<2><<<max_cams_per_sample, threads, smem, st>>>(q); break;
-        default: plain_geometry_kernel<0><<<max_cams_per_sample, threads, smem, st>>>(q); break;
+        case 1: plain_geometry_kernel<1><<<per, threads, smem, st>>>(q); break;
+        case 2: plain_geometry_kernel<2><<<per, threads, smem, st>>>(q); break;
+        default: plain_geometry_kernel<0><<<per, threads, smem, st>>>(q); break;
       }
-      plain_bin_kernel<<<max_cams_per_sample, threads, smem, st>>>(q);
+      plain_bin_kernel<<<per, threads, smem, st>>>(q);
       switch (kPlainRasterSets[plain_raster_slot(f)]) {
         case 0: plain_raster_kernel<0><<<grid, threads, smem, st>>>(q); break;
         case 1: plain_raster_kernel<1><<<grid, threads, smem, st>>>(q); break;

@@ -23,6 +23,7 @@ ORRB_ERR_UNSUPPORTED = 6
 ORRB_ERR_DEVICE = 7
 ORRB_MODE_FUSED = 0
 ORRB_MODE_PLAIN = 1
+ORRB_MODE_STAGED = 2
 ORRB_MAX_LIGHTS = 4
 ORRB_MAX_MATERIALS = 32
 ORRB_GBUFFER_PLANES = 7

@@ -51,7 +51,7 @@ def test_tiny_matches_oracle(tiny_renderer, oracle):
     assert st["depth_exact"] > 0.999
 
 
-@pytest.mark.parametrize("mode", [L.ORRB_MODE_FUSED, L.ORRB_MODE_PLAIN])
+@pytest.mark.parametrize("mode", [L.ORRB_MODE_FUSED, L.ORRB_MODE_PLAIN, L.ORRB_MODE_STAGED])
 def test_hand_full_batch_matches_oracle(hand_renderer, oracle, mode):
     b = sg.hand_batch(0, np.arange(256))
     st = compare(render_np(hand_renderer, b, config(mode=mode)), oracle.render(b, debug=True), "hand")
@@ -110,9 +110,12 @@ def test_bit_identical_across_tilings_and_modes(hand_renderer, tile, threads):
     got = render_np(hand_renderer, b, config(tile_w=tile[0], tile_h=tile[1], threads=threads))
     plain = render_np(hand_renderer, b, config(mode=L.ORRB_MODE_PLAIN, tile_w=tile[0], tile_h=tile[1],
                                                threads=threads))
+    staged = render_np(hand_renderer, b, config(mode=L.ORRB_MODE_STAGED, tile_w=tile[0], tile_h=tile[1],
+                                                threads=threads))
     for k in ref:
         np.testing.assert_array_equal(got[k], ref[k], err_msg=k)
         np.testing.assert_array_equal(plain[k], ref[k], err_msg=k)
+        np.testing.assert_array_equal(staged[k], ref[k], err_msg=k)
 
 
 def test_sample_alone_equals_sample_in_batch(hand_renderer):
@@ -391,7 +394,8 @@ def test_lights_that_light_nothing_are_flagged(hand_renderer, oracle):
 
 
 @pytest.mark.parametrize("mode,kind", [(L.ORRB_MODE_FUSED, "spot"), (L.ORRB_MODE_PLAIN, "spot"),
-                                       (L.ORRB_MODE_FUSED, "cube"), (L.ORRB_MODE_PLAIN, "cube")])
+                                       (L.ORRB_MODE_STAGED, "spot"), (L.ORRB_MODE_FUSED, "cube"),
+                                       (L.ORRB_MODE_PLAIN, "cube"), (L.ORRB_MODE_STAGED, "cube")])
 def test_shadow_maps_and_lookups_match_oracle(hand_renderer, oracle, mode, kind):
     """Shadow maps of the benchmark-like scene's spot lights (one face each) and of the hand scene's
     point lights (six cube faces each): every map of a casting face bit-identical to the oracle's
@@ -429,12 +433,12 @@ def test_shadow_maps_and_lookups_match_oracle(hand_renderer, oracle, mode, kind)
 @pytest.mark.parametrize("shadows", [True, False])
 def test_option_combinations_with_tracker_rows_match_oracle(hand_renderer, oracle, grading, shadows):
     """Tracker rows together with spot lights, emission, colour grading and shadow maps, each
-    combination its own kernel instance, fused and plain: channels, G-buffer words, maps and
+    combination its own kernel instance, fused, plain and staged: channels, G-buffer words, maps and
     tracker rows against the oracle."""
     b = sg.benchmark_batch(41, np.arange(6), res=80, grading=grading, shadow_res=96 if shadows else 0)
     o = oracle.render(b, debug=True, gbuffer=True, tracker=True)
     cast = np.arange(4)[None, :] < b.light_meta[:, :1]
-    for cfg in (config(), config(mode=L.ORRB_MODE_PLAIN)):
+    for cfg in (config(), config(mode=L.ORRB_MODE_PLAIN), config(mode=L.ORRB_MODE_STAGED)):
         g = render_np(hand_renderer, b, cfg, gbuffer=True, tracker=True)
         compare(g, o, "options")
         np.testing.assert_array_equal(g["tracker"], o["tracker"])

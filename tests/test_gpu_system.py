@@ -3,7 +3,8 @@
 - a captured graph replays to the same channels as a direct render, and again after new
   batch contents of the same shapes are copied in;
 - the uneven batch (mixed triangle counts and resolutions) renders in one persistent launch
-  and matches per-scene plain launches bit for bit;
+  and matches per-scene plain launches and batch-wide staged launches (in chunks when the
+  scratch slots do not all fit) bit for bit;
 - the autotuner returns a configuration whose output equals the default's and caches it;
 - served requests: each result equals the same request rendered alone, and batches overlap.
 """
@@ -74,6 +75,10 @@ def test_uneven_batch_in_one_launch_matches_plain_launches(renderer):
     torch.cuda.synchronize()
     assert renderer.status() == 0
     _equal(fused, plain)
+    staged = renderer.render(db, cfg=config(mode=L.ORRB_MODE_STAGED))  # (every image in one chunk)
+    torch.cuda.synchronize()
+    assert renderer.status() == 0
+    _equal(fused, staged)
 
 
 def test_autotuner_result_is_valid_and_cached(renderer, tmp_path):
@@ -201,3 +206,22 @@ def test_served_requests_with_bad_input_fail_alone():
     alone = solo.render(solo.upload(batches[4]))
     torch.cuda.synchronize()
     _equal(reqs[4].result, alone)
+
+
+def test_staged_chunks_match_the_fused_launch(renderer):
+    """The uneven batch's 2,072 images in the staged mode: with up to 50k triangles per scene the
+    scratch slots do not all fit in the staged mode's budget, so the launches run over chunks of
+    the images; every channel equals the fused launch's bit for bit (compared on the device)."""
+    b = sg.uneven_batch(0, np.arange(1024))
+    db = renderer.upload(b)
+    fused = renderer.render(db)
+    staged = renderer.render(db, cfg=config(mode=L.ORRB_MODE_STAGED))
+    torch.cuda.synchronize()
+    assert renderer.status() == 0
+    # the plain mode holds one slot per camera of a scene: its workspace gives a slot's size
+    per_scene = int(db.shape.max_cams_per_sample)
+    slot = (L.orrb_workspace_size(renderer.ctx, db.shape, config(mode=L.ORRB_MODE_PLAIN)) - 256) // per_scene
+    chunk = (L.orrb_workspace_size(renderer.ctx, db.shape, config(mode=L.ORRB_MODE_STAGED)) - 256) // slot
+    assert 0 < chunk < b.n_cams  # several chunks
+    for k in fused:
+        assert torch.equal(fused[k], staged[k]), k
