@@ -477,7 +477,8 @@ def run_ours(args, world, rank, local):
             "gpu_launches": args.steps,
             "roofline": roof,
             "uneven": None if uneven is None else {
-                k: uneven[k] for k in ("value", "ms_per_step", "fused_over_plain", "plain", "device_status")} | {
+                k: uneven[k] for k in ("value", "ms_per_step", "fused_over_plain", "plain", "fused_over_staged", "staged",
+                                       "device_status")} | {
                 "config": {k: uneven["config"][k] for k in ("scenes", "images", "pixels", "triangles_per_scene", "tile",
                                                              "threads")}},
             "serve": None if serve is None else {
@@ -541,6 +542,22 @@ def measure_uneven(args, world, rank, local):
     e1.record(stream)
     torch.cuda.synchronize()
     plain_ms = max_over_ranks(e0.elapsed_time(e1), world)
+    # staged: the plain kernels once each over chunks of the images (the slots of every image do not
+    # fit the staged mode's scratch budget at 50k triangles per scene)
+    scfg = config(mode=L.ORRB_MODE_STAGED, tile_w=cfg.tile_w, tile_h=cfg.tile_h, threads=cfg.threads)
+    r.render(db, out=out, cfg=scfg)
+    torch.cuda.synchronize()
+    sper = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r.render(db, out=out, cfg=scfg)
+        e1.record(stream)
+        sper.append((e0, e1))
+    torch.cuda.synchronize()
+    staged_ms = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in sper])), world)
+    slot = (L.orrb_workspace_size(r.ctx, db.shape, pcfg) - 256) // max(1, int(db.shape.max_cams_per_sample))
+    chunk = max(1, (L.orrb_workspace_size(r.ctx, db.shape, scfg) - 256) // slot)
     if rank != 0:
         return None
     peaks, _ = load_peaks()
@@ -553,6 +570,9 @@ def measure_uneven(args, world, rank, local):
             "plain": {"value": world * n / (plain_ms / 1e3), "ms_per_step": plain_ms,
                       "launches_per_step": 3 * n},
             "fused_over_plain": plain_ms / ms,
+            "staged": {"value": world * n / (staged_ms / 1e3), "ms_per_step": staged_ms,
+                       "launches_per_step": 3 * -(-batch.n_cams // chunk), "images_per_chunk": int(chunk)},
+            "fused_over_staged": staged_ms / ms,
             "roofline": {"bound": "hbm", "achieved": alg_bytes / (ms / 1e3) / 1e9, "peak": float(peaks["hbm_gbs"]),
                          "unit": "GB/s", "frac": alg_bytes / (ms / 1e3) / 1e9 / float(peaks["hbm_gbs"]),
                          "alg_bytes_per_launch": alg_bytes},
