@@ -806,7 +806,7 @@ def measure_serve(seconds, world, rank, local):
     wreqs = sg.poisson_requests(SEED + 1000 + rank, rate, 0.5)
     wbatches = [sg.request_batch(SEED + 1000, q, meshes=meshes) for q in wreqs]
     warm = Server(be, n_streams=2, max_inflight=4, tick_ms=2.0)
-    run_poisson(warm, wreqs, wbatches, 0.5)
+    run_poisson(warm, wreqs, wbatches, 0.5, keep_results=False)
     warm.close()
     del wreqs, wbatches, warm
     # the requests' arrays are long-lived: move them out of the collector's generations so that a
@@ -816,7 +816,7 @@ def measure_serve(seconds, world, rank, local):
     gc.freeze()
     try:
         srv = Server(be, n_streams=2, max_inflight=4, tick_ms=2.0)
-        subs, wall = run_poisson(srv, reqs, batches, dur)
+        subs, wall = run_poisson(srv, reqs, batches, dur, keep_results=False)
         st = srv.stats(wall)
         srv.close()
     finally:
@@ -830,7 +830,8 @@ def measure_serve(seconds, world, rank, local):
             "max_concurrent_batches": st["max_concurrent_batches"], "memory_waits": st["memory_waits"],
             "config": {"rate_hz": rate, "seconds": dur, "tick_ms": 2.0, "streams": 2, "max_inflight": 4,
                        "request_samples": "U{1..64}", "resolution": list(sg.SERVE_RES), "cameras": "U{1..3}",
-                       "host_generation_s": gen_s, "gc": "collected and frozen before the run"}}
+                       "host_generation_s": gen_s, "gc": "collected and frozen before the run",
+                       "client": "drops each request's outputs once it has completed"}}
     return line
 
 

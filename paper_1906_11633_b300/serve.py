@@ -25,7 +25,7 @@ import itertools
 import threading
 import time
 from dataclasses import dataclass, field
-from typing import Any, Dict, List, Optional
+from typing import Any, Dict, List, Optional, Tuple
 
 import numpy as np
 
@@ -72,7 +72,9 @@ class Server:
         self.inflight_bytes = 0
         self.per_stream: List[collections.deque] = [collections.deque() for _ in range(n_streams)]
         self.stream_cv = [threading.Condition() for _ in range(n_streams)]
-        self.completed: List[ServeRequest] = []
+        # (request id, latency ms, samples) of every completed request: only what stats() reads, so
+        # that a long-running server holds no request's outputs once its caller has dropped them
+        self.completed: List[Tuple[int, float, int]] = []
         self.failed: List[ServeRequest] = []   # requests whose batch failed to launch or to render
         self.max_concurrent = 0
         self.launching = 0    # batches taken from `pending` whose launch has not been recorded yet
@@ -205,7 +207,10 @@ class Server:
                 with self.lock:
                     self.inflight.pop(fl.batch_id, None)
                     self.inflight_bytes -= fl.nbytes
-                    (self.failed if error else self.completed).extend(fl.requests)
+                    if error:
+                        self.failed.extend(fl.requests)
+                    else:
+                        self.completed.extend((r.rid, r.latency_ms, r.batch.n_samples) for r in fl.requests)
                 for r in fl.requests:      # signal only once the bookkeeping is visible to stats()
                     r.event.set()
 
@@ -224,8 +229,8 @@ class Server:
         with self.lock:  # a consistent snapshot while batches may still complete
             done, n_failed = list(self.completed), len(self.failed)
             batches, conc, waits = self.batches_launched, self.max_concurrent, self.rejected_for_memory
-        lat = np.array([r.latency_ms for r in done]) if done else np.zeros(1)
-        samples = sum(r.batch.n_samples for r in done)
+        lat = np.array([ms for _, ms, _ in done]) if done else np.zeros(1)
+        samples = sum(ns for _, _, ns in done)
         return {"requests": len(done), "samples": samples, "samples_per_s": samples / wall_s,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "max_ms": float(lat.max()), "batches": batches, "failed": n_failed,
@@ -399,15 +404,26 @@ class GpuBackend:
             self._put_stage(stage)
 
 
-def run_poisson(server: Server, requests, batches, duration_s: float, warmup_s: float = 0.0):
-    """Submit `batches[i]` at arrival time `requests[i].arrival_s`; returns (submitted ServeRequests, wall seconds)."""
+def run_poisson(server: Server, requests, batches, duration_s: float, warmup_s: float = 0.0,
+                keep_results: bool = True):
+    """Submit `batches[i]` at arrival time `requests[i].arrival_s`; returns (submitted ServeRequests, wall seconds).
+    With keep_results=False the client drops each request's outputs as soon as the request has
+    completed (a client that consumes its results), so the device memory of finished batches
+    returns to the allocator during the run; latencies and errors are kept."""
     t0 = time.perf_counter()
     subs = []
+    oldest = 0  # the first request whose outputs may still be held
     for req, b in zip(requests, batches):
         delay = t0 + req.arrival_s - time.perf_counter()
         if delay > 0:
             time.sleep(delay)
         subs.append(server.submit(ServeRequest(req.rid, b)))
+        if not keep_results:
+            while oldest < len(subs) and subs[oldest].event.is_set():
+                subs[oldest].result = None
+                oldest += 1
     for s in subs:
         s.event.wait(timeout=60.0)
+        if not keep_results:
+            s.result = None
     return subs, time.perf_counter() - t0

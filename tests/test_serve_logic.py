@@ -67,7 +67,7 @@ def test_every_request_completes_within_budget_and_batches_overlap():
         assert r.event.wait(10.0)
     st = srv.stats(1.0)
     srv.close()
-    assert st["requests"] == 40 and len({r.rid for r in srv.completed}) == 40
+    assert st["requests"] == 40 and len({rid for rid, _, _ in srv.completed}) == 40
     assert all(r.result["n"] == r.batch.n_samples for r in reqs)
     assert be.peak_bytes <= be.budget
     assert 2 <= be.peak_active <= 3
