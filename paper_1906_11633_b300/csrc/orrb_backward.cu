@@ -287,7 +287,16 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_partial_kernel(Backwa
         gsum[12] += (gp[0] + gp[1] + gp[2]) * grain_centred(sh.gkey, unsigned(i));
       }
     }
-    // segmented warp reduction over the materials present in these 32 pixels
+    // segmented warp reduction over the materials present in these 32 pixels; a warp on one
+    // material (most steps: the table) reduces once without the segment search
+    const int mat0 = __shfl_sync(kFull, mat, 0);
+    if (__all_sync(kFull, mat == mat0) && mat0 >= 0) {
+      const float v = warp_sum4(dm[0], dm[1], dm[2], dm[3], lane);
+      const float v4 = bp.d_emission ? warp_sum(dm[4]) : 0.0f;
+      if ((lane & 7) == 0) sh.wmat[warp][mat0][lane >> 3] += v;
+      if (lane == 0) sh.wmat[warp][mat0][4] += v4;
+      continue;
+    }
     unsigned pending = __ballot_sync(kFull, mat >= 0);
     while (pending) {
       const int leader = __ffs(pending) - 1;
