@@ -90,13 +90,15 @@ def test_zero_intensities_give_the_unprocessed_bits(renderer):
         np.testing.assert_array_equal(zero[k], plain[k], err_msg=k)
 
 
-def test_plain_mode_and_workspace_images_agree(renderer):
+def test_plain_and_staged_modes_and_workspace_images_agree(renderer):
     b = sg.benchmark_batch(24, np.arange(4), res=72, post=True)
     db = renderer.upload(b)
     fused = to_numpy(renderer.render(db, rgb_linear=True, rgb_graded=True))
     plain = to_numpy(renderer.render(db, cfg=config(mode=L.ORRB_MODE_PLAIN), rgb_linear=True, rgb_graded=True))
+    staged = to_numpy(renderer.render(db, cfg=config(mode=L.ORRB_MODE_STAGED), rgb_linear=True, rgb_graded=True))
     for k in fused:
         np.testing.assert_array_equal(plain[k], fused[k], err_msg=k)
+        np.testing.assert_array_equal(staged[k], fused[k], err_msg=k)
     # only rgb requested: depth, normal and the linear colour live in the workspace
     out = renderer.alloc_outputs(b.total_pixels)
     rgb_only = {"rgb": out["rgb"]}
