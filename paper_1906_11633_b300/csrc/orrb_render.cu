@@ -2063,7 +2063,7 @@ int launch_render(const Params& p, int mode, int threads, int n_ctas, int max_ca
     for (int k = 0; k < 3 && e == cudaSuccess; k++) e = ensure_smem(ks[k], which[k], smem);
     Params q = p;
     // plain: one sample's images per launch; staged: a chunk of n_ctas images per launch
-    const bool staged = mode == 2;
+    const bool staged = mode == ORRB_MODE_STAGED;
     const int per = staged ? n_ctas : max_cams_per_sample;
     const int n_launches = staged ? (p.n_cams + n_ctas - 1) / n_ctas : p.n_samples;
     const dim3 grid(per, staged ? kStagedRasterSplit : kPlainRasterSplit);
